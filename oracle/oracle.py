@@ -1,0 +1,253 @@
+"""Python driver for the FP64 CPU oracle (``lgs_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module; the product path
+never does.  It shares no code with the CUDA library: it builds its own shared
+object with gcc and passes plain NumPy arrays through ctypes.
+
+What the oracle computes follows the paper's map representation (Sec. 3.1)
+and map optimisation (Sec. 3.4, Eqs. depthloss, normalloss, scaleloss,
+totalloss); binning and the depth key are specified in binary32, everything
+else is FP64 (see ``lgs_oracle.c``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lgs_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liblgs_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+# Loss weights of the paper's implementation details (Sec. 4.1): lambda_alpha,
+# lambda_n, lambda_s, lambda_{n,g}; lambda_{n,s} multiplies the N_surf term,
+# which is off on this path.
+LAMBDA_ALPHA = 0.1
+LAMBDA_N = 1.0
+LAMBDA_S = 10.0
+LAMBDA_NG = 0.05
+S_MAX = 1.0
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (binary32 binning needs -ffp-contract=off)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        i64, i32, f32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_double
+        lib.lgso_constants.argtypes = [P]
+        lib.lgso_f32_exp_spec.argtypes = [f32]; lib.lgso_f32_exp_spec.restype = f32
+        lib.lgso_f32_sin_spec.argtypes = [f32]; lib.lgso_f32_sin_spec.restype = f32
+        lib.lgso_f32_cos_spec.argtypes = [f32]; lib.lgso_f32_cos_spec.restype = f32
+        lib.lgso_f32_col_dir.argtypes = [i32, i32, P, P]
+        lib.lgso_bin_tables.argtypes = [i32, i32, i32, i32, f32, f32, P, P, P]
+        lib.lgso_bin_frame.argtypes = [P, P, i64, i32, i32, i32, i32, f32, f32, P, P, P, P, P, i64, P]
+        lib.lgso_bin_frame.restype = i64
+        lib.lgso_render_fwd.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, f64, f64, P, P, P,
+                                        P, P, P, P, P, P, P, P, i32]
+        lib.lgso_coverage_misses.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, f64, f64, P, P, P]
+        lib.lgso_coverage_misses.restype = i64
+        lib.lgso_render_bwd.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, f64, f64, P, P, P,
+                                        P, P, P, P, P, P, P, P, i32]
+        lib.lgso_loss_image.argtypes = [P, P, P, P, P, i64, f64, f64, f64, f64, P, P, P, P]
+        lib.lgso_loss_image.restype = f64
+        lib.lgso_scale_reg.argtypes = [P, i64, f64, f64, P]
+        lib.lgso_scale_reg.restype = f64
+        _lib = lib
+        return lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def constants() -> np.ndarray:
+    out = np.zeros(16, np.float64)
+    _load().lgso_constants(_p(out))
+    return out
+
+
+# --- specified binary32 helpers (exported for their own tests) --------------
+def f32_exp_spec(x: float) -> np.float32:
+    return np.float32(_load().lgso_f32_exp_spec(float(np.float32(x))))
+
+
+def f32_sin_spec(x: float) -> np.float32:
+    return np.float32(_load().lgso_f32_sin_spec(float(np.float32(x))))
+
+
+def f32_cos_spec(x: float) -> np.float32:
+    return np.float32(_load().lgso_f32_cos_spec(float(np.float32(x))))
+
+
+def f32_col_dir(c: int, W: int):
+    cs = np.zeros(1, np.float32); sn = np.zeros(1, np.float32)
+    _load().lgso_f32_col_dir(int(c), int(W), _p(cs), _p(sn))
+    return cs[0], sn[0]
+
+
+def bin_tables(frame):
+    ntr = -(-frame.H // frame.tile_h); ntc = -(-frame.W // frame.tile_w)
+    st = np.zeros(ntr, np.float32); sb = np.zeros(ntr, np.float32); c4 = np.zeros((ntc, 4), np.float32)
+    _load().lgso_bin_tables(frame.H, frame.W, frame.tile_h, frame.tile_w, float(np.float32(frame.elev_min)),
+                            float(np.float32(frame.elev_max)), _p(st), _p(sb), _p(c4))
+    return st, sb, c4
+
+
+# --- binning / sort ---------------------------------------------------------
+def bin_frame(surfels, frame, want_pairs: bool = True):
+    """Binary32 binning of one frame: depth key bits, tile counts, and the
+    (tile<<32 | depth_bits, surfel) pairs in sorted order with tile ranges."""
+    lib = _load()
+    mean = _c(surfels.mean, np.float32); ls = _c(surfels.log_scale, np.float32)
+    pose = _c(frame.pose, np.float32)
+    n = mean.shape[0]
+    ntiles = (-(-frame.H // frame.tile_h)) * (-(-frame.W // frame.tile_w))
+    depth = np.zeros(n, np.uint32); cnt = np.zeros(n, np.int32)
+    args = (frame.H, frame.W, frame.tile_h, frame.tile_w, float(np.float32(frame.elev_min)),
+            float(np.float32(frame.elev_max)), _p(pose))
+    total = lib.lgso_bin_frame(_p(mean), _p(ls), n, *args, _p(depth), _p(cnt), None, None, 0, None)
+    out = dict(depth_bits=depth, count=cnt, n_pairs=int(total))
+    if want_pairs:
+        keys = np.zeros(max(total, 1), np.uint64); vals = np.zeros(max(total, 1), np.uint32)
+        ranges = np.zeros((ntiles, 2), np.int64)
+        lib.lgso_bin_frame(_p(mean), _p(ls), n, *args, None, None, _p(keys), _p(vals), total, _p(ranges))
+        out.update(keys=keys[:total], vals=vals[:total], ranges=ranges)
+    return out
+
+
+def brute_lists(surfels, frame):
+    """All-pairs lists: every tile lists every surfel, ordered by (binary32
+    depth key, index) -- the order the tiled lists use."""
+    b = bin_frame(surfels, frame, want_pairs=False)
+    order = np.lexsort((np.arange(len(b["depth_bits"])), b["depth_bits"])).astype(np.uint32)
+    ntiles = (-(-frame.H // frame.tile_h)) * (-(-frame.W // frame.tile_w))
+    ranges = np.zeros((ntiles, 2), np.int64); ranges[:, 1] = len(order)
+    return ranges, order
+
+
+# --- FP64 forward / backward -------------------------------------------------
+def _params64(surfels):
+    return (_c(surfels.mean, np.float64), _c(surfels.quat, np.float64),
+            _c(surfels.log_scale, np.float64), _c(surfels.logit, np.float64))
+
+
+def _frame_args(frame):
+    return (frame.H, frame.W, frame.tile_h, frame.tile_w, float(np.float32(frame.elev_min)),
+            float(np.float32(frame.elev_max)), _c(np.asarray(frame.pose, np.float32), np.float64))
+
+
+def render_fwd(surfels, frame, ranges, vals, params64=None, nthreads: int = 0):
+    """FP64 forward of one frame over the given tile lists."""
+    lib = _load()
+    m, q, ls, lg = params64 if params64 is not None else _params64(surfels)
+    H, W = frame.H, frame.W
+    A = np.zeros(H * W); St = np.zeros(H * W); Sn = np.zeros(3 * H * W); Tf = np.zeros(H * W)
+    nc = np.zeros(H * W, np.int32); ne = np.zeros(H * W, np.int64); fl = np.zeros(H * W, np.uint8)
+    nv = np.zeros(H * W, np.int32)
+    fa = _frame_args(frame)
+    lib.lgso_render_fwd(_p(m), _p(q), _p(ls), _p(lg), m.shape[0], *fa[:6], _p(fa[6]),
+                        _p(_c(ranges, np.int64)), _p(_c(vals, np.uint32)),
+                        _p(A), _p(St), _p(Sn), _p(Tf), _p(nc), _p(ne), _p(fl), _p(nv), int(nthreads))
+    return dict(A=A.reshape(H, W), S_t=St.reshape(H, W), S_n=Sn.reshape(3, H, W),
+                T_final=Tf.reshape(H, W), n_contrib=nc.reshape(H, W), n_eval=ne.reshape(H, W),
+                flags=fl.reshape(H, W), n_valid=nv.reshape(H, W))
+
+
+def coverage_misses(surfels, frame, ranges, vals, params64=None) -> int:
+    """Valid (pixel, surfel) evaluations whose surfel is missing from the
+    pixel's tile list (brute force; 0 means binning is conservative)."""
+    m, q, ls, lg = params64 if params64 is not None else _params64(surfels)
+    fa = _frame_args(frame)
+    return int(_load().lgso_coverage_misses(_p(m), _p(q), _p(ls), _p(lg), m.shape[0], *fa[:6], _p(fa[6]),
+                                            _p(_c(ranges, np.int64)), _p(_c(vals, np.uint32))))
+
+
+def render_bwd(surfels, frame, ranges, vals, gA, gSt, gSn, params64=None, grads=None,
+               nthreads: int = 0):
+    """FP64 backward of one frame; accumulates into ``grads`` (dict of arrays)."""
+    lib = _load()
+    m, q, ls, lg = params64 if params64 is not None else _params64(surfels)
+    n = m.shape[0]
+    if grads is None:
+        grads = dict(mean=np.zeros((n, 3)), quat=np.zeros((n, 4)), log_scale=np.zeros((n, 2)),
+                     logit=np.zeros(n), flag=np.zeros(n, np.uint8))
+    fa = _frame_args(frame)
+    lib.lgso_render_bwd(_p(m), _p(q), _p(ls), _p(lg), n, *fa[:6], _p(fa[6]),
+                        _p(_c(ranges, np.int64)), _p(_c(vals, np.uint32)),
+                        _p(_c(gA, np.float64)), _p(_c(gSt, np.float64)), _p(_c(gSn, np.float64)),
+                        _p(grads["mean"]), _p(grads["quat"]), _p(grads["log_scale"]), _p(grads["logit"]),
+                        _p(grads["flag"]), int(nthreads))
+    return grads
+
+
+def loss_image(fwd, D, Ng, lam_alpha=LAMBDA_ALPHA, lam_n=LAMBDA_N, lam_ng=LAMBDA_NG, scale=1.0):
+    """Image terms of the mapping loss and their gradients w.r.t. (A, S_t, S_n)."""
+    lib = _load()
+    H, W = D.shape
+    npix = H * W
+    gA = np.zeros(npix); gSt = np.zeros(npix); gSn = np.zeros(3 * npix); terms = np.zeros(3)
+    L = lib.lgso_loss_image(_p(_c(fwd["A"], np.float64)), _p(_c(fwd["S_t"], np.float64)),
+                            _p(_c(fwd["S_n"], np.float64)), _p(_c(D, np.float32)), _p(_c(Ng, np.float32)),
+                            npix, lam_alpha, lam_n, lam_ng, scale, _p(gA), _p(gSt), _p(gSn), _p(terms))
+    return L, dict(dA=gA.reshape(H, W), dS_t=gSt.reshape(H, W), dS_n=gSn.reshape(3, H, W)), terms
+
+
+def scale_reg(log_scale, s_max=S_MAX, lam_s=LAMBDA_S, dls=None):
+    lib = _load()
+    ls = _c(log_scale, np.float64)
+    return lib.lgso_scale_reg(_p(ls), ls.shape[0], s_max, lam_s, _p(dls) if dls is not None else None)
+
+
+def forward_backward(surfels, frames, targets, lam_alpha=LAMBDA_ALPHA, lam_n=LAMBDA_N,
+                     lam_ng=LAMBDA_NG, lam_s=LAMBDA_S, s_max=S_MAX, params64=None, nthreads: int = 0,
+                     brute: bool = False):
+    """The whole step for a window of frames: per frame bin, render, image
+    loss (averaged over frames), backward; plus lam_s L_scale once.
+    ``targets`` is a list of (D, Ng).  Returns (L, per-frame forwards, grads, bins)."""
+    n = surfels.mean.shape[0]
+    grads = dict(mean=np.zeros((n, 3)), quat=np.zeros((n, 4)), log_scale=np.zeros((n, 2)),
+                 logit=np.zeros(n), flag=np.zeros(n, np.uint8))
+    F = len(frames)
+    L = 0.0
+    fwds, bins = [], []
+    for f, (frame, (D, Ng)) in enumerate(zip(frames, targets)):
+        if brute:
+            ranges, vals = brute_lists(surfels, frame)
+            b = dict(ranges=ranges, vals=vals)
+        else:
+            b = bin_frame(surfels, frame)
+        fw = render_fwd(surfels, frame, b["ranges"], b["vals"], params64, nthreads)
+        Lf, g, _ = loss_image(fw, D, Ng, lam_alpha, lam_n, lam_ng, scale=1.0 / F)
+        render_bwd(surfels, frame, b["ranges"], b["vals"], g["dA"], g["dS_t"], g["dS_n"], params64,
+                   grads, nthreads)
+        L += Lf
+        fwds.append(fw); bins.append(b)
+    ls = params64[2] if params64 is not None else surfels.log_scale
+    L += scale_reg(ls, s_max, lam_s, grads["log_scale"])
+    return L, fwds, grads, bins
