@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Benchmark: fwd+bwd rays/s of the differentiable spherical surfel rasterizer
+on the 200k-surfel 128 x 1024 street frame (one mapping step = bin + sort,
+forward, mapping loss, backward to every surfel parameter).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One process per GPU (torchrun for N > 1); every rank renders its own replica
+of the workload (the path has no exchange step), so scaling is weak and the
+reported value is the sum over ranks.  Prints one JSON line on rank 0.
+
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd rays/s at 200k surfels, 128x1024"
+UNIT = "rays/s"
+WORKLOAD = dict(workload="street 200k surfels, 128x1024 range image, +-45 deg, 16x16 tiles", surfels=200_000,
+                H=128, W=1024, tile="16x16", frames=1, loss="depth L1 + 0.1 opacity BCE + 0.05 normal cosine + 10 scale")
+# FP32 operations per ray/surfel evaluation and per composited pair (FMA = 2),
+# counted from the definition (see the design notes).
+FLOP_EVAL = 27
+FLOP_COMPOSITE = 12
+FLOP_BWD_VALID = 70
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x lanes x FMA x max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--persistent", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(seconds: float):
+    """The oracle, as it stands, on the full street frame, repeated for about
+    ``seconds`` of wall time on all host cores."""
+    from oracle import oracle as O
+    from paper_2607_04127_gb300 import scenes
+    O.build()
+    surf, frame, tgt = scenes.street()
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        O.forward_backward(surf, [frame], [(tgt.D, tgt.N)], nthreads=0)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or reps >= 50:
+            break
+    cores = os.cpu_count() or 1
+    return dict(value=reps * frame.H * frame.W / el, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{reps} full fwd+loss+bwd passes of the street frame (FP64 oracle, OpenMP over tiles, "
+                       f"{cores} threads) in {el:.1f} s")
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.cpu_seconds)
+    line = dict(metric=METRIC, value=cb["value"], unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * WORKLOAD["H"] * WORKLOAD["W"] / cb["value"],
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(WORKLOAD, parallelism="host cores"), impl="reference", cpu_baseline=cb,
+                e2e=dict(value=cb["value"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for ln in open(self.path):
+                p = [x.strip() for x in ln.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"], samples=0)
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return dict(sm_mhz=statistics.median(load) if load else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=reasons, samples=len(rows))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2607_04127_gb300 import build
+    build.build()
+    from paper_2607_04127_gb300 import render, scenes
+    surf, frame, tgt = scenes.street()
+    params = render.map_tensors(surf, dev)
+    targets = [render.target_tensors(tgt, dev)]
+    grads = [[torch.zeros_like(p) for p in params]]
+    rast = render.Rasterizer([frame], device=dev.index, batch=args.batch, persistent=args.persistent)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    # warm-up (also sizes the workspace: the first bin_sort checks capacity)
+    rast.step([params], targets, grads, check=True)
+    for _ in range(max(args.warmup, 3)):
+        rast.step([params], targets, grads)
+    torch.cuda.synchronize()
+    rast.session.check_status()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    c0 = rast.counters()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(dev.index)).split(",")[0])
+                if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else dev.index) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            e = ev[k]
+            e[0].record(stream)
+            S = rast.bin_sort([params], check=False)
+            e[1].record(stream)
+            rast.forward([params], S)
+            e[2].record(stream)
+            rast.loss([params], targets, grads[0:1], S)
+            e[3].record(stream)
+            rast.backward([params], grads, S=S)
+            e[4].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    rast.session.check_status()
+    c1 = rast.counters()
+    step_ms = [e[0].elapsed_time(e[4]) for e in ev]
+    fwd_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    bwd_ms = [e[3].elapsed_time(e[4]) for e in ev]
+    bin_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    loss_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    rays = frame.H * frame.W
+    value = world * args.steps * rays / total_s
+
+    # algorithmic work of one step (counters are cumulative since the last bin_sort)
+    c_last = rast.counters()
+    evf, evb = c_last["evals_fwd"], c_last["evals_bwd"]
+    cf, cb_ = c_last["contrib_fwd"], c_last["contrib_bwd"]
+    fl_fwd = FLOP_EVAL * evf + FLOP_COMPOSITE * cf
+    fl_bwd = FLOP_EVAL * evb + FLOP_BWD_VALID * cb_
+    fwd_s = statistics.mean(fwd_ms) / 1e3
+    bwd_s = statistics.mean(bwd_ms) / 1e3
+    dominant = "bwd" if bwd_s >= fwd_s else "fwd"
+    achieved = (fl_bwd / bwd_s if dominant == "bwd" else fl_fwd / fwd_s) / 1e12
+    launches_per_step = (c1["launches"] - c0["launches"]) / args.steps
+
+    # end to end through the public API with host buffers
+    host = [p.cpu().pin_memory() for p in params]
+    host_t = [t.cpu().pin_memory() for t in targets[0]]
+    dev_p = [torch.empty_like(p) for p in params]
+    dev_t = [torch.empty_like(t) for t in targets[0]]
+    out_g = [torch.empty(p.shape, dtype=p.dtype, pin_memory=True) for p in params]
+    out_l = torch.empty(1, pin_memory=True)
+    h2d = sum(h.numel() * 4 for h in host) + sum(h.numel() * 4 for h in host_t)
+    d2h = sum(g.numel() * 4 for g in out_g) + 4
+    e2e_steps = max(10, args.steps // 2)
+    ee = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(e2e_steps)]
+    g2 = [[torch.zeros_like(p) for p in params]]
+    for k in range(e2e_steps):
+        flush.zero_()
+        ee[k][0].record(stream)
+        for d_, h_ in zip(dev_p, host):
+            d_.copy_(h_, non_blocking=True)
+        for d_, h_ in zip(dev_t, host_t):
+            d_.copy_(h_, non_blocking=True)
+        for g in g2[0]:
+            g.zero_()
+        L = rast.step([dev_p], [tuple(dev_t)], g2)
+        for o, g in zip(out_g, g2[0]):
+            o.copy_(g, non_blocking=True)
+        out_l.copy_(L[:1], non_blocking=True)
+        ee[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_s = sum(e[0].elapsed_time(e[1]) for e in ee) / 1e3
+    e2e_value = world * e2e_steps * rays / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+    clocks = clk.summary()
+    if rank != 0:
+        return
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=statistics.mean(step_ms), higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32", data="synthetic (seeded street scene, see scenes.street)",
+        config=dict(WORKLOAD, parallelism=f"replicas x{world}", batch=args.batch, persistent=args.persistent,
+                    l2="flushed between steps (256 MB write); per-step CUDA events, flush not timed"),
+        evals_per_s=world * args.steps * (evf + evb) / total_s,
+        stages_ms=dict(bin_sort=statistics.mean(bin_ms), fwd=statistics.mean(fwd_ms),
+                       loss=statistics.mean(loss_ms), bwd=statistics.mean(bwd_ms)),
+        work=dict(pairs=c_last["n_pairs"], visible_items=c_last["n_visible"], evals_fwd=evf, evals_bwd=evb,
+                  composited_fwd=cf, valid_bwd=cb_),
+        roofline=dict(bound="alu", kernel="k_bwd" if dominant == "bwd" else "k_fwd", achieved=achieved,
+                      peak=PEAK_FP32_TFLOPS, unit="TFLOP/s", frac=achieved / PEAK_FP32_TFLOPS, traffic=None,
+                      peak_source="derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz"),
+        e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+        gpu_launches=int(round(launches_per_step * args.steps)),
+        clocks=clocks, wall_s=t_wall,
+    )
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    rast.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

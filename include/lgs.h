@@ -1,0 +1,302 @@
+/*
+ * lgs.h -- C ABI of the GB300 differentiable spherical rasterizer of 2D
+ * Gaussian surfels into LiDAR range images.
+ *
+ * The operation (paper Sec. 3.1 "Map Representation" and Sec. 3.4 "Map
+ * Optimization"): a map of 2D Gaussian surfels (mean mu, orientation q,
+ * in-plane log-scale s~, opacity alpha) is rendered under the spherical
+ * projection of a spinning LiDAR into a range image, giving per pixel the
+ * accumulated opacity A, the weighted range sum S_t and the weighted normal
+ * sum S_n, from which the expected depth D = S_t/(A+1e-6) and the normal
+ * N = S_n/|S_n| follow; the mapping losses (Eqs. depthloss, normalloss,
+ * scaleloss, totalloss) compare them with the scan and are differentiated
+ * back to every surfel parameter.
+ *
+ * Definitions shared by every entry point
+ *  - Frame: H x W pixels, row 0 at the top elevation elev_max, pixel-centre
+ *    elevation elev_max - (r + 1/2)(elev_max - elev_min)/H; azimuth
+ *    (c + 1/2) 2 pi / W counter-clockwise from the sensor +x axis, full
+ *    360 degrees.  pose = sensor-to-world [R | t], 3 x 4 row-major; rays are
+ *    unit vectors from the sensor origin.
+ *  - Tiles: tile_h x tile_w pixels (the last row/column of tiles may be
+ *    ragged); tile_h * tile_w is a multiple of 32 and at most 256 (one CUDA
+ *    thread per pixel).  Every frame of one call uses the same tile shape.
+ *  - Surfel i: centre mean[3i..3i+2] (world), quaternion quat[4i..4i+3]
+ *    = (w,x,y,z) (normalised inside), log_scale[2i..2i+1] (scales
+ *    exp(log_scale), tangent axes R(q)e0 and R(q)e1), opacity
+ *    sigmoid(opacity_logit[i]); normal R(q)e2.
+ *  - Per pixel, the surfels listed for its tile are visited in ascending
+ *    (binary32 |mu_sensor| bit pattern, surfel index); each is intersected as
+ *    a plane, t = (n.mu)/(n.d), skipped if |n.d| < 1e-6, t <= 0.2 m,
+ *    u^2+v^2 > 9 or a = min(alpha exp(-(u^2+v^2)/2), 0.99) < 1/255, and
+ *    composited front to back (w = a T, T *= 1-a) until T (1-a) < 1e-4, in
+ *    which case that surfel is not composited and the pixel stops.
+ *  - Binning (which surfels a tile lists) is a conservative bounding-cone
+ *    test in specified binary32 arithmetic; the sorted lists are bit-exact
+ *    reproducible (see the design notes for the exact definition).
+ *
+ * Conventions
+ *  - All array pointers are DEVICE pointers owned by the caller, FP32 unless
+ *    stated, densely packed.  The library never frees them.
+ *  - Per-frame image planes are [H*W] row-major; S_n and the normal targets
+ *    are planar [3][H*W].
+ *  - A session owns descriptors and a small pinned status buffer only;
+ *    all scratch lives in a caller-provided device workspace
+ *    (lgs_*_workspace_size / lgs_session_set_workspace).
+ *  - Calls enqueue work on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and return without synchronising, except
+ *    lgs_session_status / lgs_session_pair_count, which synchronise.
+ *  - Argument errors are returned at once and enqueue nothing.  Conditions
+ *    found on the device (pair capacity exceeded, a bounded wait that gave
+ *    up, a bounds check in checked builds) are recorded in a device status
+ *    word and reported by lgs_session_status.
+ *  - A session is used from one host thread and one stream at a time.
+ *  - lgs_render_bwd needs the bins of the lgs_bin_sort that preceded the
+ *    matching lgs_render_fwd: they stay in the workspace until the next
+ *    lgs_bin_sort on the same session.
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef LGS_H
+#define LGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LGS_API __attribute__((visibility("default")))
+#else
+#define LGS_API
+#endif
+
+typedef struct lgs_session_s* lgs_session;
+
+typedef enum {
+    LGS_OK = 0,
+    LGS_ERR_INVALID_ARG = 1,   /* bad pointer, size, tile shape, elevation range ... */
+    LGS_ERR_CAPACITY = 2,      /* more (tile, surfel) pairs than the workspace holds */
+    LGS_ERR_BUDGET = 3,        /* workspace larger than the session's HBM budget */
+    LGS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    LGS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    LGS_ERR_DEVICE_CHECK = 6,  /* a device-side bounds check failed */
+    LGS_ERR_NO_WORKSPACE = 7,  /* no (or too small a) workspace is set */
+    LGS_ERR_STATE = 8          /* call order violated (e.g. bwd without bins) */
+} lgs_status;
+
+/* Limits of one call. */
+#define LGS_MAX_FRAMES 64
+#define LGS_MAX_MAPS 64
+#define LGS_MAX_TILE_PIXELS 256
+
+typedef struct {
+    int32_t H, W, tile_h, tile_w;
+    float elev_min, elev_max;   /* radians, -pi/2 <= elev_min < elev_max <= pi/2 */
+    float pose[12];             /* sensor -> world [R | t], row-major 3 x 4 */
+} lgs_frame;
+
+typedef struct {
+    const float* mean;          /* [n,3] */
+    const float* quat;          /* [n,4] (w,x,y,z) */
+    const float* log_scale;     /* [n,2] */
+    const float* opacity_logit; /* [n]   */
+    int64_t n;
+} lgs_surfels;
+
+/* Forward outputs of one frame (device, caller-owned, overwritten). */
+typedef struct {
+    float* A;          /* [H*W]   accumulated opacity  sum_k w_k            */
+    float* S_t;        /* [H*W]   sum_k w_k t_k (range along the unit ray)   */
+    float* S_n;        /* [3,H*W] sum_k w_k n'_k, n' = -sign(n.d) n          */
+    float* T_final;    /* [H*W]   transmittance after the last contributor   */
+    int32_t* n_contrib;/* [H*W]   list position of the last contributor + 1  */
+} lgs_fwd_out;
+
+/* Upstream gradients dL/d(A, S_t, S_n) of one frame (device). */
+typedef struct {
+    const float* dA;   /* [H*W]   */
+    const float* dS_t; /* [H*W]   */
+    const float* dS_n; /* [3,H*W] */
+} lgs_fwd_grad;
+
+/* Gradients w.r.t. the raw surfel parameters (device); ACCUMULATED (+=). */
+typedef struct {
+    float* d_mean;          /* [n,3] */
+    float* d_quat;          /* [n,4] */
+    float* d_log_scale;     /* [n,2] */
+    float* d_opacity_logit; /* [n]   */
+} lgs_surfel_grad;
+
+/* Writable per-frame gradient planes (device), filled by lgs_loss. */
+typedef struct {
+    float* dA;         /* [H*W]   */
+    float* dS_t;       /* [H*W]   */
+    float* dS_n;       /* [3,H*W] */
+} lgs_fwd_grad_out;
+
+/* Measured scan of one frame (device). */
+typedef struct {
+    const float* D;      /* [H*W] range, 0 = no return (mask M_D = [D > 0]) */
+    const float* N_gicp; /* [3,H*W] tracking normals, zero = undefined       */
+} lgs_target;
+
+/* Loss weights (paper Sec. 4.1 implementation details). */
+typedef struct {
+    float lambda_alpha;  /* 0.1  */
+    float lambda_n;      /* 1.0  */
+    float lambda_ng;     /* 0.05 */
+    float lambda_s;      /* 10.0 */
+    float s_max;         /* 1.0 m, threshold of the scale regulariser */
+} lgs_loss_params;
+
+/* Tuning knobs of the compositing kernels (results do not depend on them). */
+typedef struct {
+    int32_t batch;       /* surfel records per shared-memory batch: 64..512, multiple of 32 */
+    int32_t persistent;  /* 1: persistent CTAs claim tiles, longest list first */
+} lgs_tuning;
+
+/* ---- sessions and workspace -------------------------------------------- */
+
+/* Create a session on `device` that will refuse workspaces larger than
+ * hbm_budget_bytes (0 = no limit).  *out receives the handle. */
+LGS_API lgs_status lgs_session_create(int device, size_t hbm_budget_bytes, lgs_session* out);
+
+/* Destroy a session (does not free the caller's workspace). */
+LGS_API lgs_status lgs_session_destroy(lgs_session s);
+
+/* Bytes of workspace needed to bin and render `n_frames` frames of one map
+ * of n_surfels surfels with room for max_pairs (tile, surfel) pairs. */
+LGS_API lgs_status lgs_session_workspace_size(lgs_session s, int64_t n_surfels, const lgs_frame* frames,
+                                      int n_frames, int64_t max_pairs, size_t* bytes);
+
+/* Same for a batch: frame f renders map frame_map[f] (0 <= . < n_maps). */
+LGS_API lgs_status lgs_batch_workspace_size(lgs_session s, const int64_t* map_sizes, int n_maps,
+                                    const lgs_frame* frames, const int32_t* frame_map, int n_frames,
+                                    int64_t max_pairs, size_t* bytes);
+
+/* Hand the session a device workspace (256-byte aligned) of `bytes` bytes.
+ * LGS_ERR_BUDGET if bytes exceed the session budget. */
+LGS_API lgs_status lgs_session_set_workspace(lgs_session s, void* dev_ptr, size_t bytes);
+
+/* Synchronise with the session's last stream and read the device status:
+ * LGS_OK, LGS_ERR_CAPACITY (then *required_pairs is the number needed),
+ * LGS_ERR_TIMEOUT or LGS_ERR_DEVICE_CHECK.  required_pairs may be NULL. */
+LGS_API lgs_status lgs_session_status(lgs_session s, int64_t* required_pairs);
+
+/* Synchronise and return the pair count of the last bin_sort. */
+LGS_API lgs_status lgs_session_pair_count(lgs_session s, int64_t* n_pairs);
+
+/* Synchronise and read the counters of the last bin_sort: out[0] pairs,
+ * out[1] items covering at least one tile, out[2] ray/surfel evaluations of
+ * the forward calls since that bin_sort, out[3] the same for the backward,
+ * out[4] composited pairs of the forward calls, out[5] valid pairs the
+ * backward re-evaluated, out[6] CUDA kernels this session has enqueued since
+ * it was created, out[7] reserved (0). */
+LGS_API lgs_status lgs_session_counters(lgs_session s, int64_t out[8]);
+
+/* Device pointers into the workspace describing the last bin_sort, valid
+ * until the next one: tile_of_pair[P] (global tile id, frame f's tiles start
+ * at the sum of the tile counts of frames < f), item_of_pair[P] (frame-major
+ * item f*n + surfel for one map), ranges[2*T] (start, end per global tile),
+ * depth_key[items] (binary32 bits of |mu_sensor|). */
+LGS_API lgs_status lgs_session_bins(lgs_session s, const uint32_t** tile_of_pair, const uint32_t** item_of_pair,
+                            const uint32_t** ranges, const uint32_t** depth_key);
+
+/* Synchronise and copy the last bin_sort's lists to HOST buffers (any may be
+ * NULL): tile_of_pair / item_of_pair [n_pairs] (only if cap_pairs >= n_pairs,
+ * else LGS_ERR_CAPACITY), ranges [2 * total tiles], depth_key [items]. */
+LGS_API lgs_status lgs_session_read_bins(lgs_session s, uint32_t* tile_of_pair, uint32_t* item_of_pair,
+                                 uint32_t* ranges, uint32_t* depth_key, int64_t cap_pairs);
+
+/* ---- the hot path -------------------------------------------------------- */
+
+/* Bin and sort: per frame, transform the surfels to the sensor frame, list
+ * each surfel under every angular tile its bounding cone meets (azimuth seam
+ * handled by circular column ranges), and sort each tile's list by
+ * (depth key, surfel index) (paper Sec. 3.1: render under the spherical
+ * projection; the sort realises front-to-back order). */
+LGS_API lgs_status lgs_bin_sort(lgs_session s, const lgs_surfels* surfels, const lgs_frame* frames,
+                        int n_frames, void* stream);
+
+/* Forward compositing of every frame of the last lgs_bin_sort (Sec. 3.4:
+ * rasterise the map into (D, A, N)).  per_frame[f] receives frame f. */
+LGS_API lgs_status lgs_render_fwd(lgs_session s, const lgs_surfels* surfels, const lgs_frame* frames,
+                          int n_frames, const lgs_fwd_out* per_frame, void* stream);
+
+/* Backward: given the forward outputs and upstream gradients of every frame,
+ * ACCUMULATE dL/d(mean, quat, log_scale, logit) into *grad (Sec. 3.4:
+ * optimise Theta = {mu, q, s~, alpha}).  The forward is recomputed per tile
+ * in reverse order; no per-pixel surfel lists are stored. */
+LGS_API lgs_status lgs_render_bwd(lgs_session s, const lgs_surfels* surfels, const lgs_frame* frames,
+                          int n_frames, const lgs_fwd_out* fwd, const lgs_fwd_grad* upstream,
+                          const lgs_surfel_grad* grad, void* stream);
+
+/* Mapping loss of a window of frames (Eqs. depthloss, normalloss, scaleloss,
+ * totalloss): L = (1/F) sum_f [L_depth + la L_alpha + ln lng L_ng]_f
+ * + ls L_scale.  Writes dL/d(A, S_t, S_n) per frame into grads_out[f]
+ * (overwritten), adds ls dL_scale/d(log
+ * scale) into grad->d_log_scale (if grad != NULL), and stores on the device
+ * loss_out[0] = L, loss_out[1+3f .. 3+3f] = (L_depth, L_alpha, L_ng) of
+ * frame f, and loss_out[1 + 3 n_frames + m] = the part of L of map m
+ * (loss_out has 1 + 3 n_frames + n_maps floats; one map for lgs_loss).
+ * With several frames per map the image terms of that map are averaged over
+ * its frames, so a map's gradient does not depend on the other maps of a
+ * batch. */
+LGS_API lgs_status lgs_loss(lgs_session s, const lgs_surfels* surfels, const lgs_frame* frames, int n_frames,
+                    const lgs_fwd_out* fwd, const lgs_target* targets, const lgs_loss_params* params,
+                    const lgs_fwd_grad_out* grads_out, const lgs_surfel_grad* grad, float* loss_out,
+                    void* stream);
+
+/* Batched forms: maps[m] for m < n_maps; frame f renders maps[frame_map[f]];
+ * grads[m] receives map m's gradient. */
+LGS_API lgs_status lgs_bin_sort_batch(lgs_session s, const lgs_surfels* maps, int n_maps,
+                              const lgs_frame* frames, const int32_t* frame_map, int n_frames,
+                              void* stream);
+LGS_API lgs_status lgs_render_fwd_batch(lgs_session s, const lgs_surfels* maps, int n_maps,
+                                const lgs_frame* frames, const int32_t* frame_map, int n_frames,
+                                const lgs_fwd_out* per_frame, void* stream);
+LGS_API lgs_status lgs_render_bwd_batch(lgs_session s, const lgs_surfels* maps, int n_maps,
+                                const lgs_frame* frames, const int32_t* frame_map, int n_frames,
+                                const lgs_fwd_out* fwd, const lgs_fwd_grad* upstream,
+                                const lgs_surfel_grad* grads, void* stream);
+LGS_API lgs_status lgs_loss_batch(lgs_session s, const lgs_surfels* maps, int n_maps, const lgs_frame* frames,
+                          const int32_t* frame_map, int n_frames, const lgs_fwd_out* fwd,
+                          const lgs_target* targets, const lgs_loss_params* params,
+                          const lgs_fwd_grad_out* grads_out, const lgs_surfel_grad* grads,
+                          float* loss_out, void* stream);
+
+/* Set the compositing knobs of a session (defaults: batch 256, persistent 0). */
+LGS_API lgs_status lgs_session_set_tuning(lgs_session s, const lgs_tuning* t);
+
+/* One Adam step over the n surfels' 10 parameters (optimiser of the mapping
+ * loop; the paper does not name it): m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, p -= lr_group * mhat / (sqrt(vhat) + eps) with bias
+ * correction for step `step` (>= 1); lr[0..3] for mean, quat, log_scale,
+ * logit.  Zeroes the gradients afterwards when zero_grad != 0.  All pointers
+ * device, layouts as lgs_surfels; m and v have the parameters' layout. */
+LGS_API lgs_status lgs_adam_step(float* mean, float* quat, float* log_scale, float* logit,
+                         const lgs_surfel_grad* grad, float* m_state, float* v_state, int64_t n,
+                         int64_t step, const float lr[4], float beta1, float beta2, float eps,
+                         int zero_grad, void* stream);
+
+/* ---- misc ---------------------------------------------------------------- */
+LGS_API const char* lgs_status_string(lgs_status st);
+
+/* Text of the last error recorded on the calling host thread ("" if none). */
+LGS_API const char* lgs_last_error(void);
+
+/* The library's constants, for cross-checking with an independent oracle:
+ * [0] t_near 0.2, [1] cut-off 9, [2] 1/255, [3] clamp 0.99, [4] T stop 1e-4,
+ * [5] grazing 1e-6, [6] eps_A 1e-6, [7] eps_N 1e-6, [8] eps_log 1e-6,
+ * [9] binning radius factor 3, [10] radius margin 1.0001, [11] 1e-5 m/m. */
+LGS_API void lgs_constants(float out[16]);
+
+/* Library version string. */
+LGS_API const char* lgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGS_H */

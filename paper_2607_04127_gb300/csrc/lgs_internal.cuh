@@ -1,0 +1,377 @@
+// lgs_internal.cuh -- device-side descriptors and shared device functions of
+// the GB300 surfel rasterizer (CUDA path only).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lgs.h"
+
+namespace lgs {
+
+// ---------------------------------------------------------------------------
+// Descriptors (written once per call into the workspace by k_write_desc)
+// ---------------------------------------------------------------------------
+struct FrameDev {
+  int32_t H, W, th, tw, ntr, ntc;
+  int32_t map;             // index of the surfel set this frame renders
+  uint32_t tile_base;      // global id of the frame's tile 0
+  int64_t item_base;       // global id of (this frame, surfel 0)
+  int64_t n;               // surfels of the map
+  uint32_t row_tab;        // float offset of [2*ntr] (sin_top, sin_bot) in tables
+  uint32_t col_tab;        // float offset of [4*ntc] (cos0, sin0, cos1, sin1) in tables
+  float emin, emax;
+  float R[9];              // sensor -> world rotation, row-major
+  float o[3];              // sensor origin (world)
+  // per-call pointers (caller-owned device memory)
+  float *A, *St, *Sn, *Tf;
+  int32_t* nc;
+  const float *gA, *gSt, *gSn;
+  float *oA, *oSt, *oSn;   // loss: gradient planes to write
+  const float *D, *Ng;     // loss: targets
+};
+
+struct MapDev {
+  const float *mean, *quat, *ls, *logit;
+  int64_t n;
+  int64_t surf_base;       // first surfel of this map in the flattened surfel range
+  float *d_mean, *d_quat, *d_ls, *d_logit;
+  int32_t n_frames;        // frames of the call that render this map
+  int32_t pad;
+};
+
+struct Desc {
+  int32_t n_frames, n_maps;
+  int32_t th, tw;
+  uint32_t n_tiles;        // total over frames
+  int64_t n_items;         // total (frame, surfel) items
+  int64_t n_surf;          // total surfels over maps
+  FrameDev f[LGS_MAX_FRAMES];
+  MapDev m[LGS_MAX_MAPS];
+};
+
+// Status words (device, in the workspace).
+struct Status {
+  unsigned long long required_pairs;  // pairs the last bin_sort needed
+  unsigned long long n_pairs;         // pairs actually emitted (0 on overflow)
+  unsigned int n_vis;                 // items with at least one tile
+  unsigned int overflow;              // 1 if required_pairs > capacity
+  unsigned int timeout;               // a bounded wait gave up
+  unsigned int check;                 // a checked-build bounds check failed
+  unsigned int work_counter;          // persistent scheduler: next work item
+  unsigned int work_counter2;
+  unsigned long long evals_fwd;       // ray/surfel evaluations (cumulative since bin_sort)
+  unsigned long long evals_bwd;
+  unsigned long long contrib_fwd;     // composited (fwd) / valid re-evaluated (bwd) pairs
+  unsigned long long contrib_bwd;
+  int loss_count[2 * LGS_MAX_FRAMES]; // per frame |Omega_D|, |Omega_N|
+};
+
+// Radix-sort / scan geometry shared by the host layout and the kernels.
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortChunk = kSortThreads * kSortItems;   // 4096 keys per CTA
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;   // 2048 per CTA
+
+// Workspace layout (byte offsets; computed on the host, passed by value).
+struct Layout {
+  size_t desc, status, tables, rec, key, cnt, srtA_k, srtA_v, srtB_k, srtB_v, offs, bsum,
+      pk_A, pk_B, pv_A, pv_B, hist, dtot, ranges, g13, work, loss_part, total;
+  int64_t items_cap, pairs_cap;
+  uint32_t tiles_cap;
+  uint32_t tables_cap;     // floats
+  int32_t hist_blocks;     // radix CTAs for the larger of items / pairs
+  int32_t loss_blocks;
+};
+
+struct WsPtrs {
+  Desc* desc;
+  Status* st;
+  float* tables;
+  float4* rec;             // [items][4]
+  uint32_t* key;           // depth key per item
+  uint32_t* cnt;           // tile count per item
+  uint32_t *sk_a, *sv_a, *sk_b, *sv_b;   // item sort ping-pong (key, item)
+  uint32_t* offs;          // pair offset per sorted item
+  unsigned long long* bsum;// scan block sums
+  uint32_t *pk_a, *pk_b, *pv_a, *pv_b;   // pair sort ping-pong (tile, item)
+  uint32_t* hist;          // [256][blocks]
+  uint32_t* dtot;          // [passes][256] digit totals
+  uint2* ranges;           // [tiles]
+  float* g13;              // [items][16]
+  uint32_t* work;          // persistent scheduler tile order
+  double* loss_part;       // [blocks][4]
+};
+
+inline WsPtrs ws_ptrs(void* base, const Layout& L) {
+  char* b = static_cast<char*>(base);
+  WsPtrs p;
+  p.desc = reinterpret_cast<Desc*>(b + L.desc);
+  p.st = reinterpret_cast<Status*>(b + L.status);
+  p.tables = reinterpret_cast<float*>(b + L.tables);
+  p.rec = reinterpret_cast<float4*>(b + L.rec);
+  p.key = reinterpret_cast<uint32_t*>(b + L.key);
+  p.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
+  p.sk_a = reinterpret_cast<uint32_t*>(b + L.srtA_k);
+  p.sv_a = reinterpret_cast<uint32_t*>(b + L.srtA_v);
+  p.sk_b = reinterpret_cast<uint32_t*>(b + L.srtB_k);
+  p.sv_b = reinterpret_cast<uint32_t*>(b + L.srtB_v);
+  p.offs = reinterpret_cast<uint32_t*>(b + L.offs);
+  p.bsum = reinterpret_cast<unsigned long long*>(b + L.bsum);
+  p.pk_a = reinterpret_cast<uint32_t*>(b + L.pk_A);
+  p.pk_b = reinterpret_cast<uint32_t*>(b + L.pk_B);
+  p.pv_a = reinterpret_cast<uint32_t*>(b + L.pv_A);
+  p.pv_b = reinterpret_cast<uint32_t*>(b + L.pv_B);
+  p.hist = reinterpret_cast<uint32_t*>(b + L.hist);
+  p.dtot = reinterpret_cast<uint32_t*>(b + L.dtot);
+  p.ranges = reinterpret_cast<uint2*>(b + L.ranges);
+  p.g13 = reinterpret_cast<float*>(b + L.g13);
+  p.work = reinterpret_cast<uint32_t*>(b + L.work);
+  p.loss_part = reinterpret_cast<double*>(b + L.loss_part);
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// Binary32 binning arithmetic.  Every operation below is a single correctly
+// rounded IEEE operation (the __f*_rn intrinsics forbid contraction into
+// FMA), so the binning decision and the depth key are a fixed function of the
+// FP32 inputs.  Transcendentals are replaced by fixed polynomials:
+//   exp: x = k ln2 + r (ln2 = 0x1.62e4p-1 + 0x1.7f7d1cp-20), e^r by its
+//        Taylor series through r^7, then an exact scaling by 2^k;
+//   sin / cos on [-pi/2, pi/2]: Taylor series through x^11 / x^12.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+
+__device__ __forceinline__ float bin_exp(float x) {
+  if (!(x < 80.0f)) x = 80.0f;
+  if (x < -80.0f) x = -80.0f;
+  const float kf = rintf(fmul(x, 0x1.715476p+0f));
+  float r = fsub(x, fmul(kf, 0x1.62e4p-1f));
+  r = fsub(r, fmul(kf, 0x1.7f7d1cp-20f));
+  float p = 0x1.a01a02p-13f;
+  p = fadd(fmul(p, r), 0x1.6c16c2p-10f);
+  p = fadd(fmul(p, r), 0x1.111112p-7f);
+  p = fadd(fmul(p, r), 0x1.555556p-5f);
+  p = fadd(fmul(p, r), 0x1.555556p-3f);
+  p = fadd(fmul(p, r), 0.5f);
+  p = fadd(fmul(p, r), 1.0f);
+  p = fadd(fmul(p, r), 1.0f);
+  const int k = static_cast<int>(kf);
+  return fmul(p, __int_as_float((k + 127) << 23));
+}
+
+__device__ __forceinline__ float bin_sin(float x) {
+  const float x2 = fmul(x, x);
+  float p = -0x1.ae6456p-26f;
+  p = fadd(fmul(p, x2), 0x1.71de3ap-19f);
+  p = fsub(fmul(p, x2), 0x1.a01a02p-13f);
+  p = fadd(fmul(p, x2), 0x1.111112p-7f);
+  p = fsub(fmul(p, x2), 0x1.555556p-3f);
+  p = fmul(p, x2);
+  return fadd(fmul(p, x), x);
+}
+
+__device__ __forceinline__ float bin_cos(float x) {
+  const float x2 = fmul(x, x);
+  float p = 0x1.1eed8ep-29f;
+  p = fsub(fmul(p, x2), 0x1.27e4fcp-22f);
+  p = fadd(fmul(p, x2), 0x1.a01a02p-16f);
+  p = fsub(fmul(p, x2), 0x1.6c16c2p-10f);
+  p = fadd(fmul(p, x2), 0x1.555556p-5f);
+  p = fsub(fmul(p, x2), 0.5f);
+  return fadd(fmul(p, x2), 1.0f);
+}
+
+// elevation of pixel row r (row 0 at the top)
+__device__ __forceinline__ float bin_row_elev(int r, int H, float emin, float emax) {
+  const float dth = fdiv(fsub(emax, emin), static_cast<float>(H));
+  return fsub(emax, fmul(fadd(static_cast<float>(r), 0.5f), dth));
+}
+
+// (cos, sin) of the azimuth 2 pi (2c+1)/(2W) of pixel column c
+__device__ __forceinline__ void bin_col_dir(int c, int W, float& cs, float& sn) {
+  const float f = fdiv(static_cast<float>(2 * c + 1), static_cast<float>(2 * W));
+  int k = static_cast<int>(fmul(f, 4.0f));
+  k = k > 3 ? 3 : k;
+  const float rq = fsub(f, fmul(static_cast<float>(k), 0.25f));
+  const float x = fmul(rq, 0x1.921fb6p+2f);
+  const float s0 = bin_sin(x), c0 = bin_cos(x);
+  switch (k) {
+    case 0: cs = c0; sn = s0; break;
+    case 1: cs = -s0; sn = c0; break;
+    case 2: cs = -c0; sn = -s0; break;
+    default: cs = s0; sn = -c0; break;
+  }
+}
+
+// Bounding cone of one surfel in one frame.
+struct BinGeom {
+  float x, y, z, r, h, rho, sin_hi, sin_lo;
+  bool all_rows, all_cols;
+};
+
+__device__ __forceinline__ void bin_geom(const float* __restrict__ mw, const float* __restrict__ ls,
+                                         const FrameDev& F, BinGeom& g) {
+  const float dx = fsub(mw[0], F.o[0]), dy = fsub(mw[1], F.o[1]), dz = fsub(mw[2], F.o[2]);
+  g.x = fadd(fadd(fmul(F.R[0], dx), fmul(F.R[3], dy)), fmul(F.R[6], dz));
+  g.y = fadd(fadd(fmul(F.R[1], dx), fmul(F.R[4], dy)), fmul(F.R[7], dz));
+  g.z = fadd(fadd(fmul(F.R[2], dx), fmul(F.R[5], dy)), fmul(F.R[8], dz));
+  const float h2 = fadd(fmul(g.x, g.x), fmul(g.y, g.y));
+  const float r2 = fadd(h2, fmul(g.z, g.z));
+  g.r = fsqrt(r2);
+  g.h = fsqrt(h2);
+  const float sm = ls[0] >= ls[1] ? ls[0] : ls[1];
+  const float s = bin_exp(sm);
+  g.rho = fadd(fmul(fmul(3.0f, s), 1.0001f), fmul(1e-5f, fadd(g.r, 1.0f)));
+  g.all_rows = false;
+  g.all_cols = false;
+  g.sin_hi = 2.0f;
+  g.sin_lo = -2.0f;
+  const float rr = fsub(r2, fmul(g.rho, g.rho));
+  if (!(rr > 0.0f)) {
+    g.all_rows = true;
+    g.all_cols = true;
+    return;
+  }
+  const float c = fsqrt(rr);
+  const float hc = fmul(g.h, c), zp = fmul(g.z, g.rho), zc = fmul(g.z, c), hp = fmul(g.h, g.rho);
+  const bool north = hc <= zp, south = hc <= -zp;
+  g.sin_hi = north ? 2.0f : fdiv(fadd(zc, hp), r2);
+  g.sin_lo = south ? -2.0f : fdiv(fsub(zc, hp), r2);
+  g.all_cols = north || south;
+}
+
+__device__ __forceinline__ bool bin_row_hit(const BinGeom& g, float s_top, float s_bot) {
+  return g.all_rows || (s_bot <= g.sin_hi && s_top >= g.sin_lo);
+}
+
+__device__ __forceinline__ bool bin_dir_in_cap(const BinGeom& g, float cs, float sn) {
+  const float dt = fadd(fmul(g.x, cs), fmul(g.y, sn));
+  const float cr = fsub(fmul(g.x, sn), fmul(g.y, cs));
+  return dt > 0.0f && fabsf(cr) <= g.rho;
+}
+
+__device__ __forceinline__ bool bin_col_hit(const BinGeom& g, float4 c) {
+  if (g.all_cols) return true;
+  if (bin_dir_in_cap(g, c.x, c.y) || bin_dir_in_cap(g, c.z, c.w)) return true;
+  return fsub(fmul(c.x, g.y), fmul(c.y, g.x)) >= 0.0f && fsub(fmul(g.x, c.w), fmul(g.y, c.z)) >= 0.0f;
+}
+
+// Candidate tile columns, as up to two inclusive ranges [a0,a1] and [b0,b1]
+// (b empty when b0 > b1), guaranteed to contain every column bin_col_hit
+// accepts: the cone's azimuth interval widened by two pixel columns on each
+// side, split at the azimuth seam.  Not part of the binning definition; it
+// only prunes the search.
+struct ColWin {
+  int a0, a1, b0, b1;
+};
+
+__device__ __forceinline__ void bin_col_window(const BinGeom& g, const FrameDev& F, ColWin& w) {
+  w.b0 = 1;
+  w.b1 = 0;
+  w.a0 = 0;
+  w.a1 = F.ntc - 1;
+  if (g.all_cols) return;
+  const float two_pi = 6.283185307f;
+  float phic = atan2f(g.y, g.x);
+  if (phic < 0.0f) phic += two_pi;
+  const float dphi = asinf(fminf(g.rho / g.h, 1.0f));
+  const float cpr = static_cast<float>(F.W) / two_pi;  // pixel columns per radian
+  const int cl = static_cast<int>(floorf((phic - dphi) * cpr - 0.5f)) - 2;
+  const int ch = static_cast<int>(ceilf((phic + dphi) * cpr - 0.5f)) + 2;
+  if (ch - cl + 1 >= F.W - 2 * F.tw) return;  // nearly everything: take all columns
+  if (cl < 0) {
+    w.a0 = (cl + F.W) / F.tw; w.a1 = F.ntc - 1; w.b0 = 0; w.b1 = ch / F.tw;
+  } else if (ch >= F.W) {
+    w.a0 = cl / F.tw; w.a1 = F.ntc - 1; w.b0 = 0; w.b1 = (ch - F.W) / F.tw;
+  } else {
+    w.a0 = cl / F.tw; w.a1 = ch / F.tw;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compositing record (4 x float4 = 64 B per item):
+//   r0 = (n, h = n.mu), r1 = (a_u = t_u/s_u, b_u = t_u.mu/s_u),
+//   r2 = (a_v, b_v), r3 = (alpha, 0, 0, 0); sensor frame.
+// Then for a unit ray d: den = n.d, t = h/den, u = t (a_u.d) - b_u,
+// v = t (a_v.d) - b_v.
+// ---------------------------------------------------------------------------
+struct Eval {
+  float den, t, ud, vd, u, v, q, G, araw, a;
+  bool valid;
+};
+
+// One ray / surfel evaluation, arithmetic pinned (explicit fma / rounded mul)
+// so the forward and backward kernels take identical skip decisions.
+__device__ __forceinline__ void eval_pair(const float4& r0, const float4& r1, const float4& r2,
+                                          float alpha, float dx, float dy, float dz, Eval& e) {
+  e.den = __fmaf_rn(r0.z, dz, __fmaf_rn(r0.y, dy, __fmul_rn(r0.x, dx)));
+  e.t = __fdividef(r0.w, e.den);
+  e.ud = __fmaf_rn(r1.z, dz, __fmaf_rn(r1.y, dy, __fmul_rn(r1.x, dx)));
+  e.vd = __fmaf_rn(r2.z, dz, __fmaf_rn(r2.y, dy, __fmul_rn(r2.x, dx)));
+  e.u = __fmaf_rn(e.t, e.ud, -r1.w);
+  e.v = __fmaf_rn(e.t, e.vd, -r2.w);
+  e.q = __fmaf_rn(e.u, e.u, __fmul_rn(e.v, e.v));
+  e.G = __expf(__fmul_rn(-0.5f, e.q));
+  e.araw = __fmul_rn(alpha, e.G);
+  e.a = fminf(e.araw, 0.99f);
+  e.valid = (fabsf(e.den) >= 1e-6f) && (e.t > 0.2f) && (e.q <= 9.0f) && (e.a >= (1.0f / 255.0f));
+}
+
+// Unit ray of pixel (r, c) (accuracy only, not part of any bit-exact contract).
+__device__ __forceinline__ void pixel_ray(const FrameDev& F, int r, int c, float& dx, float& dy, float& dz) {
+  const float th = F.emax - (static_cast<float>(r) + 0.5f) * ((F.emax - F.emin) / static_cast<float>(F.H));
+  float st, ct, sp, cp;
+  sincosf(th, &st, &ct);
+  sincospif((2.0f * static_cast<float>(c) + 1.0f) / static_cast<float>(F.W), &sp, &cp);
+  dx = ct * cp;
+  dy = ct * sp;
+  dz = st;
+}
+
+// Frame of a global tile id (binary search over the frames' tile bases).
+__device__ __forceinline__ int frame_of_tile(const Desc& D, uint32_t tile) {
+  int lo = 0, hi = D.n_frames - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (D.f[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int frame_of_item(const Desc& D, int64_t item) {
+  int lo = 0, hi = D.n_frames - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (D.f[mid].item_base <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (one per translation unit).
+// ---------------------------------------------------------------------------
+cudaError_t launch_write_desc(const Desc& h, Desc* d, Status* st, cudaStream_t s);
+cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n_items, uint32_t n_tiles,
+                       cudaStream_t s);
+int pair_sort_result_in_b(uint32_t n_tiles);
+int bin_kernel_count(uint32_t n_tiles);
+cudaError_t launch_raster_fwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
+                              int persistent, cudaStream_t s);
+cudaError_t launch_raster_bwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
+                              int persistent, cudaStream_t s);
+size_t loss_part_bytes();
+cudaError_t launch_preprocess_bwd(const Layout& L, const WsPtrs& w, const Desc& h, cudaStream_t s);
+cudaError_t launch_loss(const Layout& L, const WsPtrs& w, const Desc& h, const lgs_loss_params& p,
+                        bool scale_grad, float* loss_out, cudaStream_t s);
+cudaError_t launch_adam(float* p[4], float* g[4], float* m[4], float* v[4], const int64_t cnt[4],
+                        int64_t step, const float lr[4], float b1, float b2, float eps, int zero_grad,
+                        cudaStream_t s);
+
+}  // namespace lgs

@@ -1,0 +1,347 @@
+// lgs_optim.cu -- chain of the per-record gradients to the raw surfel
+// parameters, the mapping loss (image terms + scale regulariser) with its
+// upstream gradients, and a fused Adam step.
+#include <cuda_runtime.h>
+
+#include "lgs_internal.cuh"
+
+namespace lgs {
+
+// ---------------------------------------------------------------------------
+// Preprocess backward: for every surfel, sum over the frames that render its
+// map the record gradient (n, h, a_u, b_u, a_v, b_v, alpha) chained through
+//   h = n.mu, a_u = t_u/s_u, b_u = t_u.mu/s_u (same for v),
+//   mu = R^T (mean - o), [t_u t_v n] = R^T R(q/|q|), s = exp(log_scale),
+//   alpha = sigmoid(logit),
+// then ACCUMULATE into the caller's gradient arrays.  The per-item gradient
+// buffer is zeroed as it is read, so it is all-zero between backward calls.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int map_of_surfel(const Desc& D, int64_t s) {
+  int lo = 0, hi = D.n_maps - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (D.m[mid].surf_base <= s) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__ D, float* __restrict__ g13) {
+  const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= D->n_surf) return;
+  const int m = map_of_surfel(*D, s);
+  const MapDev& M = D->m[m];
+  const int64_t i = s - M.surf_base;
+  if (i >= M.n) return;
+  const float4 q = reinterpret_cast<const float4*>(M.quat)[i];
+  const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  const float inv = rsqrtf(qn2);
+  const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+  const float c0[3] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y)};
+  const float c1[3] = {2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x)};
+  const float c2[3] = {2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y)};
+  const float su = expf(M.ls[2 * i]), sv = expf(M.ls[2 * i + 1]);
+  const float isu = 1.f / su, isv = 1.f / sv;
+  const float alpha = 1.0f / (1.0f + expf(-M.logit[i]));
+  const float mw[3] = {M.mean[3 * i], M.mean[3 * i + 1], M.mean[3 * i + 2]};
+  float gm[3] = {0.f, 0.f, 0.f}, G0[3] = {0.f, 0.f, 0.f}, G1[3] = {0.f, 0.f, 0.f}, G2[3] = {0.f, 0.f, 0.f};
+  float gls0 = 0.f, gls1 = 0.f, galpha = 0.f;
+  bool any = false;
+  for (int f = 0; f < D->n_frames; ++f) {
+    const FrameDev& F = D->f[f];
+    if (F.map != m) continue;
+    float4* gp = reinterpret_cast<float4*>(g13 + 16 * (F.item_base + i));
+    const float4 a = gp[0], b = gp[1], c = gp[2], d = gp[3];
+    if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f && b.x == 0.f && b.y == 0.f && b.z == 0.f &&
+        b.w == 0.f && c.x == 0.f && c.y == 0.f && c.z == 0.f && c.w == 0.f && d.x == 0.f)
+      continue;
+    any = true;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    gp[0] = zero; gp[1] = zero; gp[2] = zero; gp[3] = zero;
+    const float* R = F.R;
+    // sensor frame quantities
+    float tu[3], tv[3], n[3], mu[3];
+    const float dm[3] = {mw[0] - F.o[0], mw[1] - F.o[1], mw[2] - F.o[2]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      tu[k] = R[k] * c0[0] + R[3 + k] * c0[1] + R[6 + k] * c0[2];
+      tv[k] = R[k] * c1[0] + R[3 + k] * c1[1] + R[6 + k] * c1[2];
+      n[k] = R[k] * c2[0] + R[3 + k] * c2[1] + R[6 + k] * c2[2];
+      mu[k] = R[k] * dm[0] + R[3 + k] * dm[1] + R[6 + k] * dm[2];
+    }
+    const float g_n[3] = {a.x, a.y, a.z}, g_h = a.w;
+    const float g_au[3] = {b.x, b.y, b.z}, g_bu = b.w;
+    const float g_av[3] = {c.x, c.y, c.z}, g_bv = c.w;
+    const float g_al = d.x;
+    const float bu = (tu[0] * mu[0] + tu[1] * mu[1] + tu[2] * mu[2]) * isu;
+    const float bv = (tv[0] * mu[0] + tv[1] * mu[1] + tv[2] * mu[2]) * isv;
+    float gtu[3], gtv[3], gnn[3], gmu[3];
+    float dau = 0.f, dav = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gtu[k] = (g_au[k] + g_bu * mu[k]) * isu;
+      gtv[k] = (g_av[k] + g_bv * mu[k]) * isv;
+      gnn[k] = g_n[k] + g_h * mu[k];
+      gmu[k] = g_h * n[k] + g_bu * isu * tu[k] + g_bv * isv * tv[k];
+      dau += g_au[k] * tu[k] * isu;
+      dav += g_av[k] * tv[k] * isv;
+    }
+    gls0 -= dau + g_bu * bu;
+    gls1 -= dav + g_bv * bv;
+    galpha += g_al;
+    // back to the world frame: v_w = R v_s
+#pragma unroll
+    for (int a2 = 0; a2 < 3; ++a2) {
+      gm[a2] += R[3 * a2] * gmu[0] + R[3 * a2 + 1] * gmu[1] + R[3 * a2 + 2] * gmu[2];
+      G0[a2] += R[3 * a2] * gtu[0] + R[3 * a2 + 1] * gtu[1] + R[3 * a2 + 2] * gtu[2];
+      G1[a2] += R[3 * a2] * gtv[0] + R[3 * a2 + 1] * gtv[1] + R[3 * a2 + 2] * gtv[2];
+      G2[a2] += R[3 * a2] * gnn[0] + R[3 * a2 + 1] * gnn[1] + R[3 * a2 + 2] * gnn[2];
+    }
+  }
+  if (!any) return;
+  // d/dq_hat of the columns of R(q_hat), contracted with (G0, G1, G2)
+  const float gw = G0[1] * 2.f * z - G0[2] * 2.f * y - G1[0] * 2.f * z + G1[2] * 2.f * x + G2[0] * 2.f * y -
+                   G2[1] * 2.f * x;
+  const float gx = G0[1] * 2.f * y + G0[2] * 2.f * z + G1[0] * 2.f * y - G1[1] * 4.f * x + G1[2] * 2.f * w +
+                   G2[0] * 2.f * z - G2[1] * 2.f * w - G2[2] * 4.f * x;
+  const float gy = -G0[0] * 4.f * y + G0[1] * 2.f * x - G0[2] * 2.f * w + G1[0] * 2.f * x + G1[2] * 2.f * z +
+                   G2[0] * 2.f * w + G2[1] * 2.f * z - G2[2] * 4.f * y;
+  const float gz = -G0[0] * 4.f * z + G0[1] * 2.f * w + G0[2] * 2.f * x - G1[0] * 2.f * w - G1[1] * 4.f * z +
+                   G1[2] * 2.f * y + G2[0] * 2.f * x + G2[1] * 2.f * y;
+  // through q_hat = q / |q|
+  const float pr = gw * w + gx * x + gy * y + gz * z;
+  M.d_quat[4 * i] += (gw - w * pr) * inv;
+  M.d_quat[4 * i + 1] += (gx - x * pr) * inv;
+  M.d_quat[4 * i + 2] += (gy - y * pr) * inv;
+  M.d_quat[4 * i + 3] += (gz - z * pr) * inv;
+  M.d_mean[3 * i] += gm[0];
+  M.d_mean[3 * i + 1] += gm[1];
+  M.d_mean[3 * i + 2] += gm[2];
+  M.d_ls[2 * i] += gls0;
+  M.d_ls[2 * i + 1] += gls1;
+  M.d_logit[i] += galpha * alpha * (1.f - alpha);
+}
+
+cudaError_t launch_preprocess_bwd(const Layout&, const WsPtrs& w, const Desc& h, cudaStream_t s) {
+  const int64_t n = h.n_surf > 0 ? h.n_surf : 1;
+  k_preprocess_bwd<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(w.desc, w.g13);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Mapping loss (Eqs. depthloss, normalloss, scaleloss, totalloss)
+//   per frame f of map m (F_m frames render map m):
+//     L_img,f = L_depth + la L_alpha + ln lng L_ng
+//   L = sum_m [ (1/F_m) sum_{f in m} L_img,f + ls L_scale,m ]
+// with masked means over M_D = [D > 0] and M_N = M_D [|N_gicp| > 0].
+// ---------------------------------------------------------------------------
+constexpr int kLossBlocks = 64;   // CTAs per frame (fixed: deterministic partial sums)
+constexpr int kScaleBlocks = 64;  // CTAs per map for the scale regulariser
+
+__device__ __forceinline__ double block_sum_d(double v, double* s_w) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) s_w[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) t += s_w[i];
+  return t;
+}
+
+__global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, Status* __restrict__ st) {
+  const FrameDev& F = D->f[blockIdx.y];
+  const int HW = F.H * F.W;
+  int md = 0, mn = 0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
+    const bool d = F.D[p] > 0.f;
+    const float a = F.Ng[p], b = F.Ng[HW + p], c = F.Ng[2 * HW + p];
+    md += d;
+    mn += d && (a * a + b * b + c * c > 0.f);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    md += __shfl_xor_sync(0xffffffffu, md, o);
+    mn += __shfl_xor_sync(0xffffffffu, mn, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (md) atomicAdd(&st->loss_count[2 * blockIdx.y], md);
+    if (mn) atomicAdd(&st->loss_count[2 * blockIdx.y + 1], mn);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_loss_pixel(const Desc* __restrict__ D, const Status* __restrict__ st,
+                                                     lgs_loss_params P, double* __restrict__ part) {
+  __shared__ double s_w[8];
+  const int f = blockIdx.y;
+  const FrameDev& F = D->f[f];
+  const int HW = F.H * F.W;
+  const int nd = st->loss_count[2 * f], nn = st->loss_count[2 * f + 1];
+  const float scale = 1.0f / static_cast<float>(D->m[F.map].n_frames);
+  const float ind = nd > 0 ? 1.0f / static_cast<float>(nd) : 0.f;
+  const float inn = nn > 0 ? 1.0f / static_cast<float>(nn) : 0.f;
+  double ld = 0.0, la = 0.0, ln = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
+    float gA = 0.f, gSt = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    const float Dm = F.D[p];
+    if (Dm > 0.f) {
+      const float A = F.A[p], St = F.St[p];
+      const float a = A + 1e-6f;
+      const float Dh = St / a;
+      const float diff = Dh - Dm;
+      ld += fabsf(diff);
+      const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+      const float gDh = sgn * ind;
+      gSt = scale * gDh / a;
+      gA = scale * (-gDh * St / (a * a));
+      la -= logf(A + 1e-6f);
+      gA -= scale * P.lambda_alpha * ind / (A + 1e-6f);
+      const float nx = F.Ng[p], ny = F.Ng[HW + p], nz = F.Ng[2 * HW + p];
+      if (nx * nx + ny * ny + nz * nz > 0.f) {
+        const float sx = F.Sn[p], sy = F.Sn[HW + p], sz = F.Sn[2 * HW + p];
+        const float m = sqrtf(sx * sx + sy * sy + sz * sz + 1e-12f);
+        const float im = 1.f / m;
+        ln += 1.0 - static_cast<double>((sx * nx + sy * ny + sz * nz) * im);
+        const float k = -P.lambda_n * P.lambda_ng * inn;
+        const float g0 = k * nx, g1 = k * ny, g2 = k * nz;
+        const float sg = (sx * g0 + sy * g1 + sz * g2) * im * im * im;
+        gx = scale * (g0 * im - sx * sg);
+        gy = scale * (g1 * im - sy * sg);
+        gz = scale * (g2 * im - sz * sg);
+      }
+    }
+    F.oA[p] = gA;
+    F.oSt[p] = gSt;
+    F.oSn[p] = gx;
+    F.oSn[HW + p] = gy;
+    F.oSn[2 * HW + p] = gz;
+  }
+  const double t0 = block_sum_d(ld, s_w);
+  const double t1 = block_sum_d(la, s_w);
+  const double t2 = block_sum_d(ln, s_w);
+  if (threadIdx.x == 0) {
+    double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + blockIdx.x);
+    o[0] = t0;
+    o[1] = t1;
+    o[2] = t2;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scale_reg(const Desc* __restrict__ D, lgs_loss_params P, int write_grad,
+                                                    double* __restrict__ part) {
+  __shared__ double s_w[8];
+  const MapDev& M = D->m[blockIdx.y];
+  double acc = 0.0;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < M.n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float s0 = expf(M.ls[2 * i]), s1 = expf(M.ls[2 * i + 1]);
+    const bool first = s0 >= s1;
+    const float sm = first ? s0 : s1;
+    if (sm > P.s_max) {
+      acc += static_cast<double>(sm - P.s_max);
+      if (write_grad) M.d_ls[2 * i + (first ? 0 : 1)] += P.lambda_s * sm;
+    }
+  }
+  const double t = block_sum_d(acc, s_w);
+  if (threadIdx.x == 0) part[blockIdx.y * kScaleBlocks + blockIdx.x] = t;
+}
+
+__global__ void k_loss_final(const Desc* __restrict__ D, const Status* __restrict__ st, lgs_loss_params P,
+                             const double* __restrict__ part, const double* __restrict__ spart,
+                             float* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double Lmap[LGS_MAX_MAPS];
+  for (int m = 0; m < D->n_maps; ++m) Lmap[m] = 0.0;
+  for (int f = 0; f < D->n_frames; ++f) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int b = 0; b < kLossBlocks; ++b) {
+      const double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + b);
+      s0 += o[0];
+      s1 += o[1];
+      s2 += o[2];
+    }
+    const int nd = st->loss_count[2 * f], nn = st->loss_count[2 * f + 1];
+    const double Ld = nd ? s0 / nd : 0.0, La = nd ? s1 / nd : 0.0, Ln = nn ? s2 / nn : 0.0;
+    out[1 + 3 * f] = static_cast<float>(Ld);
+    out[2 + 3 * f] = static_cast<float>(La);
+    out[3 + 3 * f] = static_cast<float>(Ln);
+    const int m = D->f[f].map;
+    Lmap[m] += (Ld + P.lambda_alpha * La + static_cast<double>(P.lambda_n) * P.lambda_ng * Ln) / D->m[m].n_frames;
+  }
+  double L = 0.0;
+  for (int m = 0; m < D->n_maps; ++m) {
+    double sr = 0.0;
+    for (int b = 0; b < kScaleBlocks; ++b) sr += spart[m * kScaleBlocks + b];
+    Lmap[m] += P.lambda_s * sr;
+    out[1 + 3 * D->n_frames + m] = static_cast<float>(Lmap[m]);
+    L += Lmap[m];
+  }
+  out[0] = static_cast<float>(L);
+}
+
+cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
+                        float* loss_out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(w.st->loss_count, 0, sizeof(int) * 2 * LGS_MAX_FRAMES, s);
+  if (e != cudaSuccess) return e;
+  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, w.st);
+  k_loss_pixel<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, w.st, p, w.loss_part);
+  double* spart = w.loss_part + 4 * static_cast<int64_t>(LGS_MAX_FRAMES) * kLossBlocks;
+  k_scale_reg<<<dim3(kScaleBlocks, h.n_maps), 256, 0, s>>>(w.desc, p, scale_grad ? 1 : 0, spart);
+  k_loss_final<<<1, 32, 0, s>>>(w.desc, w.st, p, w.loss_part, spart, loss_out);
+  return cudaGetLastError();
+}
+
+size_t loss_part_bytes() {
+  return sizeof(double) * (4 * static_cast<size_t>(LGS_MAX_FRAMES) * kLossBlocks +
+                           static_cast<size_t>(LGS_MAX_MAPS) * kScaleBlocks);
+}
+
+// ---------------------------------------------------------------------------
+// Adam (the paper does not name its optimiser; this is the mapping loop's)
+// ---------------------------------------------------------------------------
+struct AdamSeg {
+  float* p[4];
+  float* g[4];
+  float* m[4];
+  float* v[4];
+  int64_t n[4];
+  float lr[4];
+};
+
+__global__ void __launch_bounds__(256) k_adam(AdamSeg a, float b1, float b2, float eps, float c1, float c2,
+                                               int zero_grad) {
+  const int sgm = blockIdx.y;
+  float* __restrict__ p = a.p[sgm];
+  float* __restrict__ g = a.g[sgm];
+  float* __restrict__ m = a.m[sgm];
+  float* __restrict__ v = a.v[sgm];
+  const float lr = a.lr[sgm];
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n[sgm];
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    if (zero_grad) g[i] = 0.f;
+  }
+}
+
+cudaError_t launch_adam(float* p[4], float* g[4], float* m[4], float* v[4], const int64_t cnt[4], int64_t step,
+                        const float lr[4], float b1, float b2, float eps, int zero_grad, cudaStream_t s) {
+  AdamSeg a;
+  int64_t mx = 1;
+  for (int k = 0; k < 4; ++k) {
+    a.p[k] = p[k]; a.g[k] = g[k]; a.m[k] = m[k]; a.v[k] = v[k]; a.n[k] = cnt[k]; a.lr[k] = lr[k];
+    if (cnt[k] > mx) mx = cnt[k];
+  }
+  const double c1 = 1.0 / (1.0 - pow(static_cast<double>(b1), static_cast<double>(step)));
+  const double c2 = 1.0 / (1.0 - pow(static_cast<double>(b2), static_cast<double>(step)));
+  int64_t blocks = (mx + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_adam<<<dim3(static_cast<unsigned>(blocks), 4), 256, 0, s>>>(a, b1, b2, eps, static_cast<float>(c1),
+                                                                 static_cast<float>(c2), zero_grad);
+  return cudaGetLastError();
+}
+
+}  // namespace lgs

@@ -1,0 +1,362 @@
+// lgs_raster.cu -- per-tile front-to-back compositing (forward) and its
+// reverse-order adjoint (backward) for the spherical surfel rasterizer.
+//
+// One CTA renders one angular tile (tile_h x tile_w pixels, one thread per
+// pixel).  The tile's depth-ordered list is streamed through shared memory in
+// batches of BATCH records (64 B each, gathered by item id); every thread
+// walks the batch for its own ray.  Pixels stop once T (1 - a) would drop
+// below 1e-4; a warp whose lanes have all stopped skips the batch, and the
+// CTA leaves when every pixel has stopped.
+//
+// The backward re-evaluates the same records per tile in reverse list order
+// (no per-pixel surfel lists are stored): the transmittance before each
+// contributor is recovered as T_k = T_{k+1} / (1 - a_k) from T_final, and the
+// suffix sum S = sum_{j>k} w_j (g . c_j) gives dL/da_k = T_k (g . c_k) -
+// S / (1 - a_k).  Per entry the warp reduces its 13 record gradients with a
+// butterfly reduce-scatter (16 shuffles), 13 lanes add them into a shared
+// per-batch accumulator, and the CTA flushes one atomic add per (surfel,
+// component) into the per-item gradient buffer.
+#include <cuda_runtime.h>
+
+#include "lgs_internal.cuh"
+
+namespace lgs {
+
+constexpr int kMaxTileThreads = 256;
+
+struct TileCtx {
+  int f;
+  int r, c;
+  bool inside;
+  uint32_t start, end;
+  int64_t pix;
+  int HW;
+};
+
+__device__ __forceinline__ TileCtx tile_ctx(const Desc& D, uint32_t tile, const uint2* __restrict__ ranges) {
+  TileCtx t;
+  t.f = frame_of_tile(D, tile);
+  const FrameDev& F = D.f[t.f];
+  const int lt = static_cast<int>(tile - F.tile_base);
+  const int ti = lt / F.ntc, tj = lt - ti * F.ntc;
+  t.r = ti * F.th + static_cast<int>(threadIdx.x) / F.tw;
+  t.c = tj * F.tw + static_cast<int>(threadIdx.x) % F.tw;
+  t.inside = t.r < F.H && t.c < F.W;
+  t.pix = static_cast<int64_t>(t.r) * F.W + t.c;
+  t.HW = F.H * F.W;
+  const uint2 rg = ranges[tile];
+  t.start = rg.x;
+  t.end = rg.y;
+  return t;
+}
+
+// Work item of the CTA: its own tile, or (persistent mode) the next entry of
+// the longest-first order claimed through an atomic counter.
+__device__ __forceinline__ bool next_tile(bool persistent, const uint32_t* __restrict__ order, uint32_t n_tiles,
+                                          unsigned int* counter, uint32_t& tile, int iter) {
+  if (!persistent) {
+    tile = blockIdx.x;
+    return iter == 0;
+  }
+  __shared__ uint32_t s_tile;
+  __syncthreads();
+  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint32_t k = s_tile;
+  if (k >= n_tiles) return false;
+  tile = order ? order[k] : k;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Forward
+// ---------------------------------------------------------------------------
+template <int BATCH>
+__global__ void __launch_bounds__(kMaxTileThreads)
+    k_fwd(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
+          const float4* __restrict__ rec, const uint32_t* __restrict__ order, Status* __restrict__ st,
+          int persistent) {
+  __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[BATCH];
+  __shared__ float s_al[BATCH];
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  uint32_t tile;
+  unsigned long long evals = 0, contrib = 0;
+  for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
+    const TileCtx tc = tile_ctx(*D, tile, ranges);
+    const FrameDev& F = D->f[tc.f];
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    if (tc.inside) pixel_ray(F, tc.r, tc.c, dx, dy, dz);
+    float T = 1.0f, A = 0.0f, St = 0.0f, Sx = 0.0f, Sy = 0.0f, Sz = 0.0f;
+    int last = 0;
+    bool done = !tc.inside;
+    for (uint32_t b0 = tc.start; b0 < tc.end; b0 += BATCH) {
+      if (__syncthreads_and(done)) break;
+      const int nb = static_cast<int>(min(static_cast<uint32_t>(BATCH), tc.end - b0));
+      for (int j = tid; j < nb; j += nthr) {
+        const uint32_t item = pv[b0 + j];
+        const float4* rp = rec + 4 * static_cast<int64_t>(item);
+        s_r0[j] = rp[0];
+        s_r1[j] = rp[1];
+        s_r2[j] = rp[2];
+        s_al[j] = rp[3].x;
+      }
+      __syncthreads();
+      if (!done) {
+        int j = 0;
+        for (; j < nb; ++j) {
+          Eval e;
+          eval_pair(s_r0[j], s_r1[j], s_r2[j], s_al[j], dx, dy, dz, e);
+          if (!e.valid) continue;
+          const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.a));
+          if (Tn < 1e-4f) {
+            done = true;
+            break;
+          }
+          const float w = e.a * T;
+          const float ws = e.den > 0.f ? -w : w;
+          A += w;
+          St = fmaf(w, e.t, St);
+          Sx = fmaf(ws, s_r0[j].x, Sx);
+          Sy = fmaf(ws, s_r0[j].y, Sy);
+          Sz = fmaf(ws, s_r0[j].z, Sz);
+          T = Tn;
+          last = static_cast<int>(b0 - tc.start) + j + 1;
+          ++contrib;
+        }
+        evals += static_cast<unsigned long long>(j < nb ? j + 1 : nb);
+      }
+    }
+    if (tc.inside) {
+      F.A[tc.pix] = A;
+      F.St[tc.pix] = St;
+      F.Sn[tc.pix] = Sx;
+      F.Sn[tc.HW + tc.pix] = Sy;
+      F.Sn[2 * static_cast<int64_t>(tc.HW) + tc.pix] = Sz;
+      F.Tf[tc.pix] = T;
+      F.nc[tc.pix] = last;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    evals += __shfl_xor_sync(0xffffffffu, evals, o);
+    contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+  }
+  if ((tid & 31) == 0 && evals) atomicAdd(&st->evals_fwd, evals);
+  if ((tid & 31) == 0 && contrib) atomicAdd(&st->contrib_fwd, contrib);
+}
+
+// ---------------------------------------------------------------------------
+// Backward
+// ---------------------------------------------------------------------------
+// Butterfly reduce-scatter of 16 values over the warp: afterwards lane L holds
+// in v[0] the warp sum of value index 8 b4 + 4 b3 + 2 b2 + b1 (bits of L).
+__device__ __forceinline__ void warp_reduce16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[i] : v[i + 8];
+    const float keep = hi ? v[i + 8] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool hi = lane & 8;
+    const float send = hi ? v[i] : v[i + 4];
+    const float keep = hi ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = lane & 4;
+    const float send = hi ? v[i] : v[i + 2];
+    const float keep = hi ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool hi = lane & 2;
+    const float send = hi ? v[0] : v[1];
+    const float keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+template <int BATCH>
+__global__ void __launch_bounds__(kMaxTileThreads)
+    k_bwd(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
+          const float4* __restrict__ rec, float* __restrict__ g13, const uint32_t* __restrict__ order,
+          Status* __restrict__ st, int persistent) {
+  __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[BATCH];
+  __shared__ float s_al[BATCH];
+  __shared__ uint32_t s_item[BATCH];
+  __shared__ float s_g[13][BATCH];
+  __shared__ int s_max;
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int gidx = 8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+  const bool writer = ((lane & 1) == 0) && gidx < 13;
+  uint32_t tile;
+  unsigned long long evals = 0, contrib = 0;
+  for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
+    const TileCtx tc = tile_ctx(*D, tile, ranges);
+    const FrameDev& F = D->f[tc.f];
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    float T = 1.f, gA = 0.f, gSt = 0.f, gSx = 0.f, gSy = 0.f, gSz = 0.f;
+    int nc = 0;
+    if (tc.inside) {
+      pixel_ray(F, tc.r, tc.c, dx, dy, dz);
+      T = F.Tf[tc.pix];
+      nc = F.nc[tc.pix];
+      gA = F.gA[tc.pix];
+      gSt = F.gSt[tc.pix];
+      gSx = F.gSn[tc.pix];
+      gSy = F.gSn[tc.HW + tc.pix];
+      gSz = F.gSn[2 * static_cast<int64_t>(tc.HW) + tc.pix];
+    }
+    if (tid == 0) s_max = 0;
+    __syncthreads();
+    if (nc > 0) atomicMax(&s_max, nc);
+    __syncthreads();
+    // n_contrib comes from the caller: never walk past the tile's list
+    const uint32_t len = tc.end - tc.start;
+    const uint32_t stop = tc.start + min(static_cast<uint32_t>(s_max), len);
+    float S = 0.f;
+    for (uint32_t bend = stop; bend > tc.start;) {
+      const uint32_t b0 = bend - tc.start > static_cast<uint32_t>(BATCH) ? bend - BATCH : tc.start;
+      const int nb = static_cast<int>(bend - b0);
+      __syncthreads();
+      for (int j = tid; j < nb; j += nthr) {
+        const uint32_t item = pv[b0 + j];
+        s_item[j] = item;
+        const float4* rp = rec + 4 * static_cast<int64_t>(item);
+        s_r0[j] = rp[0];
+        s_r1[j] = rp[1];
+        s_r2[j] = rp[2];
+        s_al[j] = rp[3].x;
+#pragma unroll
+        for (int c = 0; c < 13; ++c) s_g[c][j] = 0.f;
+      }
+      __syncthreads();
+      for (int j = nb - 1; j >= 0; --j) {
+        const int k = static_cast<int>(b0 - tc.start) + j;
+        float v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = 0.f;
+        bool valid = false;
+        if (k < nc) {
+          const float4 r0 = s_r0[j];
+          const float alpha = s_al[j];
+          Eval e;
+          eval_pair(r0, s_r1[j], s_r2[j], alpha, dx, dy, dz, e);
+          ++evals;
+          valid = e.valid;
+          if (valid) {
+            ++contrib;
+            const float om = 1.0f - e.a;
+            const float Tk = __fdividef(T, om);
+            const float sg = e.den > 0.f ? -1.f : 1.f;
+            const float gc = gA + gSt * e.t + sg * (gSx * r0.x + gSy * r0.y + gSz * r0.z);
+            const float w = e.a * Tk;
+            const float dLda = Tk * gc - __fdividef(S, om);
+            S = fmaf(w, gc, S);
+            T = Tk;
+            float dLdt = w * gSt;
+            const float wsg = w * sg;
+            float dLdu = 0.f, dLdv = 0.f;
+            if (e.araw < 0.99f) {
+              v[12] = dLda * e.G;
+              const float dLdq = -0.5f * dLda * alpha * e.G;
+              dLdu = 2.f * e.u * dLdq;
+              dLdv = 2.f * e.v * dLdq;
+            }
+            dLdt = fmaf(dLdu, e.ud, fmaf(dLdv, e.vd, dLdt));
+            const float tu = dLdu * e.t, tv = dLdv * e.t;
+            v[4] = tu * dx; v[5] = tu * dy; v[6] = tu * dz; v[7] = -dLdu;
+            v[8] = tv * dx; v[9] = tv * dy; v[10] = tv * dz; v[11] = -dLdv;
+            const float inv_den = __fdividef(1.0f, e.den);
+            v[3] = dLdt * inv_den;
+            const float dden = -dLdt * e.t * inv_den;
+            v[0] = fmaf(dden, dx, wsg * gSx);
+            v[1] = fmaf(dden, dy, wsg * gSy);
+            v[2] = fmaf(dden, dz, wsg * gSz);
+          }
+        }
+        if (__any_sync(0xffffffffu, valid)) {
+          warp_reduce16(v, lane);
+          if (writer) atomicAdd(&s_g[gidx][j], v[0]);
+        }
+      }
+      __syncthreads();
+      for (int j = tid; j < nb; j += nthr) {
+        float* gp = g13 + 16 * static_cast<int64_t>(s_item[j]);
+#pragma unroll
+        for (int c = 0; c < 13; ++c) {
+          const float x = s_g[c][j];
+          if (x != 0.f) atomicAdd(gp + c, x);
+        }
+      }
+      bend = b0;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    evals += __shfl_xor_sync(0xffffffffu, evals, o);
+    contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+  }
+  if ((tid & 31) == 0 && evals) atomicAdd(&st->evals_bwd, evals);
+  if ((tid & 31) == 0 && contrib) atomicAdd(&st->contrib_bwd, contrib);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <int B>
+static cudaError_t fwd_b(const WsPtrs& w, const uint32_t* pv, const Desc& h, int persistent, int grid, cudaStream_t s) {
+  k_fwd<B><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, nullptr, w.st, persistent);
+  return cudaGetLastError();
+}
+
+template <int B>
+static cudaError_t bwd_b(const WsPtrs& w, const uint32_t* pv, const Desc& h, int persistent, int grid, cudaStream_t s) {
+  k_bwd<B><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.g13, nullptr, w.st,
+                                        persistent);
+  return cudaGetLastError();
+}
+
+static int persistent_grid(int threads) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = 2048 / (threads > 0 ? threads : 256);
+  return sms * (per_sm < 1 ? 1 : per_sm);
+}
+
+cudaError_t launch_raster_fwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
+                              int persistent, cudaStream_t s) {
+  if (persistent) {
+    cudaError_t e = cudaMemsetAsync(&w.st->work_counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
+  switch (batch) {
+    case 64: return fwd_b<64>(w, pv, h, persistent, grid, s);
+    case 128: return fwd_b<128>(w, pv, h, persistent, grid, s);
+    case 512: return fwd_b<512>(w, pv, h, persistent, grid, s);
+    default: return fwd_b<256>(w, pv, h, persistent, grid, s);
+  }
+}
+
+cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
+                              int persistent, cudaStream_t s) {
+  if (persistent) {
+    cudaError_t e = cudaMemsetAsync(&w.st->work_counter2, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
+  switch (batch) {
+    case 64: return bwd_b<64>(w, pv, h, persistent, grid, s);
+    case 128: return bwd_b<128>(w, pv, h, persistent, grid, s);
+    default: return bwd_b<256>(w, pv, h, persistent, grid, s);   // 512 is clamped by the caller
+  }
+}
+
+}  // namespace lgs

@@ -1,0 +1,400 @@
+"""Thin ctypes binding of ``liblgs.so`` (C ABI in ``include/lgs.h``).
+
+Every function named ``lgs_*`` here marshals its arguments and calls the C
+entry point of the same name; nothing of the rasterizer is computed in
+Python.  ``Session`` adds workspace management on top (a torch-allocated
+device buffer that grows when the pair capacity is exceeded) and accepts
+torch CUDA tensors.  Loading fails loudly when the library is missing: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblgs.so")
+_lib = None
+
+LGS_MAX_FRAMES = 64
+LGS_MAX_MAPS = 64
+STATUS = {0: "LGS_OK", 1: "LGS_ERR_INVALID_ARG", 2: "LGS_ERR_CAPACITY", 3: "LGS_ERR_BUDGET", 4: "LGS_ERR_CUDA",
+          5: "LGS_ERR_TIMEOUT", 6: "LGS_ERR_DEVICE_CHECK", 7: "LGS_ERR_NO_WORKSPACE", 8: "LGS_ERR_STATE"}
+LGS_OK, LGS_ERR_CAPACITY = 0, 2
+
+P = ctypes.c_void_p
+F32P = ctypes.POINTER(ctypes.c_float)
+
+
+class lgs_frame(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("tile_w", ctypes.c_int32), ("elev_min", ctypes.c_float), ("elev_max", ctypes.c_float),
+                ("pose", ctypes.c_float * 12)]
+
+
+class lgs_surfels(ctypes.Structure):
+    _fields_ = [("mean", P), ("quat", P), ("log_scale", P), ("opacity_logit", P), ("n", ctypes.c_int64)]
+
+
+class lgs_fwd_out(ctypes.Structure):
+    _fields_ = [("A", P), ("S_t", P), ("S_n", P), ("T_final", P), ("n_contrib", P)]
+
+
+class lgs_fwd_grad(ctypes.Structure):
+    _fields_ = [("dA", P), ("dS_t", P), ("dS_n", P)]
+
+
+class lgs_fwd_grad_out(ctypes.Structure):
+    _fields_ = [("dA", P), ("dS_t", P), ("dS_n", P)]
+
+
+class lgs_surfel_grad(ctypes.Structure):
+    _fields_ = [("d_mean", P), ("d_quat", P), ("d_log_scale", P), ("d_opacity_logit", P)]
+
+
+class lgs_target(ctypes.Structure):
+    _fields_ = [("D", P), ("N_gicp", P)]
+
+
+class lgs_loss_params(ctypes.Structure):
+    _fields_ = [("lambda_alpha", ctypes.c_float), ("lambda_n", ctypes.c_float), ("lambda_ng", ctypes.c_float),
+                ("lambda_s", ctypes.c_float), ("s_max", ctypes.c_float)]
+
+
+class lgs_tuning(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int32), ("persistent", ctypes.c_int32)]
+
+
+EXPORTS = [
+    "lgs_session_create", "lgs_session_destroy", "lgs_session_workspace_size", "lgs_batch_workspace_size",
+    "lgs_session_set_workspace", "lgs_session_status", "lgs_session_pair_count", "lgs_session_counters",
+    "lgs_session_bins", "lgs_session_read_bins", "lgs_bin_sort", "lgs_render_fwd", "lgs_render_bwd", "lgs_loss", "lgs_bin_sort_batch",
+    "lgs_render_fwd_batch", "lgs_render_bwd_batch", "lgs_loss_batch", "lgs_session_set_tuning", "lgs_adam_step",
+    "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version",
+]
+
+
+def load():
+    """Load liblgs.so (built by ``build.py``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_2607_04127_gb300/build.py "
+                           "(there is no CPU fallback for the rasterizer)")
+    lib = ctypes.CDLL(LIB_PATH)
+    i32, i64, sz = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    S = ctypes.c_int
+    sig = {
+        "lgs_session_create": ([i32, sz, ctypes.POINTER(P)], S),
+        "lgs_session_destroy": ([P], S),
+        "lgs_session_workspace_size": ([P, i64, P, i32, i64, ctypes.POINTER(sz)], S),
+        "lgs_batch_workspace_size": ([P, P, i32, P, P, i32, i64, ctypes.POINTER(sz)], S),
+        "lgs_session_set_workspace": ([P, P, sz], S),
+        "lgs_session_status": ([P, ctypes.POINTER(i64)], S),
+        "lgs_session_pair_count": ([P, ctypes.POINTER(i64)], S),
+        "lgs_session_counters": ([P, P], S),
+        "lgs_session_bins": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)], S),
+        "lgs_session_read_bins": ([P, P, P, P, P, i64], S),
+        "lgs_bin_sort": ([P, P, P, i32, P], S),
+        "lgs_render_fwd": ([P, P, P, i32, P, P], S),
+        "lgs_render_bwd": ([P, P, P, i32, P, P, P, P], S),
+        "lgs_loss": ([P, P, P, i32, P, P, P, P, P, P, P], S),
+        "lgs_bin_sort_batch": ([P, P, i32, P, P, i32, P], S),
+        "lgs_render_fwd_batch": ([P, P, i32, P, P, i32, P, P], S),
+        "lgs_render_bwd_batch": ([P, P, i32, P, P, i32, P, P, P, P], S),
+        "lgs_loss_batch": ([P, P, i32, P, P, i32, P, P, P, P, P, P, P], S),
+        "lgs_session_set_tuning": ([P, P], S),
+        "lgs_adam_step": ([P, P, P, P, P, P, P, i64, i64, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                           i32, P], S),
+        "lgs_status_string": ([i32], ctypes.c_char_p),
+        "lgs_last_error": ([], ctypes.c_char_p),
+        "lgs_constants": ([P], None),
+        "lgs_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+class LgsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st: int):
+    if st != LGS_OK:
+        msg = load().lgs_last_error().decode()
+        raise LgsError(st, msg)
+    return st
+
+
+def _ref(x):
+    return ctypes.byref(x)
+
+
+def _arr(ctype, items):
+    a = (ctype * len(items))()
+    for i, it in enumerate(items):
+        a[i] = it
+    return a
+
+
+# ---------------------------------------------------------------------------
+# Same-name wrappers of the C entry points (argument marshalling only)
+# ---------------------------------------------------------------------------
+def lgs_session_create(device: int = 0, hbm_budget_bytes: int = 0):
+    h = P()
+    _check(load().lgs_session_create(device, hbm_budget_bytes, ctypes.byref(h)))
+    return h
+
+
+def lgs_session_destroy(h):
+    return load().lgs_session_destroy(h)
+
+
+def lgs_session_workspace_size(h, n_surfels, frames, max_pairs) -> int:
+    fr = _arr(lgs_frame, frames)
+    out = ctypes.c_size_t()
+    _check(load().lgs_session_workspace_size(h, n_surfels, fr, len(frames), max_pairs, ctypes.byref(out)))
+    return out.value
+
+
+def lgs_batch_workspace_size(h, map_sizes, frames, frame_map, max_pairs) -> int:
+    ms = _arr(ctypes.c_int64, map_sizes)
+    fr = _arr(lgs_frame, frames)
+    fm = _arr(ctypes.c_int32, frame_map)
+    out = ctypes.c_size_t()
+    _check(load().lgs_batch_workspace_size(h, ms, len(map_sizes), fr, fm, len(frames), max_pairs,
+                                           ctypes.byref(out)))
+    return out.value
+
+
+def lgs_session_set_workspace(h, ptr: int, nbytes: int):
+    _check(load().lgs_session_set_workspace(h, P(ptr), nbytes))
+
+
+def lgs_session_status(h):
+    req = ctypes.c_int64()
+    st = load().lgs_session_status(h, ctypes.byref(req))
+    return st, req.value
+
+
+def lgs_session_pair_count(h) -> int:
+    n = ctypes.c_int64()
+    _check(load().lgs_session_pair_count(h, ctypes.byref(n)))
+    return n.value
+
+
+def lgs_session_counters(h):
+    out = (ctypes.c_int64 * 8)()
+    _check(load().lgs_session_counters(h, out))
+    return dict(n_pairs=out[0], n_visible=out[1], evals_fwd=out[2], evals_bwd=out[3], contrib_fwd=out[4],
+                contrib_bwd=out[5], launches=out[6])
+
+
+def lgs_session_bins(h):
+    a, b, c, d = P(), P(), P(), P()
+    _check(load().lgs_session_bins(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def lgs_session_read_bins(h, n_items: int, n_tiles: int):
+    """Host copies of the last bin_sort: (tile_of_pair, item_of_pair, ranges [T,2], depth_key)."""
+    n_pairs = lgs_session_pair_count(h)
+    tp = np.zeros(max(n_pairs, 1), np.uint32); ip = np.zeros(max(n_pairs, 1), np.uint32)
+    rg = np.zeros((max(n_tiles, 1), 2), np.uint32); dk = np.zeros(max(n_items, 1), np.uint32)
+    _check(load().lgs_session_read_bins(h, tp.ctypes.data, ip.ctypes.data, rg.ctypes.data, dk.ctypes.data,
+                                        n_pairs))
+    return tp[:n_pairs], ip[:n_pairs], rg[:n_tiles], dk[:n_items]
+
+
+def lgs_bin_sort_batch(h, maps, frames, frame_map, stream):
+    _check(load().lgs_bin_sort_batch(h, _arr(lgs_surfels, maps), len(maps), _arr(lgs_frame, frames),
+                                     _arr(ctypes.c_int32, frame_map), len(frames), P(stream)))
+
+
+def lgs_render_fwd_batch(h, maps, frames, frame_map, outs, stream):
+    _check(load().lgs_render_fwd_batch(h, _arr(lgs_surfels, maps), len(maps), _arr(lgs_frame, frames),
+                                       _arr(ctypes.c_int32, frame_map), len(frames), _arr(lgs_fwd_out, outs),
+                                       P(stream)))
+
+
+def lgs_render_bwd_batch(h, maps, frames, frame_map, fwd, upstream, grads, stream):
+    _check(load().lgs_render_bwd_batch(h, _arr(lgs_surfels, maps), len(maps), _arr(lgs_frame, frames),
+                                       _arr(ctypes.c_int32, frame_map), len(frames), _arr(lgs_fwd_out, fwd),
+                                       _arr(lgs_fwd_grad, upstream), _arr(lgs_surfel_grad, grads), P(stream)))
+
+
+def lgs_loss_batch(h, maps, frames, frame_map, fwd, targets, params, grads_out, grads, loss_out_ptr, stream):
+    _check(load().lgs_loss_batch(h, _arr(lgs_surfels, maps), len(maps), _arr(lgs_frame, frames),
+                                 _arr(ctypes.c_int32, frame_map), len(frames), _arr(lgs_fwd_out, fwd),
+                                 _arr(lgs_target, targets), _ref(params), _arr(lgs_fwd_grad_out, grads_out),
+                                 _arr(lgs_surfel_grad, grads) if grads is not None else None,
+                                 P(loss_out_ptr), P(stream)))
+
+
+def lgs_bin_sort(h, surfels, frames, stream):
+    _check(load().lgs_bin_sort(h, _ref(surfels), _arr(lgs_frame, frames), len(frames), P(stream)))
+
+
+def lgs_render_fwd(h, surfels, frames, outs, stream):
+    _check(load().lgs_render_fwd(h, _ref(surfels), _arr(lgs_frame, frames), len(frames), _arr(lgs_fwd_out, outs),
+                                 P(stream)))
+
+
+def lgs_render_bwd(h, surfels, frames, fwd, upstream, grad, stream):
+    _check(load().lgs_render_bwd(h, _ref(surfels), _arr(lgs_frame, frames), len(frames), _arr(lgs_fwd_out, fwd),
+                                 _arr(lgs_fwd_grad, upstream), _ref(grad), P(stream)))
+
+
+def lgs_loss(h, surfels, frames, fwd, targets, params, grads_out, grad, loss_out_ptr, stream):
+    _check(load().lgs_loss(h, _ref(surfels), _arr(lgs_frame, frames), len(frames), _arr(lgs_fwd_out, fwd),
+                           _arr(lgs_target, targets), _ref(params), _arr(lgs_fwd_grad_out, grads_out),
+                           _ref(grad) if grad is not None else None, P(loss_out_ptr), P(stream)))
+
+
+def lgs_session_set_tuning(h, batch: int = 256, persistent: int = 0):
+    _check(load().lgs_session_set_tuning(h, _ref(lgs_tuning(batch, persistent))))
+
+
+def lgs_adam_step(mean, quat, log_scale, logit, grad, m_state, v_state, n, step, lr, beta1, beta2, eps,
+                  zero_grad, stream):
+    lra = _arr(ctypes.c_float, [float(x) for x in lr])
+    _check(load().lgs_adam_step(P(mean), P(quat), P(log_scale), P(logit), _ref(grad), P(m_state), P(v_state),
+                                n, step, lra, beta1, beta2, eps, int(zero_grad), P(stream)))
+
+
+def lgs_status_string(st: int) -> str:
+    return load().lgs_status_string(st).decode()
+
+
+def lgs_constants() -> np.ndarray:
+    out = (ctypes.c_float * 16)()
+    load().lgs_constants(out)
+    return np.array(out[:], np.float32)
+
+
+def lgs_version() -> str:
+    return load().lgs_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# Conversions from scenes.Frame / torch tensors
+# ---------------------------------------------------------------------------
+def frame_struct(fr) -> lgs_frame:
+    f = lgs_frame()
+    f.H, f.W, f.tile_h, f.tile_w = int(fr.H), int(fr.W), int(fr.tile_h), int(fr.tile_w)
+    f.elev_min, f.elev_max = float(fr.elev_min), float(fr.elev_max)
+    pose = np.asarray(fr.pose, np.float32).reshape(12)
+    for k in range(12):
+        f.pose[k] = float(pose[k])
+    return f
+
+
+def surfels_struct(mean, quat, log_scale, logit) -> lgs_surfels:
+    for t in (mean, quat, log_scale, logit):
+        if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"):
+            raise ValueError("surfel tensors must be contiguous float32 CUDA tensors")
+    return lgs_surfels(mean.data_ptr(), quat.data_ptr(), log_scale.data_ptr(), logit.data_ptr(),
+                       int(mean.shape[0]))
+
+
+def grad_struct(g_mean, g_quat, g_ls, g_logit) -> lgs_surfel_grad:
+    return lgs_surfel_grad(g_mean.data_ptr(), g_quat.data_ptr(), g_ls.data_ptr(), g_logit.data_ptr())
+
+
+@dataclass
+class FwdBuffers:
+    """Per-frame forward outputs (torch CUDA tensors)."""
+    A: "object"
+    S_t: "object"
+    S_n: "object"
+    T_final: "object"
+    n_contrib: "object"
+
+    def struct(self) -> lgs_fwd_out:
+        return lgs_fwd_out(self.A.data_ptr(), self.S_t.data_ptr(), self.S_n.data_ptr(), self.T_final.data_ptr(),
+                           self.n_contrib.data_ptr())
+
+
+def alloc_fwd(frame, device) -> FwdBuffers:
+    import torch
+    H, W = int(frame.H), int(frame.W)
+    f32 = dict(dtype=torch.float32, device=device)
+    return FwdBuffers(torch.empty(H, W, **f32), torch.empty(H, W, **f32), torch.empty(3, H, W, **f32),
+                      torch.empty(H, W, **f32), torch.empty(H, W, dtype=torch.int32, device=device))
+
+
+class Session:
+    """A library session plus its torch-allocated workspace.
+
+    ``bin_sort`` sizes the workspace from a pair estimate and, when the
+    device reports that more pairs were needed, grows it and bins again
+    (that check synchronises; pass ``check=False`` in steady-state loops whose
+    workspace already has head-room, and call ``check_status`` later)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, pairs_per_item: float = 4.0,
+                 headroom: float = 1.25):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.handle = lgs_session_create(device, hbm_budget_bytes)
+        self.ws = None
+        self.pairs_per_item = pairs_per_item
+        self.headroom = headroom
+        self.max_pairs = 0
+        self._key = None
+
+    def close(self):
+        if self.handle:
+            lgs_session_destroy(self.handle)
+            self.handle = None
+            self.ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, map_sizes, frames, frame_map, max_pairs: int):
+        nbytes = lgs_batch_workspace_size(self.handle, map_sizes, frames, frame_map, max_pairs)
+        if self.ws is None or self.ws.numel() < nbytes:
+            self.ws = None
+            self.ws = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=self.device)
+            base = (self.ws.data_ptr() + 255) // 256 * 256
+            lgs_session_set_workspace(self.handle, base, nbytes)
+        self.max_pairs = max_pairs
+        self._key = (tuple(map_sizes), len(frames))
+
+    def bin_sort(self, maps, frames, frame_map=None, stream=None, check: bool = True):
+        """maps: list of lgs_surfels; frames: list of lgs_frame."""
+        frame_map = list(frame_map) if frame_map is not None else [0] * len(frames)
+        sizes = [int(m.n) for m in maps]
+        items = sum(sizes[frame_map[f]] for f in range(len(frames)))
+        want = int(max(1024, items * self.pairs_per_item))
+        if self.ws is None or self._key != (tuple(sizes), len(frames)) or self.max_pairs < want:
+            self.reserve(sizes, frames, frame_map, max(want, self.max_pairs))
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream
+        lgs_bin_sort_batch(self.handle, maps, frames, frame_map, s)
+        if check:
+            st, req = lgs_session_status(self.handle)
+            if st == LGS_ERR_CAPACITY:
+                self.pairs_per_item = max(self.pairs_per_item, self.headroom * req / max(items, 1))
+                self.reserve(sizes, frames, frame_map, int(req * self.headroom) + 1024)
+                lgs_bin_sort_batch(self.handle, maps, frames, frame_map, s)
+                st, req = lgs_session_status(self.handle)
+            _check(st)
+
+    def check_status(self):
+        st, req = lgs_session_status(self.handle)
+        _check(st)
+        return req
