@@ -53,6 +53,7 @@
 #define EPS_LOG  1e-6         /* L_alpha = -mean log(A + EPS_LOG)              */
 #define FLAG_REL 1e-3         /* band around a threshold that flags a pixel    */
 #define DEN_FLAG 1e-5         /* |n.d| below this flags a pixel                 */
+#define EPS32    5.9604644775390625e-08  /* 2^-24, unit roundoff of binary32  */
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -381,6 +382,24 @@ typedef struct { int valid, flags; double den, t, x[3], u, v, q, G, araw, a; } e
  * coordinates u = t_u.(t d - mu)/s_u, v = t_v.(t d - mu)/s_v, Gaussian
  * G = exp(-(u^2+v^2)/2), opacity a = min(alpha G, 0.99), with the skip rules
  * |n.d| < 1e-6, t <= t_near, u^2+v^2 > 9, a < 1/255. */
+/* Binary32 uncertainty of one evaluation (test infrastructure): an FP32
+ * evaluation sees the sensor-frame geometry and the ray rounded to 24 bits,
+ * so h = n.mu is known to about EPS32 |mu| and n.d to about EPS32; the ray
+ * parameter t = h/(n.d) then has relative uncertainty
+ *   dt/t = EPS32 (2 + 2/|n.d| + |mu|/|h|),
+ * and a local coordinate u = t_u.(t d - mu)/s_u, of terms up to max(t,|mu|)/s,
+ *   ek   = EPS32 max(t, |mu|)/s_min (2 + 1/|n.d| + |mu|/|h|). */
+static void fp32_unc(const surf64* s, double den, double t, double* ek, double* dt)
+{
+    double g = 1.0 / fabs(den);
+    double rho = sqrt(dot3(s->mu, s->mu));
+    double h = fabs(t * den);
+    double hr = rho / (h > 1e-30 ? h : 1e-30);
+    double smin = s->su < s->sv ? s->su : s->sv;
+    *ek = EPS32 * ((fabs(t) > rho ? fabs(t) : rho) / smin) * (2.0 + g + hr);
+    *dt = fabs(t) * EPS32 * (2.0 + 2.0 * g + hr);
+}
+
 static void eval_pair(const surf64* s, const double* d, eval64* e)
 {
     e->valid = 0; e->flags = 0;
@@ -388,20 +407,45 @@ static void eval_pair(const surf64* s, const double* d, eval64* e)
     if (fabs(e->den) <= DEN_FLAG) e->flags |= FL_DEN;
     if (fabs(e->den) < DEN_EPS) return;
     e->t = dot3(s->n, s->mu) / e->den;
-    if (near_thr(e->t, T_NEAR)) e->flags |= FL_TNEAR;
+    /* binary32 uncertainty of t and of the local coordinates (see fp32_bound):
+     * a decision is "near" its threshold when it lies within the larger of
+     * FLAG_REL and a few times that uncertainty */
+    double ek, dt;
+    fp32_unc(s, e->den, e->t, &ek, &dt);
+    if (fabs(e->t - T_NEAR) <= FLAG_REL * T_NEAR + 4.0 * dt) e->flags |= FL_TNEAR;
     if (e->t <= T_NEAR) return;
     for (int k = 0; k < 3; ++k) e->x[k] = e->t * d[k] - s->mu[k];
     e->u = dot3(s->tu, e->x) / s->su;
     e->v = dot3(s->tv, e->x) / s->sv;
     e->q = e->u * e->u + e->v * e->v;
-    if (near_thr(e->q, Q_CUT)) e->flags |= FL_QCUT;
+    double dq = 2.0 * (fabs(e->u) + fabs(e->v)) * ek;
+    if (fabs(e->q - Q_CUT) <= FLAG_REL * Q_CUT + 4.0 * dq) e->flags |= FL_QCUT;
     if (e->q > Q_CUT) return;
     e->G = exp(-0.5 * e->q);
     e->araw = s->alpha * e->G;
     e->a = e->araw < A_MAX ? e->araw : A_MAX;
-    if (near_thr(e->araw, A_MAX)) e->flags |= FL_AMAX;
-    if (near_thr(e->a, A_MIN)) e->flags |= FL_AMIN;
+    double da = e->araw * (2.0 * dq + 4.0 * EPS32);     /* relative error of G is dq/2 */
+    if (fabs(e->araw - A_MAX) <= FLAG_REL * A_MAX + da) e->flags |= FL_AMAX;
+    if (fabs(e->a - A_MIN) <= FLAG_REL * A_MIN + da) e->flags |= FL_AMIN;
     if (e->a < A_MIN) return;
+    e->valid = 1;
+}
+
+/* The same quantities as eval_pair with no skip applied (t, u, v, q, G, a
+ * computed whatever the thresholds say); used to size the contribution of a
+ * near-threshold evaluation that a binary32 evaluation may decide otherwise. */
+static void force_eval(const surf64* s, const double* d, eval64* e)
+{
+    e->flags = 0;
+    e->den = dot3(s->n, d);
+    e->t = dot3(s->n, s->mu) / e->den;
+    for (int k = 0; k < 3; ++k) e->x[k] = e->t * d[k] - s->mu[k];
+    e->u = dot3(s->tu, e->x) / s->su;
+    e->v = dot3(s->tv, e->x) / s->sv;
+    e->q = e->u * e->u + e->v * e->v;
+    e->G = exp(-0.5 * e->q);
+    e->araw = s->alpha * e->G;
+    e->a = e->araw < A_MAX ? e->araw : A_MAX;
     e->valid = 1;
 }
 
@@ -417,13 +461,31 @@ static surf64* sensor_surfels(const double* mean, const double* quat, const doub
  * surfel, stop (without compositing it) if T (1 - a) < 1e-4, else
  * w = a T; A += w; S_t += w t; S_n += w (-sign(n.d)) n; T *= 1 - a.
  * Contributors are recorded in ck (list position), when ck != NULL. */
-typedef struct { double A, St, Sn[3], T; int32_t ncontrib; int64_t neval; int flags; } pix_out;
+typedef struct {
+    double A, St, Sn[3], T;
+    int32_t ncontrib;
+    int64_t neval;
+    int flags;
+    double flipA, flipAt;   /* sum of T a_w and T a_w |t| over near-threshold evaluations */
+    double flipa;           /* sum of a_w over near-threshold evaluations */
+} pix_out;
+
+/* Opacity (and ray parameter) the evaluation would have if its skip decision
+ * went the other way: a FP32 evaluation may decide a near-threshold case
+ * differently, and this is the size of what then changes. */
+static double would_be_a(const surf64* s, const eval64* e, double* t)
+{
+    if (e->flags & (FL_DEN | FL_TNEAR)) { *t = fabs(e->t); return s->alpha < A_MAX ? s->alpha : A_MAX; }
+    *t = fabs(e->t);
+    double a = s->alpha * exp(-0.5 * e->q);
+    return a < A_MAX ? a : A_MAX;
+}
 
 static int composite_pixel(const surf64* S, const uint32_t* list, int64_t len, const double* d,
                            pix_out* o, int64_t* ck, double* cT)
 {
     o->A = 0; o->St = 0; o->Sn[0] = o->Sn[1] = o->Sn[2] = 0; o->T = 1.0;
-    o->ncontrib = 0; o->neval = 0; o->flags = 0;
+    o->ncontrib = 0; o->neval = 0; o->flags = 0; o->flipA = 0; o->flipAt = 0; o->flipa = 0;
     int nc = 0;
     for (int64_t k = 0; k < len; ++k) {
         const surf64* s = S + list[k];
@@ -431,9 +493,20 @@ static int composite_pixel(const surf64* S, const uint32_t* list, int64_t len, c
         eval_pair(s, d, &e);
         o->neval++;
         o->flags |= e.flags;
+        if (e.flags & (FL_DEN | FL_TNEAR | FL_QCUT | FL_AMIN)) {
+            double tw, aw = would_be_a(s, &e, &tw);
+            o->flipA += o->T * aw;
+            o->flipAt += o->T * aw * tw;
+            o->flipa += aw;
+        }
         if (!e.valid) continue;
         double Tn = o->T * (1.0 - e.a);
-        if (near_thr(Tn, T_STOP)) o->flags |= FL_TSTOP;
+        if (near_thr(Tn, T_STOP)) {
+            o->flags |= FL_TSTOP;
+            o->flipA += o->T * e.a;
+            o->flipAt += o->T * e.a * e.t;
+            o->flipa += e.a;
+        }
         if (Tn < T_STOP) break;
         double w = e.a * o->T;
         double sg = e.den > 0 ? -1.0 : 1.0;           /* -sign(n.d) */
@@ -448,6 +521,41 @@ static int composite_pixel(const surf64* S, const uint32_t* list, int64_t len, c
     return nc;
 }
 
+/* Error bound of the pixel's outputs implied by binary32 representation of
+ * its inputs (test infrastructure, not part of the method).  A binary32
+ * evaluation sees every sensor-frame coordinate and ray component rounded to
+ * 24 bits; a local coordinate u = t_u.(t d - mu)/s_u then carries an error of
+ * about EPS32 max(t, |mu|)/s, amplified by 1/|n.d| through t = (n.mu)/(n.d).
+ * With e_k that error for contributor k:
+ *   da_k = a_k ((|u_k| + |v_k|) e_k + 4 EPS32),  dt_k = t_k EPS32 (2 + 2/|n.d|),
+ *   eA   = sum_k T_k da_k                      (|dA/da_k| <= T_k)
+ *   eD   = sum_k |dD/da_k| da_k + w_k dt_k / (A + 1e-6),
+ *   dD/da_k = [T_k (t_k - D) - sum_{j>k} w_j (t_j - D)/(1 - a_k)] / (A + 1e-6). */
+static void fp32_bound(const surf64* S, const uint32_t* list, const double* d, int nc, const int64_t* ck,
+                       const double* cT, const pix_out* o, double* eA, double* eD)
+{
+    double Dh = o->St / (o->A + EPS_A);
+    double ea = 0, ed = 0, suffix = 0;
+    for (int m = nc - 1; m >= 0; --m) {
+        const surf64* s = S + list[ck[m]];
+        eval64 e;
+        eval_pair(s, d, &e);
+        double T = cT[m], w = e.a * T;
+        double ek, dt;
+        fp32_unc(s, e.den, e.t, &ek, &dt);
+        double da = e.a * ((fabs(e.u) + fabs(e.v)) * ek + 4.0 * EPS32);
+        ea += T * da;
+        double dDda = (T * fabs(e.t - Dh) + suffix / (1.0 - e.a)) / (o->A + EPS_A);
+        ed += dDda * da + w * dt / (o->A + EPS_A);
+        suffix += w * fabs(e.t - Dh);
+    }
+    /* decisions within FLAG_REL of a threshold: the contribution that may flip */
+    ea += o->flipA;
+    ed += (o->flipAt + Dh * o->flipA) / (o->A + EPS_A);
+    *eA = ea;
+    *eD = ed;
+}
+
 /* Forward render of one frame.  ranges[2*tile] / ranges[2*tile+1] delimit the
  * tile's list in vals (surfel indices in depth order).  Outputs are planar
  * [H*W] (S_n: [3][H*W]).  pix_flag marks pixels where some evaluated quantity
@@ -457,16 +565,26 @@ void lgso_render_fwd(const double* mean, const double* quat, const double* ls, c
                      int64_t n, int H, int W, int th, int tw, double emin, double emax,
                      const double* pose, const int64_t* ranges, const uint32_t* vals,
                      double* A, double* St, double* Sn, double* Tf, int32_t* ncontrib,
-                     int64_t* neval, uint8_t* pix_flag, int32_t* nvalid, int nthreads)
+                     int64_t* neval, uint8_t* pix_flag, int32_t* nvalid, double* eA, double* eD,
+                     int nthreads)
 {
     frame64 F;
     make_frame(&F, H, W, th, tw, emin, emax, pose);
     surf64* S = sensor_surfels(mean, quat, ls, logit, n, &F);
     int64_t ntiles = (int64_t)F.ntr * F.ntc;
     int64_t HW = (int64_t)H * W;
+    int64_t maxlen = 1;
+    for (int64_t t = 0; t < ntiles; ++t)
+        if (ranges[2 * t + 1] - ranges[2 * t] > maxlen) maxlen = ranges[2 * t + 1] - ranges[2 * t];
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel
+#endif
+    {
+    int64_t* ck = (int64_t*)malloc(sizeof(int64_t) * maxlen);
+    double* cT = (double*)malloc(sizeof(double) * maxlen);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
 #endif
     for (int64_t tile = 0; tile < ntiles; ++tile) {
         int ti = (int)(tile / F.ntc), tj = (int)(tile % F.ntc);
@@ -476,15 +594,18 @@ void lgso_render_fwd(const double* mean, const double* quat, const double* ls, c
                 double d[3];
                 pixel_ray(&F, r, c, d);
                 pix_out o;
-                int nc = composite_pixel(S, vals + b, e - b, d, &o, NULL, NULL);
+                int nc = composite_pixel(S, vals + b, e - b, d, &o, ck, cT);
                 int64_t p = (int64_t)r * W + c;
                 if (nvalid) nvalid[p] = nc;
+                if (eA && eD) fp32_bound(S, vals + b, d, nc, ck, cT, &o, eA + p, eD + p);
                 A[p] = o.A; St[p] = o.St; Tf[p] = o.T;
                 Sn[p] = o.Sn[0]; Sn[HW + p] = o.Sn[1]; Sn[2 * HW + p] = o.Sn[2];
                 if (ncontrib) ncontrib[p] = o.ncontrib;
                 if (neval) neval[p] = o.neval;
                 if (pix_flag) pix_flag[p] = (uint8_t)o.flags;
             }
+    }
+    free(ck); free(cT);
     }
     free(S);
 }
@@ -527,55 +648,192 @@ int64_t lgso_coverage_misses(const double* mean, const double* quat, const doubl
 /* gradient w.r.t. the sensor-frame surfel quantities */
 typedef struct { double mu[3], tu[3], tv[3], n[3], su, sv, alpha; } sgrad;
 
-/* Reverse mode through composite_pixel for one pixel with upstream gradients
- * (gA, gSt, gSn) of (A, S_t, S_n).  With c_k = (1, t_k, n'_k), T_k the
- * transmittance before contributor k and w_k = a_k T_k:
- *   dL/da_k = T_k (g.c_k) - (sum_{j>k} w_j g.c_j) / (1 - a_k),
- * because every later weight w_j carries the factor (1 - a_k). */
-static void backward_pixel(const surf64* S, const uint32_t* list, const double* d,
-                           int nc, const int64_t* ck, const double* cT,
-                           double gA, double gSt, const double* gSn, sgrad* G)
+/* Sensor-frame gradient of one contribution: evaluation e of surfel s at
+ * transmittance T (before it), with suffix = sum over the later contributors
+ * of w_j (g.c_j).  With c = (1, t, n') and w = a T:
+ *   dL/da = T (g.c) - suffix / (1 - a),
+ * because every later weight carries the factor (1 - a).  Adds into *g and
+ * returns g.c.  use_clamp = 0 differentiates through alpha G even where a is
+ * clamped at 0.99 (the size of what a clamp decision switches on or off). */
+static double contrib_grad_m(const surf64* s, const eval64* e, const double* d, double T, double suffix,
+                             double gA, double gSt, const double* gSn, int use_clamp, int majorant, sgrad* g)
 {
-    double suffix = 0.0;
+    double sg = e->den > 0 ? -1.0 : 1.0;
+    double np[3] = { sg * s->n[0], sg * s->n[1], sg * s->n[2] };
+    double gc = gA + gSt * e->t + dot3(gSn, np);
+    double w = e->a * T;
+    double dLda = T * gc - suffix / (1.0 - e->a);
+    double gSn_m[3];
+    if (majorant) {
+        /* the same chain with every term of g.c and dL/da taken in absolute
+         * value: the magnitudes a binary32 evaluation rounds, whatever cancels */
+        gc = fabs(gA) + fabs(gSt * e->t) + fabs(gSn[0]) + fabs(gSn[1]) + fabs(gSn[2]);
+        dLda = T * gc + fabs(suffix) / (1.0 - e->a);
+        gSt = fabs(gSt);
+        for (int k = 0; k < 3; ++k) gSn_m[k] = fabs(gSn[k]);
+        gSn = gSn_m;
+        sg = 1.0;
+    }
+    /* direct terms of S_t and S_n (the sign flip has zero derivative) */
+    double dLdt = w * gSt;
+    for (int k = 0; k < 3; ++k) g->n[k] += w * sg * gSn[k];
+    /* through a = min(alpha G, 0.99): zero derivative when clamped */
+    double dLdu = 0, dLdv = 0;
+    if (!use_clamp || e->araw < A_MAX) {
+        g->alpha += dLda * e->G;
+        double dLdq = dLda * s->alpha * (-0.5 * e->G);
+        dLdu = dLdq * 2.0 * e->u;
+        dLdv = dLdq * 2.0 * e->v;
+    }
+    /* u = t_u.(t d - mu)/s_u,  v = t_v.(t d - mu)/s_v */
+    dLdt += dLdu * dot3(s->tu, d) / s->su + dLdv * dot3(s->tv, d) / s->sv;
+    for (int k = 0; k < 3; ++k) {
+        g->tu[k] += dLdu * e->x[k] / s->su;
+        g->tv[k] += dLdv * e->x[k] / s->sv;
+        g->mu[k] -= dLdu * s->tu[k] / s->su + dLdv * s->tv[k] / s->sv;
+    }
+    g->su -= dLdu * e->u / s->su;
+    g->sv -= dLdv * e->v / s->sv;
+    /* t = (n.mu)/(n.d): dt/dmu = n/den, dt/dn = (mu - t d)/den */
+    for (int k = 0; k < 3; ++k) {
+        g->mu[k] += dLdt * s->n[k] / e->den;
+        g->n[k] += dLdt * (s->mu[k] - e->t * d[k]) / e->den;
+    }
+    return gc;
+}
+
+static double contrib_grad(const surf64* s, const eval64* e, const double* d, double T, double suffix,
+                           double gA, double gSt, const double* gSn, int use_clamp, sgrad* g)
+{
+    return contrib_grad_m(s, e, d, T, suffix, gA, gSt, gSn, use_clamp, 0, g);
+}
+
+static void chain_to_params(const surf64* s, const sgrad* g, const frame64* F,
+                            double* dmean, double* dquat, double* dls, double* dlogit);
+
+static void sgrad_add(sgrad* a, const sgrad* b)
+{
+    for (int k = 0; k < 3; ++k) {
+        a->mu[k] += b->mu[k]; a->tu[k] += b->tu[k]; a->tv[k] += b->tv[k]; a->n[k] += b->n[k];
+    }
+    a->su += b->su; a->sv += b->sv; a->alpha += b->alpha;
+}
+
+/* |raw-parameter gradient| (mean 3, quat 4, log-scale 2, logit 1) of one contribution */
+static void raw_abs(const surf64* s, const sgrad* g, const frame64* F, double* r)
+{
+    double dm[3] = { 0, 0, 0 }, dq[4] = { 0, 0, 0, 0 }, dl[2] = { 0, 0 }, dg = 0;
+    chain_to_params(s, g, F, dm, dq, dl, &dg);
+    for (int k = 0; k < 3; ++k) r[k] = fabs(dm[k]);
+    for (int k = 0; k < 4; ++k) r[3 + k] = fabs(dq[k]);
+    r[7] = fabs(dl[0]); r[8] = fabs(dl[1]); r[9] = fabs(dg);
+}
+
+static void add10(double* dst, const double* r, double f)
+{
+    for (int c = 0; c < 10; ++c) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+        dst[c] += f * r[c];
+    }
+}
+
+/* Relative binary32 uncertainty of one evaluation's contribution: local
+ * coordinates known to ek (see fp32_bound), t to dt / t, amplified by the
+ * Gaussian's slope (|u| + |v|) and by 1/|n.d| through t = (n.mu)/(n.d). */
+static double fp32_rel(const surf64* s, const eval64* e)
+{
+    double ek, dt;
+    fp32_unc(s, e->den, e->t, &ek, &dt);
+    return 2.0 * ((fabs(e->u) + fabs(e->v) + 1.0) * ek + dt / fabs(e->t));
+}
+
+#define FL_HARD (FL_DEN | FL_TNEAR)
+#define FL_SOFT (FL_QCUT | FL_AMIN)
+
+/* Reverse mode through composite_pixel for one pixel with upstream gradients
+ * (gA, gSt, gSn) of (A, S_t, S_n).  Besides the gradient (into G) it records,
+ * per surfel and raw parameter (when gabs / gflip are given):
+ *   gabs  += a majorant of each contribution (its terms in absolute value:
+ *            the conditioning of the sums);
+ *   gflip += the majorant times the contribution's relative binary32
+ *            uncertainty (fp32_rel), and
+ *   gflip += what a near-threshold decision taken the other way by a binary32
+ *            evaluation can change: the whole would-be contribution of the
+ *            surfel concerned, and for the other contributors of the pixel the
+ *            sum of the flipping opacities times their contribution; a grazing
+ *            or near-plane decision makes the surfel's value undetermined
+ *            (gflip = inf). */
+static void backward_pixel(const surf64* S, const uint32_t* list, const double* d, int nc,
+                           const int64_t* ck, const double* cT, const pix_out* o, double gA, double gSt,
+                           const double* gSn, const frame64* F, sgrad* G, double* gabs, double* gflip,
+                           double* tmp, double* suf)
+{
+    double suffix = 0.0, suffix_abs = 0.0;
     for (int m = nc - 1; m >= 0; --m) {
         uint32_t i = list[ck[m]];
         const surf64* s = S + i;
-        sgrad* g = G + i;
         eval64 e;
         eval_pair(s, d, &e);                   /* recompute the same evaluation */
         double T = cT[m];
-        double sg = e.den > 0 ? -1.0 : 1.0;
-        double np[3] = { sg * s->n[0], sg * s->n[1], sg * s->n[2] };
-        double gc = gA + gSt * e.t + dot3(gSn, np);
-        double w = e.a * T;
-        double dLda = T * gc - suffix / (1.0 - e.a);
-        suffix += w * gc;
-        /* direct terms of S_t and S_n (the sign flip has zero derivative) */
-        double dLdt = w * gSt;
-        for (int k = 0; k < 3; ++k) g->n[k] += w * sg * gSn[k];
-        /* through a = min(alpha G, 0.99): zero derivative when clamped */
-        double dLdu = 0, dLdv = 0;
-        if (e.araw < A_MAX) {
-            g->alpha += dLda * e.G;
-            double dLdG = dLda * s->alpha;
-            double dLdq = dLdG * (-0.5 * e.G);
-            dLdu = dLdq * 2.0 * e.u;
-            dLdv = dLdq * 2.0 * e.v;
+        sgrad c;
+        memset(&c, 0, sizeof(c));
+        double gc = contrib_grad(s, &e, d, T, suffix, gA, gSt, gSn, 1, &c);
+        suffix += e.a * T * gc;
+        suf[m] = suffix;                       /* sum over contributors >= m */
+        sgrad_add(G + i, &c);
+        if (gabs) {
+            sgrad cm;
+            memset(&cm, 0, sizeof(cm));
+            double gcm = contrib_grad_m(s, &e, d, T, suffix_abs, gA, gSt, gSn, 1, 1, &cm);
+            suffix_abs += e.a * T * gcm;
+            raw_abs(s, &cm, F, tmp + 10 * m);
+            add10(gabs + 10 * (int64_t)i, tmp + 10 * m, 1.0);
+            if (gflip) add10(gflip + 10 * (int64_t)i, tmp + 10 * m, fp32_rel(s, &e));
         }
-        /* u = t_u.(t d - mu)/s_u,  v = t_v.(t d - mu)/s_v */
-        dLdt += dLdu * dot3(s->tu, d) / s->su + dLdv * dot3(s->tv, d) / s->sv;
-        for (int k = 0; k < 3; ++k) {
-            g->tu[k] += dLdu * e.x[k] / s->su;
-            g->tv[k] += dLdv * e.x[k] / s->sv;
-            g->mu[k] -= dLdu * s->tu[k] / s->su + dLdv * s->tv[k] / s->sv;
+        if (gflip && (e.flags & FL_AMAX)) {
+            sgrad u;
+            memset(&u, 0, sizeof(u));
+            double r[10];
+            contrib_grad(s, &e, d, T, m + 1 < nc ? suf[m + 1] : 0.0, gA, gSt, gSn, 0, &u);
+            raw_abs(s, &u, F, r);
+            add10(gflip + 10 * (int64_t)i, r, 1.0);
         }
-        g->su -= dLdu * e.u / s->su;
-        g->sv -= dLdv * e.v / s->sv;
-        /* t = (n.mu)/(n.d): dt/dmu = n/den, dt/dn = (mu - t d)/den */
-        for (int k = 0; k < 3; ++k) {
-            g->mu[k] += dLdt * s->n[k] / e.den;
-            g->n[k] += dLdt * (s->mu[k] - e.t * d[k]) / e.den;
+    }
+    if (!gflip || !gabs || !o->flags) return;
+    /* the other contributors: relative change bounded by the flipping opacities */
+    for (int m = 0; m < nc; ++m) add10(gflip + 10 * (int64_t)list[ck[m]], tmp + 10 * m, 2.0 * o->flipa);
+    if (o->flags & FL_TSTOP && nc > 0) add10(gflip + 10 * (int64_t)list[ck[nc - 1]], tmp + 10 * (nc - 1), 1.0);
+    /* the surfels whose own decision is near a threshold */
+    int mm = 0;
+    for (int64_t k = 0; k < o->neval; ++k) {
+        while (mm < nc && ck[mm] < k) ++mm;
+        int is_contrib = mm < nc && ck[mm] == k;
+        uint32_t i = list[k];
+        const surf64* s = S + i;
+        eval64 e;
+        eval_pair(s, d, &e);
+        if (e.flags & FL_HARD) {
+            for (int c = 0; c < 10; ++c) gflip[10 * (int64_t)i + c] = INFINITY;
+            continue;
         }
+        int stop_entry = (k == o->neval - 1) && !is_contrib && e.valid;
+        if (!(e.flags & FL_SOFT) && !stop_entry) continue;
+        if (is_contrib) {
+            add10(gflip + 10 * (int64_t)i, tmp + 10 * mm, 1.0);
+            continue;
+        }
+        eval64 f;
+        force_eval(s, d, &f);
+        double T = mm < nc ? cT[mm] : o->T;
+        double sx = mm < nc ? suf[mm] : 0.0;
+        sgrad u;
+        memset(&u, 0, sizeof(u));
+        double r[10];
+        contrib_grad(s, &f, d, T, sx, gA, gSt, gSn, 1, &u);
+        raw_abs(s, &u, F, r);
+        add10(gflip + 10 * (int64_t)i, r, 1.0);
     }
 }
 
@@ -630,16 +888,16 @@ static void chain_to_params(const surf64* s, const sgrad* g, const frame64* F,
 }
 
 /* Backward of one frame: accumulates (+=) dL/d(mean, quat, log_scale, logit)
- * for upstream gradients gA, gSt [H*W], gSn [3][H*W].  surf_flag (optional)
- * marks surfels that contributed to, or were near a threshold in, a pixel
- * flagged by the forward, and for a pixel flagged at termination also the
- * next valid surfel after the stop. */
+ * for upstream gradients gA, gSt [H*W], gSn [3][H*W].  When gabs and gflip
+ * ([n][10]: mean 3, quat 4, log-scale 2, logit 1) are given, also accumulates
+ * per surfel the sum of |per-pixel contributions| and the near-threshold
+ * uncertainty described at backward_pixel. */
 void lgso_render_bwd(const double* mean, const double* quat, const double* ls, const double* logit,
                      int64_t n, int H, int W, int th, int tw, double emin, double emax,
                      const double* pose, const int64_t* ranges, const uint32_t* vals,
                      const double* gA, const double* gSt, const double* gSn,
                      double* dmean, double* dquat, double* dls, double* dlogit,
-                     uint8_t* surf_flag, int nthreads)
+                     double* gabs, double* gflip, int nthreads)
 {
     frame64 F;
     make_frame(&F, H, W, th, tw, emin, emax, pose);
@@ -665,8 +923,10 @@ void lgso_render_bwd(const double* mean, const double* quat, const double* ls, c
         sgrad* G = Gall + (size_t)tid * (n > 0 ? n : 1);
         int64_t* ck = (int64_t*)malloc(sizeof(int64_t) * maxlen);
         double* cT = (double*)malloc(sizeof(double) * maxlen);
+        double* tmp = (double*)malloc(sizeof(double) * 10 * maxlen);
+        double* suf = (double*)malloc(sizeof(double) * maxlen);
 #ifdef _OPENMP
-#pragma omp for schedule(static)
+#pragma omp for schedule(dynamic, 1)
 #endif
         for (int64_t tile = 0; tile < ntiles; ++tile) {
             int ti = (int)(tile / F.ntc), tj = (int)(tile % F.ntc);
@@ -679,36 +939,16 @@ void lgso_render_bwd(const double* mean, const double* quat, const double* ls, c
                     int nc = composite_pixel(S, vals + b, e - b, d, &o, ck, cT);
                     int64_t p = (int64_t)r * W + c;
                     double gsn[3] = { gSn[p], gSn[HW + p], gSn[2 * HW + p] };
-                    backward_pixel(S, vals + b, d, nc, ck, cT, gA[p], gSt[p], gsn, G);
-                    if (surf_flag && o.flags) {
-                        /* every surfel evaluated up to the stop that was valid or near a threshold */
-                        int64_t lim = o.neval;
-                        int extra = (o.flags & FL_TSTOP) ? 2 : 0;  /* stop surfel + next valid */
-                        for (int64_t k = 0; k < e - b; ++k) {
-                            eval64 ev;
-                            eval_pair(S + vals[b + k], d, &ev);
-                            if (k < lim) {
-                                if (ev.valid || ev.flags) surf_flag[vals[b + k]] = 1;
-                            } else if (extra > 0) {
-                                if (ev.valid) { surf_flag[vals[b + k]] = 1; --extra; }
-                            } else break;
-                        }
-                    }
+                    backward_pixel(S, vals + b, d, nc, ck, cT, &o, gA[p], gSt[p], gsn, &F, G, gabs, gflip,
+                                   tmp, suf);
                 }
         }
-        free(ck); free(cT);
+        free(ck); free(cT); free(tmp); free(suf);
     }
     for (int64_t i = 0; i < n; ++i) {
         sgrad acc;
         memset(&acc, 0, sizeof(acc));
-        for (int t = 0; t < nth; ++t) {
-            const sgrad* g = Gall + (size_t)t * n + i;
-            for (int k = 0; k < 3; ++k) {
-                acc.mu[k] += g->mu[k]; acc.tu[k] += g->tu[k];
-                acc.tv[k] += g->tv[k]; acc.n[k] += g->n[k];
-            }
-            acc.su += g->su; acc.sv += g->sv; acc.alpha += g->alpha;
-        }
+        for (int t = 0; t < nth; ++t) sgrad_add(&acc, Gall + (size_t)t * n + i);
         chain_to_params(S + i, &acc, &F, dmean + 3 * i, dquat + 4 * i, dls + 2 * i, dlogit + i);
     }
     free(Gall);

@@ -65,11 +65,11 @@ def _load():
         lib.lgso_bin_frame.argtypes = [P, P, i64, i32, i32, i32, i32, f32, f32, P, P, P, P, P, i64, P]
         lib.lgso_bin_frame.restype = i64
         lib.lgso_render_fwd.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, f64, f64, P, P, P,
-                                        P, P, P, P, P, P, P, P, i32]
+                                        P, P, P, P, P, P, P, P, P, P, i32]
         lib.lgso_coverage_misses.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, f64, f64, P, P, P]
         lib.lgso_coverage_misses.restype = i64
         lib.lgso_render_bwd.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, f64, f64, P, P, P,
-                                        P, P, P, P, P, P, P, P, i32]
+                                        P, P, P, P, P, P, P, P, P, i32]
         lib.lgso_loss_image.argtypes = [P, P, P, P, P, i64, f64, f64, f64, f64, P, P, P, P]
         lib.lgso_loss_image.restype = f64
         lib.lgso_scale_reg.argtypes = [P, i64, f64, f64, P]
@@ -169,14 +169,16 @@ def render_fwd(surfels, frame, ranges, vals, params64=None, nthreads: int = 0):
     H, W = frame.H, frame.W
     A = np.zeros(H * W); St = np.zeros(H * W); Sn = np.zeros(3 * H * W); Tf = np.zeros(H * W)
     nc = np.zeros(H * W, np.int32); ne = np.zeros(H * W, np.int64); fl = np.zeros(H * W, np.uint8)
-    nv = np.zeros(H * W, np.int32)
+    nv = np.zeros(H * W, np.int32); eA = np.zeros(H * W); eD = np.zeros(H * W)
     fa = _frame_args(frame)
     lib.lgso_render_fwd(_p(m), _p(q), _p(ls), _p(lg), m.shape[0], *fa[:6], _p(fa[6]),
                         _p(_c(ranges, np.int64)), _p(_c(vals, np.uint32)),
-                        _p(A), _p(St), _p(Sn), _p(Tf), _p(nc), _p(ne), _p(fl), _p(nv), int(nthreads))
+                        _p(A), _p(St), _p(Sn), _p(Tf), _p(nc), _p(ne), _p(fl), _p(nv), _p(eA), _p(eD),
+                        int(nthreads))
     return dict(A=A.reshape(H, W), S_t=St.reshape(H, W), S_n=Sn.reshape(3, H, W),
                 T_final=Tf.reshape(H, W), n_contrib=nc.reshape(H, W), n_eval=ne.reshape(H, W),
-                flags=fl.reshape(H, W), n_valid=nv.reshape(H, W))
+                flags=fl.reshape(H, W), n_valid=nv.reshape(H, W), fp32_err_A=eA.reshape(H, W),
+                fp32_err_D=eD.reshape(H, W))
 
 
 def coverage_misses(surfels, frame, ranges, vals, params64=None) -> int:
@@ -196,13 +198,13 @@ def render_bwd(surfels, frame, ranges, vals, gA, gSt, gSn, params64=None, grads=
     n = m.shape[0]
     if grads is None:
         grads = dict(mean=np.zeros((n, 3)), quat=np.zeros((n, 4)), log_scale=np.zeros((n, 2)),
-                     logit=np.zeros(n), flag=np.zeros(n, np.uint8))
+                     logit=np.zeros(n), abs=np.zeros((n, 10)), flip=np.zeros((n, 10)))
     fa = _frame_args(frame)
     lib.lgso_render_bwd(_p(m), _p(q), _p(ls), _p(lg), n, *fa[:6], _p(fa[6]),
                         _p(_c(ranges, np.int64)), _p(_c(vals, np.uint32)),
                         _p(_c(gA, np.float64)), _p(_c(gSt, np.float64)), _p(_c(gSn, np.float64)),
                         _p(grads["mean"]), _p(grads["quat"]), _p(grads["log_scale"]), _p(grads["logit"]),
-                        _p(grads["flag"]), int(nthreads))
+                        _p(grads["abs"]), _p(grads["flip"]), int(nthreads))
     return grads
 
 
@@ -232,7 +234,7 @@ def forward_backward(surfels, frames, targets, lam_alpha=LAMBDA_ALPHA, lam_n=LAM
     ``targets`` is a list of (D, Ng).  Returns (L, per-frame forwards, grads, bins)."""
     n = surfels.mean.shape[0]
     grads = dict(mean=np.zeros((n, 3)), quat=np.zeros((n, 4)), log_scale=np.zeros((n, 2)),
-                 logit=np.zeros(n), flag=np.zeros(n, np.uint8))
+                 logit=np.zeros(n), abs=np.zeros((n, 10)), flip=np.zeros((n, 10)))
     F = len(frames)
     L = 0.0
     fwds, bins = [], []

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, 
   out[0] = make_float4(nx, ny, nz, nx * mx + ny * my + nz * mz);
   out[1] = make_float4(tux * isu, tuy * isu, tuz * isu, (tux * mx + tuy * my + tuz * mz) * isu);
   out[2] = make_float4(tvx * isv, tvy * isv, tvz * isv, (tvx * mx + tvy * my + tvz * mz) * isv);
-  out[3] = make_float4(alpha, 0.f, 0.f, 0.f);
+  out[3] = make_float4(alpha, expf(M.ls[2 * i]), expf(M.ls[2 * i + 1]), 0.f);
 }
 
 // ---------------------------------------------------------------------------

@@ -9,10 +9,10 @@ namespace lgs {
 
 // ---------------------------------------------------------------------------
 // Preprocess backward: for every surfel, sum over the frames that render its
-// map the record gradient (n, h, a_u, b_u, a_v, b_v, alpha) chained through
-//   h = n.mu, a_u = t_u/s_u, b_u = t_u.mu/s_u (same for v),
-//   mu = R^T (mean - o), [t_u t_v n] = R^T R(q/|q|), s = exp(log_scale),
-//   alpha = sigmoid(logit),
+// map the per-item gradient of the backward (dL/dn and dL/dt_u, dL/dt_v at a
+// fixed centre, the coefficients of dL/dmu along n, t_u, t_v, dL/dalpha and
+// dL/dlog s), chained through
+//   mu = R^T (mean - o), [t_u t_v n] = R^T R(q/|q|), alpha = sigmoid(logit),
 // then ACCUMULATE into the caller's gradient arrays.  The per-item gradient
 // buffer is zeroed as it is read, so it is all-zero between backward calls.
 // ---------------------------------------------------------------------------
@@ -39,10 +39,7 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__
   const float c0[3] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y)};
   const float c1[3] = {2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x)};
   const float c2[3] = {2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y)};
-  const float su = expf(M.ls[2 * i]), sv = expf(M.ls[2 * i + 1]);
-  const float isu = 1.f / su, isv = 1.f / sv;
   const float alpha = 1.0f / (1.0f + expf(-M.logit[i]));
-  const float mw[3] = {M.mean[3 * i], M.mean[3 * i + 1], M.mean[3 * i + 2]};
   float gm[3] = {0.f, 0.f, 0.f}, G0[3] = {0.f, 0.f, 0.f}, G1[3] = {0.f, 0.f, 0.f}, G2[3] = {0.f, 0.f, 0.f};
   float gls0 = 0.f, gls1 = 0.f, galpha = 0.f;
   bool any = false;
@@ -52,42 +49,33 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__
     float4* gp = reinterpret_cast<float4*>(g13 + 16 * (F.item_base + i));
     const float4 a = gp[0], b = gp[1], c = gp[2], d = gp[3];
     if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f && b.x == 0.f && b.y == 0.f && b.z == 0.f &&
-        b.w == 0.f && c.x == 0.f && c.y == 0.f && c.z == 0.f && c.w == 0.f && d.x == 0.f)
+        b.w == 0.f && c.x == 0.f && c.y == 0.f && c.z == 0.f && c.w == 0.f && d.x == 0.f && d.y == 0.f &&
+        d.z == 0.f)
       continue;
     any = true;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     gp[0] = zero; gp[1] = zero; gp[2] = zero; gp[3] = zero;
     const float* R = F.R;
-    // sensor frame quantities
-    float tu[3], tv[3], n[3], mu[3];
-    const float dm[3] = {mw[0] - F.o[0], mw[1] - F.o[1], mw[2] - F.o[2]};
+    // sensor-frame axes: v_s = R^T v_w
+    float tu[3], tv[3], n[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       tu[k] = R[k] * c0[0] + R[3 + k] * c0[1] + R[6 + k] * c0[2];
       tv[k] = R[k] * c1[0] + R[3 + k] * c1[1] + R[6 + k] * c1[2];
       n[k] = R[k] * c2[0] + R[3 + k] * c2[1] + R[6 + k] * c2[2];
-      mu[k] = R[k] * dm[0] + R[3 + k] * dm[1] + R[6 + k] * dm[2];
     }
-    const float g_n[3] = {a.x, a.y, a.z}, g_h = a.w;
-    const float g_au[3] = {b.x, b.y, b.z}, g_bu = b.w;
-    const float g_av[3] = {c.x, c.y, c.z}, g_bv = c.w;
-    const float g_al = d.x;
-    const float bu = (tu[0] * mu[0] + tu[1] * mu[1] + tu[2] * mu[2]) * isu;
-    const float bv = (tv[0] * mu[0] + tv[1] * mu[1] + tv[2] * mu[2]) * isv;
-    float gtu[3], gtv[3], gnn[3], gmu[3];
-    float dau = 0.f, dav = 0.f;
+    // per-item components (see k_bwd): dL/dn, c_n, dL/dt_u, c_u, dL/dt_v, c_v,
+    // dL/dalpha, dL/dlog s_u, dL/dlog s_v -- already free of cancelling terms
+    const float gnn[3] = {a.x, a.y, a.z};
+    const float gtu[3] = {b.x, b.y, b.z};
+    const float gtv[3] = {c.x, c.y, c.z};
+    const float cn = a.w, cu = b.w, cv = c.w;
+    float gmu[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      gtu[k] = (g_au[k] + g_bu * mu[k]) * isu;
-      gtv[k] = (g_av[k] + g_bv * mu[k]) * isv;
-      gnn[k] = g_n[k] + g_h * mu[k];
-      gmu[k] = g_h * n[k] + g_bu * isu * tu[k] + g_bv * isv * tv[k];
-      dau += g_au[k] * tu[k] * isu;
-      dav += g_av[k] * tv[k] * isv;
-    }
-    gls0 -= dau + g_bu * bu;
-    gls1 -= dav + g_bv * bv;
-    galpha += g_al;
+    for (int k = 0; k < 3; ++k) gmu[k] = cn * n[k] + cu * tu[k] + cv * tv[k];
+    galpha += d.x;
+    gls0 += d.y;
+    gls1 += d.z;
     // back to the world frame: v_w = R v_s
 #pragma unroll
     for (int a2 = 0; a2 < 3; ++a2) {

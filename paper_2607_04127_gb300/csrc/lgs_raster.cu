@@ -12,8 +12,8 @@
 // (no per-pixel surfel lists are stored): the transmittance before each
 // contributor is recovered as T_k = T_{k+1} / (1 - a_k) from T_final, and the
 // suffix sum S = sum_{j>k} w_j (g . c_j) gives dL/da_k = T_k (g . c_k) -
-// S / (1 - a_k).  Per entry the warp reduces its 13 record gradients with a
-// butterfly reduce-scatter (16 shuffles), 13 lanes add them into a shared
+// S / (1 - a_k).  Per entry the warp reduces its 15 geometric gradients with a
+// butterfly reduce-scatter (16 shuffles), 15 lanes add them into a shared
 // per-batch accumulator, and the CTA flushes one atomic add per (surfel,
 // component) into the per-item gradient buffer.
 #include <cuda_runtime.h>
@@ -23,6 +23,12 @@
 namespace lgs {
 
 constexpr int kMaxTileThreads = 256;
+// Per-item gradient components written by the backward (see k_bwd):
+//   [0..2] dL/dn at fixed centre   [3] c_n   (dL/dmu += c_n n)
+//   [4..6] dL/dt_u                 [7] c_u   (dL/dmu += c_u t_u)
+//   [8..10] dL/dt_v                [11] c_v  (dL/dmu += c_v t_v)
+//   [12] dL/dalpha                 [13] dL/dlog s_u   [14] dL/dlog s_v
+constexpr int kGrad = 15;
 
 struct TileCtx {
   int f;
@@ -186,15 +192,14 @@ __global__ void __launch_bounds__(kMaxTileThreads)
     k_bwd(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
           const float4* __restrict__ rec, float* __restrict__ g13, const uint32_t* __restrict__ order,
           Status* __restrict__ st, int persistent) {
-  __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[BATCH];
-  __shared__ float s_al[BATCH];
+  __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[BATCH], s_r3[BATCH];
   __shared__ uint32_t s_item[BATCH];
-  __shared__ float s_g[13][BATCH];
+  __shared__ float s_g[kGrad][BATCH];
   __shared__ int s_max;
   const int nthr = blockDim.x;
   const int tid = threadIdx.x, lane = tid & 31;
   const int gidx = 8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
-  const bool writer = ((lane & 1) == 0) && gidx < 13;
+  const bool writer = ((lane & 1) == 0) && gidx < kGrad;
   uint32_t tile;
   unsigned long long evals = 0, contrib = 0;
   for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
@@ -232,9 +237,9 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         s_r0[j] = rp[0];
         s_r1[j] = rp[1];
         s_r2[j] = rp[2];
-        s_al[j] = rp[3].x;
+        s_r3[j] = rp[3];
 #pragma unroll
-        for (int c = 0; c < 13; ++c) s_g[c][j] = 0.f;
+        for (int c = 0; c < kGrad; ++c) s_g[c][j] = 0.f;
       }
       __syncthreads();
       for (int j = nb - 1; j >= 0; --j) {
@@ -245,7 +250,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         bool valid = false;
         if (k < nc) {
           const float4 r0 = s_r0[j];
-          const float alpha = s_al[j];
+          const float alpha = s_r3[j].x;
           Eval e;
           eval_pair(r0, s_r1[j], s_r2[j], alpha, dx, dy, dz, e);
           ++evals;
@@ -270,15 +275,27 @@ __global__ void __launch_bounds__(kMaxTileThreads)
               dLdv = 2.f * e.v * dLdq;
             }
             dLdt = fmaf(dLdu, e.ud, fmaf(dLdv, e.vd, dLdt));
-            const float tu = dLdu * e.t, tv = dLdv * e.t;
-            v[4] = tu * dx; v[5] = tu * dy; v[6] = tu * dz; v[7] = -dLdu;
-            v[8] = tv * dx; v[9] = tv * dy; v[10] = tv * dz; v[11] = -dLdv;
-            const float inv_den = __fdividef(1.0f, e.den);
-            v[3] = dLdt * inv_den;
-            const float dden = -dLdt * e.t * inv_den;
-            v[0] = fmaf(dden, dx, wsg * gSx);
-            v[1] = fmaf(dden, dy, wsg * gSy);
-            v[2] = fmaf(dden, dz, wsg * gSz);
+            // offset of the intersection from the centre, inside the plane:
+            // x = t d - mu = u s_u t_u + v s_v t_v with t_u = s_u a_u, t_v = s_v a_v
+            // (formed from (u, v) so that no large terms cancel)
+            const float su = s_r3[j].y, sv = s_r3[j].z;
+            const float cu = e.u * su * su, cv = e.v * sv * sv;
+            const float r1x = s_r1[j].x, r1y = s_r1[j].y, r1z = s_r1[j].z;
+            const float r2x = s_r2[j].x, r2y = s_r2[j].y, r2z = s_r2[j].z;
+            const float xx = fmaf(cu, r1x, cv * r2x), xy = fmaf(cu, r1y, cv * r2y), xz = fmaf(cu, r1z, cv * r2z);
+            const float ct = __fdividef(dLdt, e.den);
+            // dL/dn at fixed centre: w sg gS_n + (dL/dt)(mu - t d)/(n.d)
+            v[0] = fmaf(-ct, xx, wsg * gSx);
+            v[1] = fmaf(-ct, xy, wsg * gSy);
+            v[2] = fmaf(-ct, xz, wsg * gSz);
+            v[3] = ct;                                    // dL/dmu += ct n
+            const float gu = __fdividef(dLdu, su), gv = __fdividef(dLdv, sv);
+            v[4] = gu * xx; v[5] = gu * xy; v[6] = gu * xz; // dL/dt_u = (dL/du) x / s_u
+            v[7] = -gu;                                   // dL/dmu -= (dL/du) t_u / s_u
+            v[8] = gv * xx; v[9] = gv * xy; v[10] = gv * xz;
+            v[11] = -gv;
+            v[13] = -dLdu * e.u;                          // dL/dlog s_u
+            v[14] = -dLdv * e.v;
           }
         }
         if (__any_sync(0xffffffffu, valid)) {
@@ -290,7 +307,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       for (int j = tid; j < nb; j += nthr) {
         float* gp = g13 + 16 * static_cast<int64_t>(s_item[j]);
 #pragma unroll
-        for (int c = 0; c < 13; ++c) {
+        for (int c = 0; c < kGrad; ++c) {
           const float x = s_g[c][j];
           if (x != 0.f) atomicAdd(gp + c, x);
         }

@@ -2,15 +2,28 @@
 
 Bars (spec tolerances): sort order, tile lists and tile ranges
 bit-exact; expected depth and opacity within 1e-5 relative, normals within
-1e-4; gradients within 1e-3 relative.  "Relative" has a floor:
-|x - y| <= tol * max(|y|, 1e-3 max|y|).  Pixels where the oracle saw a
-quantity within 0.1 % of a threshold (cut-off 9, 1/255, 0.99 clamp, T stop
-1e-4, near plane, grazing 1e-6) may legitimately be decided the other way in
-FP32; they are excluded from the strict check and counted, and surfels that
-contributed to such a pixel are excluded from the strict gradient check.
-"""
-import math
+1e-4; gradients within 1e-3 relative.  "Relative" has a floor,
+tol * max(|y|, 1e-3 max|y|), and every bar adds the uncertainty the oracle
+computes for a binary32 evaluation of the same inputs (no pixel or surfel is
+dropped from the check):
 
+  * forward: fp32_err_A / fp32_err_D -- the error implied by representing the
+    sensor-frame geometry and the rays in binary32 (local coordinates known
+    to ~2^-24 max(t,|mu|)/s, amplified by 1/|n.d| and |mu|/|n.mu|), plus the
+    size of any contribution whose skip / stop decision lies within that
+    uncertainty (or 0.1 %) of its threshold;
+  * gradients: 1e-4 of a majorant of the per-pixel contributions (all terms
+    in absolute value: the conditioning of the sums), plus "flip": each
+    contribution's majorant times its relative binary32 uncertainty and the
+    size of near-threshold contributions; a grazing or near-plane decision
+    makes a surfel's gradient undetermined (inf, counted: < 0.1 % of the
+    street map's surfels, up to 7 % in the grazing-heavy random test shells).
+
+The loss and the backward are each checked on identical inputs: the oracle's
+loss on the GPU's forward outputs, the oracle's backward with the GPU's
+upstream gradients, so the L1 subgradient's jump at D = D_hat cannot mix
+into the comparison of the kernels.
+"""
 import numpy as np
 import pytest
 
@@ -30,17 +43,13 @@ def built():
     build.build()
 
 
-def close(x, y, tol, mask=None):
-    """Element-wise relative check with a floor; returns (ok, worst ratio)."""
-    x = np.asarray(x, np.float64); y = np.asarray(y, np.float64)
-    if mask is not None:
-        x, y = x[mask], y[mask]
-    if x.size == 0:
-        return True, 0.0
-    floor = 1e-3 * np.abs(y).max()
-    lim = tol * np.maximum(np.abs(y), floor) + 1e-30
-    r = np.abs(x - y) / lim
-    return bool(np.all(r <= 1.0)), float(r.max())
+def ratio(x, y, tol, extra=0.0):
+    """|x - y| / (tol max(|y|, 1e-3 max|y|) + extra), element-wise."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    floor = 1e-3 * np.abs(y).max() if y.size else 0.0
+    lim = tol * np.maximum(np.abs(y), floor) + extra + 1e-300
+    return np.abs(x - y) / lim, float(np.mean(np.abs(x - y) <= tol * np.maximum(np.abs(y), floor)))
 
 
 def cases():
@@ -57,16 +66,15 @@ def cases():
     s, f = scenes.random_shell(8, 1200, frame=scenes.Frame(64, 256, 8, 32, -0.8, 0.8,
                                                            scenes.pose_matrix(2.0, (0.5, -0.3, 0.2), 0.1, -0.05)))
     out.append(("shell_64x256_8x32_pose", s, f, scenes.targets_for(f, s, 4)))
+    # opacities up to 0.999: exercises the 0.99 clamp and its zero derivative
+    s, f = scenes.random_shell(9, 500, frame=scenes.Frame(32, 128, 16, 16, -0.4, 0.4))
+    s.logit[::3] = 6.0
+    out.append(("clamped_opacity", s, f, scenes.targets_for(f, s, 6)))
     return out
 
 
 CASES = cases()
 IDS = [c[0] for c in CASES]
-
-
-def oracle_frame(oracle, surf, frame, tgt):
-    L, fws, g, bins = oracle.forward_backward(surf, [frame], [(tgt.D, tgt.N)])
-    return L, fws[0], g, bins[0]
 
 
 @pytest.mark.parametrize("name,surf,frame,tgt", CASES, ids=IDS)
@@ -84,17 +92,28 @@ def test_bins_bit_exact(oracle, name, surf, frame, tgt):
 
 
 def compare_forward(gf, of, tolA=1e-5, tolN=1e-4):
-    mask = of["flags"] == 0
-    A_ok, A_w = close(gf["A"], of["A"], tolA, mask)
-    Dg = gf["S_t"] / (gf["A"] + EPS); Do = of["S_t"] / (of["A"] + EPS)
-    D_ok, D_w = close(Dg, Do, tolA, mask)
+    """Returns dict of (worst ratio, fraction within the plain bar)."""
+    out = {}
+    out["A"] = ratio(gf["A"], of["A"], tolA, 2 * of["fp32_err_A"])
+    Dg = gf["S_t"] / (gf["A"].astype(np.float64) + EPS)
+    Do = of["S_t"] / (of["A"] + EPS)
+    out["D"] = ratio(Dg, Do, tolA, 2 * of["fp32_err_D"])
+    out["T"] = ratio(gf["T_final"], of["T_final"], tolA, 2 * of["fp32_err_A"])
     Ng = gf["S_n"] / np.sqrt((gf["S_n"].astype(np.float64) ** 2).sum(0) + EPS ** 2)
     No = of["S_n"] / np.sqrt((of["S_n"] ** 2).sum(0) + EPS ** 2)
-    N_err = np.abs(Ng - No).max(0)[mask].max() if mask.any() else 0.0
-    T_ok, T_w = close(gf["T_final"], of["T_final"], tolA, mask)
-    nc_ok = np.array_equal(gf["n_contrib"][mask], of["n_contrib"][mask])
-    return dict(A=(A_ok, A_w), D=(D_ok, D_w), N=(N_err <= tolN, N_err), T=(T_ok, T_w), nc=nc_ok,
-                flagged=float((~mask).mean()))
+    nerr = np.abs(Ng - No).max(0)
+    ntol = tolN + 4 * of["fp32_err_A"] / np.maximum(of["A"], 1e-3)
+    out["N"] = (nerr / ntol, float(np.mean(nerr <= tolN)))
+    calm = of["flags"] == 0
+    out["nc_equal"] = bool(np.array_equal(gf["n_contrib"][calm], of["n_contrib"][calm]))
+    out["calm"] = float(calm.mean())
+    return out
+
+
+def assert_forward(r):
+    for k in ("A", "D", "T", "N"):
+        assert r[k][0].max() <= 1.0, (k, float(r[k][0].max()), r[k][1])
+    assert r["nc_equal"]
 
 
 @pytest.mark.parametrize("name,surf,frame,tgt", CASES, ids=IDS)
@@ -104,41 +123,86 @@ def test_forward_parity(oracle, name, surf, frame, tgt):
     o = oracle.bin_frame(surf, frame)
     of = oracle.render_fwd(surf, frame, o["ranges"], o["vals"])
     r = compare_forward(g["fwd"][0], of)
-    assert r["A"][0] and r["D"][0] and r["N"][0] and r["T"][0] and r["nc"], r
-    assert r["flagged"] < 0.2, r
-    # flagged pixels differ by at most one near-threshold contribution
-    assert np.abs(g["fwd"][0]["A"] - of["A"]).max() < 0.05
+    assert_forward(r)
+    # most pixels meet the plain 1e-5 bar without any uncertainty term
+    assert r["A"][1] > 0.95 and r["D"][1] > 0.99, (r["A"][1], r["D"][1])
+
+
+def oracle_grads(oracle, surf, frames, ups, scale_reg=True):
+    """Oracle backward of a window of frames with the given upstream planes
+    (gA, gSt, gSn per frame), plus the scale regulariser."""
+    n = surf.n
+    g = dict(mean=np.zeros((n, 3)), quat=np.zeros((n, 4)), log_scale=np.zeros((n, 2)), logit=np.zeros(n),
+             abs=np.zeros((n, 10)), flip=np.zeros((n, 10)))
+    for frame, (gA, gSt, gSn) in zip(frames, ups):
+        b = oracle.bin_frame(surf, frame)
+        oracle.render_bwd(surf, frame, b["ranges"], b["vals"], gA, gSt, gSn, grads=g)
+    if scale_reg:
+        oracle.scale_reg(surf.log_scale, dls=g["log_scale"])
+    return g
 
 
 def compare_grads(gg, og, tol=1e-3):
-    flag = og["flag"] == 0
     out = {}
-    for k, name in enumerate(("mean", "quat", "log_scale", "logit")):
-        x = gg[k].reshape(len(flag), -1).astype(np.float64)
-        y = og[name].reshape(len(flag), -1)
-        out[name] = close(x, y, tol, np.broadcast_to(flag[:, None], y.shape))
-        rel = np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-30)
-        out[name + "_global"] = rel
-    out["flagged"] = float((~flag).mean())
+    n = og["mean"].shape[0]
+    off = 0
+    undet = np.isinf(og["flip"]).any(1)
+    for k, (name, w) in enumerate((("mean", 3), ("quat", 4), ("log_scale", 2), ("logit", 1))):
+        x = np.asarray(gg[k], np.float64).reshape(n, -1)
+        y = og[name].reshape(n, -1)
+        extra = 1e-4 * og["abs"][:, off:off + w] + og["flip"][:, off:off + w]
+        off += w
+        r, plain = ratio(x, y, tol, extra)
+        r = np.where(np.isinf(extra), 0.0, r)
+        out[name] = (float(r.max()), plain)
+    out["undetermined"] = float(undet.mean())
     return out
+
+
+def assert_grads(r):
+    for name in ("mean", "quat", "log_scale", "logit"):
+        assert r[name][0] <= 1.0, (name, r)
+        assert r[name][1] > 0.99, (name, r)
+    assert r["undetermined"] < 0.1, r
+
+
+def gpu_upstream(g, f):
+    u = g["upstream"][f]
+    return (u["dA"].astype(np.float64), u["dS_t"].astype(np.float64), u["dS_n"].astype(np.float64))
+
+
+def check_loss_on_gpu_forward(oracle, g, frames, targets, scales):
+    """The oracle's loss evaluated on the GPU's forward outputs equals the
+    GPU loss, and its upstream planes equal the GPU's (pixels whose depth is
+    within 1e-5 of the target -- the L1 kink -- are skipped)."""
+    total = 0.0
+    for f, (frame, tgt) in enumerate(zip(frames, targets)):
+        fw = {k: np.asarray(v, np.float64) for k, v in g["fwd"][f].items()}
+        Lf, up, terms = oracle.loss_image(fw, tgt.D, tgt.N, scale=scales[f])
+        total += Lf
+        Dh = fw["S_t"] / (fw["A"] + EPS)
+        kink = np.abs(Dh - tgt.D) <= 1e-5 * np.abs(tgt.D)
+        for k, key in (("dA", "dA"), ("dS_t", "dS_t")):
+            r, _ = ratio(np.where(kink, 0, g["upstream"][f][key]), np.where(kink, 0, up[key]), 1e-5)
+            assert r.max() <= 1.0, (key, float(r.max()))
+        r, _ = ratio(g["upstream"][f]["dS_n"], up["dS_n"], 1e-5)
+        assert r.max() <= 1.0, ("dS_n", float(r.max()))
+        assert np.allclose(g["loss"][1 + 3 * f: 4 + 3 * f], terms, rtol=1e-5, atol=1e-9)
+    return total
 
 
 @pytest.mark.parametrize("name,surf,frame,tgt", CASES, ids=IDS)
 def test_loss_and_backward_parity(oracle, name, surf, frame, tgt):
     from tests import _gpu
     g = _gpu.run([surf], [frame], targets=[tgt])
-    L, of, og, _ = oracle_frame(oracle, surf, frame, tgt)
-    assert g["loss"][0] == pytest.approx(L, rel=1e-5)
-    mask = of["flags"] == 0
-    Lo, up, _ = oracle.loss_image(of, tgt.D, tgt.N)
-    for k in ("dA", "dS_t", "dS_n"):
-        m = mask if k != "dS_n" else np.broadcast_to(mask, up[k].shape)
-        ok, w = close(g["upstream"][0][k], up[k], 1e-4, m)
-        assert ok, (k, w)
-    r = compare_grads(g["grads"][0], og)
-    for name_ in ("mean", "quat", "log_scale", "logit"):
-        assert r[name_][0], (name_, r)
-        assert r[name_ + "_global"] < 1e-2, (name_, r)
+    Limg = check_loss_on_gpu_forward(oracle, g, [frame], [tgt], [1.0])
+    Ls = oracle.scale_reg(surf.log_scale)
+    assert g["loss"][0] == pytest.approx(Limg + Ls, rel=1e-5)
+    # end to end (oracle's own forward): the same loss to 1e-5
+    Lo, _, _, _ = oracle.forward_backward(surf, [frame], [(tgt.D, tgt.N)])
+    assert g["loss"][0] == pytest.approx(Lo, rel=1e-5)
+    og = oracle_grads(oracle, surf, [frame], [gpu_upstream(g, 0)])
+    assert_grads(compare_grads(g["grads"][0], og))
 
 
 def test_tile_shape_and_batch_do_not_change_results(oracle):
@@ -155,41 +219,43 @@ def test_tile_shape_and_batch_do_not_change_results(oracle):
 
 def test_multi_frame_multi_map_batch(oracle):
     """Two maps, three frames (two render map 0 from different poses) in one
-    call: each frame equals its oracle frame; each map's gradient equals the
-    oracle gradient of that map's own window."""
+    call: each frame equals its oracle frame; each map's loss and gradient
+    equal the oracle's for that map's own window (image terms averaged over
+    the map's frames)."""
     from tests import _gpu
     s0, f0, t0 = scenes.box_room(seed=0)
     f0b = scenes.Frame(32, 512, 16, 16, f0.elev_min, f0.elev_max, scenes.pose_matrix(0.4, (1.0, 0.5, 2.3)))
     _, _, t0b = scenes.box_room(seed=0, yaw=0.4)
     s1, f1 = scenes.random_shell(3, 500, frame=scenes.Frame(32, 512, 16, 16, -0.3, 0.3, scenes.pose_matrix(-0.2)))
     t1 = scenes.targets_for(f1, s1, 5)
-    frames = [f0, f1, f0b]
-    fmap = [0, 1, 0]
-    tg = [t0, t1, t0b]
+    frames, fmap, tg = [f0, f1, f0b], [0, 1, 0], [t0, t1, t0b]
     g = _gpu.run([s0, s1], frames, targets=tg, frame_map=fmap)
-    L0, fw0, og0, _ = oracle.forward_backward(s0, [f0, f0b], [(t0.D, t0.N), (t0b.D, t0b.N)])
-    L1, fw1, og1, _ = oracle.forward_backward(s1, [f1], [(t1.D, t1.N)])
-    for gf, of in ((g["fwd"][0], fw0[0]), (g["fwd"][1], fw1[0]), (g["fwd"][2], fw0[1])):
-        r = compare_forward(gf, of)
-        assert r["A"][0] and r["D"][0] and r["N"][0] and r["nc"], r
+    for f, (frame, m) in enumerate(zip(frames, fmap)):
+        surf = (s0, s1)[m]
+        b = oracle.bin_frame(surf, frame)
+        of = oracle.render_fwd(surf, frame, b["ranges"], b["vals"])
+        assert_forward(compare_forward(g["fwd"][f], of))
+    check_loss_on_gpu_forward(oracle, g, frames, tg, [0.5, 1.0, 0.5])
+    L0, _, _, _ = oracle.forward_backward(s0, [f0, f0b], [(t0.D, t0.N), (t0b.D, t0b.N)])
+    L1, _, _, _ = oracle.forward_backward(s1, [f1], [(t1.D, t1.N)])
     F = 3
     assert g["loss"][1 + 3 * F] == pytest.approx(L0, rel=1e-5)
     assert g["loss"][2 + 3 * F] == pytest.approx(L1, rel=1e-5)
     assert g["loss"][0] == pytest.approx(L0 + L1, rel=1e-5)
-    for gg, og in ((g["grads"][0], og0), (g["grads"][1], og1)):
-        r = compare_grads(gg, og)
-        for name_ in ("mean", "quat", "log_scale", "logit"):
-            assert r[name_][0], (name_, r)
+    og0 = oracle_grads(oracle, s0, [f0, f0b], [gpu_upstream(g, 0), gpu_upstream(g, 2)])
+    og1 = oracle_grads(oracle, s1, [f1], [gpu_upstream(g, 1)])
+    assert_grads(compare_grads(g["grads"][0], og0))
+    assert_grads(compare_grads(g["grads"][1], og1))
 
 
 def test_gradients_accumulate(oracle):
     from tests import _gpu
     surf, frame, tgt = scenes.box_room()
     g1 = _gpu.run([surf], [frame], targets=[tgt])
-    init = [g1["grads"][0]]
-    g2 = _gpu.run([surf], [frame], targets=[tgt], grads_init=init)
+    g2 = _gpu.run([surf], [frame], targets=[tgt], grads_init=[g1["grads"][0]])
+    # the backward sums with float atomics: equal up to summation order
     for a, b in zip(g2["grads"][0], g1["grads"][0]):
-        assert np.allclose(a, 2 * b, rtol=1e-5, atol=1e-9)
+        assert np.allclose(a, 2 * b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
 
 
 def test_empty_and_invisible_maps(oracle):
@@ -210,9 +276,9 @@ def test_empty_and_invisible_maps(oracle):
 def test_capacity_overflow_is_reported_and_recovered(oracle):
     import torch
     from paper_2607_04127_gb300 import lib
+    from tests import _gpu
     surf, frame, _ = scenes.box_room()
     o = oracle.bin_frame(surf, frame, want_pairs=False)
-    from tests import _gpu
     T = _gpu.to_dev(surf)
     S = lib.surfels_struct(*T)
     fr = [lib.frame_struct(frame)]
@@ -240,8 +306,8 @@ def test_invalid_arguments_are_rejected():
 
 def test_full_size_street_frame(oracle):
     """The 200k-surfel 128 x 1024 street frame in the launch configuration the
-    benchmark times (16 x 16 tiles, batch 256): bit-exact bins; forward and
-    gradients against the oracle run at full size."""
+    benchmark times (16 x 16 tiles, batch 256): bit-exact bins; forward, loss
+    and gradients against the oracle run at full size."""
     from tests import _gpu
     surf, frame, tgt = scenes.street()
     g = _gpu.run([surf], [frame], targets=[tgt], read_bins=True)
@@ -249,10 +315,12 @@ def test_full_size_street_frame(oracle):
     o = oracle.bin_frame(surf, frame)
     keys = (tp.astype(np.uint64) << np.uint64(32)) | dk[ip].astype(np.uint64)
     assert np.array_equal(keys, o["keys"]) and np.array_equal(ip, o["vals"])
-    L, of, og, _ = oracle_frame(oracle, surf, frame, tgt)
+    assert np.array_equal(rg.astype(np.int64), o["ranges"])
+    of = oracle.render_fwd(surf, frame, o["ranges"], o["vals"])
     r = compare_forward(g["fwd"][0], of)
-    assert r["A"][0] and r["D"][0] and r["N"][0] and r["nc"], r
-    assert g["loss"][0] == pytest.approx(L, rel=1e-5)
-    rg_ = compare_grads(g["grads"][0], og)
-    for name_ in ("mean", "quat", "log_scale", "logit"):
-        assert rg_[name_ + "_global"] < 1e-2, rg_
+    assert_forward(r)
+    assert r["A"][1] > 0.99 and r["D"][1] > 0.999, (r["A"][1], r["D"][1])
+    Limg = check_loss_on_gpu_forward(oracle, g, [frame], [tgt], [1.0])
+    assert g["loss"][0] == pytest.approx(Limg + oracle.scale_reg(surf.log_scale), rel=1e-5)
+    og = oracle_grads(oracle, surf, [frame], [gpu_upstream(g, 0)])
+    assert_grads(compare_grads(g["grads"][0], og))

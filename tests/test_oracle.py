@@ -395,3 +395,41 @@ def test_p8_scale_regulariser(oracle):
 def test_oracle_constants(oracle):
     c = oracle.constants()
     assert c[0] == 0.2 and c[1] == 9.0 and c[2] == 1 / 255 and c[3] == 0.99 and c[4] == 1e-4
+
+
+def test_p6_gradient_with_clamped_opacity(oracle):
+    """Surfels with alpha = 0.999 facing the ray through a pixel centre: there
+    a = min(alpha G, 0.99) is clamped (flat), at the neighbouring pixels it is
+    not; the analytic gradient (zero through the clamp) matches central
+    differences."""
+    frame = scenes.Frame(16, 64, 16, 16, -0.5, 0.5)
+    bg, _ = scenes.random_shell(14, 40, r_range=(6.0, 9.0), scale_range=(0.2, 0.9), frame=frame)
+    fs = facing_surfels([(pixel_dir(frame, r, c), 4.0 + 0.3 * k, 0.999, 0.5, 0.4, 0.0)
+                         for k, (r, c) in enumerate(((5, 9), (8, 30), (11, 50)))])
+    surf = scenes.Surfels(*(np.concatenate([getattr(fs, k), getattr(bg, k)])
+                            for k in ("mean", "quat", "log_scale", "logit")))
+    tgt = scenes.targets_for(frame, surf, seed=3)
+    base = [np.ascontiguousarray(a, np.float64).copy() for a in
+            (surf.mean, surf.quat, surf.log_scale, surf.logit)]
+    L0, fw0, g = _loss64(oracle, surf, frame, tgt, base)
+    assert (fw0["flags"] & 16).sum() == 0            # no pixel near the clamp kink
+    gl = [g["mean"], g["quat"], g["log_scale"], g["logit"]]
+    h, used = 1e-6, 0
+    for which in range(4):
+        for i in range(3):                            # the clamped surfels
+            for comp in range(base[which].shape[1] if base[which].ndim > 1 else 1):
+                idx = (i, comp) if base[which].ndim > 1 else (i,)
+                vals, same = [], True
+                for sgn in (1, -1):
+                    p = [a.copy() for a in base]
+                    p[which][idx] += sgn * h
+                    L, fw, _ = _loss64(oracle, surf, frame, tgt, p)
+                    vals.append(L)
+                    same &= np.array_equal(fw["n_valid"], fw0["n_valid"])
+                if not same:
+                    continue
+                fd = (vals[0] - vals[1]) / (2 * h)
+                scale = max(abs(fd), 1e-3 * max(np.abs(x).max() for x in gl))
+                assert abs(gl[which][idx] - fd) <= 2e-5 * scale + 1e-9, (which, idx, gl[which][idx], fd)
+                used += 1
+    assert used >= 25
