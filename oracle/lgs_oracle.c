@@ -729,6 +729,62 @@ static void raw_abs(const surf64* s, const sgrad* g, const frame64* F, double* r
     r[7] = fabs(dl[0]); r[8] = fabs(dl[1]); r[9] = fabs(dg);
 }
 
+static void rot_jacobian(const double* q, double J[9][4]);
+
+/* Majorant of the raw-parameter gradient of one contribution: the chain of
+ * chain_to_params with every product in absolute value, i.e. the sum of the
+ * magnitudes that a binary32 evaluation of the chain adds up (a rotation of an
+ * isotropic surfel about its normal, for one, cancels exactly in FP64 but not
+ * in binary32). */
+static void raw_major(const surf64* s, const sgrad* g, const frame64* F, double* r)
+{
+    double dcol[3][3];
+    for (int a = 0; a < 3; ++a) {
+        double gm = 0, g0 = 0, g1 = 0, g2 = 0;
+        for (int k = 0; k < 3; ++k) {
+            double R = fabs(F->R[3 * a + k]);
+            gm += R * fabs(g->mu[k]);
+            g0 += R * fabs(g->tu[k]);
+            g1 += R * fabs(g->tv[k]);
+            g2 += R * fabs(g->n[k]);
+        }
+        r[a] = gm;
+        dcol[0][a] = g0; dcol[1][a] = g1; dcol[2][a] = g2;
+    }
+    double J[9][4];
+    rot_jacobian(s->qh, J);
+    double dqh[4] = { 0, 0, 0, 0 };
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 4; ++c) dqh[c] += dcol[b][a] * fabs(J[3 * a + b][c]);
+    double pr = 0;
+    for (int c = 0; c < 4; ++c) pr += dqh[c] * fabs(s->qh[c]);
+    for (int c = 0; c < 4; ++c) r[3 + c] = (dqh[c] + fabs(s->qh[c]) * pr) / s->qnorm;
+    r[7] = fabs(g->su) * s->su;
+    r[8] = fabs(g->sv) * s->sv;
+    r[9] = fabs(g->alpha) * s->alpha * (1.0 - s->alpha);
+}
+
+/* The evaluation e with its local coordinates moved by (du, dv), its depth by
+ * dtt and n.d by dden, the skip and clamp decisions kept: the inputs a
+ * binary32 evaluation may see instead of e's (u and v are absolute
+ * uncertainties, so terms proportional to a small u, v or offset x are
+ * covered too). */
+static void perturb_eval(const surf64* s, const eval64* e, double du, double dv, double dtt, double dden,
+                         eval64* p)
+{
+    *p = *e;
+    p->den = e->den + dden;
+    p->t = e->t + dtt;
+    p->u = e->u + du;
+    p->v = e->v + dv;
+    for (int k = 0; k < 3; ++k) p->x[k] = e->x[k] + du * s->su * s->tu[k] + dv * s->sv * s->tv[k];
+    p->q = p->u * p->u + p->v * p->v;
+    p->G = exp(-0.5 * p->q);
+    p->araw = s->alpha * p->G;
+    p->a = e->araw < A_MAX ? p->araw : A_MAX;
+}
+
 static void add10(double* dst, const double* r, double f)
 {
     for (int c = 0; c < 10; ++c) {
@@ -739,14 +795,58 @@ static void add10(double* dst, const double* r, double f)
     }
 }
 
-/* Relative binary32 uncertainty of one evaluation's contribution: local
- * coordinates known to ek (see fp32_bound), t to dt / t, amplified by the
- * Gaussian's slope (|u| + |v|) and by 1/|n.d| through t = (n.mu)/(n.d). */
-static double fp32_rel(const surf64* s, const eval64* e)
+/* First-order binary32 uncertainty of the opacity of one evaluation: a
+ * re-derived with u, v moved by their uncertainty ek, t by dt and n.d by 4
+ * ulp, the changes added in absolute value, plus 4 ulp of rounding. */
+static double opacity_unc(const surf64* s, const eval64* e)
 {
     double ek, dt;
     fp32_unc(s, e->den, e->t, &ek, &dt);
-    return 2.0 * ((fabs(e->u) + fabs(e->v) + 1.0) * ek + dt / fabs(e->t));
+    const double dden = (e->den > 0 ? 4.0 : -4.0) * EPS32;
+    const double steps[4][4] = { { ek, 0, 0, 0 }, { 0, ek, 0, 0 }, { 0, 0, dt, 0 }, { 0, 0, 0, dden } };
+    double da = 4.0 * EPS32 * e->a;
+    for (int k = 0; k < 4; ++k) {
+        eval64 p;
+        perturb_eval(s, e, steps[k][0], steps[k][1], steps[k][2], steps[k][3], &p);
+        da += fabs(p.a - e->a);
+    }
+    return da;
+}
+
+/* First-order binary32 uncertainty of one contribution c0 (into r[10], raw
+ * parameters): c0 re-derived with u, v moved by their uncertainty ek, t by
+ * dt, n.d by 4 ulp, the transmittance T by the relative amount eT and the
+ * suffix by dS, the six changes added in absolute value.  Propagating the
+ * inputs' errors this way (instead of scaling a majorant) keeps the size of
+ * cancelling upstream terms out of the bound, and keeps terms proportional to
+ * a small u, v or offset x in it. */
+static void contrib_unc(const surf64* s, const eval64* e, const double* d, double T, double suffix, double eT,
+                        double dS, double gA, double gSt, const double* gSn, const frame64* F, const sgrad* c0,
+                        double* r)
+{
+    double ek, dt;
+    fp32_unc(s, e->den, e->t, &ek, &dt);
+    const double dden = (e->den > 0 ? 4.0 : -4.0) * EPS32;
+    const double steps[4][4] = { { ek, 0, 0, 0 }, { 0, ek, 0, 0 }, { 0, 0, dt, 0 }, { 0, 0, 0, dden } };
+    for (int c = 0; c < 10; ++c) r[c] = 0;
+    for (int k = 0; k < 6; ++k) {
+        eval64 p;
+        double Tk = T, Sk = suffix;
+        if (k < 4) perturb_eval(s, e, steps[k][0], steps[k][1], steps[k][2], steps[k][3], &p);
+        else p = *e;
+        if (k == 4) Tk = T * (1.0 + eT);
+        if (k == 5) Sk = suffix + dS;
+        sgrad g;
+        memset(&g, 0, sizeof(g));
+        contrib_grad(s, &p, d, Tk, Sk, gA, gSt, gSn, 1, &g);
+        for (int j = 0; j < 3; ++j) {
+            g.mu[j] -= c0->mu[j]; g.tu[j] -= c0->tu[j]; g.tv[j] -= c0->tv[j]; g.n[j] -= c0->n[j];
+        }
+        g.su -= c0->su; g.sv -= c0->sv; g.alpha -= c0->alpha;
+        double q[10];
+        raw_abs(s, &g, F, q);
+        for (int c = 0; c < 10; ++c) r[c] += q[c];
+    }
 }
 
 #define FL_HARD (FL_DEN | FL_TNEAR)
@@ -756,26 +856,86 @@ static double fp32_rel(const surf64* s, const eval64* e)
  * (gA, gSt, gSn) of (A, S_t, S_n).  Besides the gradient (into G) it records,
  * per surfel and raw parameter (when gabs / gflip are given):
  *   gabs  += a majorant of each contribution (its terms in absolute value:
- *            the conditioning of the sums);
- *   gflip += the majorant times the contribution's relative binary32
- *            uncertainty (fp32_rel), and
- *   gflip += what a near-threshold decision taken the other way by a binary32
- *            evaluation can change: the whole would-be contribution of the
- *            surfel concerned, and for the other contributors of the pixel the
- *            sum of the flipping opacities times their contribution; a grazing
- *            or near-plane decision makes the surfel's value undetermined
- *            (gflip = inf). */
+ *            the conditioning of the sums and of the chain to the raw
+ *            parameters);
+ *   gflip += twice the first-order change of the contribution under the
+ *            binary32 uncertainties of its inputs (contrib_unc: u, v, t, n.d,
+ *            the transmittance before it and the suffix after it, where a
+ *            near-threshold decision of another entry counts as an
+ *            uncertainty of its whole opacity), and
+ *   gflip += what a near-threshold decision of the surfel's own can change:
+ *            its whole would-be contribution; a grazing or near-plane
+ *            decision makes the surfel's value undetermined (gflip = inf). */
+/* Opacity that a binary32 evaluation may add or drop at a near-threshold
+ * decision of evaluated entry k of a pixel (contributor or not; 0 if none). */
+static double flip_opacity(const surf64* s, const double* d, const eval64* e, int is_contrib, int last_contrib,
+                           int stop_entry, const pix_out* o)
+{
+    int tstop = (o->flags & FL_TSTOP) != 0;
+    if (is_contrib) {
+        if ((e->flags & FL_SOFT) || (tstop && last_contrib)) return e->a;
+        if (e->flags & FL_AMAX) return fabs(e->araw - A_MAX);
+        return 0.0;
+    }
+    if ((e->flags & FL_SOFT) || (tstop && stop_entry)) {
+        eval64 f;
+        force_eval(s, d, &f);
+        return f.a;
+    }
+    return 0.0;
+}
+
 static void backward_pixel(const surf64* S, const uint32_t* list, const double* d, int nc,
                            const int64_t* ck, const double* cT, const pix_out* o, double gA, double gSt,
                            const double* gSn, const frame64* F, sgrad* G, double* gabs, double* gflip,
-                           double* tmp, double* suf)
+                           double* tmp, double* suf, double* et)
 {
-    double suffix = 0.0, suffix_abs = 0.0;
-    for (int m = nc - 1; m >= 0; --m) {
-        uint32_t i = list[ck[m]];
+    const int unc = gflip && gabs;
+    double suffix = 0.0, suffix_abs = 0.0, dS = 0.0;
+    if (unc) {
+        /* et[m]: relative uncertainty of the transmittance before contributor m:
+         * the earlier opacities' binary32 uncertainties, the opacities that a
+         * near-threshold decision may add or drop, and the roundings of the
+         * products / quotients that carry it */
+        double acc = 2.0 * nc * EPS32;
+        int mm = 0;
+        for (int64_t k = 0; k < o->neval; ++k) {
+            const surf64* s = S + list[k];
+            int is_contrib = mm < nc && ck[mm] == k;
+            eval64 e;
+            eval_pair(s, d, &e);
+            int stop_entry = (k == o->neval - 1) && !is_contrib && e.valid;
+            double fa = flip_opacity(s, d, &e, is_contrib, mm == nc - 1, stop_entry, o);
+            if (is_contrib) {
+                et[mm++] = acc;
+                acc += (opacity_unc(s, &e) + fa) / (1.0 - e.a);
+            } else if (fa > 0) {
+                acc += fa / (1.0 - fa);
+            }
+        }
+    }
+    int mm = nc - 1;
+    for (int64_t k = o->neval - 1; k >= 0; --k) {
+        uint32_t i = list[k];
         const surf64* s = S + i;
         eval64 e;
         eval_pair(s, d, &e);                   /* recompute the same evaluation */
+        if (mm < 0 || ck[mm] != k) {
+            /* not composited: a near-threshold entry may still be in binary32,
+             * adding its term to the suffix of the contributors before it */
+            if (!unc) continue;
+            int stop_entry = (k == o->neval - 1) && e.valid;
+            double fa = flip_opacity(s, d, &e, 0, 0, stop_entry, o);
+            if (fa > 0) {
+                eval64 f;
+                force_eval(s, d, &f);
+                double np = f.den > 0 ? -1.0 : 1.0;
+                double gcw = gA + gSt * f.t + np * dot3(gSn, s->n);
+                dS += fa * (mm + 1 < nc ? cT[mm + 1] : o->T) * fabs(gcw);
+            }
+            continue;
+        }
+        const int m = mm--;
         double T = cT[m];
         sgrad c;
         memset(&c, 0, sizeof(c));
@@ -788,9 +948,19 @@ static void backward_pixel(const surf64* S, const uint32_t* list, const double* 
             memset(&cm, 0, sizeof(cm));
             double gcm = contrib_grad_m(s, &e, d, T, suffix_abs, gA, gSt, gSn, 1, 1, &cm);
             suffix_abs += e.a * T * gcm;
-            raw_abs(s, &cm, F, tmp + 10 * m);
+            raw_major(s, &cm, F, tmp + 10 * m);
             add10(gabs + 10 * (int64_t)i, tmp + 10 * m, 1.0);
-            if (gflip) add10(gflip + 10 * (int64_t)i, tmp + 10 * m, fp32_rel(s, &e));
+        }
+        if (unc) {
+            double r[10], ek, dt;
+            /* suffix - w gc: the suffix over the later contributors only */
+            contrib_unc(s, &e, d, T, suffix - e.a * T * gc, et[m], dS, gA, gSt, gSn, F, &c, r);
+            add10(gflip + 10 * (int64_t)i, r, 2.0);
+            /* this term's own uncertainty, for the contributors before it */
+            fp32_unc(s, e.den, e.t, &ek, &dt);
+            double w = e.a * T;
+            double fa = flip_opacity(s, d, &e, 1, m == nc - 1, 0, o);
+            dS += (opacity_unc(s, &e) + fa) * T * fabs(gc) + w * fabs(gSt) * dt + et[m] * fabs(w * gc);
         }
         if (gflip && (e.flags & FL_AMAX)) {
             sgrad u;
@@ -801,12 +971,10 @@ static void backward_pixel(const surf64* S, const uint32_t* list, const double* 
             add10(gflip + 10 * (int64_t)i, r, 1.0);
         }
     }
-    if (!gflip || !gabs || !o->flags) return;
-    /* the other contributors: relative change bounded by the flipping opacities */
-    for (int m = 0; m < nc; ++m) add10(gflip + 10 * (int64_t)list[ck[m]], tmp + 10 * m, 2.0 * o->flipa);
+    if (!unc || !o->flags) return;
     if (o->flags & FL_TSTOP && nc > 0) add10(gflip + 10 * (int64_t)list[ck[nc - 1]], tmp + 10 * (nc - 1), 1.0);
     /* the surfels whose own decision is near a threshold */
-    int mm = 0;
+    mm = 0;
     for (int64_t k = 0; k < o->neval; ++k) {
         while (mm < nc && ck[mm] < k) ++mm;
         int is_contrib = mm < nc && ck[mm] == k;
@@ -925,6 +1093,7 @@ void lgso_render_bwd(const double* mean, const double* quat, const double* ls, c
         double* cT = (double*)malloc(sizeof(double) * maxlen);
         double* tmp = (double*)malloc(sizeof(double) * 10 * maxlen);
         double* suf = (double*)malloc(sizeof(double) * maxlen);
+        double* et = (double*)malloc(sizeof(double) * maxlen);
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
@@ -940,10 +1109,10 @@ void lgso_render_bwd(const double* mean, const double* quat, const double* ls, c
                     int64_t p = (int64_t)r * W + c;
                     double gsn[3] = { gSn[p], gSn[HW + p], gSn[2 * HW + p] };
                     backward_pixel(S, vals + b, d, nc, ck, cT, &o, gA[p], gSt[p], gsn, &F, G, gabs, gflip,
-                                   tmp, suf);
+                                   tmp, suf, et);
                 }
         }
-        free(ck); free(cT); free(tmp); free(suf);
+        free(ck); free(cT); free(tmp); free(suf); free(et);
     }
     for (int64_t i = 0; i < n; ++i) {
         sgrad acc;
