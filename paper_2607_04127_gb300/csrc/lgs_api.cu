@@ -181,6 +181,7 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
   L.status = take(sizeof(Status));
   L.tables = take(sizeof(float) * (table_floats + 4));
   L.rec = take(64 * I);
+  L.box = take(16 * I);
   L.key = take(4 * I);
   L.cnt = take(4 * I);
   L.srtA_k = take(4 * I);

@@ -90,8 +90,8 @@ __device__ __forceinline__ uint32_t count_tiles(const BinGeom& g, const FrameDev
 // Preprocess: record + key + count per (frame, surfel) item
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, const float* __restrict__ tab,
-                                                     float4* __restrict__ rec, uint32_t* __restrict__ key,
-                                                     uint32_t* __restrict__ cnt) {
+                                                     float4* __restrict__ rec, float4* __restrict__ box,
+                                                     uint32_t* __restrict__ key, uint32_t* __restrict__ cnt) {
   const int64_t item = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (item >= D->n_items) return;
   const int f = frame_of_item(*D, item);
@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, 
   bin_geom(M.mean + 3 * i, M.ls + 2 * i, F, g);
   key[item] = __float_as_uint(g.r);
   cnt[item] = count_tiles(g, F, tab);
+  box[item] = pixel_box(g, F);
 
   // compositing record (accuracy only): rotation of the unit quaternion,
   // axes to the sensor frame, activations
@@ -515,7 +516,8 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
   if (e != cudaSuccess) return e;
   k_tables<<<n_frames, 256, 0, s>>>(w.desc, w.tables, w.st);
   const int64_t ni = n_items > 0 ? n_items : 1;
-  k_preprocess<<<static_cast<unsigned>((ni + 255) / 256), 256, 0, s>>>(w.desc, w.tables, w.rec, w.key, w.cnt);
+  k_preprocess<<<static_cast<unsigned>((ni + 255) / 256), 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key,
+                                                                       w.cnt);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
   // depth sort of the visible items (first pass compacts)

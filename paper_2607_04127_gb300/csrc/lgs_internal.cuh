@@ -77,7 +77,7 @@ constexpr int kScanChunk = kScanThreads * kScanItems;   // 2048 per CTA
 
 // Workspace layout (byte offsets; computed on the host, passed by value).
 struct Layout {
-  size_t desc, status, tables, rec, key, cnt, srtA_k, srtA_v, srtB_k, srtB_v, offs, bsum,
+  size_t desc, status, tables, rec, box, key, cnt, srtA_k, srtA_v, srtB_k, srtB_v, offs, bsum,
       pk_A, pk_B, pv_A, pv_B, hist, dtot, ranges, g13, work, loss_part, total;
   int64_t items_cap, pairs_cap;
   uint32_t tiles_cap;
@@ -91,6 +91,7 @@ struct WsPtrs {
   Status* st;
   float* tables;
   float4* rec;             // [items][4]
+  float4* box;             // [items] conservative pixel box: row_lo, row_hi, col centre, col half-width
   uint32_t* key;           // depth key per item
   uint32_t* cnt;           // tile count per item
   uint32_t *sk_a, *sv_a, *sk_b, *sv_b;   // item sort ping-pong (key, item)
@@ -112,6 +113,7 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.st = reinterpret_cast<Status*>(b + L.status);
   p.tables = reinterpret_cast<float*>(b + L.tables);
   p.rec = reinterpret_cast<float4*>(b + L.rec);
+  p.box = reinterpret_cast<float4*>(b + L.box);
   p.key = reinterpret_cast<uint32_t*>(b + L.key);
   p.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
   p.sk_a = reinterpret_cast<uint32_t*>(b + L.srtA_k);
@@ -295,10 +297,76 @@ __device__ __forceinline__ void bin_col_window(const BinGeom& g, const FrameDev&
   }
 }
 
+// Conservative pixel-space box of the bounding cone: rows [x, y] (floats),
+// columns as a circular centre z and half-width w, padded by one pixel.  It
+// only lets a warp skip records that cannot pass the cut-off at any of its
+// pixels; results never depend on it.
+__device__ __forceinline__ float4 pixel_box(const BinGeom& g, const FrameDev& F) {
+  float r_lo = 0.f, r_hi = static_cast<float>(F.H - 1);
+  if (!g.all_rows) {
+    const float dth = (F.emax - F.emin) / static_cast<float>(F.H);
+    const float th_hi = asinf(fminf(fmaxf(g.sin_hi, -1.f), 1.f));
+    const float th_lo = asinf(fminf(fmaxf(g.sin_lo, -1.f), 1.f));
+    r_lo = fmaxf(floorf((F.emax - th_hi) / dth - 0.5f) - 1.f, 0.f);
+    r_hi = fminf(ceilf((F.emax - th_lo) / dth - 0.5f) + 1.f, static_cast<float>(F.H - 1));
+  }
+  float cc = 0.f, chw = static_cast<float>(F.W);
+  if (!g.all_cols) {
+    const float two_pi = 6.283185307f;
+    float phic = atan2f(g.y, g.x);
+    if (phic < 0.f) phic += two_pi;
+    const float dphi = asinf(fminf(g.rho / g.h, 1.f));
+    const float cpr = static_cast<float>(F.W) / two_pi;
+    cc = phic * cpr - 0.5f;
+    chw = dphi * cpr + 1.5f;
+  }
+  return make_float4(r_lo, r_hi, cc, chw);
+}
+
+// Pixel of a thread inside its tile: 4 x 8 pixel blocks per warp when the
+// tile shape allows, row-major otherwise.
+__device__ __forceinline__ void pixel_of_thread(const FrameDev& F, int tid, int& lr, int& lc) {
+  if ((F.tw & 7) == 0 && (F.th & 3) == 0) {
+    const int w = tid >> 5, lane = tid & 31, wpr = F.tw >> 3;
+    lr = (w / wpr) * 4 + (lane >> 3);
+    lc = (w % wpr) * 8 + (lane & 7);
+  } else {
+    lr = tid / F.tw;
+    lc = tid % F.tw;
+  }
+}
+
+// The pixel block of a warp: rows [r0, r1], columns centred on cmid with
+// half-width chalf (an empty block when no lane is inside the frame).
+struct WarpBox {
+  float r0, r1, cmid, chalf, W;
+};
+
+__device__ __forceinline__ WarpBox warp_box(bool inside, int r, int c, int W) {
+  const int rmin = __reduce_min_sync(0xffffffffu, inside ? r : 0x7fffffff);
+  const int rmax = __reduce_max_sync(0xffffffffu, inside ? r : -1);
+  const int cmin = __reduce_min_sync(0xffffffffu, inside ? c : 0x7fffffff);
+  const int cmax = __reduce_max_sync(0xffffffffu, inside ? c : -1);
+  WarpBox b;
+  b.r0 = static_cast<float>(rmin);
+  b.r1 = static_cast<float>(rmax);
+  b.cmid = 0.5f * (static_cast<float>(cmin) + static_cast<float>(cmax));
+  b.chalf = 0.5f * (static_cast<float>(cmax) - static_cast<float>(cmin));
+  b.W = static_cast<float>(W);
+  return b;
+}
+
+__device__ __forceinline__ bool box_hits(const float4& b, const WarpBox& w) {
+  if (b.x > w.r1 || b.y < w.r0) return false;
+  float d = b.z - w.cmid;
+  d -= w.W * rintf(d / w.W);
+  return fabsf(d) <= b.w + w.chalf;
+}
+
 // ---------------------------------------------------------------------------
 // Compositing record (4 x float4 = 64 B per item):
 //   r0 = (n, h = n.mu), r1 = (a_u = t_u/s_u, b_u = t_u.mu/s_u),
-//   r2 = (a_v, b_v), r3 = (alpha, 0, 0, 0); sensor frame.
+//   r2 = (a_v, b_v), r3 = (alpha, s_u, s_v, 0); sensor frame.
 // Then for a unit ray d: den = n.d, t = h/den, u = t (a_u.d) - b_u,
 // v = t (a_v.d) - b_v.
 // ---------------------------------------------------------------------------

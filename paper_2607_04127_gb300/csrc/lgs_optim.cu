@@ -181,7 +181,10 @@ __global__ void __launch_bounds__(256) k_loss_pixel(const Desc* __restrict__ D, 
       const float gDh = sgn * ind;
       gSt = scale * gDh / a;
       gA = scale * (-gDh * St / (a * a));
-      la -= logf(A + 1e-6f);
+      // log(A + 1e-6): for A >= 1/2 as log1p((A - 1) + 1e-6), where A - 1 is
+      // exact, so opacities near 1 keep their precision; below 1/2 directly,
+      // where A + 1e-6 is exact to half an ulp
+      la -= A >= 0.5f ? log1pf((A - 1.0f) + 1e-6f) : logf(A + 1e-6f);
       gA -= scale * P.lambda_alpha * ind / (A + 1e-6f);
       const float nx = F.Ng[p], ny = F.Ng[HW + p], nz = F.Ng[2 * HW + p];
       if (nx * nx + ny * ny + nz * nz > 0.f) {

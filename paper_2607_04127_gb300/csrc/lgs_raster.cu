@@ -45,8 +45,10 @@ __device__ __forceinline__ TileCtx tile_ctx(const Desc& D, uint32_t tile, const 
   const FrameDev& F = D.f[t.f];
   const int lt = static_cast<int>(tile - F.tile_base);
   const int ti = lt / F.ntc, tj = lt - ti * F.ntc;
-  t.r = ti * F.th + static_cast<int>(threadIdx.x) / F.tw;
-  t.c = tj * F.tw + static_cast<int>(threadIdx.x) % F.tw;
+  int lr, lc;
+  pixel_of_thread(F, static_cast<int>(threadIdx.x), lr, lc);
+  t.r = ti * F.th + lr;
+  t.c = tj * F.tw + lc;
   t.inside = t.r < F.H && t.c < F.W;
   t.pix = static_cast<int64_t>(t.r) * F.W + t.c;
   t.HW = F.H * F.W;
@@ -74,23 +76,43 @@ __device__ __forceinline__ bool next_tile(bool persistent, const uint32_t* __res
   return true;
 }
 
+// The batch entries whose pixel box meets the warp's pixel block, in list
+// order: 32 boxes tested per step (one per lane) and compacted with a ballot.
+// Returns the count (uniform over the warp).
+__device__ __forceinline__ int warp_list(const float4* s_box, int nb, const WarpBox& wb, uint16_t* list) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  int cnt = 0;
+  for (int base = 0; base < nb; base += 32) {
+    const int j = base + lane;
+    const bool hit = j < nb && box_hits(s_box[j], wb);
+    const uint32_t m = __ballot_sync(0xffffffffu, hit);
+    if (hit) list[cnt + __popc(m & lt)] = static_cast<uint16_t>(j);
+    cnt += __popc(m);
+  }
+  __syncwarp();
+  return cnt;
+}
+
 // ---------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------
 template <int BATCH>
 __global__ void __launch_bounds__(kMaxTileThreads)
     k_fwd(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
-          const float4* __restrict__ rec, const uint32_t* __restrict__ order, Status* __restrict__ st,
-          int persistent) {
-  __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[BATCH];
+          const float4* __restrict__ rec, const float4* __restrict__ box, const uint32_t* __restrict__ order,
+          Status* __restrict__ st, int persistent) {
+  __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[BATCH], s_box[BATCH];
   __shared__ float s_al[BATCH];
+  __shared__ uint16_t s_list[kMaxTileThreads / 32][BATCH];
   const int nthr = blockDim.x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, wid = tid >> 5;
   uint32_t tile;
   unsigned long long evals = 0, contrib = 0;
   for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
     const FrameDev& F = D->f[tc.f];
+    const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
     float dx = 0.f, dy = 0.f, dz = 0.f;
     if (tc.inside) pixel_ray(F, tc.r, tc.c, dx, dy, dz);
     float T = 1.0f, A = 0.0f, St = 0.0f, Sx = 0.0f, Sy = 0.0f, Sz = 0.0f;
@@ -106,11 +128,15 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         s_r1[j] = rp[1];
         s_r2[j] = rp[2];
         s_al[j] = rp[3].x;
+        s_box[j] = box[item];
       }
       __syncthreads();
+      int cnt = 0;
+      if (!__all_sync(0xffffffffu, done)) cnt = warp_list(s_box, nb, wb, s_list[wid]);
       if (!done) {
-        int j = 0;
-        for (; j < nb; ++j) {
+        for (int k = 0; k < cnt; ++k) {
+          const int j = s_list[wid][k];
+          ++evals;
           Eval e;
           eval_pair(s_r0[j], s_r1[j], s_r2[j], s_al[j], dx, dy, dz, e);
           if (!e.valid) continue;
@@ -130,7 +156,6 @@ __global__ void __launch_bounds__(kMaxTileThreads)
           last = static_cast<int>(b0 - tc.start) + j + 1;
           ++contrib;
         }
-        evals += static_cast<unsigned long long>(j < nb ? j + 1 : nb);
       }
     }
     if (tc.inside) {
@@ -190,9 +215,10 @@ __device__ __forceinline__ void warp_reduce16(float (&v)[16], int lane) {
 template <int BATCH>
 __global__ void __launch_bounds__(kMaxTileThreads)
     k_bwd(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
-          const float4* __restrict__ rec, float* __restrict__ g13, const uint32_t* __restrict__ order,
-          Status* __restrict__ st, int persistent) {
-  __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[BATCH], s_r3[BATCH];
+          const float4* __restrict__ rec, const float4* __restrict__ box, float* __restrict__ g13,
+          const uint32_t* __restrict__ order, Status* __restrict__ st, int persistent) {
+  __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[BATCH], s_r3[BATCH], s_box[BATCH];
+  __shared__ uint16_t s_list[kMaxTileThreads / 32][BATCH];
   __shared__ uint32_t s_item[BATCH];
   __shared__ float s_g[kGrad][BATCH];
   __shared__ int s_max;
@@ -205,6 +231,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
   for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
     const FrameDev& F = D->f[tc.f];
+    const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
     float dx = 0.f, dy = 0.f, dz = 0.f;
     float T = 1.f, gA = 0.f, gSt = 0.f, gSx = 0.f, gSy = 0.f, gSz = 0.f;
     int nc = 0;
@@ -238,11 +265,14 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         s_r1[j] = rp[1];
         s_r2[j] = rp[2];
         s_r3[j] = rp[3];
+        s_box[j] = box[item];
 #pragma unroll
         for (int c = 0; c < kGrad; ++c) s_g[c][j] = 0.f;
       }
       __syncthreads();
-      for (int j = nb - 1; j >= 0; --j) {
+      const int cnt = warp_list(s_box, nb, wb, s_list[tid >> 5]);
+      for (int kk = cnt - 1; kk >= 0; --kk) {
+        const int j = s_list[tid >> 5][kk];
         const int k = static_cast<int>(b0 - tc.start) + j;
         float v[16];
 #pragma unroll
@@ -328,13 +358,13 @@ __global__ void __launch_bounds__(kMaxTileThreads)
 // ---------------------------------------------------------------------------
 template <int B>
 static cudaError_t fwd_b(const WsPtrs& w, const uint32_t* pv, const Desc& h, int persistent, int grid, cudaStream_t s) {
-  k_fwd<B><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, nullptr, w.st, persistent);
+  k_fwd<B><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, nullptr, w.st, persistent);
   return cudaGetLastError();
 }
 
 template <int B>
 static cudaError_t bwd_b(const WsPtrs& w, const uint32_t* pv, const Desc& h, int persistent, int grid, cudaStream_t s) {
-  k_bwd<B><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.g13, nullptr, w.st,
+  k_bwd<B><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, nullptr, w.st,
                                         persistent);
   return cudaGetLastError();
 }
