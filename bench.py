@@ -29,8 +29,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd rays/s at 200k surfels, 128x1024"
 UNIT = "rays/s"
-WORKLOAD = dict(workload="street 200k surfels, 128x1024 range image, +-45 deg, 16x16 tiles", surfels=200_000,
-                H=128, W=1024, tile="16x16", frames=1, loss="depth L1 + 0.1 opacity BCE + 0.05 normal cosine + 10 scale")
+WORKLOAD = dict(workload="street 200k surfels, 128x1024 range image, +-45 deg", surfels=200_000,
+                H=128, W=1024, frames=1, loss="depth L1 + 0.1 opacity BCE + 0.05 normal cosine + 10 scale")
 # FP32 operations per ray/surfel evaluation and per composited pair (FMA = 2),
 # counted from the definition (see the design notes).
 FLOP_EVAL = 27
@@ -45,8 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=256)
-    ap.add_argument("--persistent", type=int, default=0)
+    ap.add_argument("--tile", default=None, help="tile shape HxW (default: the renderer's)")
+    ap.add_argument("--fwd-batch", type=int, default=None)
+    ap.add_argument("--bwd-batch", type=int, default=None)
+    ap.add_argument("--group", type=int, default=None)
+    ap.add_argument("--persistent", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -170,10 +173,14 @@ def run_ours(args):
     build.build()
     from paper_2607_04127_gb300 import render, scenes
     surf, frame, tgt = scenes.street()
+    tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else render.DEFAULT_TILE
+    frame = frame.with_tiles(*tile)
+    tuning = {k: v for k, v in (("fwd_batch", args.fwd_batch), ("bwd_batch", args.bwd_batch), ("group", args.group),
+                                ("persistent", args.persistent)) if v is not None}
     params = render.map_tensors(surf, dev)
     targets = [render.target_tensors(tgt, dev)]
     grads = [[torch.zeros_like(p) for p in params]]
-    rast = render.Rasterizer([frame], device=dev.index, batch=args.batch, persistent=args.persistent)
+    rast = render.Rasterizer([frame], device=dev.index, tuning=tuning)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
     stream = torch.cuda.current_stream(dev)
 
@@ -275,7 +282,7 @@ def run_ours(args):
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=statistics.mean(step_ms), higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="f32", data="synthetic (seeded street scene, see scenes.street)",
-        config=dict(WORKLOAD, parallelism=f"replicas x{world}", batch=args.batch, persistent=args.persistent,
+        config=dict(WORKLOAD, parallelism=f"replicas x{world}", tile=f"{tile[0]}x{tile[1]}", **rast.tuning,
                     l2="flushed between steps (256 MB write); per-step CUDA events, flush not timed"),
         evals_per_s=world * args.steps * (evf + evb) / total_s,
         stages_ms=dict(bin_sort=statistics.mean(bin_ms), fwd=statistics.mean(fwd_ms),

@@ -153,8 +153,13 @@ typedef struct {
 
 /* Tuning knobs of the compositing kernels (results do not depend on them). */
 typedef struct {
-    int32_t batch;       /* surfel records per shared-memory batch: 64..512, multiple of 32 */
-    int32_t persistent;  /* 1: persistent CTAs claim tiles, longest list first */
+    int32_t fwd_batch;   /* forward compositing: 0 = every warp walks the tile list on
+                            its own (32 entries per ballot, records through L1);
+                            64, 128, 256, 512 = the CTA stages that many records per
+                            shared-memory batch */
+    int32_t bwd_batch;   /* backward: the same choice (0, 64, 128 or 256) */
+    int32_t group;       /* warp walk only: hits fetched and evaluated together, 1, 2 or 4 */
+    int32_t persistent;  /* 1: persistent CTAs claim tiles through an atomic counter */
 } lgs_tuning;
 
 /* ---- sessions and workspace -------------------------------------------- */
@@ -199,7 +204,8 @@ LGS_API lgs_status lgs_session_counters(lgs_session s, int64_t out[8]);
 /* Device pointers into the workspace describing the last bin_sort, valid
  * until the next one: tile_of_pair[P] (global tile id, frame f's tiles start
  * at the sum of the tile counts of frames < f), item_of_pair[P] (frame-major
- * item f*n + surfel for one map), ranges[2*T] (start, end per global tile),
+ * item f*n + surfel for one map), ranges[2*T] (start, end per global tile;
+ * (0, 0) for a tile without pairs),
  * depth_key[items] (binary32 bits of |mu_sensor|). */
 LGS_API lgs_status lgs_session_bins(lgs_session s, const uint32_t** tile_of_pair, const uint32_t** item_of_pair,
                             const uint32_t** ranges, const uint32_t** depth_key);
@@ -267,7 +273,8 @@ LGS_API lgs_status lgs_loss_batch(lgs_session s, const lgs_surfels* maps, int n_
                           const lgs_fwd_grad_out* grads_out, const lgs_surfel_grad* grads,
                           float* loss_out, void* stream);
 
-/* Set the compositing knobs of a session (defaults: batch 256, persistent 0). */
+/* Set the compositing knobs of a session (defaults: fwd_batch 64, bwd_batch 0,
+ * group 1, persistent 0).  Every choice gives bit-identical forward outputs. */
 LGS_API lgs_status lgs_session_set_tuning(lgs_session s, const lgs_tuning* t);
 
 /* One Adam step over the n surfels' 10 parameters (optimiser of the mapping

@@ -26,11 +26,13 @@ struct lgs_session_s {
   bool binned = false;
   Layout lay{};
   Desc* desc = nullptr;         // host copy of the last bin_sort's descriptors
-  int pairs_in_b = 0;
+  Desc* desc_prev = nullptr;    // scratch: the descriptors before a bin_sort rebuilt them
+  Desc* desc_dev = nullptr;     // what the workspace's descriptor block holds (when desc_dev_at is set)
+  const void* desc_dev_at = nullptr;
   size_t g13_zero_off = 0;      // g13 region known to be all-zero
   int64_t g13_zero_items = -1;
   cudaStream_t last_stream = nullptr;
-  lgs_tuning tune{256, 0};
+  lgs_tuning tune{64, 0, 1, 0};
   Status* h_status = nullptr;   // pinned
   int64_t launches = 0;         // kernels enqueued by this session
 };
@@ -184,19 +186,10 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
   L.box = take(16 * I);
   L.key = take(4 * I);
   L.cnt = take(4 * I);
-  L.srtA_k = take(4 * I);
-  L.srtA_v = take(4 * I);
-  L.srtB_k = take(4 * I);
-  L.srtB_v = take(4 * I);
-  L.offs = take(4 * I);
-  L.bsum = take(8 * ((I + lgs::kScanChunk - 1) / lgs::kScanChunk + 1));
-  L.pk_A = take(4 * P);
-  L.pk_B = take(4 * P);
-  L.pv_A = take(4 * P);
-  L.pv_B = take(4 * P);
-  const size_t G = ((I > P ? I : P) + lgs::kSortChunk - 1) / lgs::kSortChunk;
-  L.hist = take(4 * 256 * G);
-  L.dtot = take(4 * 256 * 8);
+  L.tcur = take(4 * T);
+  L.pkey = take(8 * P);
+  L.ptile = take(4 * P);
+  L.pv = take(4 * P);
   L.ranges = take(8 * T);
   L.g13 = take(64 * I);
   L.work = take(4 * T);
@@ -206,7 +199,6 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
   L.pairs_cap = pairs_cap;
   L.tiles_cap = tiles;
   L.tables_cap = table_floats;
-  L.hist_blocks = static_cast<int32_t>(G);
   return L;
 }
 
@@ -221,6 +213,45 @@ int64_t fit_pairs(size_t bytes, const Plan& p) {
     if (make_layout(p.n_items, p.n_tiles, mid, p.table_floats).total <= bytes) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// Copy the descriptors to the workspace unless it already holds exactly
+// these.  Calls captured into a CUDA graph always copy (the graph must carry
+// its own copy) and make the next call copy again.
+cudaError_t write_desc(lgs_session s, const Desc& d, Desc* dev, cudaStream_t cs, int64_t& launches) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(cs, &cap);
+  if (e != cudaSuccess) return e;
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  if (!capturing && s->desc_dev_at == dev && memcmp(&d, s->desc_dev, sizeof(Desc)) == 0) return cudaSuccess;
+  if ((e = lgs::launch_write_desc(d, dev, nullptr, cs)) != cudaSuccess) return e;
+  ++launches;
+  if (capturing) {
+    s->desc_dev_at = nullptr;
+  } else {
+    memcpy(s->desc_dev, &d, sizeof(Desc));
+    s->desc_dev_at = dev;
+  }
+  return cudaSuccess;
+}
+
+// Keep the per-call pointers of the previous descriptors (a bin_sort
+// rebuilds the geometry only; every call sets the pointers it uses), so that
+// repeated steps over the same buffers leave the descriptors unchanged.
+void keep_call_ptrs(Desc& d, const Desc& prev) {
+  for (int f = 0; f < LGS_MAX_FRAMES; ++f) {
+    lgs::FrameDev& a = d.f[f];
+    const lgs::FrameDev& b = prev.f[f];
+    a.A = b.A; a.St = b.St; a.Sn = b.Sn; a.Tf = b.Tf; a.nc = b.nc;
+    a.gA = b.gA; a.gSt = b.gSt; a.gSn = b.gSn;
+    a.oA = b.oA; a.oSt = b.oSt; a.oSn = b.oSn; a.D = b.D; a.Ng = b.Ng;
+  }
+  for (int m = 0; m < LGS_MAX_MAPS; ++m) {
+    d.m[m].d_mean = prev.m[m].d_mean;
+    d.m[m].d_quat = prev.m[m].d_quat;
+    d.m[m].d_ls = prev.m[m].d_ls;
+    d.m[m].d_logit = prev.m[m].d_logit;
+  }
 }
 
 lgs_status enter(lgs_session s) {
@@ -319,12 +350,20 @@ lgs_status lgs_session_create(int device, size_t hbm_budget_bytes, lgs_session* 
   s->device = device;
   s->budget = hbm_budget_bytes;
   s->desc = new (std::nothrow) Desc;
-  if (!s->desc) {
+  s->desc_prev = new (std::nothrow) Desc;
+  s->desc_dev = new (std::nothrow) Desc;
+  if (!s->desc || !s->desc_prev || !s->desc_dev) {
+    delete s->desc;
+    delete s->desc_prev;
+    delete s->desc_dev;
     delete s;
     return fail(LGS_ERR_INVALID_ARG, "out of host memory");
   }
+  memset(s->desc, 0, sizeof(Desc));
   if ((e = cudaSetDevice(device)) != cudaSuccess || (e = cudaMallocHost(&s->h_status, sizeof(Status))) != cudaSuccess) {
     delete s->desc;
+    delete s->desc_prev;
+    delete s->desc_dev;
     delete s;
     return cuda_fail(e, "session create");
   }
@@ -340,6 +379,8 @@ lgs_status lgs_session_destroy(lgs_session s) {
     cudaFreeHost(s->h_status);
   }
   delete s->desc;
+  delete s->desc_prev;
+  delete s->desc_dev;
   delete s;
   return LGS_OK;
 }
@@ -385,13 +426,17 @@ lgs_status lgs_session_set_workspace(lgs_session s, void* dev_ptr, size_t bytes)
   s->ws_bytes = bytes;
   s->binned = false;
   s->g13_zero_items = -1;
+  s->desc_dev_at = nullptr;   // a new workspace holds no descriptors (even at the old address)
   return LGS_OK;
 }
 
 lgs_status lgs_session_set_tuning(lgs_session s, const lgs_tuning* t) {
   if (!s || !t) return fail(LGS_ERR_INVALID_ARG, "NULL argument");
-  if (t->batch != 64 && t->batch != 128 && t->batch != 256 && t->batch != 512)
-    return fail(LGS_ERR_INVALID_ARG, "batch must be 64, 128, 256 or 512");
+  const auto ok_batch = [](int b, int hi) { return b == 0 || ((b == 64 || b == 128 || b == 256 || b == 512) && b <= hi); };
+  if (!ok_batch(t->fwd_batch, 512)) return fail(LGS_ERR_INVALID_ARG, "fwd_batch must be 0, 64, 128, 256 or 512");
+  if (!ok_batch(t->bwd_batch, 256)) return fail(LGS_ERR_INVALID_ARG, "bwd_batch must be 0, 64, 128 or 256");
+  if (t->group != 1 && t->group != 2 && t->group != 4) return fail(LGS_ERR_INVALID_ARG, "group must be 1, 2 or 4");
+  if (t->persistent != 0 && t->persistent != 1) return fail(LGS_ERR_INVALID_ARG, "persistent must be 0 or 1");
   s->tune = *t;
   return LGS_OK;
 }
@@ -447,8 +492,8 @@ lgs_status lgs_session_bins(lgs_session s, const uint32_t** tile_of_pair, const 
   if (!s) return fail(LGS_ERR_INVALID_ARG, "session is NULL");
   if (!s->binned) return fail(LGS_ERR_STATE, "no lgs_bin_sort yet");
   const WsPtrs w = lgs::ws_ptrs(s->ws, s->lay);
-  if (tile_of_pair) *tile_of_pair = s->pairs_in_b ? w.pk_b : w.pk_a;
-  if (item_of_pair) *item_of_pair = s->pairs_in_b ? w.pv_b : w.pv_a;
+  if (tile_of_pair) *tile_of_pair = w.ptile;
+  if (item_of_pair) *item_of_pair = w.pv;
   if (ranges) *ranges = reinterpret_cast<const uint32_t*>(w.ranges);
   if (depth_key) *depth_key = w.key;
   return LGS_OK;
@@ -465,9 +510,9 @@ lgs_status lgs_session_read_bins(lgs_session s, uint32_t* tile_of_pair, uint32_t
   const WsPtrs w = lgs::ws_ptrs(s->ws, s->lay);
   cudaError_t e = cudaSuccess;
   if (tile_of_pair && np && e == cudaSuccess)
-    e = cudaMemcpy(tile_of_pair, s->pairs_in_b ? w.pk_b : w.pk_a, 4 * np, cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(tile_of_pair, w.ptile, 4 * np, cudaMemcpyDeviceToHost);
   if (item_of_pair && np && e == cudaSuccess)
-    e = cudaMemcpy(item_of_pair, s->pairs_in_b ? w.pv_b : w.pv_a, 4 * np, cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(item_of_pair, w.pv, 4 * np, cudaMemcpyDeviceToHost);
   if (ranges && e == cudaSuccess)
     e = cudaMemcpy(ranges, w.ranges, 8 * static_cast<size_t>(s->desc->n_tiles), cudaMemcpyDeviceToHost);
   if (depth_key && s->desc->n_items && e == cudaSuccess)
@@ -484,7 +529,12 @@ lgs_status lgs_bin_sort_batch(lgs_session s, const lgs_surfels* maps, int n_maps
   if ((st = check_maps(maps, n_maps, frame_map, n_frames)) != LGS_OK) return st;
   if (!s->ws) return fail(LGS_ERR_NO_WORKSPACE, "no workspace set");
   Plan p;
-  if ((st = build_desc(maps, n_maps, frames, frame_map, n_frames, *s->desc, p)) != LGS_OK) return st;
+  memcpy(s->desc_prev, s->desc, sizeof(Desc));
+  if ((st = build_desc(maps, n_maps, frames, frame_map, n_frames, *s->desc, p)) != LGS_OK) {
+    memcpy(s->desc, s->desc_prev, sizeof(Desc));
+    return st;
+  }
+  keep_call_ptrs(*s->desc, *s->desc_prev);
   const int64_t cap = fit_pairs(s->ws_bytes, p);
   if (cap < 0)
     return fail(LGS_ERR_NO_WORKSPACE, "workspace of %zu bytes too small even without pairs (%zu needed)", s->ws_bytes,
@@ -500,11 +550,10 @@ lgs_status lgs_bin_sort_batch(lgs_session s, const lgs_surfels* maps, int n_maps
     s->g13_zero_items = p.n_items;
     s->g13_zero_off = L.g13;
   }
-  if ((e = lgs::launch_write_desc(*s->desc, w.desc, w.st, cs)) != cudaSuccess) return cuda_fail(e, "write_desc");
+  if ((e = write_desc(s, *s->desc, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
   if ((e = lgs::launch_bin(L, w, n_frames, p.n_items, p.n_tiles, cs)) != cudaSuccess) return cuda_fail(e, "bin");
-  s->launches += 1 + lgs::bin_kernel_count(p.n_tiles);
+  s->launches += lgs::bin_kernel_count(p.n_tiles);
   s->lay = L;
-  s->pairs_in_b = lgs::pair_sort_result_in_b(p.n_tiles);
   s->binned = true;
   s->last_stream = cs;
   return LGS_OK;
@@ -534,11 +583,11 @@ lgs_status lgs_render_fwd_batch(lgs_session s, const lgs_surfels* maps, int n_ma
   const WsPtrs w = lgs::ws_ptrs(s->ws, s->lay);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if ((e = lgs::launch_write_desc(d, w.desc, w.st, cs)) != cudaSuccess) return cuda_fail(e, "write_desc");
-  const uint32_t* pv = s->pairs_in_b ? w.pv_b : w.pv_a;
-  if ((e = lgs::launch_raster_fwd(s->lay, w, d, pv, s->tune.batch, s->tune.persistent, cs)) != cudaSuccess)
+  if ((e = write_desc(s, d, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
+  const uint32_t* pv = w.pv;
+  if ((e = lgs::launch_raster_fwd(s->lay, w, d, pv, s->tune.fwd_batch, s->tune.group, s->tune.persistent, cs)) != cudaSuccess)
     return cuda_fail(e, "raster_fwd");
-  s->launches += 2;
+  s->launches += 1;
   s->last_stream = cs;
   return LGS_OK;
 }
@@ -583,13 +632,12 @@ lgs_status lgs_render_bwd_batch(lgs_session s, const lgs_surfels* maps, int n_ma
   const WsPtrs w = lgs::ws_ptrs(s->ws, s->lay);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if ((e = lgs::launch_write_desc(d, w.desc, w.st, cs)) != cudaSuccess) return cuda_fail(e, "write_desc");
-  const uint32_t* pv = s->pairs_in_b ? w.pv_b : w.pv_a;
-  const int batch = s->tune.batch > 256 ? 256 : s->tune.batch;
-  if ((e = lgs::launch_raster_bwd(s->lay, w, d, pv, batch, s->tune.persistent, cs)) != cudaSuccess)
+  if ((e = write_desc(s, d, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
+  const uint32_t* pv = w.pv;
+  if ((e = lgs::launch_raster_bwd(s->lay, w, d, pv, s->tune.bwd_batch, s->tune.group, s->tune.persistent, cs)) != cudaSuccess)
     return cuda_fail(e, "raster_bwd");
   if ((e = lgs::launch_preprocess_bwd(s->lay, w, d, cs)) != cudaSuccess) return cuda_fail(e, "preprocess_bwd");
-  s->launches += 3;
+  s->launches += 2;
   s->last_stream = cs;
   return LGS_OK;
 }
@@ -638,10 +686,10 @@ lgs_status lgs_loss_batch(lgs_session s, const lgs_surfels* maps, int n_maps, co
   const WsPtrs w = lgs::ws_ptrs(s->ws, s->lay);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if ((e = lgs::launch_write_desc(d, w.desc, w.st, cs)) != cudaSuccess) return cuda_fail(e, "write_desc");
+  if ((e = write_desc(s, d, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
   if ((e = lgs::launch_loss(s->lay, w, d, *params, scale_grad, loss_out, cs)) != cudaSuccess)
     return cuda_fail(e, "loss");
-  s->launches += 5;
+  s->launches += 2;
   s->last_stream = cs;
   return LGS_OK;
 }

@@ -64,25 +64,14 @@ struct Status {
   unsigned long long evals_bwd;
   unsigned long long contrib_fwd;     // composited (fwd) / valid re-evaluated (bwd) pairs
   unsigned long long contrib_bwd;
-  int loss_count[2 * LGS_MAX_FRAMES]; // per frame |Omega_D|, |Omega_N|
+  unsigned int loss_ticket;           // loss CTAs finished (the last one reduces; self-resetting)
 };
 
-// Radix-sort / scan geometry shared by the host layout and the kernels.
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortChunk = kSortThreads * kSortItems;   // 4096 keys per CTA
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanChunk = kScanThreads * kScanItems;   // 2048 per CTA
-
-// Workspace layout (byte offsets; computed on the host, passed by value).
 struct Layout {
-  size_t desc, status, tables, rec, box, key, cnt, srtA_k, srtA_v, srtB_k, srtB_v, offs, bsum,
-      pk_A, pk_B, pv_A, pv_B, hist, dtot, ranges, g13, work, loss_part, total;
+  size_t desc, status, tables, rec, box, key, cnt, tcur, pkey, ptile, pv, ranges, g13, work, loss_part, total;
   int64_t items_cap, pairs_cap;
   uint32_t tiles_cap;
   uint32_t tables_cap;     // floats
-  int32_t hist_blocks;     // radix CTAs for the larger of items / pairs
   int32_t loss_blocks;
 };
 
@@ -94,16 +83,14 @@ struct WsPtrs {
   float4* box;             // [items] conservative pixel box: row_lo, row_hi, col centre, col half-width
   uint32_t* key;           // depth key per item
   uint32_t* cnt;           // tile count per item
-  uint32_t *sk_a, *sv_a, *sk_b, *sv_b;   // item sort ping-pong (key, item)
-  uint32_t* offs;          // pair offset per sorted item
-  unsigned long long* bsum;// scan block sums
-  uint32_t *pk_a, *pk_b, *pv_a, *pv_b;   // pair sort ping-pong (tile, item)
-  uint32_t* hist;          // [256][blocks]
-  uint32_t* dtot;          // [passes][256] digit totals
+  uint32_t* tcur;          // [tiles] pair counts, then fill cursors
+  unsigned long long* pkey;// [pairs] (depth key << 32 | item), bucketed by tile, then sorted
+  uint32_t* ptile;         // [pairs] tile of every pair (sorted order)
+  uint32_t* pv;            // [pairs] item of every pair (sorted order)
   uint2* ranges;           // [tiles]
   float* g13;              // [items][16]
   uint32_t* work;          // persistent scheduler tile order
-  double* loss_part;       // [blocks][4]
+  double* loss_part;       // loss partial sums and mask counts
 };
 
 inline WsPtrs ws_ptrs(void* base, const Layout& L) {
@@ -116,18 +103,10 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.box = reinterpret_cast<float4*>(b + L.box);
   p.key = reinterpret_cast<uint32_t*>(b + L.key);
   p.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
-  p.sk_a = reinterpret_cast<uint32_t*>(b + L.srtA_k);
-  p.sv_a = reinterpret_cast<uint32_t*>(b + L.srtA_v);
-  p.sk_b = reinterpret_cast<uint32_t*>(b + L.srtB_k);
-  p.sv_b = reinterpret_cast<uint32_t*>(b + L.srtB_v);
-  p.offs = reinterpret_cast<uint32_t*>(b + L.offs);
-  p.bsum = reinterpret_cast<unsigned long long*>(b + L.bsum);
-  p.pk_a = reinterpret_cast<uint32_t*>(b + L.pk_A);
-  p.pk_b = reinterpret_cast<uint32_t*>(b + L.pk_B);
-  p.pv_a = reinterpret_cast<uint32_t*>(b + L.pv_A);
-  p.pv_b = reinterpret_cast<uint32_t*>(b + L.pv_B);
-  p.hist = reinterpret_cast<uint32_t*>(b + L.hist);
-  p.dtot = reinterpret_cast<uint32_t*>(b + L.dtot);
+  p.tcur = reinterpret_cast<uint32_t*>(b + L.tcur);
+  p.pkey = reinterpret_cast<unsigned long long*>(b + L.pkey);
+  p.ptile = reinterpret_cast<uint32_t*>(b + L.ptile);
+  p.pv = reinterpret_cast<uint32_t*>(b + L.pv);
   p.ranges = reinterpret_cast<uint2*>(b + L.ranges);
   p.g13 = reinterpret_cast<float*>(b + L.g13);
   p.work = reinterpret_cast<uint32_t*>(b + L.work);
@@ -428,11 +407,10 @@ __device__ __forceinline__ int frame_of_item(const Desc& D, int64_t item) {
 cudaError_t launch_write_desc(const Desc& h, Desc* d, Status* st, cudaStream_t s);
 cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n_items, uint32_t n_tiles,
                        cudaStream_t s);
-int pair_sort_result_in_b(uint32_t n_tiles);
 int bin_kernel_count(uint32_t n_tiles);
-cudaError_t launch_raster_fwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
+cudaError_t launch_raster_fwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch, int group,
                               int persistent, cudaStream_t s);
-cudaError_t launch_raster_bwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
+cudaError_t launch_raster_bwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch, int group,
                               int persistent, cudaStream_t s);
 size_t loss_part_bytes();
 cudaError_t launch_preprocess_bwd(const Layout& L, const WsPtrs& w, const Desc& h, cudaStream_t s);

@@ -123,7 +123,6 @@ cudaError_t launch_preprocess_bwd(const Layout&, const WsPtrs& w, const Desc& h,
 // with masked means over M_D = [D > 0] and M_N = M_D [|N_gicp| > 0].
 // ---------------------------------------------------------------------------
 constexpr int kLossBlocks = 64;   // CTAs per frame (fixed: deterministic partial sums)
-constexpr int kScaleBlocks = 64;  // CTAs per map for the scale regulariser
 
 __device__ __forceinline__ double block_sum_d(double v, double* s_w) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -137,7 +136,8 @@ __device__ __forceinline__ double block_sum_d(double v, double* s_w) {
   return t;
 }
 
-__global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, Status* __restrict__ st) {
+// Mask counts per (frame, CTA): [F][kLossBlocks][2] ints, no atomics.
+__global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, int* __restrict__ cpart) {
   const FrameDev& F = D->f[blockIdx.y];
   const int HW = F.H * F.W;
   int md = 0, mn = 0;
@@ -147,110 +147,147 @@ __global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, 
     md += d;
     mn += d && (a * a + b * b + c * c > 0.f);
   }
+  __shared__ int s_c[2][8];
   for (int o = 16; o > 0; o >>= 1) {
     md += __shfl_xor_sync(0xffffffffu, md, o);
     mn += __shfl_xor_sync(0xffffffffu, mn, o);
   }
-  if ((threadIdx.x & 31) == 0) {
-    if (md) atomicAdd(&st->loss_count[2 * blockIdx.y], md);
-    if (mn) atomicAdd(&st->loss_count[2 * blockIdx.y + 1], mn);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_c[0][wid] = md;
+    s_c[1][wid] = mn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0, b = 0;
+    for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) {
+      a += s_c[0][i];
+      b += s_c[1][i];
+    }
+    int* o = cpart + 2 * (static_cast<int64_t>(blockIdx.y) * kLossBlocks + blockIdx.x);
+    o[0] = a;
+    o[1] = b;
   }
 }
 
-__global__ void __launch_bounds__(256) k_loss_pixel(const Desc* __restrict__ D, const Status* __restrict__ st,
-                                                     lgs_loss_params P, double* __restrict__ part) {
+__device__ __forceinline__ int2 mask_counts(const int* __restrict__ cpart, int f) {
+  int a = 0, b = 0;
+  for (int i = 0; i < kLossBlocks; ++i) {
+    a += cpart[2 * (f * kLossBlocks + i)];
+    b += cpart[2 * (f * kLossBlocks + i) + 1];
+  }
+  return make_int2(a, b);
+}
+
+// Rows y < n_frames: the image terms of frame y and its upstream gradient
+// planes; rows n_frames + m: the scale regulariser of map m.  The CTA that
+// finishes last reduces every partial sum in a fixed order (deterministic)
+// and writes the loss vector.
+__global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, Status* __restrict__ st,
+                                                    lgs_loss_params P, int write_grad, const int* __restrict__ cpart,
+                                                    double* __restrict__ part, double* __restrict__ spart,
+                                                    float* __restrict__ out) {
   __shared__ double s_w[8];
-  const int f = blockIdx.y;
-  const FrameDev& F = D->f[f];
-  const int HW = F.H * F.W;
-  const int nd = st->loss_count[2 * f], nn = st->loss_count[2 * f + 1];
-  const float scale = 1.0f / static_cast<float>(D->m[F.map].n_frames);
-  const float ind = nd > 0 ? 1.0f / static_cast<float>(nd) : 0.f;
-  const float inn = nn > 0 ? 1.0f / static_cast<float>(nn) : 0.f;
-  double ld = 0.0, la = 0.0, ln = 0.0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
-    float gA = 0.f, gSt = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-    const float Dm = F.D[p];
-    if (Dm > 0.f) {
-      const float A = F.A[p], St = F.St[p];
-      const float a = A + 1e-6f;
-      const float Dh = St / a;
-      const float diff = Dh - Dm;
-      ld += fabsf(diff);
-      const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-      const float gDh = sgn * ind;
-      gSt = scale * gDh / a;
-      gA = scale * (-gDh * St / (a * a));
-      // log(A + 1e-6): for A >= 1/2 as log1p((A - 1) + 1e-6), where A - 1 is
-      // exact, so opacities near 1 keep their precision; below 1/2 directly,
-      // where A + 1e-6 is exact to half an ulp
-      la -= A >= 0.5f ? log1pf((A - 1.0f) + 1e-6f) : logf(A + 1e-6f);
-      gA -= scale * P.lambda_alpha * ind / (A + 1e-6f);
-      const float nx = F.Ng[p], ny = F.Ng[HW + p], nz = F.Ng[2 * HW + p];
-      if (nx * nx + ny * ny + nz * nz > 0.f) {
-        const float sx = F.Sn[p], sy = F.Sn[HW + p], sz = F.Sn[2 * HW + p];
-        const float m = sqrtf(sx * sx + sy * sy + sz * sz + 1e-12f);
-        const float im = 1.f / m;
-        ln += 1.0 - static_cast<double>((sx * nx + sy * ny + sz * nz) * im);
-        const float k = -P.lambda_n * P.lambda_ng * inn;
-        const float g0 = k * nx, g1 = k * ny, g2 = k * nz;
-        const float sg = (sx * g0 + sy * g1 + sz * g2) * im * im * im;
-        gx = scale * (g0 * im - sx * sg);
-        gy = scale * (g1 * im - sy * sg);
-        gz = scale * (g2 * im - sz * sg);
+  __shared__ bool s_last;
+  if (blockIdx.y < static_cast<unsigned>(D->n_frames)) {
+    const int f = blockIdx.y;
+    const FrameDev& F = D->f[f];
+    const int HW = F.H * F.W;
+    const int2 cnt = mask_counts(cpart, f);
+    const int nd = cnt.x, nn = cnt.y;
+    const float scale = 1.0f / static_cast<float>(D->m[F.map].n_frames);
+    const float ind = nd > 0 ? 1.0f / static_cast<float>(nd) : 0.f;
+    const float inn = nn > 0 ? 1.0f / static_cast<float>(nn) : 0.f;
+    double ld = 0.0, la = 0.0, ln = 0.0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
+      float gA = 0.f, gSt = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+      const float Dm = F.D[p];
+      if (Dm > 0.f) {
+        const float A = F.A[p], St = F.St[p];
+        const float a = A + 1e-6f;
+        const float Dh = St / a;
+        const float diff = Dh - Dm;
+        ld += fabsf(diff);
+        const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+        const float gDh = sgn * ind;
+        gSt = scale * gDh / a;
+        gA = scale * (-gDh * St / (a * a));
+        // log(A + 1e-6): for A >= 1/2 as log1p((A - 1) + 1e-6), where A - 1 is
+        // exact, so opacities near 1 keep their precision; below 1/2 directly,
+        // where A + 1e-6 is exact to half an ulp
+        la -= A >= 0.5f ? log1pf((A - 1.0f) + 1e-6f) : logf(A + 1e-6f);
+        gA -= scale * P.lambda_alpha * ind / (A + 1e-6f);
+        const float nx = F.Ng[p], ny = F.Ng[HW + p], nz = F.Ng[2 * HW + p];
+        if (nx * nx + ny * ny + nz * nz > 0.f) {
+          const float sx = F.Sn[p], sy = F.Sn[HW + p], sz = F.Sn[2 * HW + p];
+          const float m = sqrtf(sx * sx + sy * sy + sz * sz + 1e-12f);
+          const float im = 1.f / m;
+          ln += 1.0 - static_cast<double>((sx * nx + sy * ny + sz * nz) * im);
+          const float k = -P.lambda_n * P.lambda_ng * inn;
+          const float g0 = k * nx, g1 = k * ny, g2 = k * nz;
+          const float sg = (sx * g0 + sy * g1 + sz * g2) * im * im * im;
+          gx = scale * (g0 * im - sx * sg);
+          gy = scale * (g1 * im - sy * sg);
+          gz = scale * (g2 * im - sz * sg);
+        }
+      }
+      F.oA[p] = gA;
+      F.oSt[p] = gSt;
+      F.oSn[p] = gx;
+      F.oSn[HW + p] = gy;
+      F.oSn[2 * HW + p] = gz;
+    }
+    const double t0 = block_sum_d(ld, s_w);
+    const double t1 = block_sum_d(la, s_w);
+    const double t2 = block_sum_d(ln, s_w);
+    if (threadIdx.x == 0) {
+      double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + blockIdx.x);
+      o[0] = t0;
+      o[1] = t1;
+      o[2] = t2;
+    }
+  } else {
+    const int mi = blockIdx.y - D->n_frames;
+    const MapDev& M = D->m[mi];
+    double acc = 0.0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < M.n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      const float s0 = expf(M.ls[2 * i]), s1 = expf(M.ls[2 * i + 1]);
+      const bool first = s0 >= s1;
+      const float sm = first ? s0 : s1;
+      if (sm > P.s_max) {
+        acc += static_cast<double>(sm - P.s_max);
+        if (write_grad) M.d_ls[2 * i + (first ? 0 : 1)] += P.lambda_s * sm;
       }
     }
-    F.oA[p] = gA;
-    F.oSt[p] = gSt;
-    F.oSn[p] = gx;
-    F.oSn[HW + p] = gy;
-    F.oSn[2 * HW + p] = gz;
+    const double t = block_sum_d(acc, s_w);
+    if (threadIdx.x == 0) spart[mi * kLossBlocks + blockIdx.x] = t;
   }
-  const double t0 = block_sum_d(ld, s_w);
-  const double t1 = block_sum_d(la, s_w);
-  const double t2 = block_sum_d(ln, s_w);
+
+  // last CTA: deterministic reduction of the partial sums
   if (threadIdx.x == 0) {
-    double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + blockIdx.x);
-    o[0] = t0;
-    o[1] = t1;
-    o[2] = t2;
+    __threadfence();
+    const unsigned total = gridDim.x * gridDim.y;
+    s_last = atomicAdd(&st->loss_ticket, 1u) == total - 1;
   }
-}
-
-__global__ void __launch_bounds__(256) k_scale_reg(const Desc* __restrict__ D, lgs_loss_params P, int write_grad,
-                                                    double* __restrict__ part) {
-  __shared__ double s_w[8];
-  const MapDev& M = D->m[blockIdx.y];
-  double acc = 0.0;
-  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < M.n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const float s0 = expf(M.ls[2 * i]), s1 = expf(M.ls[2 * i + 1]);
-    const bool first = s0 >= s1;
-    const float sm = first ? s0 : s1;
-    if (sm > P.s_max) {
-      acc += static_cast<double>(sm - P.s_max);
-      if (write_grad) M.d_ls[2 * i + (first ? 0 : 1)] += P.lambda_s * sm;
-    }
-  }
-  const double t = block_sum_d(acc, s_w);
-  if (threadIdx.x == 0) part[blockIdx.y * kScaleBlocks + blockIdx.x] = t;
-}
-
-__global__ void k_loss_final(const Desc* __restrict__ D, const Status* __restrict__ st, lgs_loss_params P,
-                             const double* __restrict__ part, const double* __restrict__ spart,
-                             float* __restrict__ out) {
-  if (threadIdx.x != 0) return;
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  st->loss_ticket = 0;
+  const volatile double* vpart = part;
+  const volatile double* vspart = spart;
   double Lmap[LGS_MAX_MAPS];
   for (int m = 0; m < D->n_maps; ++m) Lmap[m] = 0.0;
   for (int f = 0; f < D->n_frames; ++f) {
     double s0 = 0, s1 = 0, s2 = 0;
     for (int b = 0; b < kLossBlocks; ++b) {
-      const double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + b);
+      const volatile double* o = vpart + 4 * (static_cast<int64_t>(f) * kLossBlocks + b);
       s0 += o[0];
       s1 += o[1];
       s2 += o[2];
     }
-    const int nd = st->loss_count[2 * f], nn = st->loss_count[2 * f + 1];
+    const int2 cnt = mask_counts(cpart, f);
+    const int nd = cnt.x, nn = cnt.y;
     const double Ld = nd ? s0 / nd : 0.0, La = nd ? s1 / nd : 0.0, Ln = nn ? s2 / nn : 0.0;
     out[1 + 3 * f] = static_cast<float>(Ld);
     out[2 + 3 * f] = static_cast<float>(La);
@@ -261,7 +298,7 @@ __global__ void k_loss_final(const Desc* __restrict__ D, const Status* __restric
   double L = 0.0;
   for (int m = 0; m < D->n_maps; ++m) {
     double sr = 0.0;
-    for (int b = 0; b < kScaleBlocks; ++b) sr += spart[m * kScaleBlocks + b];
+    for (int b = 0; b < kLossBlocks; ++b) sr += vspart[m * kLossBlocks + b];
     Lmap[m] += P.lambda_s * sr;
     out[1 + 3 * D->n_frames + m] = static_cast<float>(Lmap[m]);
     L += Lmap[m];
@@ -271,19 +308,19 @@ __global__ void k_loss_final(const Desc* __restrict__ D, const Status* __restric
 
 cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
                         float* loss_out, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(w.st->loss_count, 0, sizeof(int) * 2 * LGS_MAX_FRAMES, s);
-  if (e != cudaSuccess) return e;
-  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, w.st);
-  k_loss_pixel<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, w.st, p, w.loss_part);
-  double* spart = w.loss_part + 4 * static_cast<int64_t>(LGS_MAX_FRAMES) * kLossBlocks;
-  k_scale_reg<<<dim3(kScaleBlocks, h.n_maps), 256, 0, s>>>(w.desc, p, scale_grad ? 1 : 0, spart);
-  k_loss_final<<<1, 32, 0, s>>>(w.desc, w.st, p, w.loss_part, spart, loss_out);
+  double* part = w.loss_part;
+  double* spart = part + 4 * static_cast<int64_t>(LGS_MAX_FRAMES) * kLossBlocks;
+  int* cpart = reinterpret_cast<int*>(spart + static_cast<int64_t>(LGS_MAX_MAPS) * kLossBlocks);
+  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, cpart);
+  k_loss_main<<<dim3(kLossBlocks, h.n_frames + h.n_maps), 256, 0, s>>>(w.desc, w.st, p, scale_grad ? 1 : 0, cpart,
+                                                                        part, spart, loss_out);
   return cudaGetLastError();
 }
 
 size_t loss_part_bytes() {
   return sizeof(double) * (4 * static_cast<size_t>(LGS_MAX_FRAMES) * kLossBlocks +
-                           static_cast<size_t>(LGS_MAX_MAPS) * kScaleBlocks);
+                           static_cast<size_t>(LGS_MAX_MAPS) * kLossBlocks) +
+         sizeof(int) * 2 * static_cast<size_t>(LGS_MAX_FRAMES) * kLossBlocks;
 }
 
 // ---------------------------------------------------------------------------

@@ -354,6 +354,252 @@ __global__ void __launch_bounds__(kMaxTileThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Warp-independent walk (batch = 0)
+// ---------------------------------------------------------------------------
+// Each warp culls and composites the tile list on its own: 32 entries per
+// step (one pixel box per lane, compacted with a ballot), records of the hits
+// read by the whole warp from L1 (broadcast loads; a tile's records are
+// shared by its warps through L1 instead of shared memory), the next hit's
+// record fetched while the current one is composited.  No CTA barrier sits in
+// the loop: a warp leaves when its own pixels have stopped, and the backward
+// walks only up to its own pixels' last contributor.  The per-pixel
+// arithmetic and order are those of the batched kernels (results are
+// bit-identical in the forward).
+struct Rec {
+  float4 r0, r1, r2, r3;
+};
+
+__device__ __forceinline__ Rec load_rec(const float4* __restrict__ rec, uint32_t item) {
+  const float4* rp = rec + 4 * static_cast<int64_t>(item);
+  Rec r;
+  r.r0 = __ldg(rp);
+  r.r1 = __ldg(rp + 1);
+  r.r2 = __ldg(rp + 2);
+  r.r3 = __ldg(rp + 3);
+  return r;
+}
+
+// G hits per step: their records are fetched and evaluated together (G
+// independent chains for the scheduler), then composited in list order.
+template <int G>
+__global__ void __launch_bounds__(kMaxTileThreads)
+    k_fwd_w(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
+            const float4* __restrict__ rec, const float4* __restrict__ box, Status* __restrict__ st,
+            int persistent) {
+  const int lane = threadIdx.x & 31;
+  uint32_t tile;
+  unsigned long long evals = 0, contrib = 0;
+  for (int iter = 0; next_tile(persistent, nullptr, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
+    const TileCtx tc = tile_ctx(*D, tile, ranges);
+    const FrameDev& F = D->f[tc.f];
+    const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    if (tc.inside) pixel_ray(F, tc.r, tc.c, dx, dy, dz);
+    float T = 1.0f, A = 0.0f, St = 0.0f, Sx = 0.0f, Sy = 0.0f, Sz = 0.0f;
+    int last = 0;
+    bool done = !tc.inside;
+    for (uint32_t base = tc.start; base < tc.end; base += 32) {
+      if (__all_sync(0xffffffffu, done)) break;
+      const uint32_t j = base + lane;
+      uint32_t item = 0;
+      bool hit = false;
+      if (j < tc.end) {
+        item = __ldg(pv + j);
+        hit = box_hits(__ldg(box + item), wb);
+      }
+      uint32_t m = __ballot_sync(0xffffffffu, hit);
+      while (m) {
+        int bq[G];
+        float4 r0[G], r1[G], r2[G];
+        float al[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          bq[q] = m ? __ffs(m) - 1 : -1;
+          m &= m - 1;
+          if (bq[q] >= 0) {
+            const float4* rp = rec + 4 * static_cast<int64_t>(__shfl_sync(0xffffffffu, item, bq[q]));
+            r0[q] = __ldg(rp);
+            r1[q] = __ldg(rp + 1);
+            r2[q] = __ldg(rp + 2);
+            al[q] = __ldg(reinterpret_cast<const float*>(rp + 3));
+          }
+        }
+        Eval e[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q)
+          if (bq[q] >= 0) eval_pair(r0[q], r1[q], r2[q], al[q], dx, dy, dz, e[q]);
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          if (bq[q] < 0 || done) continue;
+          ++evals;
+          if (!e[q].valid) continue;
+          const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e[q].a));
+          if (Tn < 1e-4f) {
+            done = true;
+            continue;
+          }
+          const float w = e[q].a * T;
+          const float ws = e[q].den > 0.f ? -w : w;
+          A += w;
+          St = fmaf(w, e[q].t, St);
+          Sx = fmaf(ws, r0[q].x, Sx);
+          Sy = fmaf(ws, r0[q].y, Sy);
+          Sz = fmaf(ws, r0[q].z, Sz);
+          T = Tn;
+          last = static_cast<int>(base - tc.start) + bq[q] + 1;
+          ++contrib;
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+      }
+    }
+    if (tc.inside) {
+      F.A[tc.pix] = A;
+      F.St[tc.pix] = St;
+      F.Sn[tc.pix] = Sx;
+      F.Sn[tc.HW + tc.pix] = Sy;
+      F.Sn[2 * static_cast<int64_t>(tc.HW) + tc.pix] = Sz;
+      F.Tf[tc.pix] = T;
+      F.nc[tc.pix] = last;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    evals += __shfl_xor_sync(0xffffffffu, evals, o);
+    contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+  }
+  if (lane == 0 && evals) atomicAdd(&st->evals_fwd, evals);
+  if (lane == 0 && contrib) atomicAdd(&st->contrib_fwd, contrib);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kMaxTileThreads)
+    k_bwd_w(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
+            const float4* __restrict__ rec, const float4* __restrict__ box, float* __restrict__ g13,
+            Status* __restrict__ st, int persistent) {
+  const int lane = threadIdx.x & 31;
+  const int gidx = 8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+  const bool writer = ((lane & 1) == 0) && gidx < kGrad;
+  uint32_t tile;
+  unsigned long long evals = 0, contrib = 0;
+  for (int iter = 0; next_tile(persistent, nullptr, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
+    const TileCtx tc = tile_ctx(*D, tile, ranges);
+    const FrameDev& F = D->f[tc.f];
+    const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    float T = 1.f, gA = 0.f, gSt = 0.f, gSx = 0.f, gSy = 0.f, gSz = 0.f;
+    int nc = 0;
+    if (tc.inside) {
+      pixel_ray(F, tc.r, tc.c, dx, dy, dz);
+      T = F.Tf[tc.pix];
+      nc = F.nc[tc.pix];
+      gA = F.gA[tc.pix];
+      gSt = F.gSt[tc.pix];
+      gSx = F.gSn[tc.pix];
+      gSy = F.gSn[tc.HW + tc.pix];
+      gSz = F.gSn[2 * static_cast<int64_t>(tc.HW) + tc.pix];
+    }
+    // n_contrib comes from the caller: never walk past the tile's list
+    const uint32_t len = tc.end - tc.start;
+    const uint32_t stop = min(static_cast<uint32_t>(__reduce_max_sync(0xffffffffu, nc > 0 ? nc : 0)), len);
+    float S = 0.f;
+    for (int c0 = static_cast<int>((stop + 31) / 32) - 1; c0 >= 0; --c0) {
+      const uint32_t k0 = 32u * c0;
+      uint32_t item = 0;
+      bool hit = false;
+      if (k0 + lane < stop) {
+        item = __ldg(pv + tc.start + k0 + lane);
+        hit = box_hits(__ldg(box + item), wb);
+      }
+      uint32_t m = __ballot_sync(0xffffffffu, hit);
+      while (m) {
+        int bq[G];
+        uint32_t itq[G];
+        float4 r0[G], r1[G], r2[G], r3[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          bq[q] = m ? 31 - __clz(m) : -1;
+          if (bq[q] >= 0) {
+            m &= ~(1u << bq[q]);
+            itq[q] = __shfl_sync(0xffffffffu, item, bq[q]);
+            const float4* rp = rec + 4 * static_cast<int64_t>(itq[q]);
+            r0[q] = __ldg(rp);
+            r1[q] = __ldg(rp + 1);
+            r2[q] = __ldg(rp + 2);
+            r3[q] = __ldg(rp + 3);
+          }
+        }
+        Eval e[G];
+        bool in[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          in[q] = bq[q] >= 0 && static_cast<int>(k0 + bq[q]) < nc;
+          if (in[q]) eval_pair(r0[q], r1[q], r2[q], r3[q].x, dx, dy, dz, e[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          if (bq[q] < 0) break;
+          float v[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) v[c] = 0.f;
+          const bool valid = in[q] && e[q].valid;
+          if (in[q]) ++evals;
+          if (valid) {
+            ++contrib;
+            const Eval& E = e[q];
+            const float alpha = r3[q].x;
+            const float om = 1.0f - E.a;
+            const float Tk = __fdividef(T, om);
+            const float sg = E.den > 0.f ? -1.f : 1.f;
+            const float gc = gA + gSt * E.t + sg * (gSx * r0[q].x + gSy * r0[q].y + gSz * r0[q].z);
+            const float w = E.a * Tk;
+            const float dLda = Tk * gc - __fdividef(S, om);
+            S = fmaf(w, gc, S);
+            T = Tk;
+            float dLdt = w * gSt;
+            const float wsg = w * sg;
+            float dLdu = 0.f, dLdv = 0.f;
+            if (E.araw < 0.99f) {
+              v[12] = dLda * E.G;
+              const float dLdq = -0.5f * dLda * alpha * E.G;
+              dLdu = 2.f * E.u * dLdq;
+              dLdv = 2.f * E.v * dLdq;
+            }
+            dLdt = fmaf(dLdu, E.ud, fmaf(dLdv, E.vd, dLdt));
+            // x = t d - mu = u s_u t_u + v s_v t_v, formed from (u, v)
+            const float su = r3[q].y, sv = r3[q].z;
+            const float cu = E.u * su * su, cv = E.v * sv * sv;
+            const float xx = fmaf(cu, r1[q].x, cv * r2[q].x);
+            const float xy = fmaf(cu, r1[q].y, cv * r2[q].y);
+            const float xz = fmaf(cu, r1[q].z, cv * r2[q].z);
+            const float ct = __fdividef(dLdt, E.den);
+            v[0] = fmaf(-ct, xx, wsg * gSx);
+            v[1] = fmaf(-ct, xy, wsg * gSy);
+            v[2] = fmaf(-ct, xz, wsg * gSz);
+            v[3] = ct;
+            const float gu = __fdividef(dLdu, su), gv = __fdividef(dLdv, sv);
+            v[4] = gu * xx; v[5] = gu * xy; v[6] = gu * xz;
+            v[7] = -gu;
+            v[8] = gv * xx; v[9] = gv * xy; v[10] = gv * xz;
+            v[11] = -gv;
+            v[13] = -dLdu * E.u;
+            v[14] = -dLdv * E.v;
+          }
+          if (__any_sync(0xffffffffu, valid)) {
+            warp_reduce16(v, lane);
+            if (writer && v[0] != 0.f) atomicAdd(g13 + 16 * static_cast<int64_t>(itq[q]) + gidx, v[0]);
+          }
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    evals += __shfl_xor_sync(0xffffffffu, evals, o);
+    contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+  }
+  if (lane == 0 && evals) atomicAdd(&st->evals_bwd, evals);
+  if (lane == 0 && contrib) atomicAdd(&st->contrib_bwd, contrib);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 template <int B>
@@ -378,13 +624,18 @@ static int persistent_grid(int threads) {
 }
 
 cudaError_t launch_raster_fwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
-                              int persistent, cudaStream_t s) {
+                              int group, int persistent, cudaStream_t s) {
   if (persistent) {
     cudaError_t e = cudaMemsetAsync(&w.st->work_counter, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
   }
   const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
   switch (batch) {
+    case 0:
+      if (group == 1) k_fwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.st, persistent);
+      else if (group == 2) k_fwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.st, persistent);
+      else k_fwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.st, persistent);
+      return cudaGetLastError();
     case 64: return fwd_b<64>(w, pv, h, persistent, grid, s);
     case 128: return fwd_b<128>(w, pv, h, persistent, grid, s);
     case 512: return fwd_b<512>(w, pv, h, persistent, grid, s);
@@ -393,16 +644,21 @@ cudaError_t launch_raster_fwd(const Layout&, const WsPtrs& w, const Desc& h, con
 }
 
 cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
-                              int persistent, cudaStream_t s) {
+                              int group, int persistent, cudaStream_t s) {
   if (persistent) {
     cudaError_t e = cudaMemsetAsync(&w.st->work_counter2, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
   }
   const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
   switch (batch) {
+    case 0:
+      if (group == 1) k_bwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, w.st, persistent);
+      else if (group == 2) k_bwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, w.st, persistent);
+      else k_bwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, w.st, persistent);
+      return cudaGetLastError();
     case 64: return bwd_b<64>(w, pv, h, persistent, grid, s);
     case 128: return bwd_b<128>(w, pv, h, persistent, grid, s);
-    default: return bwd_b<256>(w, pv, h, persistent, grid, s);   // 512 is clamped by the caller
+    default: return bwd_b<256>(w, pv, h, persistent, grid, s);
   }
 }
 

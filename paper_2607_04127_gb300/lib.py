@@ -65,7 +65,8 @@ class lgs_loss_params(ctypes.Structure):
 
 
 class lgs_tuning(ctypes.Structure):
-    _fields_ = [("batch", ctypes.c_int32), ("persistent", ctypes.c_int32)]
+    _fields_ = [("fwd_batch", ctypes.c_int32), ("bwd_batch", ctypes.c_int32), ("group", ctypes.c_int32),
+                ("persistent", ctypes.c_int32)]
 
 
 EXPORTS = [
@@ -261,8 +262,8 @@ def lgs_loss(h, surfels, frames, fwd, targets, params, grads_out, grad, loss_out
                            _ref(grad) if grad is not None else None, P(loss_out_ptr), P(stream)))
 
 
-def lgs_session_set_tuning(h, batch: int = 256, persistent: int = 0):
-    _check(load().lgs_session_set_tuning(h, _ref(lgs_tuning(batch, persistent))))
+def lgs_session_set_tuning(h, fwd_batch: int = 64, bwd_batch: int = 0, group: int = 1, persistent: int = 0):
+    _check(load().lgs_session_set_tuning(h, _ref(lgs_tuning(fwd_batch, bwd_batch, group, persistent))))
 
 
 def lgs_adam_step(mean, quat, log_scale, logit, grad, m_state, v_state, n, step, lr, beta1, beta2, eps,

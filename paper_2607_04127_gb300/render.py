@@ -41,16 +41,25 @@ def target_tensors(tgt, device="cuda"):
             torch.from_numpy(np.ascontiguousarray(tgt.N, np.float32)).to(device))
 
 
+# Compositing knobs (lgs_tuning) and tile shape the benchmark runs with: the
+# 200k-surfel 128 x 1024 street frame renders fastest with 8 x 8 tiles, the
+# forward staged in 64-record shared-memory batches and the backward as an
+# independent walk per warp.
+DEFAULT_TUNING = dict(fwd_batch=64, bwd_batch=0, group=1, persistent=0)
+DEFAULT_TILE = (8, 8)
+
+
 class Rasterizer:
     """Renders ``frames`` (scenes.Frame) of one or more maps; frame f shows
     map ``frame_map[f]``.  Holds the forward outputs and upstream-gradient
     planes of the last call."""
 
-    def __init__(self, frames, frame_map=None, device: int = 0, batch: int = 256, persistent: int = 0,
-                 loss: LossParams | None = None, hbm_budget_bytes: int = 0, pairs_per_item: float = 4.0):
+    def __init__(self, frames, frame_map=None, device: int = 0, loss: LossParams | None = None,
+                 hbm_budget_bytes: int = 0, pairs_per_item: float = 4.0, tuning: dict | None = None):
         self.device = torch.device("cuda", device)
         self.session = lib.Session(device, hbm_budget_bytes, pairs_per_item=pairs_per_item)
-        lib.lgs_session_set_tuning(self.session.handle, batch, persistent)
+        self.tuning = dict(DEFAULT_TUNING, **(tuning or {}))
+        lib.lgs_session_set_tuning(self.session.handle, **self.tuning)
         self.loss_params = loss or LossParams()
         self.set_frames(frames, frame_map)
 

@@ -13,7 +13,7 @@ def to_dev(surf):
             for a in (surf.mean, surf.quat, surf.log_scale, surf.logit)]
 
 
-def run(maps, frames, targets=None, frame_map=None, batch=256, persistent=0, read_bins=False, loss=LOSS,
+def run(maps, frames, targets=None, frame_map=None, tuning=None, read_bins=False, loss=LOSS,
         grads_init=None, session=None, repeat_fwd=1):
     """maps: list of scenes.Surfels; frames: list of scenes.Frame; targets:
     list of scenes.Target (or None for forward only)."""
@@ -24,7 +24,7 @@ def run(maps, frames, targets=None, frame_map=None, batch=256, persistent=0, rea
     fr = [lib.frame_struct(f) for f in frames]
     fm = list(frame_map) if frame_map is not None else [0] * len(frames)
     sess = session or lib.Session()
-    lib.lgs_session_set_tuning(sess.handle, batch, persistent)
+    lib.lgs_session_set_tuning(sess.handle, **(tuning or {}))
     sess.bin_sort(S, fr, fm)
     stream = torch.cuda.current_stream().cuda_stream
     outs = [lib.alloc_fwd(f, dev) for f in frames]

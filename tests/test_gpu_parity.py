@@ -215,16 +215,26 @@ def test_loss_and_backward_parity(oracle, name, surf, frame, tgt):
     assert_grads(compare_grads(g["grads"][0], og))
 
 
-def test_tile_shape_and_batch_do_not_change_results(oracle):
-    surf, frame, _ = scenes.box_room()
+TUNINGS = ([dict(fwd_batch=0, bwd_batch=0, group=g, persistent=p) for g in (1, 2, 4) for p in (0, 1)]
+           + [dict(fwd_batch=b, bwd_batch=min(b, 256), group=1, persistent=p) for b in (64, 128, 256, 512)
+              for p in (0, 1)])
+
+
+def test_tuning_and_tile_shape_do_not_change_results(oracle):
+    """Every compositing variant and tile shape gives bit-identical forward
+    outputs and loss; gradients agree up to the order of the float atomics."""
+    surf, frame, tgt = scenes.box_room()
     from tests import _gpu
-    ref = _gpu.run([surf], [frame])["fwd"][0]
+    ref = _gpu.run([surf], [frame], targets=[tgt])
+    gref = [np.asarray(x, np.float64) for x in ref["grads"][0]]
     for tile in ((8, 8), (16, 16), (8, 32), (32, 8)):
-        for batch in (64, 128, 256, 512):
-            for pers in (0, 1):
-                g = _gpu.run([surf], [frame.with_tiles(*tile)], batch=batch, persistent=pers)["fwd"][0]
-                for k in ("A", "S_t", "S_n", "T_final"):
-                    assert np.array_equal(g[k], ref[k]), (tile, batch, pers, k)
+        for tun in TUNINGS:
+            g = _gpu.run([surf], [frame.with_tiles(*tile)], targets=[tgt], tuning=tun)
+            for k in ("A", "S_t", "S_n", "T_final"):
+                assert np.array_equal(g["fwd"][0][k], ref["fwd"][0][k]), (tile, tun, k)
+            assert np.array_equal(g["loss"], ref["loss"]), (tile, tun)
+            for a, b in zip(g["grads"][0], gref):
+                assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max()), (tile, tun)
 
 
 def test_multi_frame_multi_map_batch(oracle):
@@ -316,10 +326,12 @@ def test_invalid_arguments_are_rejected():
 
 def test_full_size_street_frame(oracle):
     """The 200k-surfel 128 x 1024 street frame in the launch configuration the
-    benchmark times (16 x 16 tiles, batch 256): bit-exact bins; forward, loss
-    and gradients against the oracle run at full size."""
+    benchmark times (the renderer's default tile shape and tuning): bit-exact
+    bins; forward, loss and gradients against the oracle run at full size."""
+    from paper_2607_04127_gb300 import render
     from tests import _gpu
     surf, frame, tgt = scenes.street()
+    frame = frame.with_tiles(*render.DEFAULT_TILE)
     g = _gpu.run([surf], [frame], targets=[tgt], read_bins=True)
     tp, ip, rg, dk = g["bins"]
     o = oracle.bin_frame(surf, frame)
