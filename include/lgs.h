@@ -274,7 +274,7 @@ LGS_API lgs_status lgs_loss_batch(lgs_session s, const lgs_surfels* maps, int n_
                           float* loss_out, void* stream);
 
 /* Set the compositing knobs of a session (defaults: fwd_batch 64, bwd_batch 0,
- * group 1, persistent 0).  Every choice gives bit-identical forward outputs. */
+ * group 2, persistent 0).  Every choice gives bit-identical forward outputs. */
 LGS_API lgs_status lgs_session_set_tuning(lgs_session s, const lgs_tuning* t);
 
 /* One Adam step over the n surfels' 10 parameters (optimiser of the mapping

@@ -32,7 +32,7 @@ struct lgs_session_s {
   size_t g13_zero_off = 0;      // g13 region known to be all-zero
   int64_t g13_zero_items = -1;
   cudaStream_t last_stream = nullptr;
-  lgs_tuning tune{64, 0, 1, 0};
+  lgs_tuning tune{64, 0, 2, 0};
   Status* h_status = nullptr;   // pinned
   int64_t launches = 0;         // kernels enqueued by this session
 };

@@ -9,12 +9,18 @@ namespace lgs {
 
 // ---------------------------------------------------------------------------
 // Preprocess backward: for every surfel, sum over the frames that render its
-// map the per-item gradient of the backward (dL/dn and dL/dt_u, dL/dt_v at a
-// fixed centre, the coefficients of dL/dmu along n, t_u, t_v, dL/dalpha and
-// dL/dlog s), chained through
-//   mu = R^T (mean - o), [t_u t_v n] = R^T R(q/|q|), alpha = sigmoid(logit),
-// then ACCUMULATE into the caller's gradient arrays.  The per-item gradient
-// buffer is zeroed as it is read, so it is all-zero between backward calls.
+// map the per-item gradient moments of the backward (see the layout in the
+// compositing kernels), form the sensor-frame gradients of one item
+//   dL/dmu  = (sum ct) n + (sum u g / s_u) t_u + (sum v g / s_v) t_v
+//   dL/dt_u = -(sum u^2 g) t_u - (s_v / s_u)(sum u v g) t_v
+//   dL/dt_v = -(s_u / s_v)(sum u v g) t_u - (sum v^2 g) t_v
+//   dL/dn   = -s_u (sum ct u) t_u - s_v (sum ct v) t_v + sum w sg gS_n
+//   dL/dlog s_u = sum u^2 g,  dL/dlog s_v = sum v^2 g,  dL/dlogit = (1 - alpha) sum g
+// (t_u, t_v, n the unit axes; the axes enter at a fixed centre, and the
+// intersection offset inside the plane is u s_u t_u + v s_v t_v), chain them
+// through mu = R^T (mean - o), [t_u t_v n] = R^T R(q/|q|), then ACCUMULATE
+// into the caller's gradient arrays.  The per-item buffer is zeroed as it is
+// read, so it is all-zero between backward calls.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int map_of_surfel(const Desc& D, int64_t s) {
   int lo = 0, hi = D.n_maps - 1;
@@ -40,21 +46,22 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__
   const float c1[3] = {2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x)};
   const float c2[3] = {2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y)};
   const float alpha = 1.0f / (1.0f + expf(-M.logit[i]));
+  const float su = expf(M.ls[2 * i]), sv = expf(M.ls[2 * i + 1]);
   float gm[3] = {0.f, 0.f, 0.f}, G0[3] = {0.f, 0.f, 0.f}, G1[3] = {0.f, 0.f, 0.f}, G2[3] = {0.f, 0.f, 0.f};
-  float gls0 = 0.f, gls1 = 0.f, galpha = 0.f;
+  float gls0 = 0.f, gls1 = 0.f, gsum = 0.f;
   bool any = false;
   for (int f = 0; f < D->n_frames; ++f) {
     const FrameDev& F = D->f[f];
     if (F.map != m) continue;
     float4* gp = reinterpret_cast<float4*>(g13 + 16 * (F.item_base + i));
-    const float4 a = gp[0], b = gp[1], c = gp[2], d = gp[3];
+    const float4 a = gp[0], b = gp[1], c = gp[2];
     if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f && b.x == 0.f && b.y == 0.f && b.z == 0.f &&
-        b.w == 0.f && c.x == 0.f && c.y == 0.f && c.z == 0.f && c.w == 0.f && d.x == 0.f && d.y == 0.f &&
-        d.z == 0.f)
+        b.w == 0.f && c.x == 0.f && c.y == 0.f && c.z == 0.f && c.w == 0.f)
       continue;
     any = true;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    gp[0] = zero; gp[1] = zero; gp[2] = zero; gp[3] = zero;
+    gp[0] = zero; gp[1] = zero; gp[2] = zero;
+    // moments: a = (g, u g, v g, u^2 g), b = (v^2 g, u v g, ct, ct u), c = (ct v, w sg gS_n)
     const float* R = F.R;
     // sensor-frame axes: v_s = R^T v_w
     float tu[3], tv[3], n[3];
@@ -64,18 +71,22 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__
       tv[k] = R[k] * c1[0] + R[3 + k] * c1[1] + R[6 + k] * c1[2];
       n[k] = R[k] * c2[0] + R[3 + k] * c2[1] + R[6 + k] * c2[2];
     }
-    // per-item components (see k_bwd): dL/dn, c_n, dL/dt_u, c_u, dL/dt_v, c_v,
-    // dL/dalpha, dL/dlog s_u, dL/dlog s_v -- already free of cancelling terms
-    const float gnn[3] = {a.x, a.y, a.z};
-    const float gtu[3] = {b.x, b.y, b.z};
-    const float gtv[3] = {c.x, c.y, c.z};
-    const float cn = a.w, cu = b.w, cv = c.w;
-    float gmu[3];
+    const float cmu_u = a.y / su, cmu_v = a.z / sv, uv = b.y;
+    const float ktu_u = -a.w, ktu_v = -(sv / su) * uv;
+    const float ktv_u = -(su / sv) * uv, ktv_v = -b.x;
+    const float kn_u = -su * b.w, kn_v = -sv * c.x;
+    float gmu[3], gtu[3], gtv[3], gnn[3];
+    const float wsn[3] = {c.y, c.z, c.w};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) gmu[k] = cn * n[k] + cu * tu[k] + cv * tv[k];
-    galpha += d.x;
-    gls0 += d.y;
-    gls1 += d.z;
+    for (int k = 0; k < 3; ++k) {
+      gmu[k] = b.z * n[k] + cmu_u * tu[k] + cmu_v * tv[k];
+      gtu[k] = ktu_u * tu[k] + ktu_v * tv[k];
+      gtv[k] = ktv_u * tu[k] + ktv_v * tv[k];
+      gnn[k] = kn_u * tu[k] + kn_v * tv[k] + wsn[k];
+    }
+    gsum += a.x;
+    gls0 += a.w;
+    gls1 += b.x;
     // back to the world frame: v_w = R v_s
 #pragma unroll
     for (int a2 = 0; a2 < 3; ++a2) {
@@ -106,7 +117,7 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__
   M.d_mean[3 * i + 2] += gm[2];
   M.d_ls[2 * i] += gls0;
   M.d_ls[2 * i + 1] += gls1;
-  M.d_logit[i] += galpha * alpha * (1.f - alpha);
+  M.d_logit[i] += gsum * (1.f - alpha);
 }
 
 cudaError_t launch_preprocess_bwd(const Layout&, const WsPtrs& w, const Desc& h, cudaStream_t s) {
@@ -122,7 +133,7 @@ cudaError_t launch_preprocess_bwd(const Layout&, const WsPtrs& w, const Desc& h,
 //   L = sum_m [ (1/F_m) sum_{f in m} L_img,f + ls L_scale,m ]
 // with masked means over M_D = [D > 0] and M_N = M_D [|N_gicp| > 0].
 // ---------------------------------------------------------------------------
-constexpr int kLossBlocks = 64;   // CTAs per frame (fixed: deterministic partial sums)
+constexpr int kLossBlocks = 256;  // CTAs per frame and map (fixed: deterministic partial sums)
 
 __device__ __forceinline__ double block_sum_d(double v, double* s_w) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -170,13 +181,31 @@ __global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, 
   }
 }
 
-__device__ __forceinline__ int2 mask_counts(const int* __restrict__ cpart, int f) {
+// |M_D|, |M_N| of frame f from the per-CTA counts; every thread of the CTA
+// calls it and receives the totals.
+__device__ __forceinline__ int2 mask_counts(const int* __restrict__ cpart, int f, int* s_i) {
   int a = 0, b = 0;
-  for (int i = 0; i < kLossBlocks; ++i) {
+  for (int i = threadIdx.x; i < kLossBlocks; i += blockDim.x) {
     a += cpart[2 * (f * kLossBlocks + i)];
     b += cpart[2 * (f * kLossBlocks + i) + 1];
   }
-  return make_int2(a, b);
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = static_cast<int>(blockDim.x >> 5);
+  __syncthreads();
+  if (lane == 0) {
+    s_i[2 * wid] = a;
+    s_i[2 * wid + 1] = b;
+  }
+  __syncthreads();
+  int ta = 0, tb = 0;
+  for (int i = 0; i < nw; ++i) {
+    ta += s_i[2 * i];
+    tb += s_i[2 * i + 1];
+  }
+  return make_int2(ta, tb);
 }
 
 // Rows y < n_frames: the image terms of frame y and its upstream gradient
@@ -188,12 +217,13 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
                                                     double* __restrict__ part, double* __restrict__ spart,
                                                     float* __restrict__ out) {
   __shared__ double s_w[8];
+  __shared__ int s_i[16];
   __shared__ bool s_last;
   if (blockIdx.y < static_cast<unsigned>(D->n_frames)) {
     const int f = blockIdx.y;
     const FrameDev& F = D->f[f];
     const int HW = F.H * F.W;
-    const int2 cnt = mask_counts(cpart, f);
+    const int2 cnt = mask_counts(cpart, f, s_i);
     const int nd = cnt.x, nn = cnt.y;
     const float scale = 1.0f / static_cast<float>(D->m[F.map].n_frames);
     const float ind = nd > 0 ? 1.0f / static_cast<float>(nd) : 0.f;
@@ -264,46 +294,51 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
     if (threadIdx.x == 0) spart[mi * kLossBlocks + blockIdx.x] = t;
   }
 
-  // last CTA: deterministic reduction of the partial sums
+  // last CTA: deterministic reduction of the partial sums (fixed order:
+  // strided per-thread sums, then the fixed block tree)
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned total = gridDim.x * gridDim.y;
     s_last = atomicAdd(&st->loss_ticket, 1u) == total - 1;
   }
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last) return;
   __threadfence();
-  st->loss_ticket = 0;
-  const volatile double* vpart = part;
-  const volatile double* vspart = spart;
-  double Lmap[LGS_MAX_MAPS];
+  if (threadIdx.x == 0) st->loss_ticket = 0;
+  double Lmap[LGS_MAX_MAPS];   // thread 0 only
   for (int m = 0; m < D->n_maps; ++m) Lmap[m] = 0.0;
   for (int f = 0; f < D->n_frames; ++f) {
-    double s0 = 0, s1 = 0, s2 = 0;
-    for (int b = 0; b < kLossBlocks; ++b) {
-      const volatile double* o = vpart + 4 * (static_cast<int64_t>(f) * kLossBlocks + b);
-      s0 += o[0];
-      s1 += o[1];
-      s2 += o[2];
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int b = threadIdx.x; b < kLossBlocks; b += blockDim.x) {
+      const double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + b);
+      a0 += __ldcg(o);
+      a1 += __ldcg(o + 1);
+      a2 += __ldcg(o + 2);
     }
-    const int2 cnt = mask_counts(cpart, f);
-    const int nd = cnt.x, nn = cnt.y;
-    const double Ld = nd ? s0 / nd : 0.0, La = nd ? s1 / nd : 0.0, Ln = nn ? s2 / nn : 0.0;
-    out[1 + 3 * f] = static_cast<float>(Ld);
-    out[2 + 3 * f] = static_cast<float>(La);
-    out[3 + 3 * f] = static_cast<float>(Ln);
-    const int m = D->f[f].map;
-    Lmap[m] += (Ld + P.lambda_alpha * La + static_cast<double>(P.lambda_n) * P.lambda_ng * Ln) / D->m[m].n_frames;
+    const double s0 = block_sum_d(a0, s_w), s1 = block_sum_d(a1, s_w), s2 = block_sum_d(a2, s_w);
+    const int2 cnt = mask_counts(cpart, f, s_i);
+    if (threadIdx.x == 0) {
+      const int nd = cnt.x, nn = cnt.y;
+      const double Ld = nd ? s0 / nd : 0.0, La = nd ? s1 / nd : 0.0, Ln = nn ? s2 / nn : 0.0;
+      out[1 + 3 * f] = static_cast<float>(Ld);
+      out[2 + 3 * f] = static_cast<float>(La);
+      out[3 + 3 * f] = static_cast<float>(Ln);
+      const int m = D->f[f].map;
+      Lmap[m] += (Ld + P.lambda_alpha * La + static_cast<double>(P.lambda_n) * P.lambda_ng * Ln) / D->m[m].n_frames;
+    }
   }
   double L = 0.0;
   for (int m = 0; m < D->n_maps; ++m) {
-    double sr = 0.0;
-    for (int b = 0; b < kLossBlocks; ++b) sr += vspart[m * kLossBlocks + b];
-    Lmap[m] += P.lambda_s * sr;
-    out[1 + 3 * D->n_frames + m] = static_cast<float>(Lmap[m]);
-    L += Lmap[m];
+    double a = 0;
+    for (int b = threadIdx.x; b < kLossBlocks; b += blockDim.x) a += __ldcg(spart + m * kLossBlocks + b);
+    const double sr = block_sum_d(a, s_w);
+    if (threadIdx.x == 0) {
+      Lmap[m] += P.lambda_s * sr;
+      out[1 + 3 * D->n_frames + m] = static_cast<float>(Lmap[m]);
+      L += Lmap[m];
+    }
   }
-  out[0] = static_cast<float>(L);
+  if (threadIdx.x == 0) out[0] = static_cast<float>(L);
 }
 
 cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,

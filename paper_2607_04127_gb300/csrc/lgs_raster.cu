@@ -23,12 +23,46 @@
 namespace lgs {
 
 constexpr int kMaxTileThreads = 256;
-// Per-item gradient components written by the backward (see k_bwd):
-//   [0..2] dL/dn at fixed centre   [3] c_n   (dL/dmu += c_n n)
-//   [4..6] dL/dt_u                 [7] c_u   (dL/dmu += c_u t_u)
-//   [8..10] dL/dt_v                [11] c_v  (dL/dmu += c_v t_v)
-//   [12] dL/dalpha                 [13] dL/dlog s_u   [14] dL/dlog s_v
-constexpr int kGrad = 15;
+// Per-item gradient moments written by the backward.  With the unclamped
+// opacity derivative g = alpha G dL/da of a contribution (0 where a is
+// clamped), its offset (u, v) in the plane, ct = (dL/dt) / (n.d) and the
+// direct normal term w sg gS_n, every surfel gradient is a fixed combination
+// of their sums over the contributions (k_preprocess_bwd forms it):
+//   [0] g  [1] u g  [2] v g  [3] u^2 g  [4] v^2 g  [5] u v g
+//   [6] ct  [7] ct u  [8] ct v  [9..11] w sg gS_n
+// because dL/du = -u g, dL/dv = -v g and the intersection offset inside the
+// plane is u s_u t_u + v s_v t_v.
+constexpr int kGrad = 12;
+
+// Reverse-order step of one valid contribution: updates the transmittance T
+// (before it) and the suffix S, and writes its 12 moments into v.
+__device__ __forceinline__ void contrib_moments(const Eval& E, const float4& r0, float gA, float gSt, float gSx,
+                                                float gSy, float gSz, float& T, float& S, float (&v)[16]) {
+  const float iom = __fdividef(1.0f, 1.0f - E.a);
+  const float Tk = T * iom;
+  const float sg = E.den > 0.f ? -1.f : 1.f;
+  const float gc = gA + gSt * E.t + sg * (gSx * r0.x + gSy * r0.y + gSz * r0.z);
+  const float w = E.a * Tk;
+  const float dLda = Tk * gc - S * iom;
+  S = fmaf(w, gc, S);
+  T = Tk;
+  const float g = E.araw < 0.99f ? E.araw * dLda : 0.f;
+  const float ug = E.u * g, vg = E.v * g;
+  const float ct = __fdividef(fmaf(w, gSt, -fmaf(ug, E.ud, vg * E.vd)), E.den);
+  const float wsg = w * sg;
+  v[0] = g;
+  v[1] = ug;
+  v[2] = vg;
+  v[3] = E.u * ug;
+  v[4] = E.v * vg;
+  v[5] = E.u * vg;
+  v[6] = ct;
+  v[7] = ct * E.u;
+  v[8] = ct * E.v;
+  v[9] = wsg * gSx;
+  v[10] = wsg * gSy;
+  v[11] = wsg * gSz;
+}
 
 struct TileCtx {
   int f;
@@ -108,7 +142,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
   const int nthr = blockDim.x;
   const int tid = threadIdx.x, wid = tid >> 5;
   uint32_t tile;
-  unsigned long long evals = 0, contrib = 0;
+  uint32_t evals = 0, contrib = 0;
   for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
     const FrameDev& F = D->f[tc.f];
@@ -168,12 +202,13 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       F.nc[tc.pix] = last;
     }
   }
+  unsigned long long ev = evals, co = contrib;
   for (int o = 16; o > 0; o >>= 1) {
-    evals += __shfl_xor_sync(0xffffffffu, evals, o);
-    contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    co += __shfl_xor_sync(0xffffffffu, co, o);
   }
-  if ((tid & 31) == 0 && evals) atomicAdd(&st->evals_fwd, evals);
-  if ((tid & 31) == 0 && contrib) atomicAdd(&st->contrib_fwd, contrib);
+  if ((tid & 31) == 0 && ev) atomicAdd(&st->evals_fwd, ev);
+  if ((tid & 31) == 0 && co) atomicAdd(&st->contrib_fwd, co);
 }
 
 // ---------------------------------------------------------------------------
@@ -227,7 +262,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
   const int gidx = 8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
   const bool writer = ((lane & 1) == 0) && gidx < kGrad;
   uint32_t tile;
-  unsigned long long evals = 0, contrib = 0;
+  uint32_t evals = 0, contrib = 0;
   for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
     const FrameDev& F = D->f[tc.f];
@@ -287,45 +322,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
           valid = e.valid;
           if (valid) {
             ++contrib;
-            const float om = 1.0f - e.a;
-            const float Tk = __fdividef(T, om);
-            const float sg = e.den > 0.f ? -1.f : 1.f;
-            const float gc = gA + gSt * e.t + sg * (gSx * r0.x + gSy * r0.y + gSz * r0.z);
-            const float w = e.a * Tk;
-            const float dLda = Tk * gc - __fdividef(S, om);
-            S = fmaf(w, gc, S);
-            T = Tk;
-            float dLdt = w * gSt;
-            const float wsg = w * sg;
-            float dLdu = 0.f, dLdv = 0.f;
-            if (e.araw < 0.99f) {
-              v[12] = dLda * e.G;
-              const float dLdq = -0.5f * dLda * alpha * e.G;
-              dLdu = 2.f * e.u * dLdq;
-              dLdv = 2.f * e.v * dLdq;
-            }
-            dLdt = fmaf(dLdu, e.ud, fmaf(dLdv, e.vd, dLdt));
-            // offset of the intersection from the centre, inside the plane:
-            // x = t d - mu = u s_u t_u + v s_v t_v with t_u = s_u a_u, t_v = s_v a_v
-            // (formed from (u, v) so that no large terms cancel)
-            const float su = s_r3[j].y, sv = s_r3[j].z;
-            const float cu = e.u * su * su, cv = e.v * sv * sv;
-            const float r1x = s_r1[j].x, r1y = s_r1[j].y, r1z = s_r1[j].z;
-            const float r2x = s_r2[j].x, r2y = s_r2[j].y, r2z = s_r2[j].z;
-            const float xx = fmaf(cu, r1x, cv * r2x), xy = fmaf(cu, r1y, cv * r2y), xz = fmaf(cu, r1z, cv * r2z);
-            const float ct = __fdividef(dLdt, e.den);
-            // dL/dn at fixed centre: w sg gS_n + (dL/dt)(mu - t d)/(n.d)
-            v[0] = fmaf(-ct, xx, wsg * gSx);
-            v[1] = fmaf(-ct, xy, wsg * gSy);
-            v[2] = fmaf(-ct, xz, wsg * gSz);
-            v[3] = ct;                                    // dL/dmu += ct n
-            const float gu = __fdividef(dLdu, su), gv = __fdividef(dLdv, sv);
-            v[4] = gu * xx; v[5] = gu * xy; v[6] = gu * xz; // dL/dt_u = (dL/du) x / s_u
-            v[7] = -gu;                                   // dL/dmu -= (dL/du) t_u / s_u
-            v[8] = gv * xx; v[9] = gv * xy; v[10] = gv * xz;
-            v[11] = -gv;
-            v[13] = -dLdu * e.u;                          // dL/dlog s_u
-            v[14] = -dLdv * e.v;
+            contrib_moments(e, r0, gA, gSt, gSx, gSy, gSz, T, S, v);
           }
         }
         if (__any_sync(0xffffffffu, valid)) {
@@ -345,12 +342,13 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       bend = b0;
     }
   }
+  unsigned long long ev = evals, co = contrib;
   for (int o = 16; o > 0; o >>= 1) {
-    evals += __shfl_xor_sync(0xffffffffu, evals, o);
-    contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    co += __shfl_xor_sync(0xffffffffu, co, o);
   }
-  if ((tid & 31) == 0 && evals) atomicAdd(&st->evals_bwd, evals);
-  if ((tid & 31) == 0 && contrib) atomicAdd(&st->contrib_bwd, contrib);
+  if ((tid & 31) == 0 && ev) atomicAdd(&st->evals_bwd, ev);
+  if ((tid & 31) == 0 && co) atomicAdd(&st->contrib_bwd, co);
 }
 
 // ---------------------------------------------------------------------------
@@ -388,7 +386,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
             int persistent) {
   const int lane = threadIdx.x & 31;
   uint32_t tile;
-  unsigned long long evals = 0, contrib = 0;
+  uint32_t evals = 0, contrib = 0;
   for (int iter = 0; next_tile(persistent, nullptr, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
     const FrameDev& F = D->f[tc.f];
@@ -462,12 +460,13 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       F.nc[tc.pix] = last;
     }
   }
+  unsigned long long ev = evals, co = contrib;
   for (int o = 16; o > 0; o >>= 1) {
-    evals += __shfl_xor_sync(0xffffffffu, evals, o);
-    contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    co += __shfl_xor_sync(0xffffffffu, co, o);
   }
-  if (lane == 0 && evals) atomicAdd(&st->evals_fwd, evals);
-  if (lane == 0 && contrib) atomicAdd(&st->contrib_fwd, contrib);
+  if (lane == 0 && ev) atomicAdd(&st->evals_fwd, ev);
+  if (lane == 0 && co) atomicAdd(&st->contrib_fwd, co);
 }
 
 template <int G>
@@ -479,7 +478,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
   const int gidx = 8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
   const bool writer = ((lane & 1) == 0) && gidx < kGrad;
   uint32_t tile;
-  unsigned long long evals = 0, contrib = 0;
+  uint32_t evals = 0, contrib = 0;
   for (int iter = 0; next_tile(persistent, nullptr, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
     const FrameDev& F = D->f[tc.f];
@@ -513,7 +512,8 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       while (m) {
         int bq[G];
         uint32_t itq[G];
-        float4 r0[G], r1[G], r2[G], r3[G];
+        float4 r0[G], r1[G], r2[G];
+        float al[G];
 #pragma unroll
         for (int q = 0; q < G; ++q) {
           bq[q] = m ? 31 - __clz(m) : -1;
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
             r0[q] = __ldg(rp);
             r1[q] = __ldg(rp + 1);
             r2[q] = __ldg(rp + 2);
-            r3[q] = __ldg(rp + 3);
+            al[q] = __ldg(reinterpret_cast<const float*>(rp + 3));
           }
         }
         Eval e[G];
@@ -532,56 +532,19 @@ __global__ void __launch_bounds__(kMaxTileThreads)
 #pragma unroll
         for (int q = 0; q < G; ++q) {
           in[q] = bq[q] >= 0 && static_cast<int>(k0 + bq[q]) < nc;
-          if (in[q]) eval_pair(r0[q], r1[q], r2[q], r3[q].x, dx, dy, dz, e[q]);
+          if (in[q]) eval_pair(r0[q], r1[q], r2[q], al[q], dx, dy, dz, e[q]);
         }
 #pragma unroll
         for (int q = 0; q < G; ++q) {
           if (bq[q] < 0) break;
+          const bool valid = in[q] && e[q].valid;
+          evals += in[q];
           float v[16];
 #pragma unroll
           for (int c = 0; c < 16; ++c) v[c] = 0.f;
-          const bool valid = in[q] && e[q].valid;
-          if (in[q]) ++evals;
           if (valid) {
             ++contrib;
-            const Eval& E = e[q];
-            const float alpha = r3[q].x;
-            const float om = 1.0f - E.a;
-            const float Tk = __fdividef(T, om);
-            const float sg = E.den > 0.f ? -1.f : 1.f;
-            const float gc = gA + gSt * E.t + sg * (gSx * r0[q].x + gSy * r0[q].y + gSz * r0[q].z);
-            const float w = E.a * Tk;
-            const float dLda = Tk * gc - __fdividef(S, om);
-            S = fmaf(w, gc, S);
-            T = Tk;
-            float dLdt = w * gSt;
-            const float wsg = w * sg;
-            float dLdu = 0.f, dLdv = 0.f;
-            if (E.araw < 0.99f) {
-              v[12] = dLda * E.G;
-              const float dLdq = -0.5f * dLda * alpha * E.G;
-              dLdu = 2.f * E.u * dLdq;
-              dLdv = 2.f * E.v * dLdq;
-            }
-            dLdt = fmaf(dLdu, E.ud, fmaf(dLdv, E.vd, dLdt));
-            // x = t d - mu = u s_u t_u + v s_v t_v, formed from (u, v)
-            const float su = r3[q].y, sv = r3[q].z;
-            const float cu = E.u * su * su, cv = E.v * sv * sv;
-            const float xx = fmaf(cu, r1[q].x, cv * r2[q].x);
-            const float xy = fmaf(cu, r1[q].y, cv * r2[q].y);
-            const float xz = fmaf(cu, r1[q].z, cv * r2[q].z);
-            const float ct = __fdividef(dLdt, E.den);
-            v[0] = fmaf(-ct, xx, wsg * gSx);
-            v[1] = fmaf(-ct, xy, wsg * gSy);
-            v[2] = fmaf(-ct, xz, wsg * gSz);
-            v[3] = ct;
-            const float gu = __fdividef(dLdu, su), gv = __fdividef(dLdv, sv);
-            v[4] = gu * xx; v[5] = gu * xy; v[6] = gu * xz;
-            v[7] = -gu;
-            v[8] = gv * xx; v[9] = gv * xy; v[10] = gv * xz;
-            v[11] = -gv;
-            v[13] = -dLdu * E.u;
-            v[14] = -dLdv * E.v;
+            contrib_moments(e[q], r0[q], gA, gSt, gSx, gSy, gSz, T, S, v);
           }
           if (__any_sync(0xffffffffu, valid)) {
             warp_reduce16(v, lane);
@@ -591,12 +554,13 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       }
     }
   }
+  unsigned long long ev = evals, co = contrib;
   for (int o = 16; o > 0; o >>= 1) {
-    evals += __shfl_xor_sync(0xffffffffu, evals, o);
-    contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    co += __shfl_xor_sync(0xffffffffu, co, o);
   }
-  if (lane == 0 && evals) atomicAdd(&st->evals_bwd, evals);
-  if (lane == 0 && contrib) atomicAdd(&st->contrib_bwd, contrib);
+  if (lane == 0 && ev) atomicAdd(&st->evals_bwd, ev);
+  if (lane == 0 && co) atomicAdd(&st->contrib_bwd, co);
 }
 
 // ---------------------------------------------------------------------------

@@ -262,7 +262,7 @@ def lgs_loss(h, surfels, frames, fwd, targets, params, grads_out, grad, loss_out
                            _ref(grad) if grad is not None else None, P(loss_out_ptr), P(stream)))
 
 
-def lgs_session_set_tuning(h, fwd_batch: int = 64, bwd_batch: int = 0, group: int = 1, persistent: int = 0):
+def lgs_session_set_tuning(h, fwd_batch: int = 64, bwd_batch: int = 0, group: int = 2, persistent: int = 0):
     _check(load().lgs_session_set_tuning(h, _ref(lgs_tuning(fwd_batch, bwd_batch, group, persistent))))
 
 
