@@ -31,8 +31,13 @@ METRIC = "fwd+bwd rays/s at 200k surfels, 128x1024"
 UNIT = "rays/s"
 WORKLOAD = dict(workload="street 200k surfels, 128x1024 range image, +-45 deg", surfels=200_000,
                 H=128, W=1024, frames=1, loss="depth L1 + 0.1 opacity BCE + 0.05 normal cosine + 10 scale")
-# FP32 operations per ray/surfel evaluation and per composited pair (FMA = 2),
-# counted from the definition (see the design notes).
+# FP32 operations (FMA = 2) counted from the definition: an evaluation forms
+# three dot products with the ray (n.d, a_u.d, a_v.d: 15), t = h/den (1),
+# u, v (4), q (3), exp(-q/2) (2) and alpha G (1) plus the clamp (1) = 27; a
+# composited pair adds T(1-a), w, A, S_t and the flipped normal sum (12); the
+# reverse step of a contributing pair (dL/da through T and the suffix, and the
+# chain to h, n, a_u, b_u, a_v, b_v, alpha as the reverse mode of the
+# evaluation) costs 70.
 FLOP_EVAL = 27
 FLOP_COMPOSITE = 12
 FLOP_BWD_VALID = 70
@@ -42,7 +47,7 @@ PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x lanes x FMA x max c
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", default=None, help="tile shape HxW (default: the renderer's)")
@@ -53,6 +58,29 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernel's sources changed since that capture."""
+    import hashlib
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    m = hashlib.sha256()
+    for p in d["sources"]:
+        try:
+            m.update(open(os.path.join(ROOT, p), "rb").read())
+        except OSError:
+            return None
+    return d["dram_bytes_per_launch"] if m.hexdigest()[:16] == d["sources_sha256_16"] else None
+
+
+def kname(tuning, which):
+    b = tuning["fwd_batch" if which == "fwd" else "bwd_batch"]
+    base = "k_fwd" if which == "fwd" else "k_bwd"
+    return f"{base}_w<{tuning['group']}>" if b == 0 else f"{base}<{b}>"
 
 
 def dist_env():
@@ -114,7 +142,7 @@ class Clocks:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -230,14 +258,31 @@ def run_ours(args):
     rays = frame.H * frame.W
     value = world * args.steps * rays / total_s
 
-    # algorithmic work of one step (counters are cumulative since the last bin_sort)
+    # algorithmic work of one step (counters are cumulative since the last
+    # bin_sort): forward = list entries up to each pixel's stop point, backward
+    # = entries up to each pixel's last contributor (the sum of n_contrib)
     c_last = rast.counters()
     evf, evb = c_last["evals_fwd"], c_last["evals_bwd"]
     cf, cb_ = c_last["contrib_fwd"], c_last["contrib_bwd"]
-    fl_fwd = FLOP_EVAL * evf + FLOP_COMPOSITE * cf
-    fl_bwd = FLOP_EVAL * evb + FLOP_BWD_VALID * cb_
-    fwd_s = statistics.mean(fwd_ms) / 1e3
-    bwd_s = statistics.mean(bwd_ms) / 1e3
+    alg_f = c_last["alg_fwd"]
+    alg_b = int(rast.out[0].n_contrib.sum().item())
+    fl_fwd = FLOP_EVAL * alg_f + FLOP_COMPOSITE * cf
+    fl_bwd = FLOP_EVAL * alg_b + FLOP_BWD_VALID * cb_
+
+    # device time of every kernel group, from events the library records
+    # around its own launches on this stream (a separate pass of the same steps)
+    k_steps = min(args.steps, 20)
+    rast.set_timing(True)
+    for _ in range(k_steps):
+        flush.zero_()
+        S = rast.bin_sort([params], check=False)
+        rast.forward([params], S)
+        rast.loss([params], targets, grads[0:1], S)
+        rast.backward([params], grads, S=S)
+    kt = rast.kernel_times()
+    rast.set_timing(False)
+    kernels_ms = {g: (ms / n if n else 0.0) for g, (ms, n) in kt.items()}
+    fwd_s, bwd_s = kernels_ms["fwd"] / 1e3, kernels_ms["bwd"] / 1e3
     dominant = "bwd" if bwd_s >= fwd_s else "fwd"
     achieved = (fl_bwd / bwd_s if dominant == "bwd" else fl_fwd / fwd_s) / 1e12
     launches_per_step = (c1["launches"] - c0["launches"]) / args.steps
@@ -284,13 +329,16 @@ def run_ours(args):
         dtype="f32", data="synthetic (seeded street scene, see scenes.street)",
         config=dict(WORKLOAD, parallelism=f"replicas x{world}", tile=f"{tile[0]}x{tile[1]}", **rast.tuning,
                     l2="flushed between steps (256 MB write); per-step CUDA events, flush not timed"),
-        evals_per_s=world * args.steps * (evf + evb) / total_s,
+        evals_per_s=world * args.steps * (alg_f + alg_b) / total_s,
         stages_ms=dict(bin_sort=statistics.mean(bin_ms), fwd=statistics.mean(fwd_ms),
                        loss=statistics.mean(loss_ms), bwd=statistics.mean(bwd_ms)),
-        work=dict(pairs=c_last["n_pairs"], visible_items=c_last["n_visible"], evals_fwd=evf, evals_bwd=evb,
-                  composited_fwd=cf, valid_bwd=cb_),
-        roofline=dict(bound="alu", kernel="k_bwd" if dominant == "bwd" else "k_fwd", achieved=achieved,
-                      peak=PEAK_FP32_TFLOPS, unit="TFLOP/s", frac=achieved / PEAK_FP32_TFLOPS, traffic=None,
+        kernels_ms=kernels_ms,
+        work=dict(pairs=c_last["n_pairs"], visible_items=c_last["n_visible"], alg_evals_fwd=alg_f,
+                  alg_evals_bwd=alg_b, culled_evals_fwd=evf, culled_evals_bwd=evb, composited_fwd=cf,
+                  valid_bwd=cb_),
+        roofline=dict(bound="alu", kernel=kname(rast.tuning, dominant), achieved=achieved,
+                      peak=PEAK_FP32_TFLOPS, unit="TFLOP/s", frac=achieved / PEAK_FP32_TFLOPS,
+                      traffic=measured_traffic(kname(rast.tuning, dominant)),
                       peak_source="derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz"),
         e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
         gpu_launches=int(round(launches_per_step * args.steps)),

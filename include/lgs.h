@@ -198,8 +198,31 @@ LGS_API lgs_status lgs_session_pair_count(lgs_session s, int64_t* n_pairs);
  * the forward calls since that bin_sort, out[3] the same for the backward,
  * out[4] composited pairs of the forward calls, out[5] valid pairs the
  * backward re-evaluated, out[6] CUDA kernels this session has enqueued since
- * it was created, out[7] reserved (0). */
+ * it was created, out[7] the forward's algorithmic evaluations: per pixel,
+ * the tile-list entries up to and including its stop point (the whole list
+ * when it never stops), summed over the forward calls since that bin_sort. */
 LGS_API lgs_status lgs_session_counters(lgs_session s, int64_t out[8]);
+
+/* Kernel groups timed by lgs_session_set_timing. */
+enum {
+    LGS_TIME_DESC = 0,       /* descriptor copies */
+    LGS_TIME_BIN = 1,        /* lgs_bin_sort: preprocess, bucket scan, emission, per-tile sort */
+    LGS_TIME_FWD = 2,        /* forward compositing kernel */
+    LGS_TIME_LOSS = 3,       /* loss kernels */
+    LGS_TIME_BWD = 4,        /* backward compositing kernel */
+    LGS_TIME_BWD_CHAIN = 5,  /* chain of the per-item moments to the surfel parameters */
+    LGS_TIME_GROUPS = 8
+};
+
+/* enable != 0: from now on, every kernel group this session enqueues outside
+ * a stream capture is bracketed by CUDA events on its stream (a few
+ * microseconds of overhead per call).  enable == 0 stops and discards. */
+LGS_API lgs_status lgs_session_set_timing(lgs_session s, int enable);
+
+/* Synchronise on the recorded events and return, per group, the summed
+ * device milliseconds and the number of timed calls since the last read
+ * (then forget them).  Arrays of LGS_TIME_GROUPS entries; either may be NULL. */
+LGS_API lgs_status lgs_session_kernel_times(lgs_session s, double* ms, int64_t* calls);
 
 /* Device pointers into the workspace describing the last bin_sort, valid
  * until the next one: tile_of_pair[P] (global tile id, frame f's tiles start

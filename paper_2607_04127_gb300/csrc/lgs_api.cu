@@ -2,6 +2,8 @@
 // argument validation and the launch sequence of every entry point.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -35,6 +37,14 @@ struct lgs_session_s {
   lgs_tuning tune{64, 0, 2, 0};
   Status* h_status = nullptr;   // pinned
   int64_t launches = 0;         // kernels enqueued by this session
+  // optional device timing of kernel groups
+  struct Timed {
+    int group;
+    cudaEvent_t a, b;
+  };
+  bool timing = false;
+  std::vector<Timed> timed;
+  std::vector<cudaEvent_t> ev_pool;
 };
 
 namespace {
@@ -215,6 +225,41 @@ int64_t fit_pairs(size_t bytes, const Plan& p) {
   return lo;
 }
 
+cudaEvent_t take_event(lgs_session s) {
+  if (!s->ev_pool.empty()) {
+    cudaEvent_t e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Runs launch() between two events on cs when timing is on and cs is not
+// capturing.
+template <class F>
+cudaError_t timed(lgs_session s, int group, cudaStream_t cs, F launch) {
+  if (!s->timing) return launch();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(cs, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return launch();
+  cudaEvent_t a = take_event(s), b = take_event(s);
+  if (!a || !b) return launch();
+  cudaEventRecord(a, cs);
+  const cudaError_t e = launch();
+  cudaEventRecord(b, cs);
+  s->timed.push_back({group, a, b});
+  return e;
+}
+
+void drop_timing(lgs_session s) {
+  for (auto& t : s->timed) {
+    s->ev_pool.push_back(t.a);
+    s->ev_pool.push_back(t.b);
+  }
+  s->timed.clear();
+}
+
 // Copy the descriptors to the workspace unless it already holds exactly
 // these.  Calls captured into a CUDA graph always copy (the graph must carry
 // its own copy) and make the next call copy again.
@@ -224,7 +269,8 @@ cudaError_t write_desc(lgs_session s, const Desc& d, Desc* dev, cudaStream_t cs,
   if (e != cudaSuccess) return e;
   const bool capturing = cap != cudaStreamCaptureStatusNone;
   if (!capturing && s->desc_dev_at == dev && memcmp(&d, s->desc_dev, sizeof(Desc)) == 0) return cudaSuccess;
-  if ((e = lgs::launch_write_desc(d, dev, nullptr, cs)) != cudaSuccess) return e;
+  if ((e = timed(s, LGS_TIME_DESC, cs, [&] { return lgs::launch_write_desc(d, dev, nullptr, cs); })) != cudaSuccess)
+    return e;
   ++launches;
   if (capturing) {
     s->desc_dev_at = nullptr;
@@ -378,6 +424,11 @@ lgs_status lgs_session_destroy(lgs_session s) {
     cudaSetDevice(s->device);
     cudaFreeHost(s->h_status);
   }
+  drop_timing(s);
+  if (!s->ev_pool.empty()) {
+    cudaSetDevice(s->device);
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  }
   delete s->desc;
   delete s->desc_prev;
   delete s->desc_dev;
@@ -483,7 +534,40 @@ lgs_status lgs_session_counters(lgs_session s, int64_t out[8]) {
   out[4] = static_cast<int64_t>(s->h_status->contrib_fwd);
   out[5] = static_cast<int64_t>(s->h_status->contrib_bwd);
   out[6] = s->launches;
-  out[7] = 0;
+  out[7] = static_cast<int64_t>(s->h_status->alg_fwd);
+  return LGS_OK;
+}
+
+lgs_status lgs_session_set_timing(lgs_session s, int enable) {
+  if (!s) return fail(LGS_ERR_INVALID_ARG, "session is NULL");
+  s->timing = enable != 0;
+  if (!s->timing) drop_timing(s);
+  return LGS_OK;
+}
+
+lgs_status lgs_session_kernel_times(lgs_session s, double* ms, int64_t* calls) {
+  lgs_status st = enter(s);
+  if (st != LGS_OK) return st;
+  double t[LGS_TIME_GROUPS] = {0};
+  int64_t n[LGS_TIME_GROUPS] = {0};
+  cudaError_t err = cudaSuccess;
+  for (auto& r : s->timed) {
+    float x = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&x, r.a, r.b);
+    if (e != cudaSuccess) {
+      err = e;
+      continue;
+    }
+    t[r.group] += x;
+    n[r.group] += 1;
+  }
+  drop_timing(s);
+  if (err != cudaSuccess) return cuda_fail(err, "kernel timing");
+  for (int g = 0; g < LGS_TIME_GROUPS; ++g) {
+    if (ms) ms[g] = t[g];
+    if (calls) calls[g] = n[g];
+  }
   return LGS_OK;
 }
 
@@ -551,7 +635,9 @@ lgs_status lgs_bin_sort_batch(lgs_session s, const lgs_surfels* maps, int n_maps
     s->g13_zero_off = L.g13;
   }
   if ((e = write_desc(s, *s->desc, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
-  if ((e = lgs::launch_bin(L, w, n_frames, p.n_items, p.n_tiles, cs)) != cudaSuccess) return cuda_fail(e, "bin");
+  if ((e = timed(s, LGS_TIME_BIN, cs, [&] { return lgs::launch_bin(L, w, n_frames, p.n_items, p.n_tiles, cs); })) !=
+      cudaSuccess)
+    return cuda_fail(e, "bin");
   s->launches += lgs::bin_kernel_count(p.n_tiles);
   s->lay = L;
   s->binned = true;
@@ -585,7 +671,9 @@ lgs_status lgs_render_fwd_batch(lgs_session s, const lgs_surfels* maps, int n_ma
   cudaError_t e;
   if ((e = write_desc(s, d, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
   const uint32_t* pv = w.pv;
-  if ((e = lgs::launch_raster_fwd(s->lay, w, d, pv, s->tune.fwd_batch, s->tune.group, s->tune.persistent, cs)) != cudaSuccess)
+  if ((e = timed(s, LGS_TIME_FWD, cs, [&] {
+         return lgs::launch_raster_fwd(s->lay, w, d, pv, s->tune.fwd_batch, s->tune.group, s->tune.persistent, cs);
+       })) != cudaSuccess)
     return cuda_fail(e, "raster_fwd");
   s->launches += 1;
   s->last_stream = cs;
@@ -634,9 +722,13 @@ lgs_status lgs_render_bwd_batch(lgs_session s, const lgs_surfels* maps, int n_ma
   cudaError_t e;
   if ((e = write_desc(s, d, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
   const uint32_t* pv = w.pv;
-  if ((e = lgs::launch_raster_bwd(s->lay, w, d, pv, s->tune.bwd_batch, s->tune.group, s->tune.persistent, cs)) != cudaSuccess)
+  if ((e = timed(s, LGS_TIME_BWD, cs, [&] {
+         return lgs::launch_raster_bwd(s->lay, w, d, pv, s->tune.bwd_batch, s->tune.group, s->tune.persistent, cs);
+       })) != cudaSuccess)
     return cuda_fail(e, "raster_bwd");
-  if ((e = lgs::launch_preprocess_bwd(s->lay, w, d, cs)) != cudaSuccess) return cuda_fail(e, "preprocess_bwd");
+  if ((e = timed(s, LGS_TIME_BWD_CHAIN, cs, [&] { return lgs::launch_preprocess_bwd(s->lay, w, d, cs); })) !=
+      cudaSuccess)
+    return cuda_fail(e, "preprocess_bwd");
   s->launches += 2;
   s->last_stream = cs;
   return LGS_OK;
@@ -687,7 +779,8 @@ lgs_status lgs_loss_batch(lgs_session s, const lgs_surfels* maps, int n_maps, co
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if ((e = write_desc(s, d, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
-  if ((e = lgs::launch_loss(s->lay, w, d, *params, scale_grad, loss_out, cs)) != cudaSuccess)
+  if ((e = timed(s, LGS_TIME_LOSS, cs,
+                 [&] { return lgs::launch_loss(s->lay, w, d, *params, scale_grad, loss_out, cs); })) != cudaSuccess)
     return cuda_fail(e, "loss");
   s->launches += 2;
   s->last_stream = cs;

@@ -51,6 +51,7 @@ __global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, St
     st->evals_bwd = 0;
     st->contrib_fwd = 0;
     st->contrib_bwd = 0;
+    st->alg_fwd = 0;
     st->loss_ticket = 0;
   }
   for (int i = threadIdx.x; i < F.ntr; i += blockDim.x) {

@@ -64,6 +64,7 @@ struct Status {
   unsigned long long evals_bwd;
   unsigned long long contrib_fwd;     // composited (fwd) / valid re-evaluated (bwd) pairs
   unsigned long long contrib_bwd;
+  unsigned long long alg_fwd;         // list entries up to and including each pixel's stop point
   unsigned int loss_ticket;           // loss CTAs finished (the last one reduces; self-resetting)
 };
 

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
   const int nthr = blockDim.x;
   const int tid = threadIdx.x, wid = tid >> 5;
   uint32_t tile;
-  uint32_t evals = 0, contrib = 0;
+  uint32_t evals = 0, contrib = 0, alg = 0;
   for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
     const FrameDev& F = D->f[tc.f];
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
     float dx = 0.f, dy = 0.f, dz = 0.f;
     if (tc.inside) pixel_ray(F, tc.r, tc.c, dx, dy, dz);
     float T = 1.0f, A = 0.0f, St = 0.0f, Sx = 0.0f, Sy = 0.0f, Sz = 0.0f;
-    int last = 0;
+    int last = 0, stop_at = -1;
     bool done = !tc.inside;
     for (uint32_t b0 = tc.start; b0 < tc.end; b0 += BATCH) {
       if (__syncthreads_and(done)) break;
@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
           const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.a));
           if (Tn < 1e-4f) {
             done = true;
+            stop_at = static_cast<int>(b0 - tc.start) + j + 1;
             break;
           }
           const float w = e.a * T;
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       F.Sn[2 * static_cast<int64_t>(tc.HW) + tc.pix] = Sz;
       F.Tf[tc.pix] = T;
       F.nc[tc.pix] = last;
+      alg += stop_at >= 0 ? static_cast<uint32_t>(stop_at) : tc.end - tc.start;
     }
   }
   unsigned long long ev = evals, co = contrib;
@@ -207,8 +209,11 @@ __global__ void __launch_bounds__(kMaxTileThreads)
     ev += __shfl_xor_sync(0xffffffffu, ev, o);
     co += __shfl_xor_sync(0xffffffffu, co, o);
   }
+  unsigned long long al = alg;
+  for (int o = 16; o > 0; o >>= 1) al += __shfl_xor_sync(0xffffffffu, al, o);
   if ((tid & 31) == 0 && ev) atomicAdd(&st->evals_fwd, ev);
   if ((tid & 31) == 0 && co) atomicAdd(&st->contrib_fwd, co);
+  if ((tid & 31) == 0 && al) atomicAdd(&st->alg_fwd, al);
 }
 
 // ---------------------------------------------------------------------------
@@ -386,7 +391,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
             int persistent) {
   const int lane = threadIdx.x & 31;
   uint32_t tile;
-  uint32_t evals = 0, contrib = 0;
+  uint32_t evals = 0, contrib = 0, alg = 0;
   for (int iter = 0; next_tile(persistent, nullptr, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
     const FrameDev& F = D->f[tc.f];
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
     float dx = 0.f, dy = 0.f, dz = 0.f;
     if (tc.inside) pixel_ray(F, tc.r, tc.c, dx, dy, dz);
     float T = 1.0f, A = 0.0f, St = 0.0f, Sx = 0.0f, Sy = 0.0f, Sz = 0.0f;
-    int last = 0;
+    int last = 0, stop_at = -1;
     bool done = !tc.inside;
     for (uint32_t base = tc.start; base < tc.end; base += 32) {
       if (__all_sync(0xffffffffu, done)) break;
@@ -434,6 +439,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
           const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e[q].a));
           if (Tn < 1e-4f) {
             done = true;
+            stop_at = static_cast<int>(base - tc.start) + bq[q] + 1;
             continue;
           }
           const float w = e[q].a * T;
@@ -458,6 +464,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       F.Sn[2 * static_cast<int64_t>(tc.HW) + tc.pix] = Sz;
       F.Tf[tc.pix] = T;
       F.nc[tc.pix] = last;
+      alg += stop_at >= 0 ? static_cast<uint32_t>(stop_at) : tc.end - tc.start;
     }
   }
   unsigned long long ev = evals, co = contrib;
@@ -465,8 +472,11 @@ __global__ void __launch_bounds__(kMaxTileThreads)
     ev += __shfl_xor_sync(0xffffffffu, ev, o);
     co += __shfl_xor_sync(0xffffffffu, co, o);
   }
+  unsigned long long al = alg;
+  for (int o = 16; o > 0; o >>= 1) al += __shfl_xor_sync(0xffffffffu, al, o);
   if (lane == 0 && ev) atomicAdd(&st->evals_fwd, ev);
   if (lane == 0 && co) atomicAdd(&st->contrib_fwd, co);
+  if (lane == 0 && al) atomicAdd(&st->alg_fwd, al);
 }
 
 template <int G>

@@ -74,6 +74,7 @@ EXPORTS = [
     "lgs_session_set_workspace", "lgs_session_status", "lgs_session_pair_count", "lgs_session_counters",
     "lgs_session_bins", "lgs_session_read_bins", "lgs_bin_sort", "lgs_render_fwd", "lgs_render_bwd", "lgs_loss", "lgs_bin_sort_batch",
     "lgs_render_fwd_batch", "lgs_render_bwd_batch", "lgs_loss_batch", "lgs_session_set_tuning", "lgs_adam_step",
+    "lgs_session_set_timing", "lgs_session_kernel_times",
     "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version",
 ]
 
@@ -109,6 +110,8 @@ def load():
         "lgs_render_bwd_batch": ([P, P, i32, P, P, i32, P, P, P, P], S),
         "lgs_loss_batch": ([P, P, i32, P, P, i32, P, P, P, P, P, P, P], S),
         "lgs_session_set_tuning": ([P, P], S),
+        "lgs_session_set_timing": ([P, i32], S),
+        "lgs_session_kernel_times": ([P, P, P], S),
         "lgs_adam_step": ([P, P, P, P, P, P, P, i64, i64, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            i32, P], S),
         "lgs_status_string": ([i32], ctypes.c_char_p),
@@ -198,7 +201,22 @@ def lgs_session_counters(h):
     out = (ctypes.c_int64 * 8)()
     _check(load().lgs_session_counters(h, out))
     return dict(n_pairs=out[0], n_visible=out[1], evals_fwd=out[2], evals_bwd=out[3], contrib_fwd=out[4],
-                contrib_bwd=out[5], launches=out[6])
+                contrib_bwd=out[5], launches=out[6], alg_fwd=out[7])
+
+
+TIME_GROUPS = ("desc", "bin", "fwd", "loss", "bwd", "bwd_chain")
+
+
+def lgs_session_set_timing(h, enable: bool):
+    _check(load().lgs_session_set_timing(h, 1 if enable else 0))
+
+
+def lgs_session_kernel_times(h):
+    """{group: (summed device ms, timed calls)} since the last read."""
+    ms = (ctypes.c_double * 8)()
+    n = (ctypes.c_int64 * 8)()
+    _check(load().lgs_session_kernel_times(h, ms, n))
+    return {g: (ms[i], n[i]) for i, g in enumerate(TIME_GROUPS)}
 
 
 def lgs_session_bins(h):

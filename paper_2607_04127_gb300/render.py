@@ -74,6 +74,14 @@ class Rasterizer:
         self.n_maps = max(self.frame_map) + 1
         self.loss_out = torch.zeros(1 + 3 * len(self.frames) + self.n_maps, **z)
 
+    def set_timing(self, enable: bool):
+        """Bracket every kernel group of this rasterizer with CUDA events."""
+        lib.lgs_session_set_timing(self.session.handle, enable)
+
+    def kernel_times(self):
+        """{group: (device ms summed, calls)} of the timed calls since the last read."""
+        return lib.lgs_session_kernel_times(self.session.handle)
+
     def close(self):
         self.session.close()
 
