@@ -10,9 +10,11 @@
 //                 [start, end) and its fill cursor; capacity check
 //   k_emit        every item appends (depth key << 32 | item) to the bucket
 //                 of each tile it covers (order inside a bucket arbitrary)
-//   k_tile_sort   one CTA per tile: sorts its bucket by the 64-bit key in
-//                 shared memory (bitonic network; buckets beyond 4096 entries
-//                 merge through global memory) and writes the item list
+//   k_tile_sort_merge / k_tile_sort
+//                 sort every bucket by the 64-bit key: up to 2048 keys by a
+//                 merge sort in shared memory, longer buckets by a bitonic
+//                 network (up to 4096 in shared memory, beyond that chunks
+//                 merged through global memory); then write the item list
 // The result is the order of the key (tile, depth, item): per tile, by depth,
 // ties by item index.
 #include <cuda_runtime.h>
@@ -75,14 +77,22 @@ __global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, St
 
 // Calls fn(global tile id) for every tile the item's bounding cone meets:
 // rows ascending, then the candidate column ranges of bin_col_window in order.
+// Only the tile rows that hold a pixel row of the item's pixel box (which
+// pads the cone's elevation band by a whole pixel row on each side) are
+// tested: a tile row the cone meets always holds one.
 template <class Fn>
 __device__ __forceinline__ uint32_t for_each_tile(const BinGeom& g, const FrameDev& F, const float* __restrict__ tab,
-                                                  Fn fn) {
+                                                  const float4& pbox, Fn fn) {
   const float4* ct = reinterpret_cast<const float4*>(tab + F.col_tab);
   ColWin w;
   bin_col_window(g, F, w);
+  int ra = 0, rb = F.ntr - 1;
+  if (!g.all_rows) {
+    ra = max(0, static_cast<int>(pbox.x) / F.th);
+    rb = min(F.ntr - 1, static_cast<int>(pbox.y) / F.th);
+  }
   uint32_t n = 0;
-  for (int r = 0; r < F.ntr; ++r) {
+  for (int r = ra; r <= rb; ++r) {
     if (!bin_row_hit(g, tab[F.row_tab + 2 * r], tab[F.row_tab + 2 * r + 1])) continue;
     const uint32_t rowbase = F.tile_base + static_cast<uint32_t>(r * F.ntc);
     for (int pass = 0; pass < 2; ++pass) {
@@ -97,6 +107,34 @@ __device__ __forceinline__ uint32_t for_each_tile(const BinGeom& g, const FrameD
   return n;
 }
 
+// Per-CTA tile counters in shared memory: when all of a CTA's items belong
+// to one frame with at most kAggTiles tiles, its per-tile atomics go to
+// shared memory and each tile it touched gets one global atomic (items are
+// usually stored in scan order, so a CTA touches few tiles).
+constexpr int kAggTiles = 4096;
+
+struct AggWin {
+  bool local;
+  uint32_t base, n;   // global id of the frame's tile 0, tiles of the frame
+};
+
+__device__ __forceinline__ AggWin agg_window(const Desc& D) {
+  const int64_t first = static_cast<int64_t>(blockIdx.x) * blockDim.x;
+  int64_t last = first + blockDim.x - 1;
+  if (last >= D.n_items) last = D.n_items - 1;
+  AggWin a;
+  a.local = false;
+  a.base = 0;
+  a.n = 0;
+  if (first > last) return a;
+  const int f0 = frame_of_item(D, first), f1 = frame_of_item(D, last);
+  const FrameDev& F = D.f[f0];
+  a.n = static_cast<uint32_t>(F.ntr * F.ntc);
+  a.base = F.tile_base;
+  a.local = f0 == f1 && a.n <= static_cast<uint32_t>(kAggTiles);
+  return a;
+}
+
 // ---------------------------------------------------------------------------
 // Preprocess: record + key + box per (frame, surfel) item; tile counts
 // ---------------------------------------------------------------------------
@@ -104,24 +142,35 @@ __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, 
                                                      float4* __restrict__ rec, float4* __restrict__ box,
                                                      uint32_t* __restrict__ key, uint32_t* __restrict__ cnt,
                                                      uint32_t* __restrict__ tcount, Status* __restrict__ st) {
+  __shared__ uint32_t s_cnt[kAggTiles];
   const int64_t item = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool live = item < D->n_items;
+  const AggWin aw = agg_window(*D);
+  if (aw.local) {
+    for (uint32_t t = threadIdx.x; t < aw.n; t += blockDim.x) s_cnt[t] = 0u;
+    __syncthreads();
+  }
   uint32_t c = 0;
   if (live) {
     const int f = frame_of_item(*D, item);
     const FrameDev& F = D->f[f];
     const MapDev& M = D->m[F.map];
     const int64_t i = item - F.item_base;
+    // every parameter load issued up front (the atomics below would otherwise
+    // keep the compiler from hoisting them)
+    const float4 q = reinterpret_cast<const float4*>(M.quat)[i];
+    const float ls0 = M.ls[2 * i], ls1 = M.ls[2 * i + 1], lg = M.logit[i];
     BinGeom g;
     bin_geom(M.mean + 3 * i, M.ls + 2 * i, F, g);
     key[item] = __float_as_uint(g.r);
-    c = for_each_tile(g, F, tab, [&](uint32_t t) { atomicAdd(tcount + t, 1u); });
+    const float4 pb = pixel_box(g, F);
+    box[item] = pb;
+    if (aw.local) c = for_each_tile(g, F, tab, pb, [&](uint32_t t) { atomicAdd(s_cnt + (t - aw.base), 1u); });
+    else c = for_each_tile(g, F, tab, pb, [&](uint32_t t) { atomicAdd(tcount + t, 1u); });
     cnt[item] = c;
-    box[item] = pixel_box(g, F);
 
     // compositing record (accuracy only): rotation of the unit quaternion,
     // axes to the sensor frame, activations
-    const float4 q = reinterpret_cast<const float4*>(M.quat)[i];
     const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
     // world-frame columns of R(q)
@@ -136,18 +185,23 @@ __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, 
                 tvz = R[2] * c1x + R[5] * c1y + R[8] * c1z;
     const float nx = R[0] * c2x + R[3] * c2y + R[6] * c2z, ny = R[1] * c2x + R[4] * c2y + R[7] * c2z,
                 nz = R[2] * c2x + R[5] * c2y + R[8] * c2z;
-    const float isu = expf(-M.ls[2 * i]), isv = expf(-M.ls[2 * i + 1]);
-    const float alpha = 1.0f / (1.0f + expf(-M.logit[i]));
+    const float isu = expf(-ls0), isv = expf(-ls1);
+    const float alpha = 1.0f / (1.0f + expf(-lg));
     const float mx = g.x, my = g.y, mz = g.z;
     float4* out = rec + 4 * item;
     out[0] = make_float4(nx, ny, nz, nx * mx + ny * my + nz * mz);
     out[1] = make_float4(tux * isu, tuy * isu, tuz * isu, (tux * mx + tuy * my + tuz * mz) * isu);
     out[2] = make_float4(tvx * isv, tvy * isv, tvz * isv, (tvx * mx + tvy * my + tvz * mz) * isv);
-    out[3] = make_float4(alpha, expf(M.ls[2 * i]), expf(M.ls[2 * i + 1]), 0.f);
+    out[3] = make_float4(alpha, expf(ls0), expf(ls1), 0.f);
   }
   // visible-item count, one atomic per warp
   const uint32_t vis = __ballot_sync(0xffffffffu, c > 0);
   if ((threadIdx.x & 31) == 0 && vis) atomicAdd(&st->n_vis, static_cast<unsigned int>(__popc(vis)));
+  if (aw.local) {
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < aw.n; t += blockDim.x)
+      if (s_cnt[t]) atomicAdd(tcount + aw.base + t, s_cnt[t]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -207,27 +261,63 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_emit(const Desc* __restrict__ D, const float* __restrict__ tab,
                                                const uint32_t* __restrict__ key, const uint32_t* __restrict__ cnt,
+                                               const float4* __restrict__ box,
                                                uint32_t* __restrict__ tcur, const uint2* __restrict__ ranges,
                                                Status* __restrict__ st, unsigned long long* __restrict__ pkey) {
+  __shared__ uint32_t s_cnt[kAggTiles], s_base[kAggTiles];
+  if (st->overflow) return;
   const int64_t item = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (item >= D->n_items || st->overflow) return;
-  const uint32_t c = cnt[item];
-  if (c == 0) return;
-  const int f = frame_of_item(*D, item);
-  const FrameDev& F = D->f[f];
-  const MapDev& M = D->m[F.map];
-  const int64_t i = item - F.item_base;
+  const AggWin aw = agg_window(*D);
+  uint32_t c = 0;
   BinGeom g;
-  bin_geom(M.mean + 3 * i, M.ls + 2 * i, F, g);
-  const unsigned long long k = (static_cast<unsigned long long>(key[item]) << 32) | static_cast<uint32_t>(item);
-  const uint32_t n = for_each_tile(g, F, tab, [&](uint32_t t) {
-    const uint32_t pos = atomicAdd(tcur + t, 1u);
-    // the enumeration repeats the counting pass exactly, so every slot
-    // lies inside the tile's run; a slot outside it is dropped and recorded
+  float4 pb = make_float4(0.f, 0.f, 0.f, 0.f);
+  const FrameDev* F = nullptr;
+  unsigned long long k = 0;
+  if (item < D->n_items) {
+    c = cnt[item];
+    if (c) {
+      const int f = frame_of_item(*D, item);
+      F = &D->f[f];
+      const MapDev& M = D->m[F->map];
+      const int64_t i = item - F->item_base;
+      bin_geom(M.mean + 3 * i, M.ls + 2 * i, *F, g);
+      pb = box[item];
+      k = (static_cast<unsigned long long>(key[item]) << 32) | static_cast<uint32_t>(item);
+    }
+  }
+  // the enumeration repeats the counting pass exactly, so every slot lies
+  // inside the tile's run; a slot outside it is dropped and recorded
+  const auto put = [&](uint32_t t, uint32_t pos) {
     if (pos < ranges[t].y) pkey[pos] = k;
     else st->check = 1u;
+  };
+  if (!aw.local) {
+    if (c) {
+      const uint32_t n = for_each_tile(g, *F, tab, pb, [&](uint32_t t) { put(t, atomicAdd(tcur + t, 1u)); });
+      if (n != c) st->check = 1u;
+    }
+    return;
+  }
+  // shared counters: count, reserve one run per touched tile, then fill it
+  for (uint32_t t = threadIdx.x; t < aw.n; t += blockDim.x) s_cnt[t] = 0u;
+  __syncthreads();
+  if (c) {
+    const uint32_t n = for_each_tile(g, *F, tab, pb, [&](uint32_t t) { atomicAdd(s_cnt + (t - aw.base), 1u); });
+    if (n != c) st->check = 1u;
+  }
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < aw.n; t += blockDim.x) {
+    const uint32_t m = s_cnt[t];
+    if (m) {
+      s_base[t] = atomicAdd(tcur + aw.base + t, m);
+      s_cnt[t] = 0u;
+    }
+  }
+  __syncthreads();
+  if (c) for_each_tile(g, *F, tab, pb, [&](uint32_t t) {
+    const uint32_t lt = t - aw.base;
+    put(t, s_base[lt] + atomicAdd(s_cnt + lt, 1u));
   });
-  if (n != c) st->check = 1u;
 }
 
 // ---------------------------------------------------------------------------
@@ -248,34 +338,55 @@ __device__ __forceinline__ void cas(unsigned long long* a, uint32_t i, uint32_t 
   }
 }
 
+// Comparator p of a step with stride j = 2^lj (half-cleaner) or of the
+// mirror step of a merge of blocks k = 2^(lj+1): its lower index.  For
+// strides below 64 the 32 comparators of a warp stay inside one 64-key
+// block, so those steps need only a warp barrier.
+__device__ __forceinline__ uint32_t lower_index(uint32_t p, uint32_t lj) {
+  return ((p >> lj) << (lj + 1)) | (p & ((1u << lj) - 1u));
+}
+
+// Barrier around a step of the given stride: a step that crosses warps
+// (stride >= 64) is fenced by block barriers on both sides; between two
+// warp-local steps a warp barrier suffices.
+__device__ __forceinline__ void step_sync(uint32_t stride) {
+  if (stride >= 64) __syncthreads();
+  else __syncwarp();
+}
+
 // Full sort of s[0, N) in shared memory (N a power of two <= kSortSmem).
 __device__ void smem_sort(unsigned long long* s, uint32_t N) {
-  for (uint32_t k = 2; k <= N; k <<= 1) {
-    const uint32_t hk = k >> 1;
+  for (uint32_t lk = 1; (1u << lk) <= N; ++lk) {
+    const uint32_t k = 1u << lk;
+    if ((k >> 1) >= 64) __syncthreads();
     for (uint32_t p = threadIdx.x; p < N / 2; p += blockDim.x) {
-      const uint32_t i = (p / hk) * k + (p % hk);
+      const uint32_t i = lower_index(p, lk - 1);
       cas(s, i, i ^ (k - 1));
     }
-    __syncthreads();
-    for (uint32_t j = k >> 2; j > 0; j >>= 1) {
+    step_sync(k >> 1);
+    for (int lj = static_cast<int>(lk) - 2; lj >= 0; --lj) {
+      if ((1u << lj) >= 64) __syncthreads();
       for (uint32_t p = threadIdx.x; p < N / 2; p += blockDim.x) {
-        const uint32_t i = (p / j) * 2 * j + (p % j);
-        cas(s, i, i + j);
+        const uint32_t i = lower_index(p, lj);
+        cas(s, i, i + (1u << lj));
       }
-      __syncthreads();
+      step_sync(1u << lj);
     }
   }
+  __syncthreads();
 }
 
 // Half-cleaners j = S/2 .. 1 on s[0, S) (the tail of a merge step).
 __device__ void smem_clean(unsigned long long* s, uint32_t S) {
-  for (uint32_t j = S >> 1; j > 0; j >>= 1) {
+  for (int lj = 31 - __clz(S) - 1; lj >= 0; --lj) {
+    if ((1u << lj) >= 64) __syncthreads();
     for (uint32_t p = threadIdx.x; p < S / 2; p += blockDim.x) {
-      const uint32_t i = (p / j) * 2 * j + (p % j);
-      cas(s, i, i + j);
+      const uint32_t i = lower_index(p, lj);
+      cas(s, i, i + (1u << lj));
     }
-    __syncthreads();
+    step_sync(1u << lj);
   }
+  __syncthreads();
 }
 
 __device__ void chunk_load(unsigned long long* s, const unsigned long long* g, uint32_t base, uint32_t n, uint32_t S) {
@@ -289,6 +400,101 @@ __device__ void chunk_store(const unsigned long long* s, unsigned long long* g, 
   __syncthreads();
 }
 
+// ---- buckets of at most 2048 keys: merge sort in shared memory -----------
+// Every thread sorts 8 keys in registers (a 19-comparator network), then
+// runs of 8, 16, ... keys are merged pairwise until one run remains: each
+// thread finds where its 8 outputs start in its pair of runs by a binary
+// search along the merge path (ties, which only the padding has, go to the
+// first run) and merges them sequentially.  The bucket is padded with +inf to
+// N = 8 * 2^m keys.
+constexpr int kMergeCta = 256;
+constexpr int kMergeMax = 8 * kMergeCta;   // 2048 keys
+
+__device__ __forceinline__ void cas_reg(unsigned long long& a, unsigned long long& b) {
+  const unsigned long long x = a, y = b;
+  const bool sw = x > y;
+  a = sw ? y : x;
+  b = sw ? x : y;
+}
+
+__device__ __forceinline__ void sort8(unsigned long long (&k)[8]) {
+  // Batcher's odd-even merge network for 8 inputs (19 comparators)
+  cas_reg(k[0], k[1]); cas_reg(k[2], k[3]); cas_reg(k[4], k[5]); cas_reg(k[6], k[7]);
+  cas_reg(k[0], k[2]); cas_reg(k[1], k[3]); cas_reg(k[4], k[6]); cas_reg(k[5], k[7]);
+  cas_reg(k[1], k[2]); cas_reg(k[5], k[6]);
+  cas_reg(k[0], k[4]); cas_reg(k[1], k[5]); cas_reg(k[2], k[6]); cas_reg(k[3], k[7]);
+  cas_reg(k[2], k[4]); cas_reg(k[3], k[5]);
+  cas_reg(k[1], k[2]); cas_reg(k[3], k[4]); cas_reg(k[5], k[6]);
+}
+
+// Shared-memory index of key x: one padding slot after every 8 keys, so the
+// 8-key rows of consecutive threads start in different banks.
+__device__ __forceinline__ uint32_t pad8(uint32_t x) { return x + (x >> 3); }
+
+__global__ void __launch_bounds__(kMergeCta) k_tile_sort_merge(const uint2* __restrict__ ranges,
+                                                               const Status* __restrict__ st,
+                                                               const unsigned long long* __restrict__ pkey,
+                                                               uint32_t* __restrict__ ptile,
+                                                               uint32_t* __restrict__ pv) {
+  __shared__ unsigned long long sa[kMergeMax + kMergeMax / 8], sb[kMergeMax + kMergeMax / 8];
+  if (st->overflow) return;
+  const uint32_t tile = blockIdx.x;
+  const uint2 rg = ranges[tile];
+  const uint32_t n = rg.y - rg.x;
+  if (n == 0 || n > kMergeMax) return;
+  uint32_t N = 8;
+  while (N < n) N <<= 1;
+  const unsigned long long* g = pkey + rg.x;
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) sa[pad8(i)] = i < n ? g[i] : ~0ull;
+  __syncthreads();
+  const uint32_t t = threadIdx.x;
+  const bool act = 8 * t < N;
+  if (act) {
+    unsigned long long k[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) k[r] = sa[9 * t + r];
+    sort8(k);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sa[9 * t + r] = k[r];
+  }
+  __syncthreads();
+  unsigned long long *src = sa, *dst = sb;
+  for (uint32_t L = 8; L < N; L <<= 1) {
+    if (act) {
+      const uint32_t tpp = L / 4;                  // threads per pair of runs
+      const uint32_t pair = t / tpp, d = 8 * (t % tpp);
+      const uint32_t a0 = 2 * L * pair, b0 = a0 + L;   // runs A = [a0, a0 + L), B = [b0, b0 + L)
+      // i = number of the first d outputs taken from A
+      uint32_t lo = d > L ? d - L : 0, hi = d < L ? d : L;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (src[pad8(a0 + mid)] > src[pad8(b0 + d - mid - 1)]) hi = mid;
+        else lo = mid + 1;
+      }
+      uint32_t i = lo, j = d - lo;
+      const uint32_t o = 9 * (a0 / 8 + d / 8);        // pad8 of the 8-aligned output row
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        // ties (only the +inf padding) go to A first, as in the search
+        const unsigned long long a = i < L ? src[pad8(a0 + i)] : ~0ull, b = j < L ? src[pad8(b0 + j)] : ~0ull;
+        const bool takeA = j >= L || (i < L && a <= b);
+        dst[o + r] = takeA ? a : b;
+        i += takeA;
+        j += !takeA;
+      }
+    }
+    __syncthreads();
+    unsigned long long* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    pv[rg.x + i] = static_cast<uint32_t>(src[pad8(i)]);
+    ptile[rg.x + i] = tile;
+  }
+}
+
+// ---- longer buckets: one CTA -----------------------------------------------
 __global__ void __launch_bounds__(kSortCta) k_tile_sort(const uint2* __restrict__ ranges, const Status* __restrict__ st,
                                                         unsigned long long* __restrict__ pkey,
                                                         uint32_t* __restrict__ ptile, uint32_t* __restrict__ pv) {
@@ -297,7 +503,7 @@ __global__ void __launch_bounds__(kSortCta) k_tile_sort(const uint2* __restrict_
   const uint32_t tile = blockIdx.x;
   const uint2 rg = ranges[tile];
   const uint32_t n = rg.y - rg.x;
-  if (n == 0) return;
+  if (n <= kMergeMax) return;   // k_tile_sort_merge's
   unsigned long long* g = pkey + rg.x;
   if (n <= kSortSmem) {
     uint32_t N = 2;
@@ -321,17 +527,17 @@ __global__ void __launch_bounds__(kSortCta) k_tile_sort(const uint2* __restrict_
     smem_sort(s, S);
     chunk_store(s, g, b, n, S);
   }
-  for (uint32_t k = 2 * S; k <= N; k <<= 1) {
-    const uint32_t hk = k >> 1;
+  for (uint32_t lk = 31 - __clz(2 * S); (1u << lk) <= N; ++lk) {
+    const uint32_t k = 1u << lk;
     for (uint32_t p = threadIdx.x; p < N / 2; p += blockDim.x) {
-      const uint32_t i = (p / hk) * k + (p % hk), j = i ^ (k - 1);
+      const uint32_t i = lower_index(p, lk - 1), j = i ^ (k - 1);
       if (j < n) cas(g, i, j);
     }
     __syncthreads();
-    for (uint32_t j = k >> 2; j >= S; j >>= 1) {
+    for (uint32_t lj = lk - 2; (1u << lj) >= S; --lj) {
       for (uint32_t p = threadIdx.x; p < N / 2; p += blockDim.x) {
-        const uint32_t i = (p / j) * 2 * j + (p % j);
-        if (i + j < n) cas(g, i, i + j);
+        const uint32_t i = lower_index(p, lj);
+        if (i + (1u << lj) < n) cas(g, i, i + (1u << lj));
       }
       __syncthreads();
     }
@@ -351,7 +557,7 @@ __global__ void __launch_bounds__(kSortCta) k_tile_sort(const uint2* __restrict_
 // Orchestration
 // ---------------------------------------------------------------------------
 // kernels launch_bin enqueues (memsets not counted)
-int bin_kernel_count(uint32_t) { return 5; }
+int bin_kernel_count(uint32_t) { return 6; }
 
 cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n_items, uint32_t n_tiles,
                        cudaStream_t s) {
@@ -364,8 +570,11 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
   k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tcur, w.st);
   k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap);
-  k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.tcur, w.ranges, w.st, w.pkey);
-  if (n_tiles > 0) k_tile_sort<<<n_tiles, kSortCta, 0, s>>>(w.ranges, w.st, w.pkey, w.ptile, w.pv);
+  k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.box, w.tcur, w.ranges, w.st, w.pkey);
+  if (n_tiles > 0) {
+    k_tile_sort_merge<<<n_tiles, kMergeCta, 0, s>>>(w.ranges, w.st, w.pkey, w.ptile, w.pv);
+    k_tile_sort<<<n_tiles, kSortCta, 0, s>>>(w.ranges, w.st, w.pkey, w.ptile, w.pv);
+  }
   return cudaGetLastError();
 }
 

@@ -279,8 +279,9 @@ __device__ __forceinline__ void bin_col_window(const BinGeom& g, const FrameDev&
 
 // Conservative pixel-space box of the bounding cone: rows [x, y] (floats),
 // columns as a circular centre z and half-width w, padded by one pixel.  It
-// only lets a warp skip records that cannot pass the cut-off at any of its
-// pixels; results never depend on it.
+// only prunes searches (a warp skips records that cannot pass the cut-off at
+// any of its pixels; the binning tests only the tile rows it spans); results
+// never depend on it.
 __device__ __forceinline__ float4 pixel_box(const BinGeom& g, const FrameDev& F) {
   float r_lo = 0.f, r_hi = static_cast<float>(F.H - 1);
   if (!g.all_rows) {

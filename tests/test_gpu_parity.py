@@ -278,6 +278,32 @@ def test_gradients_accumulate(oracle):
         assert np.allclose(a, 2 * b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
 
 
+@pytest.mark.parametrize("n,lo,hi", [(5000, 2048, 4096), (12000, 4096, 1 << 30)])
+def test_long_tile_bucket_bit_exact(oracle, n, lo, hi):
+    """Buckets beyond the merge sort's 2048 keys take the shared-memory
+    bitonic network (up to 4096) or its chunked path through global memory
+    (beyond): bins stay bit-exact and the forward matches the oracle."""
+    from tests import _gpu
+    rng = np.random.default_rng(11)
+    frame = scenes.Frame(32, 512, 16, 16, -0.26, 0.26)
+    az = 0.3 + rng.uniform(-0.035, 0.035, n)
+    el = rng.uniform(-0.035, 0.035, n)
+    r = rng.uniform(6.0, 12.0, n)
+    mean = np.stack([r * np.cos(el) * np.cos(az), r * np.cos(el) * np.sin(az), r * np.sin(el)], 1)
+    surf = scenes.Surfels(mean.astype(np.float32), rng.normal(size=(n, 4)).astype(np.float32),
+                          np.log(rng.uniform(0.005, 0.02, (n, 2))).astype(np.float32),
+                          rng.normal(size=n).astype(np.float32))
+    g = _gpu.run([surf], [frame], read_bins=True)
+    tp, ip, rg, dk = g["bins"]
+    o = oracle.bin_frame(surf, frame)
+    assert lo < (o["ranges"][:, 1] - o["ranges"][:, 0]).max() <= hi
+    keys = (tp.astype(np.uint64) << np.uint64(32)) | dk[ip].astype(np.uint64)
+    assert np.array_equal(keys, o["keys"]) and np.array_equal(ip, o["vals"])
+    assert np.array_equal(rg.astype(np.int64), o["ranges"])
+    of = oracle.render_fwd(surf, frame, o["ranges"], o["vals"])
+    assert_forward(compare_forward(g["fwd"][0], of))
+
+
 def test_empty_and_invisible_maps(oracle):
     from tests import _gpu
     frame = scenes.Frame(32, 64, 16, 16, -0.2, 0.2)
