@@ -253,3 +253,19 @@ def forward_backward(surfels, frames, targets, lam_alpha=LAMBDA_ALPHA, lam_n=LAM
     ls = params64[2] if params64 is not None else surfels.log_scale
     L += scale_reg(ls, s_max, lam_s, grads["log_scale"])
     return L, fwds, grads, bins
+
+
+def adam(p, g, m, v, step: int, lr, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15):
+    """One Adam step in FP64 (Kingma and Ba, ICLR 2015, Algorithm 1).  The
+    paper optimises the map (Sec. 3.4) without naming its optimiser; the
+    mapping loop here uses Adam with per-parameter-group learning rates.
+      m <- beta1 m + (1 - beta1) g,   v <- beta2 v + (1 - beta2) g^2,
+      p <- p - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps)
+    with t = ``step`` >= 1.  Returns the new (p, m, v) as float64 arrays."""
+    p = np.asarray(p, np.float64)
+    g = np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** step)
+    vhat = v / (1.0 - beta2 ** step)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v

@@ -433,3 +433,32 @@ def test_p6_gradient_with_clamped_opacity(oracle):
                 assert abs(gl[which][idx] - fd) <= 2e-5 * scale + 1e-9, (which, idx, gl[which][idx], fd)
                 used += 1
     assert used >= 25
+
+
+# --------------------------------------------------------------------------
+# Adam of the mapping loop: closed forms
+# --------------------------------------------------------------------------
+def test_adam_first_step_is_signed_learning_rate(oracle):
+    """At t = 1 the bias corrections give mhat = g, vhat = g^2, so every
+    parameter moves by lr g / (|g| + eps): -lr sign(g) for |g| >> eps."""
+    rng = np.random.default_rng(3)
+    p0 = rng.normal(size=50)
+    g = rng.normal(size=50) * 10.0 ** rng.uniform(-6, 2, 50)
+    p1, m, v = oracle.adam(p0, g, np.zeros(50), np.zeros(50), 1, 1e-3)
+    assert np.allclose(p1, p0 - 1e-3 * g / (np.abs(g) + 1e-15), rtol=0, atol=1e-15)
+    assert np.all(np.abs(p1 - (p0 - 1e-3 * np.sign(g))) <= 1e-3 * 1e-15 / np.abs(g) + 1e-15)
+    assert np.allclose(m, 0.1 * g, rtol=1e-15) and np.allclose(v, 0.001 * g * g, rtol=1e-15)
+
+
+def test_adam_constant_gradient_moves_linearly(oracle):
+    """With a constant gradient the bias-corrected moments stay g and g^2, so
+    k steps move every parameter by k lr sign(g); lr = 0 moves nothing."""
+    rng = np.random.default_rng(4)
+    p = p0 = rng.normal(size=20)
+    g = rng.normal(size=20)
+    m = v = np.zeros(20)
+    for t in range(1, 8):
+        p, m, v = oracle.adam(p, g, m, v, t, 5e-3)
+    assert np.allclose(p, p0 - 7 * 5e-3 * np.sign(g), rtol=0, atol=1e-12)
+    q, _, _ = oracle.adam(p0, g, np.zeros(20), np.zeros(20), 1, 0.0)
+    assert np.array_equal(q, p0)
