@@ -7,7 +7,8 @@
 //                 box, depth key = bits of binary32 |mu_sensor|; counts one
 //                 per covered tile (atomic per-tile counters)
 //   k_tile_scan   one CTA: exclusive scan of the tile counts -> every tile's
-//                 [start, end) and its fill cursor; capacity check
+//                 [start, end) and its fill cursor; capacity check; the
+//                 longest-first tile order of the persistent kernels
 //   k_emit        every item appends (depth key << 32 | item) to the bucket
 //                 of each tile it covers (order inside a bucket arbitrary)
 //   k_tile_sort_merge / k_tile_sort
@@ -209,13 +210,20 @@ __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, 
 // ---------------------------------------------------------------------------
 constexpr int kScanCta = 1024;
 
+// Bucket of a tile list length for the longest-first order: floor(log2(n)) + 1
+// (0 for an empty tile), reversed so that bucket 0 holds the longest lists.
+constexpr int kOrderBuckets = 33;
+__device__ __forceinline__ int order_bucket(uint32_t n) { return kOrderBuckets - 1 - (n ? 32 - __clz(n) : 0); }
+
 __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ tcur, uint32_t n_tiles,
                                                           uint2* __restrict__ ranges, Status* __restrict__ st,
-                                                          int64_t cap) {
+                                                          int64_t cap, uint32_t* __restrict__ order) {
   __shared__ unsigned long long s_w[32];
   __shared__ unsigned long long s_carry;
+  __shared__ uint32_t s_bucket[kOrderBuckets];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_carry = 0;
+  if (tid < kOrderBuckets) s_bucket[tid] = 0;
   __syncthreads();
   for (uint32_t b0 = 0; b0 < n_tiles; b0 += kScanCta) {
     const uint32_t t = b0 + tid;
@@ -253,6 +261,28 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
   if (over) {
     // nothing is emitted: every tile renders empty
     for (uint32_t t = tid; t < n_tiles; t += kScanCta) ranges[t] = make_uint2(0u, 0u);
+  }
+  // work order of the persistent kernels: tiles by list length, longest
+  // power-of-two class first (order inside a class is arbitrary; results do
+  // not depend on it).  Both passes read the final ranges.
+  __syncthreads();
+  for (uint32_t t = tid; t < n_tiles; t += kScanCta) {
+    const uint2 rg = ranges[t];
+    atomicAdd(&s_bucket[order_bucket(rg.y - rg.x)], 1u);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t acc = 0;
+    for (int b = 0; b < kOrderBuckets; ++b) {
+      const uint32_t c = s_bucket[b];
+      s_bucket[b] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  for (uint32_t t = tid; t < n_tiles; t += kScanCta) {
+    const uint2 rg = ranges[t];
+    order[atomicAdd(&s_bucket[order_bucket(rg.y - rg.x)], 1u)] = t;
   }
 }
 
@@ -569,7 +599,7 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
   const int64_t ni = n_items > 0 ? n_items : 1;
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
   k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tcur, w.st);
-  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap);
+  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work);
   k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.box, w.tcur, w.ranges, w.st, w.pkey);
   if (n_tiles > 0) {
     k_tile_sort_merge<<<n_tiles, kMergeCta, 0, s>>>(w.ranges, w.st, w.pkey, w.ptile, w.pv);

@@ -387,12 +387,12 @@ __device__ __forceinline__ Rec load_rec(const float4* __restrict__ rec, uint32_t
 template <int G>
 __global__ void __launch_bounds__(kMaxTileThreads)
     k_fwd_w(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
-            const float4* __restrict__ rec, const float4* __restrict__ box, Status* __restrict__ st,
-            int persistent) {
+            const float4* __restrict__ rec, const float4* __restrict__ box, const uint32_t* __restrict__ order,
+            Status* __restrict__ st, int persistent) {
   const int lane = threadIdx.x & 31;
   uint32_t tile;
   uint32_t evals = 0, contrib = 0, alg = 0;
-  for (int iter = 0; next_tile(persistent, nullptr, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
+  for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
     const FrameDev& F = D->f[tc.f];
     const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
@@ -483,13 +483,13 @@ template <int G>
 __global__ void __launch_bounds__(kMaxTileThreads)
     k_bwd_w(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
             const float4* __restrict__ rec, const float4* __restrict__ box, float* __restrict__ g13,
-            Status* __restrict__ st, int persistent) {
+            const uint32_t* __restrict__ order, Status* __restrict__ st, int persistent) {
   const int lane = threadIdx.x & 31;
   const int gidx = 8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
   const bool writer = ((lane & 1) == 0) && gidx < kGrad;
   uint32_t tile;
   uint32_t evals = 0, contrib = 0;
-  for (int iter = 0; next_tile(persistent, nullptr, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
+  for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
     const FrameDev& F = D->f[tc.f];
     const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
@@ -578,14 +578,15 @@ __global__ void __launch_bounds__(kMaxTileThreads)
 // ---------------------------------------------------------------------------
 template <int B>
 static cudaError_t fwd_b(const WsPtrs& w, const uint32_t* pv, const Desc& h, int persistent, int grid, cudaStream_t s) {
-  k_fwd<B><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, nullptr, w.st, persistent);
+  k_fwd<B><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, persistent ? w.work : nullptr, w.st,
+                                        persistent);
   return cudaGetLastError();
 }
 
 template <int B>
 static cudaError_t bwd_b(const WsPtrs& w, const uint32_t* pv, const Desc& h, int persistent, int grid, cudaStream_t s) {
-  k_bwd<B><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, nullptr, w.st,
-                                        persistent);
+  k_bwd<B><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, persistent ? w.work : nullptr,
+                                        w.st, persistent);
   return cudaGetLastError();
 }
 
@@ -604,11 +605,12 @@ cudaError_t launch_raster_fwd(const Layout&, const WsPtrs& w, const Desc& h, con
     if (e != cudaSuccess) return e;
   }
   const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
+  const uint32_t* ord = persistent ? w.work : nullptr;
   switch (batch) {
     case 0:
-      if (group == 1) k_fwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.st, persistent);
-      else if (group == 2) k_fwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.st, persistent);
-      else k_fwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.st, persistent);
+      if (group == 1) k_fwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
+      else if (group == 2) k_fwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
+      else k_fwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       return cudaGetLastError();
     case 64: return fwd_b<64>(w, pv, h, persistent, grid, s);
     case 128: return fwd_b<128>(w, pv, h, persistent, grid, s);
@@ -624,11 +626,12 @@ cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, con
     if (e != cudaSuccess) return e;
   }
   const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
+  const uint32_t* ord = persistent ? w.work : nullptr;
   switch (batch) {
     case 0:
-      if (group == 1) k_bwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, w.st, persistent);
-      else if (group == 2) k_bwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, w.st, persistent);
-      else k_bwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, w.st, persistent);
+      if (group == 1) k_bwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, ord, w.st, persistent);
+      else if (group == 2) k_bwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, ord, w.st, persistent);
+      else k_bwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, ord, w.st, persistent);
       return cudaGetLastError();
     case 64: return bwd_b<64>(w, pv, h, persistent, grid, s);
     case 128: return bwd_b<128>(w, pv, h, persistent, grid, s);

@@ -503,3 +503,81 @@ def targets_for(frame: Frame, surf: Surfels, seed: int = 0, drop: float = 0.1):
     N /= np.linalg.norm(N, axis=0, keepdims=True)
     N[:, rng.random((H, W)) < 0.05] = 0.0
     return Target(D, N.astype(np.float32))
+
+
+def sample_street_surfaces(scene: Scene, rng: np.random.Generator, n: int, x_range):
+    """``n`` points uniform by area on the street's surfaces with x in
+    ``x_range`` (ground, both facades, cylinder sides, box tops and sides),
+    with their true normals: a map that many viewpoints would have built."""
+    x0, x1 = x_range
+    gz, fy, ft = scene.ground_z, scene.facade_y, scene.facade_top
+    cyl = scene.cylinders[(scene.cylinders[:, 0] >= x0) & (scene.cylinders[:, 0] <= x1)]
+    box = scene.boxes[(scene.boxes[:, 0] >= x0) & (scene.boxes[:, 3] <= x1)]
+    ex = box[:, 3:] - box[:, :3]
+    parts = [("ground", 2 * fy * (x1 - x0)), ("facades", 2 * (x1 - x0) * (ft - gz)),
+             ("cyl", float((2 * np.pi * cyl[:, 2] * (cyl[:, 4] - cyl[:, 3])).sum())),
+             ("box", float((ex[:, 0] * ex[:, 1] + 2 * ex[:, 2] * (ex[:, 0] + ex[:, 1])).sum()))]
+    areas = np.array([a for _, a in parts])
+    counts = rng.multinomial(n, areas / areas.sum())
+    P, N = [], []
+    m = counts[0]
+    P.append(np.stack([rng.uniform(x0, x1, m), rng.uniform(-fy, fy, m), np.full(m, gz)], 1))
+    N.append(np.broadcast_to([0.0, 0.0, 1.0], (m, 3)))
+    m = counts[1]
+    side = rng.choice([-1.0, 1.0], m)
+    P.append(np.stack([rng.uniform(x0, x1, m), side * fy, rng.uniform(gz, ft, m)], 1))
+    N.append(np.stack([np.zeros(m), -side, np.zeros(m)], 1))
+    m = counts[2]
+    if m and len(cyl):
+        w = 2 * np.pi * cyl[:, 2] * (cyl[:, 4] - cyl[:, 3])
+        c = cyl[rng.choice(len(cyl), m, p=w / w.sum())]
+        a = rng.uniform(0, 2 * np.pi, m)
+        P.append(np.stack([c[:, 0] + c[:, 2] * np.cos(a), c[:, 1] + c[:, 2] * np.sin(a),
+                           rng.uniform(c[:, 3], c[:, 4])], 1))
+        N.append(np.stack([np.cos(a), np.sin(a), np.zeros(m)], 1))
+    m = counts[3]
+    if m and len(box):
+        fa = np.stack([ex[:, 0] * ex[:, 1], ex[:, 1] * ex[:, 2], ex[:, 1] * ex[:, 2], ex[:, 0] * ex[:, 2],
+                       ex[:, 0] * ex[:, 2]], 1)            # top, -x, +x, -y, +y
+        flat = fa.ravel() / fa.sum()
+        k = rng.choice(flat.size, m, p=flat)
+        b, f = k // 5, k % 5
+        lo, hi = box[b, :3], box[b, 3:]
+        u = rng.uniform(lo, hi)
+        nrm = np.zeros((m, 3))
+        top = f == 0
+        u[top, 2] = hi[top, 2]; nrm[top, 2] = 1.0
+        for face, axis, sgn in ((1, 0, -1.0), (2, 0, 1.0), (3, 1, -1.0), (4, 1, 1.0)):
+            sel = f == face
+            u[sel, axis] = np.where(sgn > 0, hi[sel, axis], lo[sel, axis])
+            nrm[sel, axis] = sgn
+        P.append(u)
+        N.append(nrm)
+    return np.concatenate(P), np.concatenate(N)
+
+
+def street_maps(seed: int, sizes, shapes, tile=(8, 8), spacing: float = 25.0, noise_targets: bool = True):
+    """Independent maps of uneven size along one long street (one per entry of
+    ``sizes``), each with one frame of shape ``shapes[i % len(shapes)]`` (H, W)
+    at the map's centre and its simulated target scan.  Map ``i`` holds
+    ``sizes[i]`` surfels on the street's surfaces within +-(20 + n / 25k) m
+    of its sensor, with range-adaptive scales.  Returns [(surfels, frame,
+    target)]."""
+    rng = np.random.default_rng(seed)
+    M = len(sizes)
+    xs = (np.arange(M) - (M - 1) / 2) * spacing
+    span = max(20.0 + max(sizes) / 25000.0, spacing)
+    scene = street_scene(rng, x_extent=(xs[0] - span - 10, xs[-1] + span + 10),
+                         n_boxes=int(2000 * (xs[-1] - xs[0] + 2 * span) / 120),
+                         keep_clear=[(x, 0.0) for x in xs])
+    out = []
+    for i, (n, x) in enumerate(zip(sizes, xs)):
+        H, W = shapes[i % len(shapes)]
+        half = 20.0 + n / 25000.0
+        pts, nrm = sample_street_surfaces(scene, rng, int(n), (x - half, x + half))
+        o = np.array([x, 0.0, 0.0])
+        fr = lidar_frame(H, W, tile, pose=pose_matrix(0.1 * i, (x, 0.0, 0.0)))
+        surf = surfels_from_points(pts, np.broadcast_to(o, pts.shape), rng, _kappa(fr), normals=nrm)
+        D, p, nr, v = simulate_scan(scene, fr, rng)
+        out.append((surf, fr, target_from_scan(D, p, v, true_normals=nr)))
+    return out
