@@ -1,0 +1,191 @@
+"""Serving loop for many concurrent mapping sessions (continuous batching).
+
+Every session owns one surfel map whose parameters, gradients and Adam
+moments stay resident on the device.  Clients submit render-and-optimise
+requests (one keyframe: pose + measured range image + tracking normals,
+``iters`` mapping iterations).  Sessions are admitted against an HBM budget
+(resident bytes of the map and its optimiser state plus the per-frame
+buffers); a session that does not fit is rejected.
+
+The scheduler runs ticks.  A tick takes every active request one mapping
+iteration further with ONE call per stage over all of their frames (each
+frame renders its own session's map: ``lgs_*_batch`` with a frame->map
+table), then one Adam step per map.  Requests that arrived meanwhile join at
+the next tick as slots free up (at most ``slots`` active requests, at most
+one per session: a session's keyframes update the same map and are served in
+arrival order).  A request completes after ``iters`` ticks; its latency is
+completion time minus arrival time.
+
+``plain=True`` serves the same requests one at a time with per-request
+launches (the baseline the batched form is measured against).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+import torch
+
+from . import render
+
+BYTES_PER_SURFEL = 160          # parameters, gradients, Adam m and v: 4 x 10 floats
+WORKSPACE_PER_SURFEL = 220      # record, box, keys, counters, moments, about 6 pairs (upper estimate)
+
+
+@dataclasses.dataclass
+class Request:
+    session: int
+    frame: object               # scenes.Frame (pose of the keyframe)
+    target: object              # scenes.Target
+    arrival: float              # seconds since the start of the run
+    iters: int = 10
+    done_iters: int = 0
+    start: float | None = None
+    finish: float | None = None
+    losses: list = dataclasses.field(default_factory=list)
+
+
+class MapSession:
+    def __init__(self, sid: int, surf, device):
+        self.sid = sid
+        self.params = render.map_tensors(surf, device)
+        self.grads = [torch.zeros_like(p) for p in self.params]
+        n = int(self.params[0].shape[0])
+        self.m = torch.zeros(10 * n, device=device)
+        self.v = torch.zeros(10 * n, device=device)
+        self.t = 0
+        self.n = n
+
+    @property
+    def resident_bytes(self) -> int:
+        return BYTES_PER_SURFEL * self.n
+
+
+class Server:
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 150 << 30, slots: int = 16,
+                 tuning: dict | None = None, lr=(1e-3, 1e-3, 5e-3, 5e-3), plain: bool = False):
+        self.device = torch.device("cuda", device)
+        self.budget = hbm_budget_bytes
+        self.slots = 1 if plain else slots
+        self.tuning = tuning
+        self.lr = lr
+        self.plain = plain
+        self.sessions: dict[int, MapSession] = {}
+        self.rejected_sessions: list[int] = []
+        self.used = 0
+        self.rast = None
+        self.frame_shape = None
+
+    # -- admission ----------------------------------------------------------
+    def open_session(self, sid: int, surf, frame_pixels: int) -> bool:
+        need = BYTES_PER_SURFEL * surf.n + WORKSPACE_PER_SURFEL * surf.n + 40 * frame_pixels
+        if self.used + need > self.budget:
+            self.rejected_sessions.append(sid)
+            return False
+        self.sessions[sid] = MapSession(sid, surf, self.device)
+        self.used += need
+        return True
+
+    def close(self):
+        if self.rast is not None:
+            self.rast.close()
+        self.sessions.clear()
+
+    # -- one tick -------------------------------------------------------------
+    def _tick(self, active):
+        frames = [r.frame for r in active]
+        if self.rast is None:
+            self.rast = render.Rasterizer(frames, frame_map=list(range(len(active))), device=self.device.index,
+                                          tuning=self.tuning)
+        else:
+            self.rast.set_frames(frames, list(range(len(active))))
+        maps = [self.sessions[r.session] for r in active]
+        params = [s.params for s in maps]
+        grads = [s.grads for s in maps]
+        targets = [render.target_tensors(r.target, self.device) if not hasattr(r, "_t") else r._t for r in active]
+        for r, t in zip(active, targets):
+            r._t = t
+        for g in grads:
+            for x in g:
+                x.zero_()
+        out = self.rast.step(params, targets, grads, check=True)
+        for s in maps:
+            s.t += 1
+            render.adam_step(s.params, s.grads, s.m, s.v, s.t, lr=self.lr, zero_grad=False)
+        return out
+
+    # -- the loop ---------------------------------------------------------------
+    def run(self, requests):
+        """Serve ``requests`` (sorted by arrival; times relative to now).
+        Returns the completed requests."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting = collections.deque()
+        active, done = [], []
+        busy = set()
+        t0 = time.perf_counter()
+        while pending or waiting or active:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                r = pending.popleft()
+                if r.session in self.sessions:
+                    waiting.append(r)
+            # fill free slots, at most one request per session, in arrival order
+            keep = collections.deque()
+            while waiting:
+                r = waiting.popleft()
+                if len(active) < self.slots and r.session not in busy:
+                    r.start = now
+                    active.append(r)
+                    busy.add(r.session)
+                else:
+                    keep.append(r)
+            waiting = keep
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, min(pending[0].arrival - now, 0.002)))
+                continue
+            out = self._tick(active)
+            F = len(active)
+            torch.cuda.synchronize(self.device)
+            L = out[1 + 3 * F: 1 + 3 * F + F].cpu().numpy()     # per-map loss (one frame per map)
+            now = time.perf_counter() - t0
+            still = []
+            for r, l in zip(active, L):
+                r.done_iters += 1
+                r.losses.append(float(l))
+                if r.done_iters >= r.iters:
+                    r.finish = now
+                    done.append(r)
+                    busy.discard(r.session)
+                    del r._t
+                else:
+                    still.append(r)
+            active = still
+        return done
+
+
+def poisson_requests(rng: np.random.Generator, sessions, frames_of, targets_of, duration: float, rate_range=(10, 20),
+                     iters: int = 10):
+    """Requests of every session as a Poisson stream at a per-session rate
+    U(rate_range) Hz over ``duration`` seconds.  ``frames_of(sid, k)`` and
+    ``targets_of(sid, k)`` give the k-th keyframe of a session."""
+    reqs = []
+    for sid in sessions:
+        rate = rng.uniform(*rate_range)
+        t, k = rng.exponential(1.0 / rate), 0
+        while t < duration:
+            reqs.append(Request(sid, frames_of(sid, k), targets_of(sid, k), t, iters))
+            t += rng.exponential(1.0 / rate)
+            k += 1
+    return sorted(reqs, key=lambda r: r.arrival)
+
+
+def latency_stats(done, duration: float, offered: int, rejected_sessions: int, n_sessions: int):
+    lat = np.array([r.finish - r.arrival for r in done]) * 1e3
+    wall = max([r.finish for r in done] + [duration])
+    return dict(completed=len(done), offered=offered, p50_ms=float(np.percentile(lat, 50)) if len(lat) else None,
+                p99_ms=float(np.percentile(lat, 99)) if len(lat) else None,
+                frames_per_s=len(done) / wall, rejected_sessions=rejected_sessions,
+                rejection_rate=rejected_sessions / max(n_sessions, 1))
