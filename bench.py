@@ -4,6 +4,7 @@ on the 200k-surfel 128 x 1024 street frame (one mapping step = bin + sort,
 forward, mapping loss, backward to every surfel parameter).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload street|mapping|batched|serving]
 
 One process per GPU (torchrun for N > 1); every rank renders its own replica
 of the workload (the path has no exchange step), so scaling is weak and the
@@ -57,6 +58,10 @@ def parse():
     ap.add_argument("--persistent", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="street", choices=["street", "mapping", "batched", "serving"],
+                    help="street: the headline line; the others print their own line")
+    ap.add_argument("--no-serving", action="store_true", help="skip the reduced serving run of the street line")
+    ap.add_argument("--serve-seconds", type=float, default=None)
     return ap.parse_args()
 
 
@@ -185,6 +190,136 @@ class Clocks:
         load = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
         return dict(sm_mhz=statistics.median(load) if load else None, sm_max_mhz=max(mx) if mx else None,
                     reasons=reasons, samples=len(rows))
+
+
+# ---------------------------------------------------------------------------
+def serving_work(n_sessions, sizes_range, seed=0, shapes=((128, 1024),)):
+    """Maps with log-uniform sizes in ``sizes_range``, one keyframe each."""
+    import numpy as np
+    from paper_2607_04127_gb300 import render, scenes
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(sizes_range[0]), np.log(sizes_range[1]), n_sessions)).astype(int)
+    return scenes.street_maps(seed, [int(x) for x in sizes], list(shapes), tile=render.DEFAULT_TILE)
+
+
+def serving_run(work, seconds, seed=0, plain=False, slots=16, iters=10, budget=150 << 30, keep_latest=True,
+                rates=(10, 20)):
+    """Every session a Poisson request stream at U(10, 20) Hz of
+    ``iters``-iteration render-and-optimise requests for its keyframe;
+    returns the latency statistics."""
+    import numpy as np
+    from paper_2607_04127_gb300 import serve
+    rng = np.random.default_rng(seed)
+    srv = serve.Server(hbm_budget_bytes=budget, slots=slots, plain=plain, keep_latest=keep_latest)
+    sids = []
+    for sid, (surf, fr, _) in enumerate(work):
+        if srv.open_session(sid, surf, fr.H * fr.W):
+            sids.append(sid)
+    reqs = serve.poisson_requests(rng, sids, lambda sid, k: work[sid][1], lambda sid, k: work[sid][2], seconds,
+                                  rate_range=rates, iters=iters)
+    # warm-up request (kernels, workspace), not timed
+    srv.run([serve.Request(sids[0], work[sids[0]][1], work[sids[0]][2], 0.0, 2)])
+    srv.dropped.clear()
+    done = srv.run(reqs)
+    st = serve.latency_stats(done, seconds, len(reqs), len(srv.rejected_sessions), len(work), len(srv.dropped))
+    sizes = [s.n for s, _, _ in work]
+    st.update(sessions=len(work), map_sizes=[int(min(sizes)), int(max(sizes))], seconds=seconds, iters=iters,
+              rate_hz=list(rates), keep_latest=keep_latest,
+              mode="plain per-request" if plain else f"continuous batching, {slots} slots")
+    srv.close()
+    return st
+
+
+def run_mapping(args):
+    """Differentiable mapping window: 1M-surfel street track, 8 keyframes
+    (128 x 1024) rendered together, 10 Adam iterations; fused and autograd
+    drivers."""
+    import torch
+    from paper_2607_04127_gb300 import build, mapping, render, scenes
+    build.build()
+    surf, frames, targets = scenes.street_track()
+    frames = [f.with_tiles(*render.DEFAULT_TILE) for f in frames]
+    res = {}
+    for ag in (False, True):
+        w = mapping.MappingWindow(surf, frames, targets, autograd=ag)
+        w.run(2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        L = w.run(10)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        rays = 10 * sum(f.H * f.W for f in frames)
+        res["autograd" if ag else "fused"] = dict(ms_per_iteration=ms / 10, rays_per_s=rays / (ms / 1e3),
+                                                  loss_first=float(L[0]), loss_last=float(L[-1]))
+        w.close()
+    line = dict(metric="mapping window rays/s (1M surfels, 8 keyframes 128x1024, 10 Adam iterations)",
+                value=res["fused"]["rays_per_s"], unit="rays/s", higher_is_better=True, dtype="f32",
+                data="synthetic (seeded 200 m street track, scenes.street_track)", n_gpus=1,
+                config=dict(workload="mapping window", surfels=surf.n, keyframes=len(frames), iterations=10,
+                            tile="%dx%d" % render.DEFAULT_TILE), drivers=res)
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args):
+    """Sixteen independent maps of 50k..2M surfels with 64x1024 / 128x1024 /
+    128x2048 frames: one call per stage (autotuned, persistent, CUDA graph)
+    against sixteen sequential plain launches."""
+    import torch
+    from paper_2607_04127_gb300 import autotune, batched, build, render, scenes
+    build.build()
+    sizes = [50_000, 100_000, 250_000, 500_000, 1_000_000, 2_000_000] * 3
+    sizes = sizes[:16]
+    work = scenes.street_maps(1, sizes, [(64, 1024), (128, 1024), (128, 2048)], tile=render.DEFAULT_TILE)
+    maps, frames, targets = zip(*work)
+    rays = sum(f.H * f.W for f in frames)
+    steps = 10
+    seq = batched.SequentialMaps(maps, frames, targets)
+    t_seq = autotune.time_steps(seq, steps)
+    seq.close()
+
+    def make(tile, tun):
+        return batched.BatchedMaps(maps, [f.with_tiles(*tile) for f in frames], targets, tuning=tun)
+
+    tile, tun, log = autotune.autotune(make, steps=3)
+    B = make(tile, tun)
+    B.capture()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        B.replay()
+    b.record()
+    torch.cuda.synchronize()
+    B.rast.session.check_status()
+    t_b = a.elapsed_time(b) / steps
+    B.close()
+    line = dict(metric="batched fwd+bwd rays/s, 16 uneven maps (8.7M surfels) in one launch per stage",
+                value=rays / (t_b / 1e3), unit="rays/s", higher_is_better=True, dtype="f32", n_gpus=1,
+                data="synthetic (seeded street maps, scenes.street_maps)",
+                config=dict(workload="16 maps 50k-2M surfels, 64x1024/128x1024/128x2048", surfels=int(sum(sizes)),
+                            rays=rays, tile="%dx%d" % tile, **tun, graph=True),
+                ms_per_step=t_b, sequential=dict(ms_per_step=t_seq, rays_per_s=rays / (t_seq / 1e3),
+                                                 tile="%dx%d" % render.DEFAULT_TILE),
+                speedup_vs_sequential=t_seq / t_b, autotune_ms=log)
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Thirty-two sessions (100k..2M surfels), Poisson 10-20 Hz each, 10
+    iterations per request, 150 GB budget: continuous batching against
+    per-request plain launches."""
+    from paper_2607_04127_gb300 import build
+    build.build()
+    secs = args.serve_seconds or 10.0
+    work = serving_work(32, (100_000, 2_000_000), seed=2)
+    b = serving_run(work, secs, seed=2)
+    p = serving_run(work, secs, seed=2, plain=True)
+    line = dict(metric="serving p50/p99 frame latency and frames/s, 32 mapping sessions", value=b["p99_ms"],
+                unit="ms (p99)", higher_is_better=False, dtype="f32", n_gpus=1,
+                data="synthetic (seeded street maps, Poisson request streams)", serving=b, plain=p)
+    print(json.dumps(line), flush=True)
 
 
 def run_ours(args):
@@ -320,6 +455,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        rast.close()
+        serving = serving_run(serving_work(8, (100_000, 400_000), seed=4), args.serve_seconds or 2.0, seed=4,
+                              iters=10)
     clocks = clk.summary()
     if rank != 0:
         return
@@ -346,8 +486,11 @@ def run_ours(args):
     )
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if serving is not None:
+        line["serving"] = serving
     print(json.dumps(line), flush=True)
-    rast.close()
+    if serving is None:
+        rast.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -356,6 +499,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "mapping":
+        run_mapping(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

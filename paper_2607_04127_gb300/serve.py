@@ -14,7 +14,10 @@ table), then one Adam step per map.  Requests that arrived meanwhile join at
 the next tick as slots free up (at most ``slots`` active requests, at most
 one per session: a session's keyframes update the same map and are served in
 arrival order).  A request completes after ``iters`` ticks; its latency is
-completion time minus arrival time.
+completion time minus arrival time.  With ``keep_latest`` a session keeps at
+most one waiting request: a newer keyframe supersedes a waiting older one,
+which is dropped and counted (mapping always works on the newest keyframe),
+so queues stay bounded under overload.
 
 ``plain=True`` serves the same requests one at a time with per-request
 launches (the baseline the batched form is measured against).
@@ -65,7 +68,8 @@ class MapSession:
 
 class Server:
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 150 << 30, slots: int = 16,
-                 tuning: dict | None = None, lr=(1e-3, 1e-3, 5e-3, 5e-3), plain: bool = False):
+                 tuning: dict | None = None, lr=(1e-3, 1e-3, 5e-3, 5e-3), plain: bool = False,
+                 keep_latest: bool = False):
         self.device = torch.device("cuda", device)
         self.budget = hbm_budget_bytes
         self.slots = 1 if plain else slots
@@ -76,7 +80,8 @@ class Server:
         self.rejected_sessions: list[int] = []
         self.used = 0
         self.rast = None
-        self.frame_shape = None
+        self.keep_latest = keep_latest
+        self.dropped: list[Request] = []
 
     # -- admission ----------------------------------------------------------
     def open_session(self, sid: int, surf, frame_pixels: int) -> bool:
@@ -129,8 +134,13 @@ class Server:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 r = pending.popleft()
-                if r.session in self.sessions:
-                    waiting.append(r)
+                if r.session not in self.sessions:
+                    continue
+                if self.keep_latest:
+                    for old in [w for w in waiting if w.session == r.session]:
+                        waiting.remove(old)
+                        self.dropped.append(old)
+                waiting.append(r)
             # fill free slots, at most one request per session, in arrival order
             keep = collections.deque()
             while waiting:
@@ -182,10 +192,14 @@ def poisson_requests(rng: np.random.Generator, sessions, frames_of, targets_of, 
     return sorted(reqs, key=lambda r: r.arrival)
 
 
-def latency_stats(done, duration: float, offered: int, rejected_sessions: int, n_sessions: int):
+def latency_stats(done, duration: float, offered: int, rejected_sessions: int, n_sessions: int, dropped: int = 0):
+    """p50 / p99 latency (ms) of the completed requests, completed frames per
+    second of wall time, and the rejections: sessions refused at admission,
+    requests superseded by a newer keyframe of their session."""
     lat = np.array([r.finish - r.arrival for r in done]) * 1e3
     wall = max([r.finish for r in done] + [duration])
     return dict(completed=len(done), offered=offered, p50_ms=float(np.percentile(lat, 50)) if len(lat) else None,
                 p99_ms=float(np.percentile(lat, 99)) if len(lat) else None,
                 frames_per_s=len(done) / wall, rejected_sessions=rejected_sessions,
-                rejection_rate=rejected_sessions / max(n_sessions, 1))
+                session_rejection_rate=rejected_sessions / max(n_sessions, 1), dropped_requests=dropped,
+                request_rejection_rate=dropped / max(offered, 1))

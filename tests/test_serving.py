@@ -101,3 +101,14 @@ def test_poisson_stream_latency_stats(workload):
     st = serve.latency_stats(done, 0.5, len(reqs), 0, len(sids))
     assert st["completed"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
     srv.close()
+
+
+def test_keep_latest_supersedes_waiting_keyframes(workload):
+    from paper_2607_04127_gb300 import serve
+    surf, fr, tgt = workload[0]
+    srv = serve.Server(slots=4, keep_latest=True)
+    srv.open_session(0, surf, fr.H * fr.W)
+    reqs = [serve.Request(0, fr, tgt, 0.0, 2) for _ in range(3)]
+    done = srv.run(reqs)
+    assert len(done) == 1 and done[0] is reqs[2] and len(srv.dropped) == 2
+    srv.close()
