@@ -296,6 +296,40 @@ LGS_API lgs_status lgs_loss_batch(lgs_session s, const lgs_surfels* maps, int n_
                           const lgs_fwd_grad_out* grads_out, const lgs_surfel_grad* grads,
                           float* loss_out, void* stream);
 
+/* ---- image loss without a session or workspace --------------------------
+ * The paper has no counterpart to this call; it is an interface for callers
+ * that cannot allocate device memory at the point where they evaluate the
+ * loss (for instance a mapping thread whose device memory is all reserved up
+ * front, or code that holds no lgs workspace) and still need the image terms
+ * of the mapping loss (Eqs. depthloss, normalloss) of frames they rendered.
+ *
+ * Computes, for n_frames frames of one map (each weighted 1 / n_frames), the
+ * image terms and their upstream gradient planes with the same arithmetic and
+ * reduction order as the image part of lgs_loss: on the device,
+ * loss_out[0] = (1/F) sum_f [L_depth + la L_alpha + ln lng L_ng]_f and
+ * loss_out[1+3f .. 3+3f] = (L_depth, L_alpha, L_ng) of frame f (1 + 3
+ * n_frames floats); grads_out[f] (overwritten) as in lgs_loss.  H[f], W[f]:
+ * host arrays of the frames' sizes; fwd, targets, grads_out: host arrays of
+ * device pointers as in lgs_loss; params->lambda_s and s_max are unused.
+ *
+ * Nothing is allocated, by the library or by the caller: the scratch (per-CTA
+ * partial sums, mask counts, a completion counter) is one static device array
+ * of LGS_NOALLOC_SCRATCH_BYTES inside the library, sized for at most
+ * LGS_NOALLOC_MAX_FRAMES frames per call; more frames are rejected with
+ * LGS_ERR_INVALID_ARG.  The caller zeroes nothing: the completion counter is
+ * zero when the library loads and the call clears it on the device before
+ * use.  The first call on a device looks up the scratch's address
+ * (cudaGetSymbolAddress, with that device current) and caches it, so make one
+ * call on each device before timing-critical use.  Every call on a device
+ * shares the one scratch: calls that overlap in time (on other streams or
+ * from other threads) corrupt each other's results and must be serialised by
+ * the caller. */
+#define LGS_NOALLOC_MAX_FRAMES 8
+#define LGS_NOALLOC_SCRATCH_BYTES (8 * 4 * LGS_NOALLOC_MAX_FRAMES * 256 + 4 * 2 * LGS_NOALLOC_MAX_FRAMES * 256 + 256)
+LGS_API lgs_status lgs_image_loss_noalloc(const int32_t* H, const int32_t* W, int n_frames, const lgs_fwd_out* fwd,
+                                          const lgs_target* targets, const lgs_loss_params* params,
+                                          const lgs_fwd_grad_out* grads_out, float* loss_out, void* stream);
+
 /* Set the compositing knobs of a session (defaults: fwd_batch 64, bwd_batch 0,
  * group 2, persistent 0).  Every choice gives bit-identical forward outputs. */
 LGS_API lgs_status lgs_session_set_tuning(lgs_session s, const lgs_tuning* t);

@@ -794,6 +794,34 @@ lgs_status lgs_loss(lgs_session s, const lgs_surfels* surfels, const lgs_frame* 
                         stream);
 }
 
+lgs_status lgs_image_loss_noalloc(const int32_t* H, const int32_t* W, int n_frames, const lgs_fwd_out* fwd,
+                                  const lgs_target* targets, const lgs_loss_params* params,
+                                  const lgs_fwd_grad_out* grads_out, float* loss_out, void* stream) {
+  static_assert(LGS_NOALLOC_SCRATCH_BYTES >= 0, "scratch size");
+  if (!H || !W || !fwd || !targets || !params || !grads_out || !loss_out)
+    return fail(LGS_ERR_INVALID_ARG, "NULL argument");
+  if (n_frames < 1) return fail(LGS_ERR_INVALID_ARG, "n_frames must be >= 1");
+  if (n_frames > LGS_NOALLOC_MAX_FRAMES)
+    return fail(LGS_ERR_INVALID_ARG, "n_frames = %d exceeds the static scratch (at most %d frames per call)", n_frames,
+                LGS_NOALLOC_MAX_FRAMES);
+  if (lgs::noalloc_scratch_bytes() != static_cast<size_t>(LGS_NOALLOC_SCRATCH_BYTES))
+    return fail(LGS_ERR_INVALID_ARG, "scratch size mismatch between header and library");
+  for (int f = 0; f < n_frames; ++f) {
+    if (H[f] < 1 || W[f] < 1 || static_cast<int64_t>(H[f]) * W[f] >= (1ll << 31))
+      return fail(LGS_ERR_INVALID_ARG, "frame %d: bad size %d x %d", f, H[f], W[f]);
+    if (!fwd[f].A || !fwd[f].S_t || !fwd[f].S_n || !targets[f].D || !targets[f].N_gicp || !grads_out[f].dA ||
+        !grads_out[f].dS_t || !grads_out[f].dS_n)
+      return fail(LGS_ERR_INVALID_ARG, "frame %d: NULL plane", f);
+  }
+  void* scratch = nullptr;
+  cudaError_t e = lgs::noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the loss scratch");
+  e = lgs::launch_image_loss_noalloc(scratch, n_frames, H, W, fwd, targets, *params, grads_out, loss_out,
+                                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "image loss");
+  return LGS_OK;
+}
+
 lgs_status lgs_adam_step(float* mean, float* quat, float* log_scale, float* logit, const lgs_surfel_grad* grad,
                          float* m_state, float* v_state, int64_t n, int64_t step, const float lr[4], float beta1,
                          float beta2, float eps, int zero_grad, void* stream) {

@@ -415,6 +415,12 @@ cudaError_t launch_raster_fwd(const Layout& L, const WsPtrs& w, const Desc& h, c
 cudaError_t launch_raster_bwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch, int group,
                               int persistent, cudaStream_t s);
 size_t loss_part_bytes();
+size_t noalloc_scratch_bytes();
+cudaError_t noalloc_scratch(void** out);
+cudaError_t launch_image_loss_noalloc(void* scratch, int n_frames, const int32_t* H, const int32_t* W,
+                                      const lgs_fwd_out* fwd, const lgs_target* targets,
+                                      const lgs_loss_params& P, const lgs_fwd_grad_out* grads_out, float* loss_out,
+                                      cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const Layout& L, const WsPtrs& w, const Desc& h, cudaStream_t s);
 cudaError_t launch_loss(const Layout& L, const WsPtrs& w, const Desc& h, const lgs_loss_params& p,
                         bool scale_grad, float* loss_out, cudaStream_t s);

@@ -74,7 +74,7 @@ EXPORTS = [
     "lgs_session_set_workspace", "lgs_session_status", "lgs_session_pair_count", "lgs_session_counters",
     "lgs_session_bins", "lgs_session_read_bins", "lgs_bin_sort", "lgs_render_fwd", "lgs_render_bwd", "lgs_loss", "lgs_bin_sort_batch",
     "lgs_render_fwd_batch", "lgs_render_bwd_batch", "lgs_loss_batch", "lgs_session_set_tuning", "lgs_adam_step",
-    "lgs_session_set_timing", "lgs_session_kernel_times",
+    "lgs_session_set_timing", "lgs_session_kernel_times", "lgs_image_loss_noalloc",
     "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version",
 ]
 
@@ -112,6 +112,7 @@ def load():
         "lgs_session_set_tuning": ([P, P], S),
         "lgs_session_set_timing": ([P, i32], S),
         "lgs_session_kernel_times": ([P, P, P], S),
+        "lgs_image_loss_noalloc": ([P, P, i32, P, P, P, P, P, P], S),
         "lgs_adam_step": ([P, P, P, P, P, P, P, i64, i64, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            i32, P], S),
         "lgs_status_string": ([i32], ctypes.c_char_p),
@@ -417,3 +418,14 @@ class Session:
         st, req = lgs_session_status(self.handle)
         _check(st)
         return req
+
+
+def lgs_image_loss_noalloc(shapes, fwd, targets, params, grads_out, loss_out_ptr: int, stream):
+    """shapes: [(H, W)] per frame; fwd: [lgs_fwd_out]; targets: [lgs_target];
+    params: lgs_loss_params; grads_out: [lgs_fwd_grad_out]; loss_out_ptr:
+    device pointer to 1 + 3 n floats."""
+    n = len(shapes)
+    Hs = (ctypes.c_int32 * n)(*[h for h, _ in shapes])
+    Ws = (ctypes.c_int32 * n)(*[w for _, w in shapes])
+    _check(load().lgs_image_loss_noalloc(Hs, Ws, n, _arr(lgs_fwd_out, fwd), _arr(lgs_target, targets), _ref(params),
+                                         _arr(lgs_fwd_grad_out, grads_out), loss_out_ptr, stream))
