@@ -203,6 +203,7 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
   L.ranges = take(8 * T);
   L.g13 = take(64 * I);
   L.work = take(4 * T);
+  L.longt = take(4 * T);
   L.loss_part = take(lgs::loss_part_bytes());
   L.total = off;
   L.items_cap = items;
@@ -675,7 +676,7 @@ lgs_status lgs_render_fwd_batch(lgs_session s, const lgs_surfels* maps, int n_ma
          return lgs::launch_raster_fwd(s->lay, w, d, pv, s->tune.fwd_batch, s->tune.group, s->tune.persistent, cs);
        })) != cudaSuccess)
     return cuda_fail(e, "raster_fwd");
-  s->launches += 1;
+  s->launches += 2;   // per-tile and long-list kernels
   s->last_stream = cs;
   return LGS_OK;
 }
@@ -729,7 +730,7 @@ lgs_status lgs_render_bwd_batch(lgs_session s, const lgs_surfels* maps, int n_ma
   if ((e = timed(s, LGS_TIME_BWD_CHAIN, cs, [&] { return lgs::launch_preprocess_bwd(s->lay, w, d, cs); })) !=
       cudaSuccess)
     return cuda_fail(e, "preprocess_bwd");
-  s->launches += 2;
+  s->launches += 3;   // per-tile and long-list kernels, chain
   s->last_stream = cs;
   return LGS_OK;
 }

@@ -8,7 +8,8 @@
 //                 per covered tile (atomic per-tile counters)
 //   k_tile_scan   one CTA: exclusive scan of the tile counts -> every tile's
 //                 [start, end) and its fill cursor; capacity check; the
-//                 longest-first tile order of the persistent kernels
+//                 longest-first tile order of the persistent kernels; the
+//                 list of tiles longer than kLongList
 //   k_emit        every item appends (depth key << 32 | item) to the bucket
 //                 of each tile it covers (order inside a bucket arbitrary)
 //   k_tile_sort_merge / k_tile_sort
@@ -56,6 +57,11 @@ __global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, St
     st->contrib_bwd = 0;
     st->alg_fwd = 0;
     st->loss_ticket = 0;
+    st->n_long = 0;
+    st->long_counter_fwd = 0;
+    st->long_counter_bwd = 0;
+    st->long_done_fwd = 0;
+    st->long_done_bwd = 0;
   }
   for (int i = threadIdx.x; i < F.ntr; i += blockDim.x) {
     const int r0 = i * F.th;
@@ -217,7 +223,8 @@ __device__ __forceinline__ int order_bucket(uint32_t n) { return kOrderBuckets -
 
 __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ tcur, uint32_t n_tiles,
                                                           uint2* __restrict__ ranges, Status* __restrict__ st,
-                                                          int64_t cap, uint32_t* __restrict__ order) {
+                                                          int64_t cap, uint32_t* __restrict__ order,
+                                                          uint32_t* __restrict__ longt) {
   __shared__ unsigned long long s_w[32];
   __shared__ unsigned long long s_carry;
   __shared__ uint32_t s_bucket[kOrderBuckets];
@@ -283,6 +290,7 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
   for (uint32_t t = tid; t < n_tiles; t += kScanCta) {
     const uint2 rg = ranges[t];
     order[atomicAdd(&s_bucket[order_bucket(rg.y - rg.x)], 1u)] = t;
+    if (rg.y - rg.x > kLongList) longt[atomicAdd(&st->n_long, 1u)] = t;
   }
 }
 
@@ -599,7 +607,7 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
   const int64_t ni = n_items > 0 ? n_items : 1;
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
   k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tcur, w.st);
-  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work);
+  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work, w.longt);
   k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.box, w.tcur, w.ranges, w.st, w.pkey);
   if (n_tiles > 0) {
     k_tile_sort_merge<<<n_tiles, kMergeCta, 0, s>>>(w.ranges, w.st, w.pkey, w.ptile, w.pv);

@@ -60,6 +60,11 @@ struct Status {
   unsigned int check;                 // a checked-build bounds check failed
   unsigned int work_counter;          // persistent scheduler: next work item
   unsigned int work_counter2;
+  unsigned int n_long;                // tiles whose list is longer than kLongList
+  unsigned int long_counter_fwd;      // work counters of the long-list kernels (self-resetting)
+  unsigned int long_counter_bwd;
+  unsigned int long_done_fwd;         // warps of the long-list kernels that have finished
+  unsigned int long_done_bwd;
   unsigned long long evals_fwd;       // ray/surfel evaluations (cumulative since bin_sort)
   unsigned long long evals_bwd;
   unsigned long long contrib_fwd;     // composited (fwd) / valid re-evaluated (bwd) pairs
@@ -69,7 +74,7 @@ struct Status {
 };
 
 struct Layout {
-  size_t desc, status, tables, rec, box, key, cnt, tcur, pkey, ptile, pv, ranges, g13, work, loss_part, total;
+  size_t desc, status, tables, rec, box, key, cnt, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part, total;
   int64_t items_cap, pairs_cap;
   uint32_t tiles_cap;
   uint32_t tables_cap;     // floats
@@ -91,6 +96,7 @@ struct WsPtrs {
   uint2* ranges;           // [tiles]
   float* g13;              // [items][16]
   uint32_t* work;          // persistent scheduler tile order
+  uint32_t* longt;         // tiles with lists longer than kLongList (st->n_long of them)
   double* loss_part;       // loss partial sums and mask counts
 };
 
@@ -111,6 +117,7 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.ranges = reinterpret_cast<uint2*>(b + L.ranges);
   p.g13 = reinterpret_cast<float*>(b + L.g13);
   p.work = reinterpret_cast<uint32_t*>(b + L.work);
+  p.longt = reinterpret_cast<uint32_t*>(b + L.longt);
   p.loss_part = reinterpret_cast<double*>(b + L.loss_part);
   return p;
 }
@@ -351,6 +358,11 @@ __device__ __forceinline__ bool box_hits(const float4& b, const WarpBox& w) {
 // Then for a unit ray d: den = n.d, t = h/den, u = t (a_u.d) - b_u,
 // v = t (a_v.d) - b_v.
 // ---------------------------------------------------------------------------
+// Tiles whose list is longer than this are composited by the entry-parallel
+// per-pixel kernels instead of the per-tile ones (their pixels would walk the
+// whole list one entry at a time).
+constexpr uint32_t kLongList = 4096;
+
 struct Eval {
   float den, t, ud, vd, u, v, q, G, araw, a;
   bool valid;

@@ -34,8 +34,35 @@ constexpr int kMaxTileThreads = 256;
 // plane is u s_u t_u + v s_v t_v.
 constexpr int kGrad = 12;
 
+// The 12 moments of one valid contribution with transmittance Tk before it
+// and suffix S (the sum over the later contributors of w (g.c)), added into v.
+__device__ __forceinline__ void moments(const Eval& E, const float4& r0, float Tk, float S, float iom, float gA,
+                                        float gSt, float gSx, float gSy, float gSz, float (&v)[16]) {
+  const float sg = E.den > 0.f ? -1.f : 1.f;
+  const float gc = gA + gSt * E.t + sg * (gSx * r0.x + gSy * r0.y + gSz * r0.z);
+  const float w = E.a * Tk;
+  const float dLda = Tk * gc - S * iom;
+  const float g = E.araw < 0.99f ? E.araw * dLda : 0.f;
+  const float ug = E.u * g, vg = E.v * g;
+  const float ct = __fdividef(fmaf(w, gSt, -fmaf(ug, E.ud, vg * E.vd)), E.den);
+  const float wsg = w * sg;
+  v[0] += g;
+  v[1] += ug;
+  v[2] += vg;
+  v[3] += E.u * ug;
+  v[4] += E.v * vg;
+  v[5] += E.u * vg;
+  v[6] += ct;
+  v[7] += ct * E.u;
+  v[8] += ct * E.v;
+  v[9] += wsg * gSx;
+  v[10] += wsg * gSy;
+  v[11] += wsg * gSz;
+}
+
 // Reverse-order step of one valid contribution: updates the transmittance T
-// (before it) and the suffix S, and writes its 12 moments into v.
+// (before it) and the suffix S, and adds its 12 moments into v (the same
+// arithmetic as moments(), with S updated in place).
 __device__ __forceinline__ void contrib_moments(const Eval& E, const float4& r0, float gA, float gSt, float gSx,
                                                 float gSy, float gSz, float& T, float& S, float (&v)[16]) {
   const float iom = __fdividef(1.0f, 1.0f - E.a);
@@ -50,18 +77,18 @@ __device__ __forceinline__ void contrib_moments(const Eval& E, const float4& r0,
   const float ug = E.u * g, vg = E.v * g;
   const float ct = __fdividef(fmaf(w, gSt, -fmaf(ug, E.ud, vg * E.vd)), E.den);
   const float wsg = w * sg;
-  v[0] = g;
-  v[1] = ug;
-  v[2] = vg;
-  v[3] = E.u * ug;
-  v[4] = E.v * vg;
-  v[5] = E.u * vg;
-  v[6] = ct;
-  v[7] = ct * E.u;
-  v[8] = ct * E.v;
-  v[9] = wsg * gSx;
-  v[10] = wsg * gSy;
-  v[11] = wsg * gSz;
+  v[0] += g;
+  v[1] += ug;
+  v[2] += vg;
+  v[3] += E.u * ug;
+  v[4] += E.v * vg;
+  v[5] += E.u * vg;
+  v[6] += ct;
+  v[7] += ct * E.u;
+  v[8] += ct * E.v;
+  v[9] += wsg * gSx;
+  v[10] += wsg * gSy;
+  v[11] += wsg * gSz;
 }
 
 struct TileCtx {
@@ -145,6 +172,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
   uint32_t evals = 0, contrib = 0, alg = 0;
   for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
+    if (tc.end - tc.start > kLongList) continue;   // the long-list kernels' tile
     const FrameDev& F = D->f[tc.f];
     const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
     float dx = 0.f, dy = 0.f, dz = 0.f;
@@ -270,6 +298,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
   uint32_t evals = 0, contrib = 0;
   for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
+    if (tc.end - tc.start > kLongList) continue;   // the long-list kernels' tile
     const FrameDev& F = D->f[tc.f];
     const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
     float dx = 0.f, dy = 0.f, dz = 0.f;
@@ -394,6 +423,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
   uint32_t evals = 0, contrib = 0, alg = 0;
   for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
+    if (tc.end - tc.start > kLongList) continue;   // the long-list kernels' tile
     const FrameDev& F = D->f[tc.f];
     const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
     float dx = 0.f, dy = 0.f, dz = 0.f;
@@ -491,6 +521,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
   uint32_t evals = 0, contrib = 0;
   for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
     const TileCtx tc = tile_ctx(*D, tile, ranges);
+    if (tc.end - tc.start > kLongList) continue;   // the long-list kernels' tile
     const FrameDev& F = D->f[tc.f];
     const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
     float dx = 0.f, dy = 0.f, dz = 0.f;
@@ -574,6 +605,269 @@ __global__ void __launch_bounds__(kMaxTileThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Long lists (more than kLongList entries): one warp per pixel
+// ---------------------------------------------------------------------------
+// A tile with a very long list (a far horizon seen along a street: tens of
+// thousands of entries, few of which any pixel composites) would make its
+// CTA walk the list one entry at a time while the rest of the frame is done.
+// Here a work item is one (long tile, pixel), claimed through an atomic
+// counter; the 32 lanes take 32 consecutive entries of the list for the
+// warp's pixel.  Forward: the transmittance before each entry is T times a
+// multiplicative scan of (1 - a) over the lanes, the early stop is the first
+// lane whose T (1 - a) falls below 1e-4, and the composited sums are warp
+// reductions.  Backward: from T_final, the transmittance before each entry
+// is T divided by the suffix product of (1 - a), the suffix S a suffix sum;
+// every valid lane adds its own entry's 12 moments with atomics.  The products
+// and sums associate differently from the per-tile kernels (same values to a
+// few ulps).
+struct LongPix {
+  const FrameDev* F;
+  int r, c;
+  bool inside;
+  uint32_t start, end;
+  int64_t pix;
+  int HW;
+};
+
+__device__ __forceinline__ bool long_item(const Desc& D, const uint2* __restrict__ ranges,
+                                          const uint32_t* __restrict__ longt, uint32_t n_long, uint32_t id,
+                                          LongPix& p) {
+  const uint32_t tp = static_cast<uint32_t>(D.th * D.tw);
+  const uint32_t gi = id / tp, k = id - gi * tp;
+  if (gi >= n_long) return false;
+  const uint32_t tile = longt[gi];
+  const int f = frame_of_tile(D, tile);
+  const FrameDev& F = D.f[f];
+  const int lt = static_cast<int>(tile - F.tile_base);
+  const int ti = lt / F.ntc, tj = lt - ti * F.ntc;
+  p.F = &F;
+  p.r = ti * F.th + static_cast<int>(k) / F.tw;
+  p.c = tj * F.tw + static_cast<int>(k) % F.tw;
+  p.inside = p.r < F.H && p.c < F.W;
+  p.pix = static_cast<int64_t>(p.r) * F.W + p.c;
+  p.HW = F.H * F.W;
+  const uint2 rg = ranges[tile];
+  p.start = rg.x;
+  p.end = rg.y;
+  return true;
+}
+
+__device__ __forceinline__ uint32_t warp_claim(unsigned int* counter) {
+  uint32_t id = 0;
+  if ((threadIdx.x & 31) == 0) id = atomicAdd(counter, 1u);
+  return __shfl_sync(0xffffffffu, id, 0);
+}
+
+// A warp that finds no work left counts itself done; the last one resets the
+// work and done counters to zero for the next launch on the stream.
+__device__ __forceinline__ void long_finish(unsigned int* counter, unsigned int* done) {
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence();
+    const unsigned int total = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(done, 1u) == total - 1) {
+      *counter = 0u;
+      *done = 0u;
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, const uint2* __restrict__ ranges,
+                                                  const uint32_t* __restrict__ pv, const float4* __restrict__ rec,
+                                                  const float4* __restrict__ box,
+                                                  const uint32_t* __restrict__ longt, Status* __restrict__ st) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t n_long = st->n_long;
+  if (n_long == 0) return;
+  uint32_t evals = 0, contrib = 0, alg = 0;
+  LongPix P;
+  while (long_item(*D, ranges, longt, n_long, warp_claim(&st->long_counter_fwd), P)) {
+    if (!P.inside) continue;
+    const FrameDev& F = *P.F;
+    float dx, dy, dz;
+    pixel_ray(F, P.r, P.c, dx, dy, dz);
+    WarpBox pb;
+    pb.r0 = pb.r1 = static_cast<float>(P.r);
+    pb.cmid = static_cast<float>(P.c);
+    pb.chalf = 0.f;
+    pb.W = static_cast<float>(F.W);
+    float T = 1.f, A = 0.f, St = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f;
+    int last = 0, stop_at = -1;
+    for (uint32_t base = P.start; base < P.end; base += 32) {
+      const uint32_t j = base + lane;
+      bool valid = false;
+      Eval e;
+      float nx = 0.f, ny = 0.f, nz = 0.f;
+      if (j < P.end) {
+        const uint32_t item = __ldg(pv + j);
+        if (box_hits(__ldg(box + item), pb)) {
+          const float4* rp = rec + 4 * static_cast<int64_t>(item);
+          const float4 r0 = __ldg(rp);
+          eval_pair(r0, __ldg(rp + 1), __ldg(rp + 2), __ldg(reinterpret_cast<const float*>(rp + 3)), dx, dy, dz, e);
+          valid = e.valid;
+          nx = r0.x; ny = r0.y; nz = r0.z;
+          ++evals;
+        }
+      }
+      // P_j = prod_{i <= j} (1 - a_i) over the valid lanes
+      float Pj = valid ? __fsub_rn(1.0f, e.a) : 1.0f;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, Pj, o);
+        if (lane >= o) Pj *= y;
+      }
+      float Pex = __shfl_up_sync(0xffffffffu, Pj, 1);
+      if (lane == 0) Pex = 1.0f;
+      const uint32_t sm = __ballot_sync(0xffffffffu, valid && T * Pj < 1e-4f);
+      const int fs = sm ? __ffs(sm) - 1 : 32;
+      const bool inc = valid && lane < fs;
+      const float w = inc ? e.a * (T * Pex) : 0.f;
+      const float ws = valid && e.den > 0.f ? -w : w;
+      A += warp_sum(w);
+      St += warp_sum(inc ? w * e.t : 0.f);
+      Sx += warp_sum(ws * nx);
+      Sy += warp_sum(ws * ny);
+      Sz += warp_sum(ws * nz);
+      contrib += inc;
+      const uint32_t im = __ballot_sync(0xffffffffu, inc);
+      if (im) last = static_cast<int>(base - P.start) + (31 - __clz(im)) + 1;
+      T *= __shfl_sync(0xffffffffu, fs < 32 ? Pex : Pj, fs < 32 ? fs : 31);
+      if (sm) {
+        stop_at = static_cast<int>(base - P.start) + fs + 1;
+        break;
+      }
+    }
+    if (lane == 0) {
+      F.A[P.pix] = A;
+      F.St[P.pix] = St;
+      F.Sn[P.pix] = Sx;
+      F.Sn[P.HW + P.pix] = Sy;
+      F.Sn[2 * static_cast<int64_t>(P.HW) + P.pix] = Sz;
+      F.Tf[P.pix] = T;
+      F.nc[P.pix] = last;
+      alg += stop_at >= 0 ? static_cast<uint32_t>(stop_at) : P.end - P.start;
+    }
+  }
+  long_finish(&st->long_counter_fwd, &st->long_done_fwd);
+  unsigned long long ev = evals, co = contrib, al = alg;
+  for (int o = 16; o > 0; o >>= 1) {
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    co += __shfl_xor_sync(0xffffffffu, co, o);
+  }
+  if (lane == 0 && ev) atomicAdd(&st->evals_fwd, ev);
+  if (lane == 0 && co) atomicAdd(&st->contrib_fwd, co);
+  if (lane == 0 && al) atomicAdd(&st->alg_fwd, al);
+}
+
+__global__ void __launch_bounds__(256) k_bwd_long(const Desc* __restrict__ D, const uint2* __restrict__ ranges,
+                                                  const uint32_t* __restrict__ pv, const float4* __restrict__ rec,
+                                                  const float4* __restrict__ box, float* __restrict__ g13,
+                                                  const uint32_t* __restrict__ longt, Status* __restrict__ st) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t n_long = st->n_long;
+  if (n_long == 0) return;
+  uint32_t evals = 0, contrib = 0;
+  LongPix P;
+  while (long_item(*D, ranges, longt, n_long, warp_claim(&st->long_counter_bwd), P)) {
+    if (!P.inside) continue;
+    const FrameDev& F = *P.F;
+    const int nc = F.nc[P.pix];
+    // n_contrib comes from the caller: never walk past the tile's list
+    const uint32_t stop = min(static_cast<uint32_t>(nc > 0 ? nc : 0), P.end - P.start);
+    if (stop == 0) continue;
+    float dx, dy, dz;
+    pixel_ray(F, P.r, P.c, dx, dy, dz);
+    const float gA = F.gA[P.pix], gSt = F.gSt[P.pix];
+    const float gSx = F.gSn[P.pix], gSy = F.gSn[P.HW + P.pix], gSz = F.gSn[2 * static_cast<int64_t>(P.HW) + P.pix];
+    WarpBox pb;
+    pb.r0 = pb.r1 = static_cast<float>(P.r);
+    pb.cmid = static_cast<float>(P.c);
+    pb.chalf = 0.f;
+    pb.W = static_cast<float>(F.W);
+    float T = F.Tf[P.pix], S = 0.f;
+    for (int c0 = static_cast<int>((stop + 31) / 32) - 1; c0 >= 0; --c0) {
+      const uint32_t k = 32u * c0 + lane;
+      bool valid = false;
+      Eval e;
+      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+      uint32_t item = 0;
+      if (k < stop) {
+        item = __ldg(pv + P.start + k);
+        if (box_hits(__ldg(box + item), pb)) {
+          const float4* rp = rec + 4 * static_cast<int64_t>(item);
+          r0 = __ldg(rp);
+          eval_pair(r0, __ldg(rp + 1), __ldg(rp + 2), __ldg(reinterpret_cast<const float*>(rp + 3)), dx, dy, dz, e);
+          valid = e.valid;
+          ++evals;
+        }
+      }
+      const float om = valid ? 1.0f - e.a : 1.0f;
+      // Q_j = prod_{i >= j} (1 - a_i) over the chunk's valid lanes
+      float Qj = om;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_down_sync(0xffffffffu, Qj, o);
+        if (lane + o < 32) Qj *= y;
+      }
+      const float Tk = __fdividef(T, Qj);   // transmittance before entry j
+      float c = 0.f, gc = 0.f;
+      if (valid) {
+        const float sg = e.den > 0.f ? -1.f : 1.f;
+        gc = gA + gSt * e.t + sg * (gSx * r0.x + gSy * r0.y + gSz * r0.z);
+        c = e.a * Tk * gc;
+      }
+      // suffix sums of w (g.c): after entry j (exclusive) and over the chunk
+      float Cs = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_down_sync(0xffffffffu, Cs, o);
+        if (lane + o < 32) Cs += y;
+      }
+      float Cex = __shfl_down_sync(0xffffffffu, Cs, 1);
+      if (lane == 31) Cex = 0.f;
+      if (valid) {
+        ++contrib;
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = 0.f;
+        moments(e, r0, Tk, S + Cex, __fdividef(1.0f, om), gA, gSt, gSx, gSy, gSz, v);
+        float* gp = g13 + 16 * static_cast<int64_t>(item);
+#pragma unroll
+        for (int q = 0; q < kGrad; ++q)
+          if (v[q] != 0.f) atomicAdd(gp + q, v[q]);
+      }
+      T = __fdividef(T, __shfl_sync(0xffffffffu, Qj, 0));
+      S += __shfl_sync(0xffffffffu, Cs, 0);
+    }
+  }
+  long_finish(&st->long_counter_bwd, &st->long_done_bwd);
+  unsigned long long ev = evals, co = contrib;
+  for (int o = 16; o > 0; o >>= 1) {
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    co += __shfl_xor_sync(0xffffffffu, co, o);
+  }
+  if (lane == 0 && ev) atomicAdd(&st->evals_bwd, ev);
+  if (lane == 0 && co) atomicAdd(&st->contrib_bwd, co);
+}
+
+// The work counters start at zero (reset at binning and by the last warp of
+// every launch), so no memset precedes the launch.
+static cudaError_t launch_long(bool fwd, const WsPtrs& w, const uint32_t* pv, cudaStream_t s) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = 2 * sms;   // warps claim (tile, pixel) items until none are left
+  if (fwd) k_fwd_long<<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.longt, w.st);
+  else k_bwd_long<<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, w.longt, w.st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 template <int B>
@@ -598,8 +892,8 @@ static int persistent_grid(int threads) {
   return sms * (per_sm < 1 ? 1 : per_sm);
 }
 
-cudaError_t launch_raster_fwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
-                              int group, int persistent, cudaStream_t s) {
+static cudaError_t launch_raster_fwd_tiles(const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
+                                           int group, int persistent, cudaStream_t s) {
   if (persistent) {
     cudaError_t e = cudaMemsetAsync(&w.st->work_counter, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
@@ -619,8 +913,8 @@ cudaError_t launch_raster_fwd(const Layout&, const WsPtrs& w, const Desc& h, con
   }
 }
 
-cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
-                              int group, int persistent, cudaStream_t s) {
+static cudaError_t launch_raster_bwd_tiles(const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
+                                           int group, int persistent, cudaStream_t s) {
   if (persistent) {
     cudaError_t e = cudaMemsetAsync(&w.st->work_counter2, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
@@ -637,6 +931,21 @@ cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, con
     case 128: return bwd_b<128>(w, pv, h, persistent, grid, s);
     default: return bwd_b<256>(w, pv, h, persistent, grid, s);
   }
+}
+
+// The per-tile kernel, then the long-list kernel for the tiles it skipped.
+cudaError_t launch_raster_fwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
+                              int group, int persistent, cudaStream_t s) {
+  cudaError_t e = launch_raster_fwd_tiles(w, h, pv, batch, group, persistent, s);
+  if (e != cudaSuccess) return e;
+  return launch_long(true, w, pv, s);
+}
+
+cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
+                              int group, int persistent, cudaStream_t s) {
+  cudaError_t e = launch_raster_bwd_tiles(w, h, pv, batch, group, persistent, s);
+  if (e != cudaSuccess) return e;
+  return launch_long(false, w, pv, s);
 }
 
 }  // namespace lgs

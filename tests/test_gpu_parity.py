@@ -282,7 +282,8 @@ def test_gradients_accumulate(oracle):
 def test_long_tile_bucket_bit_exact(oracle, n, lo, hi):
     """Buckets beyond the merge sort's 2048 keys take the shared-memory
     bitonic network (up to 4096) or its chunked path through global memory
-    (beyond): bins stay bit-exact and the forward matches the oracle."""
+    (beyond), and lists beyond 4096 entries the entry-parallel compositing
+    kernels: bins stay bit-exact, forward and gradients match the oracle."""
     from tests import _gpu
     rng = np.random.default_rng(11)
     frame = scenes.Frame(32, 512, 16, 16, -0.26, 0.26)
@@ -293,7 +294,8 @@ def test_long_tile_bucket_bit_exact(oracle, n, lo, hi):
     surf = scenes.Surfels(mean.astype(np.float32), rng.normal(size=(n, 4)).astype(np.float32),
                           np.log(rng.uniform(0.005, 0.02, (n, 2))).astype(np.float32),
                           rng.normal(size=n).astype(np.float32))
-    g = _gpu.run([surf], [frame], read_bins=True)
+    tgt = scenes.targets_for(frame, surf, 7)
+    g = _gpu.run([surf], [frame], targets=[tgt], read_bins=True)
     tp, ip, rg, dk = g["bins"]
     o = oracle.bin_frame(surf, frame)
     assert lo < (o["ranges"][:, 1] - o["ranges"][:, 0]).max() <= hi
@@ -302,6 +304,9 @@ def test_long_tile_bucket_bit_exact(oracle, n, lo, hi):
     assert np.array_equal(rg.astype(np.int64), o["ranges"])
     of = oracle.render_fwd(surf, frame, o["ranges"], o["vals"])
     assert_forward(compare_forward(g["fwd"][0], of))
+    # lists beyond 4096 entries take the entry-parallel per-pixel kernels
+    og = oracle_grads(oracle, surf, [frame], [gpu_upstream(g, 0)])
+    assert_grads(compare_grads(g["grads"][0], og))
 
 
 def test_empty_and_invisible_maps(oracle):
