@@ -330,7 +330,7 @@ LGS_API lgs_status lgs_image_loss_noalloc(const int32_t* H, const int32_t* W, in
                                           const lgs_target* targets, const lgs_loss_params* params,
                                           const lgs_fwd_grad_out* grads_out, float* loss_out, void* stream);
 
-/* Set the compositing knobs of a session (defaults: fwd_batch 64, bwd_batch 0,
+/* Set the compositing knobs of a session (defaults: fwd_batch 128, bwd_batch 0,
  * group 2, persistent 0).  Every choice gives bit-identical forward outputs. */
 LGS_API lgs_status lgs_session_set_tuning(lgs_session s, const lgs_tuning* t);
 
@@ -344,6 +344,21 @@ LGS_API lgs_status lgs_adam_step(float* mean, float* quat, float* log_scale, flo
                          const lgs_surfel_grad* grad, float* m_state, float* v_state, int64_t n,
                          int64_t step, const float lr[4], float beta1, float beta2, float eps,
                          int zero_grad, void* stream);
+
+/* One map of a batched Adam step (the arguments of lgs_adam_step). */
+typedef struct {
+    float *mean, *quat, *log_scale, *logit;
+    lgs_surfel_grad grad;
+    float *m_state, *v_state;
+    int64_t n;
+    int64_t step;                /* this map's own step count (>= 1) */
+    float lr[4];
+} lgs_adam_map;
+
+/* lgs_adam_step for n_maps maps (at most LGS_MAX_MAPS) in one launch, each
+ * with its own step count and learning rates. */
+LGS_API lgs_status lgs_adam_step_batch(const lgs_adam_map* maps, int n_maps, float beta1, float beta2, float eps,
+                                       int zero_grad, void* stream);
 
 /* ---- misc ---------------------------------------------------------------- */
 LGS_API const char* lgs_status_string(lgs_status st);

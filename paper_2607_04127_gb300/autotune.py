@@ -35,7 +35,7 @@ def time_steps(stepper, steps: int = 3) -> float:
 def autotune(make, base: dict | None = None, steps: int = 3, tiles=TILES, fwd=FWD, bwd=BWD):
     """``make(tile, tuning)`` builds a stepper (an object with ``step(check)``
     and ``close()``).  Returns (tile, tuning, {description: ms})."""
-    tun = dict(fwd_batch=64, bwd_batch=0, group=2, persistent=0, **(base or {}))
+    tun = dict(fwd_batch=128, bwd_batch=0, group=2, persistent=0, **(base or {}))
     log = {}
 
     def run(tile, t):

@@ -39,9 +39,10 @@ class BatchedMaps:
         return self.rast.step(self.params, self.targets, self.grads, check=check)
 
     def adam(self):
+        """One fused Adam launch over every map."""
         self.t += 1
-        for ps, gs, m, v in zip(self.params, self.grads, self.m, self.v):
-            render.adam_step(ps, gs, m, v, self.t, lr=self.lr, zero_grad=False)
+        render.adam_step_batch([(ps, gs, m, v, self.t, self.lr)
+                                for ps, gs, m, v in zip(self.params, self.grads, self.m, self.v)], zero_grad=False)
 
     def capture(self):
         """Size the workspace with one checked step, then capture one step

@@ -34,7 +34,7 @@ struct lgs_session_s {
   size_t g13_zero_off = 0;      // g13 region known to be all-zero
   int64_t g13_zero_items = -1;
   cudaStream_t last_stream = nullptr;
-  lgs_tuning tune{64, 0, 2, 0};
+  lgs_tuning tune{128, 0, 2, 0};
   Status* h_status = nullptr;   // pinned
   int64_t launches = 0;         // kernels enqueued by this session
   // optional device timing of kernel groups
@@ -820,6 +820,25 @@ lgs_status lgs_image_loss_noalloc(const int32_t* H, const int32_t* W, int n_fram
   e = lgs::launch_image_loss_noalloc(scratch, n_frames, H, W, fwd, targets, *params, grads_out, loss_out,
                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "image loss");
+  return LGS_OK;
+}
+
+lgs_status lgs_adam_step_batch(const lgs_adam_map* maps, int n_maps, float beta1, float beta2, float eps,
+                               int zero_grad, void* stream) {
+  if (!maps || n_maps < 1 || n_maps > LGS_MAX_MAPS)
+    return fail(LGS_ERR_INVALID_ARG, "n_maps must be 1..%d", LGS_MAX_MAPS);
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f))
+    return fail(LGS_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
+  for (int k = 0; k < n_maps; ++k) {
+    const lgs_adam_map& M = maps[k];
+    if (M.n < 0 || M.step < 1) return fail(LGS_ERR_INVALID_ARG, "map %d: bad size or step", k);
+    if (M.n > 0 && (!M.mean || !M.quat || !M.log_scale || !M.logit || !M.m_state || !M.v_state ||
+                    !M.grad.d_mean || !M.grad.d_quat || !M.grad.d_log_scale || !M.grad.d_opacity_logit))
+      return fail(LGS_ERR_INVALID_ARG, "map %d: NULL pointer", k);
+  }
+  const cudaError_t e = lgs::launch_adam_batch(maps, n_maps, beta1, beta2, eps, zero_grad,
+                                               static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "adam_batch");
   return LGS_OK;
 }
 

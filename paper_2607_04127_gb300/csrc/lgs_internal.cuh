@@ -436,6 +436,8 @@ cudaError_t launch_image_loss_noalloc(void* scratch, int n_frames, const int32_t
 cudaError_t launch_preprocess_bwd(const Layout& L, const WsPtrs& w, const Desc& h, cudaStream_t s);
 cudaError_t launch_loss(const Layout& L, const WsPtrs& w, const Desc& h, const lgs_loss_params& p,
                         bool scale_grad, float* loss_out, cudaStream_t s);
+cudaError_t launch_adam_batch(const lgs_adam_map* maps, int n_maps, float b1, float b2, float eps, int zero_grad,
+                              cudaStream_t s);
 cudaError_t launch_adam(float* p[4], float* g[4], float* m[4], float* v[4], const int64_t cnt[4],
                         int64_t step, const float lr[4], float b1, float b2, float eps, int zero_grad,
                         cudaStream_t s);

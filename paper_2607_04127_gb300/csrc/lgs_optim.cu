@@ -407,4 +407,65 @@ cudaError_t launch_adam(float* p[4], float* g[4], float* m[4], float* v[4], cons
   return cudaGetLastError();
 }
 
+// Batched form: segment 4 k + g is parameter group g of map k, each map with
+// its own bias corrections.
+struct AdamBatch {
+  float* p[4 * LGS_MAX_MAPS];
+  float* g[4 * LGS_MAX_MAPS];
+  float* m[4 * LGS_MAX_MAPS];
+  float* v[4 * LGS_MAX_MAPS];
+  int64_t n[4 * LGS_MAX_MAPS];
+  float lr[4 * LGS_MAX_MAPS];
+  float c1[LGS_MAX_MAPS], c2[LGS_MAX_MAPS];
+};
+
+__global__ void __launch_bounds__(256) k_adam_batch(const __grid_constant__ AdamBatch a, float b1, float b2, float eps,
+                                                    int zero_grad) {
+  const int sgm = blockIdx.y, map = sgm >> 2;
+  float* __restrict__ p = a.p[sgm];
+  float* __restrict__ g = a.g[sgm];
+  float* __restrict__ m = a.m[sgm];
+  float* __restrict__ v = a.v[sgm];
+  const float lr = a.lr[sgm], c1 = a.c1[map], c2 = a.c2[map];
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n[sgm];
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    if (zero_grad) g[i] = 0.f;
+  }
+}
+
+cudaError_t launch_adam_batch(const lgs_adam_map* maps, int n_maps, float b1, float b2, float eps, int zero_grad,
+                              cudaStream_t s) {
+  static_assert(sizeof(AdamBatch) < 32000, "kernel parameter size");
+  AdamBatch a;
+  int64_t mx = 1;
+  for (int k = 0; k < n_maps; ++k) {
+    const lgs_adam_map& M = maps[k];
+    float* p[4] = {M.mean, M.quat, M.log_scale, M.logit};
+    float* g[4] = {M.grad.d_mean, M.grad.d_quat, M.grad.d_log_scale, M.grad.d_opacity_logit};
+    const int64_t cnt[4] = {3 * M.n, 4 * M.n, 2 * M.n, M.n};
+    const int64_t off[4] = {0, 3 * M.n, 7 * M.n, 9 * M.n};
+    for (int q = 0; q < 4; ++q) {
+      a.p[4 * k + q] = p[q];
+      a.g[4 * k + q] = g[q];
+      a.m[4 * k + q] = M.m_state + off[q];
+      a.v[4 * k + q] = M.v_state + off[q];
+      a.n[4 * k + q] = cnt[q];
+      a.lr[4 * k + q] = M.lr[q];
+      if (cnt[q] > mx) mx = cnt[q];
+    }
+    a.c1[k] = static_cast<float>(1.0 / (1.0 - pow(static_cast<double>(b1), static_cast<double>(M.step))));
+    a.c2[k] = static_cast<float>(1.0 / (1.0 - pow(static_cast<double>(b2), static_cast<double>(M.step))));
+  }
+  int64_t blocks = (mx + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_adam_batch<<<dim3(static_cast<unsigned>(blocks), 4 * n_maps), 256, 0, s>>>(a, b1, b2, eps, zero_grad);
+  return cudaGetLastError();
+}
+
 }  // namespace lgs

@@ -196,28 +196,36 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       int cnt = 0;
       if (!__all_sync(0xffffffffu, done)) cnt = warp_list(s_box, nb, wb, s_list[wid]);
       if (!done) {
-        for (int k = 0; k < cnt; ++k) {
-          const int j = s_list[wid][k];
-          ++evals;
-          Eval e;
-          eval_pair(s_r0[j], s_r1[j], s_r2[j], s_al[j], dx, dy, dz, e);
-          if (!e.valid) continue;
-          const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.a));
-          if (Tn < 1e-4f) {
-            done = true;
-            stop_at = static_cast<int>(b0 - tc.start) + j + 1;
-            break;
+        for (int k = 0; k < cnt; k += 2) {
+          const int jj[2] = {s_list[wid][k], k + 1 < cnt ? s_list[wid][k + 1] : s_list[wid][k]};
+          Eval ee[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) eval_pair(s_r0[jj[q]], s_r1[jj[q]], s_r2[jj[q]], s_al[jj[q]], dx, dy, dz, ee[q]);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            if (done || k + q >= cnt) break;
+            const int j = jj[q];
+            const Eval& e = ee[q];
+            ++evals;
+            if (!e.valid) continue;
+            const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.a));
+            if (Tn < 1e-4f) {
+              done = true;
+              stop_at = static_cast<int>(b0 - tc.start) + j + 1;
+              break;
+            }
+            const float w = e.a * T;
+            const float ws = e.den > 0.f ? -w : w;
+            A += w;
+            St = fmaf(w, e.t, St);
+            Sx = fmaf(ws, s_r0[j].x, Sx);
+            Sy = fmaf(ws, s_r0[j].y, Sy);
+            Sz = fmaf(ws, s_r0[j].z, Sz);
+            T = Tn;
+            last = static_cast<int>(b0 - tc.start) + j + 1;
+            ++contrib;
           }
-          const float w = e.a * T;
-          const float ws = e.den > 0.f ? -w : w;
-          A += w;
-          St = fmaf(w, e.t, St);
-          Sx = fmaf(ws, s_r0[j].x, Sx);
-          Sy = fmaf(ws, s_r0[j].y, Sy);
-          Sz = fmaf(ws, s_r0[j].z, Sz);
-          T = Tn;
-          last = static_cast<int>(b0 - tc.start) + j + 1;
-          ++contrib;
+          if (done) break;
         }
       }
     }

@@ -64,6 +64,12 @@ class lgs_loss_params(ctypes.Structure):
                 ("lambda_s", ctypes.c_float), ("s_max", ctypes.c_float)]
 
 
+class lgs_adam_map(ctypes.Structure):
+    _fields_ = [("mean", P), ("quat", P), ("log_scale", P), ("logit", P), ("grad", lgs_surfel_grad),
+                ("m_state", P), ("v_state", P), ("n", ctypes.c_int64), ("step", ctypes.c_int64),
+                ("lr", ctypes.c_float * 4)]
+
+
 class lgs_tuning(ctypes.Structure):
     _fields_ = [("fwd_batch", ctypes.c_int32), ("bwd_batch", ctypes.c_int32), ("group", ctypes.c_int32),
                 ("persistent", ctypes.c_int32)]
@@ -74,7 +80,7 @@ EXPORTS = [
     "lgs_session_set_workspace", "lgs_session_status", "lgs_session_pair_count", "lgs_session_counters",
     "lgs_session_bins", "lgs_session_read_bins", "lgs_bin_sort", "lgs_render_fwd", "lgs_render_bwd", "lgs_loss", "lgs_bin_sort_batch",
     "lgs_render_fwd_batch", "lgs_render_bwd_batch", "lgs_loss_batch", "lgs_session_set_tuning", "lgs_adam_step",
-    "lgs_session_set_timing", "lgs_session_kernel_times", "lgs_image_loss_noalloc",
+    "lgs_session_set_timing", "lgs_session_kernel_times", "lgs_image_loss_noalloc", "lgs_adam_step_batch",
     "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version",
 ]
 
@@ -113,6 +119,7 @@ def load():
         "lgs_session_set_timing": ([P, i32], S),
         "lgs_session_kernel_times": ([P, P, P], S),
         "lgs_image_loss_noalloc": ([P, P, i32, P, P, P, P, P, P], S),
+        "lgs_adam_step_batch": ([P, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, P], S),
         "lgs_adam_step": ([P, P, P, P, P, P, P, i64, i64, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            i32, P], S),
         "lgs_status_string": ([i32], ctypes.c_char_p),
@@ -281,7 +288,7 @@ def lgs_loss(h, surfels, frames, fwd, targets, params, grads_out, grad, loss_out
                            _ref(grad) if grad is not None else None, P(loss_out_ptr), P(stream)))
 
 
-def lgs_session_set_tuning(h, fwd_batch: int = 64, bwd_batch: int = 0, group: int = 2, persistent: int = 0):
+def lgs_session_set_tuning(h, fwd_batch: int = 128, bwd_batch: int = 0, group: int = 2, persistent: int = 0):
     _check(load().lgs_session_set_tuning(h, _ref(lgs_tuning(fwd_batch, bwd_batch, group, persistent))))
 
 
@@ -429,3 +436,9 @@ def lgs_image_loss_noalloc(shapes, fwd, targets, params, grads_out, loss_out_ptr
     Ws = (ctypes.c_int32 * n)(*[w for _, w in shapes])
     _check(load().lgs_image_loss_noalloc(Hs, Ws, n, _arr(lgs_fwd_out, fwd), _arr(lgs_target, targets), _ref(params),
                                          _arr(lgs_fwd_grad_out, grads_out), loss_out_ptr, stream))
+
+
+def lgs_adam_step_batch(items, beta1: float, beta2: float, eps: float, zero_grad: bool, stream):
+    """items: list of lgs_adam_map."""
+    _check(load().lgs_adam_step_batch(_arr(lgs_adam_map, items), len(items), beta1, beta2, eps,
+                                      1 if zero_grad else 0, stream))

@@ -9,6 +9,7 @@ Theta = {mu, q, s~, alpha}).
 """
 from __future__ import annotations
 
+import ctypes
 from dataclasses import dataclass
 
 import numpy as np
@@ -43,9 +44,9 @@ def target_tensors(tgt, device="cuda"):
 
 # Compositing knobs (lgs_tuning) and tile shape the benchmark runs with: the
 # 200k-surfel 128 x 1024 street frame renders fastest with 8 x 8 tiles, the
-# forward staged in 64-record shared-memory batches and the backward as an
+# forward staged in 128-record shared-memory batches and the backward as an
 # independent walk per warp taking two hits at a time.
-DEFAULT_TUNING = dict(fwd_batch=64, bwd_batch=0, group=2, persistent=0)
+DEFAULT_TUNING = dict(fwd_batch=128, bwd_batch=0, group=2, persistent=0)
 DEFAULT_TILE = (8, 8)
 
 
@@ -63,14 +64,15 @@ class Rasterizer:
         self.loss_params = loss or LossParams()
         self.set_frames(frames, frame_map)
 
-    def set_frames(self, frames, frame_map=None):
+    def set_frames(self, frames, frame_map=None, outs=None, ups=None):
+        """Frames of the next calls; ``outs`` / ``ups`` (per frame: FwdBuffers
+        and the (dA, dS_t, dS_n) planes) may be supplied to avoid allocation."""
         self.frames = list(frames)
         self.frame_map = list(frame_map) if frame_map is not None else [0] * len(self.frames)
         self.fr = [lib.frame_struct(f) for f in self.frames]
-        self.out = [lib.alloc_fwd(f, self.device) for f in self.frames]
+        self.out = list(outs) if outs is not None else [lib.alloc_fwd(f, self.device) for f in self.frames]
+        self.up = list(ups) if ups is not None else [upstream_planes(f, self.device) for f in self.frames]
         z = dict(dtype=torch.float32, device=self.device)
-        self.up = [(torch.zeros(f.H, f.W, **z), torch.zeros(f.H, f.W, **z), torch.zeros(3, f.H, f.W, **z))
-                   for f in self.frames]
         self.n_maps = max(self.frame_map) + 1
         self.loss_out = torch.zeros(1 + 3 * len(self.frames) + self.n_maps, **z)
 
@@ -131,6 +133,25 @@ class Rasterizer:
 
     def counters(self):
         return lib.lgs_session_counters(self.session.handle)
+
+
+def upstream_planes(frame, device):
+    z = dict(dtype=torch.float32, device=device)
+    return (torch.zeros(frame.H, frame.W, **z), torch.zeros(frame.H, frame.W, **z),
+            torch.zeros(3, frame.H, frame.W, **z))
+
+
+def adam_step_batch(items, betas=(0.9, 0.999), eps: float = 1e-15, zero_grad: bool = True, stream=None):
+    """One fused Adam launch over several maps: items = [(params, grads,
+    m_state, v_state, step, lr)] with each map's own step count."""
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    maps = []
+    for params, grads, m, v, step, lr in items:
+        maps.append(lib.lgs_adam_map(params[0].data_ptr(), params[1].data_ptr(), params[2].data_ptr(),
+                                     params[3].data_ptr(), lib.grad_struct(*grads), m.data_ptr(), v.data_ptr(),
+                                     int(params[0].shape[0]), int(step), (ctypes.c_float * 4)(*lr)))
+    for k in range(0, len(maps), 64):
+        lib.lgs_adam_step_batch(maps[k:k + 64], betas[0], betas[1], eps, zero_grad, s)
 
 
 def adam_step(params, grads, m_state, v_state, step: int, lr=(1e-3, 1e-3, 5e-3, 5e-3), betas=(0.9, 0.999),

@@ -48,6 +48,7 @@ class Request:
     start: float | None = None
     finish: float | None = None
     losses: list = dataclasses.field(default_factory=list)
+    buffers: object = None      # device buffers while active: (target tensors, FwdBuffers, upstream planes)
 
 
 class MapSession:
@@ -100,26 +101,39 @@ class Server:
 
     # -- one tick -------------------------------------------------------------
     def _tick(self, active):
+        """One iteration of every active request: one call per stage over their
+        frames, a capacity check at the tick's single synchronisation, one
+        fused Adam launch over their maps.  Returns the per-map losses."""
+        from . import lib
+        for r in active:
+            if r.buffers is None:      # device buffers for the request's lifetime
+                r.buffers = (render.target_tensors(r.target, self.device), lib.alloc_fwd(r.frame, self.device),
+                             render.upstream_planes(r.frame, self.device))
         frames = [r.frame for r in active]
+        fmap = list(range(len(active)))
+        outs = [r.buffers[1] for r in active]
+        ups = [r.buffers[2] for r in active]
         if self.rast is None:
-            self.rast = render.Rasterizer(frames, frame_map=list(range(len(active))), device=self.device.index,
-                                          tuning=self.tuning)
-        else:
-            self.rast.set_frames(frames, list(range(len(active))))
+            self.rast = render.Rasterizer(frames, frame_map=fmap, device=self.device.index, tuning=self.tuning)
+        self.rast.set_frames(frames, fmap, outs=outs, ups=ups)
         maps = [self.sessions[r.session] for r in active]
         params = [s.params for s in maps]
-        grads = [s.grads for s in maps]
-        targets = [render.target_tensors(r.target, self.device) if not hasattr(r, "_t") else r._t for r in active]
-        for r, t in zip(active, targets):
-            r._t = t
-        for g in grads:
-            for x in g:
-                x.zero_()
-        out = self.rast.step(params, targets, grads, check=True)
+        grads = [s.grads for s in maps]      # zero: the previous Adam step cleared them
+        targets = [r.buffers[0] for r in active]
+        out = self.rast.step(params, targets, grads, check=False)
+        torch.cuda.synchronize(self.device)
+        st, _ = lib.lgs_session_status(self.rast.session.handle)
+        if st == lib.LGS_ERR_CAPACITY:       # grow the workspace and redo the tick
+            for g in grads:
+                for x in g:
+                    x.zero_()
+            out = self.rast.step(params, targets, grads, check=True)
+        F = len(active)
+        losses = out[1 + 3 * F: 1 + 3 * F + F].cpu().numpy()
         for s in maps:
             s.t += 1
-            render.adam_step(s.params, s.grads, s.m, s.v, s.t, lr=self.lr, zero_grad=False)
-        return out
+        render.adam_step_batch([(s.params, s.grads, s.m, s.v, s.t, self.lr) for s in maps], zero_grad=True)
+        return losses
 
     # -- the loop ---------------------------------------------------------------
     def run(self, requests):
@@ -156,10 +170,7 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(pending[0].arrival - now, 0.002)))
                 continue
-            out = self._tick(active)
-            F = len(active)
-            torch.cuda.synchronize(self.device)
-            L = out[1 + 3 * F: 1 + 3 * F + F].cpu().numpy()     # per-map loss (one frame per map)
+            L = self._tick(active)     # per-map loss (one frame per map)
             now = time.perf_counter() - t0
             still = []
             for r, l in zip(active, L):
@@ -169,7 +180,7 @@ class Server:
                     r.finish = now
                     done.append(r)
                     busy.discard(r.session)
-                    del r._t
+                    r.buffers = None
                 else:
                     still.append(r)
             active = still

@@ -51,3 +51,5 @@ def test_argument_errors_without_device(lgslib):
     assert L.lgs_session_workspace_size(None, 10, None, 1, 10, None) == 1
     assert L.lgs_session_set_workspace(None, None, 0) == 1
     assert L.lgs_adam_step(None, None, None, None, None, None, None, -1, 1, None, 0.9, 0.999, 1e-15, 0, None) == 1
+    assert L.lgs_adam_step_batch(None, 1, 0.9, 0.999, 1e-15, 0, None) == 1
+    assert L.lgs_adam_step_batch(None, 0, 0.9, 0.999, 1e-15, 0, None) == 1
