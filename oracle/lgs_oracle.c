@@ -1182,6 +1182,100 @@ double lgso_loss_image(const double* A, const double* St, const double* Sn, cons
     return scale * (Ld + lam_alpha * La + lam_n * lam_ng * Ln);
 }
 
+/* Second term of Eq. normalloss: the surface normal N_surf "computed from
+ * the rendered depth" (Sec. 3.4), compared with the rendered normal Nh by the
+ * cosine loss over Omega_D.  The paper gives no formula for N_surf; the
+ * reading taken here:
+ *   X_p    = Dh_p d_p, the rendered range of pixel p back-projected along its
+ *            ray (sensor frame, Dh = S_t/(A+1e-6));
+ *   e_c    = X(r, c+1 mod W) - X(r, c)   azimuth neighbour (the image wraps at
+ *                                        2 pi, so column W-1 pairs with 0);
+ *   e_r    = X(r+1, c) - X(r, c)         next row (lower elevation);
+ *   N_surf = (e_c x e_r) / sqrt(|e_c x e_r|^2 + 1e-12); for a surface seen
+ *            from the front this points back at the sensor, like Nh;
+ *   L_ns   = (1/|Omega_D|) sum over pixels p with D > 0 at p and at both
+ *            neighbours (the last row has none) of (1 - Nh_p . N_surf_p),
+ *            normalised by |Omega_D| as Eq. normalloss writes it.
+ * The gradient flows into Nh_p and, through N_surf, into the rendered ranges
+ * of the three pixels.  Accumulates (+=) scale * lam * dL_ns/d(A, S_t, S_n)
+ * (lam = lambda_n lambda_{n,s}) and returns the unscaled L_ns. */
+static void cross3(const double* a, const double* b, double* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+double lgso_surf_normal_loss(const double* A, const double* St, const double* Sn, const float* D, int H, int W,
+                             double emin, double emax, double lam, double scale, double* gA, double* gSt,
+                             double* gSn)
+{
+    const int64_t HW = (int64_t)H * W;
+    int64_t nd = 0;
+    for (int64_t p = 0; p < HW; ++p) nd += D[p] > 0.0f;
+    if (nd == 0 || H < 2) return 0.0;
+    frame64 F;
+    const double ident[12] = { 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0 };
+    make_frame(&F, H, W, 1, 1, emin, emax, ident);
+    double* ray = (double*)malloc(sizeof(double) * 3 * HW);
+    double* X = (double*)malloc(sizeof(double) * 3 * HW);
+    double* gX = (double*)calloc(3 * HW, sizeof(double));
+    for (int r = 0; r < H; ++r)
+        for (int c = 0; c < W; ++c) {
+            int64_t p = (int64_t)r * W + c;
+            pixel_ray(&F, r, c, ray + 3 * p);
+            double Dh = St[p] / (A[p] + EPS_A);
+            for (int k = 0; k < 3; ++k) X[3 * p + k] = Dh * ray[3 * p + k];
+        }
+    const double k = lam / (double)nd;
+    double sum = 0.0;
+    for (int r = 0; r + 1 < H; ++r)
+        for (int c = 0; c < W; ++c) {
+            int64_t p = (int64_t)r * W + c, pr = (int64_t)r * W + (c + 1) % W, pb = p + W;
+            if (!(D[p] > 0.0f && D[pr] > 0.0f && D[pb] > 0.0f)) continue;
+            double ec[3], er[3], cr[3];
+            for (int q = 0; q < 3; ++q) {
+                ec[q] = X[3 * pr + q] - X[3 * p + q];
+                er[q] = X[3 * pb + q] - X[3 * p + q];
+            }
+            cross3(ec, er, cr);
+            double mc = sqrt(dot3(cr, cr) + EPS_N * EPS_N);
+            double ns[3] = { cr[0] / mc, cr[1] / mc, cr[2] / mc };
+            double sn[3] = { Sn[p], Sn[HW + p], Sn[2 * HW + p] };
+            double m = sqrt(dot3(sn, sn) + EPS_N * EPS_N);
+            double nh[3] = { sn[0] / m, sn[1] / m, sn[2] / m };
+            sum += 1.0 - dot3(nh, ns);
+            /* dL/dNh = -k N_surf through Nh = S_n/m */
+            double g[3] = { -k * ns[0], -k * ns[1], -k * ns[2] };
+            double sg = dot3(sn, g);
+            for (int q = 0; q < 3; ++q) gSn[q * HW + p] += scale * (g[q] / m - sn[q] * sg / (m * m * m));
+            /* dL/dN_surf = -k Nh through N_surf = cr/mc, then cr = e_c x e_r:
+               dL/de_c = e_r x gcr, dL/de_r = gcr x e_c */
+            double gc[3] = { -k * nh[0], -k * nh[1], -k * nh[2] };
+            double cg = dot3(cr, gc);
+            double gcr[3] = { gc[0] / mc - cr[0] * cg / (mc * mc * mc), gc[1] / mc - cr[1] * cg / (mc * mc * mc),
+                              gc[2] / mc - cr[2] * cg / (mc * mc * mc) };
+            double gec[3], ger[3];
+            cross3(er, gcr, gec);
+            cross3(gcr, ec, ger);
+            for (int q = 0; q < 3; ++q) {
+                gX[3 * pr + q] += gec[q];
+                gX[3 * pb + q] += ger[q];
+                gX[3 * p + q] -= gec[q] + ger[q];
+            }
+        }
+    /* X = Dh d, Dh = S_t/(A+eps) */
+    for (int64_t p = 0; p < HW; ++p) {
+        double gD = dot3(gX + 3 * p, ray + 3 * p);
+        if (gD == 0.0) continue;
+        double a = A[p] + EPS_A;
+        gSt[p] += scale * gD / a;
+        gA[p] += scale * (-gD * St[p] / (a * a));
+    }
+    free(ray); free(X); free(gX);
+    return sum / (double)nd;
+}
+
 /* L_scale = sum_i max(0, max(s_i0, s_i1) - s_max), s = exp(log-scale); returns
  * lam_s L_scale and accumulates lam_s dL_scale/d(log-scale) (+=).  For equal
  * scales the subgradient goes to the first component. */

@@ -26,12 +26,14 @@ _lib = None
 _lock = threading.Lock()
 
 # Loss weights of the paper's implementation details (Sec. 4.1): lambda_alpha,
-# lambda_n, lambda_s, lambda_{n,g}; lambda_{n,s} multiplies the N_surf term,
-# which is off on this path.
+# lambda_n, lambda_s, lambda_{n,g}, lambda_{n,s}.  The N_surf term (weight
+# lambda_{n,s}) is switched on only once densification has begun (Sec. 3.4),
+# so loss_image takes it as an argument that defaults to off.
 LAMBDA_ALPHA = 0.1
 LAMBDA_N = 1.0
 LAMBDA_S = 10.0
 LAMBDA_NG = 0.05
+LAMBDA_NS = 0.01
 S_MAX = 1.0
 
 
@@ -72,6 +74,8 @@ def _load():
                                         P, P, P, P, P, P, P, P, P, i32]
         lib.lgso_loss_image.argtypes = [P, P, P, P, P, i64, f64, f64, f64, f64, P, P, P, P]
         lib.lgso_loss_image.restype = f64
+        lib.lgso_surf_normal_loss.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, f64, f64, f64, f64, P, P, P]
+        lib.lgso_surf_normal_loss.restype = f64
         lib.lgso_scale_reg.argtypes = [P, i64, f64, f64, P]
         lib.lgso_scale_reg.restype = f64
         _lib = lib
@@ -208,15 +212,27 @@ def render_bwd(surfels, frame, ranges, vals, gA, gSt, gSn, params64=None, grads=
     return grads
 
 
-def loss_image(fwd, D, Ng, lam_alpha=LAMBDA_ALPHA, lam_n=LAMBDA_N, lam_ng=LAMBDA_NG, scale=1.0):
-    """Image terms of the mapping loss and their gradients w.r.t. (A, S_t, S_n)."""
+def loss_image(fwd, D, Ng, lam_alpha=LAMBDA_ALPHA, lam_n=LAMBDA_N, lam_ng=LAMBDA_NG, scale=1.0, lam_ns=0.0,
+               frame=None):
+    """Image terms of the mapping loss and their gradients w.r.t. (A, S_t, S_n).
+    terms = (L_depth, L_alpha, L_ng, L_ns); the N_surf term (needs ``frame``
+    for the pixel rays) is included when lam_ns != 0."""
     lib = _load()
     H, W = D.shape
     npix = H * W
-    gA = np.zeros(npix); gSt = np.zeros(npix); gSn = np.zeros(3 * npix); terms = np.zeros(3)
-    L = lib.lgso_loss_image(_p(_c(fwd["A"], np.float64)), _p(_c(fwd["S_t"], np.float64)),
-                            _p(_c(fwd["S_n"], np.float64)), _p(_c(D, np.float32)), _p(_c(Ng, np.float32)),
+    gA = np.zeros(npix); gSt = np.zeros(npix); gSn = np.zeros(3 * npix); terms = np.zeros(4)
+    A = _c(fwd["A"], np.float64); St = _c(fwd["S_t"], np.float64); Sn = _c(fwd["S_n"], np.float64)
+    Dm = _c(D, np.float32)
+    L = lib.lgso_loss_image(_p(A), _p(St), _p(Sn), _p(Dm), _p(_c(Ng, np.float32)),
                             npix, lam_alpha, lam_n, lam_ng, scale, _p(gA), _p(gSt), _p(gSn), _p(terms))
+    if lam_ns != 0.0:
+        if frame is None:
+            raise ValueError("the N_surf term needs the frame (pixel rays)")
+        lns = lib.lgso_surf_normal_loss(_p(A), _p(St), _p(Sn), _p(Dm), H, W, float(np.float32(frame.elev_min)),
+                                        float(np.float32(frame.elev_max)), lam_n * lam_ns, scale, _p(gA), _p(gSt),
+                                        _p(gSn))
+        terms[3] = lns
+        L += scale * lam_n * lam_ns * lns
     return L, dict(dA=gA.reshape(H, W), dS_t=gSt.reshape(H, W), dS_n=gSn.reshape(3, H, W)), terms
 
 
@@ -228,7 +244,7 @@ def scale_reg(log_scale, s_max=S_MAX, lam_s=LAMBDA_S, dls=None):
 
 def forward_backward(surfels, frames, targets, lam_alpha=LAMBDA_ALPHA, lam_n=LAMBDA_N,
                      lam_ng=LAMBDA_NG, lam_s=LAMBDA_S, s_max=S_MAX, params64=None, nthreads: int = 0,
-                     brute: bool = False):
+                     brute: bool = False, lam_ns: float = 0.0):
     """The whole step for a window of frames: per frame bin, render, image
     loss (averaged over frames), backward; plus lam_s L_scale once.
     ``targets`` is a list of (D, Ng).  Returns (L, per-frame forwards, grads, bins)."""
@@ -245,7 +261,7 @@ def forward_backward(surfels, frames, targets, lam_alpha=LAMBDA_ALPHA, lam_n=LAM
         else:
             b = bin_frame(surfels, frame)
         fw = render_fwd(surfels, frame, b["ranges"], b["vals"], params64, nthreads)
-        Lf, g, _ = loss_image(fw, D, Ng, lam_alpha, lam_n, lam_ng, scale=1.0 / F)
+        Lf, g, _ = loss_image(fw, D, Ng, lam_alpha, lam_n, lam_ng, scale=1.0 / F, lam_ns=lam_ns, frame=frame)
         render_bwd(surfels, frame, b["ranges"], b["vals"], g["dA"], g["dS_t"], g["dS_n"], params64,
                    grads, nthreads)
         L += Lf

@@ -13,6 +13,8 @@ optimisation, Eqs. depthloss / normalloss / scaleloss / totalloss):
   P6 analytic gradient == central finite differences (steps 1e-6 and 1e-4)
   P7 special-case derivatives of P1
   P8 loss closed forms and mask invariances
+  P9 the N_surf term: plane closed form (orientation, masks, azimuth wrap,
+     mean over Omega_D), column-shift invariance, finite differences
 and the binary32 polynomial exp / sin / cos used by binning.
 """
 import math
@@ -390,6 +392,113 @@ def test_p8_scale_regulariser(oracle):
     d = np.zeros((4, 2))
     oracle.scale_reg(np.log(s), s_max=1.0, lam_s=10.0, dls=d)
     assert np.allclose(d, [[0, 0], [13.0, 0], [0, 17.5], [20.0, 0]])
+
+
+# --------------------------------------------------------------------------
+# P9: the surface-normal term of Eq. normalloss (N_surf from rendered depth)
+# --------------------------------------------------------------------------
+def _plane_image(frame, m, rho, A0=0.85):
+    """Rendered planes of the plane {X : m.X = rho} (m unit, rho > 0) seen
+    from the origin: D_hat = rho / (m.d) exactly where m.d > 0.2, else no
+    return.  Returns (A, S_t, valid, rays)."""
+    H, W = frame.H, frame.W
+    d = np.array([[pixel_dir(frame, r, c) for c in range(W)] for r in range(H)])   # [H, W, 3]
+    md = d @ m
+    valid = md > 0.2
+    t = np.where(valid, rho / np.where(valid, md, 1.0), 0.0)
+    A = np.full((H, W), A0)
+    return A, t * (A + EPS), valid, t
+
+
+def _perp(v, seed):
+    rng = np.random.default_rng(seed)
+    p = np.cross(v, rng.normal(size=v.shape))
+    return p / np.linalg.norm(p, axis=-1, keepdims=True)
+
+
+def test_p9_surface_normal_of_a_plane(oracle):
+    """Back-projected rendered ranges of a plane are coplanar, so N_surf is
+    the plane's normal turned towards the sensor; with N_hat at a known angle
+    theta_p from it, L_ns = sum over the pixels that have a term (a return
+    there, at the next column -- column W-1 pairs with column 0 -- and at the
+    next row) of (1 - cos theta_p), divided by |Omega_D|."""
+    frame = scenes.Frame(6, 32, 16, 16, -0.35, 0.35)
+    H, W = frame.H, frame.W
+    m = np.array([1.0, 0.15, -0.25]); m /= np.linalg.norm(m)
+    A, St, valid, t = _plane_image(frame, m, 5.0)
+    D = np.where(valid, t, 0.0).astype(np.float32)
+    assert valid[:, 0].all() and valid[:, W - 1].all()        # the seam lies on the plane
+    D[2, 5] = 0.0; D[4, 30] = 0.0                               # holes
+    ok = D > 0
+    rng = np.random.default_rng(4)
+    theta = rng.uniform(0.0, 0.6, (H, W))
+    theta[1, W - 1] = math.pi                                   # one normal pointing away
+    perp = _perp(np.broadcast_to(m, (H, W, 3)), 5)
+    nh = np.cos(theta)[..., None] * (-m) + np.sin(theta)[..., None] * perp
+    Sn = 3.0 * nh.transpose(2, 0, 1)
+    N = np.zeros((3, H, W), np.float32)                         # no G-ICP normals
+    has = np.zeros((H, W), bool)
+    for r in range(H - 1):
+        for c in range(W):
+            has[r, c] = ok[r, c] and ok[r, (c + 1) % W] and ok[r + 1, c]
+    assert has[1, W - 1] and not has[H - 1].any() and not has[2, 4] and not has[1, 5]
+    expect = (1.0 - np.cos(theta))[has].sum() / ok.sum()
+    fw = dict(A=A, S_t=St, S_n=Sn)
+    L0, _, t0 = oracle.loss_image(fw, D, N)
+    L, _, terms = oracle.loss_image(fw, D, N, lam_ns=0.01, frame=frame)
+    assert t0[3] == 0.0
+    assert terms[3] == pytest.approx(expect, rel=1e-9)
+    assert L - L0 == pytest.approx(0.01 * expect, rel=1e-6)
+    # N_hat facing the sensor everywhere: no loss
+    _, _, tz = oracle.loss_image(dict(A=A, S_t=St, S_n=np.broadcast_to(-m[:, None, None], (3, H, W))), D, N,
+                                 lam_ns=1.0, frame=frame)
+    assert abs(tz[3]) < 1e-12
+
+
+def test_p9_column_shift_invariance(oracle):
+    """Rolling every plane by W/4 columns while turning S_n by +90 degrees
+    about z is the same scene turned by 90 degrees: the same L_ns, and the
+    gradients roll with it (the wrap at 2 pi is a pixel pair like any other)."""
+    frame = scenes.Frame(5, 16, 16, 16, -0.4, 0.3)
+    rng = np.random.default_rng(6)
+    H, W = frame.H, frame.W
+    A = rng.uniform(0.3, 0.95, (H, W)); St = rng.uniform(3, 8, (H, W)) * (A + EPS)
+    Sn = rng.normal(size=(3, H, W))
+    D = rng.uniform(3, 8, (H, W)).astype(np.float32); D[1, 3] = 0.0; D[3, 15] = 0.0
+    N = np.zeros((3, H, W), np.float32)
+    L, g, t = oracle.loss_image(dict(A=A, S_t=St, S_n=Sn), D, N, lam_ns=1.0, frame=frame)
+    k = W // 4
+    roll = lambda x: np.roll(x, k, axis=-1)
+    Sn2 = np.stack([-Sn[1], Sn[0], Sn[2]])
+    L2, g2, t2 = oracle.loss_image(dict(A=roll(A), S_t=roll(St), S_n=roll(Sn2)), roll(D), N, lam_ns=1.0,
+                                   frame=frame)
+    assert t2[3] == pytest.approx(t[3], rel=1e-12)
+    assert np.allclose(g2["dA"], roll(g["dA"]), rtol=1e-9, atol=1e-14)
+    assert np.allclose(g2["dS_t"], roll(g["dS_t"]), rtol=1e-9, atol=1e-14)
+    gsn = np.stack([-g["dS_n"][1], g["dS_n"][0], g["dS_n"][2]])
+    assert np.allclose(g2["dS_n"], roll(gsn), rtol=1e-9, atol=1e-14)
+
+
+def test_p9_surface_normal_gradient_matches_finite_differences(oracle):
+    frame = scenes.Frame(4, 6, 16, 16, -0.5, 0.5)
+    rng = np.random.default_rng(7)
+    H, W = frame.H, frame.W
+    A = rng.uniform(0.3, 0.95, (H, W)); St = rng.uniform(3, 8, (H, W)) * (A + EPS)
+    Sn = rng.normal(size=(3, H, W))
+    D = (St / (A + EPS) + rng.choice([-1.0, 1.0], (H, W)) * rng.uniform(0.5, 1.0, (H, W))).astype(np.float32)
+    D[2, 1] = 0.0
+    N = rng.normal(size=(3, H, W)).astype(np.float32)
+    f = lambda a, st, sn: oracle.loss_image(dict(A=a, S_t=st, S_n=sn), D, N, lam_ns=0.5, frame=frame)
+    _, g, terms = f(A, St, Sn)
+    assert terms[3] > 0
+    h = 1e-6
+    for name, arr in (("dA", A), ("dS_t", St), ("dS_n", Sn)):
+        for idx in np.ndindex(arr.shape):
+            p, m = arr.copy(), arr.copy()
+            p[idx] += h; m[idx] -= h
+            sel = lambda x: (x if name == "dA" else A, x if name == "dS_t" else St, x if name == "dS_n" else Sn)
+            fd = (f(*sel(p))[0] - f(*sel(m))[0]) / (2 * h)
+            assert g[name][idx] == pytest.approx(fd, rel=1e-5, abs=1e-8), (name, idx)
 
 
 def test_oracle_constants(oracle):
