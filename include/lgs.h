@@ -149,7 +149,12 @@ typedef struct {
     float lambda_ng;     /* 0.05 */
     float lambda_s;      /* 10.0 */
     float s_max;         /* 1.0 m, threshold of the scale regulariser */
+    float lambda_ns;     /* 0.01 once densification has begun (Sec. 3.4), 0 = the
+                            N_surf term is off; must be >= 0 */
 } lgs_loss_params;
+
+/* Image terms per frame in a loss vector: L_depth, L_alpha, L_ng, L_ns. */
+#define LGS_LOSS_TERMS 4
 
 /* Tuning knobs of the compositing kernels (results do not depend on them). */
 typedef struct {
@@ -263,13 +268,22 @@ LGS_API lgs_status lgs_render_bwd(lgs_session s, const lgs_surfels* surfels, con
                           const lgs_surfel_grad* grad, void* stream);
 
 /* Mapping loss of a window of frames (Eqs. depthloss, normalloss, scaleloss,
- * totalloss): L = (1/F) sum_f [L_depth + la L_alpha + ln lng L_ng]_f
- * + ls L_scale.  Writes dL/d(A, S_t, S_n) per frame into grads_out[f]
+ * totalloss): L = (1/F) sum_f [L_depth + la L_alpha + ln (lng L_ng + lns L_ns)]_f
+ * + ls L_scale.  L_ns, the second term of Eq. normalloss, compares the
+ * rendered normal with N_surf, the normal of the rendered depth: with X the
+ * rendered range of a pixel back-projected along its ray, N_surf =
+ * normalise((X(r, c+1) - X(r, c)) x (X(r+1, c) - X(r, c))), columns wrapping
+ * at 2 pi; it is taken at pixels with a return and a rendered surface (A > 0)
+ * there and at both neighbours (not on the last row), averaged over the
+ * pixels with a return, and
+ * differentiated through both normals (into S_n of the pixel and S_t, A of
+ * the three pixels).  Writes dL/d(A, S_t, S_n) per frame into grads_out[f]
  * (overwritten), adds ls dL_scale/d(log
  * scale) into grad->d_log_scale (if grad != NULL), and stores on the device
- * loss_out[0] = L, loss_out[1+3f .. 3+3f] = (L_depth, L_alpha, L_ng) of
- * frame f, and loss_out[1 + 3 n_frames + m] = the part of L of map m
- * (loss_out has 1 + 3 n_frames + n_maps floats; one map for lgs_loss).
+ * loss_out[0] = L, loss_out[1 + 4f .. 4 + 4f] = (L_depth, L_alpha, L_ng,
+ * L_ns) of frame f, and loss_out[1 + 4 n_frames + m] = the part of L of map m
+ * (loss_out has 1 + LGS_LOSS_TERMS n_frames + n_maps floats; one map for
+ * lgs_loss).
  * With several frames per map the image terms of that map are averaged over
  * its frames, so a map's gradient does not depend on the other maps of a
  * batch. */
@@ -311,6 +325,8 @@ LGS_API lgs_status lgs_loss_batch(lgs_session s, const lgs_surfels* maps, int n_
  * n_frames floats); grads_out[f] (overwritten) as in lgs_loss.  H[f], W[f]:
  * host arrays of the frames' sizes; fwd, targets, grads_out: host arrays of
  * device pointers as in lgs_loss; params->lambda_s and s_max are unused.
+ * The call has no frame geometry (pixel rays), so it has no N_surf term:
+ * params->lambda_ns must be 0 (else LGS_ERR_INVALID_ARG).
  *
  * Nothing is allocated, by the library or by the caller: the scratch (per-CTA
  * partial sums, mask counts, a completion counter) is one static device array

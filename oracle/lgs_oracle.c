@@ -1193,12 +1193,33 @@ double lgso_loss_image(const double* A, const double* St, const double* Sn, cons
  *   e_r    = X(r+1, c) - X(r, c)         next row (lower elevation);
  *   N_surf = (e_c x e_r) / sqrt(|e_c x e_r|^2 + 1e-12); for a surface seen
  *            from the front this points back at the sensor, like Nh;
- *   L_ns   = (1/|Omega_D|) sum over pixels p with D > 0 at p and at both
- *            neighbours (the last row has none) of (1 - Nh_p . N_surf_p),
- *            normalised by |Omega_D| as Eq. normalloss writes it.
+ *   L_ns   = (1/|Omega_D|) sum over pixels p with D > 0 and a rendered
+ *            surface (A > 0, i.e. at least one composited surfel, so A >=
+ *            1/255) at p and at both neighbours (the last row has none) of
+ *            (1 - Nh_p . N_surf_p), normalised by |Omega_D| as Eq.
+ *            normalloss writes it.  Without the A > 0 condition a pixel
+ *            that renders nothing would enter with X = 0, and two such
+ *            neighbours make e_c parallel to e_r: N_surf = 0 and a gradient
+ *            of order 1/1e-6.
  * The gradient flows into Nh_p and, through N_surf, into the rendered ranges
  * of the three pixels.  Accumulates (+=) scale * lam * dL_ns/d(A, S_t, S_n)
- * (lam = lambda_n lambda_{n,s}) and returns the unscaled L_ns. */
+ * (lam = lambda_n lambda_{n,s}) and returns the unscaled L_ns.
+ *
+ * err (optional, [2 H W + 1]) receives what a binary32 evaluation of the
+ * same formulas may be off by (a first-order bound, not part of the loss):
+ * with u = 2^-24 and each back-projected X good to 3u |X|, e_c and e_r are
+ * off by 3u (|X| + |X'|), so the cross product c = e_c x e_r and N_surf are
+ * off relatively by about
+ *   rho = u (12 ((|X_p| + |X_R|) |e_r| + |e_c| (|X_p| + |X_B|)) / |c| + 8).
+ * The gradients project lam/|Omega_D| Nh (resp. N_surf) orthogonally to
+ * N_surf (resp. Nh): where the two normals nearly agree that is a small
+ * difference of large terms, so their error scales with the terms, not
+ * with the result: rho g0 (|e_c| + |e_r|) on dL/dX of each of the three
+ * pixels, g0 = lam / (|Omega_D| |c|), and rho lam / (|Omega_D| |S_n|) on
+ * dL/dS_n.  err[p] += scale times the first per term touching pixel p (a
+ * bound on the range gradient d.dL/dX_p, before the chain into A and S_t),
+ * err[HW + p] = scale times the second, err[2 HW] = (sum of rho over the
+ * terms) / |Omega_D| (on L_ns). */
 static void cross3(const double* a, const double* b, double* c)
 {
     c[0] = a[1] * b[2] - a[2] * b[1];
@@ -1208,7 +1229,7 @@ static void cross3(const double* a, const double* b, double* c)
 
 double lgso_surf_normal_loss(const double* A, const double* St, const double* Sn, const float* D, int H, int W,
                              double emin, double emax, double lam, double scale, double* gA, double* gSt,
-                             double* gSn)
+                             double* gSn, double* err)
 {
     const int64_t HW = (int64_t)H * W;
     int64_t nd = 0;
@@ -1220,6 +1241,8 @@ double lgso_surf_normal_loss(const double* A, const double* St, const double* Sn
     double* ray = (double*)malloc(sizeof(double) * 3 * HW);
     double* X = (double*)malloc(sizeof(double) * 3 * HW);
     double* gX = (double*)calloc(3 * HW, sizeof(double));
+    double* eX = (double*)calloc(HW, sizeof(double));      /* sum of rho |g| per pixel */
+    double rho_sum = 0.0;
     for (int r = 0; r < H; ++r)
         for (int c = 0; c < W; ++c) {
             int64_t p = (int64_t)r * W + c;
@@ -1233,6 +1256,7 @@ double lgso_surf_normal_loss(const double* A, const double* St, const double* Sn
         for (int c = 0; c < W; ++c) {
             int64_t p = (int64_t)r * W + c, pr = (int64_t)r * W + (c + 1) % W, pb = p + W;
             if (!(D[p] > 0.0f && D[pr] > 0.0f && D[pb] > 0.0f)) continue;
+            if (!(A[p] > 0.0 && A[pr] > 0.0 && A[pb] > 0.0)) continue;
             double ec[3], er[3], cr[3];
             for (int q = 0; q < 3; ++q) {
                 ec[q] = X[3 * pr + q] - X[3 * p + q];
@@ -1263,6 +1287,19 @@ double lgso_surf_normal_loss(const double* A, const double* St, const double* Sn
                 gX[3 * pb + q] += ger[q];
                 gX[3 * p + q] -= gec[q] + ger[q];
             }
+            if (err) {
+                const double U = 0x1p-24;
+                double xp = sqrt(dot3(X + 3 * p, X + 3 * p)), xr = sqrt(dot3(X + 3 * pr, X + 3 * pr));
+                double xb = sqrt(dot3(X + 3 * pb, X + 3 * pb));
+                double rho = U * (12.0 * ((xp + xr) * sqrt(dot3(er, er)) + sqrt(dot3(ec, ec)) * (xp + xb)) /
+                                  sqrt(dot3(cr, cr) + 1e-300) + 8.0);
+                double gx = rho * k / mc * (sqrt(dot3(ec, ec)) + sqrt(dot3(er, er)));
+                eX[pr] += gx;
+                eX[pb] += gx;
+                eX[p] += 2.0 * gx;
+                err[HW + p] = rho * scale * k / m;
+                rho_sum += rho;
+            }
         }
     /* X = Dh d, Dh = S_t/(A+eps) */
     for (int64_t p = 0; p < HW; ++p) {
@@ -1272,7 +1309,11 @@ double lgso_surf_normal_loss(const double* A, const double* St, const double* Sn
         gSt[p] += scale * gD / a;
         gA[p] += scale * (-gD * St[p] / (a * a));
     }
-    free(ray); free(X); free(gX);
+    if (err) {
+        for (int64_t p = 0; p < HW; ++p) err[p] = scale * eX[p];
+        err[2 * HW] = rho_sum / (double)nd;
+    }
+    free(ray); free(X); free(gX); free(eX);
     return sum / (double)nd;
 }
 

@@ -74,7 +74,8 @@ def _load():
                                         P, P, P, P, P, P, P, P, P, i32]
         lib.lgso_loss_image.argtypes = [P, P, P, P, P, i64, f64, f64, f64, f64, P, P, P, P]
         lib.lgso_loss_image.restype = f64
-        lib.lgso_surf_normal_loss.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, f64, f64, f64, f64, P, P, P]
+        lib.lgso_surf_normal_loss.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, f64, f64, f64, f64, P, P, P,
+                                              P]
         lib.lgso_surf_normal_loss.restype = f64
         lib.lgso_scale_reg.argtypes = [P, i64, f64, f64, P]
         lib.lgso_scale_reg.restype = f64
@@ -213,10 +214,12 @@ def render_bwd(surfels, frame, ranges, vals, gA, gSt, gSn, params64=None, grads=
 
 
 def loss_image(fwd, D, Ng, lam_alpha=LAMBDA_ALPHA, lam_n=LAMBDA_N, lam_ng=LAMBDA_NG, scale=1.0, lam_ns=0.0,
-               frame=None):
+               frame=None, ns_err=None):
     """Image terms of the mapping loss and their gradients w.r.t. (A, S_t, S_n).
     terms = (L_depth, L_alpha, L_ng, L_ns); the N_surf term (needs ``frame``
-    for the pixel rays) is included when lam_ns != 0."""
+    for the pixel rays) is included when lam_ns != 0.  ``ns_err`` (a dict)
+    receives the binary32 bounds of the N_surf term: dD (on dL/dDh per
+    pixel), dS_n (per pixel) and L_ns (on terms[3])."""
     lib = _load()
     H, W = D.shape
     npix = H * W
@@ -228,9 +231,13 @@ def loss_image(fwd, D, Ng, lam_alpha=LAMBDA_ALPHA, lam_n=LAMBDA_N, lam_ng=LAMBDA
     if lam_ns != 0.0:
         if frame is None:
             raise ValueError("the N_surf term needs the frame (pixel rays)")
+        err = np.zeros(2 * npix + 1) if ns_err is not None else None
         lns = lib.lgso_surf_normal_loss(_p(A), _p(St), _p(Sn), _p(Dm), H, W, float(np.float32(frame.elev_min)),
                                         float(np.float32(frame.elev_max)), lam_n * lam_ns, scale, _p(gA), _p(gSt),
-                                        _p(gSn))
+                                        _p(gSn), _p(err))
+        if err is not None:
+            ns_err.update(dD=err[:npix].reshape(H, W), dS_n=err[npix:2 * npix].reshape(H, W),
+                          L_ns=err[2 * npix])
         terms[3] = lns
         L += scale * lam_n * lam_ns * lns
     return L, dict(dA=gA.reshape(H, W), dS_t=gSt.reshape(H, W), dS_n=gSn.reshape(3, H, W)), terms

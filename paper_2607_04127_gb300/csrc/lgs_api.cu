@@ -757,6 +757,8 @@ lgs_status lgs_loss_batch(lgs_session s, const lgs_surfels* maps, int n_maps, co
       return fail(LGS_ERR_INVALID_ARG, "frame %d: NULL gradient output", f);
   }
   if (!(params->s_max > 0.f)) return fail(LGS_ERR_INVALID_ARG, "s_max must be positive");
+  if (!(params->lambda_ns >= 0.f && params->lambda_ns < 1e30f))
+    return fail(LGS_ERR_INVALID_ARG, "lambda_ns must be finite and >= 0");
   Desc& d = *s->desc;
   set_map_ptrs(d, maps, n_maps);
   for (int f = 0; f < n_frames; ++f) {
@@ -805,6 +807,8 @@ lgs_status lgs_image_loss_noalloc(const int32_t* H, const int32_t* W, int n_fram
   if (n_frames > LGS_NOALLOC_MAX_FRAMES)
     return fail(LGS_ERR_INVALID_ARG, "n_frames = %d exceeds the static scratch (at most %d frames per call)", n_frames,
                 LGS_NOALLOC_MAX_FRAMES);
+  if (params->lambda_ns != 0.f)
+    return fail(LGS_ERR_INVALID_ARG, "lambda_ns must be 0: this call has no frame geometry for N_surf");
   if (lgs::noalloc_scratch_bytes() != static_cast<size_t>(LGS_NOALLOC_SCRATCH_BYTES))
     return fail(LGS_ERR_INVALID_ARG, "scratch size mismatch between header and library");
   for (int f = 0; f < n_frames; ++f) {

@@ -208,6 +208,66 @@ __device__ __forceinline__ int2 mask_counts(const int* __restrict__ cpart, int f
   return make_int2(ta, tb);
 }
 
+// ---- the N_surf term of Eq. normalloss ---------------------------------------
+// X = Dh d: the rendered range of pixel (r, c) back-projected along its ray.
+__device__ __forceinline__ float3 backproject(const FrameDev& F, int r, int c, float3& d) {
+  const int p = r * F.W + c;
+  const float Dh = F.St[p] / (F.A[p] + 1e-6f);
+  pixel_ray(F, r, c, d.x, d.y, d.z);
+  return make_float3(Dh * d.x, Dh * d.y, Dh * d.z);
+}
+
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 axpy3(float a, float3 x, float3 y) {
+  return make_float3(a * x.x + y.x, a * x.y + y.y, a * x.z + y.z);
+}
+
+// The term of pixel (r, c): none on the last row, or unless the pixel, its
+// next column (wrapping at 2 pi) and its next row all have a return (D > 0)
+// and a rendered surface (A > 0: at least one composited surfel; a pixel that
+// renders nothing has X = 0, and two such neighbours would make e_c parallel
+// to e_r).  Otherwise
+// N_surf = normalise(e_c x e_r), e_c = X(r, c+1) - X(r, c), e_r = X(r+1, c) -
+// X(r, c); val = 1 - Nh . N_surf, and the gradients of k val w.r.t. X(r, c),
+// X(r, c+1), X(r+1, c) and S_n(r, c).
+struct NsTerm {
+  float val;
+  float3 gp, gr, gb, gsn;
+};
+
+__device__ bool ns_term(const FrameDev& F, int r, int c, float k, NsTerm& t) {
+  if (r < 0 || r + 1 >= F.H) return false;
+  const int W = F.W, HW = F.H * F.W;
+  const int cr = c + 1 == W ? 0 : c + 1;
+  const int p = r * W + c, pr = r * W + cr, pb = p + W;
+  if (!(F.D[p] > 0.f && F.D[pr] > 0.f && F.D[pb] > 0.f)) return false;
+  if (!(F.A[p] > 0.f && F.A[pr] > 0.f && F.A[pb] > 0.f)) return false;
+  float3 d;
+  const float3 X = backproject(F, r, c, d), XR = backproject(F, r, cr, d), XB = backproject(F, r + 1, c, d);
+  const float3 ec = make_float3(XR.x - X.x, XR.y - X.y, XR.z - X.z);
+  const float3 er = make_float3(XB.x - X.x, XB.y - X.y, XB.z - X.z);
+  const float3 cx = cross3(ec, er);
+  const float imc = 1.f / sqrtf(dot3(cx, cx) + 1e-12f);
+  const float3 ns = make_float3(cx.x * imc, cx.y * imc, cx.z * imc);
+  const float3 sn = make_float3(F.Sn[p], F.Sn[HW + p], F.Sn[2 * HW + p]);
+  const float im = 1.f / sqrtf(dot3(sn, sn) + 1e-12f);
+  const float3 nh = make_float3(sn.x * im, sn.y * im, sn.z * im);
+  t.val = dot3(nh, ns);   // the caller forms 1 - val in double
+  // dL/dNh = -k N_surf through Nh = S_n / |S_n|
+  const float3 g = make_float3(-k * ns.x, -k * ns.y, -k * ns.z);
+  t.gsn = axpy3(-dot3(sn, g) * im * im * im, sn, make_float3(g.x * im, g.y * im, g.z * im));
+  // dL/dN_surf = -k Nh through N_surf = c / |c|, c = e_c x e_r
+  const float3 gc = make_float3(-k * nh.x, -k * nh.y, -k * nh.z);
+  const float3 gcx = axpy3(-dot3(cx, gc) * imc * imc * imc, cx, make_float3(gc.x * imc, gc.y * imc, gc.z * imc));
+  t.gr = cross3(er, gcx);
+  t.gb = cross3(gcx, ec);
+  t.gp = make_float3(-(t.gr.x + t.gb.x), -(t.gr.y + t.gb.y), -(t.gr.z + t.gb.z));
+  return true;
+}
+
 // Rows y < n_frames: the image terms of frame y and its upstream gradient
 // planes; rows n_frames + m: the scale regulariser of map m.  The CTA that
 // finishes last reduces every partial sum in a fixed order (deterministic)
@@ -228,7 +288,8 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
     const float scale = 1.0f / static_cast<float>(D->m[F.map].n_frames);
     const float ind = nd > 0 ? 1.0f / static_cast<float>(nd) : 0.f;
     const float inn = nn > 0 ? 1.0f / static_cast<float>(nn) : 0.f;
-    double ld = 0.0, la = 0.0, ln = 0.0;
+    const float kns = P.lambda_n * P.lambda_ns * ind;
+    double ld = 0.0, la = 0.0, ln = 0.0, ls = 0.0;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
       float gA = 0.f, gSt = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
       const float Dm = F.D[p];
@@ -260,6 +321,27 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
           gy = scale * (g1 * im - sy * sg);
           gz = scale * (g2 * im - sz * sg);
         }
+        if (kns != 0.f) {
+          // this pixel's own term, and the terms of its left and upper
+          // neighbours, in which it is the next column / the next row
+          const int r = p / F.W, c = p - r * F.W;
+          float3 gX = make_float3(0.f, 0.f, 0.f);
+          NsTerm t;
+          if (ns_term(F, r, c, kns, t)) {
+            ls += 1.0 - static_cast<double>(t.val);
+            gX = t.gp;
+            gx += scale * t.gsn.x;
+            gy += scale * t.gsn.y;
+            gz += scale * t.gsn.z;
+          }
+          if (ns_term(F, r, c == 0 ? F.W - 1 : c - 1, kns, t)) gX = axpy3(1.f, t.gr, gX);
+          if (ns_term(F, r - 1, c, kns, t)) gX = axpy3(1.f, t.gb, gX);
+          float3 d;
+          pixel_ray(F, r, c, d.x, d.y, d.z);
+          const float gD = dot3(gX, d);
+          gSt += scale * gD / a;
+          gA += scale * (-gD * St / (a * a));
+        }
       }
       F.oA[p] = gA;
       F.oSt[p] = gSt;
@@ -270,11 +352,13 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
     const double t0 = block_sum_d(ld, s_w);
     const double t1 = block_sum_d(la, s_w);
     const double t2 = block_sum_d(ln, s_w);
+    const double t3 = block_sum_d(ls, s_w);
     if (threadIdx.x == 0) {
       double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + blockIdx.x);
       o[0] = t0;
       o[1] = t1;
       o[2] = t2;
+      o[3] = t3;
     }
   } else {
     const int mi = blockIdx.y - D->n_frames;
@@ -308,23 +392,30 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
   double Lmap[LGS_MAX_MAPS];   // thread 0 only
   for (int m = 0; m < D->n_maps; ++m) Lmap[m] = 0.0;
   for (int f = 0; f < D->n_frames; ++f) {
-    double a0 = 0, a1 = 0, a2 = 0;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     for (int b = threadIdx.x; b < kLossBlocks; b += blockDim.x) {
       const double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + b);
       a0 += __ldcg(o);
       a1 += __ldcg(o + 1);
       a2 += __ldcg(o + 2);
+      a3 += __ldcg(o + 3);
     }
     const double s0 = block_sum_d(a0, s_w), s1 = block_sum_d(a1, s_w), s2 = block_sum_d(a2, s_w);
+    const double s3 = block_sum_d(a3, s_w);
     const int2 cnt = mask_counts(cpart, f, s_i);
     if (threadIdx.x == 0) {
       const int nd = cnt.x, nn = cnt.y;
       const double Ld = nd ? s0 / nd : 0.0, La = nd ? s1 / nd : 0.0, Ln = nn ? s2 / nn : 0.0;
-      out[1 + 3 * f] = static_cast<float>(Ld);
-      out[2 + 3 * f] = static_cast<float>(La);
-      out[3 + 3 * f] = static_cast<float>(Ln);
+      const double Ls = nd ? s3 / nd : 0.0;
+      float* o = out + 1 + LGS_LOSS_TERMS * f;
+      o[0] = static_cast<float>(Ld);
+      o[1] = static_cast<float>(La);
+      o[2] = static_cast<float>(Ln);
+      o[3] = static_cast<float>(Ls);
       const int m = D->f[f].map;
-      Lmap[m] += (Ld + P.lambda_alpha * La + static_cast<double>(P.lambda_n) * P.lambda_ng * Ln) / D->m[m].n_frames;
+      Lmap[m] += (Ld + P.lambda_alpha * La + static_cast<double>(P.lambda_n) * P.lambda_ng * Ln +
+                  static_cast<double>(P.lambda_n) * P.lambda_ns * Ls) /
+                 D->m[m].n_frames;
     }
   }
   double L = 0.0;
@@ -334,7 +425,7 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
     const double sr = block_sum_d(a, s_w);
     if (threadIdx.x == 0) {
       Lmap[m] += P.lambda_s * sr;
-      out[1 + 3 * D->n_frames + m] = static_cast<float>(Lmap[m]);
+      out[1 + LGS_LOSS_TERMS * D->n_frames + m] = static_cast<float>(Lmap[m]);
       L += Lmap[m];
     }
   }

@@ -24,6 +24,7 @@ LGS_MAX_MAPS = 64
 STATUS = {0: "LGS_OK", 1: "LGS_ERR_INVALID_ARG", 2: "LGS_ERR_CAPACITY", 3: "LGS_ERR_BUDGET", 4: "LGS_ERR_CUDA",
           5: "LGS_ERR_TIMEOUT", 6: "LGS_ERR_DEVICE_CHECK", 7: "LGS_ERR_NO_WORKSPACE", 8: "LGS_ERR_STATE"}
 LGS_OK, LGS_ERR_CAPACITY = 0, 2
+LOSS_TERMS = 4           # per-frame image terms in a loss vector: L_depth, L_alpha, L_ng, L_ns
 
 P = ctypes.c_void_p
 F32P = ctypes.POINTER(ctypes.c_float)
@@ -61,7 +62,7 @@ class lgs_target(ctypes.Structure):
 
 class lgs_loss_params(ctypes.Structure):
     _fields_ = [("lambda_alpha", ctypes.c_float), ("lambda_n", ctypes.c_float), ("lambda_ng", ctypes.c_float),
-                ("lambda_s", ctypes.c_float), ("s_max", ctypes.c_float)]
+                ("lambda_s", ctypes.c_float), ("s_max", ctypes.c_float), ("lambda_ns", ctypes.c_float)]
 
 
 class lgs_adam_map(ctypes.Structure):

@@ -46,6 +46,11 @@ class MappingWindow:
         self.t = 0
         self.grads = None if autograd else [torch.zeros_like(p) for p in self.params]
 
+    def set_loss_params(self, loss: render.LossParams):
+        """Loss weights from the next iteration on (the paper switches the
+        N_surf term, lambda_{n,s}, on once densification has begun)."""
+        self.rast.loss_params = loss
+
     @property
     def n(self) -> int:
         return int(self.params[0].shape[0])

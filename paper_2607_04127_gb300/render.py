@@ -26,9 +26,11 @@ class LossParams:
     lambda_ng: float = 0.05
     lambda_s: float = 10.0
     s_max: float = 1.0
+    lambda_ns: float = 0.0      # N_surf term: 0.01 once densification has begun (Sec. 3.4)
 
     def struct(self):
-        return lib.lgs_loss_params(self.lambda_alpha, self.lambda_n, self.lambda_ng, self.lambda_s, self.s_max)
+        return lib.lgs_loss_params(self.lambda_alpha, self.lambda_n, self.lambda_ng, self.lambda_s, self.s_max,
+                                   self.lambda_ns)
 
 
 def map_tensors(surf, device="cuda"):
@@ -74,7 +76,7 @@ class Rasterizer:
         self.up = list(ups) if ups is not None else [upstream_planes(f, self.device) for f in self.frames]
         z = dict(dtype=torch.float32, device=self.device)
         self.n_maps = max(self.frame_map) + 1
-        self.loss_out = torch.zeros(1 + 3 * len(self.frames) + self.n_maps, **z)
+        self.loss_out = torch.zeros(1 + lib.LOSS_TERMS * len(self.frames) + self.n_maps, **z)
 
     def set_timing(self, enable: bool):
         """Bracket every kernel group of this rasterizer with CUDA events."""

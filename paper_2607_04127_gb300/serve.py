@@ -31,7 +31,7 @@ import time
 import numpy as np
 import torch
 
-from . import render
+from . import lib, render
 
 BYTES_PER_SURFEL = 160          # parameters, gradients, Adam m and v: 4 x 10 floats
 WORKSPACE_PER_SURFEL = 220      # record, box, keys, counters, moments, about 6 pairs (upper estimate)
@@ -104,7 +104,6 @@ class Server:
         """One iteration of every active request: one call per stage over their
         frames, a capacity check at the tick's single synchronisation, one
         fused Adam launch over their maps.  Returns the per-map losses."""
-        from . import lib
         for r in active:
             if r.buffers is None:      # device buffers for the request's lifetime
                 r.buffers = (render.target_tensors(r.target, self.device), lib.alloc_fwd(r.frame, self.device),
@@ -129,7 +128,8 @@ class Server:
                     x.zero_()
             out = self.rast.step(params, targets, grads, check=True)
         F = len(active)
-        losses = out[1 + 3 * F: 1 + 3 * F + F].cpu().numpy()
+        k = 1 + lib.LOSS_TERMS * F
+        losses = out[k: k + F].cpu().numpy()
         for s in maps:
             s.t += 1
         render.adam_step_batch([(s.params, s.grads, s.m, s.v, s.t, self.lr) for s in maps], zero_grad=True)

@@ -40,7 +40,7 @@ def run(maps, frames, targets=None, frame_map=None, tuning=None, read_bins=False
         tg = [(torch.from_numpy(t.D).cuda(), torch.from_numpy(np.ascontiguousarray(t.N)).cuda()) for t in targets]
         gp = [dict(dA=torch.zeros(f.H, f.W, device=dev), dS_t=torch.zeros(f.H, f.W, device=dev),
                    dS_n=torch.zeros(3, f.H, f.W, device=dev)) for f in frames]
-        loss_out = torch.zeros(1 + 3 * F + M, device=dev)
+        loss_out = torch.zeros(1 + lib.LOSS_TERMS * F + M, device=dev)
         grads = []
         for k, t in enumerate(T):
             g = [torch.zeros_like(x) for x in t]

@@ -55,7 +55,7 @@ def test_batched_equals_sequential(workload):
     _compare(B.outputs(), S.outputs())
     F, M = len(frames), len(maps)
     for m, r in enumerate(S.rasts):
-        assert float(LB[1 + 3 * F + m]) == float(r.loss_out[0])
+        assert float(LB[1 + 4 * F + m]) == float(r.loss_out[0])
     _grads_close(B.grads, S.grads)
     B.close()
     S.close()

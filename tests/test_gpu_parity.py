@@ -197,7 +197,7 @@ def check_loss_on_gpu_forward(oracle, g, frames, targets, scales):
         gterm = scales[f] * 1.0 * 0.05 / nn / m
         r, _ = ratio(g["upstream"][f]["dS_n"], up["dS_n"], 1e-5, 1e-5 * gterm[None])
         assert r.max() <= 1.0, ("dS_n", float(r.max()))
-        assert np.allclose(g["loss"][1 + 3 * f: 4 + 3 * f], terms, rtol=1e-5, atol=1e-9)
+        assert np.allclose(g["loss"][1 + 4 * f: 5 + 4 * f], terms, rtol=1e-5, atol=1e-9)
     return total
 
 
@@ -211,6 +211,51 @@ def test_loss_and_backward_parity(oracle, name, surf, frame, tgt):
     # end to end (oracle's own forward): the same loss to 1e-5
     Lo, _, _, _ = oracle.forward_backward(surf, [frame], [(tgt.D, tgt.N)])
     assert g["loss"][0] == pytest.approx(Lo, rel=1e-5)
+    og = oracle_grads(oracle, surf, [frame], [gpu_upstream(g, 0)])
+    assert_grads(compare_grads(g["grads"][0], og))
+
+
+NS_CASES = [(c, lam) for c in CASES if c[0] in ("box_room_32x512", "ragged_37x100_8x8", "near_sensor_poles")
+            for lam in (0.01, 1.0)]
+
+
+@pytest.mark.parametrize("name,surf,frame,tgt,lam_ns", [c + (lam,) for c, lam in NS_CASES],
+                         ids=[f"{c[0]}-{lam}" for c, lam in NS_CASES])
+def test_surface_normal_term_parity(oracle, name, surf, frame, tgt, lam_ns):
+    """The N_surf term of Eq. normalloss (normal of the rendered depth, image
+    columns wrapping at 2 pi): on the GPU's forward outputs the oracle gives
+    the same L_ns and upstream planes, within 1e-5 plus the oracle's bound
+    on a binary32 evaluation of the term (cross products of differences of
+    neighbouring back-projected ranges); the surfel gradients through those
+    planes match as in the plain loss."""
+    from tests import _gpu
+    g = _gpu.run([surf], [frame], targets=[tgt], loss=dict(_gpu.LOSS, lambda_ns=lam_ns))
+    fw = {k: np.asarray(v, np.float64) for k, v in g["fwd"][0].items()}
+    err = {}
+    Lf, up, terms = oracle.loss_image(fw, tgt.D, tgt.N, lam_ns=lam_ns, frame=frame, ns_err=err)
+    _, up0, _ = oracle.loss_image(fw, tgt.D, tgt.N)
+    assert terms[3] > 0.0
+    # the term moves most planes' values by far more than the tolerance (it is exercised)
+    moved = np.abs(up["dS_t"] - up0["dS_t"]) > 1e-3 * np.abs(up0["dS_t"])
+    assert moved[tgt.D > 0].mean() > 0.3
+    a = fw["A"] + EPS
+    Dh = fw["S_t"] / a
+    kink = np.abs(Dh - tgt.D) <= 1e-5 * np.abs(tgt.D)
+    extra = dict(dA=err["dD"] * np.abs(fw["S_t"]) / a ** 2, dS_t=err["dD"] / a)
+    for key in ("dA", "dS_t"):
+        r, _ = ratio(np.where(kink, 0, g["upstream"][0][key]), np.where(kink, 0, up[key]), 1e-5, extra[key])
+        assert r.max() <= 1.0, (key, float(r.max()))
+    m = np.sqrt((fw["S_n"] ** 2).sum(0) + EPS ** 2)
+    nn = max(int(((tgt.D > 0) & ((tgt.N.astype(np.float64) ** 2).sum(0) > 0)).sum()), 1)
+    nd = max(int((tgt.D > 0).sum()), 1)
+    gterm = (0.05 / nn + lam_ns / nd) / m
+    r, _ = ratio(g["upstream"][0]["dS_n"], up["dS_n"], 1e-5, 1e-5 * gterm[None] + err["dS_n"][None])
+    assert r.max() <= 1.0, ("dS_n", float(r.max()))
+    gt = g["loss"][1:5]
+    assert np.allclose(gt[:3], terms[:3], rtol=1e-5, atol=1e-9)
+    assert abs(gt[3] - terms[3]) <= 1e-5 * terms[3] + err["L_ns"], (gt[3], terms[3], err["L_ns"])
+    Ls = oracle.scale_reg(surf.log_scale)
+    assert g["loss"][0] == pytest.approx(Lf + Ls, rel=1e-5)
     og = oracle_grads(oracle, surf, [frame], [gpu_upstream(g, 0)])
     assert_grads(compare_grads(g["grads"][0], og))
 
@@ -259,8 +304,8 @@ def test_multi_frame_multi_map_batch(oracle):
     L0, _, _, _ = oracle.forward_backward(s0, [f0, f0b], [(t0.D, t0.N), (t0b.D, t0b.N)])
     L1, _, _, _ = oracle.forward_backward(s1, [f1], [(t1.D, t1.N)])
     F = 3
-    assert g["loss"][1 + 3 * F] == pytest.approx(L0, rel=1e-5)
-    assert g["loss"][2 + 3 * F] == pytest.approx(L1, rel=1e-5)
+    assert g["loss"][1 + 4 * F] == pytest.approx(L0, rel=1e-5)
+    assert g["loss"][2 + 4 * F] == pytest.approx(L1, rel=1e-5)
     assert g["loss"][0] == pytest.approx(L0 + L1, rel=1e-5)
     og0 = oracle_grads(oracle, s0, [f0, f0b], [gpu_upstream(g, 0), gpu_upstream(g, 2)])
     og1 = oracle_grads(oracle, s1, [f1], [gpu_upstream(g, 1)])

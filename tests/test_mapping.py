@@ -107,11 +107,13 @@ def _window():
     return start, [f0, f1], [t0, t1]
 
 
-def test_autograd_path_equals_fused_path(oracle):
-    from paper_2607_04127_gb300 import mapping
+@pytest.mark.parametrize("lambda_ns", [0.0, 0.01])
+def test_autograd_path_equals_fused_path(oracle, lambda_ns):
+    from paper_2607_04127_gb300 import mapping, render
     surf, frames, targets = _window()
-    a = mapping.MappingWindow(surf, frames, targets, autograd=True)
-    b = mapping.MappingWindow(surf, frames, targets, autograd=False)
+    lp = render.LossParams(lambda_ns=lambda_ns)
+    a = mapping.MappingWindow(surf, frames, targets, autograd=True, loss=lp)
+    b = mapping.MappingWindow(surf, frames, targets, autograd=False, loss=lp)
     La, ga = a.loss_and_grads()
     Lb, gb = b.loss_and_grads()
     assert float(La) == float(Lb)
@@ -130,6 +132,22 @@ def test_window_loss_decreases(oracle, autograd):
     L = w.run(10).cpu().numpy()
     assert np.all(np.isfinite(L))
     assert L[-1] < 0.95 * L[0] and np.sum(np.diff(L) < 0) >= 8, L
+    w.close()
+
+
+def test_surface_normal_term_switched_on_mid_run(oracle):
+    """The N_surf term enters once switched on (as after densification): every
+    frame reports a positive L_ns and the loss keeps decreasing."""
+    from paper_2607_04127_gb300 import mapping, render
+    surf, frames, targets = _window()
+    w = mapping.MappingWindow(surf, frames, targets, autograd=False)
+    L0 = w.run(5).cpu().numpy()
+    w.set_loss_params(render.LossParams(lambda_ns=0.01))
+    L1 = w.run(10).cpu().numpy()
+    terms = w.rast.loss_out.cpu().numpy()[1:9].reshape(2, 4)
+    assert np.all(terms[:, 3] > 0)
+    assert np.all(np.isfinite(L0)) and np.all(np.isfinite(L1))
+    assert L1[-1] < L1[0] and np.sum(np.diff(L1) < 0) >= 7, L1
     w.close()
 
 

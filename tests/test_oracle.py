@@ -420,16 +420,19 @@ def test_p9_surface_normal_of_a_plane(oracle):
     """Back-projected rendered ranges of a plane are coplanar, so N_surf is
     the plane's normal turned towards the sensor; with N_hat at a known angle
     theta_p from it, L_ns = sum over the pixels that have a term (a return
-    there, at the next column -- column W-1 pairs with column 0 -- and at the
-    next row) of (1 - cos theta_p), divided by |Omega_D|."""
+    and a rendered surface there, at the next column -- column W-1 pairs with
+    column 0 -- and at the next row) of (1 - cos theta_p), divided by
+    |Omega_D|."""
     frame = scenes.Frame(6, 32, 16, 16, -0.35, 0.35)
     H, W = frame.H, frame.W
     m = np.array([1.0, 0.15, -0.25]); m /= np.linalg.norm(m)
     A, St, valid, t = _plane_image(frame, m, 5.0)
     D = np.where(valid, t, 0.0).astype(np.float32)
     assert valid[:, 0].all() and valid[:, W - 1].all()        # the seam lies on the plane
-    D[2, 5] = 0.0; D[4, 30] = 0.0                               # holes
+    D[2, 5] = 0.0; D[4, 30] = 0.0                               # holes in the scan
+    A[3, 1] = 0.0; St[3, 1] = 0.0                               # a pixel that renders nothing
     ok = D > 0
+    rend = ok & (A > 0)
     rng = np.random.default_rng(4)
     theta = rng.uniform(0.0, 0.6, (H, W))
     theta[1, W - 1] = math.pi                                   # one normal pointing away
@@ -440,8 +443,9 @@ def test_p9_surface_normal_of_a_plane(oracle):
     has = np.zeros((H, W), bool)
     for r in range(H - 1):
         for c in range(W):
-            has[r, c] = ok[r, c] and ok[r, (c + 1) % W] and ok[r + 1, c]
+            has[r, c] = rend[r, c] and rend[r, (c + 1) % W] and rend[r + 1, c]
     assert has[1, W - 1] and not has[H - 1].any() and not has[2, 4] and not has[1, 5]
+    assert not has[3, 1] and not has[3, 0] and not has[2, 1] and has[3, 2]
     expect = (1.0 - np.cos(theta))[has].sum() / ok.sum()
     fw = dict(A=A, S_t=St, S_n=Sn)
     L0, _, t0 = oracle.loss_image(fw, D, N)

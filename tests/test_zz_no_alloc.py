@@ -57,7 +57,7 @@ def test_noalloc_loss_equals_session_loss():
     targets = [lib.lgs_target(d.data_ptr(), n.data_ptr()) for d, n in tg]
     # the session loss
     gs = _planes(frames, dev)
-    Ls = torch.zeros(1 + 3 * F + 1, device=dev)
+    Ls = torch.zeros(1 + 4 * F + 1, device=dev)
     lib.lgs_loss_batch(sess.handle, S, fr, [0, 0], [o.struct() for o in outs], targets, lp,
                        [lib.lgs_fwd_grad_out(g["dA"].data_ptr(), g["dS_t"].data_ptr(), g["dS_n"].data_ptr())
                         for g in gs], None, Ls.data_ptr(), stream)
@@ -71,11 +71,12 @@ def test_noalloc_loss_equals_session_loss():
                                    Ln.data_ptr(), stream)
         torch.cuda.synchronize()
         ln, ls = Ln.cpu().numpy(), Ls.cpu().numpy()
-        assert np.array_equal(ln[1:], ls[1:1 + 3 * F]), call
+        terms = ls[1:1 + 4 * F].reshape(F, 4)      # (L_depth, L_alpha, L_ng, L_ns): no N_surf term here
+        assert np.array_equal(ln[1:].reshape(F, 3), terms[:, :3]) and np.all(terms[:, 3] == 0), call
         for a, b in zip(gn, gs):
             for k in ("dA", "dS_t", "dS_n"):
                 assert torch.equal(a[k], b[k]), (call, k)
-        t = ls[1:1 + 3 * F].astype(np.float64).reshape(F, 3)
+        t = terms[:, :3].astype(np.float64)
         img = np.mean(t[:, 0] + LOSS["lambda_alpha"] * t[:, 1] + LOSS["lambda_n"] * LOSS["lambda_ng"] * t[:, 2])
         assert ln[0] == pytest.approx(img, rel=1e-6), call
     sess.close()
