@@ -159,11 +159,13 @@ typedef struct {
 /* Tuning knobs of the compositing kernels (results do not depend on them). */
 typedef struct {
     int32_t fwd_batch;   /* forward compositing: 0 = every warp walks the tile list on
-                            its own (32 entries per ballot, records through L1);
-                            64, 128, 256, 512 = the CTA stages that many records per
-                            shared-memory batch */
+                            its own, 32 entries per ballot; 64, 128, 256, 512 = the
+                            CTA stages that many records per shared-memory batch */
     int32_t bwd_batch;   /* backward: the same choice (0, 64, 128 or 256) */
-    int32_t group;       /* warp walk only: hits fetched and evaluated together, 1, 2 or 4 */
+    int32_t group;       /* warp walk only: 16 = the records of a chunk's hits are
+                            staged in the warp's own shared memory and read back by
+                            broadcast; 1, 2 or 4 = records read through L1, that many
+                            hits fetched and evaluated together */
     int32_t persistent;  /* 1: persistent CTAs claim tiles through an atomic counter */
 } lgs_tuning;
 
@@ -346,8 +348,8 @@ LGS_API lgs_status lgs_image_loss_noalloc(const int32_t* H, const int32_t* W, in
                                           const lgs_target* targets, const lgs_loss_params* params,
                                           const lgs_fwd_grad_out* grads_out, float* loss_out, void* stream);
 
-/* Set the compositing knobs of a session (defaults: fwd_batch 128, bwd_batch 0,
- * group 2, persistent 0).  Every choice gives bit-identical forward outputs. */
+/* Set the compositing knobs of a session (defaults: fwd_batch 0, bwd_batch 0,
+ * group 16, persistent 0).  Every choice gives bit-identical forward outputs. */
 LGS_API lgs_status lgs_session_set_tuning(lgs_session s, const lgs_tuning* t);
 
 /* One Adam step over the n surfels' 10 parameters (optimiser of the mapping

@@ -1,6 +1,8 @@
 """Autotuner of the compositing knobs: tile shape (8 x 8, 16 x 16, 32 columns
 x 8 rows), forward and backward variants (shared-memory batch of 64..512
-records, or the per-warp walk with 1, 2 or 4 hits per step) and persistent
+records, or the per-warp walk: records of each chunk's hits staged in the
+warp's shared memory, or read through L1 with 1, 2 or 4 hits per step) and
+persistent
 scheduling, chosen by timing whole steps of the actual workload on the
 device.  The search is coordinate-wise (tile shape first, then the forward,
 the backward and the scheduling), each candidate timed over a few steps with
@@ -15,8 +17,8 @@ from __future__ import annotations
 import torch
 
 TILES = ((8, 8), (16, 16), (8, 32))
-FWD = ((64, 1), (128, 1), (256, 1), (0, 2))           # (fwd_batch, group when 0)
-BWD = ((0, 1), (0, 2), (64, 2), (128, 2))             # (bwd_batch, group)
+FWD = ((0, 16), (64, 16), (128, 16), (0, 2))         # (fwd_batch, group when 0)
+BWD = ((0, 16), (0, 2), (64, 16), (128, 16))          # (bwd_batch, group)
 
 
 def time_steps(stepper, steps: int = 3) -> float:
@@ -35,7 +37,7 @@ def time_steps(stepper, steps: int = 3) -> float:
 def autotune(make, base: dict | None = None, steps: int = 3, tiles=TILES, fwd=FWD, bwd=BWD):
     """``make(tile, tuning)`` builds a stepper (an object with ``step(check)``
     and ``close()``).  Returns (tile, tuning, {description: ms})."""
-    tun = dict(fwd_batch=128, bwd_batch=0, group=2, persistent=0, **(base or {}))
+    tun = dict(fwd_batch=0, bwd_batch=0, group=16, persistent=0, **(base or {}))
     log = {}
 
     def run(tile, t):

@@ -34,7 +34,7 @@ struct lgs_session_s {
   size_t g13_zero_off = 0;      // g13 region known to be all-zero
   int64_t g13_zero_items = -1;
   cudaStream_t last_stream = nullptr;
-  lgs_tuning tune{128, 0, 2, 0};
+  lgs_tuning tune{0, 0, 16, 0};
   Status* h_status = nullptr;   // pinned
   int64_t launches = 0;         // kernels enqueued by this session
   // optional device timing of kernel groups
@@ -487,7 +487,8 @@ lgs_status lgs_session_set_tuning(lgs_session s, const lgs_tuning* t) {
   const auto ok_batch = [](int b, int hi) { return b == 0 || ((b == 64 || b == 128 || b == 256 || b == 512) && b <= hi); };
   if (!ok_batch(t->fwd_batch, 512)) return fail(LGS_ERR_INVALID_ARG, "fwd_batch must be 0, 64, 128, 256 or 512");
   if (!ok_batch(t->bwd_batch, 256)) return fail(LGS_ERR_INVALID_ARG, "bwd_batch must be 0, 64, 128 or 256");
-  if (t->group != 1 && t->group != 2 && t->group != 4) return fail(LGS_ERR_INVALID_ARG, "group must be 1, 2 or 4");
+  if (t->group != 1 && t->group != 2 && t->group != 4 && t->group != 16)
+    return fail(LGS_ERR_INVALID_ARG, "group must be 1, 2, 4 or 16");
   if (t->persistent != 0 && t->persistent != 1) return fail(LGS_ERR_INVALID_ARG, "persistent must be 0 or 1");
   s->tune = *t;
   return LGS_OK;

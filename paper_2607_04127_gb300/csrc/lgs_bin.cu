@@ -171,7 +171,6 @@ __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, 
     bin_geom(M.mean + 3 * i, M.ls + 2 * i, F, g);
     key[item] = __float_as_uint(g.r);
     const float4 pb = pixel_box(g, F);
-    box[item] = pb;
     if (aw.local) c = for_each_tile(g, F, tab, pb, [&](uint32_t t) { atomicAdd(s_cnt + (t - aw.base), 1u); });
     else c = for_each_tile(g, F, tab, pb, [&](uint32_t t) { atomicAdd(tcount + t, 1u); });
     cnt[item] = c;
@@ -199,7 +198,9 @@ __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, 
     out[0] = make_float4(nx, ny, nz, nx * mx + ny * my + nz * mz);
     out[1] = make_float4(tux * isu, tuy * isu, tuz * isu, (tux * mx + tuy * my + tuz * mz) * isu);
     out[2] = make_float4(tvx * isv, tvy * isv, tvz * isv, (tvx * mx + tvy * my + tvz * mz) * isv);
-    out[3] = make_float4(alpha, expf(ls0), expf(ls1), 0.f);
+    const float su = expf(ls0), sv = expf(ls1);
+    out[3] = make_float4(alpha, su, sv, 0.f);
+    box[item] = cull_box(g, F, pb, tux, tuy, tuz, tvx, tvy, tvz, su, sv);
   }
   // visible-item count, one atomic per warp
   const uint32_t vis = __ballot_sync(0xffffffffu, c > 0);
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(256) k_emit(const Desc* __restrict__ D, const 
       const MapDev& M = D->m[F->map];
       const int64_t i = item - F->item_base;
       bin_geom(M.mean + 3 * i, M.ls + 2 * i, *F, g);
-      pb = box[item];
+      pb = pixel_box(g, *F);   // the sphere box the counting pass used (the stored box is the culling box)
       k = (static_cast<unsigned long long>(key[item]) << 32) | static_cast<uint32_t>(item);
     }
   }

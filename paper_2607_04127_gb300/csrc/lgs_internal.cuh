@@ -311,6 +311,59 @@ __device__ __forceinline__ float4 pixel_box(const BinGeom& g, const FrameDev& F)
   return make_float4(r_lo, r_hi, cc, chw);
 }
 
+// Culling box of the compositing kernels: the pixels whose centre ray can
+// meet the surfel's 3-sigma disc {mu + A c + B s : c^2 + s^2 <= 1}, A = 3 s_u
+// t_u, B = 3 s_v t_v (sensor frame), intersected with the bounding-sphere box
+// sb (same column centre).  Over the disc, sin(elevation) g(p) = p_z / |p|
+// and the azimuth phi(p) = atan2(p_y, p_x) are bounded by their first-order
+// terms, whose maximum over the disc is |(grad . A, grad . B)|, plus the
+// Taylor remainder: |x^T H x| <= 3 |x|^2 / |p|^2 for g and |x|^2 / h^2 for phi
+// (h the distance from the z axis), so with rho >= |A c + B s| the remainder
+// is at most 1.5 rho^2 / (|mu| - rho)^2, resp. 0.5 rho^2 / (h - rho)^2.  The
+// disc is widened by 0.1 % and the pixel bounds by 0.02 pixels for binary32
+// rounding.  Only the compositing kernels read this box; binning keeps the
+// sphere box.
+__device__ __forceinline__ float4 cull_box(const BinGeom& g, const FrameDev& F, const float4& sb, float tux,
+                                           float tuy, float tuz, float tvx, float tvy, float tvz, float su,
+                                           float sv) {
+  float4 b = sb;
+  const float ka = 3.003f * su, kb = 3.003f * sv;
+  const float Ax = ka * tux, Ay = ka * tuy, Az = ka * tuz;
+  const float Bx = kb * tvx, By = kb * tvy, Bz = kb * tvz;
+  const float rho = fmaxf(ka, kb) * 1.001f;
+  const float r = g.r;
+  if (!g.all_rows && r > 1.01f * rho) {
+    const float ir = 1.0f / r;
+    const float g0 = g.z * ir;
+    // grad g = (z_hat - g0 p_hat) / |p|
+    const float gx = -g0 * g.x * ir * ir, gy = -g0 * g.y * ir * ir, gz = (1.0f - g0 * g.z * ir) * ir;
+    const float la = gx * Ax + gy * Ay + gz * Az, lb = gx * Bx + gy * By + gz * Bz;
+    const float d = r - rho;
+    const float ext = sqrtf(la * la + lb * lb) * 1.001f + 1.5f * rho * rho / (d * d);
+    const float s_hi = g0 + ext, s_lo = g0 - ext;
+    const float dth = (F.emax - F.emin) / static_cast<float>(F.H);
+    if (s_hi < 1.0f && s_lo > -1.0f) {
+      // rows whose centre elevation emax - (r + 1/2) dth lies in the band
+      const float rl = ceilf((F.emax - asinf(s_hi)) / dth - 0.52f);
+      const float rh = floorf((F.emax - asinf(s_lo)) / dth - 0.48f);
+      b.x = fmaxf(b.x, rl);
+      b.y = fminf(b.y, rh);
+    }
+  }
+  if (!g.all_cols && g.h > 1.01f * rho) {
+    const float ih2 = 1.0f / (g.h * g.h);
+    // grad phi = (-y, x, 0) / h^2
+    const float la = (g.x * Ay - g.y * Ax) * ih2, lb = (g.x * By - g.y * Bx) * ih2;
+    const float d = g.h - rho;
+    const float half = sqrtf(la * la + lb * lb) * 1.001f + 0.5f * rho * rho / (d * d);
+    if (half < 3.0f) {
+      const float cpr = static_cast<float>(F.W) / 6.283185307f;
+      b.w = fminf(b.w, half * cpr + 0.02f);
+    }
+  }
+  return b;
+}
+
 // Pixel of a thread inside its tile: 4 x 8 pixel blocks per warp when the
 // tile shape allows, row-major otherwise.
 __device__ __forceinline__ void pixel_of_thread(const FrameDev& F, int tid, int& lr, int& lc) {
@@ -364,22 +417,43 @@ __device__ __forceinline__ bool box_hits(const float4& b, const WarpBox& w) {
 constexpr uint32_t kLongList = 4096;
 
 struct Eval {
-  float den, t, ud, vd, u, v, q, G, araw, a;
+  float den, rden, t, ud, vd, u, v, q, G, araw, a;
   bool valid;
 };
+
+// Hardware reciprocal and base-2 exponential (PTX rcp.approx.ftz.f32,
+// ex2.approx.ftz.f32).  The flush-to-zero forms map to one MUFU instruction
+// each; the IEEE-denormal forms add range fix-ups around it.  No input of
+// the compositing arithmetic is near the denormal range (|n.d| >= 1e-6 on
+// every accepted pair, exponents >= -4.5 log2 e).
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// exp(-q / 2) = 2^(q * (-log2(e) / 2)); -log2(e) / 2 = -1 / (2 ln 2).
+constexpr float kNegHalfLog2e = -0.72134752044448170368f;
 
 // One ray / surfel evaluation, arithmetic pinned (explicit fma / rounded mul)
 // so the forward and backward kernels take identical skip decisions.
 __device__ __forceinline__ void eval_pair(const float4& r0, const float4& r1, const float4& r2,
                                           float alpha, float dx, float dy, float dz, Eval& e) {
   e.den = __fmaf_rn(r0.z, dz, __fmaf_rn(r0.y, dy, __fmul_rn(r0.x, dx)));
-  e.t = __fdividef(r0.w, e.den);
+  e.rden = rcp_ftz(e.den);
+  e.t = __fmul_rn(r0.w, e.rden);
   e.ud = __fmaf_rn(r1.z, dz, __fmaf_rn(r1.y, dy, __fmul_rn(r1.x, dx)));
   e.vd = __fmaf_rn(r2.z, dz, __fmaf_rn(r2.y, dy, __fmul_rn(r2.x, dx)));
   e.u = __fmaf_rn(e.t, e.ud, -r1.w);
   e.v = __fmaf_rn(e.t, e.vd, -r2.w);
   e.q = __fmaf_rn(e.u, e.u, __fmul_rn(e.v, e.v));
-  e.G = __expf(__fmul_rn(-0.5f, e.q));
+  e.G = ex2_ftz(__fmul_rn(kNegHalfLog2e, e.q));
   e.araw = __fmul_rn(alpha, e.G);
   e.a = fminf(e.araw, 0.99f);
   e.valid = (fabsf(e.den) >= 1e-6f) && (e.t > 0.2f) && (e.q <= 9.0f) && (e.a >= (1.0f / 255.0f));

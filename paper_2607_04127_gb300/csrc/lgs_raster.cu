@@ -44,7 +44,7 @@ __device__ __forceinline__ void moments(const Eval& E, const float4& r0, float T
   const float dLda = Tk * gc - S * iom;
   const float g = E.araw < 0.99f ? E.araw * dLda : 0.f;
   const float ug = E.u * g, vg = E.v * g;
-  const float ct = __fdividef(fmaf(w, gSt, -fmaf(ug, E.ud, vg * E.vd)), E.den);
+  const float ct = fmaf(w, gSt, -fmaf(ug, E.ud, vg * E.vd)) * E.rden;
   const float wsg = w * sg;
   v[0] += g;
   v[1] += ug;
@@ -65,7 +65,7 @@ __device__ __forceinline__ void moments(const Eval& E, const float4& r0, float T
 // arithmetic as moments(), with S updated in place).
 __device__ __forceinline__ void contrib_moments(const Eval& E, const float4& r0, float gA, float gSt, float gSx,
                                                 float gSy, float gSz, float& T, float& S, float (&v)[16]) {
-  const float iom = __fdividef(1.0f, 1.0f - E.a);
+  const float iom = rcp_ftz(1.0f - E.a);
   const float Tk = T * iom;
   const float sg = E.den > 0.f ? -1.f : 1.f;
   const float gc = gA + gSt * E.t + sg * (gSx * r0.x + gSy * r0.y + gSz * r0.z);
@@ -75,7 +75,7 @@ __device__ __forceinline__ void contrib_moments(const Eval& E, const float4& r0,
   T = Tk;
   const float g = E.araw < 0.99f ? E.araw * dLda : 0.f;
   const float ug = E.u * g, vg = E.v * g;
-  const float ct = __fdividef(fmaf(w, gSt, -fmaf(ug, E.ud, vg * E.vd)), E.den);
+  const float ct = fmaf(w, gSt, -fmaf(ug, E.ud, vg * E.vd)) * E.rden;
   const float wsg = w * sg;
   v[0] += g;
   v[1] += ug;
@@ -613,6 +613,262 @@ __global__ void __launch_bounds__(kMaxTileThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Reduce-scatter of the 12 gradient moments of one (warp, entry) over the
+// warp: 15 shuffles for 12 values.
+// ---------------------------------------------------------------------------
+// Reduce-scatter of 12 values over the warp.  Afterwards the warp sum of
+// value 6 b4 + 3 b3 + b2 is held by the lanes with (lane & 3) == 0 and that
+// of value 6 b4 + 3 b3 + 2 by the lanes with (lane & 7) == 1 (b4, b3, b2 the
+// lane's bits); returns the lane's value and sets idx (-1: not a writer).
+__device__ __forceinline__ float warp_reduce12(const float (&v)[12], int lane, int& idx) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float w[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float send = b4 ? v[i] : v[i + 6];
+    const float keep = b4 ? v[i + 6] : v[i];
+    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float x[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float send = b3 ? w[i] : w[i + 3];
+    const float keep = b3 ? w[i + 3] : w[i];
+    x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float y0, y2;
+  {
+    const float send = b2 ? x[0] : x[1];
+    const float keep = b2 ? x[1] : x[0];
+    y0 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    y2 = x[2] + __shfl_xor_sync(0xffffffffu, x[2], 4);
+  }
+  y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+  y2 += __shfl_xor_sync(0xffffffffu, y2, 2);
+  y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
+  y2 += __shfl_xor_sync(0xffffffffu, y2, 1);
+  const int base = (b4 ? 6 : 0) + (b3 ? 3 : 0);
+  const bool first = (lane & 3) == 0;
+  idx = first ? base + (b2 ? 1 : 0) : ((lane & 7) == 1 ? base + 2 : -1);
+  return first ? y0 : y2;
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory walk (group 16): each warp walks its tile list in chunks of
+// 32 entries; the records of the chunk's hits are staged in the warp's own
+// shared-memory slots (one 48-B record per lane) and read back with broadcast
+// loads, so a hit costs no shuffle, no 64-bit address arithmetic and no
+// global load on the critical path.  No CTA barrier: warps proceed alone.
+// ---------------------------------------------------------------------------
+struct WarpRecs {
+  float4 r0[32], r1[32], r2[32];
+  float al[32];
+};
+
+__device__ __forceinline__ void stage_hit(const float4* __restrict__ rec, uint32_t item, WarpRecs& s, int lane) {
+  const float4* rp = rec + 4 * static_cast<int64_t>(item);
+  s.r0[lane] = __ldg(rp);
+  s.r1[lane] = __ldg(rp + 1);
+  s.r2[lane] = __ldg(rp + 2);
+  s.al[lane] = __ldg(reinterpret_cast<const float*>(rp + 3));
+}
+
+__global__ void __launch_bounds__(kMaxTileThreads)
+    k_fwd_s(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
+            const float4* __restrict__ rec, const float4* __restrict__ box, const uint32_t* __restrict__ order,
+            Status* __restrict__ st, int persistent) {
+  __shared__ WarpRecs s_w[kMaxTileThreads / 32];
+  const int lane = threadIdx.x & 31;
+  WarpRecs& sw = s_w[threadIdx.x >> 5];
+  uint32_t tile;
+  uint32_t evals = 0, contrib = 0, alg = 0;
+  for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter, tile, iter); ++iter) {
+    const TileCtx tc = tile_ctx(*D, tile, ranges);
+    if (tc.end - tc.start > kLongList) continue;   // the long-list kernels' tile
+    const FrameDev& F = D->f[tc.f];
+    const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    if (tc.inside) pixel_ray(F, tc.r, tc.c, dx, dy, dz);
+    float T = 1.0f, A = 0.0f, St = 0.0f, Sx = 0.0f, Sy = 0.0f, Sz = 0.0f;
+    int last = 0, stop_at = -1;
+    bool done = !tc.inside;
+    for (uint32_t base = tc.start; base < tc.end; base += 32) {
+      if (__all_sync(0xffffffffu, done)) break;
+      const uint32_t j = base + lane;
+      uint32_t item = 0;
+      bool hit = false;
+      if (j < tc.end) {
+        item = __ldg(pv + j);
+        hit = box_hits(__ldg(box + item), wb);
+      }
+      uint32_t m = __ballot_sync(0xffffffffu, hit);
+      if (!m) continue;
+      __syncwarp();
+      if (hit) stage_hit(rec, item, sw, lane);
+      __syncwarp();
+      const int k0 = static_cast<int>(base - tc.start) + 1;
+      do {
+        const int bq = __ffs(m) - 1;
+        m &= m - 1;
+        const float4 r0 = sw.r0[bq];
+        Eval e;
+        eval_pair(r0, sw.r1[bq], sw.r2[bq], sw.al[bq], dx, dy, dz, e);
+        // composite without branches: lanes that are done or see an invalid
+        // pair add zeros and keep T (t and the weight are zeroed first, so no
+        // inf or NaN of a rejected pair reaches the sums)
+        const bool act = !done && e.valid;
+        evals += !done;
+        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.a));
+        const bool stop = act && Tn < 1e-4f;
+        const bool comp = act && !(Tn < 1e-4f);
+        const float w = comp ? e.a * T : 0.0f;
+        const float tt = comp ? e.t : 0.0f;
+        const float ws = e.den > 0.f ? -w : w;
+        A += w;
+        St = fmaf(w, tt, St);
+        Sx = fmaf(ws, r0.x, Sx);
+        Sy = fmaf(ws, r0.y, Sy);
+        Sz = fmaf(ws, r0.z, Sz);
+        T = comp ? Tn : T;
+        last = comp ? k0 + bq : last;
+        contrib += comp;
+        stop_at = stop ? k0 + bq : stop_at;
+        done = done || stop;
+        if (__all_sync(0xffffffffu, done)) break;
+      } while (m);
+    }
+    if (tc.inside) {
+      F.A[tc.pix] = A;
+      F.St[tc.pix] = St;
+      F.Sn[tc.pix] = Sx;
+      F.Sn[tc.HW + tc.pix] = Sy;
+      F.Sn[2 * static_cast<int64_t>(tc.HW) + tc.pix] = Sz;
+      F.Tf[tc.pix] = T;
+      F.nc[tc.pix] = last;
+      alg += stop_at >= 0 ? static_cast<uint32_t>(stop_at) : tc.end - tc.start;
+    }
+  }
+  unsigned long long ev = evals, co = contrib;
+  for (int o = 16; o > 0; o >>= 1) {
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    co += __shfl_xor_sync(0xffffffffu, co, o);
+  }
+  unsigned long long al = alg;
+  for (int o = 16; o > 0; o >>= 1) al += __shfl_xor_sync(0xffffffffu, al, o);
+  if (lane == 0 && ev) atomicAdd(&st->evals_fwd, ev);
+  if (lane == 0 && co) atomicAdd(&st->contrib_fwd, co);
+  if (lane == 0 && al) atomicAdd(&st->alg_fwd, al);
+}
+
+__global__ void __launch_bounds__(kMaxTileThreads)
+    k_bwd_s(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
+            const float4* __restrict__ rec, const float4* __restrict__ box, float* __restrict__ g13,
+            const uint32_t* __restrict__ order, Status* __restrict__ st, int persistent) {
+  __shared__ WarpRecs s_w[kMaxTileThreads / 32];
+  __shared__ uint32_t s_item[kMaxTileThreads / 32][32];
+  const int lane = threadIdx.x & 31;
+  WarpRecs& sw = s_w[threadIdx.x >> 5];
+  uint32_t* si = s_item[threadIdx.x >> 5];
+  uint32_t tile;
+  uint32_t evals = 0, contrib = 0;
+  for (int iter = 0; next_tile(persistent, order, D->n_tiles, &st->work_counter2, tile, iter); ++iter) {
+    const TileCtx tc = tile_ctx(*D, tile, ranges);
+    if (tc.end - tc.start > kLongList) continue;   // the long-list kernels' tile
+    const FrameDev& F = D->f[tc.f];
+    const WarpBox wb = warp_box(tc.inside, tc.r, tc.c, F.W);
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    float T = 1.f, gA = 0.f, gSt = 0.f, gSx = 0.f, gSy = 0.f, gSz = 0.f;
+    int nc = 0;
+    if (tc.inside) {
+      pixel_ray(F, tc.r, tc.c, dx, dy, dz);
+      T = F.Tf[tc.pix];
+      nc = F.nc[tc.pix];
+      gA = F.gA[tc.pix];
+      gSt = F.gSt[tc.pix];
+      gSx = F.gSn[tc.pix];
+      gSy = F.gSn[tc.HW + tc.pix];
+      gSz = F.gSn[2 * static_cast<int64_t>(tc.HW) + tc.pix];
+    }
+    // n_contrib comes from the caller: never walk past the tile's list
+    const uint32_t len = tc.end - tc.start;
+    const uint32_t stop = min(static_cast<uint32_t>(__reduce_max_sync(0xffffffffu, nc > 0 ? nc : 0)), len);
+    float S = 0.f;
+    for (int c0 = static_cast<int>((stop + 31) / 32) - 1; c0 >= 0; --c0) {
+      const int k0 = 32 * c0;
+      uint32_t item = 0;
+      bool hit = false;
+      if (static_cast<uint32_t>(k0 + lane) < stop) {
+        item = __ldg(pv + tc.start + k0 + lane);
+        hit = box_hits(__ldg(box + item), wb);
+      }
+      uint32_t m = __ballot_sync(0xffffffffu, hit);
+      if (!m) continue;
+      __syncwarp();
+      if (hit) {
+        stage_hit(rec, item, sw, lane);
+        si[lane] = item;
+      }
+      __syncwarp();
+      do {
+        const int bq = 31 - __clz(m);
+        m &= ~(1u << bq);
+        const bool in = k0 + bq < nc;
+        const float4 r0 = sw.r0[bq];
+        Eval e;
+        eval_pair(r0, sw.r1[bq], sw.r2[bq], sw.al[bq], dx, dy, dz, e);
+        const bool valid = in && e.valid;
+        evals += in;
+        contrib += valid;
+        if (!__any_sync(0xffffffffu, valid)) continue;
+        // invalid lanes: zero opacity and finite inputs, so every moment is
+        // exactly 0 and T, S pass through unchanged
+        const float a = valid ? e.a : 0.f;
+        const float araw = valid ? e.araw : 0.f;
+        const float t = valid ? e.t : 0.f;
+        const float u = valid ? e.u : 0.f;
+        const float v = valid ? e.v : 0.f;
+        const float rden = valid ? e.rden : 0.f;
+        const float iom = rcp_ftz(1.0f - a);
+        const float Tk = T * iom;
+        const float sg = e.den > 0.f ? -1.f : 1.f;
+        const float gc = gA + gSt * t + sg * (gSx * r0.x + gSy * r0.y + gSz * r0.z);
+        const float w = a * Tk;
+        const float dLda = Tk * gc - S * iom;
+        S = fmaf(w, gc, S);
+        T = Tk;
+        const float g = araw < 0.99f ? araw * dLda : 0.f;
+        const float ug = u * g, vg = v * g;
+        const float ct = fmaf(w, gSt, -fmaf(ug, e.ud, vg * e.vd)) * rden;
+        const float wsg = w * sg;
+        float mv[12];
+        mv[0] = g;
+        mv[1] = ug;
+        mv[2] = vg;
+        mv[3] = u * ug;
+        mv[4] = v * vg;
+        mv[5] = u * vg;
+        mv[6] = ct;
+        mv[7] = ct * u;
+        mv[8] = ct * v;
+        mv[9] = wsg * gSx;
+        mv[10] = wsg * gSy;
+        mv[11] = wsg * gSz;
+        int idx;
+        const float r = warp_reduce12(mv, lane, idx);
+        if (idx >= 0 && r != 0.f) atomicAdd(g13 + 16 * static_cast<int64_t>(si[bq]) + idx, r);
+      } while (m);
+    }
+  }
+  unsigned long long ev = evals, co = contrib;
+  for (int o = 16; o > 0; o >>= 1) {
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    co += __shfl_xor_sync(0xffffffffu, co, o);
+  }
+  if (lane == 0 && ev) atomicAdd(&st->evals_bwd, ev);
+  if (lane == 0 && co) atomicAdd(&st->contrib_bwd, co);
+}
+
+// ---------------------------------------------------------------------------
 // Long lists (more than kLongList entries): one warp per pixel
 // ---------------------------------------------------------------------------
 // A tile with a very long list (a far horizon seen along a street: tens of
@@ -843,7 +1099,7 @@ __global__ void __launch_bounds__(256) k_bwd_long(const Desc* __restrict__ D, co
         float v[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) v[q] = 0.f;
-        moments(e, r0, Tk, S + Cex, __fdividef(1.0f, om), gA, gSt, gSx, gSy, gSz, v);
+        moments(e, r0, Tk, S + Cex, rcp_ftz(om), gA, gSt, gSx, gSy, gSz, v);
         float* gp = g13 + 16 * static_cast<int64_t>(item);
 #pragma unroll
         for (int q = 0; q < kGrad; ++q)
@@ -910,7 +1166,8 @@ static cudaError_t launch_raster_fwd_tiles(const WsPtrs& w, const Desc& h, const
   const uint32_t* ord = persistent ? w.work : nullptr;
   switch (batch) {
     case 0:
-      if (group == 1) k_fwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
+      if (group == 16) k_fwd_s<<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
+      else if (group == 1) k_fwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       else if (group == 2) k_fwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       else k_fwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       return cudaGetLastError();
@@ -931,7 +1188,8 @@ static cudaError_t launch_raster_bwd_tiles(const WsPtrs& w, const Desc& h, const
   const uint32_t* ord = persistent ? w.work : nullptr;
   switch (batch) {
     case 0:
-      if (group == 1) k_bwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, ord, w.st, persistent);
+      if (group == 16) k_bwd_s<<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, ord, w.st, persistent);
+      else if (group == 1) k_bwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, ord, w.st, persistent);
       else if (group == 2) k_bwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, ord, w.st, persistent);
       else k_bwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, ord, w.st, persistent);
       return cudaGetLastError();

@@ -45,10 +45,10 @@ def target_tensors(tgt, device="cuda"):
 
 
 # Compositing knobs (lgs_tuning) and tile shape the benchmark runs with: the
-# 200k-surfel 128 x 1024 street frame renders fastest with 8 x 8 tiles, the
-# forward staged in 128-record shared-memory batches and the backward as an
-# independent walk per warp taking two hits at a time.
-DEFAULT_TUNING = dict(fwd_batch=128, bwd_batch=0, group=2, persistent=0)
+# 200k-surfel 128 x 1024 street frame renders fastest with 8 x 8 tiles and
+# both passes as an independent walk per warp that stages the records of each
+# 32-entry chunk's hits in its own shared memory.
+DEFAULT_TUNING = dict(fwd_batch=0, bwd_batch=0, group=16, persistent=0)
 DEFAULT_TILE = (8, 8)
 
 

@@ -260,7 +260,7 @@ def test_surface_normal_term_parity(oracle, name, surf, frame, tgt, lam_ns):
     assert_grads(compare_grads(g["grads"][0], og))
 
 
-TUNINGS = ([dict(fwd_batch=0, bwd_batch=0, group=g, persistent=p) for g in (1, 2, 4) for p in (0, 1)]
+TUNINGS = ([dict(fwd_batch=0, bwd_batch=0, group=g, persistent=p) for g in (1, 2, 4, 16) for p in (0, 1)]
            + [dict(fwd_batch=b, bwd_batch=min(b, 256), group=1, persistent=p) for b in (64, 128, 256, 512)
               for p in (0, 1)])
 
