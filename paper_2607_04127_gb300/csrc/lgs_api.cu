@@ -35,6 +35,7 @@ struct lgs_session_s {
   int64_t g13_zero_items = -1;
   cudaStream_t last_stream = nullptr;
   lgs_tuning tune{0, 0, 16, 0};
+  bool ckpt_valid = false;      // the last forward since binning wrote the backward's chunk checkpoints
   Status* h_status = nullptr;   // pinned
   int64_t launches = 0;         // kernels enqueued by this session
   // optional device timing of kernel groups
@@ -116,6 +117,7 @@ struct Plan {
   int64_t n_items = 0, n_surf = 0;
   uint32_t n_tiles = 0;
   uint32_t table_floats = 0;
+  uint32_t tile_pixels = 0;
 };
 
 lgs_status build_desc(const lgs_surfels* maps, int n_maps, const lgs_frame* frames, const int32_t* frame_map,
@@ -175,10 +177,17 @@ lgs_status build_desc(const lgs_surfels* maps, int n_maps, const lgs_frame* fram
   p.n_surf = surf;
   p.n_tiles = d.n_tiles;
   p.table_floats = static_cast<uint32_t>(tab);
+  p.tile_pixels = static_cast<uint32_t>(d.th * d.tw);
   return LGS_OK;
 }
 
-Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t table_floats) {
+// Backward chunks that pairs_cap pairs over `tiles` tiles can form: every
+// non-empty tile list of n entries has ceil(n / kChunk) <= n / kChunk + 1.
+int64_t chunk_cap(int64_t pairs_cap, uint32_t tiles) {
+  return (pairs_cap > 0 ? pairs_cap : 0) / lgs::kChunk + static_cast<int64_t>(tiles) + 1;
+}
+
+Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t table_floats, uint32_t tile_pixels) {
   Layout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -205,6 +214,11 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
   L.work = take(4 * T);
   L.longt = take(4 * T);
   L.loss_part = take(lgs::loss_part_bytes());
+  const int64_t C = chunk_cap(pairs_cap, tiles);
+  L.cbase = take(4 * T);
+  L.citem = take(8 * static_cast<size_t>(C));
+  L.ckpt = take(sizeof(float) * 6 * static_cast<size_t>(tile_pixels) * static_cast<size_t>(C));
+  L.chunks_cap = C;
   L.total = off;
   L.items_cap = items;
   L.pairs_cap = pairs_cap;
@@ -215,13 +229,13 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
 
 // Largest pair capacity whose layout fits in `bytes` (-1 if none).
 int64_t fit_pairs(size_t bytes, const Plan& p) {
-  if (make_layout(p.n_items, p.n_tiles, 0, p.table_floats).total > bytes) return -1;
+  if (make_layout(p.n_items, p.n_tiles, 0, p.table_floats, p.tile_pixels).total > bytes) return -1;
   int64_t lo = 0, hi = 1;
-  while (hi < (1ll << 32) && make_layout(p.n_items, p.n_tiles, hi, p.table_floats).total <= bytes) hi *= 2;
+  while (hi < (1ll << 32) && make_layout(p.n_items, p.n_tiles, hi, p.table_floats, p.tile_pixels).total <= bytes) hi *= 2;
   if (hi > 0xfffffffell) hi = 0xfffffffell;
   while (lo < hi) {
     const int64_t mid = lo + (hi - lo + 1) / 2;
-    if (make_layout(p.n_items, p.n_tiles, mid, p.table_floats).total <= bytes) lo = mid; else hi = mid - 1;
+    if (make_layout(p.n_items, p.n_tiles, mid, p.table_floats, p.tile_pixels).total <= bytes) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -459,7 +473,7 @@ lgs_status lgs_batch_workspace_size(lgs_session s, const int64_t* map_sizes, int
   st = build_desc(tmp, n_maps, frames, frame_map, n_frames, *d, p);
   delete d;
   if (st != LGS_OK) return st;
-  *bytes = make_layout(p.n_items, p.n_tiles, max_pairs, p.table_floats).total;
+  *bytes = make_layout(p.n_items, p.n_tiles, max_pairs, p.table_floats, p.tile_pixels).total;
   return LGS_OK;
 }
 
@@ -624,8 +638,8 @@ lgs_status lgs_bin_sort_batch(lgs_session s, const lgs_surfels* maps, int n_maps
   const int64_t cap = fit_pairs(s->ws_bytes, p);
   if (cap < 0)
     return fail(LGS_ERR_NO_WORKSPACE, "workspace of %zu bytes too small even without pairs (%zu needed)", s->ws_bytes,
-                make_layout(p.n_items, p.n_tiles, 0, p.table_floats).total);
-  const Layout L = make_layout(p.n_items, p.n_tiles, cap, p.table_floats);
+                make_layout(p.n_items, p.n_tiles, 0, p.table_floats, p.tile_pixels).total);
+  const Layout L = make_layout(p.n_items, p.n_tiles, cap, p.table_floats, p.tile_pixels);
   const WsPtrs w = lgs::ws_ptrs(s->ws, L);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e;
@@ -643,6 +657,7 @@ lgs_status lgs_bin_sort_batch(lgs_session s, const lgs_surfels* maps, int n_maps
   s->launches += lgs::bin_kernel_count(p.n_tiles);
   s->lay = L;
   s->binned = true;
+  s->ckpt_valid = false;
   s->last_stream = cs;
   return LGS_OK;
 }
@@ -679,6 +694,7 @@ lgs_status lgs_render_fwd_batch(lgs_session s, const lgs_surfels* maps, int n_ma
     return cuda_fail(e, "raster_fwd");
   s->launches += 2;   // per-tile and long-list kernels
   s->last_stream = cs;
+  s->ckpt_valid = s->tune.fwd_batch == 0 && s->tune.group == 16;
   return LGS_OK;
 }
 
@@ -725,7 +741,9 @@ lgs_status lgs_render_bwd_batch(lgs_session s, const lgs_surfels* maps, int n_ma
   if ((e = write_desc(s, d, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
   const uint32_t* pv = w.pv;
   if ((e = timed(s, LGS_TIME_BWD, cs, [&] {
-         return lgs::launch_raster_bwd(s->lay, w, d, pv, s->tune.bwd_batch, s->tune.group, s->tune.persistent, cs);
+         const bool chunked = s->ckpt_valid && s->tune.bwd_batch == 0 && s->tune.group == 16;
+         return lgs::launch_raster_bwd(s->lay, w, d, pv, s->tune.bwd_batch, s->tune.group, s->tune.persistent,
+                                       chunked, cs);
        })) != cudaSuccess)
     return cuda_fail(e, "raster_bwd");
   if ((e = timed(s, LGS_TIME_BWD_CHAIN, cs, [&] { return lgs::launch_preprocess_bwd(s->lay, w, d, cs); })) !=

@@ -225,28 +225,50 @@ __device__ __forceinline__ int order_bucket(uint32_t n) { return kOrderBuckets -
 __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ tcur, uint32_t n_tiles,
                                                           uint2* __restrict__ ranges, Status* __restrict__ st,
                                                           int64_t cap, uint32_t* __restrict__ order,
-                                                          uint32_t* __restrict__ longt) {
+                                                          uint32_t* __restrict__ longt, uint32_t* __restrict__ cbase,
+                                                          uint2* __restrict__ citem, int64_t chunk_cap) {
   __shared__ unsigned long long s_w[32];
+  __shared__ uint32_t s_wc[32];
   __shared__ unsigned long long s_carry;
+  __shared__ uint32_t s_ccarry;
   __shared__ uint32_t s_bucket[kOrderBuckets];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) s_carry = 0;
+  if (tid == 0) {
+    s_carry = 0;
+    s_ccarry = 0;
+  }
   if (tid < kOrderBuckets) s_bucket[tid] = 0;
   __syncthreads();
   for (uint32_t b0 = 0; b0 < n_tiles; b0 += kScanCta) {
     const uint32_t t = b0 + tid;
     const unsigned long long x = t < n_tiles ? tcur[t] : 0ull;
+    // backward chunks of the list: ceil(n / kChunk) for n <= kLongList
+    // entries (longer lists have their own kernels)
+    const uint32_t xc = x <= kLongList ? static_cast<uint32_t>((x + kChunk - 1) / kChunk) : 0u;
     unsigned long long v = x;
+    uint32_t vc = xc;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
+      const uint32_t yc = __shfl_up_sync(0xffffffffu, vc, o);
+      if (lane >= o) {
+        v += y;
+        vc += yc;
+      }
     }
-    if (lane == 31) s_w[wid] = v;
+    if (lane == 31) {
+      s_w[wid] = v;
+      s_wc[wid] = vc;
+    }
     __syncthreads();
     unsigned long long wpre = 0, tot = 0;
+    uint32_t cpre = 0, ctot = 0;
     for (int i = 0; i < 32; ++i) {
-      if (i < wid) wpre += s_w[i];
+      if (i < wid) {
+        wpre += s_w[i];
+        cpre += s_wc[i];
+      }
       tot += s_w[i];
+      ctot += s_wc[i];
     }
     const unsigned long long start = s_carry + wpre + v - x;
     if (t < n_tiles) {
@@ -254,9 +276,19 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
       const uint32_t s32 = static_cast<uint32_t>(start);
       tcur[t] = s32;
       ranges[t] = x ? make_uint2(s32, static_cast<uint32_t>(start + x)) : make_uint2(0u, 0u);   // empty: (0, 0)
+      // first chunk of the tile and the (tile, index) of each of its chunks
+      const uint32_t first = s_ccarry + cpre + vc - xc;
+      cbase[t] = first;
+      // (past the pair capacity the chunk table may not fit: then nothing is
+      // emitted and no chunk is used, so the entries are dropped)
+      for (uint32_t c = 0; c < xc; ++c)
+        if (static_cast<int64_t>(first) + c < chunk_cap) citem[first + c] = make_uint2(t, c);
     }
     __syncthreads();
-    if (tid == 0) s_carry += tot;
+    if (tid == 0) {
+      s_carry += tot;
+      s_ccarry += ctot;
+    }
     __syncthreads();
   }
   const unsigned long long total = s_carry;
@@ -265,6 +297,7 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
     st->required_pairs = total;
     st->overflow = over ? 1u : 0u;
     st->n_pairs = over ? 0ull : total;
+    st->n_chunks = over ? 0u : s_ccarry;   // at most pairs / kChunk + tiles
   }
   if (over) {
     // nothing is emitted: every tile renders empty
@@ -608,7 +641,8 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
   const int64_t ni = n_items > 0 ? n_items : 1;
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
   k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tcur, w.st);
-  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work, w.longt);
+  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work, w.longt, w.cbase,
+                                     w.citem, L.chunks_cap);
   k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.box, w.tcur, w.ranges, w.st, w.pkey);
   if (n_tiles > 0) {
     k_tile_sort_merge<<<n_tiles, kMergeCta, 0, s>>>(w.ranges, w.st, w.pkey, w.ptile, w.pv);

@@ -71,11 +71,13 @@ struct Status {
   unsigned long long contrib_bwd;
   unsigned long long alg_fwd;         // list entries up to and including each pixel's stop point
   unsigned int loss_ticket;           // loss CTAs finished (the last one reduces; self-resetting)
+  unsigned int n_chunks;              // backward chunks of the last binning (kChunk list entries each)
 };
 
 struct Layout {
-  size_t desc, status, tables, rec, box, key, cnt, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part, total;
-  int64_t items_cap, pairs_cap;
+  size_t desc, status, tables, rec, box, key, cnt, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part, cbase,
+      citem, ckpt, total;
+  int64_t items_cap, pairs_cap, chunks_cap;
   uint32_t tiles_cap;
   uint32_t tables_cap;     // floats
   int32_t loss_blocks;
@@ -98,6 +100,9 @@ struct WsPtrs {
   uint32_t* work;          // persistent scheduler tile order
   uint32_t* longt;         // tiles with lists longer than kLongList (st->n_long of them)
   double* loss_part;       // loss partial sums and mask counts
+  uint32_t* cbase;         // [tiles] first backward chunk of every tile
+  uint2* citem;            // [chunks] (tile, chunk index in the tile) of every chunk
+  float* ckpt;             // [chunks][6][tile pixels] forward checkpoint at every chunk end
 };
 
 inline WsPtrs ws_ptrs(void* base, const Layout& L) {
@@ -119,6 +124,9 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.work = reinterpret_cast<uint32_t*>(b + L.work);
   p.longt = reinterpret_cast<uint32_t*>(b + L.longt);
   p.loss_part = reinterpret_cast<double*>(b + L.loss_part);
+  p.cbase = reinterpret_cast<uint32_t*>(b + L.cbase);
+  p.citem = reinterpret_cast<uint2*>(b + L.citem);
+  p.ckpt = reinterpret_cast<float*>(b + L.ckpt);
   return p;
 }
 
@@ -416,6 +424,12 @@ __device__ __forceinline__ bool box_hits(const float4& b, const WarpBox& w) {
 // whole list one entry at a time).
 constexpr uint32_t kLongList = 4096;
 
+// Backward work unit of the chunked walk: kChunk consecutive entries of a
+// tile list.  The forward records, per pixel, at the end of every chunk the
+// transmittance and the chunk's own sums of w, w t and w n' (a checkpoint of
+// six floats), so every chunk's reverse walk can start on its own.
+constexpr uint32_t kChunk = 64;
+
 struct Eval {
   float den, rden, t, ud, vd, u, v, q, G, araw, a;
   bool valid;
@@ -498,8 +512,10 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
 int bin_kernel_count(uint32_t n_tiles);
 cudaError_t launch_raster_fwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch, int group,
                               int persistent, cudaStream_t s);
+// chunked: the forward was the shared-memory walk, which wrote the chunk
+// checkpoints the chunked backward starts from.
 cudaError_t launch_raster_bwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch, int group,
-                              int persistent, cudaStream_t s);
+                              int persistent, bool chunked, cudaStream_t s);
 size_t loss_part_bytes();
 size_t noalloc_scratch_bytes();
 cudaError_t noalloc_scratch(void** out);

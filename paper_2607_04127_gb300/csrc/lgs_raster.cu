@@ -676,7 +676,7 @@ __device__ __forceinline__ void stage_hit(const float4* __restrict__ rec, uint32
 __global__ void __launch_bounds__(kMaxTileThreads)
     k_fwd_s(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
             const float4* __restrict__ rec, const float4* __restrict__ box, const uint32_t* __restrict__ order,
-            Status* __restrict__ st, int persistent) {
+            Status* __restrict__ st, int persistent, const uint32_t* __restrict__ cbase, float* __restrict__ ckpt) {
   __shared__ WarpRecs s_w[kMaxTileThreads / 32];
   const int lane = threadIdx.x & 31;
   WarpRecs& sw = s_w[threadIdx.x >> 5];
@@ -692,7 +692,26 @@ __global__ void __launch_bounds__(kMaxTileThreads)
     float T = 1.0f, A = 0.0f, St = 0.0f, Sx = 0.0f, Sy = 0.0f, Sz = 0.0f;
     int last = 0, stop_at = -1;
     bool done = !tc.inside;
+    // checkpoint of the backward chunks: this chunk's own sums, written with
+    // T at every chunk end (the chunk holding the end of the walk included)
+    float cA = 0.f, cSt = 0.f, cSx = 0.f, cSy = 0.f, cSz = 0.f;
+    uint32_t chunk = 0;
+    const int npx = static_cast<int>(blockDim.x);
+    const auto checkpoint = [&]() {
+      float* o = ckpt + (static_cast<int64_t>(cbase[tile] + chunk) * 6) * npx + threadIdx.x;
+      o[0] = T;
+      o[npx] = cA;
+      o[2 * npx] = cSt;
+      o[3 * npx] = cSx;
+      o[4 * npx] = cSy;
+      o[5 * npx] = cSz;
+      cA = cSt = cSx = cSy = cSz = 0.f;
+    };
     for (uint32_t base = tc.start; base < tc.end; base += 32) {
+      if (base - tc.start >= (chunk + 1) * kChunk) {
+        checkpoint();
+        ++chunk;
+      }
       if (__all_sync(0xffffffffu, done)) break;
       const uint32_t j = base + lane;
       uint32_t item = 0;
@@ -729,6 +748,11 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         Sx = fmaf(ws, r0.x, Sx);
         Sy = fmaf(ws, r0.y, Sy);
         Sz = fmaf(ws, r0.z, Sz);
+        cA += w;
+        cSt = fmaf(w, tt, cSt);
+        cSx = fmaf(ws, r0.x, cSx);
+        cSy = fmaf(ws, r0.y, cSy);
+        cSz = fmaf(ws, r0.z, cSz);
         T = comp ? Tn : T;
         last = comp ? k0 + bq : last;
         contrib += comp;
@@ -737,6 +761,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         if (__all_sync(0xffffffffu, done)) break;
       } while (m);
     }
+    if (tc.end > tc.start) checkpoint();
     if (tc.inside) {
       F.A[tc.pix] = A;
       F.St[tc.pix] = St;
@@ -856,6 +881,150 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         int idx;
         const float r = warp_reduce12(mv, lane, idx);
         if (idx >= 0 && r != 0.f) atomicAdd(g13 + 16 * static_cast<int64_t>(si[bq]) + idx, r);
+      } while (m);
+    }
+  }
+  unsigned long long ev = evals, co = contrib;
+  for (int o = 16; o > 0; o >>= 1) {
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    co += __shfl_xor_sync(0xffffffffu, co, o);
+  }
+  if (lane == 0 && ev) atomicAdd(&st->evals_bwd, ev);
+  if (lane == 0 && co) atomicAdd(&st->contrib_bwd, co);
+}
+
+// ---------------------------------------------------------------------------
+// Chunked backward (group 16 after the shared-memory forward): a work item
+// is one warp's 4 x 8 pixel block of a tile over one chunk of kChunk list
+// entries, claimed through an atomic counter.  The reverse walk of chunk c
+// starts from the forward's checkpoint: T at the end of the chunk, and the
+// suffix S = sum over the later chunks c' of gA dA_c' + gSt dSt_c' + gS .
+// dSn_c' (their own sums of w, w t, w n').  Items are independent, so a
+// frame offers several times more warps than pixel blocks.
+// ---------------------------------------------------------------------------
+constexpr int kBwdChunkCta = 256;
+
+__global__ void __launch_bounds__(kBwdChunkCta)
+    k_bwd_c(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
+            const float4* __restrict__ rec, const float4* __restrict__ box, float* __restrict__ g13,
+            const uint2* __restrict__ citem, const uint32_t* __restrict__ cbase, const float* __restrict__ ckpt,
+            Status* __restrict__ st) {
+  __shared__ WarpRecs s_w[kBwdChunkCta / 32];
+  __shared__ uint32_t s_item[kBwdChunkCta / 32][32];
+  const int lane = threadIdx.x & 31;
+  WarpRecs& sw = s_w[threadIdx.x >> 5];
+  uint32_t* si = s_item[threadIdx.x >> 5];
+  const int npx = D->th * D->tw, wpt = npx >> 5;
+  const uint32_t n_work = st->n_chunks * static_cast<uint32_t>(wpt);
+  uint32_t evals = 0, contrib = 0;
+  while (true) {
+    uint32_t id = 0;
+    if (lane == 0) id = atomicAdd(&st->work_counter2, 1u);
+    id = __shfl_sync(0xffffffffu, id, 0);
+    if (id >= n_work) break;
+    const uint32_t k = id / static_cast<uint32_t>(wpt);
+    const int vt = static_cast<int>(id - k * static_cast<uint32_t>(wpt)) * 32 + lane;   // thread of the tile
+    const uint2 ci = citem[k];
+    const uint32_t tile = ci.x, c = ci.y;
+    const int f = frame_of_tile(*D, tile);
+    const FrameDev& F = D->f[f];
+    const int lt = static_cast<int>(tile - F.tile_base);
+    const int ti = lt / F.ntc, tj = lt - ti * F.ntc;
+    int lr, lc;
+    pixel_of_thread(F, vt, lr, lc);
+    const int r = ti * F.th + lr, col = tj * F.tw + lc;
+    const bool inside = r < F.H && col < F.W;
+    const int HW = F.H * F.W;
+    const int64_t pix = static_cast<int64_t>(r) * F.W + col;
+    const uint2 rg = ranges[tile];
+    const int k_lo = static_cast<int>(c * kChunk);
+    const int nc = inside ? F.nc[pix] : 0;
+    const bool act = nc > k_lo;
+    const WarpBox wb = warp_box(act, r, col, F.W);
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    float T = 1.f, S = 0.f, gA = 0.f, gSt = 0.f, gSx = 0.f, gSy = 0.f, gSz = 0.f;
+    if (act) {
+      pixel_ray(F, r, col, dx, dy, dz);
+      gA = F.gA[pix];
+      gSt = F.gSt[pix];
+      gSx = F.gSn[pix];
+      gSy = F.gSn[HW + pix];
+      gSz = F.gSn[2 * static_cast<int64_t>(HW) + pix];
+      const float* o = ckpt + (static_cast<int64_t>(cbase[tile] + c) * 6) * npx + vt;
+      T = o[0];
+      const uint32_t c_last = static_cast<uint32_t>(nc - 1) / kChunk;
+      for (uint32_t c2 = c + 1; c2 <= c_last; ++c2) {
+        const float* q = ckpt + (static_cast<int64_t>(cbase[tile] + c2) * 6) * npx + vt;
+        S += gA * q[npx] + gSt * q[2 * npx] + gSx * q[3 * npx] + gSy * q[4 * npx] + gSz * q[5 * npx];
+      }
+    }
+    // entries [k_lo, k_hi) of the list, walked down in 32-entry steps; a
+    // lane takes the entries below its pixel's n_contrib
+    const uint32_t len = rg.y - rg.x;
+    const int k_hi = static_cast<int>(min(min(static_cast<uint32_t>(k_lo) + kChunk, len),
+                                          static_cast<uint32_t>(__reduce_max_sync(0xffffffffu, act ? nc : 0))));
+    for (int k0 = k_lo + ((k_hi - k_lo + 31) / 32 - 1) * 32; k0 >= k_lo; k0 -= 32) {
+      uint32_t item = 0;
+      bool hit = false;
+      if (k0 + lane < k_hi) {
+        item = __ldg(pv + rg.x + k0 + lane);
+        hit = box_hits(__ldg(box + item), wb);
+      }
+      uint32_t m = __ballot_sync(0xffffffffu, hit);
+      if (!m) continue;
+      __syncwarp();
+      if (hit) {
+        stage_hit(rec, item, sw, lane);
+        si[lane] = item;
+      }
+      __syncwarp();
+      do {
+        const int bq = 31 - __clz(m);
+        m &= ~(1u << bq);
+        const bool in = k0 + bq < nc;
+        const float4 r0 = sw.r0[bq];
+        Eval e;
+        eval_pair(r0, sw.r1[bq], sw.r2[bq], sw.al[bq], dx, dy, dz, e);
+        const bool valid = in && e.valid;
+        evals += in;
+        contrib += valid;
+        if (!__any_sync(0xffffffffu, valid)) continue;
+        // invalid lanes: zero opacity and finite inputs, so every moment is
+        // exactly 0 and T, S pass through unchanged
+        const float a = valid ? e.a : 0.f;
+        const float araw = valid ? e.araw : 0.f;
+        const float t = valid ? e.t : 0.f;
+        const float u = valid ? e.u : 0.f;
+        const float v = valid ? e.v : 0.f;
+        const float rden = valid ? e.rden : 0.f;
+        const float iom = rcp_ftz(1.0f - a);
+        const float Tk = T * iom;
+        const float sg = e.den > 0.f ? -1.f : 1.f;
+        const float gc = gA + gSt * t + sg * (gSx * r0.x + gSy * r0.y + gSz * r0.z);
+        const float w = a * Tk;
+        const float dLda = Tk * gc - S * iom;
+        S = fmaf(w, gc, S);
+        T = Tk;
+        const float g = araw < 0.99f ? araw * dLda : 0.f;
+        const float ug = u * g, vg = v * g;
+        const float ct = fmaf(w, gSt, -fmaf(ug, e.ud, vg * e.vd)) * rden;
+        const float wsg = w * sg;
+        float mv[12];
+        mv[0] = g;
+        mv[1] = ug;
+        mv[2] = vg;
+        mv[3] = u * ug;
+        mv[4] = v * vg;
+        mv[5] = u * vg;
+        mv[6] = ct;
+        mv[7] = ct * u;
+        mv[8] = ct * v;
+        mv[9] = wsg * gSx;
+        mv[10] = wsg * gSy;
+        mv[11] = wsg * gSz;
+        int idx;
+        const float red = warp_reduce12(mv, lane, idx);
+        if (idx >= 0 && red != 0.f) atomicAdd(g13 + 16 * static_cast<int64_t>(si[bq]) + idx, red);
       } while (m);
     }
   }
@@ -1166,7 +1335,9 @@ static cudaError_t launch_raster_fwd_tiles(const WsPtrs& w, const Desc& h, const
   const uint32_t* ord = persistent ? w.work : nullptr;
   switch (batch) {
     case 0:
-      if (group == 16) k_fwd_s<<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
+      if (group == 16)
+        k_fwd_s<<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent, w.cbase,
+                                             w.ckpt);
       else if (group == 1) k_fwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       else if (group == 2) k_fwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       else k_fwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
@@ -1207,9 +1378,24 @@ cudaError_t launch_raster_fwd(const Layout&, const WsPtrs& w, const Desc& h, con
   return launch_long(true, w, pv, s);
 }
 
+// Chunked backward: as many resident CTAs as fit, warps claim (chunk, pixel
+// block) items until none are left.
+static cudaError_t launch_raster_bwd_chunks(const WsPtrs& w, const uint32_t* pv, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&w.st->work_counter2, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 152, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_c, kBwdChunkCta, 0);
+  k_bwd_c<<<sms * (per_sm > 0 ? per_sm : 1), kBwdChunkCta, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13,
+                                                                     w.citem, w.cbase, w.ckpt, w.st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
-                              int group, int persistent, cudaStream_t s) {
-  cudaError_t e = launch_raster_bwd_tiles(w, h, pv, batch, group, persistent, s);
+                              int group, int persistent, bool chunked, cudaStream_t s) {
+  cudaError_t e = chunked ? launch_raster_bwd_chunks(w, pv, s)
+                          : launch_raster_bwd_tiles(w, h, pv, batch, group, persistent, s);
   if (e != cudaSuccess) return e;
   return launch_long(false, w, pv, s);
 }
