@@ -83,9 +83,16 @@ def measured_traffic(kernel):
 
 
 def kname(tuning, which):
+    """Name of the compositing kernel a tuning runs for the forward or the
+    backward (the chunked backward follows the shared-memory forward)."""
     b = tuning["fwd_batch" if which == "fwd" else "bwd_batch"]
-    base = "k_fwd" if which == "fwd" else "k_bwd"
-    return f"{base}_w<{tuning['group']}>" if b == 0 else f"{base}<{b}>"
+    if b:
+        return f"k_fwd<{b}>" if which == "fwd" else f"k_bwd<{b}>"
+    if tuning["group"] == 16:
+        if which == "fwd":
+            return "k_fwd_s"
+        return "k_bwd_c" if tuning["fwd_batch"] == 0 else "k_bwd_s"
+    return f"k_fwd_w<{tuning['group']}>" if which == "fwd" else f"k_bwd_w<{tuning['group']}>"
 
 
 def dist_env():

@@ -57,6 +57,7 @@ __global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, St
     st->contrib_bwd = 0;
     st->alg_fwd = 0;
     st->loss_ticket = 0;
+    st->count_ticket = 0;
     st->n_long = 0;
     st->long_counter_fwd = 0;
     st->long_counter_bwd = 0;
@@ -225,8 +226,7 @@ __device__ __forceinline__ int order_bucket(uint32_t n) { return kOrderBuckets -
 __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ tcur, uint32_t n_tiles,
                                                           uint2* __restrict__ ranges, Status* __restrict__ st,
                                                           int64_t cap, uint32_t* __restrict__ order,
-                                                          uint32_t* __restrict__ longt, uint32_t* __restrict__ cbase,
-                                                          uint2* __restrict__ citem, int64_t chunk_cap) {
+                                                          uint32_t* __restrict__ longt, uint32_t* __restrict__ cbase) {
   __shared__ unsigned long long s_w[32];
   __shared__ uint32_t s_wc[32];
   __shared__ unsigned long long s_carry;
@@ -276,13 +276,9 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
       const uint32_t s32 = static_cast<uint32_t>(start);
       tcur[t] = s32;
       ranges[t] = x ? make_uint2(s32, static_cast<uint32_t>(start + x)) : make_uint2(0u, 0u);   // empty: (0, 0)
-      // first chunk of the tile and the (tile, index) of each of its chunks
-      const uint32_t first = s_ccarry + cpre + vc - xc;
-      cbase[t] = first;
-      // (past the pair capacity the chunk table may not fit: then nothing is
-      // emitted and no chunk is used, so the entries are dropped)
-      for (uint32_t c = 0; c < xc; ++c)
-        if (static_cast<int64_t>(first) + c < chunk_cap) citem[first + c] = make_uint2(t, c);
+      // first chunk of the tile (non-decreasing over tiles: the chunk of a
+      // global chunk index is found by binary search)
+      cbase[t] = s_ccarry + cpre + vc - xc;
     }
     __syncthreads();
     if (tid == 0) {
@@ -307,9 +303,13 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
   // power-of-two class first (order inside a class is arbitrary; results do
   // not depend on it).  Both passes read the final ranges.
   __syncthreads();
-  for (uint32_t t = tid; t < n_tiles; t += kScanCta) {
-    const uint2 rg = ranges[t];
-    atomicAdd(&s_bucket[order_bucket(rg.y - rg.x)], 1u);
+  // one shared atomic per distinct class in a warp (most tiles of a frame
+  // fall in a few classes, so per-tile atomics would serialise)
+  for (uint32_t b0 = 0; b0 < n_tiles; b0 += kScanCta) {
+    const uint32_t t = b0 + tid;
+    const int b = t < n_tiles ? order_bucket(ranges[t].y - ranges[t].x) : -1;
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_bucket[b], static_cast<uint32_t>(__popc(peers)));
   }
   __syncthreads();
   if (tid == 0) {
@@ -321,10 +321,18 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
     }
   }
   __syncthreads();
-  for (uint32_t t = tid; t < n_tiles; t += kScanCta) {
-    const uint2 rg = ranges[t];
-    order[atomicAdd(&s_bucket[order_bucket(rg.y - rg.x)], 1u)] = t;
-    if (rg.y - rg.x > kLongList) longt[atomicAdd(&st->n_long, 1u)] = t;
+  for (uint32_t b0 = 0; b0 < n_tiles; b0 += kScanCta) {
+    const uint32_t t = b0 + tid;
+    uint2 rg = make_uint2(0u, 0u);
+    if (t < n_tiles) rg = ranges[t];
+    const int b = t < n_tiles ? order_bucket(rg.y - rg.x) : -1;
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t pos = 0;
+    if (b >= 0 && lane == leader) pos = atomicAdd(&s_bucket[b], static_cast<uint32_t>(__popc(peers)));
+    pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & ((1u << lane) - 1u));
+    if (b >= 0) order[pos] = t;
+    if (t < n_tiles && rg.y - rg.x > kLongList) longt[atomicAdd(&st->n_long, 1u)] = t;
   }
 }
 
@@ -641,8 +649,7 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
   const int64_t ni = n_items > 0 ? n_items : 1;
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
   k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tcur, w.st);
-  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work, w.longt, w.cbase,
-                                     w.citem, L.chunks_cap);
+  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work, w.longt, w.cbase);
   k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.box, w.tcur, w.ranges, w.st, w.pkey);
   if (n_tiles > 0) {
     k_tile_sort_merge<<<n_tiles, kMergeCta, 0, s>>>(w.ranges, w.st, w.pkey, w.ptile, w.pv);

@@ -72,11 +72,12 @@ struct Status {
   unsigned long long alg_fwd;         // list entries up to and including each pixel's stop point
   unsigned int loss_ticket;           // loss CTAs finished (the last one reduces; self-resetting)
   unsigned int n_chunks;              // backward chunks of the last binning (kChunk list entries each)
+  unsigned int count_ticket;          // mask-count CTAs finished (the last one adds up; self-resetting)
 };
 
 struct Layout {
   size_t desc, status, tables, rec, box, key, cnt, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part, cbase,
-      citem, ckpt, total;
+      ckpt, total;
   int64_t items_cap, pairs_cap, chunks_cap;
   uint32_t tiles_cap;
   uint32_t tables_cap;     // floats
@@ -101,7 +102,6 @@ struct WsPtrs {
   uint32_t* longt;         // tiles with lists longer than kLongList (st->n_long of them)
   double* loss_part;       // loss partial sums and mask counts
   uint32_t* cbase;         // [tiles] first backward chunk of every tile
-  uint2* citem;            // [chunks] (tile, chunk index in the tile) of every chunk
   float* ckpt;             // [chunks][6][tile pixels] forward checkpoint at every chunk end
 };
 
@@ -125,7 +125,6 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.longt = reinterpret_cast<uint32_t*>(b + L.longt);
   p.loss_part = reinterpret_cast<double*>(b + L.loss_part);
   p.cbase = reinterpret_cast<uint32_t*>(b + L.cbase);
-  p.citem = reinterpret_cast<uint2*>(b + L.citem);
   p.ckpt = reinterpret_cast<float*>(b + L.ckpt);
   return p;
 }
@@ -482,6 +481,30 @@ __device__ __forceinline__ void pixel_ray(const FrameDev& F, int r, int c, float
   dx = ct * cp;
   dy = ct * sp;
   dz = st;
+}
+
+// Mean of a loss term from its double sum over n pixels (0 for an empty
+// mask), divided in binary32.
+__device__ __forceinline__ float loss_mean(double sum, int n) {
+  return n ? static_cast<float>(sum) / static_cast<float>(n) : 0.0f;
+}
+
+// Final reduction of the loss partial sums, by one warp: component k (< NV)
+// of n partials laid out as base[4 b + k]; lane l adds partials l, l + 32,
+// ... in order, then a butterfly over the lanes (every lane gets the sums).
+// The fixed order both loss entry points use, so their terms agree bitwise.
+template <int NV>
+__device__ __forceinline__ void warp_sum_partials(const double* __restrict__ base, int n, double (&a)[4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a[k] = 0.0;
+  for (int b = lane; b < n; b += 32) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) a[k] += __ldcg(base + 4 * b + k);
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
 }
 
 // Frame of a global tile id (binary search over the frames' tile bases).

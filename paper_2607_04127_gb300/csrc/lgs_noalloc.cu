@@ -182,29 +182,39 @@ __global__ void __launch_bounds__(kNaThreads) k_na_main(NaFrames fr, NaScratch s
     s_last = atomicAdd(sc.ticket, 1u) == gridDim.x * gridDim.y - 1;
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last || threadIdx.x >= 32) return;
   __threadfence();
-  if (threadIdx.x == 0) *sc.ticket = 0u;
-  double L = 0.0;   // thread 0
+  // the first warp of the last CTA: partial sums in the fixed order of
+  // warp_sum_partials (the order the session loss uses), terms per lane
+  __shared__ double s_fr[LGS_NOALLOC_MAX_FRAMES][3];
+  const int lane = threadIdx.x;
+  if (lane == 0) *sc.ticket = 0u;
   for (int g = 0; g < fr.n; ++g) {
-    double a0 = 0, a1 = 0, a2 = 0;
-    for (int b = threadIdx.x; b < kNaBlocks; b += blockDim.x) {
-      const double* o = sc.part + 4 * (static_cast<int64_t>(g) * kNaBlocks + b);
-      a0 += __ldcg(o);
-      a1 += __ldcg(o + 1);
-      a2 += __ldcg(o + 2);
-    }
-    const double s0 = na_block_sum(a0, s_w), s1 = na_block_sum(a1, s_w), s2 = na_block_sum(a2, s_w);
-    const int2 c = na_counts(sc.cpart, g, s_i);
-    if (threadIdx.x == 0) {
-      const double Ld = c.x ? s0 / c.x : 0.0, La = c.x ? s1 / c.x : 0.0, Ln = c.y ? s2 / c.y : 0.0;
-      out[1 + 3 * g] = static_cast<float>(Ld);
-      out[2 + 3 * g] = static_cast<float>(La);
-      out[3 + 3 * g] = static_cast<float>(Ln);
-      L += (Ld + P.lambda_alpha * La + static_cast<double>(P.lambda_n) * P.lambda_ng * Ln) / fr.n;
-    }
+    double a[4];
+    warp_sum_partials<3>(sc.part + 4 * static_cast<int64_t>(g) * kNaBlocks, kNaBlocks, a);
+    if (lane == 0)
+      for (int k = 0; k < 3; ++k) s_fr[g][k] = a[k];
   }
-  if (threadIdx.x == 0) out[0] = static_cast<float>(L);
+  __syncwarp();
+  for (int g = lane; g < fr.n; g += 32) {
+    int cd = 0, cn = 0;
+    for (int b = 0; b < kNaBlocks; ++b) {
+      cd += __ldcg(sc.cpart + 2 * (g * kNaBlocks + b));
+      cn += __ldcg(sc.cpart + 2 * (g * kNaBlocks + b) + 1);
+    }
+    const float Ld = loss_mean(s_fr[g][0], cd), La = loss_mean(s_fr[g][1], cd), Ln = loss_mean(s_fr[g][2], cn);
+    out[1 + 3 * g] = Ld;
+    out[2 + 3 * g] = La;
+    out[3 + 3 * g] = Ln;
+    s_fr[g][0] = static_cast<double>(Ld + P.lambda_alpha * La + P.lambda_n * P.lambda_ng * Ln) /
+                 static_cast<double>(fr.n);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double L = 0.0;
+    for (int g = 0; g < fr.n; ++g) L += s_fr[g][0];
+    out[0] = static_cast<float>(L);
+  }
 }
 
 std::mutex g_mu;

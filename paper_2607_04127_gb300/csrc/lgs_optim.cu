@@ -31,7 +31,7 @@ __device__ __forceinline__ int map_of_surfel(const Desc& D, int64_t s) {
   return lo;
 }
 
-__global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__ D, float* __restrict__ g13) {
+__global__ void __launch_bounds__(256, 4) k_preprocess_bwd(const Desc* __restrict__ D, float* __restrict__ g13) {
   const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= D->n_surf) return;
   const int m = map_of_surfel(*D, s);
@@ -39,14 +39,16 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__
   const int64_t i = s - M.surf_base;
   if (i >= M.n) return;
   const float4 q = reinterpret_cast<const float4*>(M.quat)[i];
+  const float lg = M.logit[i];
+  const float ls0 = M.ls[2 * i], ls1 = M.ls[2 * i + 1];
   const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
   const float inv = rsqrtf(qn2);
   const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
   const float c0[3] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y)};
   const float c1[3] = {2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x)};
   const float c2[3] = {2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y)};
-  const float alpha = 1.0f / (1.0f + expf(-M.logit[i]));
-  const float su = expf(M.ls[2 * i]), sv = expf(M.ls[2 * i + 1]);
+  const float alpha = 1.0f / (1.0f + expf(-lg));
+  const float su = expf(ls0), sv = expf(ls1);
   float gm[3] = {0.f, 0.f, 0.f}, G0[3] = {0.f, 0.f, 0.f}, G1[3] = {0.f, 0.f, 0.f}, G2[3] = {0.f, 0.f, 0.f};
   float gls0 = 0.f, gls1 = 0.f, gsum = 0.f;
   bool any = false;
@@ -147,8 +149,32 @@ __device__ __forceinline__ double block_sum_d(double v, double* s_w) {
   return t;
 }
 
-// Mask counts per (frame, CTA): [F][kLossBlocks][2] ints, no atomics.
-__global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, int* __restrict__ cpart) {
+// Four block sums at once, each in the order block_sum_d uses (warp
+// butterfly, then warp totals in warp order by thread 0): one barrier pair
+// instead of four.  Valid in thread 0.
+__device__ __forceinline__ void block_sum_d4(double (&v)[4], double (*s_w4)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s_w4[wid][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double t = 0.0;
+      for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) t += s_w4[i][k];
+      v[k] = t;
+    }
+}
+
+// Mask counts per (frame, CTA): [F][kLossBlocks][2] ints, no atomics; the
+// CTA that finishes last adds them up into ctot[F][2] (integers: any order).
+__global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, int* __restrict__ cpart,
+                                                     int* __restrict__ ctot, Status* __restrict__ st) {
   const FrameDev& F = D->f[blockIdx.y];
   const int HW = F.H * F.W;
   int md = 0, mn = 0;
@@ -179,34 +205,32 @@ __global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, 
     o[0] = a;
     o[1] = b;
   }
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&st->count_ticket, 1u) == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int f = wid; f < D->n_frames; f += static_cast<int>(blockDim.x >> 5)) {
+    int a = 0, b = 0;
+    for (int i = lane; i < kLossBlocks; i += 32) {
+      a += __ldcg(cpart + 2 * (f * kLossBlocks + i));
+      b += __ldcg(cpart + 2 * (f * kLossBlocks + i) + 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      ctot[2 * f] = a;
+      ctot[2 * f + 1] = b;
+    }
+  }
+  if (threadIdx.x == 0) st->count_ticket = 0;
 }
 
-// |M_D|, |M_N| of frame f from the per-CTA counts; every thread of the CTA
-// calls it and receives the totals.
-__device__ __forceinline__ int2 mask_counts(const int* __restrict__ cpart, int f, int* s_i) {
-  int a = 0, b = 0;
-  for (int i = threadIdx.x; i < kLossBlocks; i += blockDim.x) {
-    a += cpart[2 * (f * kLossBlocks + i)];
-    b += cpart[2 * (f * kLossBlocks + i) + 1];
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = static_cast<int>(blockDim.x >> 5);
-  __syncthreads();
-  if (lane == 0) {
-    s_i[2 * wid] = a;
-    s_i[2 * wid + 1] = b;
-  }
-  __syncthreads();
-  int ta = 0, tb = 0;
-  for (int i = 0; i < nw; ++i) {
-    ta += s_i[2 * i];
-    tb += s_i[2 * i + 1];
-  }
-  return make_int2(ta, tb);
-}
 
 // ---- the N_surf term of Eq. normalloss ---------------------------------------
 // X = Dh d: the rendered range of pixel (r, c) back-projected along its ray.
@@ -273,18 +297,17 @@ __device__ bool ns_term(const FrameDev& F, int r, int c, float k, NsTerm& t) {
 // finishes last reduces every partial sum in a fixed order (deterministic)
 // and writes the loss vector.
 __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, Status* __restrict__ st,
-                                                    lgs_loss_params P, int write_grad, const int* __restrict__ cpart,
+                                                    lgs_loss_params P, int write_grad, const int* __restrict__ ctot,
                                                     double* __restrict__ part, double* __restrict__ spart,
                                                     float* __restrict__ out) {
   __shared__ double s_w[8];
-  __shared__ int s_i[16];
+  __shared__ double s_w4[8][4];
   __shared__ bool s_last;
   if (blockIdx.y < static_cast<unsigned>(D->n_frames)) {
     const int f = blockIdx.y;
     const FrameDev& F = D->f[f];
     const int HW = F.H * F.W;
-    const int2 cnt = mask_counts(cpart, f, s_i);
-    const int nd = cnt.x, nn = cnt.y;
+    const int nd = __ldcg(ctot + 2 * f), nn = __ldcg(ctot + 2 * f + 1);
     const float scale = 1.0f / static_cast<float>(D->m[F.map].n_frames);
     const float ind = nd > 0 ? 1.0f / static_cast<float>(nd) : 0.f;
     const float inn = nn > 0 ? 1.0f / static_cast<float>(nn) : 0.f;
@@ -292,9 +315,13 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
     double ld = 0.0, la = 0.0, ln = 0.0, ls = 0.0;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
       float gA = 0.f, gSt = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+      // every plane of the pixel is loaded before any decision, so the loads
+      // of a pixel overlap instead of following the mask test
       const float Dm = F.D[p];
+      const float A = F.A[p], St = F.St[p];
+      const float nx = F.Ng[p], ny = F.Ng[HW + p], nz = F.Ng[2 * HW + p];
+      const float sx = F.Sn[p], sy = F.Sn[HW + p], sz = F.Sn[2 * HW + p];
       if (Dm > 0.f) {
-        const float A = F.A[p], St = F.St[p];
         const float a = A + 1e-6f;
         const float Dh = St / a;
         const float diff = Dh - Dm;
@@ -308,9 +335,7 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
         // where A + 1e-6 is exact to half an ulp
         la -= A >= 0.5f ? log1pf((A - 1.0f) + 1e-6f) : logf(A + 1e-6f);
         gA -= scale * P.lambda_alpha * ind / (A + 1e-6f);
-        const float nx = F.Ng[p], ny = F.Ng[HW + p], nz = F.Ng[2 * HW + p];
         if (nx * nx + ny * ny + nz * nz > 0.f) {
-          const float sx = F.Sn[p], sy = F.Sn[HW + p], sz = F.Sn[2 * HW + p];
           const float m = sqrtf(sx * sx + sy * sy + sz * sz + 1e-12f);
           const float im = 1.f / m;
           ln += 1.0 - static_cast<double>((sx * nx + sy * ny + sz * nz) * im);
@@ -349,16 +374,14 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
       F.oSn[HW + p] = gy;
       F.oSn[2 * HW + p] = gz;
     }
-    const double t0 = block_sum_d(ld, s_w);
-    const double t1 = block_sum_d(la, s_w);
-    const double t2 = block_sum_d(ln, s_w);
-    const double t3 = block_sum_d(ls, s_w);
+    double t[4] = {ld, la, ln, ls};
+    block_sum_d4(t, s_w4);
     if (threadIdx.x == 0) {
       double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + blockIdx.x);
-      o[0] = t0;
-      o[1] = t1;
-      o[2] = t2;
-      o[3] = t3;
+      o[0] = t[0];
+      o[1] = t[1];
+      o[2] = t[2];
+      o[3] = t[3];
     }
   } else {
     const int mi = blockIdx.y - D->n_frames;
@@ -378,58 +401,64 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
     if (threadIdx.x == 0) spart[mi * kLossBlocks + blockIdx.x] = t;
   }
 
-  // last CTA: deterministic reduction of the partial sums (fixed order:
-  // strided per-thread sums, then the fixed block tree)
+  // last CTA: deterministic reduction of the partial sums by its first warp
+  // (fixed order, warp_sum_partials); the per-frame terms are formed by the
+  // lanes in parallel, the map totals by lane 0 in frame order
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned total = gridDim.x * gridDim.y;
     s_last = atomicAdd(&st->loss_ticket, 1u) == total - 1;
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last || threadIdx.x >= 32) return;
   __threadfence();
-  if (threadIdx.x == 0) st->loss_ticket = 0;
-  double Lmap[LGS_MAX_MAPS];   // thread 0 only
-  for (int m = 0; m < D->n_maps; ++m) Lmap[m] = 0.0;
-  for (int f = 0; f < D->n_frames; ++f) {
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    for (int b = threadIdx.x; b < kLossBlocks; b += blockDim.x) {
-      const double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + b);
-      a0 += __ldcg(o);
-      a1 += __ldcg(o + 1);
-      a2 += __ldcg(o + 2);
-      a3 += __ldcg(o + 3);
-    }
-    const double s0 = block_sum_d(a0, s_w), s1 = block_sum_d(a1, s_w), s2 = block_sum_d(a2, s_w);
-    const double s3 = block_sum_d(a3, s_w);
-    const int2 cnt = mask_counts(cpart, f, s_i);
-    if (threadIdx.x == 0) {
-      const int nd = cnt.x, nn = cnt.y;
-      const double Ld = nd ? s0 / nd : 0.0, La = nd ? s1 / nd : 0.0, Ln = nn ? s2 / nn : 0.0;
-      const double Ls = nd ? s3 / nd : 0.0;
-      float* o = out + 1 + LGS_LOSS_TERMS * f;
-      o[0] = static_cast<float>(Ld);
-      o[1] = static_cast<float>(La);
-      o[2] = static_cast<float>(Ln);
-      o[3] = static_cast<float>(Ls);
-      const int m = D->f[f].map;
-      Lmap[m] += (Ld + P.lambda_alpha * La + static_cast<double>(P.lambda_n) * P.lambda_ng * Ln +
-                  static_cast<double>(P.lambda_n) * P.lambda_ns * Ls) /
-                 D->m[m].n_frames;
-    }
+  __shared__ double s_fr[LGS_MAX_FRAMES][4];
+  __shared__ double s_mp[LGS_MAX_MAPS];
+  const int lane = threadIdx.x;
+  if (lane == 0) st->loss_ticket = 0;
+  const int nf = D->n_frames, nmap = D->n_maps;
+  for (int f = 0; f < nf; ++f) {
+    double a[4];
+    warp_sum_partials<4>(part + 4 * static_cast<int64_t>(f) * kLossBlocks, kLossBlocks, a);
+    if (lane == 0)
+      for (int k = 0; k < 4; ++k) s_fr[f][k] = a[k];
   }
-  double L = 0.0;
-  for (int m = 0; m < D->n_maps; ++m) {
-    double a = 0;
-    for (int b = threadIdx.x; b < kLossBlocks; b += blockDim.x) a += __ldcg(spart + m * kLossBlocks + b);
-    const double sr = block_sum_d(a, s_w);
-    if (threadIdx.x == 0) {
-      Lmap[m] += P.lambda_s * sr;
-      out[1 + LGS_LOSS_TERMS * D->n_frames + m] = static_cast<float>(Lmap[m]);
+  __syncwarp();
+  for (int f = lane; f < nf; f += 32) {
+    const int nd = __ldcg(ctot + 2 * f), nn = __ldcg(ctot + 2 * f + 1);
+    // means in binary32 (the sums are double; FP64 division is slow here)
+    const float Ld = loss_mean(s_fr[f][0], nd), La = loss_mean(s_fr[f][1], nd);
+    const float Ln = loss_mean(s_fr[f][2], nn), Ls = loss_mean(s_fr[f][3], nd);
+    float* o = out + 1 + LGS_LOSS_TERMS * f;
+    o[0] = Ld;
+    o[1] = La;
+    o[2] = Ln;
+    o[3] = Ls;
+    s_fr[f][0] = static_cast<double>(Ld + P.lambda_alpha * La + P.lambda_n * P.lambda_ng * Ln +
+                                     P.lambda_n * P.lambda_ns * Ls) /
+                 static_cast<double>(D->m[D->f[f].map].n_frames);
+  }
+  for (int m = 0; m < nmap; ++m) {
+    double a[4];
+    // spart is [maps][kLossBlocks] doubles: read as one component of stride 1
+    a[0] = 0.0;
+    for (int b = lane; b < kLossBlocks; b += 32) a[0] += __ldcg(spart + m * kLossBlocks + b);
+    for (int o = 16; o > 0; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+    if (lane == 0) s_mp[m] = P.lambda_s * a[0];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double Lmap[LGS_MAX_MAPS];
+    for (int m = 0; m < nmap; ++m) Lmap[m] = 0.0;
+    for (int f = 0; f < nf; ++f) Lmap[D->f[f].map] += s_fr[f][0];
+    double L = 0.0;
+    for (int m = 0; m < nmap; ++m) {
+      Lmap[m] += s_mp[m];
+      out[1 + LGS_LOSS_TERMS * nf + m] = static_cast<float>(Lmap[m]);
       L += Lmap[m];
     }
+    out[0] = static_cast<float>(L);
   }
-  if (threadIdx.x == 0) out[0] = static_cast<float>(L);
 }
 
 cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
@@ -437,8 +466,9 @@ cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs
   double* part = w.loss_part;
   double* spart = part + 4 * static_cast<int64_t>(LGS_MAX_FRAMES) * kLossBlocks;
   int* cpart = reinterpret_cast<int*>(spart + static_cast<int64_t>(LGS_MAX_MAPS) * kLossBlocks);
-  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, cpart);
-  k_loss_main<<<dim3(kLossBlocks, h.n_frames + h.n_maps), 256, 0, s>>>(w.desc, w.st, p, scale_grad ? 1 : 0, cpart,
+  int* ctot = cpart + 2 * static_cast<int64_t>(LGS_MAX_FRAMES) * kLossBlocks;
+  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, cpart, ctot, w.st);
+  k_loss_main<<<dim3(kLossBlocks, h.n_frames + h.n_maps), 256, 0, s>>>(w.desc, w.st, p, scale_grad ? 1 : 0, ctot,
                                                                         part, spart, loss_out);
   return cudaGetLastError();
 }
@@ -446,7 +476,7 @@ cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs
 size_t loss_part_bytes() {
   return sizeof(double) * (4 * static_cast<size_t>(LGS_MAX_FRAMES) * kLossBlocks +
                            static_cast<size_t>(LGS_MAX_MAPS) * kLossBlocks) +
-         sizeof(int) * 2 * static_cast<size_t>(LGS_MAX_FRAMES) * kLossBlocks;
+         sizeof(int) * 2 * static_cast<size_t>(LGS_MAX_FRAMES) * (kLossBlocks + 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -907,8 +907,7 @@ constexpr int kBwdChunkCta = 256;
 __global__ void __launch_bounds__(kBwdChunkCta)
     k_bwd_c(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
             const float4* __restrict__ rec, const float4* __restrict__ box, float* __restrict__ g13,
-            const uint2* __restrict__ citem, const uint32_t* __restrict__ cbase, const float* __restrict__ ckpt,
-            Status* __restrict__ st) {
+            const uint32_t* __restrict__ cbase, const float* __restrict__ ckpt, Status* __restrict__ st) {
   __shared__ WarpRecs s_w[kBwdChunkCta / 32];
   __shared__ uint32_t s_item[kBwdChunkCta / 32][32];
   const int lane = threadIdx.x & 31;
@@ -924,8 +923,14 @@ __global__ void __launch_bounds__(kBwdChunkCta)
     if (id >= n_work) break;
     const uint32_t k = id / static_cast<uint32_t>(wpt);
     const int vt = static_cast<int>(id - k * static_cast<uint32_t>(wpt)) * 32 + lane;   // thread of the tile
-    const uint2 ci = citem[k];
-    const uint32_t tile = ci.x, c = ci.y;
+    // tile of chunk k: the last tile whose first chunk is <= k (tiles
+    // without chunks share their successor's first chunk)
+    uint32_t lo = 0, hi = D->n_tiles - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (__ldg(cbase + mid) <= k) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t tile = lo, c = k - __ldg(cbase + lo);
     const int f = frame_of_tile(*D, tile);
     const FrameDev& F = D->f[f];
     const int lt = static_cast<int>(tile - F.tile_base);
@@ -1388,7 +1393,7 @@ static cudaError_t launch_raster_bwd_chunks(const WsPtrs& w, const uint32_t* pv,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_c, kBwdChunkCta, 0);
   k_bwd_c<<<sms * (per_sm > 0 ? per_sm : 1), kBwdChunkCta, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13,
-                                                                     w.citem, w.cbase, w.ckpt, w.st);
+                                                                     w.cbase, w.ckpt, w.st);
   return cudaGetLastError();
 }
 
