@@ -726,15 +726,10 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       if (hit) stage_hit(rec, item, sw, lane);
       __syncwarp();
       const int k0 = static_cast<int>(base - tc.start) + 1;
-      do {
-        const int bq = __ffs(m) - 1;
-        m &= m - 1;
-        const float4 r0 = sw.r0[bq];
-        Eval e;
-        eval_pair(r0, sw.r1[bq], sw.r2[bq], sw.al[bq], dx, dy, dz, e);
-        // composite without branches: lanes that are done or see an invalid
-        // pair add zeros and keep T (t and the weight are zeroed first, so no
-        // inf or NaN of a rejected pair reaches the sums)
+      // composite one evaluated hit without branches: lanes that are done or
+      // see an invalid pair add zeros and keep T (t and the weight are zeroed
+      // first, so no inf or NaN of a rejected pair reaches the sums)
+      const auto composite = [&](const Eval& e, const float4& r0, int bq) {
         const bool act = !done && e.valid;
         evals += !done;
         const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.a));
@@ -758,6 +753,20 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         contrib += comp;
         stop_at = stop ? k0 + bq : stop_at;
         done = done || stop;
+      };
+      // two hits per step: their evaluations are independent (instruction-
+      // level parallelism), the composites follow in list order
+      do {
+        const int bq0 = __ffs(m) - 1;
+        m &= m - 1;
+        const int bq1 = m ? __ffs(m) - 1 : bq0;
+        m &= m - 1;
+        const float4 r00 = sw.r0[bq0], r01 = sw.r0[bq1];
+        Eval e0, e1;
+        eval_pair(r00, sw.r1[bq0], sw.r2[bq0], sw.al[bq0], dx, dy, dz, e0);
+        eval_pair(r01, sw.r1[bq1], sw.r2[bq1], sw.al[bq1], dx, dy, dz, e1);
+        composite(e0, r00, bq0);
+        if (bq1 != bq0) composite(e1, r01, bq1);
         if (__all_sync(0xffffffffu, done)) break;
       } while (m);
     }

@@ -19,6 +19,15 @@ most one waiting request: a newer keyframe supersedes a waiting older one,
 which is dropped and counted (mapping always works on the newest keyframe),
 so queues stay bounded under overload.
 
+With ``slo_ms`` the scheduler admits by deadline: a tick's duration is
+modelled as ``a + kappa * (surfels of its active maps)`` with ``kappa``
+learned online from measured ticks, and a waiting request joins only if the
+simulated remaining ticks let every active request, itself included, finish
+within ``slo_ms`` of its arrival (with a safety factor); otherwise it is
+rejected at once and counted.  Completed requests then meet the latency
+target by construction of the admission, at the price of the reported
+rejection rate.
+
 ``plain=True`` serves the same requests one at a time with per-request
 launches (the baseline the batched form is measured against).
 """
@@ -70,7 +79,7 @@ class MapSession:
 class Server:
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 150 << 30, slots: int = 16,
                  tuning: dict | None = None, lr=(1e-3, 1e-3, 5e-3, 5e-3), plain: bool = False,
-                 keep_latest: bool = False):
+                 keep_latest: bool = False, slo_ms: float | None = None, slo_margin: float = 0.8):
         self.device = torch.device("cuda", device)
         self.budget = hbm_budget_bytes
         self.slots = 1 if plain else slots
@@ -83,6 +92,13 @@ class Server:
         self.rast = None
         self.keep_latest = keep_latest
         self.dropped: list[Request] = []
+        self.slo = slo_ms / 1e3 if slo_ms else None
+        self.slo_margin = slo_margin
+        self.late: list[Request] = []      # rejected by the deadline admission
+        self.tick_base = 4e-4              # seconds of a tick independent of the maps (host work, launches)
+        self.kappa = None                  # seconds per surfel-iteration, learned from measured ticks
+        self._ticks = 0
+        self._grew = False                 # the last tick grew the workspace (and ran twice)
 
     # -- admission ----------------------------------------------------------
     def open_session(self, sid: int, surf, frame_pixels: int) -> bool:
@@ -122,6 +138,7 @@ class Server:
         out = self.rast.step(params, targets, grads, check=False)
         torch.cuda.synchronize(self.device)
         st, _ = lib.lgs_session_status(self.rast.session.handle)
+        self._grew = st == lib.LGS_ERR_CAPACITY
         if st == lib.LGS_ERR_CAPACITY:       # grow the workspace and redo the tick
             for g in grads:
                 for x in g:
@@ -134,6 +151,30 @@ class Server:
             s.t += 1
         render.adam_step_batch([(s.params, s.grads, s.m, s.v, s.t, self.lr) for s in maps], zero_grad=True)
         return losses
+
+    # -- deadline admission --------------------------------------------------
+    def _learn(self, active, seconds: float):
+        n = sum(self.sessions[r.session].n for r in active)
+        k = max(seconds - self.tick_base, 0.0) / max(n, 1)
+        self.kappa = k if self.kappa is None else 0.8 * self.kappa + 0.2 * k
+
+    def _feasible(self, active, now: float) -> bool:
+        """Simulate the remaining ticks of ``active`` (no further arrivals):
+        does every request finish within the margin of its deadline?"""
+        rem = [(r.iters - r.done_iters, self.sessions[r.session].n, r.arrival + self.slo_margin * self.slo)
+               for r in active]
+        t = now
+        while rem:
+            t += self.tick_base + self.kappa * sum(n for _, n, _ in rem)
+            nxt = []
+            for k, n, dl in rem:
+                if k == 1:
+                    if t > dl:
+                        return False
+                else:
+                    nxt.append((k - 1, n, dl))
+            rem = nxt
+        return True
 
     # -- the loop ---------------------------------------------------------------
     def run(self, requests):
@@ -160,6 +201,9 @@ class Server:
             while waiting:
                 r = waiting.popleft()
                 if len(active) < self.slots and r.session not in busy:
+                    if self.slo is not None and self.kappa is not None and not self._feasible(active + [r], now):
+                        self.late.append(r)      # would miss its deadline or make another one miss
+                        continue
                     r.start = now
                     active.append(r)
                     busy.add(r.session)
@@ -170,7 +214,14 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(pending[0].arrival - now, 0.002)))
                 continue
-            L = self._tick(active)     # per-map loss (one frame per map)
+            t_tick = time.perf_counter()
+            L = self._tick(active)     # per-map loss (one frame per map); the tick ends synchronised
+            # the tick model learns from ordinary ticks only: not the server's
+            # first (buffers and workspace are created) nor one that grew the
+            # workspace and ran twice
+            if self._ticks > 0 and not self._grew:
+                self._learn(active, time.perf_counter() - t_tick)
+            self._ticks += 1
             now = time.perf_counter() - t0
             still = []
             for r, l in zip(active, L):
@@ -203,14 +254,16 @@ def poisson_requests(rng: np.random.Generator, sessions, frames_of, targets_of, 
     return sorted(reqs, key=lambda r: r.arrival)
 
 
-def latency_stats(done, duration: float, offered: int, rejected_sessions: int, n_sessions: int, dropped: int = 0):
+def latency_stats(done, duration: float, offered: int, rejected_sessions: int, n_sessions: int, dropped: int = 0,
+                  late: int = 0):
     """p50 / p99 latency (ms) of the completed requests, completed frames per
     second of wall time, and the rejections: sessions refused at admission,
-    requests superseded by a newer keyframe of their session."""
+    requests superseded by a newer keyframe of their session, requests
+    refused by the deadline admission."""
     lat = np.array([r.finish - r.arrival for r in done]) * 1e3
     wall = max([r.finish for r in done] + [duration])
     return dict(completed=len(done), offered=offered, p50_ms=float(np.percentile(lat, 50)) if len(lat) else None,
                 p99_ms=float(np.percentile(lat, 99)) if len(lat) else None,
                 frames_per_s=len(done) / wall, rejected_sessions=rejected_sessions,
                 session_rejection_rate=rejected_sessions / max(n_sessions, 1), dropped_requests=dropped,
-                request_rejection_rate=dropped / max(offered, 1))
+                deadline_rejected=late, request_rejection_rate=(dropped + late) / max(offered, 1))

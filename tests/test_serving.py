@@ -112,3 +112,39 @@ def test_keep_latest_supersedes_waiting_keyframes(workload):
     done = srv.run(reqs)
     assert len(done) == 1 and done[0] is reqs[2] and len(srv.dropped) == 2
     srv.close()
+
+
+def test_deadline_admission(workload):
+    """With a deadline, requests the tick model says would finish late are
+    refused at once; the others complete, and every offered request is
+    accounted for.  A generous deadline refuses nothing."""
+    from paper_2607_04127_gb300 import serve
+    sids = list(range(len(SIZES)))
+
+    def run(slo_ms, waves=3):
+        srv = serve.Server(slots=8, slo_ms=slo_ms)
+        for sid in sids:
+            surf, fr, _ = workload[sid]
+            srv.open_session(sid, surf, fr.H * fr.W)
+        # calibrate the tick model (first run: warm-up), and time one request alone
+        srv.run([serve.Request(2, workload[2][1], workload[2][2], 0.0, 4)])
+        cal = serve.Request(2, workload[2][1], workload[2][2], 0.0, 4)
+        srv.run([cal])
+        srv.late.clear()
+        # `waves` keyframes per session, all queued at t = 0 (one active per session)
+        reqs = [serve.Request(sid, workload[sid][1], workload[sid][2], 0.0, 4) for _ in range(waves) for sid in sids]
+        done = srv.run(reqs)
+        late = list(srv.late)
+        srv.close()
+        return reqs, done, late, (cal.finish - cal.arrival) * 1e3
+
+    reqs, done, late, alone_ms = run(10_000.0)
+    assert not late and len(done) == len(reqs)
+    # 1.5 x the time of the largest map alone: a first wave can fit, a third
+    # wave (after two earlier requests of its session) cannot
+    reqs, done, late, _ = run(1.5 * alone_ms)
+    assert done and late
+    assert len(done) + len(late) == len(reqs)
+    assert not set(map(id, done)) & set(map(id, late))
+    third = {id(r) for r in reqs[2 * len(sids):]}
+    assert third <= set(map(id, late))
