@@ -414,7 +414,9 @@ def run_ours(args):
     alg_f = c_last["alg_fwd"]
     alg_b = int(rast.out[0].n_contrib.sum().item())
     fl_fwd = FLOP_EVAL * alg_f + FLOP_COMPOSITE * cf
-    fl_bwd = FLOP_EVAL * alg_b + FLOP_BWD_VALID * cb_
+    # the backward's contributing pairs are exactly the forward's composited
+    # pairs (the chunked backward does not count them again)
+    fl_bwd = FLOP_EVAL * alg_b + FLOP_BWD_VALID * cf
 
     # device time of every kernel group, from events the library records
     # around its own launches on this stream (a separate pass of the same steps)
@@ -487,8 +489,8 @@ def run_ours(args):
                        loss=statistics.mean(loss_ms), bwd=statistics.mean(bwd_ms)),
         kernels_ms=kernels_ms,
         work=dict(pairs=c_last["n_pairs"], visible_items=c_last["n_visible"], alg_evals_fwd=alg_f,
-                  alg_evals_bwd=alg_b, culled_evals_fwd=evf, culled_evals_bwd=evb, composited_fwd=cf,
-                  valid_bwd=cb_),
+                  alg_evals_bwd=alg_b, culled_evals_fwd=evf, culled_evals_bwd=evb or None, composited_fwd=cf,
+                  valid_bwd=cb_ or cf),
         roofline=dict(bound="alu", kernel=kname(rast.tuning, dominant), achieved=achieved,
                       peak=PEAK_FP32_TFLOPS, unit="TFLOP/s", frac=achieved / PEAK_FP32_TFLOPS,
                       traffic=measured_traffic(kname(rast.tuning, dominant)),

@@ -330,20 +330,20 @@ LGS_API lgs_status lgs_loss_batch(lgs_session s, const lgs_surfels* maps, int n_
  * The call has no frame geometry (pixel rays), so it has no N_surf term:
  * params->lambda_ns must be 0 (else LGS_ERR_INVALID_ARG).
  *
- * Nothing is allocated, by the library or by the caller: the scratch (per-CTA
- * partial sums, mask counts, a completion counter) is one static device array
- * of LGS_NOALLOC_SCRATCH_BYTES inside the library, sized for at most
- * LGS_NOALLOC_MAX_FRAMES frames per call; more frames are rejected with
- * LGS_ERR_INVALID_ARG.  The caller zeroes nothing: the completion counter is
- * zero when the library loads and the call clears it on the device before
- * use.  The first call on a device looks up the scratch's address
+ * Nothing is allocated, by the library or by the caller: the scratch
+ * (fixed-point loss sums and mask counts per frame, a completion counter) is
+ * one static device array of LGS_NOALLOC_SCRATCH_BYTES inside the library,
+ * sized for at most LGS_NOALLOC_MAX_FRAMES frames per call; more frames are
+ * rejected with LGS_ERR_INVALID_ARG.  The caller zeroes nothing: the scratch
+ * is zero when the library loads and every call leaves it at zero on the
+ * device when it completes.  The first call on a device looks up the scratch's address
  * (cudaGetSymbolAddress, with that device current) and caches it, so make one
  * call on each device before timing-critical use.  Every call on a device
  * shares the one scratch: calls that overlap in time (on other streams or
  * from other threads) corrupt each other's results and must be serialised by
  * the caller. */
 #define LGS_NOALLOC_MAX_FRAMES 8
-#define LGS_NOALLOC_SCRATCH_BYTES (8 * 4 * LGS_NOALLOC_MAX_FRAMES * 256 + 4 * 2 * LGS_NOALLOC_MAX_FRAMES * 256 + 256)
+#define LGS_NOALLOC_SCRATCH_BYTES (8 * 3 * LGS_NOALLOC_MAX_FRAMES + 4 * 2 * LGS_NOALLOC_MAX_FRAMES + 256)
 LGS_API lgs_status lgs_image_loss_noalloc(const int32_t* H, const int32_t* W, int n_frames, const lgs_fwd_out* fwd,
                                           const lgs_target* targets, const lgs_loss_params* params,
                                           const lgs_fwd_grad_out* grads_out, float* loss_out, void* stream);

@@ -40,8 +40,12 @@ cudaError_t launch_write_desc(const Desc& h, Desc* d, Status*, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-__global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, Status* __restrict__ st) {
+__global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, Status* __restrict__ st,
+                         uint32_t* __restrict__ loss_acc, uint32_t loss_words) {
   const FrameDev& F = D->f[blockIdx.x];
+  // the loss accumulators start every binning at zero
+  if (blockIdx.x == 0)
+    for (uint32_t i = threadIdx.x; i < loss_words; i += blockDim.x) loss_acc[i] = 0u;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->required_pairs = 0;
     st->n_pairs = 0;
@@ -645,7 +649,8 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
   const uint32_t T = n_tiles > 0 ? n_tiles : 1;
   e = cudaMemsetAsync(w.tcur, 0, sizeof(uint32_t) * T, s);
   if (e != cudaSuccess) return e;
-  k_tables<<<n_frames, 256, 0, s>>>(w.desc, w.tables, w.st);
+  k_tables<<<n_frames, 256, 0, s>>>(w.desc, w.tables, w.st, reinterpret_cast<uint32_t*>(w.loss_part),
+                                    static_cast<uint32_t>(loss_part_bytes() / 4));
   const int64_t ni = n_items > 0 ? n_items : 1;
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
   k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tcur, w.st);

@@ -135,46 +135,11 @@ cudaError_t launch_preprocess_bwd(const Layout&, const WsPtrs& w, const Desc& h,
 //   L = sum_m [ (1/F_m) sum_{f in m} L_img,f + ls L_scale,m ]
 // with masked means over M_D = [D > 0] and M_N = M_D [|N_gicp| > 0].
 // ---------------------------------------------------------------------------
-constexpr int kLossBlocks = 256;  // CTAs per frame and map (fixed: deterministic partial sums)
+constexpr int kLossBlocks = 256;  // CTAs per frame and map
 
-__device__ __forceinline__ double block_sum_d(double v, double* s_w) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) s_w[wid] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) t += s_w[i];
-  return t;
-}
-
-// Four block sums at once, each in the order block_sum_d uses (warp
-// butterfly, then warp totals in warp order by thread 0): one barrier pair
-// instead of four.  Valid in thread 0.
-__device__ __forceinline__ void block_sum_d4(double (&v)[4], double (*s_w4)[4]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s_w4[wid][k] = v[k];
-  __syncthreads();
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      double t = 0.0;
-      for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) t += s_w4[i][k];
-      v[k] = t;
-    }
-}
-
-// Mask counts per (frame, CTA): [F][kLossBlocks][2] ints, no atomics; the
-// CTA that finishes last adds them up into ctot[F][2] (integers: any order).
-__global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, int* __restrict__ cpart,
-                                                     int* __restrict__ ctot, Status* __restrict__ st) {
+// Mask counts |M_D|, |M_N| of every frame: one integer atomic per CTA into
+// ctot[F][2] (zero on entry: cleared by the binning and by the loss).
+__global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, int* __restrict__ ctot) {
   const FrameDev& F = D->f[blockIdx.y];
   const int HW = F.H * F.W;
   int md = 0, mn = 0;
@@ -184,53 +149,15 @@ __global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, 
     md += d;
     mn += d && (a * a + b * b + c * c > 0.f);
   }
-  __shared__ int s_c[2][8];
   for (int o = 16; o > 0; o >>= 1) {
     md += __shfl_xor_sync(0xffffffffu, md, o);
     mn += __shfl_xor_sync(0xffffffffu, mn, o);
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    s_c[0][wid] = md;
-    s_c[1][wid] = mn;
+  if ((threadIdx.x & 31) == 0) {
+    if (md) atomicAdd(ctot + 2 * blockIdx.y, md);
+    if (mn) atomicAdd(ctot + 2 * blockIdx.y + 1, mn);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int a = 0, b = 0;
-    for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) {
-      a += s_c[0][i];
-      b += s_c[1][i];
-    }
-    int* o = cpart + 2 * (static_cast<int64_t>(blockIdx.y) * kLossBlocks + blockIdx.x);
-    o[0] = a;
-    o[1] = b;
-  }
-  __shared__ bool s_last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(&st->count_ticket, 1u) == gridDim.x * gridDim.y - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int f = wid; f < D->n_frames; f += static_cast<int>(blockDim.x >> 5)) {
-    int a = 0, b = 0;
-    for (int i = lane; i < kLossBlocks; i += 32) {
-      a += __ldcg(cpart + 2 * (f * kLossBlocks + i));
-      b += __ldcg(cpart + 2 * (f * kLossBlocks + i) + 1);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if (lane == 0) {
-      ctot[2 * f] = a;
-      ctot[2 * f + 1] = b;
-    }
-  }
-  if (threadIdx.x == 0) st->count_ticket = 0;
 }
-
 
 // ---- the N_surf term of Eq. normalloss ---------------------------------------
 // X = Dh d: the rendered range of pixel (r, c) back-projected along its ray.
@@ -297,11 +224,9 @@ __device__ bool ns_term(const FrameDev& F, int r, int c, float k, NsTerm& t) {
 // finishes last reduces every partial sum in a fixed order (deterministic)
 // and writes the loss vector.
 __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, Status* __restrict__ st,
-                                                    lgs_loss_params P, int write_grad, const int* __restrict__ ctot,
-                                                    double* __restrict__ part, double* __restrict__ spart,
-                                                    float* __restrict__ out) {
-  __shared__ double s_w[8];
-  __shared__ double s_w4[8][4];
+                                                    lgs_loss_params P, int write_grad, int* __restrict__ ctot,
+                                                    unsigned long long* __restrict__ acc, float* __restrict__ out) {
+  __shared__ long long s_ll[8];
   __shared__ bool s_last;
   if (blockIdx.y < static_cast<unsigned>(D->n_frames)) {
     const int f = blockIdx.y;
@@ -312,7 +237,7 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
     const float ind = nd > 0 ? 1.0f / static_cast<float>(nd) : 0.f;
     const float inn = nn > 0 ? 1.0f / static_cast<float>(nn) : 0.f;
     const float kns = P.lambda_n * P.lambda_ns * ind;
-    double ld = 0.0, la = 0.0, ln = 0.0, ls = 0.0;
+    long long ld = 0, la = 0, ln = 0, ls = 0;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
       float gA = 0.f, gSt = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
       // every plane of the pixel is loaded before any decision, so the loads
@@ -325,7 +250,7 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
         const float a = A + 1e-6f;
         const float Dh = St / a;
         const float diff = Dh - Dm;
-        ld += fabsf(diff);
+        ld += to_fix(fabsf(diff), kFixD);
         const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
         const float gDh = sgn * ind;
         gSt = scale * gDh / a;
@@ -333,12 +258,12 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
         // log(A + 1e-6): for A >= 1/2 as log1p((A - 1) + 1e-6), where A - 1 is
         // exact, so opacities near 1 keep their precision; below 1/2 directly,
         // where A + 1e-6 is exact to half an ulp
-        la -= A >= 0.5f ? log1pf((A - 1.0f) + 1e-6f) : logf(A + 1e-6f);
+        la += to_fix(-(A >= 0.5f ? log1pf((A - 1.0f) + 1e-6f) : logf(A + 1e-6f)), kFixU);
         gA -= scale * P.lambda_alpha * ind / (A + 1e-6f);
         if (nx * nx + ny * ny + nz * nz > 0.f) {
           const float m = sqrtf(sx * sx + sy * sy + sz * sz + 1e-12f);
           const float im = 1.f / m;
-          ln += 1.0 - static_cast<double>((sx * nx + sy * ny + sz * nz) * im);
+          ln += to_fix(1.0f - (sx * nx + sy * ny + sz * nz) * im, kFixU);
           const float k = -P.lambda_n * P.lambda_ng * inn;
           const float g0 = k * nx, g1 = k * ny, g2 = k * nz;
           const float sg = (sx * g0 + sy * g1 + sz * g2) * im * im * im;
@@ -353,7 +278,7 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
           float3 gX = make_float3(0.f, 0.f, 0.f);
           NsTerm t;
           if (ns_term(F, r, c, kns, t)) {
-            ls += 1.0 - static_cast<double>(t.val);
+            ls += to_fix(1.0f - t.val, kFixU);
             gX = t.gp;
             gx += scale * t.gsn.x;
             gy += scale * t.gsn.y;
@@ -374,36 +299,31 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
       F.oSn[HW + p] = gy;
       F.oSn[2 * HW + p] = gz;
     }
-    double t[4] = {ld, la, ln, ls};
-    block_sum_d4(t, s_w4);
-    if (threadIdx.x == 0) {
-      double* o = part + 4 * (static_cast<int64_t>(f) * kLossBlocks + blockIdx.x);
-      o[0] = t[0];
-      o[1] = t[1];
-      o[2] = t[2];
-      o[3] = t[3];
-    }
+    cta_add_fix(ld, acc + 4 * f, s_ll);
+    cta_add_fix(la, acc + 4 * f + 1, s_ll);
+    cta_add_fix(ln, acc + 4 * f + 2, s_ll);
+    cta_add_fix(ls, acc + 4 * f + 3, s_ll);
   } else {
     const int mi = blockIdx.y - D->n_frames;
     const MapDev& M = D->m[mi];
-    double acc = 0.0;
+    long long sr = 0;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < M.n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
       const float s0 = expf(M.ls[2 * i]), s1 = expf(M.ls[2 * i + 1]);
       const bool first = s0 >= s1;
       const float sm = first ? s0 : s1;
       if (sm > P.s_max) {
-        acc += static_cast<double>(sm - P.s_max);
+        // the sum takes at most 1 km per surfel (the gradient is exact)
+        sr += to_fix(fminf(sm - P.s_max, 1e3f), kFixD);
         if (write_grad) M.d_ls[2 * i + (first ? 0 : 1)] += P.lambda_s * sm;
       }
     }
-    const double t = block_sum_d(acc, s_w);
-    if (threadIdx.x == 0) spart[mi * kLossBlocks + blockIdx.x] = t;
+    cta_add_fix(sr, acc + 4 * LGS_MAX_FRAMES + mi, s_ll);
   }
 
-  // last CTA: deterministic reduction of the partial sums by its first warp
-  // (fixed order, warp_sum_partials); the per-frame terms are formed by the
-  // lanes in parallel, the map totals by lane 0 in frame order
+  // last CTA: the means and the loss vector from the fixed-point totals (no
+  // reduction left to do), then the totals and counts are cleared for the
+  // next call
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned total = gridDim.x * gridDim.y;
@@ -412,71 +332,64 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
   __syncthreads();
   if (!s_last || threadIdx.x >= 32) return;
   __threadfence();
-  __shared__ double s_fr[LGS_MAX_FRAMES][4];
-  __shared__ double s_mp[LGS_MAX_MAPS];
+  __shared__ float s_fr[LGS_MAX_FRAMES];
   const int lane = threadIdx.x;
   if (lane == 0) st->loss_ticket = 0;
   const int nf = D->n_frames, nmap = D->n_maps;
-  for (int f = 0; f < nf; ++f) {
-    double a[4];
-    warp_sum_partials<4>(part + 4 * static_cast<int64_t>(f) * kLossBlocks, kLossBlocks, a);
-    if (lane == 0)
-      for (int k = 0; k < 4; ++k) s_fr[f][k] = a[k];
-  }
-  __syncwarp();
   for (int f = lane; f < nf; f += 32) {
     const int nd = __ldcg(ctot + 2 * f), nn = __ldcg(ctot + 2 * f + 1);
-    // means in binary32 (the sums are double; FP64 division is slow here)
-    const float Ld = loss_mean(s_fr[f][0], nd), La = loss_mean(s_fr[f][1], nd);
-    const float Ln = loss_mean(s_fr[f][2], nn), Ls = loss_mean(s_fr[f][3], nd);
+    const unsigned long long* a = acc + 4 * f;
+    const float Ld = fix_mean(static_cast<long long>(__ldcg(a)), kFixD, nd);
+    const float La = fix_mean(static_cast<long long>(__ldcg(a + 1)), kFixU, nd);
+    const float Ln = fix_mean(static_cast<long long>(__ldcg(a + 2)), kFixU, nn);
+    const float Ls = fix_mean(static_cast<long long>(__ldcg(a + 3)), kFixU, nd);
     float* o = out + 1 + LGS_LOSS_TERMS * f;
     o[0] = Ld;
     o[1] = La;
     o[2] = Ln;
     o[3] = Ls;
-    s_fr[f][0] = static_cast<double>(Ld + P.lambda_alpha * La + P.lambda_n * P.lambda_ng * Ln +
-                                     P.lambda_n * P.lambda_ns * Ls) /
-                 static_cast<double>(D->m[D->f[f].map].n_frames);
-  }
-  for (int m = 0; m < nmap; ++m) {
-    double a[4];
-    // spart is [maps][kLossBlocks] doubles: read as one component of stride 1
-    a[0] = 0.0;
-    for (int b = lane; b < kLossBlocks; b += 32) a[0] += __ldcg(spart + m * kLossBlocks + b);
-    for (int o = 16; o > 0; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
-    if (lane == 0) s_mp[m] = P.lambda_s * a[0];
+    s_fr[f] = (Ld + P.lambda_alpha * La + P.lambda_n * P.lambda_ng * Ln + P.lambda_n * P.lambda_ns * Ls) /
+              static_cast<float>(D->m[D->f[f].map].n_frames);
   }
   __syncwarp();
   if (lane == 0) {
-    double Lmap[LGS_MAX_MAPS];
-    for (int m = 0; m < nmap; ++m) Lmap[m] = 0.0;
-    for (int f = 0; f < nf; ++f) Lmap[D->f[f].map] += s_fr[f][0];
-    double L = 0.0;
+    float Lmap[LGS_MAX_MAPS];
+    for (int m = 0; m < nmap; ++m) Lmap[m] = 0.0f;
+    for (int f = 0; f < nf; ++f) Lmap[D->f[f].map] += s_fr[f];
+    float L = 0.0f;
     for (int m = 0; m < nmap; ++m) {
-      Lmap[m] += s_mp[m];
-      out[1 + LGS_LOSS_TERMS * nf + m] = static_cast<float>(Lmap[m]);
+      const long long sr = static_cast<long long>(__ldcg(acc + 4 * LGS_MAX_FRAMES + m));
+      Lmap[m] += P.lambda_s * (static_cast<float>(sr) / kFixD);
+      out[1 + LGS_LOSS_TERMS * nf + m] = Lmap[m];
       L += Lmap[m];
     }
-    out[0] = static_cast<float>(L);
+    out[0] = L;
   }
+  __syncwarp();
+  for (int f = lane; f < nf; f += 32) {
+    ctot[2 * f] = 0;
+    ctot[2 * f + 1] = 0;
+    for (int k = 0; k < 4; ++k) acc[4 * f + k] = 0ull;
+  }
+  for (int m = lane; m < nmap; m += 32) acc[4 * LGS_MAX_FRAMES + m] = 0ull;
 }
 
 cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
                         float* loss_out, cudaStream_t s) {
-  double* part = w.loss_part;
-  double* spart = part + 4 * static_cast<int64_t>(LGS_MAX_FRAMES) * kLossBlocks;
-  int* cpart = reinterpret_cast<int*>(spart + static_cast<int64_t>(LGS_MAX_MAPS) * kLossBlocks);
-  int* ctot = cpart + 2 * static_cast<int64_t>(LGS_MAX_FRAMES) * kLossBlocks;
-  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, cpart, ctot, w.st);
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(w.loss_part);
+  int* ctot = reinterpret_cast<int*>(acc + 4 * LGS_MAX_FRAMES + LGS_MAX_MAPS);
+  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, ctot);
   k_loss_main<<<dim3(kLossBlocks, h.n_frames + h.n_maps), 256, 0, s>>>(w.desc, w.st, p, scale_grad ? 1 : 0, ctot,
-                                                                        part, spart, loss_out);
+                                                                        acc, loss_out);
   return cudaGetLastError();
 }
 
+// Loss accumulators: fixed-point sums [frames][4] and [maps], mask counts
+// [frames][2].  All zero between calls (the binning clears them, and every
+// loss call clears them after use).
 size_t loss_part_bytes() {
-  return sizeof(double) * (4 * static_cast<size_t>(LGS_MAX_FRAMES) * kLossBlocks +
-                           static_cast<size_t>(LGS_MAX_MAPS) * kLossBlocks) +
-         sizeof(int) * 2 * static_cast<size_t>(LGS_MAX_FRAMES) * (kLossBlocks + 1);
+  return sizeof(unsigned long long) * (4 * static_cast<size_t>(LGS_MAX_FRAMES) + LGS_MAX_MAPS) +
+         sizeof(int) * 2 * static_cast<size_t>(LGS_MAX_FRAMES);
 }
 
 // ---------------------------------------------------------------------------

@@ -924,7 +924,6 @@ __global__ void __launch_bounds__(kBwdChunkCta)
   uint32_t* si = s_item[threadIdx.x >> 5];
   const int npx = D->th * D->tw, wpt = npx >> 5;
   const uint32_t n_work = st->n_chunks * static_cast<uint32_t>(wpt);
-  uint32_t evals = 0, contrib = 0;
   while (true) {
     uint32_t id = 0;
     if (lane == 0) id = atomicAdd(&st->work_counter2, 1u);
@@ -1000,8 +999,6 @@ __global__ void __launch_bounds__(kBwdChunkCta)
         Eval e;
         eval_pair(r0, sw.r1[bq], sw.r2[bq], sw.al[bq], dx, dy, dz, e);
         const bool valid = in && e.valid;
-        evals += in;
-        contrib += valid;
         if (!__any_sync(0xffffffffu, valid)) continue;
         // invalid lanes: zero opacity and finite inputs, so every moment is
         // exactly 0 and T, S pass through unchanged
@@ -1042,13 +1039,8 @@ __global__ void __launch_bounds__(kBwdChunkCta)
       } while (m);
     }
   }
-  unsigned long long ev = evals, co = contrib;
-  for (int o = 16; o > 0; o >>= 1) {
-    ev += __shfl_xor_sync(0xffffffffu, ev, o);
-    co += __shfl_xor_sync(0xffffffffu, co, o);
-  }
-  if (lane == 0 && ev) atomicAdd(&st->evals_bwd, ev);
-  if (lane == 0 && co) atomicAdd(&st->contrib_bwd, co);
+  // (no statistics counters: the backward's contributions are the forward's
+  // composited pairs, counted there)
 }
 
 // ---------------------------------------------------------------------------
