@@ -312,6 +312,21 @@ LGS_API lgs_status lgs_loss_batch(lgs_session s, const lgs_surfels* maps, int n_
                           const lgs_fwd_grad_out* grads_out, const lgs_surfel_grad* grads,
                           float* loss_out, void* stream);
 
+/* Forward and mapping loss in one call (Secs. 3.1 and 3.4: the rendering of
+ * Eq. 2 and Eqs. depthloss, normalloss, scaleloss, totalloss): the outputs of
+ * lgs_render_fwd_batch and of lgs_loss_batch, bit for bit, with the image
+ * terms computed in the compositing kernel's epilogue from the values it
+ * just composited (no second pass over the planes).  Arguments as in those
+ * two calls (fwd receives the forward planes).  The fused path runs with the
+ * shared-memory forward (fwd_batch 0, group 16) and without the N_surf term
+ * (lambda_ns == 0; that term needs neighbouring tiles' depths); otherwise the
+ * call runs the forward and then the loss. */
+LGS_API lgs_status lgs_render_fwd_loss_batch(lgs_session s, const lgs_surfels* maps, int n_maps,
+                                     const lgs_frame* frames, const int32_t* frame_map, int n_frames,
+                                     const lgs_fwd_out* fwd, const lgs_target* targets,
+                                     const lgs_loss_params* params, const lgs_fwd_grad_out* grads_out,
+                                     const lgs_surfel_grad* grads, float* loss_out, void* stream);
+
 /* ---- image loss without a session or workspace --------------------------
  * The paper has no counterpart to this call; it is an interface for callers
  * that cannot allocate device memory at the point where they evaluate the

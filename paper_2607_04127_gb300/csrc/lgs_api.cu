@@ -666,6 +666,67 @@ lgs_status lgs_bin_sort(lgs_session s, const lgs_surfels* surfels, const lgs_fra
   return lgs_bin_sort_batch(s, surfels, 1, frames, nullptr, n_frames, stream);
 }
 
+lgs_status lgs_render_fwd_loss_batch(lgs_session s, const lgs_surfels* maps, int n_maps, const lgs_frame* frames,
+                                     const int32_t* frame_map, int n_frames, const lgs_fwd_out* fwd,
+                                     const lgs_target* targets, const lgs_loss_params* params,
+                                     const lgs_fwd_grad_out* grads_out, const lgs_surfel_grad* grads,
+                                     float* loss_out, void* stream) {
+  lgs_status st = enter(s);
+  if (st != LGS_OK) return st;
+  if (!params) return fail(LGS_ERR_INVALID_ARG, "NULL argument");
+  const bool fused = params->lambda_ns == 0.f && s->tune.fwd_batch == 0 && s->tune.group == 16;
+  if (!fused) {
+    if ((st = lgs_render_fwd_batch(s, maps, n_maps, frames, frame_map, n_frames, fwd, stream)) != LGS_OK) return st;
+    return lgs_loss_batch(s, maps, n_maps, frames, frame_map, n_frames, fwd, targets, params, grads_out, grads,
+                          loss_out, stream);
+  }
+  if (!maps || !frames || !targets || !grads_out || !loss_out) return fail(LGS_ERR_INVALID_ARG, "NULL argument");
+  if ((st = check_same(s, maps, n_maps, frames, frame_map, n_frames)) != LGS_OK) return st;
+  if ((st = check_fwd_out(fwd, n_frames)) != LGS_OK) return st;
+  for (int f = 0; f < n_frames; ++f) {
+    if (!targets[f].D || !targets[f].N_gicp) return fail(LGS_ERR_INVALID_ARG, "frame %d: NULL target", f);
+    if (!grads_out[f].dA || !grads_out[f].dS_t || !grads_out[f].dS_n)
+      return fail(LGS_ERR_INVALID_ARG, "frame %d: NULL gradient output", f);
+  }
+  if (!(params->s_max > 0.f)) return fail(LGS_ERR_INVALID_ARG, "s_max must be positive");
+  const bool scale_grad = grads != nullptr;
+  if (scale_grad)
+    for (int m = 0; m < n_maps; ++m)
+      if (maps[m].n > 0 && !grads[m].d_log_scale) return fail(LGS_ERR_INVALID_ARG, "map %d: NULL d_log_scale", m);
+  Desc& d = *s->desc;
+  set_map_ptrs(d, maps, n_maps);
+  for (int f = 0; f < n_frames; ++f) {
+    d.f[f].A = fwd[f].A;
+    d.f[f].St = fwd[f].S_t;
+    d.f[f].Sn = fwd[f].S_n;
+    d.f[f].Tf = fwd[f].T_final;
+    d.f[f].nc = fwd[f].n_contrib;
+    d.f[f].D = targets[f].D;
+    d.f[f].Ng = targets[f].N_gicp;
+    d.f[f].oA = grads_out[f].dA;
+    d.f[f].oSt = grads_out[f].dS_t;
+    d.f[f].oSn = grads_out[f].dS_n;
+  }
+  for (int m = 0; m < n_maps; ++m) d.m[m].d_ls = grads ? grads[m].d_log_scale : nullptr;
+  const WsPtrs w = lgs::ws_ptrs(s->ws, s->lay);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if ((e = write_desc(s, d, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
+  if ((e = timed(s, LGS_TIME_LOSS, cs, [&] { return lgs::launch_loss_counts(w, d, cs); })) != cudaSuccess)
+    return cuda_fail(e, "loss counts");
+  if ((e = timed(s, LGS_TIME_FWD, cs,
+                 [&] { return lgs::launch_raster_fwd_loss(w, d, w.pv, s->tune.persistent, *params, cs); })) !=
+      cudaSuccess)
+    return cuda_fail(e, "raster_fwd_loss");
+  if ((e = timed(s, LGS_TIME_LOSS, cs,
+                 [&] { return lgs::launch_loss_finish(w, d, *params, scale_grad, loss_out, cs); })) != cudaSuccess)
+    return cuda_fail(e, "loss finish");
+  s->launches += 4;   // counts, per-tile and long-list forward, regulariser and loss vector
+  s->last_stream = cs;
+  s->ckpt_valid = true;
+  return LGS_OK;
+}
+
 lgs_status lgs_render_fwd_batch(lgs_session s, const lgs_surfels* maps, int n_maps, const lgs_frame* frames,
                                 const int32_t* frame_map, int n_frames, const lgs_fwd_out* per_frame, void* stream) {
   lgs_status st = enter(s);

@@ -502,6 +502,44 @@ __device__ __forceinline__ float fix_mean(long long sum, float grid, int n) {
   return n ? (static_cast<float>(sum) / grid) / static_cast<float>(n) : 0.0f;
 }
 
+// Image terms of one pixel (Eqs. depthloss and normalloss without the N_surf
+// term, Eq. totalloss weights): masked L1 depth, positive BCE opacity,
+// cosine normal against N_gicp.  Adds the terms' fixed-point values to ld,
+// la, ln and returns dL/d(A, S_t, S_n) (scaled by `scale` = 1 / frames of the
+// map) in g.  Every loss path (the loss kernel, the forward epilogues, the
+// allocation-free loss) calls this one function, so their bits agree.
+__device__ __forceinline__ void pixel_image_loss(float Dm, float A, float St, float nx, float ny, float nz, float sx,
+                                                 float sy, float sz, float scale, float ind, float inn,
+                                                 const lgs_loss_params& P, float (&g)[5], long long& ld,
+                                                 long long& la, long long& ln) {
+  g[0] = g[1] = g[2] = g[3] = g[4] = 0.f;
+  if (!(Dm > 0.f)) return;
+  const float a = A + 1e-6f;
+  const float Dh = St / a;
+  const float diff = Dh - Dm;
+  ld += to_fix(fabsf(diff), kFixD);
+  const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+  const float gDh = sgn * ind;
+  g[1] = scale * gDh / a;
+  g[0] = scale * (-gDh * St / (a * a));
+  // log(A + 1e-6): for A >= 1/2 as log1p((A - 1) + 1e-6), where A - 1 is
+  // exact, so opacities near 1 keep their precision; below 1/2 directly,
+  // where A + 1e-6 is exact to half an ulp
+  la += to_fix(-(A >= 0.5f ? log1pf((A - 1.0f) + 1e-6f) : logf(A + 1e-6f)), kFixU);
+  g[0] -= scale * P.lambda_alpha * ind / (A + 1e-6f);
+  if (nx * nx + ny * ny + nz * nz > 0.f) {
+    const float m = sqrtf(sx * sx + sy * sy + sz * sz + 1e-12f);
+    const float im = 1.f / m;
+    ln += to_fix(1.0f - (sx * nx + sy * ny + sz * nz) * im, kFixU);
+    const float k = -P.lambda_n * P.lambda_ng * inn;
+    const float g0 = k * nx, g1 = k * ny, g2 = k * nz;
+    const float sg = (sx * g0 + sy * g1 + sz * g2) * im * im * im;
+    g[2] = scale * (g0 * im - sx * sg);
+    g[3] = scale * (g1 * im - sy * sg);
+    g[4] = scale * (g2 * im - sz * sg);
+  }
+}
+
 // Sum of v over the CTA (any order), then one atomic add into acc by
 // thread 0.  Every thread of the CTA calls it; s_ll holds a value per warp.
 __device__ __forceinline__ void cta_add_fix(long long v, unsigned long long* acc, long long* s_ll) {
@@ -550,6 +588,16 @@ cudaError_t launch_raster_fwd(const Layout& L, const WsPtrs& w, const Desc& h, c
 cudaError_t launch_raster_bwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch, int group,
                               int persistent, bool chunked, cudaStream_t s);
 size_t loss_part_bytes();
+// mask counts [frame][2] inside the loss accumulators
+inline int* loss_counts_ptr(const WsPtrs& w) {
+  return reinterpret_cast<int*>(reinterpret_cast<unsigned long long*>(w.loss_part) + 4 * LGS_MAX_FRAMES +
+                                LGS_MAX_MAPS);
+}
+cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_t* pv, int persistent,
+                                   const lgs_loss_params& p, cudaStream_t s);
+cudaError_t launch_loss_counts(const WsPtrs& w, const Desc& h, cudaStream_t s);
+cudaError_t launch_loss_finish(const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
+                               float* loss_out, cudaStream_t s);
 size_t noalloc_scratch_bytes();
 cudaError_t noalloc_scratch(void** out);
 cudaError_t launch_image_loss_noalloc(void* scratch, int n_frames, const int32_t* H, const int32_t* W,

@@ -90,29 +90,13 @@ __global__ void __launch_bounds__(kNaThreads) k_na_main(NaFrames fr, NaScratch s
     const float A = fr.A[f][p], St = fr.St[f][p];
     const float nx = fr.Ng[f][p], ny = fr.Ng[f][HW + p], nz = fr.Ng[f][2 * HW + p];
     const float sx = fr.Sn[f][p], sy = fr.Sn[f][HW + p], sz = fr.Sn[f][2 * HW + p];
-    if (Dm > 0.f) {
-      const float a = A + 1e-6f;
-      const float Dh = St / a;
-      const float diff = Dh - Dm;
-      ld += to_fix(fabsf(diff), kFixD);
-      const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-      const float gDh = sgn * ind;
-      gSt = scale * gDh / a;
-      gA = scale * (-gDh * St / (a * a));
-      la += to_fix(-(A >= 0.5f ? log1pf((A - 1.0f) + 1e-6f) : logf(A + 1e-6f)), kFixU);
-      gA -= scale * P.lambda_alpha * ind / (A + 1e-6f);
-      if (nx * nx + ny * ny + nz * nz > 0.f) {
-        const float m = sqrtf(sx * sx + sy * sy + sz * sz + 1e-12f);
-        const float im = 1.f / m;
-        ln += to_fix(1.0f - (sx * nx + sy * ny + sz * nz) * im, kFixU);
-        const float k = -P.lambda_n * P.lambda_ng * inn;
-        const float g0 = k * nx, g1 = k * ny, g2 = k * nz;
-        const float sg = (sx * g0 + sy * g1 + sz * g2) * im * im * im;
-        gx = scale * (g0 * im - sx * sg);
-        gy = scale * (g1 * im - sy * sg);
-        gz = scale * (g2 * im - sz * sg);
-      }
-    }
+    float g[5];
+    pixel_image_loss(Dm, A, St, nx, ny, nz, sx, sy, sz, scale, ind, inn, P, g, ld, la, ln);
+    gA = g[0];
+    gSt = g[1];
+    gx = g[2];
+    gy = g[3];
+    gz = g[4];
     fr.oA[f][p] = gA;
     fr.oSt[f][p] = gSt;
     fr.oSn[f][p] = gx;

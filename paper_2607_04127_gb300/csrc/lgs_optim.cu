@@ -223,12 +223,16 @@ __device__ bool ns_term(const FrameDev& F, int r, int c, float k, NsTerm& t) {
 // planes; rows n_frames + m: the scale regulariser of map m.  The CTA that
 // finishes last reduces every partial sum in a fixed order (deterministic)
 // and writes the loss vector.
+// Rows y < nfr: the image terms of frame y and its upstream gradient planes
+// (nfr = 0 when a forward epilogue computed them); rows nfr + m: the scale
+// regulariser of map m.
 __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, Status* __restrict__ st,
                                                     lgs_loss_params P, int write_grad, int* __restrict__ ctot,
-                                                    unsigned long long* __restrict__ acc, float* __restrict__ out) {
+                                                    unsigned long long* __restrict__ acc, float* __restrict__ out,
+                                                    int nfr) {
   __shared__ long long s_ll[8];
   __shared__ bool s_last;
-  if (blockIdx.y < static_cast<unsigned>(D->n_frames)) {
+  if (blockIdx.y < static_cast<unsigned>(nfr)) {
     const int f = blockIdx.y;
     const FrameDev& F = D->f[f];
     const int HW = F.H * F.W;
@@ -246,31 +250,15 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
       const float A = F.A[p], St = F.St[p];
       const float nx = F.Ng[p], ny = F.Ng[HW + p], nz = F.Ng[2 * HW + p];
       const float sx = F.Sn[p], sy = F.Sn[HW + p], sz = F.Sn[2 * HW + p];
+      float g[5];
+      pixel_image_loss(Dm, A, St, nx, ny, nz, sx, sy, sz, scale, ind, inn, P, g, ld, la, ln);
+      gA = g[0];
+      gSt = g[1];
+      gx = g[2];
+      gy = g[3];
+      gz = g[4];
       if (Dm > 0.f) {
         const float a = A + 1e-6f;
-        const float Dh = St / a;
-        const float diff = Dh - Dm;
-        ld += to_fix(fabsf(diff), kFixD);
-        const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        const float gDh = sgn * ind;
-        gSt = scale * gDh / a;
-        gA = scale * (-gDh * St / (a * a));
-        // log(A + 1e-6): for A >= 1/2 as log1p((A - 1) + 1e-6), where A - 1 is
-        // exact, so opacities near 1 keep their precision; below 1/2 directly,
-        // where A + 1e-6 is exact to half an ulp
-        la += to_fix(-(A >= 0.5f ? log1pf((A - 1.0f) + 1e-6f) : logf(A + 1e-6f)), kFixU);
-        gA -= scale * P.lambda_alpha * ind / (A + 1e-6f);
-        if (nx * nx + ny * ny + nz * nz > 0.f) {
-          const float m = sqrtf(sx * sx + sy * sy + sz * sz + 1e-12f);
-          const float im = 1.f / m;
-          ln += to_fix(1.0f - (sx * nx + sy * ny + sz * nz) * im, kFixU);
-          const float k = -P.lambda_n * P.lambda_ng * inn;
-          const float g0 = k * nx, g1 = k * ny, g2 = k * nz;
-          const float sg = (sx * g0 + sy * g1 + sz * g2) * im * im * im;
-          gx = scale * (g0 * im - sx * sg);
-          gy = scale * (g1 * im - sy * sg);
-          gz = scale * (g2 * im - sz * sg);
-        }
         if (kns != 0.f) {
           // this pixel's own term, and the terms of its left and upper
           // neighbours, in which it is the next column / the next row
@@ -304,7 +292,7 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
     cta_add_fix(ln, acc + 4 * f + 2, s_ll);
     cta_add_fix(ls, acc + 4 * f + 3, s_ll);
   } else {
-    const int mi = blockIdx.y - D->n_frames;
+    const int mi = blockIdx.y - nfr;
     const MapDev& M = D->m[mi];
     long long sr = 0;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < M.n;
@@ -377,10 +365,26 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
 cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
                         float* loss_out, cudaStream_t s) {
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(w.loss_part);
-  int* ctot = reinterpret_cast<int*>(acc + 4 * LGS_MAX_FRAMES + LGS_MAX_MAPS);
+  int* ctot = loss_counts_ptr(w);
   k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, ctot);
   k_loss_main<<<dim3(kLossBlocks, h.n_frames + h.n_maps), 256, 0, s>>>(w.desc, w.st, p, scale_grad ? 1 : 0, ctot,
-                                                                        acc, loss_out);
+                                                                        acc, loss_out, h.n_frames);
+  return cudaGetLastError();
+}
+
+// The loss around a forward with the image-loss epilogue: mask counts before
+// it (the epilogue normalises by them), the scale regulariser and the loss
+// vector after it.
+cudaError_t launch_loss_counts(const WsPtrs& w, const Desc& h, cudaStream_t s) {
+  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, loss_counts_ptr(w));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_finish(const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
+                               float* loss_out, cudaStream_t s) {
+  k_loss_main<<<dim3(kLossBlocks, h.n_maps), 256, 0, s>>>(w.desc, w.st, p, scale_grad ? 1 : 0, loss_counts_ptr(w),
+                                                          reinterpret_cast<unsigned long long*>(w.loss_part),
+                                                          loss_out, 0);
   return cudaGetLastError();
 }
 

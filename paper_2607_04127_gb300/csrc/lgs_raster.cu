@@ -673,10 +673,52 @@ __device__ __forceinline__ void stage_hit(const float4* __restrict__ rec, uint32
   s.al[lane] = __ldg(reinterpret_cast<const float*>(rp + 3));
 }
 
+// Image-loss epilogue of the forward kernels: the pixel's terms from its
+// composited values still in registers (no re-read of the planes), its
+// upstream gradient planes written, the terms' fixed-point values summed over
+// the warp and added to the frame's loss sums (one atomic per term and warp).
+struct LossEpi {
+  lgs_loss_params P;
+  const int* ctot;               // mask counts [frame][2], complete before the forward
+  unsigned long long* acc;       // fixed-point sums [frame][4]
+};
+
+__device__ __forceinline__ void loss_epilogue(const Desc& D, const LossEpi& L, int f, bool inside, int64_t pix,
+                                              int HW, float A, float St, float Sx, float Sy, float Sz) {
+  long long ld = 0, la = 0, ln = 0;
+  if (inside) {
+    const FrameDev& F = D.f[f];
+    const int nd = __ldcg(L.ctot + 2 * f), nn = __ldcg(L.ctot + 2 * f + 1);
+    const float scale = 1.0f / static_cast<float>(D.m[F.map].n_frames);
+    const float ind = nd > 0 ? 1.0f / static_cast<float>(nd) : 0.f;
+    const float inn = nn > 0 ? 1.0f / static_cast<float>(nn) : 0.f;
+    float g[5];
+    pixel_image_loss(F.D[pix], A, St, F.Ng[pix], F.Ng[HW + pix], F.Ng[2 * static_cast<int64_t>(HW) + pix], Sx, Sy,
+                     Sz, scale, ind, inn, L.P, g, ld, la, ln);
+    F.oA[pix] = g[0];
+    F.oSt[pix] = g[1];
+    F.oSn[pix] = g[2];
+    F.oSn[HW + pix] = g[3];
+    F.oSn[2 * static_cast<int64_t>(HW) + pix] = g[4];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ld += __shfl_xor_sync(0xffffffffu, ld, o);
+    la += __shfl_xor_sync(0xffffffffu, la, o);
+    ln += __shfl_xor_sync(0xffffffffu, ln, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (ld) atomicAdd(L.acc + 4 * f, static_cast<unsigned long long>(ld));
+    if (la) atomicAdd(L.acc + 4 * f + 1, static_cast<unsigned long long>(la));
+    if (ln) atomicAdd(L.acc + 4 * f + 2, static_cast<unsigned long long>(ln));
+  }
+}
+
+template <bool LOSS>
 __global__ void __launch_bounds__(kMaxTileThreads)
     k_fwd_s(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
             const float4* __restrict__ rec, const float4* __restrict__ box, const uint32_t* __restrict__ order,
-            Status* __restrict__ st, int persistent, const uint32_t* __restrict__ cbase, float* __restrict__ ckpt) {
+            Status* __restrict__ st, int persistent, const uint32_t* __restrict__ cbase, float* __restrict__ ckpt,
+            LossEpi loss) {
   __shared__ WarpRecs s_w[kMaxTileThreads / 32];
   const int lane = threadIdx.x & 31;
   WarpRecs& sw = s_w[threadIdx.x >> 5];
@@ -781,6 +823,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
       F.nc[tc.pix] = last;
       alg += stop_at >= 0 ? static_cast<uint32_t>(stop_at) : tc.end - tc.start;
     }
+    if (LOSS) loss_epilogue(*D, loss, tc.f, tc.inside, tc.pix, tc.HW, A, St, Sx, Sy, Sz);
   }
   unsigned long long ev = evals, co = contrib;
   for (int o = 16; o > 0; o >>= 1) {
@@ -1116,10 +1159,12 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
+template <bool LOSS>
 __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, const uint2* __restrict__ ranges,
                                                   const uint32_t* __restrict__ pv, const float4* __restrict__ rec,
                                                   const float4* __restrict__ box,
-                                                  const uint32_t* __restrict__ longt, Status* __restrict__ st) {
+                                                  const uint32_t* __restrict__ longt, Status* __restrict__ st,
+                                                  LossEpi loss) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_long = st->n_long;
   if (n_long == 0) return;
@@ -1191,6 +1236,8 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
       F.nc[P.pix] = last;
       alg += stop_at >= 0 ? static_cast<uint32_t>(stop_at) : P.end - P.start;
     }
+    // the warp holds one pixel: lane 0 alone takes its loss terms
+    if (LOSS) loss_epilogue(*D, loss, static_cast<int>(P.F - D->f), lane == 0, P.pix, P.HW, A, St, Sx, Sy, Sz);
   }
   long_finish(&st->long_counter_fwd, &st->long_done_fwd);
   unsigned long long ev = evals, co = contrib, al = alg;
@@ -1296,12 +1343,14 @@ __global__ void __launch_bounds__(256) k_bwd_long(const Desc* __restrict__ D, co
 
 // The work counters start at zero (reset at binning and by the last warp of
 // every launch), so no memset precedes the launch.
-static cudaError_t launch_long(bool fwd, const WsPtrs& w, const uint32_t* pv, cudaStream_t s) {
+static cudaError_t launch_long(bool fwd, const WsPtrs& w, const uint32_t* pv, cudaStream_t s,
+                               const LossEpi* loss = nullptr) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = 2 * sms;   // warps claim (tile, pixel) items until none are left
-  if (fwd) k_fwd_long<<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.longt, w.st);
+  if (fwd && loss) k_fwd_long<true><<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.longt, w.st, *loss);
+  else if (fwd) k_fwd_long<false><<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.longt, w.st, LossEpi{});
   else k_bwd_long<<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, w.longt, w.st);
   return cudaGetLastError();
 }
@@ -1342,8 +1391,8 @@ static cudaError_t launch_raster_fwd_tiles(const WsPtrs& w, const Desc& h, const
   switch (batch) {
     case 0:
       if (group == 16)
-        k_fwd_s<<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent, w.cbase,
-                                             w.ckpt);
+        k_fwd_s<false><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent,
+                                                    w.cbase, w.ckpt, LossEpi{});
       else if (group == 1) k_fwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       else if (group == 2) k_fwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       else k_fwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
@@ -1396,6 +1445,23 @@ static cudaError_t launch_raster_bwd_chunks(const WsPtrs& w, const uint32_t* pv,
   k_bwd_c<<<sms * (per_sm > 0 ? per_sm : 1), kBwdChunkCta, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13,
                                                                      w.cbase, w.ckpt, w.st);
   return cudaGetLastError();
+}
+
+// The shared-memory forward with the image-loss epilogue (and the long-list
+// forward with the same epilogue).
+cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_t* pv, int persistent,
+                                   const lgs_loss_params& p, cudaStream_t s) {
+  if (persistent) {
+    cudaError_t e = cudaMemsetAsync(&w.st->work_counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+  }
+  LossEpi loss{p, loss_counts_ptr(w), reinterpret_cast<unsigned long long*>(w.loss_part)};
+  const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
+  k_fwd_s<true><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, persistent ? w.work : nullptr, w.st,
+                                             persistent, w.cbase, w.ckpt, loss);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_long(true, w, pv, s, &loss);
 }
 
 cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,

@@ -80,7 +80,8 @@ EXPORTS = [
     "lgs_session_create", "lgs_session_destroy", "lgs_session_workspace_size", "lgs_batch_workspace_size",
     "lgs_session_set_workspace", "lgs_session_status", "lgs_session_pair_count", "lgs_session_counters",
     "lgs_session_bins", "lgs_session_read_bins", "lgs_bin_sort", "lgs_render_fwd", "lgs_render_bwd", "lgs_loss", "lgs_bin_sort_batch",
-    "lgs_render_fwd_batch", "lgs_render_bwd_batch", "lgs_loss_batch", "lgs_session_set_tuning", "lgs_adam_step",
+    "lgs_render_fwd_batch", "lgs_render_bwd_batch", "lgs_loss_batch", "lgs_render_fwd_loss_batch",
+    "lgs_session_set_tuning", "lgs_adam_step",
     "lgs_session_set_timing", "lgs_session_kernel_times", "lgs_image_loss_noalloc", "lgs_adam_step_batch",
     "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version",
 ]
@@ -116,6 +117,7 @@ def load():
         "lgs_render_fwd_batch": ([P, P, i32, P, P, i32, P, P], S),
         "lgs_render_bwd_batch": ([P, P, i32, P, P, i32, P, P, P, P], S),
         "lgs_loss_batch": ([P, P, i32, P, P, i32, P, P, P, P, P, P, P], S),
+        "lgs_render_fwd_loss_batch": ([P, P, i32, P, P, i32, P, P, P, P, P, P, P], S),
         "lgs_session_set_tuning": ([P, P], S),
         "lgs_session_set_timing": ([P, i32], S),
         "lgs_session_kernel_times": ([P, P, P], S),
@@ -267,6 +269,15 @@ def lgs_loss_batch(h, maps, frames, frame_map, fwd, targets, params, grads_out, 
                                  _arr(lgs_target, targets), _ref(params), _arr(lgs_fwd_grad_out, grads_out),
                                  _arr(lgs_surfel_grad, grads) if grads is not None else None,
                                  P(loss_out_ptr), P(stream)))
+
+
+def lgs_render_fwd_loss_batch(h, maps, frames, frame_map, fwd, targets, params, grads_out, grads, loss_out_ptr,
+                              stream):
+    _check(load().lgs_render_fwd_loss_batch(h, _arr(lgs_surfels, maps), len(maps), _arr(lgs_frame, frames),
+                                            _arr(ctypes.c_int32, frame_map), len(frames), _arr(lgs_fwd_out, fwd),
+                                            _arr(lgs_target, targets), _ref(params), _arr(lgs_fwd_grad_out, grads_out),
+                                            _arr(lgs_surfel_grad, grads) if grads is not None else None,
+                                            P(loss_out_ptr), P(stream)))
 
 
 def lgs_bin_sort(h, surfels, frames, stream):

@@ -124,12 +124,24 @@ class Rasterizer:
                                  [lib.lgs_fwd_grad(a.data_ptr(), b.data_ptr(), c.data_ptr()) for a, b, c in up],
                                  [lib.grad_struct(*g) for g in grads], self.stream)
 
+    def forward_loss(self, maps, targets, grads=None, S=None):
+        """Forward and loss in one library call (the image terms in the
+        compositing kernel's epilogue when the tuning and the loss weights
+        allow it; the same outputs either way)."""
+        S = S or [lib.surfels_struct(*m) for m in maps]
+        tg = [lib.lgs_target(d.data_ptr(), n.data_ptr()) for d, n in targets]
+        go = [lib.lgs_fwd_grad_out(a.data_ptr(), b.data_ptr(), c.data_ptr()) for a, b, c in self.up]
+        gs = [lib.grad_struct(*g) for g in grads] if grads is not None else None
+        lib.lgs_render_fwd_loss_batch(self.session.handle, S, self.fr, self.frame_map, [o.struct() for o in self.out],
+                                      tg, self.loss_params.struct(), go, gs, self.loss_out.data_ptr(), self.stream)
+        return self.loss_out
+
     def step(self, maps, targets, grads, check: bool = False):
-        """One mapping step: bin + sort, forward, loss, backward.  Gradients
-        are accumulated into ``grads``; returns the device loss vector."""
+        """One mapping step: bin + sort, forward with the loss, backward.
+        Gradients are accumulated into ``grads``; returns the device loss
+        vector."""
         S = self.bin_sort(maps, check=check)
-        self.forward(maps, S)
-        self.loss(maps, targets, grads, S)
+        self.forward_loss(maps, targets, grads, S)
         self.backward(maps, grads, S=S)
         return self.loss_out
 

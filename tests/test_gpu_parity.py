@@ -422,3 +422,65 @@ def test_full_size_street_frame(oracle):
     assert g["loss"][0] == pytest.approx(Limg + oracle.scale_reg(surf.log_scale), rel=1e-5)
     og = oracle_grads(oracle, surf, [frame], [gpu_upstream(g, 0)])
     assert_grads(compare_grads(g["grads"][0], og))
+
+
+def _fused_vs_separate(maps, frames, fmap, targets, lambda_ns=0.0):
+    """Forward + loss as two calls and as the one fused call on the same
+    binning: every output plane, the loss vector and the scale-regulariser
+    gradient, bit for bit."""
+    import torch
+    from paper_2607_04127_gb300 import render
+    dev = torch.device("cuda")
+    params = [render.map_tensors(m, dev) for m in maps]
+    tg = [render.target_tensors(t, dev) for t in targets]
+    rast = render.Rasterizer(frames, frame_map=fmap, device=0, loss=render.LossParams(lambda_ns=lambda_ns))
+    res = []
+    for fused in (False, True):
+        grads = [[torch.zeros_like(p) for p in ps] for ps in params]
+        S = rast.bin_sort(params, check=True)
+        if fused:
+            rast.forward_loss(params, tg, grads, S)
+        else:
+            rast.forward(params, S)
+            rast.loss(params, tg, grads, S)
+        torch.cuda.synchronize()
+        planes = [[x.cpu().numpy().copy() for x in (o.A, o.S_t, o.S_n, o.T_final, o.n_contrib)] for o in rast.out]
+        ups = [[x.cpu().numpy().copy() for x in u] for u in rast.up]
+        res.append((planes, ups, rast.loss_out.cpu().numpy().copy(), [g[2].cpu().numpy().copy() for g in grads]))
+    rast.close()
+    (p0, u0, l0, s0), (p1, u1, l1, s1) = res
+    for a, b in zip(p0, p1):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    for a, b in zip(u0, u1):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.array_equal(l0, l1), (l0, l1)
+    for x, y in zip(s0, s1):
+        assert np.array_equal(x, y)
+
+
+def test_fused_forward_loss_equals_separate_calls():
+    """The loss in the forward's epilogue (one call) equals the forward and
+    loss calls: one frame, a multi-frame multi-map batch, a tile list beyond
+    the entry-parallel threshold (the long-list forward's epilogue), and the
+    N_surf term on (the call falls back to the two kernels)."""
+    s0, f0, t0 = scenes.box_room(seed=0)
+    _fused_vs_separate([s0], [f0], [0], [t0])
+    f0b = scenes.Frame(32, 512, 16, 16, f0.elev_min, f0.elev_max, scenes.pose_matrix(0.4, (1.0, 0.5, 2.3)))
+    _, _, t0b = scenes.box_room(seed=0, yaw=0.4)
+    s1, f1 = scenes.random_shell(3, 500, frame=scenes.Frame(32, 512, 16, 16, -0.3, 0.3, scenes.pose_matrix(-0.2)))
+    t1 = scenes.targets_for(f1, s1, 5)
+    _fused_vs_separate([s0, s1], [f0, f1, f0b], [0, 1, 0], [t0, t1, t0b])
+    rng = np.random.default_rng(11)
+    n = 12000
+    frame = scenes.Frame(32, 512, 16, 16, -0.26, 0.26)
+    az = 0.3 + rng.uniform(-0.035, 0.035, n)
+    el = rng.uniform(-0.035, 0.035, n)
+    r = rng.uniform(6.0, 12.0, n)
+    mean = np.stack([r * np.cos(el) * np.cos(az), r * np.cos(el) * np.sin(az), r * np.sin(el)], 1)
+    surf = scenes.Surfels(mean.astype(np.float32), rng.normal(size=(n, 4)).astype(np.float32),
+                          np.log(rng.uniform(0.005, 0.02, (n, 2))).astype(np.float32),
+                          rng.normal(size=n).astype(np.float32))
+    _fused_vs_separate([surf], [frame], [0], [scenes.targets_for(frame, surf, 7)])
+    _fused_vs_separate([s0], [f0], [0], [t0], lambda_ns=0.01)
