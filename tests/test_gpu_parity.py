@@ -29,6 +29,8 @@ loss on the GPU's forward outputs, the oracle's backward with the GPU's
 upstream gradients, so the L1 subgradient's jump at D = D_hat cannot mix
 into the comparison of the kernels.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -75,7 +77,33 @@ def cases():
     s, f = scenes.random_shell(9, 500, frame=scenes.Frame(32, 128, 16, 16, -0.4, 0.4))
     s.logit[::3] = 6.0
     out.append(("clamped_opacity", s, f, scenes.targets_for(f, s, 6)))
+    out.append(("grazing_ground_seam",) + grazing_ground_seam())
     return out
+
+
+def grazing_ground_seam(seed=12):
+    """Thin, anisotropic surfels on a ground plane 1.8 m below the sensor
+    (seen at grazing incidence: footprints one or two rows tall, where the
+    compositing kernels' 3-sigma-disc culling box is much tighter than the
+    bounding sphere) plus a cluster straddling the 0 / 2 pi azimuth seam."""
+    rng = np.random.default_rng(seed)
+    n_g, n_s = 2500, 600
+    xy = rng.uniform(-15.0, 15.0, (n_g, 2))
+    ground = np.column_stack([xy, -1.8 + rng.normal(0.0, 0.01, n_g)])
+    n_ground = np.column_stack([rng.normal(0.0, 0.05, (n_g, 2)), np.ones(n_g)])
+    phi = rng.uniform(-0.12, 0.12, n_s)
+    el = rng.uniform(-0.6, 0.6, n_s)
+    r = rng.uniform(2.0, 9.0, n_s)
+    seam = np.column_stack([r * np.cos(el) * np.cos(phi), r * np.cos(el) * np.sin(phi), r * np.sin(el)])
+    mean = np.concatenate([ground, seam])
+    nrm = np.concatenate([n_ground, rng.normal(size=(n_s, 3))])
+    Rm = scenes.frames_from_axes(rng.normal(size=(n_g + n_s, 3)), nrm)
+    scale = np.column_stack([rng.uniform(0.02, 0.3, n_g + n_s), rng.uniform(0.004, 0.05, n_g + n_s)])
+    alpha = rng.uniform(0.3, 0.95, n_g + n_s)
+    surf = scenes.Surfels(mean.astype(np.float32), scenes.rot_to_quat(Rm).astype(np.float32),
+                          np.log(scale).astype(np.float32), np.log(alpha / (1 - alpha)).astype(np.float32))
+    frame = scenes.Frame(64, 512, 8, 8, -math.radians(45), math.radians(45))
+    return surf, frame, scenes.targets_for(frame, surf, 8)
 
 
 CASES = cases()
