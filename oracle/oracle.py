@@ -13,6 +13,7 @@ else is FP64 (see ``lgs_oracle.c``).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -292,3 +293,51 @@ def adam(p, g, m, v, step: int, lr, beta1: float = 0.9, beta2: float = 0.999, ep
     mhat = m / (1.0 - beta1 ** step)
     vhat = v / (1.0 - beta2 ** step)
     return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+# --- tracking-side targets (Sec. 3.2) ------------------------------------------
+def logit_threshold(alpha_min: float) -> np.float32:
+    """The opacity threshold as a binary32 logit: alpha >= alpha_min is
+    decided as logit >= this value in binary32 on both sides (the sigmoid is
+    monotone), so the selection is exact and shared."""
+    return np.float32(math.log(alpha_min / (1.0 - alpha_min)))
+
+
+def trackable_targets(surfels, mask, last_kf, k_min: int, alpha_min: float, thickness: float = 0.01,
+                      eps: float = 1e-6, w_max: float = 10.0):
+    """Targets the tracker registers against (Sec. 3.2, Eqs. trackable_select,
+    anisotropy, anisotropy_norm, weight_func), in FP64 from the FP32 inputs.
+
+    Selection: m_i = 1, k_i >= k_min and alpha_i >= alpha_min (the last in
+    binary32 on the logit).  For each selected surfel, in ascending index:
+    its mean; the surfel-like covariance R(q) diag(s_x^2, s_y^2, thickness^2)
+    R(q)^T (q normalised, columns of R the tangent axes and the normal); the
+    anisotropy kappa = s_0 / (s_1 + eps) with s_0 >= s_1 the sorted in-plane
+    scales, normalised over the selected set by its minimum and maximum
+    (kappa_bar = 0 when they coincide), and the weight
+    w = min(1 / (kappa_bar + eps), w_max).
+    Returns (index int64 [k], mean [k,3], cov [k,6] as xx, xy, xz, yy, yz, zz,
+    weight [k])."""
+    lg = np.asarray(surfels.logit, np.float32)
+    sel = (np.asarray(mask) != 0) & (np.asarray(last_kf) >= k_min) & (lg >= logit_threshold(alpha_min))
+    idx = np.nonzero(sel)[0].astype(np.int64)
+    mean = np.asarray(surfels.mean, np.float64)[idx]
+    q = np.asarray(surfels.quat, np.float64)[idx]
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w_, x, y, z = q.T
+    R = np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w_ * z), 2 * (x * z + w_ * y)], -1),
+                  np.stack([2 * (x * y + w_ * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w_ * x)], -1),
+                  np.stack([2 * (x * z - w_ * y), 2 * (y * z + w_ * x), 1 - 2 * (x * x + y * y)], -1)], 1)
+    s = np.exp(np.asarray(surfels.log_scale, np.float64)[idx])
+    lam = np.stack([s[:, 0] ** 2, s[:, 1] ** 2, np.full(len(idx), thickness ** 2)], 1)
+    C = np.einsum("nij,nj,nkj->nik", R, lam, R)
+    cov = np.stack([C[:, 0, 0], C[:, 0, 1], C[:, 0, 2], C[:, 1, 1], C[:, 1, 2], C[:, 2, 2]], 1)
+    s0, s1 = s.max(1), s.min(1)
+    kappa = s0 / (s1 + eps)
+    if len(idx):
+        kmin, kmax = kappa.min(), kappa.max()
+        kb = (kappa - kmin) / (kmax - kmin) if kmax > kmin else np.zeros_like(kappa)
+    else:
+        kb = kappa
+    weight = np.minimum(1.0 / (kb + eps), w_max)
+    return idx, mean, cov, weight

@@ -575,3 +575,76 @@ def test_adam_constant_gradient_moves_linearly(oracle):
     assert np.allclose(p, p0 - 7 * 5e-3 * np.sign(g), rtol=0, atol=1e-12)
     q, _, _ = oracle.adam(p0, g, np.zeros(20), np.zeros(20), 1, 0.0)
     assert np.array_equal(q, p0)
+
+
+# --- P10 tracking-side targets (Sec. 3.2) ---------------------------------------
+def _surfels_from_axes(tu, n, scales, alpha, means=None):
+    k = len(scales)
+    R = scenes.frames_from_axes(np.asarray(tu, float), np.asarray(n, float))
+    q = scenes.rot_to_quat(R)
+    mean = np.zeros((k, 3)) if means is None else np.asarray(means, float)
+    return scenes.Surfels(mean.astype(np.float32), q.astype(np.float32),
+                          np.log(np.asarray(scales, float)).astype(np.float32),
+                          np.log(np.asarray(alpha) / (1 - np.asarray(alpha))).astype(np.float32)), R
+
+
+def test_target_covariance_eigenstructure(oracle):
+    """C = R diag(s_x^2, s_y^2, eps^2) R^T: the axes the surfel was built from
+    are its eigenvectors with those eigenvalues (checked against the axes of
+    the construction, not the oracle's rotation)."""
+    rng = np.random.default_rng(3)
+    k = 50
+    tu, n = rng.normal(size=(k, 3)), rng.normal(size=(k, 3))
+    scales = rng.uniform(0.02, 0.8, (k, 2))
+    surf, R = _surfels_from_axes(tu, n, scales, np.full(k, 0.5))
+    idx, _, cov, _ = oracle.trackable_targets(surf, np.ones(k), np.zeros(k, np.int32), 0, 0.1, thickness=0.01)
+    assert np.array_equal(idx, np.arange(k))
+    s = np.exp(surf.log_scale.astype(np.float64))
+    for i in range(k):
+        c = cov[i]
+        C = np.array([[c[0], c[1], c[2]], [c[1], c[3], c[4]], [c[2], c[4], c[5]]])
+        ax = R[i] / np.linalg.norm(R[i], axis=0)
+        lam = (s[i, 0] ** 2, s[i, 1] ** 2, 1e-4)
+        for j in range(3):
+            assert np.allclose(C @ ax[:, j], lam[j] * ax[:, j], atol=2e-6 * max(lam))
+        assert np.trace(C) == pytest.approx(sum(lam), rel=1e-9)
+
+
+def test_target_weights_from_anisotropy(oracle):
+    """kappa = s_0 / (s_1 + eps) normalised over the set: the least anisotropic
+    surfel gets w_max = 10, the most anisotropic 1 / (1 + eps), the middle one
+    1 / (1/2 + eps); the order of the two scales does not matter."""
+    k = 3
+    tu = np.tile([1.0, 0.0, 0.0], (k, 1))
+    n = np.tile([0.0, 0.0, 1.0], (k, 1))
+    scales = [[0.1, 0.1], [0.1, 0.2], [0.3, 0.1]]          # kappa ~ 1, 2, 3
+    surf, _ = _surfels_from_axes(tu, n, scales, [0.5] * k)
+    _, _, _, w = oracle.trackable_targets(surf, np.ones(k), np.zeros(k, np.int32), 0, 0.1)
+    s = np.exp(surf.log_scale.astype(np.float64))
+    kap = s.max(1) / (s.min(1) + 1e-6)
+    assert np.argmin(kap) == 0 and np.argmax(kap) == 2
+    assert w[0] == 10.0
+    assert w[2] == pytest.approx(1.0 / (1.0 + 1e-6), rel=1e-12)
+    mid = (kap[1] - kap[0]) / (kap[2] - kap[0])
+    assert mid == pytest.approx(0.5, abs=1e-5)
+    assert w[1] == pytest.approx(1.0 / (mid + 1e-6), rel=1e-12)
+    # one anisotropy for all: nothing to normalise, every weight is w_max
+    surf2, _ = _surfels_from_axes(tu, n, [[0.2, 0.1]] * 3, [0.5] * 3)
+    _, _, _, w2 = oracle.trackable_targets(surf2, np.ones(3), np.zeros(3, np.int32), 0, 0.1)
+    assert np.all(w2 == 10.0)
+
+
+def test_trackable_selection_rule(oracle):
+    """m_i = 1, k_i >= k_min, alpha_i >= alpha_min, in ascending index; an
+    empty selection gives empty arrays."""
+    alpha = [0.9, 0.9, 0.2, 0.9, 0.9, 0.6]
+    mask = [1, 0, 1, 1, 1, 1]
+    kf = [5, 5, 5, 2, 7, 3]
+    k = len(alpha)
+    surf, _ = _surfels_from_axes(np.tile([1.0, 0, 0], (k, 1)), np.tile([0, 0, 1.0], (k, 1)),
+                                 [[0.1, 0.05]] * k, alpha, means=np.arange(3 * k).reshape(k, 3))
+    idx, mean, _, _ = oracle.trackable_targets(surf, np.array(mask), np.array(kf, np.int32), 3, 0.5)
+    assert idx.tolist() == [0, 4, 5]
+    assert np.array_equal(mean, np.arange(3 * k).reshape(k, 3)[[0, 4, 5]])
+    idx, mean, cov, w = oracle.trackable_targets(surf, np.zeros(k), np.array(kf, np.int32), 3, 0.5)
+    assert idx.size == 0 and mean.shape == (0, 3) and cov.shape == (0, 6) and w.size == 0
