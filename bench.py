@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--persistent", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="street", choices=["street", "mapping", "batched", "serving"],
+    ap.add_argument("--workload", default="street", choices=["street", "mapping", "batched", "serving", "tracking"],
                     help="street: the headline line; the others print their own line")
     ap.add_argument("--no-serving", action="store_true", help="skip the reduced serving run of the street line")
     ap.add_argument("--serve-seconds", type=float, default=None)
@@ -334,6 +334,68 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tracking(args):
+    """Tracking-side targets (Sec. 3.2) of the 1M-surfel street-track map:
+    trackable selection, target covariances and weights per call, timed with
+    CUDA events over a map larger than L2; HBM roofline of the three kernels."""
+    import numpy as np
+    import torch
+    from paper_2607_04127_gb300 import build, lib, render, scenes
+    build.build()
+    surf, _, _ = scenes.street_track(n_keyframes=1)
+    dev = torch.device("cuda", 0)
+    params = render.map_tensors(surf, dev)
+    rng = np.random.default_rng(0)
+    n = surf.n
+    mask = torch.from_numpy((rng.uniform(size=n) < 0.8).astype(np.uint8)).to(dev)
+    kf = torch.from_numpy(rng.integers(0, 10, n).astype(np.int32)).to(dev)
+    scratch = torch.empty(lib.lgs_trackable_scratch_bytes(n), dtype=torch.uint8, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    mean = torch.empty(n, 3, device=dev)
+    cov = torch.empty(n, 6, device=dev)
+    w = torch.empty(n, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    p = lib.lgs_track_params(3, 0.5, 0.01, 1e-6, 10.0)
+    S = lib.surfels_struct(*params)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def call():
+        lib.lgs_trackable_targets(S, mask.data_ptr(), kf.data_ptr(), p, scratch.data_ptr(), scratch.numel(),
+                                  idx.data_ptr(), mean.data_ptr(), cov.data_ptr(), w.data_ptr(), cnt.data_ptr(),
+                                  stream)
+    for _ in range(max(args.warmup, 3)):
+        call()
+    torch.cuda.synchronize()
+    k = selected = None
+    ms = []
+    for _ in range(max(args.steps // 10, 20)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        call()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    selected = int(cnt.item())
+    t = statistics.median(ms) / 1e3
+    # algorithmic bytes: select reads logit, mask, last_kf, log-scales of all
+    # surfels; write re-reads them and reads mean and quaternion of the
+    # selected, writing index, mean, covariance and weight (44 B) for them
+    byts = n * (4 + 1 + 4 + 8) * 2 + selected * (12 + 16 + 44)
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    line = dict(metric="tracking targets: surfels/s (selection, target covariance, weight)", value=n / t,
+                unit="surfels/s", higher_is_better=True, dtype="f32", n_gpus=1,
+                data="synthetic (seeded 200 m street track, scenes.street_track)",
+                config=dict(workload="1M-surfel map, 80 % trackable mask, 10 keyframe indices, k_min 3, alpha_min 0.5",
+                            surfels=n, selected=selected, l2="flushed between calls (256 MB write)"),
+                ms_per_call=t * 1e3,
+                roofline=dict(bound="hbm", achieved=byts / t / 1e9, peak=peak, unit="GB/s",
+                              frac=byts / t / 1e9 / peak, traffic=None))
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -517,6 +579,8 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "tracking":
+        run_tracking(args)
     else:
         run_ours(args)
 

@@ -327,6 +327,41 @@ LGS_API lgs_status lgs_render_fwd_loss_batch(lgs_session s, const lgs_surfels* m
                                      const lgs_loss_params* params, const lgs_fwd_grad_out* grads_out,
                                      const lgs_surfel_grad* grads, float* loss_out, void* stream);
 
+/* ---- tracking-side targets (Sec. 3.2) -------------------------------------
+ * The trackable subset of the map (Eq. trackable_select) and, for each member,
+ * what covariance-weighted G-ICP needs from it without any map-side k-NN:
+ * the mean, the surfel-like target covariance R(q) diag(s_x^2, s_y^2, t^2)
+ * R(q)^T (q normalised; t = thickness along the normal) and the geometry
+ * weight w = min(1 / (kappa_bar + eps), w_max) (Eqs. anisotropy,
+ * anisotropy_norm, weight_func) with kappa = s_0 / (s_1 + eps) of the sorted
+ * in-plane scales, normalised over the selected set by its minimum and
+ * maximum (kappa_bar = 0 when they coincide). */
+typedef struct {
+    int32_t k_min;       /* selected: mask != 0, last_kf >= k_min, ... */
+    float alpha_min;     /* ... and opacity >= alpha_min, in (0, 1); decided in
+                            binary32 as logit >= log(alpha_min / (1 - alpha_min)) */
+    float thickness;     /* t, metres, > 0 (0.01 is the library's reading) */
+    float eps;           /* > 0 (1e-6) */
+    float w_max;         /* > 0 (10, as the paper sets omega_max) */
+} lgs_track_params;
+
+/* Bytes of device scratch lgs_trackable_targets needs for n surfels. */
+LGS_API size_t lgs_trackable_scratch_bytes(int64_t n);
+
+/* map: one surfel set (device, as lgs_surfels); mask [n] uint8 and last_kf
+ * [n] int32: device arrays (the trackable mask m_i and the last keyframe that
+ * updated the surfel, k_i).  Writes, in ascending surfel index, the selected
+ * surfels' index [count] int32, mean [count][3], cov [count][6] (xx, xy, xz,
+ * yy, yz, zz) and weight [count], all device arrays with room for n entries
+ * (caller-owned), and count (one int64 on the device).  scratch: device
+ * memory of lgs_trackable_scratch_bytes(n) bytes, 4-byte aligned, its
+ * contents irrelevant.  Enqueues on stream without a host sync; argument
+ * errors return LGS_ERR_INVALID_ARG. */
+LGS_API lgs_status lgs_trackable_targets(const lgs_surfels* map, const uint8_t* mask, const int32_t* last_kf,
+                                 const lgs_track_params* params, void* scratch, size_t scratch_bytes,
+                                 int32_t* index, float* mean, float* cov, float* weight, int64_t* count,
+                                 void* stream);
+
 /* ---- image loss without a session or workspace --------------------------
  * The paper has no counterpart to this call; it is an interface for callers
  * that cannot allocate device memory at the point where they evaluate the

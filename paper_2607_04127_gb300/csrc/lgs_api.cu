@@ -666,6 +666,29 @@ lgs_status lgs_bin_sort(lgs_session s, const lgs_surfels* surfels, const lgs_fra
   return lgs_bin_sort_batch(s, surfels, 1, frames, nullptr, n_frames, stream);
 }
 
+size_t lgs_trackable_scratch_bytes(int64_t n) { return lgs::trackable_scratch_bytes(n); }
+
+lgs_status lgs_trackable_targets(const lgs_surfels* map, const uint8_t* mask, const int32_t* last_kf,
+                                 const lgs_track_params* p, void* scratch, size_t scratch_bytes, int32_t* index,
+                                 float* mean, float* cov, float* weight, int64_t* count, void* stream) {
+  if (!map || !p || !scratch || !count) return fail(LGS_ERR_INVALID_ARG, "NULL argument");
+  if (map->n < 0 || map->n > 0x7fffffffll) return fail(LGS_ERR_INVALID_ARG, "n outside [0, 2^31)");
+  if (map->n > 0 && (!map->mean || !map->quat || !map->log_scale || !map->opacity_logit || !mask || !last_kf ||
+                     !index || !mean || !cov || !weight))
+    return fail(LGS_ERR_INVALID_ARG, "NULL array");
+  if (!(p->alpha_min > 0.f && p->alpha_min < 1.f)) return fail(LGS_ERR_INVALID_ARG, "alpha_min outside (0, 1)");
+  if (!(p->thickness > 0.f && p->eps > 0.f && p->w_max > 0.f))
+    return fail(LGS_ERR_INVALID_ARG, "thickness, eps and w_max must be positive");
+  if (scratch_bytes < lgs::trackable_scratch_bytes(map->n) || (reinterpret_cast<uintptr_t>(scratch) & 3))
+    return fail(LGS_ERR_INVALID_ARG, "scratch too small or not 4-byte aligned");
+  const double a = p->alpha_min;
+  const float logit_min = static_cast<float>(std::log(a / (1.0 - a)));
+  const cudaError_t e = lgs::launch_trackable(*map, mask, last_kf, p->k_min, logit_min, p->thickness, p->eps,
+                                              p->w_max, scratch, index, mean, cov, weight, count,
+                                              static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? LGS_OK : cuda_fail(e, "trackable targets");
+}
+
 lgs_status lgs_render_fwd_loss_batch(lgs_session s, const lgs_surfels* maps, int n_maps, const lgs_frame* frames,
                                      const int32_t* frame_map, int n_frames, const lgs_fwd_out* fwd,
                                      const lgs_target* targets, const lgs_loss_params* params,

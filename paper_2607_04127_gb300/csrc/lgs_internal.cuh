@@ -593,6 +593,10 @@ inline int* loss_counts_ptr(const WsPtrs& w) {
   return reinterpret_cast<int*>(reinterpret_cast<unsigned long long*>(w.loss_part) + 4 * LGS_MAX_FRAMES +
                                 LGS_MAX_MAPS);
 }
+size_t trackable_scratch_bytes(int64_t n);
+cudaError_t launch_trackable(const lgs_surfels& M, const uint8_t* mask, const int32_t* last_kf, int32_t k_min,
+                             float logit_min, float thick, float eps, float w_max, void* scratch, int32_t* index,
+                             float* mean, float* cov, float* weight, int64_t* count, cudaStream_t s);
 cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_t* pv, int persistent,
                                    const lgs_loss_params& p, cudaStream_t s);
 cudaError_t launch_loss_counts(const WsPtrs& w, const Desc& h, cudaStream_t s);

@@ -83,7 +83,8 @@ EXPORTS = [
     "lgs_render_fwd_batch", "lgs_render_bwd_batch", "lgs_loss_batch", "lgs_render_fwd_loss_batch",
     "lgs_session_set_tuning", "lgs_adam_step",
     "lgs_session_set_timing", "lgs_session_kernel_times", "lgs_image_loss_noalloc", "lgs_adam_step_batch",
-    "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version",
+    "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version", "lgs_trackable_scratch_bytes",
+    "lgs_trackable_targets",
 ]
 
 
@@ -118,6 +119,8 @@ def load():
         "lgs_render_bwd_batch": ([P, P, i32, P, P, i32, P, P, P, P], S),
         "lgs_loss_batch": ([P, P, i32, P, P, i32, P, P, P, P, P, P, P], S),
         "lgs_render_fwd_loss_batch": ([P, P, i32, P, P, i32, P, P, P, P, P, P, P], S),
+        "lgs_trackable_scratch_bytes": ([i64], ctypes.c_size_t),
+        "lgs_trackable_targets": ([P, P, P, P, P, ctypes.c_size_t, P, P, P, P, P, P], S),
         "lgs_session_set_tuning": ([P, P], S),
         "lgs_session_set_timing": ([P, i32], S),
         "lgs_session_kernel_times": ([P, P, P], S),
@@ -278,6 +281,22 @@ def lgs_render_fwd_loss_batch(h, maps, frames, frame_map, fwd, targets, params, 
                                             _arr(lgs_target, targets), _ref(params), _arr(lgs_fwd_grad_out, grads_out),
                                             _arr(lgs_surfel_grad, grads) if grads is not None else None,
                                             P(loss_out_ptr), P(stream)))
+
+
+class lgs_track_params(ctypes.Structure):
+    _fields_ = [("k_min", ctypes.c_int32), ("alpha_min", ctypes.c_float), ("thickness", ctypes.c_float),
+                ("eps", ctypes.c_float), ("w_max", ctypes.c_float)]
+
+
+def lgs_trackable_scratch_bytes(n):
+    return int(load().lgs_trackable_scratch_bytes(int(n)))
+
+
+def lgs_trackable_targets(surfels, mask_ptr, last_kf_ptr, params, scratch_ptr, scratch_bytes, index_ptr, mean_ptr,
+                          cov_ptr, weight_ptr, count_ptr, stream):
+    _check(load().lgs_trackable_targets(_ref(surfels), P(mask_ptr), P(last_kf_ptr), _ref(params), P(scratch_ptr),
+                                        scratch_bytes, P(index_ptr), P(mean_ptr), P(cov_ptr), P(weight_ptr),
+                                        P(count_ptr), P(stream)))
 
 
 def lgs_bin_sort(h, surfels, frames, stream):
