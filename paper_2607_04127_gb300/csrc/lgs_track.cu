@@ -4,11 +4,11 @@
 // O(1) from its own parameters (no map-side k-NN), and its geometry weight
 // (Eqs. anisotropy, anisotropy_norm, weight_func).
 //
-// Three launches over the surfels: select (flag, anisotropy, per-CTA counts,
-// exact min / max of the anisotropy over the selection through integer
-// atomics on its float bits), scan (one CTA: first output slot of every CTA,
-// the count), write (stable compaction in ascending surfel index: mean,
-// covariance, weight).  Scratch is the caller's (lgs_trackable_scratch_bytes).
+// Three launches over the surfels: select (flag, anisotropy; per CTA the
+// count and the minimum / maximum anisotropy as float bits, exact in any
+// order), scan (one CTA: first output slot of every CTA, the count, the
+// global minimum / maximum), write (stable compaction in ascending surfel
+// index: mean, covariance, weight).  No global atomics.  Scratch is the caller's (lgs_trackable_scratch_bytes).
 #include <cuda_runtime.h>
 
 #include "lgs_internal.cuh"
@@ -21,7 +21,9 @@ constexpr int kTrkScanCta = 1024;
 
 struct TrkScratch {
   uint32_t* count;      // [ctas] selected surfels per CTA, then their first output slot
-  uint32_t* kbits;      // [2] min and max anisotropy (float bits; all positive)
+  uint32_t* kmin;       // [ctas] smallest anisotropy of the CTA's selection (float bits; all positive)
+  uint32_t* kmax;       // [ctas] largest
+  uint32_t* kbits;      // [2] min and max over the whole selection
 };
 
 __device__ __forceinline__ bool trk_selected(const lgs_surfels& M, const uint8_t* mask, const int32_t* last_kf,
@@ -48,26 +50,57 @@ __global__ void __launch_bounds__(kTrkCta) k_trk_select(lgs_surfels M, const uin
   const uint32_t bal = __ballot_sync(0xffffffffu, sel);
   kb_min = __reduce_min_sync(0xffffffffu, kb_min);
   kb_max = __reduce_max_sync(0xffffffffu, kb_max);
-  __shared__ uint32_t s_n;
-  if (threadIdx.x == 0) s_n = 0;
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) {
-    if (bal) atomicAdd(&s_n, static_cast<uint32_t>(__popc(bal)));
-    if (kb_min != 0xffffffffu) atomicMin(sc.kbits, kb_min);
-    if (kb_max != 0u) atomicMax(sc.kbits + 1, kb_max);
+  // per-CTA totals in the CTA's own slots (no global atomics: the scan
+  // reduces them)
+  __shared__ uint32_t s_n[kTrkCta / 32], s_lo[kTrkCta / 32], s_hi[kTrkCta / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_n[wid] = __popc(bal);
+    s_lo[wid] = kb_min;
+    s_hi[wid] = kb_max;
   }
   __syncthreads();
-  if (threadIdx.x == 0) sc.count[blockIdx.x] = s_n;
+  if (threadIdx.x < 32) {
+    const bool in = lane < kTrkCta / 32;
+    const uint32_t n = __reduce_add_sync(0xffffffffu, in ? s_n[lane] : 0u);
+    const uint32_t lo = __reduce_min_sync(0xffffffffu, in ? s_lo[lane] : 0xffffffffu);
+    const uint32_t hi = __reduce_max_sync(0xffffffffu, in ? s_hi[lane] : 0u);
+    if (lane == 0) {
+      sc.count[blockIdx.x] = n;
+      sc.kmin[blockIdx.x] = lo;
+      sc.kmax[blockIdx.x] = hi;
+    }
+  }
 }
 
-// Exclusive scan of the per-CTA counts (in place) and the total.
+// Exclusive scan of the per-CTA counts (in place), the total, and the
+// minimum and maximum anisotropy over all CTAs.
 __global__ void __launch_bounds__(kTrkScanCta) k_trk_scan(TrkScratch sc, uint32_t ctas,
                                                           int64_t* __restrict__ total) {
-  __shared__ uint32_t s_w[32];
+  __shared__ uint32_t s_w[32], s_lo[32], s_hi[32];
   __shared__ uint32_t s_carry;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_carry = 0;
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (uint32_t b = tid; b < ctas; b += kTrkScanCta) {
+    lo = min(lo, sc.kmin[b]);
+    hi = max(hi, sc.kmax[b]);
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if (lane == 0) {
+    s_lo[wid] = lo;
+    s_hi[wid] = hi;
+  }
   __syncthreads();
+  if (tid < 32) {
+    lo = __reduce_min_sync(0xffffffffu, s_lo[tid]);
+    hi = __reduce_max_sync(0xffffffffu, s_hi[tid]);
+    if (tid == 0) {
+      sc.kbits[0] = lo;
+      sc.kbits[1] = hi;
+    }
+  }
   for (uint32_t b0 = 0; b0 < ctas; b0 += kTrkScanCta) {
     const uint32_t b = b0 + tid;
     const uint32_t x = b < ctas ? sc.count[b] : 0u;
@@ -142,7 +175,7 @@ __global__ void __launch_bounds__(kTrkCta) k_trk_write(lgs_surfels M, const uint
 
 size_t trackable_scratch_bytes(int64_t n) {
   const int64_t ctas = (n + kTrkCta - 1) / kTrkCta;
-  return sizeof(uint32_t) * (static_cast<size_t>(ctas > 0 ? ctas : 1) + 2);
+  return sizeof(uint32_t) * (3 * static_cast<size_t>(ctas > 0 ? ctas : 1) + 2);
 }
 
 cudaError_t launch_trackable(const lgs_surfels& M, const uint8_t* mask, const int32_t* last_kf, int32_t k_min,
@@ -150,10 +183,9 @@ cudaError_t launch_trackable(const lgs_surfels& M, const uint8_t* mask, const in
                              float* mean, float* cov, float* weight, int64_t* count, cudaStream_t s) {
   const int64_t n = M.n;
   const uint32_t ctas = static_cast<uint32_t>(n > 0 ? (n + kTrkCta - 1) / kTrkCta : 0);
-  TrkScratch sc{static_cast<uint32_t*>(scratch), static_cast<uint32_t*>(scratch) + (ctas > 0 ? ctas : 1)};
-  cudaError_t e = cudaMemsetAsync(sc.kbits, 0xff, sizeof(uint32_t), s);   // min: above every positive float
-  if (e == cudaSuccess) e = cudaMemsetAsync(sc.kbits + 1, 0, sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
+  uint32_t* base = static_cast<uint32_t*>(scratch);
+  const uint32_t c1 = ctas > 0 ? ctas : 1;
+  TrkScratch sc{base, base + c1, base + 2 * c1, base + 3 * c1};
   if (ctas == 0) return cudaMemsetAsync(count, 0, sizeof(int64_t), s);
   k_trk_select<<<ctas, kTrkCta, 0, s>>>(M, mask, last_kf, k_min, logit_min, eps, sc);
   k_trk_scan<<<1, kTrkScanCta, 0, s>>>(sc, ctas, count);
