@@ -63,6 +63,7 @@ __global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, St
     st->loss_ticket = 0;
     st->count_ticket = 0;
     st->n_long = 0;
+    st->n_big = 0;
     st->long_counter_fwd = 0;
     st->long_counter_bwd = 0;
     st->long_done_fwd = 0;
@@ -224,13 +225,18 @@ constexpr int kScanCta = 1024;
 
 // Bucket of a tile list length for the longest-first order: floor(log2(n)) + 1
 // (0 for an empty tile), reversed so that bucket 0 holds the longest lists.
+// Buckets of up to kMergeMax keys take the merge sort (one CTA per tile, all
+// in one launch: a bucket's sort is a long serial chain, so every bucket
+// runs concurrently); longer ones the bitonic network, over their own list.
+constexpr int kMergeMax = 2048;
 constexpr int kOrderBuckets = 33;
 __device__ __forceinline__ int order_bucket(uint32_t n) { return kOrderBuckets - 1 - (n ? 32 - __clz(n) : 0); }
 
 __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ tcur, uint32_t n_tiles,
                                                           uint2* __restrict__ ranges, Status* __restrict__ st,
                                                           int64_t cap, uint32_t* __restrict__ order,
-                                                          uint32_t* __restrict__ longt, uint32_t* __restrict__ cbase) {
+                                                          uint32_t* __restrict__ longt, uint32_t* __restrict__ cbase,
+                                                          uint32_t* __restrict__ sortl) {
   __shared__ unsigned long long s_w[32];
   __shared__ uint32_t s_wc[32];
   __shared__ unsigned long long s_carry;
@@ -337,6 +343,8 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
     pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & ((1u << lane) - 1u));
     if (b >= 0) order[pos] = t;
     if (t < n_tiles && rg.y - rg.x > kLongList) longt[atomicAdd(&st->n_long, 1u)] = t;
+    // buckets beyond the merge sort, for the bitonic sort
+    if (t < n_tiles && rg.y - rg.x > kMergeMax) sortl[atomicAdd(&st->n_big, 1u)] = t;
   }
 }
 
@@ -491,8 +499,6 @@ __device__ void chunk_store(const unsigned long long* s, unsigned long long* g, 
 // search along the merge path (ties, which only the padding has, go to the
 // first run) and merges them sequentially.  The bucket is padded with +inf to
 // N = 8 * 2^m keys.
-constexpr int kMergeCta = 256;
-constexpr int kMergeMax = 8 * kMergeCta;   // 2048 keys
 
 __device__ __forceinline__ void cas_reg(unsigned long long& a, unsigned long long& b) {
   const unsigned long long x = a, y = b;
@@ -514,6 +520,8 @@ __device__ __forceinline__ void sort8(unsigned long long (&k)[8]) {
 // Shared-memory index of key x: one padding slot after every 8 keys, so the
 // 8-key rows of consecutive threads start in different banks.
 __device__ __forceinline__ uint32_t pad8(uint32_t x) { return x + (x >> 3); }
+
+constexpr int kMergeCta = kMergeMax / 8;   // 8 keys per thread
 
 __global__ void __launch_bounds__(kMergeCta) k_tile_sort_merge(const uint2* __restrict__ ranges,
                                                                const Status* __restrict__ st,
@@ -580,14 +588,16 @@ __global__ void __launch_bounds__(kMergeCta) k_tile_sort_merge(const uint2* __re
 
 // ---- longer buckets: one CTA -----------------------------------------------
 __global__ void __launch_bounds__(kSortCta) k_tile_sort(const uint2* __restrict__ ranges, const Status* __restrict__ st,
+                                                        const uint32_t* __restrict__ sortl, uint32_t n_tiles,
                                                         unsigned long long* __restrict__ pkey,
                                                         uint32_t* __restrict__ ptile, uint32_t* __restrict__ pv) {
   __shared__ unsigned long long s[kSortSmem];
   if (st->overflow) return;
-  const uint32_t tile = blockIdx.x;
+  for (uint32_t kk = blockIdx.x; kk < st->n_big; kk += gridDim.x) {
+  __syncthreads();   // the previous tile's readers are done with s
+  const uint32_t tile = sortl[kk];
   const uint2 rg = ranges[tile];
   const uint32_t n = rg.y - rg.x;
-  if (n <= kMergeMax) return;   // k_tile_sort_merge's
   unsigned long long* g = pkey + rg.x;
   if (n <= kSortSmem) {
     uint32_t N = 2;
@@ -598,7 +608,7 @@ __global__ void __launch_bounds__(kSortCta) k_tile_sort(const uint2* __restrict_
       pv[rg.x + i] = static_cast<uint32_t>(s[i]);
       ptile[rg.x + i] = tile;
     }
-    return;
+    continue;
   }
   // long bucket: sorted chunks of kSortSmem, then the merge steps whose
   // stride spans chunks run in global memory (this CTA only; __syncthreads
@@ -635,6 +645,7 @@ __global__ void __launch_bounds__(kSortCta) k_tile_sort(const uint2* __restrict_
     pv[rg.x + i] = static_cast<uint32_t>(g[i]);
     ptile[rg.x + i] = tile;
   }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -654,11 +665,16 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
   const int64_t ni = n_items > 0 ? n_items : 1;
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
   k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tcur, w.st);
-  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work, w.longt, w.cbase);
+  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work, w.longt, w.cbase,
+                                     w.sortl);
   k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.box, w.tcur, w.ranges, w.st, w.pkey);
   if (n_tiles > 0) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned few = static_cast<unsigned>(sms) < n_tiles ? static_cast<unsigned>(sms) : n_tiles;
     k_tile_sort_merge<<<n_tiles, kMergeCta, 0, s>>>(w.ranges, w.st, w.pkey, w.ptile, w.pv);
-    k_tile_sort<<<n_tiles, kSortCta, 0, s>>>(w.ranges, w.st, w.pkey, w.ptile, w.pv);
+    k_tile_sort<<<few, kSortCta, 0, s>>>(w.ranges, w.st, w.sortl, n_tiles, w.pkey, w.ptile, w.pv);
   }
   return cudaGetLastError();
 }

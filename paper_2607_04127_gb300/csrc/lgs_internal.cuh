@@ -73,11 +73,12 @@ struct Status {
   unsigned int loss_ticket;           // loss CTAs finished (the last one reduces; self-resetting)
   unsigned int n_chunks;              // backward chunks of the last binning (kChunk list entries each)
   unsigned int count_ticket;          // mask-count CTAs finished (the last one adds up; self-resetting)
+  unsigned int n_big;                 // buckets of more than 2048 keys (the bitonic sort)
 };
 
 struct Layout {
   size_t desc, status, tables, rec, box, key, cnt, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part, cbase,
-      ckpt, total;
+      ckpt, sortl, total;
   int64_t items_cap, pairs_cap, chunks_cap;
   uint32_t tiles_cap;
   uint32_t tables_cap;     // floats
@@ -103,6 +104,7 @@ struct WsPtrs {
   double* loss_part;       // loss partial sums and mask counts
   uint32_t* cbase;         // [tiles] first backward chunk of every tile
   float* ckpt;             // [chunks][6][tile pixels] forward checkpoint at every chunk end
+  uint32_t* sortl;         // [tiles] tiles whose bucket exceeds the merge sort (st->n_big of them)
 };
 
 inline WsPtrs ws_ptrs(void* base, const Layout& L) {
@@ -126,6 +128,7 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.loss_part = reinterpret_cast<double*>(b + L.loss_part);
   p.cbase = reinterpret_cast<uint32_t*>(b + L.cbase);
   p.ckpt = reinterpret_cast<float*>(b + L.ckpt);
+  p.sortl = reinterpret_cast<uint32_t*>(b + L.sortl);
   return p;
 }
 

@@ -156,7 +156,7 @@ class Server:
     def _learn(self, active, seconds: float):
         n = sum(self.sessions[r.session].n for r in active)
         k = max(seconds - self.tick_base, 0.0) / max(n, 1)
-        self.kappa = k if self.kappa is None else 0.8 * self.kappa + 0.2 * k
+        self.kappa = k if self.kappa is None else 0.5 * self.kappa + 0.5 * k
 
     def _feasible(self, active, now: float) -> bool:
         """Simulate the remaining ticks of ``active`` (no further arrivals):

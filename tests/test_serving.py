@@ -126,8 +126,9 @@ def test_deadline_admission(workload):
         for sid in sids:
             surf, fr, _ = workload[sid]
             srv.open_session(sid, surf, fr.H * fr.W)
-        # calibrate the tick model (first run: warm-up), and time one request alone
-        srv.run([serve.Request(2, workload[2][1], workload[2][2], 0.0, 4)])
+        # calibrate the tick model (first runs: warm-up), and time one request alone
+        for _ in range(3):
+            srv.run([serve.Request(2, workload[2][1], workload[2][2], 0.0, 4)])
         cal = serve.Request(2, workload[2][1], workload[2][2], 0.0, 4)
         srv.run([cal])
         srv.late.clear()
