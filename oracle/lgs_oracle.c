@@ -99,6 +99,13 @@ float lgso_f32_exp_spec(float x)
     return p * f32_from_bits((uint32_t)(k + 127) << 23);
 }
 
+/* The same, over an array (map management specifies the surfels' scales with
+ * it, so that its binary32 decisions are a fixed function of the inputs). */
+void lgso_f32_exp_spec_n(const float* x, float* y, int64_t n)
+{
+    for (int64_t i = 0; i < n; i++) y[i] = lgso_f32_exp_spec(x[i]);
+}
+
 /* sin and cos on [-pi/2, pi/2] by their Taylor series (through x^11 and
  * x^12), Horner form in x^2, each operation rounded once. */
 float lgso_f32_sin_spec(float x)

@@ -61,6 +61,7 @@ def _load():
         i64, i32, f32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_double
         lib.lgso_constants.argtypes = [P]
         lib.lgso_f32_exp_spec.argtypes = [f32]; lib.lgso_f32_exp_spec.restype = f32
+        lib.lgso_f32_exp_spec_n.argtypes = [P, P, i64]
         lib.lgso_f32_sin_spec.argtypes = [f32]; lib.lgso_f32_sin_spec.restype = f32
         lib.lgso_f32_cos_spec.argtypes = [f32]; lib.lgso_f32_cos_spec.restype = f32
         lib.lgso_f32_col_dir.argtypes = [i32, i32, P, P]
@@ -101,6 +102,14 @@ def constants() -> np.ndarray:
 # --- specified binary32 helpers (exported for their own tests) --------------
 def f32_exp_spec(x: float) -> np.float32:
     return np.float32(_load().lgso_f32_exp_spec(float(np.float32(x))))
+
+
+def f32_exp_spec_n(x) -> np.ndarray:
+    """f32_exp_spec over an array (binary32 in, binary32 out)."""
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.empty_like(x)
+    _load().lgso_f32_exp_spec_n(_p(x), _p(y), x.size)
+    return y
 
 
 def f32_sin_spec(x: float) -> np.float32:
