@@ -58,7 +58,9 @@ def parse():
     ap.add_argument("--persistent", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="street", choices=["street", "mapping", "batched", "serving", "tracking"],
+    ap.add_argument("--manage-n", type=int, default=2_000_000, help="map size of the manage workload")
+    ap.add_argument("--workload", default="street",
+                    choices=["street", "mapping", "batched", "serving", "tracking", "manage"],
                     help="street: the headline line; the others print their own line")
     ap.add_argument("--no-serving", action="store_true", help="skip the reduced serving run of the street line")
     ap.add_argument("--serve-seconds", type=float, default=None)
@@ -396,6 +398,101 @@ def run_tracking(args):
     print(json.dumps(line), flush=True)
 
 
+def run_manage(args):
+    """Map management (Sec. 3.3 control score; Sec. 3.5 opacity prune, planar
+    cover-and-prune over three planes, adaptive split) of a street-track map
+    of --manage-n surfels with tracking signals from its own k-NN
+    covariances.  A step is one lgs_map_manage call: device-timed with CUDA
+    events (inputs resident, L2 flushed between steps); end to end from
+    pinned host buffers with the new map read back; the oracle on a bounded
+    sample of the same map."""
+    import numpy as np
+    import torch
+    from paper_2607_04127_gb300 import build, lib, manage, scenes
+    build.build()
+    surf, _, _ = scenes.street_track(n=args.manage_n, n_keyframes=1)
+    lam, res = scenes.manage_signals(surf.mean)
+    host = [np.ascontiguousarray(x) for x in (surf.mean, surf.quat, surf.log_scale, surf.logit, lam, res)]
+    n = surf.n
+    dev = torch.device("cuda", 0)
+    t = [torch.from_numpy(x).to(dev) for x in host]
+    m = manage.MapManager(dev)
+    p = manage.params()
+    out = m.launch(t[:4], t[4], t[5], p)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        m.launch(t[:4], t[4], t[5], p, out=out)
+    torch.cuda.synchronize()
+    steps = max(min(args.steps, 50), 10)
+    ms = []
+    with Clocks(0) as clk:
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            m.launch(t[:4], t[4], t[5], p, out=out)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+    counts = out["counts"].cpu().tolist()
+    step_s = statistics.median(ms) / 1e3
+    # end to end: pinned host inputs copied in, the new map's rows read back
+    pinned = [torch.from_numpy(x).pin_memory() for x in host]
+    dst = [torch.empty(out["capacity"] * w, dtype=torch.float32).pin_memory() for w in (3, 4, 2, 1)]
+    h2d = sum(x.numel() * 4 for x in pinned)
+    e2e_ms, d2h = [], 0
+    for _ in range(5):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d, s_ in zip(t, pinned):
+            d.copy_(s_, non_blocking=True)
+        m.launch(t[:4], t[4], t[5], p, out=out)
+        k = int(out["counts"][0].item())
+        d2h = 48
+        for d, key, w in zip(dst, ("mean", "quat", "log_scale", "logit"), (3, 4, 2, 1)):
+            d[: k * w].copy_(out[key].reshape(-1)[: k * w], non_blocking=True)
+            d2h += k * w * 4
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_s = statistics.median(e2e_ms) / 1e3
+    # oracle on a bounded sample: the first surfels of the map, repeated for ~10 s
+    from oracle import manage as omg
+    sample = min(n, 100_000)
+    P = omg.Params()
+    sub = [x[:sample] for x in host]
+    t0 = time.perf_counter()
+    runs = 0
+    while runs == 0 or time.perf_counter() - t0 < min(args.cpu_seconds, 10.0):
+        omg.manage(*sub, P)
+        runs += 1
+    cpu_s = time.perf_counter() - t0
+    # algorithmic bytes of a step: the inputs read once (mean 12, quat 16,
+    # log-scale 8, logit 4, eigenvalues 12, residual 4) and the score (4) per
+    # surfel, the new map (40) with its parent index and role (5) per row
+    alg = n * (56 + 4) + counts[0] * 45
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    line = dict(metric="map management: surfels/s (control score, opacity prune, 3-pass cover-and-prune, split)",
+                value=n / step_s, unit="surfels/s", higher_is_better=True, n_gpus=1, steps=steps,
+                warmup=max(args.warmup, 3), ms_per_step=step_s * 1e3, scaling="weak", vs_baseline=None, dtype="f32",
+                data="synthetic (seeded 200 m street track, scenes.street_track; k-NN signals, scenes.manage_signals)",
+                config=dict(workload=f"{n}-surfel street-track map, library default parameters", surfels=n,
+                            counts=dict(n_out=counts[0], opacity_pruned=counts[1], plane_pruned=counts[2:5],
+                                        split=counts[5]),
+                            l2="flushed between steps (256 MB write)"),
+                roofline=dict(bound="hbm", kernel="whole step", achieved=alg / step_s / 1e9, peak=peak, unit="GB/s",
+                              frac=alg / step_s / 1e9 / peak, traffic=None,
+                              note="algorithmic bytes of the step over its CUDA-event time"),
+                e2e=dict(value=n / e2e_s, unit="surfels/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+                cpu_baseline=dict(value=sample * runs / cpu_s, unit="surfels/s", cores=1, kind="oracle",
+                                  sample=f"{runs} oracle runs over the first {sample} surfels of the map "
+                                         f"in {cpu_s:.1f} s (NumPy, one thread)"),
+                gpu_launches=lib.lgs_manage_launches(p) * steps,
+                clocks=clk.summary())
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -581,6 +678,8 @@ def main():
         run_serving(args)
     elif args.workload == "tracking":
         run_tracking(args)
+    elif args.workload == "manage":
+        run_manage(args)
     else:
         run_ours(args)
 

@@ -362,6 +362,92 @@ LGS_API lgs_status lgs_trackable_targets(const lgs_surfels* map, const uint8_t* 
                                  int32_t* index, float* mean, float* cov, float* weight, int64_t* count,
                                  void* stream);
 
+/* ---- map management (Sec. 3.3 control score, Sec. 3.5 map budget control) --
+ * One map-management step over one surfel map, on the device:
+ *  1. control score (Eq. controlscore) c_i = clip(w_l lin_i + w_c curv~_i +
+ *     w_r res~_i, 0, 1) from the tracking covariance's eigenvalues
+ *     lambda_i (any order; sorted descending inside): lin = (l0 - l1) /
+ *     (l0 + eps), curv = l2 / (l0 + l1 + l2 + eps), curv~ = min(3 curv, 1)
+ *     (curv spans [0, 1/3]); the residual normalised by its own quantile,
+ *     res~ = min(res / (Q_{q_res}(res) + eps), 1);
+ *  2. opacity prune: alpha < alpha_prune is removed (the Table 4 baseline);
+ *  3. n_passes passes of planar cover-and-prune over the planes xy, yz, zx:
+ *     candidates are survivors with c <= Q_{q_plane}(survivors' c) and
+ *     alpha >= alpha_min; grouped by the 2D voxel (floor(mu_a / voxel),
+ *     floor(mu_b / voxel)) of the pass's plane; the representative is the
+ *     group's largest alpha (ties: lowest index); the other candidates within
+ *     |n_r . (mu_j - mu_r)| <= slab are members, with cover radius
+ *     u^2 + v^2 in the representative's tangent frame scaled by its scales;
+ *     the cover region is the representative's ellipse enlarged to include a
+ *     q_cover fraction of the members (the ceil(q_cover m) closest, ties
+ *     included), whose members are removed; at most floor(prune_cap x
+ *     survivors) per pass, the lowest c first (then lowest index);
+ *  4. structure-aware split: survivors with c >= Q_{q_split}(survivors' c)
+ *     and alpha >= alpha_min, at most floor(split_cap x survivors), the
+ *     highest c first (then lowest index); each is replaced by two children
+ *     at mu +- split_shift s_0 a_i along a_i = R(q_i) e0 with
+ *     log-scale s~_0 + split_dlog (orientation, s~_1 and opacity kept).
+ * Quantiles are the lower order statistic sorted[floor(q (n - 1))].  Every
+ * decision is made in binary32 with correctly rounded operations in a fixed
+ * order and the scales through a fixed polynomial exponential, so the result
+ * is the same on every run and launch shape. */
+typedef struct {
+    float alpha_prune;   /* in (0, 1); 0.005 (the paper gives no value) */
+    float alpha_min;     /* in (0, 1); 0.1 */
+    float w_l, w_c, w_r; /* 0.55, 0.30, 0.15 (the paper's values) */
+    float q_res;         /* in [0, 1]; 0.95 */
+    float eps;           /* > 0; 1e-6 */
+    float q_plane;       /* in [0, 1]; 0.3 */
+    float voxel;         /* > 0, metres; 1.0 */
+    int32_t n_passes;    /* 0..3; 3 */
+    float q_cover;       /* in [0, 1]; 0.5 */
+    float slab;          /* >= 0, metres; 0.05 */
+    float prune_cap;     /* in [0, 1]; 0.1 */
+    float q_split;       /* in [0, 1]; 0.9 */
+    float split_cap;     /* in [0, 1]; 0.05 */
+    float split_shift;   /* finite; 0.5 */
+    float split_dlog;    /* finite; log 0.5 */
+} lgs_manage_params;
+
+/* Writable surfel parameters (device, layouts as lgs_surfels). */
+typedef struct {
+    float *mean, *quat, *log_scale, *opacity_logit;
+} lgs_surfel_params_out;
+
+/* The defaults listed above. */
+LGS_API void lgs_manage_default_params(lgs_manage_params* p);
+/* Bytes of device scratch lgs_map_manage needs for n surfels. */
+LGS_API size_t lgs_manage_scratch_bytes(int64_t n);
+/* Kernel launches one lgs_map_manage call makes (for launch accounting). */
+LGS_API int32_t lgs_manage_launches(const lgs_manage_params* p);
+/* Rows the new map may need: n + floor(split_cap n). */
+LGS_API int64_t lgs_manage_capacity(int64_t n, const lgs_manage_params* p);
+
+/* map: the surfels (device, n <= 2^28); lam [n][3] and res [n]: device
+ * arrays of the tracking covariance's eigenvalues (>= 0) and G-ICP residuals
+ * (>= 0), finite.  scratch: lgs_manage_scratch_bytes(n) bytes of device
+ * memory, 256-byte aligned, contents irrelevant.  Writes score [n] (c_i),
+ * the new map into out (rows [0, n_out), capacity rows of room), src
+ * [capacity] int32 (the parent of each new row), role [capacity] uint8 (0
+ * copy, 1 child at +shift, 2 child at -shift) and counts [6] int64 (n_out,
+ * opacity-pruned, pruned by passes 0, 1, 2, split), all device and
+ * caller-owned; out must not overlap map.  Enqueues on stream without a host
+ * sync; argument errors return LGS_ERR_INVALID_ARG before anything is
+ * enqueued. */
+LGS_API lgs_status lgs_map_manage(const lgs_surfels* map, const float* lam, const float* res,
+                                  const lgs_manage_params* params, void* scratch, size_t scratch_bytes,
+                                  float* score, const lgs_surfel_params_out* out, int64_t capacity, int32_t* src,
+                                  uint8_t* role, int64_t* counts, void* stream);
+
+/* Carries a per-surfel array (words_per_row 32-bit words a row, e.g. Adam
+ * moments) over to the new map: out[j] = in[src[j]] for j < counts[0]
+ * (clamped to capacity); rows of children are zero when zero_children != 0.
+ * src, role and counts as written by lgs_map_manage; in and out device,
+ * 4-byte aligned, not overlapping. */
+LGS_API lgs_status lgs_map_gather(const int32_t* src, const uint8_t* role, const int64_t* counts, int64_t capacity,
+                                  const void* in, void* out, int32_t words_per_row, int32_t zero_children,
+                                  void* stream);
+
 /* ---- image loss without a session or workspace --------------------------
  * The paper has no counterpart to this call; it is an interface for callers
  * that cannot allocate device memory at the point where they evaluate the

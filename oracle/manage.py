@@ -184,11 +184,12 @@ def cover_prune_pass(mean, quat, log_scale, logit, c, alive, plane, p: Params = 
         m = memb.size
         if m == 0:
             continue
-        r2 = (u * u + v * v)[inside]
+        rk = (u * u + v * v)[inside].view(np.uint32)   # non-negative: bits order like values
         k = math.ceil(k_frac * m)
-        rk = r2.view(np.uint32)
-        less = (rk[None, :] < rk[:, None]).sum(1)     # members strictly closer
-        flagged.extend(idx[memb[less < k]].tolist())
+        if k == 0:
+            continue
+        beta2 = np.sort(rk)[k - 1]                     # the k-th smallest u^2 + v^2
+        flagged.extend(idx[memb[rk <= beta2]].tolist())
     flagged = np.asarray(sorted(flagged), np.int64)
     cap = math.floor(float(F(p.prune_cap)) * n_a)
     if flagged.size > cap:

@@ -690,6 +690,87 @@ lgs_status lgs_trackable_targets(const lgs_surfels* map, const uint8_t* mask, co
   return e == cudaSuccess ? LGS_OK : cuda_fail(e, "trackable targets");
 }
 
+void lgs_manage_default_params(lgs_manage_params* p) {
+  if (!p) return;
+  p->alpha_prune = 0.005f;
+  p->alpha_min = 0.1f;
+  p->w_l = 0.55f;
+  p->w_c = 0.30f;
+  p->w_r = 0.15f;
+  p->q_res = 0.95f;
+  p->eps = 1e-6f;
+  p->q_plane = 0.3f;
+  p->voxel = 1.0f;
+  p->n_passes = 3;
+  p->q_cover = 0.5f;
+  p->slab = 0.05f;
+  p->prune_cap = 0.1f;
+  p->q_split = 0.9f;
+  p->split_cap = 0.05f;
+  p->split_shift = 0.5f;
+  p->split_dlog = static_cast<float>(std::log(0.5));
+}
+
+size_t lgs_manage_scratch_bytes(int64_t n) { return lgs::manage_scratch_bytes(n < 0 ? 0 : n); }
+
+int32_t lgs_manage_launches(const lgs_manage_params* p) {
+  return p && p->n_passes >= 0 && p->n_passes <= 3 ? lgs::manage_kernel_count(p->n_passes) : -1;
+}
+
+int64_t lgs_manage_capacity(int64_t n, const lgs_manage_params* p) {
+  if (n < 0 || !p || !(p->split_cap >= 0.f && p->split_cap <= 1.f)) return -1;
+  return n + static_cast<int64_t>(std::floor(static_cast<double>(p->split_cap) * static_cast<double>(n)));
+}
+
+namespace {
+bool unit_closed(float v) { return v >= 0.f && v <= 1.f; }
+bool unit_open(float v) { return v > 0.f && v < 1.f; }
+float logit_f32(float a) { return static_cast<float>(std::log(static_cast<double>(a) / (1.0 - a))); }
+}  // namespace
+
+lgs_status lgs_map_manage(const lgs_surfels* map, const float* lam, const float* res, const lgs_manage_params* p,
+                          void* scratch, size_t scratch_bytes, float* score, const lgs_surfel_params_out* out,
+                          int64_t capacity, int32_t* src, uint8_t* role, int64_t* counts, void* stream) {
+  if (!map || !p || !scratch || !out || !counts) return fail(LGS_ERR_INVALID_ARG, "NULL argument");
+  if (map->n < 0 || map->n > (1ll << 28)) return fail(LGS_ERR_INVALID_ARG, "n outside [0, 2^28]");
+  if (map->n > 0 && (!map->mean || !map->quat || !map->log_scale || !map->opacity_logit || !lam || !res ||
+                     !score || !out->mean || !out->quat || !out->log_scale || !out->opacity_logit || !src || !role))
+    return fail(LGS_ERR_INVALID_ARG, "NULL array");
+  if (!unit_open(p->alpha_prune) || !unit_open(p->alpha_min))
+    return fail(LGS_ERR_INVALID_ARG, "alpha_prune and alpha_min must lie in (0, 1)");
+  if (!unit_closed(p->q_res) || !unit_closed(p->q_plane) || !unit_closed(p->q_cover) || !unit_closed(p->q_split) ||
+      !unit_closed(p->prune_cap) || !unit_closed(p->split_cap))
+    return fail(LGS_ERR_INVALID_ARG, "quantiles and caps must lie in [0, 1]");
+  if (!(p->eps > 0.f) || !(p->voxel > 0.f) || !std::isfinite(p->voxel) || !(p->slab >= 0.f) ||
+      !std::isfinite(p->w_l) || !std::isfinite(p->w_c) || !std::isfinite(p->w_r) ||
+      !std::isfinite(p->split_shift) || !std::isfinite(p->split_dlog))
+    return fail(LGS_ERR_INVALID_ARG, "eps and voxel must be positive, slab >= 0, weights and split finite");
+  if (p->n_passes < 0 || p->n_passes > 3) return fail(LGS_ERR_INVALID_ARG, "n_passes outside [0, 3]");
+  if (capacity < lgs_manage_capacity(map->n, p))
+    return fail(LGS_ERR_INVALID_ARG, "capacity below n + floor(split_cap n)");
+  if (scratch_bytes < lgs::manage_scratch_bytes(map->n) || (reinterpret_cast<uintptr_t>(scratch) & 255))
+    return fail(LGS_ERR_INVALID_ARG, "scratch too small or not 256-byte aligned");
+  lgs::MgHostParams H;
+  H.p = *p;
+  H.logit_prune = logit_f32(p->alpha_prune);
+  H.logit_min = logit_f32(p->alpha_min);
+  const cudaError_t e = lgs::launch_manage(*map, lam, res, H, scratch, score, *out, capacity, src, role, counts,
+                                           static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? LGS_OK : cuda_fail(e, "map management");
+}
+
+lgs_status lgs_map_gather(const int32_t* src, const uint8_t* role, const int64_t* counts, int64_t capacity,
+                          const void* in, void* out, int32_t words_per_row, int32_t zero_children, void* stream) {
+  if (!counts || capacity < 0 || words_per_row < 1) return fail(LGS_ERR_INVALID_ARG, "bad counts / capacity / words");
+  if (capacity > 0 && (!src || !role || !in || !out)) return fail(LGS_ERR_INVALID_ARG, "NULL array");
+  if ((reinterpret_cast<uintptr_t>(in) & 3) || (reinterpret_cast<uintptr_t>(out) & 3))
+    return fail(LGS_ERR_INVALID_ARG, "in and out must be 4-byte aligned");
+  if (capacity == 0) return LGS_OK;
+  const cudaError_t e = lgs::launch_manage_gather(src, role, counts, capacity, in, out, words_per_row, zero_children,
+                                                  static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? LGS_OK : cuda_fail(e, "map gather");
+}
+
 lgs_status lgs_render_fwd_loss_batch(lgs_session s, const lgs_surfels* maps, int n_maps, const lgs_frame* frames,
                                      const int32_t* frame_map, int n_frames, const lgs_fwd_out* fwd,
                                      const lgs_target* targets, const lgs_loss_params* params,

@@ -596,6 +596,19 @@ inline int* loss_counts_ptr(const WsPtrs& w) {
   return reinterpret_cast<int*>(reinterpret_cast<unsigned long long*>(w.loss_part) + 4 * LGS_MAX_FRAMES +
                                 LGS_MAX_MAPS);
 }
+// map management (lgs_manage.cu)
+struct MgHostParams {
+  lgs_manage_params p;
+  float logit_prune, logit_min;   // binary32 logits of alpha_prune, alpha_min
+};
+size_t manage_scratch_bytes(int64_t n);
+int manage_kernel_count(int n_passes);
+cudaError_t launch_manage(const lgs_surfels& M, const float* lam, const float* res, const MgHostParams& H,
+                          void* scratch, float* score, const lgs_surfel_params_out& out, int64_t capacity,
+                          int32_t* src, uint8_t* role, int64_t* counts, cudaStream_t s);
+cudaError_t launch_manage_gather(const int32_t* src, const uint8_t* role, const int64_t* counts, int64_t capacity,
+                                 const void* in, void* out, int words, int zero_children, cudaStream_t s);
+
 size_t trackable_scratch_bytes(int64_t n);
 cudaError_t launch_trackable(const lgs_surfels& M, const uint8_t* mask, const int32_t* last_kf, int32_t k_min,
                              float logit_min, float thick, float eps, float w_max, void* scratch, int32_t* index,

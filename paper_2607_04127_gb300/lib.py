@@ -84,7 +84,8 @@ EXPORTS = [
     "lgs_session_set_tuning", "lgs_adam_step",
     "lgs_session_set_timing", "lgs_session_kernel_times", "lgs_image_loss_noalloc", "lgs_adam_step_batch",
     "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version", "lgs_trackable_scratch_bytes",
-    "lgs_trackable_targets",
+    "lgs_trackable_targets", "lgs_manage_default_params", "lgs_manage_scratch_bytes", "lgs_manage_capacity", "lgs_manage_launches",
+    "lgs_map_manage", "lgs_map_gather",
 ]
 
 
@@ -121,6 +122,12 @@ def load():
         "lgs_render_fwd_loss_batch": ([P, P, i32, P, P, i32, P, P, P, P, P, P, P], S),
         "lgs_trackable_scratch_bytes": ([i64], ctypes.c_size_t),
         "lgs_trackable_targets": ([P, P, P, P, P, ctypes.c_size_t, P, P, P, P, P, P], S),
+        "lgs_manage_default_params": ([P], None),
+        "lgs_manage_scratch_bytes": ([i64], ctypes.c_size_t),
+        "lgs_manage_capacity": ([i64, P], i64),
+        "lgs_manage_launches": ([P], i32),
+        "lgs_map_manage": ([P, P, P, P, P, ctypes.c_size_t, P, P, i64, P, P, P, P], S),
+        "lgs_map_gather": ([P, P, P, i64, P, P, i32, i32, P], S),
         "lgs_session_set_tuning": ([P, P], S),
         "lgs_session_set_timing": ([P, i32], S),
         "lgs_session_kernel_times": ([P, P, P], S),
@@ -355,6 +362,49 @@ def frame_struct(fr) -> lgs_frame:
     for k in range(12):
         f.pose[k] = float(pose[k])
     return f
+
+
+class lgs_manage_params(ctypes.Structure):
+    _fields_ = [("alpha_prune", ctypes.c_float), ("alpha_min", ctypes.c_float), ("w_l", ctypes.c_float),
+                ("w_c", ctypes.c_float), ("w_r", ctypes.c_float), ("q_res", ctypes.c_float),
+                ("eps", ctypes.c_float), ("q_plane", ctypes.c_float), ("voxel", ctypes.c_float),
+                ("n_passes", ctypes.c_int32), ("q_cover", ctypes.c_float), ("slab", ctypes.c_float),
+                ("prune_cap", ctypes.c_float), ("q_split", ctypes.c_float), ("split_cap", ctypes.c_float),
+                ("split_shift", ctypes.c_float), ("split_dlog", ctypes.c_float)]
+
+
+class lgs_surfel_params_out(ctypes.Structure):
+    _fields_ = [("mean", P), ("quat", P), ("log_scale", P), ("opacity_logit", P)]
+
+
+def lgs_manage_default_params() -> lgs_manage_params:
+    p = lgs_manage_params()
+    load().lgs_manage_default_params(_ref(p))
+    return p
+
+
+def lgs_manage_scratch_bytes(n) -> int:
+    return int(load().lgs_manage_scratch_bytes(int(n)))
+
+
+def lgs_manage_launches(params) -> int:
+    return int(load().lgs_manage_launches(_ref(params)))
+
+
+def lgs_manage_capacity(n, params) -> int:
+    return int(load().lgs_manage_capacity(int(n), _ref(params)))
+
+
+def lgs_map_manage(surfels, lam_ptr, res_ptr, params, scratch_ptr, scratch_bytes, score_ptr, out, capacity, src_ptr,
+                   role_ptr, counts_ptr, stream):
+    _check(load().lgs_map_manage(_ref(surfels), P(lam_ptr), P(res_ptr), _ref(params), P(scratch_ptr), scratch_bytes,
+                                 P(score_ptr), _ref(out), int(capacity), P(src_ptr), P(role_ptr), P(counts_ptr),
+                                 P(stream)))
+
+
+def lgs_map_gather(src_ptr, role_ptr, counts_ptr, capacity, in_ptr, out_ptr, words_per_row, zero_children, stream):
+    _check(load().lgs_map_gather(P(src_ptr), P(role_ptr), P(counts_ptr), int(capacity), P(in_ptr), P(out_ptr),
+                                 int(words_per_row), int(zero_children), P(stream)))
 
 
 def surfels_struct(mean, quat, log_scale, logit) -> lgs_surfels:

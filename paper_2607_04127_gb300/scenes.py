@@ -581,3 +581,52 @@ def street_maps(seed: int, sizes, shapes, tile=(8, 8), spacing: float = 25.0, no
         D, p, nr, v = simulate_scan(scene, fr, rng)
         out.append((surf, fr, target_from_scan(D, p, v, true_normals=nr)))
     return out
+
+
+# --- inputs of map management --------------------------------------------------
+def manage_cluster(seed: int, n: int):
+    """A small clustered map: surfels on two planes (z = -0.5 and x = 0.2,
+    1 cm jitter) and scattered clutter in a 4 m box about the origin, with the
+    tracking signals map management reads: covariance eigenvalues near
+    (1, 0.8, 0) on the planes and random on the clutter, and exponential
+    residuals.  Returns (mean, quat, log_scale, logit, lam, res), float32."""
+    rng = np.random.default_rng(seed)
+    kind = rng.integers(0, 3, n)
+    pos = rng.uniform(-2, 2, (n, 3))
+    pos[kind == 0, 2] = rng.normal(-0.5, 0.01, (kind == 0).sum())
+    pos[kind == 1, 0] = rng.normal(0.2, 0.01, (kind == 1).sum())
+    nrm = np.where((kind == 0)[:, None], [0, 0, 1.0],
+                   np.where((kind == 1)[:, None], [1.0, 0, 0], rng.normal(size=(n, 3))))
+    R = frames_from_axes(rng.normal(size=(n, 3)), nrm)
+    quat = rot_to_quat(R).astype(np.float32)
+    ls = np.log(rng.uniform(0.05, 0.4, (n, 2))).astype(np.float32)
+    logit = rng.normal(0.5, 2.0, n).astype(np.float32)
+    lam = np.where((kind == 2)[:, None], rng.uniform(0, 1, (n, 3)), [1.0, 0.8, 0.0])
+    lam = (lam + rng.uniform(0, 0.05, (n, 3))).astype(np.float32)
+    res = rng.exponential(0.02, n).astype(np.float32)
+    return pos.astype(np.float32), quat, ls, logit, lam, res
+
+
+def manage_signals(points: np.ndarray, k: int = 20, seed: int = 0, noise: float = 0.01):
+    """Stand-ins for the per-surfel signals tracking hands to map management
+    (Sec. 3.3): the eigenvalues (descending) of the k-NN covariance of the
+    map's own means, and a registration residual: the distance from the
+    point to its neighbours' plane plus |N(0, noise)|.  Returns float32
+    (lam [n, 3], res [n])."""
+    from scipy.spatial import cKDTree
+    pts = np.asarray(points, np.float64)
+    tree = cKDTree(pts)
+    _, idx = tree.query(pts, k=k, workers=-1)
+    lam = np.empty((pts.shape[0], 3))
+    res = np.empty(pts.shape[0])
+    step = 1 << 18
+    for a in range(0, pts.shape[0], step):
+        nb = pts[idx[a:a + step]]
+        mu = nb.mean(1)
+        c = nb - mu[:, None]
+        cov = np.einsum("nki,nkj->nij", c, c) / k
+        w, v = np.linalg.eigh(cov)
+        lam[a:a + step] = np.maximum(w[:, ::-1], 0.0)
+        res[a:a + step] = np.abs(((pts[a:a + step] - mu) * v[:, :, 0]).sum(1))
+    res += np.abs(np.random.default_rng(seed).normal(0.0, noise, pts.shape[0]))
+    return lam.astype(np.float32), res.astype(np.float32)

@@ -276,23 +276,7 @@ def _brute(mean, quat, ls, logit, lam, res, P, mg, oracle):
     return src
 
 
-def _clustered(seed, n):
-    """Surfels on two planes (z = -0.5, x = 0.2) and scattered clutter with
-    jitter, in a 4 m box about the origin (voxels on both sides of 0)."""
-    rng = np.random.default_rng(seed)
-    kind = rng.integers(0, 3, n)
-    pos = rng.uniform(-2, 2, (n, 3))
-    pos[kind == 0, 2] = rng.normal(-0.5, 0.01, (kind == 0).sum())
-    pos[kind == 1, 0] = rng.normal(0.2, 0.01, (kind == 1).sum())
-    nrm = np.where((kind == 0)[:, None], [0, 0, 1.0], np.where((kind == 1)[:, None], [1.0, 0, 0], rng.normal(size=(n, 3))))
-    R = scenes.frames_from_axes(rng.normal(size=(n, 3)), nrm)
-    quat = scenes.rot_to_quat(R).astype(F)
-    ls = np.log(rng.uniform(0.05, 0.4, (n, 2))).astype(F)
-    logit = rng.normal(0.5, 2.0, n).astype(F)
-    lam = np.where((kind == 2)[:, None], rng.uniform(0, 1, (n, 3)), [1.0, 0.8, 0.0])
-    lam = (lam + rng.uniform(0, 0.05, (n, 3))).astype(F)
-    res = rng.exponential(0.02, n).astype(F)
-    return pos.astype(F), quat, ls, logit, lam, res
+_clustered = scenes.manage_cluster
 
 
 @pytest.mark.parametrize("seed,n", [(0, 40), (1, 90), (2, 150)])
