@@ -46,8 +46,8 @@ enum : uint32_t { kAlive = 1u, kCand = 2u, kMember = 4u, kFlag = 8u, kSplit = 16
 enum : uint32_t { kSelNone = 0u, kSelAll = 1u, kSelKth = 2u };
 
 // State of one radix select.  count accumulates the keys taking part (reset
-// by the setup kernel that reads it); base is the number of survivors a cap is
-// a fraction of; after the last digit prefix is the selected key.
+// by the first digit, which reads it); base is the number of survivors a cap
+// is a fraction of; after the last digit prefix is the selected key.
 struct Sel {
   unsigned long long prefix;
   uint32_t count;
@@ -55,7 +55,10 @@ struct Sel {
   uint32_t kind;
   uint32_t base;
   uint32_t n_big;              // groups of the current pass with more than kSmallGroup members
-  uint32_t hist[256];
+  uint32_t n_small;            // the other groups with members
+  uint32_t ticket;             // CTAs of the current digit done (the last one picks)
+  uint32_t ccount[2];          // keys in the two compaction buffers
+  uint32_t hist[2048];
 };
 
 struct MgScratch {
@@ -65,7 +68,9 @@ struct MgScratch {
   uint32_t* slot;              // [n] hash slot of a candidate's group
   uint32_t* r2;                // [n] a member's squared cover radius (float bits)
   uint32_t* pos;               // [n + 1] output weights, then their exclusive scan
-  uint32_t* bucket;            // [n] members' radii grouped by slot
+  unsigned long long* bucket;  // [n] members (radius bits << 32 | index) grouped by slot
+  unsigned long long* cbuf[2]; // [n] each: keys still matching the select's prefix
+  uint32_t* small;             // [n] slots of the groups with 1..kSmallGroup members
   unsigned long long* htab;    // [T] voxel keys (kNoKey: empty)
   unsigned long long* rep;     // [T] packed representative: order key of the logit << 32 | ~index
   uint32_t* cnt;               // [T] members per slot
@@ -87,7 +92,7 @@ uint32_t scan_blocks(uint64_t len) { return static_cast<uint32_t>((len + kScanBl
 
 // Byte offsets of the scratch arrays; the total is the size.
 struct MgLayout {
-  size_t sel, flags, key, slot, r2, pos, bucket, htab, rep, cnt, off, big, part, total;
+  size_t sel, flags, key, slot, r2, pos, bucket, cbuf0, cbuf1, small, htab, rep, cnt, off, big, part, total;
   uint32_t T;
 };
 
@@ -103,7 +108,10 @@ MgLayout mg_layout(int64_t n) {
   L.slot = take(4 * N);
   L.r2 = take(4 * N);
   L.pos = take(4 * (N + 1));
-  L.bucket = take(4 * N);
+  L.bucket = take(8 * N);
+  L.cbuf0 = take(8 * N);
+  L.cbuf1 = take(8 * N);
+  L.small = take(4 * N);
   L.htab = take(8 * static_cast<size_t>(L.T));
   L.rep = take(8 * static_cast<size_t>(L.T));
   L.cnt = take(4 * static_cast<size_t>(L.T));
@@ -125,7 +133,10 @@ MgScratch mg_scratch(void* base, int64_t n) {
   s.slot = reinterpret_cast<uint32_t*>(b + L.slot);
   s.r2 = reinterpret_cast<uint32_t*>(b + L.r2);
   s.pos = reinterpret_cast<uint32_t*>(b + L.pos);
-  s.bucket = reinterpret_cast<uint32_t*>(b + L.bucket);
+  s.bucket = reinterpret_cast<unsigned long long*>(b + L.bucket);
+  s.cbuf[0] = reinterpret_cast<unsigned long long*>(b + L.cbuf0);
+  s.cbuf[1] = reinterpret_cast<unsigned long long*>(b + L.cbuf1);
+  s.small = reinterpret_cast<uint32_t*>(b + L.small);
   s.htab = reinterpret_cast<unsigned long long*>(b + L.htab);
   s.rep = reinterpret_cast<unsigned long long*>(b + L.rep);
   s.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
@@ -191,15 +202,26 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
   return x ^ (x >> 31);
 }
 
-// warp-aggregated count into a 32-bit or 64-bit counter
-__device__ __forceinline__ void warp_count(bool pred, uint32_t* ctr) {
-  const uint32_t b = __ballot_sync(0xffffffffu, pred);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(ctr, static_cast<uint32_t>(__popc(b)));
+// One atomic per CTA: the CTA's sum of v into a 32-bit or 64-bit counter
+// (every thread of the CTA calls it, after its grid-stride loop).
+__device__ __forceinline__ uint32_t block_sum(uint32_t v) {
+  __shared__ uint32_t s_sum;
+  if (threadIdx.x == 0) s_sum = 0;
+  __syncthreads();
+  v = __reduce_add_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_sum, v);
+  __syncthreads();
+  const uint32_t t = s_sum;
+  __syncthreads();   // read by all before a second call resets it
+  return t;
 }
-__device__ __forceinline__ void warp_count64(bool pred, int64_t* ctr) {
-  const uint32_t b = __ballot_sync(0xffffffffu, pred);
-  if ((threadIdx.x & 31) == 0 && b)
-    atomicAdd(reinterpret_cast<unsigned long long*>(ctr), static_cast<unsigned long long>(__popc(b)));
+__device__ __forceinline__ void block_count(uint32_t v, uint32_t* ctr) {
+  const uint32_t t = block_sum(v);
+  if (threadIdx.x == 0 && t) atomicAdd(ctr, t);
+}
+__device__ __forceinline__ void block_count64(uint32_t v, int64_t* ctr) {
+  const uint32_t t = block_sum(v);
+  if (threadIdx.x == 0 && t) atomicAdd(reinterpret_cast<unsigned long long*>(ctr), static_cast<unsigned long long>(t));
 }
 
 // ---------------------------------------------------------------------------
@@ -285,82 +307,195 @@ void launch_scan(const uint32_t* in, uint32_t* out, uint32_t len, uint32_t* part
 // ---------------------------------------------------------------------------
 // radix select of the k-th smallest 64-bit key
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kMgCta) k_sel_hist(const unsigned long long* __restrict__ key, uint32_t n,
-                                                     Sel* __restrict__ sel, int shift) {
-  if (sel->kind != kSelKth) return;
-  __shared__ uint32_t h[256];
-  for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
-  __syncthreads();
-  const unsigned long long pre = sel->prefix;
-  const unsigned long long hi = shift >= 56 ? 0ull : (~0ull << (shift + 8));
-  const int lane = threadIdx.x & 31;
-  // warp-uniform loop: every lane reaches the match; lanes with equal digits
-  // add once (long runs of equal keys are common: planar scores of 0)
-  for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    const uint32_t i = i0 + threadIdx.x;
-    uint32_t bin = 256u;
-    if (i < n) {
-      const unsigned long long k = key[i];
-      if (k != kNoKey && !((k ^ pre) & hi)) bin = static_cast<uint32_t>((k >> shift) & 255u);
+// Digits of the select, most significant first: 11 bits each, so a quantile
+// (keys significant in their upper 32 bits) takes 3 digits and a cap (all 64
+// bits) 6.
+struct Digit {
+  int shift, width;
+};
+constexpr Digit kDigits64[6] = {{53, 11}, {42, 11}, {31, 11}, {20, 11}, {9, 11}, {0, 9}};
+constexpr Digit kDigits32[3] = {{53, 11}, {42, 11}, {32, 10}};
+constexpr uint32_t kBins = 2048;
+
+enum : int { kSetupNone = 0, kSetupQuantile = 1, kSetupCap = 2 };
+
+// The select's kind and rank from the counted keys.  Quantile: the
+// floor(q (count - 1))-th smallest; cap: at most floor(q base) keys, the
+// smallest first (every key when count <= cap).
+__device__ void sel_setup(const Sel* sel, int mode, float q, uint32_t& kind, uint32_t& k, uint32_t& base) {
+  const uint32_t c = sel->count;
+  k = 0;
+  if (mode == kSetupQuantile) {
+    base = c;
+    if (c == 0) {
+      kind = kSelNone;
+    } else {
+      kind = kSelKth;
+      k = static_cast<uint32_t>(floor(static_cast<double>(q) * static_cast<double>(c - 1)));
     }
-    const uint32_t peers = __match_any_sync(0xffffffffu, bin);
-    if (bin < 256u && lane == __ffs(peers) - 1) atomicAdd(&h[bin], static_cast<uint32_t>(__popc(peers)));
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < 256; t += blockDim.x)
-    if (h[t]) atomicAdd(&sel->hist[t], h[t]);
-}
-
-__global__ void __launch_bounds__(256) k_sel_pick(Sel* __restrict__ sel, int shift) {
-  if (sel->kind != kSelKth) return;
-  __shared__ uint32_t s_warp[32];
-  const uint32_t k = sel->k;
-  const uint32_t v = sel->hist[threadIdx.x];
-  uint32_t total;
-  const uint32_t ex = block_exclusive_scan(v, s_warp, total);
-  if (ex <= k && k < ex + v) {
-    sel->prefix |= static_cast<unsigned long long>(threadIdx.x) << shift;
-    sel->k = k - ex;
-  }
-  sel->hist[threadIdx.x] = 0;
-}
-
-// quantile: the floor(q (count - 1))-th smallest of the keys counted
-__global__ void k_sel_quantile(Sel* __restrict__ sel, float q) {
-  const uint32_t c = sel->count;
-  sel->base = c;
-  sel->count = 0;
-  sel->prefix = 0;
-  if (c == 0) {
-    sel->kind = kSelNone;
-    return;
-  }
-  sel->kind = kSelKth;
-  sel->k = static_cast<uint32_t>(floor(static_cast<double>(q) * static_cast<double>(c - 1)));
-}
-
-// cap: at most floor(frac * base) of the keys counted, the smallest first
-__global__ void k_sel_cap(Sel* __restrict__ sel, float frac) {
-  const uint32_t c = sel->count;
-  const double cap = floor(static_cast<double>(frac) * static_cast<double>(sel->base));
-  sel->count = 0;
-  sel->prefix = 0;
-  if (static_cast<double>(c) <= cap) {
-    sel->kind = kSelAll;
-  } else if (cap < 1.0) {
-    sel->kind = kSelNone;
   } else {
-    sel->kind = kSelKth;
-    sel->k = static_cast<uint32_t>(cap) - 1u;
+    base = sel->base;
+    const double cap = floor(static_cast<double>(q) * static_cast<double>(base));
+    if (static_cast<double>(c) <= cap) {
+      kind = kSelAll;
+    } else if (cap < 1.0) {
+      kind = kSelNone;
+    } else {
+      kind = kSelKth;
+      k = static_cast<uint32_t>(cap) - 1u;
+    }
   }
 }
 
-void launch_select(const unsigned long long* key, uint32_t n, Sel* sel, int digits, int grid, cudaStream_t s) {
-  for (int d = 0; d < digits; ++d) {
-    const int shift = 56 - 8 * d;
-    k_sel_hist<<<grid, kMgCta, 0, s>>>(key, n, sel, shift);
-    k_sel_pick<<<1, 256, 0, s>>>(sel, shift);
+constexpr uint32_t kStage = 256;   // keys a warp stages before it appends them
+
+__device__ __forceinline__ void flush_stage(const unsigned long long* stage, uint32_t sc, unsigned long long* dst,
+                                            uint32_t* dcount, int lane) {
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(dcount, sc);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (uint32_t t = lane; t < sc; t += 32) dst[base + t] = stage[t];
+  __syncwarp();   // the stage is rewritten only after every lane has copied out
+}
+
+// One digit of the radix select: every CTA histograms its share of the keys
+// that match the prefix so far; the last CTA to finish (ticket) picks the bin
+// holding rank k, extends the prefix and clears the histogram.  The first
+// digit also sets the select up from the counted keys (mode != kSetupNone).
+// Digit 0 and 1 read every key; digit 1 and later also copy the keys that
+// match the prefix into a compaction buffer, which the next digit reads
+// instead (keys never leave the prefix's range once they fall out of it).
+__global__ void __launch_bounds__(kMgCta) k_sel_digit(const unsigned long long* __restrict__ key, uint32_t n,
+                                                      Sel* __restrict__ sel, unsigned long long* cbuf0,
+                                                      unsigned long long* cbuf1, int d, int last, int shift,
+                                                      int width, int mode, float q) {
+  __shared__ uint32_t h[kBins];
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_kind, s_k, s_base, s_last;
+  __shared__ unsigned long long s_pre;
+  __shared__ unsigned long long s_stage[kMgCta / 32][kStage];
+  if (threadIdx.x == 0) {
+    if (mode != kSetupNone) {
+      sel_setup(sel, mode, q, s_kind, s_k, s_base);
+      s_pre = 0ull;
+    } else {
+      s_kind = sel->kind;
+      s_k = sel->k;
+      s_pre = sel->prefix;
+    }
   }
+  for (uint32_t t = threadIdx.x; t < kBins; t += blockDim.x) h[t] = 0;
+  __syncthreads();
+  const bool active = s_kind == kSelKth;
+  if (active) {
+    // digit d >= 2 reads the buffer digit d - 1 wrote; digit d >= 1 writes
+    // the other one (unless it is the last digit)
+    const unsigned long long* src = key;
+    uint32_t len = n;
+    if (d >= 2) {
+      src = ((d - 2) & 1) ? cbuf1 : cbuf0;
+      len = sel->ccount[(d - 2) & 1];
+    }
+    unsigned long long* dst = ((d - 1) & 1) ? cbuf1 : cbuf0;
+    uint32_t* dcount = &sel->ccount[(d - 1) & 1];
+    const bool compact = d >= 1 && !last;
+    unsigned long long* stage = s_stage[threadIdx.x >> 5];
+    uint32_t sc = 0;   // keys staged by this warp (warp-uniform)
+    const unsigned long long pre = s_pre;
+    const unsigned long long hi = shift + width >= 64 ? 0ull : (~0ull << (shift + width));
+    const uint32_t dmask = (1u << width) - 1u;
+    const int lane = threadIdx.x & 31;
+    // kUnroll keys per thread per round, loaded before use (the loop is
+    // latency-bound otherwise); warp-uniform rounds
+    constexpr int kUnroll = 4;
+    const uint32_t step = gridDim.x * blockDim.x * kUnroll;
+    for (uint32_t i0 = blockIdx.x * blockDim.x * kUnroll; i0 < len; i0 += step) {
+      unsigned long long kk[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const uint32_t i = i0 + u * blockDim.x + threadIdx.x;
+        kk[u] = i < len ? src[i] : kNoKey;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const unsigned long long k = kk[u];
+        const uint32_t bin =
+            (k != kNoKey && !((k ^ pre) & hi)) ? (static_cast<uint32_t>(k >> shift) & dmask) : kBins;
+        // a warp whose keys share one bin adds once; otherwise each lane adds
+        const uint32_t b0 = __shfl_sync(0xffffffffu, bin, 0);
+        if (__all_sync(0xffffffffu, bin == b0)) {
+          if (lane == 0 && b0 < kBins) atomicAdd(&h[b0], 32u);
+        } else if (bin < kBins) {
+          atomicAdd(&h[bin], 1u);
+        }
+        if (compact) {
+          // staged per warp, flushed with one atomic per ~224 keys
+          const uint32_t m = __ballot_sync(0xffffffffu, bin < kBins);
+          if (bin < kBins) stage[sc + __popc(m & ((1u << lane) - 1u))] = k;
+          sc += __popc(m);
+          if (sc > kStage - 32) {
+            __syncwarp();
+            flush_stage(stage, sc, dst, dcount, lane);
+            sc = 0;
+          }
+        }
+      }
+    }
+    if (compact && sc) {
+      __syncwarp();
+      flush_stage(stage, sc, dst, dcount, lane);
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < kBins; t += blockDim.x)
+      if (h[t]) atomicAdd(&sel->hist[t], h[t]);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&sel->ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    sel->ticket = 0;
+    sel->ccount[d & 1] = 0;   // the buffer digit d + 1 writes (digit d read it, or nobody did)
+    if (mode != kSetupNone) {
+      sel->kind = s_kind;
+      sel->k = s_k;
+      sel->base = s_base;
+      sel->count = 0;
+      sel->prefix = 0ull;
+    }
+  }
+  if (!active) return;
+  // pick: each of the 256 threads owns 8 consecutive bins
+  constexpr int kPer = kBins / kMgCta;
+  volatile uint32_t* vh = sel->hist;
+  uint32_t v[kPer], sum = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    v[j] = vh[threadIdx.x * kPer + j];
+    sum += v[j];
+  }
+  const uint32_t kk = s_k;
+  uint32_t total;
+  uint32_t ex = block_exclusive_scan(sum, s_warp, total);
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    if (ex <= kk && kk < ex + v[j]) {
+      sel->prefix = s_pre | (static_cast<unsigned long long>(threadIdx.x * kPer + j) << shift);
+      sel->k = kk - ex;
+    }
+    ex += v[j];
+    vh[threadIdx.x * kPer + j] = 0u;
+  }
+}
+
+template <int D>
+void launch_select(const unsigned long long* key, uint32_t n, Sel* sel, unsigned long long* const (&cbuf)[2],
+                   const Digit (&digits)[D], int mode, float q, int grid, cudaStream_t s) {
+  for (int d = 0; d < D; ++d)
+    k_sel_digit<<<grid, kMgCta, 0, s>>>(key, n, sel, cbuf[0], cbuf[1], d, d == D - 1 ? 1 : 0, digits[d].shift,
+                                        digits[d].width, d == 0 ? mode : kSetupNone, q);
 }
 
 // selected if the select takes every key, or the key is at most the k-th
@@ -371,34 +506,52 @@ __device__ __forceinline__ bool sel_takes(uint32_t kind, unsigned long long pref
 // ---------------------------------------------------------------------------
 // kernels of the step
 // ---------------------------------------------------------------------------
-__global__ void k_mg_init(Sel* __restrict__ sel, uint32_t n, int64_t* __restrict__ counts) {
-  for (int t = threadIdx.x; t < 256; t += blockDim.x) sel->hist[t] = 0;
-  if (threadIdx.x == 0) {
-    sel->prefix = 0;
-    sel->count = n;      // the residual quantile takes every surfel
-    sel->k = 0;
-    sel->kind = kSelNone;
-    sel->base = 0;
-    sel->n_big = 0;
-  }
-  if (threadIdx.x < 6) counts[threadIdx.x] = 0;
-}
-
+// Residual keys for its quantile; CTA 0 also resets the select and the counts.
 __global__ void __launch_bounds__(kMgCta) k_mg_res_keys(const float* __restrict__ res, uint32_t n,
-                                                        unsigned long long* __restrict__ key) {
+                                                        unsigned long long* __restrict__ key, Sel* __restrict__ sel,
+                                                        int64_t* __restrict__ counts) {
+  if (blockIdx.x == 0) {
+    for (uint32_t t = threadIdx.x; t < kBins; t += blockDim.x) sel->hist[t] = 0;
+    if (threadIdx.x == 0) {
+      sel->prefix = 0;
+      sel->count = n;      // the residual quantile takes every surfel
+      sel->k = 0;
+      sel->kind = kSelNone;
+      sel->base = 0;
+      sel->n_big = 0;
+      sel->n_small = 0;
+      sel->ticket = 0;
+      sel->ccount[0] = 0;
+      sel->ccount[1] = 0;
+    }
+    if (threadIdx.x < 6) counts[threadIdx.x] = 0;
+  }
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     key[i] = static_cast<unsigned long long>(okey(res[i])) << 32;
+}
+
+// Clears the hash table of a pass (and its large-group list).
+__device__ __forceinline__ void clear_table(const MgScratch& S) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S.sel->n_big = 0;
+    S.sel->n_small = 0;
+  }
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < S.T; i += gridDim.x * blockDim.x) {
+    S.htab[i] = kNoKey;
+    S.rep[i] = 0ull;
+    S.cnt[i] = 0u;
+  }
 }
 
 // Control score (Eq. controlscore) with the residual normalised by its
 // quantile, and the opacity prune.
 __global__ void __launch_bounds__(kMgCta) k_mg_score(const float* __restrict__ lam, const float* __restrict__ res,
-                                                     const float* __restrict__ logit, uint32_t n,
-                                                     const Sel* __restrict__ sel, MgParams P,
-                                                     float* __restrict__ score, uint32_t* __restrict__ flags,
+                                                     const float* __restrict__ logit, uint32_t n, MgParams P,
+                                                     float* __restrict__ score, MgScratch S,
                                                      int64_t* __restrict__ counts) {
-  const float rq = okey_inv(static_cast<uint32_t>(sel->prefix >> 32));
+  const float rq = okey_inv(static_cast<uint32_t>(S.sel->prefix >> 32));
   const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t n_dead = 0, n_alive = 0;
   for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
     const uint32_t i = i0 + threadIdx.x;
     bool dead = false;
@@ -419,41 +572,17 @@ __global__ void __launch_bounds__(kMgCta) k_mg_score(const float* __restrict__ l
       s = s > 0.f ? s : 0.f;
       score[i] = s;
       const bool alive = logit[i] >= P.logit_prune;
-      flags[i] = alive ? kAlive : 0u;
+      S.flags[i] = alive ? kAlive : 0u;
+      // the survivors' scores are the keys of the next quantile
+      S.key[i] = alive ? static_cast<unsigned long long>(__float_as_uint(s)) << 32 : kNoKey;
       dead = !alive;
     }
-    warp_count64(dead, &counts[1]);
+    n_dead += dead ? 1u : 0u;
+    n_alive += (i < n && !dead) ? 1u : 0u;
   }
-}
-
-// select keys of the survivors' scores (and the start of a pass: per-pass
-// flags cleared)
-__global__ void __launch_bounds__(kMgCta) k_mg_alive_keys(const float* __restrict__ score, uint32_t n,
-                                                          uint32_t* __restrict__ flags,
-                                                          unsigned long long* __restrict__ key, Sel* __restrict__ sel) {
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
-    const uint32_t i = i0 + threadIdx.x;
-    bool alive = false;
-    if (i < n) {
-      const uint32_t f = flags[i] & kAlive;
-      flags[i] = f;
-      alive = f != 0;
-      key[i] = alive ? static_cast<unsigned long long>(__float_as_uint(score[i])) << 32 : kNoKey;
-    }
-    warp_count(alive, &sel->count);
-  }
-}
-
-__global__ void __launch_bounds__(kMgCta) k_mg_clear(unsigned long long* __restrict__ htab,
-                                                     unsigned long long* __restrict__ rep, uint32_t* __restrict__ cnt,
-                                                     uint32_t T, Sel* __restrict__ sel) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) sel->n_big = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
-    htab[i] = kNoKey;
-    rep[i] = 0ull;
-    cnt[i] = 0u;
-  }
+  block_count64(n_dead, &counts[1]);
+  block_count(n_alive, &S.sel->count);
+  clear_table(S);
 }
 
 // Planar candidates of the pass join their voxel's group; the group's
@@ -554,103 +683,163 @@ __global__ void __launch_bounds__(kMgCta) k_mg_scatter(uint32_t n, MgScratch S) 
     old = __shfl_sync(peers, old, lead);
     // the peers take slots old-1, old-2, ... of the group's bucket
     const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-    S.bucket[b + old - 1u - rank] = S.r2[i];
-    // the first decrement of a large group lists it for the radix select
-    if (lane == lead && old == m && m > kSmallGroup) S.big[atomicAdd(&S.sel->n_big, 1u)] = h;
+    S.bucket[b + old - 1u - rank] = (static_cast<unsigned long long>(S.r2[i]) << 32) | i;
+    // the first decrement lists the group for k_mg_decide
+    if (lane == lead && old == m) {
+      if (m > kSmallGroup) S.big[atomicAdd(&S.sel->n_big, 1u)] = h;
+      else S.small[atomicAdd(&S.sel->n_small, 1u)] = h;
+    }
   }
 }
 
-// k-th smallest radius of each large group by a one-CTA radix select over
-// its bucket (4 digits of 8 bits); the result goes to cnt[h] (all zero after
-// the scatter), read by the members in k_mg_decide.
-__global__ void __launch_bounds__(kMgCta) k_mg_big_select(MgScratch S, MgParams P) {
-  __shared__ uint32_t h[256];
+// Marks a member covered: the cap select takes its key (score, index).
+__device__ __forceinline__ void cover(const float* __restrict__ score, const MgScratch& S, uint32_t i) {
+  S.flags[i] |= kFlag;
+  S.key[i] = (static_cast<unsigned long long>(__float_as_uint(score[i])) << 32) | i;
+}
+
+// A member is covered when its radius is at most the k-th smallest of its
+// group, k = ceil(q_cover m).  Large groups (more than kSmallGroup members):
+// one CTA finds the k-th smallest by a radix select over the bucket (4
+// digits of 8 bits) and flags; the others: one warp per group stages the
+// radii in shared memory and each member counts the strictly smaller ones
+// (fewer than k: covered).
+__global__ void __launch_bounds__(kMgCta) k_mg_decide(const float* __restrict__ score, MgParams P, MgScratch S) {
+  __shared__ uint32_t h[kBins];
   __shared__ uint32_t s_warp[32];
-  __shared__ uint32_t s_pre, s_k;
-  const uint32_t nb = S.sel->n_big;
+  __shared__ uint32_t s_pre, s_k, s_cov;
+  __shared__ uint4 s_r2[kMgCta / 32][kSmallGroup / 4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t nb = S.sel->n_big, ns = S.sel->n_small;
   for (uint32_t g = blockIdx.x; g < nb; g += gridDim.x) {
     const uint32_t slot = S.big[g];
     const uint32_t b = S.off[slot], e = S.off[slot + 1];
     const uint32_t k = static_cast<uint32_t>(ceil(static_cast<double>(P.q_cover) * static_cast<double>(e - b)));
+    if (k == 0) continue;   // uniform across the CTA
     if (threadIdx.x == 0) {
       s_pre = 0;
       s_k = k - 1u;
+      s_cov = 0;
     }
-    if (k == 0) {   // uniform across the CTA
-      if (threadIdx.x == 0) S.cnt[slot] = 0u;   // unused: no member is covered
-      __syncthreads();
-      continue;
-    }
-    for (int shift = 24; shift >= 0; shift -= 8) {
-      h[threadIdx.x] = 0;
+    // digits of 11, 11 and 10 bits over the 32-bit radii
+    for (int d = 0; d < 3; ++d) {
+      const int shift = d == 0 ? 21 : (d == 1 ? 10 : 0);
+      const int width = d == 2 ? 10 : 11;
+      for (uint32_t t = threadIdx.x; t < kBins; t += blockDim.x) h[t] = 0;
       __syncthreads();
       const uint32_t pre = s_pre;
-      const uint32_t hi = shift == 24 ? 0u : (~0u << (shift + 8));
-      for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-        const uint32_t x = S.bucket[j];
-        if ((x ^ pre) & hi) continue;
-        atomicAdd(&h[(x >> shift) & 255u], 1u);
+      const uint32_t hi = d == 0 ? 0u : (~0u << (shift + width));
+      const uint32_t dmask = (1u << width) - 1u;
+      constexpr int kUnroll = 4;
+      for (uint32_t j0 = b + threadIdx.x; j0 < e; j0 += blockDim.x * kUnroll) {
+        uint32_t x[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const uint32_t j = j0 + u * blockDim.x;
+          x[u] = j < e ? static_cast<uint32_t>(S.bucket[j] >> 32) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+          if (j0 + u * blockDim.x < e && !((x[u] ^ pre) & hi)) atomicAdd(&h[(x[u] >> shift) & dmask], 1u);
       }
       __syncthreads();
-      const uint32_t v = h[threadIdx.x];
+      constexpr int kPer = kBins / kMgCta;
+      uint32_t v[kPer], sum = 0;
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        v[j] = h[threadIdx.x * kPer + j];
+        sum += v[j];
+      }
       const uint32_t kk = s_k;
       uint32_t total;
-      const uint32_t ex = block_exclusive_scan(v, s_warp, total);
-      if (ex <= kk && kk < ex + v) {
-        s_pre = pre | (threadIdx.x << shift);
-        s_k = kk - ex;
+      uint32_t ex = block_exclusive_scan(sum, s_warp, total);
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        if (ex <= kk && kk < ex + v[j]) {
+          s_pre = pre | ((threadIdx.x * kPer + j) << shift);
+          s_k = kk - ex;
+        }
+        ex += v[j];
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) S.cnt[slot] = s_pre;
-    __syncthreads();
-  }
-}
-
-// A member is covered when fewer than k = ceil(q_cover m) members of its
-// group are strictly closer (its radius is then at most the k-th smallest).
-__global__ void __launch_bounds__(kMgCta) k_mg_decide(const float* __restrict__ score, uint32_t n, MgParams P,
-                                                      MgScratch S) {
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
-    const uint32_t i = i0 + threadIdx.x;
-    bool flagged = false;
-    if (i < n && (S.flags[i] & kMember)) {
-      const uint32_t h = S.slot[i];
-      const uint32_t b = S.off[h], e = S.off[h + 1];
-      const uint32_t k = static_cast<uint32_t>(ceil(static_cast<double>(P.q_cover) * static_cast<double>(e - b)));
-      const uint32_t x = S.r2[i];
-      bool covered;
-      if (e - b > kSmallGroup) {
-        covered = k > 0 && x <= S.cnt[h];   // the k-th smallest from k_mg_big_select
-      } else {
-        uint32_t less = 0;
-        for (uint32_t j = b; j < e && less < k; ++j) less += S.bucket[j] < x ? 1u : 0u;
-        covered = less < k;
-      }
-      if (covered) {
-        flagged = true;
-        S.flags[i] |= kFlag;
-        S.key[i] = (static_cast<unsigned long long>(__float_as_uint(score[i])) << 32) | i;
+    const uint32_t beta2 = s_pre;
+    uint32_t mine = 0;
+    for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+      const unsigned long long bj = S.bucket[j];
+      if (static_cast<uint32_t>(bj >> 32) <= beta2) {
+        cover(score, S, static_cast<uint32_t>(bj));
+        ++mine;
       }
     }
-    warp_count(flagged, &S.sel->count);
+    atomicAdd(&s_cov, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&S.sel->count, s_cov);
+    __syncthreads();
+  }
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  uint4* r4 = s_r2[wid];
+  uint32_t* r2 = reinterpret_cast<uint32_t*>(r4);
+  for (uint32_t g = blockIdx.x * (blockDim.x >> 5) + wid; g < ns; g += warps) {
+    const uint32_t slot = S.small[g];
+    const uint32_t b = S.off[slot], m = S.off[slot + 1] - b;
+    const uint32_t k = static_cast<uint32_t>(ceil(static_cast<double>(P.q_cover) * static_cast<double>(m)));
+    const uint32_t m4 = (m + 3) / 4;
+    // radii staged in shared memory, the tail padded with the largest key
+    // (never strictly smaller than a radius)
+    for (uint32_t j = lane; j < 4 * m4; j += 32) r2[j] = j < m ? static_cast<uint32_t>(S.bucket[b + j] >> 32) : ~0u;
+    __syncwarp();
+    uint32_t cov = 0;
+    for (uint32_t j0 = 0; j0 < m; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      const uint32_t x = j < m ? r2[j] : 0u;
+      // strictly smaller radii of the group: every lane reads the same
+      // 16-byte words (broadcast); four independent partial counts
+      uint32_t l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+      for (uint32_t t = 0; t < m4; ++t) {
+        const uint4 v = r4[t];
+        l0 += v.x < x;
+        l1 += v.y < x;
+        l2 += v.z < x;
+        l3 += v.w < x;
+      }
+      const bool covered = j < m && (l0 + l1) + (l2 + l3) < k;
+      if (covered) cover(score, S, static_cast<uint32_t>(S.bucket[b + j]));
+      cov += __popc(__ballot_sync(0xffffffffu, covered));
+    }
+    if (lane == 0 && cov) atomicAdd(&S.sel->count, cov);
+    __syncwarp();   // the staged radii are read before the next group overwrites them
   }
 }
 
-__global__ void __launch_bounds__(kMgCta) k_mg_apply_prune(uint32_t n, MgScratch S, int64_t* __restrict__ removed) {
+// Removes the covered members the cap admits; writes the survivors' score
+// keys for the next quantile (counted into the select) and clears the table.
+__global__ void __launch_bounds__(kMgCta) k_mg_apply_prune(const float* __restrict__ score, uint32_t n, MgScratch S,
+                                                           int64_t* __restrict__ removed) {
   const uint32_t kind = S.sel->kind;
   const unsigned long long prefix = S.sel->prefix;
   const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t n_rm = 0, n_alive = 0;
   for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
     const uint32_t i = i0 + threadIdx.x;
-    bool rm = false;
-    if (i < n && (S.flags[i] & kFlag) && sel_takes(kind, prefix, S.key[i])) {
-      rm = true;
-      S.flags[i] &= ~kAlive;
+    bool rm = false, alive = false;
+    if (i < n) {
+      uint32_t f = S.flags[i];
+      if ((f & kFlag) && sel_takes(kind, prefix, S.key[i])) {
+        rm = true;
+        f &= ~kAlive;
+      }
+      f &= kAlive;
+      S.flags[i] = f;
+      alive = f != 0;
+      S.key[i] = alive ? static_cast<unsigned long long>(__float_as_uint(score[i])) << 32 : kNoKey;
     }
-    warp_count64(rm, removed);
+    n_rm += rm ? 1u : 0u;
+    n_alive += alive ? 1u : 0u;
   }
+  block_count64(n_rm, removed);
+  block_count(n_alive, &S.sel->count);
+  clear_table(S);
 }
 
 // split candidates: survivors with c >= Q_{q_split} and alpha >= alpha_min,
@@ -661,6 +850,7 @@ __global__ void __launch_bounds__(kMgCta) k_mg_split_keys(const float* __restric
   const bool any = S.sel->kind != kSelNone;
   const float qs = __uint_as_float(static_cast<uint32_t>(S.sel->prefix >> 32));
   const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t n_cand = 0;
   for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
     const uint32_t i = i0 + threadIdx.x;
     bool cand = false;
@@ -669,8 +859,9 @@ __global__ void __launch_bounds__(kMgCta) k_mg_split_keys(const float* __restric
       cand = any && (S.flags[i] & kAlive) && c >= qs && logit[i] >= P.logit_min;
       S.key[i] = cand ? ((static_cast<unsigned long long>(~__float_as_uint(c)) << 32) | i) : kNoKey;
     }
-    warp_count(cand, &S.sel->count);
+    n_cand += cand ? 1u : 0u;
   }
+  block_count(n_cand, &S.sel->count);
 }
 
 __global__ void __launch_bounds__(kMgCta) k_mg_weights(uint32_t n, MgScratch S) {
@@ -695,6 +886,7 @@ __global__ void __launch_bounds__(kMgCta) k_mg_write(const float* __restrict__ m
                                                      int32_t* __restrict__ src, uint8_t* __restrict__ role,
                                                      int64_t* __restrict__ counts) {
   const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t n_split = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) counts[0] = S.pos[n];
   for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
     const uint32_t i = i0 + threadIdx.x;
@@ -735,8 +927,9 @@ __global__ void __launch_bounds__(kMgCta) k_mg_write(const float* __restrict__ m
         role[o] = static_cast<uint8_t>(split ? 1 + c : 0);
       }
     }
-    warp_count64(split, &counts[5]);
+    n_split += split ? 1u : 0u;
   }
+  block_count64(n_split, &counts[5]);
 }
 
 __global__ void __launch_bounds__(kMgCta) k_mg_gather(const int32_t* __restrict__ src, const uint8_t* __restrict__ role,
@@ -771,12 +964,10 @@ int sm_count() {
 size_t manage_scratch_bytes(int64_t n) { return mg_layout(n).total; }
 
 int manage_kernel_count(int n_passes) {
-  // init, residual keys + 4 digits, score; per pass: keys, quantile + 4
-  // digits, clear, insert, measure, scan (3), scatter, large-group select,
-  // decide, cap + 8 digits, apply; split: keys, quantile + 4 digits, split keys, cap + 8
-  // digits, weights, scan (3), write
-  return 1 + (1 + 8) + 1 + 1 + n_passes * (1 + 1 + 8 + 1 + 1 + 1 + 3 + 1 + 1 + 1 + 1 + 16 + 1) +
-         (1 + 1 + 8 + 1 + 1 + 16 + 1 + 3 + 1);
+  // residual keys, 3 digits, score; per pass: 3 digits, insert, measure,
+  // scan (3), scatter, decide, 6 digits, apply; split: 3 digits, split keys,
+  // 6 digits, weights, scan (3), write
+  return 1 + 3 + 1 + n_passes * (3 + 1 + 1 + 3 + 1 + 1 + 6 + 1) + (3 + 1 + 6 + 1 + 3 + 1);
 }
 
 cudaError_t launch_manage(const lgs_surfels& M, const float* lam, const float* res, const MgHostParams& H,
@@ -786,7 +977,8 @@ cudaError_t launch_manage(const lgs_surfels& M, const float* lam, const float* r
   const MgScratch S = mg_scratch(scratch, M.n);
   const int sms = sm_count();
   const int g = grid_for(n, sms);
-  const int gT = grid_for(S.T, sms);
+  const int gc = grid_for(n > S.T ? n : S.T, sms);   // kernels that also clear the table
+  const int gs = grid_for(n, sms) < 2 * sms ? grid_for(n, sms) : 2 * sms;   // select digits
   MgParams P;
   P.logit_prune = H.logit_prune;
   P.logit_min = H.logit_min;
@@ -806,32 +998,22 @@ cudaError_t launch_manage(const lgs_surfels& M, const float* lam, const float* r
   P.split_dlog = H.p.split_dlog;
   static const int planes[3][2] = {{0, 1}, {1, 2}, {2, 0}};
 
-  k_mg_init<<<1, 256, 0, s>>>(S.sel, n, counts);
-  k_mg_res_keys<<<g, kMgCta, 0, s>>>(res, n, S.key);
-  k_sel_quantile<<<1, 1, 0, s>>>(S.sel, P.q_res);
-  launch_select(S.key, n, S.sel, 4, g, s);
-  k_mg_score<<<g, kMgCta, 0, s>>>(lam, res, M.opacity_logit, n, S.sel, P, score, S.flags, counts);
+  k_mg_res_keys<<<g, kMgCta, 0, s>>>(res, n, S.key, S.sel, counts);
+  launch_select(S.key, n, S.sel, S.cbuf, kDigits32, kSetupQuantile, P.q_res, gs, s);
+  k_mg_score<<<gc, kMgCta, 0, s>>>(lam, res, M.opacity_logit, n, P, score, S, counts);
   for (int p = 0; p < H.p.n_passes; ++p) {
-    k_mg_alive_keys<<<g, kMgCta, 0, s>>>(score, n, S.flags, S.key, S.sel);
-    k_sel_quantile<<<1, 1, 0, s>>>(S.sel, P.q_plane);
-    launch_select(S.key, n, S.sel, 4, g, s);
-    k_mg_clear<<<gT, kMgCta, 0, s>>>(S.htab, S.rep, S.cnt, S.T, S.sel);
+    launch_select(S.key, n, S.sel, S.cbuf, kDigits32, kSetupQuantile, P.q_plane, gs, s);
     k_mg_insert<<<g, kMgCta, 0, s>>>(M.mean, M.opacity_logit, score, n, S.sel, P, planes[p][0], planes[p][1], S);
     k_mg_measure<<<g, kMgCta, 0, s>>>(M.mean, M.quat, M.log_scale, n, P, S);
     launch_scan(S.cnt, S.off, S.T, S.part, s);
     k_mg_scatter<<<g, kMgCta, 0, s>>>(n, S);
-    k_mg_big_select<<<sms * 4, kMgCta, 0, s>>>(S, P);
-    k_mg_decide<<<g, kMgCta, 0, s>>>(score, n, P, S);
-    k_sel_cap<<<1, 1, 0, s>>>(S.sel, P.prune_cap);
-    launch_select(S.key, n, S.sel, 8, g, s);
-    k_mg_apply_prune<<<g, kMgCta, 0, s>>>(n, S, counts + 2 + p);
+    k_mg_decide<<<sms * 4, kMgCta, 0, s>>>(score, P, S);
+    launch_select(S.key, n, S.sel, S.cbuf, kDigits64, kSetupCap, P.prune_cap, gs, s);
+    k_mg_apply_prune<<<gc, kMgCta, 0, s>>>(score, n, S, counts + 2 + p);
   }
-  k_mg_alive_keys<<<g, kMgCta, 0, s>>>(score, n, S.flags, S.key, S.sel);
-  k_sel_quantile<<<1, 1, 0, s>>>(S.sel, P.q_split);
-  launch_select(S.key, n, S.sel, 4, g, s);
+  launch_select(S.key, n, S.sel, S.cbuf, kDigits32, kSetupQuantile, P.q_split, gs, s);
   k_mg_split_keys<<<g, kMgCta, 0, s>>>(M.opacity_logit, score, n, P, S);
-  k_sel_cap<<<1, 1, 0, s>>>(S.sel, P.split_cap);
-  launch_select(S.key, n, S.sel, 8, g, s);
+  launch_select(S.key, n, S.sel, S.cbuf, kDigits64, kSetupCap, P.split_cap, gs, s);
   k_mg_weights<<<g, kMgCta, 0, s>>>(n, S);
   launch_scan(S.pos, S.pos, n, S.part, s);
   k_mg_write<<<g, kMgCta, 0, s>>>(M.mean, M.quat, M.log_scale, M.opacity_logit, n, P, S, out, capacity, src, role,
