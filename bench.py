@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--manage-n", type=int, default=2_000_000, help="map size of the manage workload")
     ap.add_argument("--workload", default="street",
-                    choices=["street", "mapping", "batched", "serving", "tracking", "manage"],
+                    choices=["street", "mapping", "batched", "serving", "tracking", "manage", "keyframe"],
                     help="street: the headline line; the others print their own line")
     ap.add_argument("--no-serving", action="store_true", help="skip the reduced serving run of the street line")
     ap.add_argument("--serve-seconds", type=float, default=None)
@@ -493,6 +493,93 @@ def run_manage(args):
     print(json.dumps(line), flush=True)
 
 
+def run_keyframe(args):
+    """Keyframe initialisation (Sec. 3.2 k-NN covariance; Sec. 3.3 scale,
+    confidence, opacity) of one 128 x 1024 street scan: a step is one
+    lgs_keyframe_init call over every valid point (k = 20), device-timed with
+    CUDA events (points resident, L2 flushed between steps); end to end from
+    pinned host points with the new surfels read back; the oracle on sampled
+    rows of the same scan."""
+    import numpy as np
+    import torch
+    from paper_2607_04127_gb300 import build, keyframe, scenes
+    build.build()
+    pts, pose = scenes.keyframe_points(11, 128, 1024)
+    n = len(pts)
+    dev = torch.device("cuda", 0)
+    t = torch.from_numpy(pts).to(dev)
+    p = keyframe.params()
+    out = keyframe.initialise(t, pose, p)
+    pairs = torch.zeros(1, dtype=torch.int64, device=dev)
+    keyframe.initialise(t, pose, p, out=out, pairs=pairs)
+    torch.cuda.synchronize()
+    n_pairs = int(pairs.item())
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        keyframe.initialise(t, pose, p, out=out)
+    torch.cuda.synchronize()
+    steps = max(min(args.steps, 50), 10)
+    ms = []
+    with Clocks(0) as clk:
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            keyframe.initialise(t, pose, p, out=out)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+    step_s = statistics.median(ms) / 1e3
+    host = torch.from_numpy(pts).pin_memory()
+    dst = {k: torch.empty(out[k].shape, dtype=out[k].dtype).pin_memory()
+           for k in ("mean", "quat", "log_scale", "logit", "lam", "u")}
+    e2e_ms = []
+    for _ in range(5):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t.copy_(host, non_blocking=True)
+        keyframe.initialise(t, pose, p, out=out)
+        for k, d in dst.items():
+            d.copy_(out[k], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_s = statistics.median(e2e_ms) / 1e3
+    d2h = sum(d.numel() * d.element_size() for d in dst.values())
+    from oracle import init as oinit
+    P = oinit.Params()
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    done = 0
+    while done == 0 or time.perf_counter() - t0 < min(args.cpu_seconds, 10.0):
+        rows = np.sort(rng.choice(n, 500, replace=False))
+        oinit.initialise(pts, pose, P, rows=rows)
+        done += rows.size
+    cpu_s = time.perf_counter() - t0
+    # ALU roofline: 8 FP32 operations per evaluated distance (3 sub, 3 mul,
+    # 2 add) against one operation per FP32 lane per clock
+    lanes_peak = 152 * 128 * 2.07e9 / 1e12
+    achieved = n_pairs * 8 / step_s / 1e12
+    line = dict(metric="keyframe initialisation: points/s (exact 20-NN covariance, eigendecomposition, scale, "
+                       "confidence, opacity)",
+                value=n / step_s, unit="points/s", higher_is_better=True, n_gpus=1, steps=steps,
+                warmup=max(args.warmup, 3), ms_per_step=step_s * 1e3, scaling="weak", vs_baseline=None, dtype="f32",
+                data="synthetic (seeded street scan, scenes.keyframe_points)",
+                config=dict(workload=f"one 128x1024 street scan, {n} points, k = 20", points=n, k=p.k,
+                            pairs_evaluated=n_pairs, brute_force_pairs=n * n,
+                            l2="flushed between steps (256 MB write)"),
+                roofline=dict(bound="alu", kernel="whole call (k-NN dominant)", achieved=achieved,
+                              peak=lanes_peak, unit="Tops/s", frac=achieved / lanes_peak, traffic=None,
+                              note="8 FP32 operations per evaluated distance over the call's CUDA-event time; "
+                                   "peak = 152 SMs x 128 FP32 lanes x 2.07 GHz"),
+                e2e=dict(value=n / e2e_s, unit="points/s", h2d_bytes_per_step=n * 12, d2h_bytes_per_step=d2h),
+                cpu_baseline=dict(value=done / cpu_s, unit="points/s", cores=1, kind="oracle",
+                                  sample=f"{done} sampled rows of the same scan in {cpu_s:.1f} s (NumPy brute-force "
+                                         f"k-NN over all {n} points, FP64 frames)"),
+                gpu_launches=3 * steps, clocks=clk.summary())
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -680,6 +767,8 @@ def main():
         run_tracking(args)
     elif args.workload == "manage":
         run_manage(args)
+    elif args.workload == "keyframe":
+        run_keyframe(args)
     else:
         run_ours(args)
 

@@ -448,6 +448,55 @@ LGS_API lgs_status lgs_map_gather(const int32_t* src, const uint8_t* role, const
                                   const void* in, void* out, int32_t words_per_row, int32_t zero_children,
                                   void* stream);
 
+/* ---- keyframe initialisation (Sec. 3.2 k-NN covariance; Sec. 3.3) ------------
+ * New surfels at the points of a keyframe scan: for each point its k nearest
+ * neighbours among the scan's points (itself included; binary32 squared
+ * distance ((dx dx + dy dy) + dz dz), ties to the lower index), the
+ * covariance of the neighbourhood about its mean (1/k) and its
+ * eigendecomposition (lambda_0 >= lambda_1 >= lambda_2), then
+ *  - orientation: normal = the smallest eigenvector turned toward the sensor,
+ *    t_u = the largest (its sign is free), t_v = n x t_u, rotated to the
+ *    world by the pose;
+ *  - the range-adaptive scale s = clip(kappa max(|p|, 1) sigma_tan, s_min,
+ *    s_max) with sigma_tan = (1, sigma_1 / sigma_0), sigma = sqrt(lambda)
+ *    (normalised by the largest, as G-ICP normalises its covariances);
+ *  - the physics-based confidence u = exp(-(|p| / r0)^2) clip((c - c0) /
+ *    (1 - c0 + eps), 0, 1), c = |n . p / |p|| (Eq. physconf);
+ *  - the opacity alpha = alpha_min + (alpha_max - alpha_min) u (Eq.
+ *    alpha_init), stored as its logit.
+ * The eigenvalues are returned for the control score of map management. */
+typedef struct {
+    int32_t k;           /* neighbours, 3..32, <= n; 20 */
+    float kappa;         /* > 0; 0.0184 (1.5 x the pitch of a 128-beam +-45 deg sensor) */
+    float s_min, s_max;  /* 0 < s_min <= s_max; 1e-3, 1.0 (metres) */
+    float r0;            /* > 0; 100 (metres) */
+    float c0;            /* in [0, 1); 0.1 */
+    float eps;           /* > 0; 1e-6 */
+    float alpha_min, alpha_max;   /* 0 < alpha_min <= alpha_max < 1; 0.3, 0.9 */
+} lgs_init_params;
+
+/* The defaults listed above. */
+LGS_API void lgs_init_default_params(lgs_init_params* p);
+/* Bytes of device scratch lgs_keyframe_init needs for n points. */
+LGS_API size_t lgs_init_scratch_bytes(int64_t n);
+/* Points per call at most (2^20). */
+LGS_API int64_t lgs_init_max_points(void);
+
+/* points [n][3]: device, the scan's points in the sensor frame, finite and
+ * not at the origin; pose: host, 12 floats (sensor -> world, R row-major |
+ * t).  scratch: lgs_init_scratch_bytes(n) bytes of device memory, 16-byte
+ * aligned, contents irrelevant.  Writes knn [n][k] int32 (ascending
+ * distance), the new surfels into out (n rows, world frame), lam [n][3] and
+ * u [n], all device and caller-owned.  pairs: NULL, or a device int64 to
+ * which the k-NN adds the number of (query, candidate) distances it
+ * evaluated (tiles it could not rule out by their bounding boxes).  Enqueues
+ * on stream without a host sync; argument errors return LGS_ERR_INVALID_ARG
+ * before anything is enqueued. */
+LGS_API lgs_status lgs_keyframe_init(const float* points, int64_t n, const float pose[12],
+                                     const lgs_init_params* params, void* scratch, size_t scratch_bytes,
+                                     int32_t* knn, const lgs_surfel_params_out* out, float* lam, float* u,
+                                     int64_t* pairs, void* stream);
+
 /* ---- image loss without a session or workspace --------------------------
  * The paper has no counterpart to this call; it is an interface for callers
  * that cannot allocate device memory at the point where they evaluate the

@@ -47,20 +47,23 @@ class Params:
     alpha_max: float = 0.9      # opacity at u = 1
 
 
-def knn(points, k: int, chunk: int = 512):
-    """The k nearest neighbours of every point among the points (itself
-    included), by binary32 squared distance, ties to the lower index, in
-    ascending (distance, index) order.  Returns (index int32 [n, k],
-    squared distance float32 [n, k])."""
+def knn(points, k: int, rows=None, chunk: int = 512):
+    """The k nearest neighbours of every point (or of the points ``rows``)
+    among all the points (itself included), by binary32 squared distance,
+    ties to the lower index, in ascending (distance, index) order.  Returns
+    (index int32 [m, k], squared distance float32 [m, k])."""
     p = np.asarray(points, F)
     n = p.shape[0]
     if k > n:
         raise ValueError("k exceeds the number of points")
-    idx = np.empty((n, k), np.int32)
-    d2 = np.empty((n, k), F)
+    rows = np.arange(n) if rows is None else np.asarray(rows)
+    m = rows.size
+    chunk = max(1, min(chunk, 20_000_000 // max(n, 1)))     # bounded temporaries
+    idx = np.empty((m, k), np.int32)
+    d2 = np.empty((m, k), F)
     cols = np.arange(n, dtype=np.int64)
-    for a in range(0, n, chunk):
-        q = p[a:a + chunk]
+    for a in range(0, m, chunk):
+        q = p[rows[a:a + chunk]]
         dx = p[None, :, 0] - q[:, None, 0]
         dy = p[None, :, 1] - q[:, None, 1]
         dz = p[None, :, 2] - q[:, None, 2]
@@ -86,9 +89,10 @@ def covariance(points, idx):
     return np.einsum("nki,nkj->nij", c, c) / idx.shape[1]
 
 
-def initialise(points, pose, p: Params = Params()):
+def initialise(points, pose, p: Params = Params(), rows=None):
     """New surfels at the scan's points (sensor frame, binary32 [n, 3]) for a
-    keyframe at ``pose`` (sensor -> world, R row-major | t, 12 values).
+    keyframe at ``pose`` (sensor -> world, R row-major | t, 12 values); with
+    ``rows``, only for those points (their neighbours still among all).
 
     Returns a dict: knn [n, k] int32; lam [n, 3] eigenvalues descending (>= 0);
     normal_s, tu_s [n, 3] the sensor-frame normal (toward the sensor) and
@@ -96,13 +100,13 @@ def initialise(points, pose, p: Params = Params()):
     [t_u, t_v, n] as columns; quat [n, 4] (w, x, y, z), w >= 0; log_scale
     [n, 2]; u [n]; alpha [n]; logit [n]; all FP64 but knn."""
     pts = np.asarray(points, F)
-    n = pts.shape[0]
-    idx, _ = knn(pts, p.k)
+    rows = np.arange(pts.shape[0]) if rows is None else np.asarray(rows)
+    idx, _ = knn(pts, p.k, rows)
     C = covariance(pts, idx)
     w, v = np.linalg.eigh(C)                      # ascending
     lam = np.maximum(w[:, ::-1], 0.0)
     e0, e2 = v[:, :, 2], v[:, :, 0]
-    ps = pts.astype(np.float64)
+    ps = pts[rows].astype(np.float64)
     rng = np.linalg.norm(ps, axis=1)
     # normal toward the sensor (at the origin of the sensor frame)
     nrm = np.where(((e2 * ps).sum(1) > 0)[:, None], -e2, e2)

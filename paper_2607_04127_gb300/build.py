@@ -15,7 +15,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblgs.so")
-SOURCES = ["lgs_api.cu", "lgs_bin.cu", "lgs_raster.cu", "lgs_optim.cu", "lgs_noalloc.cu", "lgs_track.cu", "lgs_manage.cu"]
+SOURCES = ["lgs_api.cu", "lgs_bin.cu", "lgs_raster.cu", "lgs_optim.cu", "lgs_noalloc.cu", "lgs_track.cu", "lgs_manage.cu", "lgs_init.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

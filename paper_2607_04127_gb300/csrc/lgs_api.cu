@@ -771,6 +771,46 @@ lgs_status lgs_map_gather(const int32_t* src, const uint8_t* role, const int64_t
   return e == cudaSuccess ? LGS_OK : cuda_fail(e, "map gather");
 }
 
+void lgs_init_default_params(lgs_init_params* p) {
+  if (!p) return;
+  p->k = 20;
+  p->kappa = 0.0184f;
+  p->s_min = 1e-3f;
+  p->s_max = 1.0f;
+  p->r0 = 100.f;
+  p->c0 = 0.1f;
+  p->eps = 1e-6f;
+  p->alpha_min = 0.3f;
+  p->alpha_max = 0.9f;
+}
+
+size_t lgs_init_scratch_bytes(int64_t n) { return lgs::init_scratch_bytes(n < 0 ? 0 : n); }
+
+int64_t lgs_init_max_points(void) { return lgs::init_max_points(); }
+
+lgs_status lgs_keyframe_init(const float* points, int64_t n, const float pose[12], const lgs_init_params* p,
+                             void* scratch, size_t scratch_bytes, int32_t* knn, const lgs_surfel_params_out* out,
+                             float* lam, float* u, int64_t* pairs, void* stream) {
+  if (!pose || !p || !out) return fail(LGS_ERR_INVALID_ARG, "NULL argument");
+  if (n < 0 || n > lgs::init_max_points()) return fail(LGS_ERR_INVALID_ARG, "n outside [0, 2^20]");
+  if (n > 0 && (!points || !scratch || !knn || !out->mean || !out->quat || !out->log_scale ||
+                !out->opacity_logit || !lam || !u))
+    return fail(LGS_ERR_INVALID_ARG, "NULL array");
+  if (p->k < 3 || p->k > 32 || (n > 0 && p->k > n)) return fail(LGS_ERR_INVALID_ARG, "k outside [3, min(32, n)]");
+  if (!(p->kappa > 0.f) || !(p->s_min > 0.f) || !(p->s_max >= p->s_min) || !(p->r0 > 0.f) ||
+      !(p->c0 >= 0.f && p->c0 < 1.f) || !(p->eps > 0.f) || !(p->alpha_min > 0.f) ||
+      !(p->alpha_max >= p->alpha_min) || !(p->alpha_max < 1.f) || !std::isfinite(p->s_max) ||
+      !std::isfinite(p->kappa))
+    return fail(LGS_ERR_INVALID_ARG, "initialisation parameters out of range");
+  for (int a = 0; a < 12; ++a)
+    if (!std::isfinite(pose[a])) return fail(LGS_ERR_INVALID_ARG, "pose not finite");
+  if (n > 0 && (scratch_bytes < lgs::init_scratch_bytes(n) || (reinterpret_cast<uintptr_t>(scratch) & 15)))
+    return fail(LGS_ERR_INVALID_ARG, "scratch too small or not 16-byte aligned");
+  const cudaError_t e = lgs::launch_keyframe_init(points, n, pose, *p, scratch, knn, *out, lam, u, pairs,
+                                                  static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? LGS_OK : cuda_fail(e, "keyframe initialisation");
+}
+
 lgs_status lgs_render_fwd_loss_batch(lgs_session s, const lgs_surfels* maps, int n_maps, const lgs_frame* frames,
                                      const int32_t* frame_map, int n_frames, const lgs_fwd_out* fwd,
                                      const lgs_target* targets, const lgs_loss_params* params,

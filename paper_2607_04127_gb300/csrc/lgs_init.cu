@@ -1,0 +1,381 @@
+// lgs_init.cu -- keyframe initialisation of new surfels from a scan (paper
+// Sec. 3.2 "Covariance construction and reuse": the k-NN covariance of each
+// point and its eigendecomposition; Sec. 3.3: the range-adaptive scale
+// initialisation, the physics-based confidence u of Eq. physconf and the
+// opacity of Eq. alpha_init).
+//
+// Three launches: per-tile bounding boxes of the points (tiles of 256
+// consecutive points); the k nearest neighbours (one CTA per query tile, an
+// exact top-K kept sorted in registers, candidate tiles staged in shared
+// memory; the CTA's own and neighbouring tiles first, then only tiles whose
+// box can still hold a point closer than the CTA's current K-th distance);
+// the frame of each point (covariance of the neighbourhood, cyclic Jacobi
+// eigendecomposition, scales, confidence, opacity, orientation).
+//
+// The neighbour sets are integer outcomes: the squared distance that decides
+// them is binary32 ((dx dx + dy dy) + dz dz), each operation correctly
+// rounded, ties to the lower index, so the sets are a fixed function of the
+// input (and bit-exact against the oracle).  Tile pruning is conservative
+// (a margin of 1e-5 on the box distance, far above the few ulps that separate
+// the box bound from any binary32 distance), so it never changes a set.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "lgs_internal.cuh"
+
+namespace lgs {
+namespace {
+
+constexpr int kIniTile = 256;        // points per tile = queries per CTA
+constexpr int kIniWindow = 17;       // tiles visited before pruning: own, +-1, ..., +-8
+constexpr int kIniMaxTiles = 4096;   // n <= 2^20
+
+struct IniBox {
+  float lo[3], hi[3];
+};
+
+struct IniParams {
+  float R[9], t[3];                  // pose: sensor -> world
+  float kappa, s_min, s_max, r0, c0, eps, alpha_min, alpha_max;
+  int k;
+};
+
+__global__ void __launch_bounds__(kIniTile) k_ini_boxes(const float* __restrict__ pts, uint32_t n,
+                                                        IniBox* __restrict__ boxes) {
+  __shared__ float s_lo[3][kIniTile / 32], s_hi[3][kIniTile / 32];
+  const uint32_t i = blockIdx.x * kIniTile + threadIdx.x;
+  const bool ok = i < n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int a = 0; a < 3; ++a) {
+    const float v = ok ? pts[3 * i + a] : 0.f;
+    float lo = ok ? v : INFINITY, hi = ok ? v : -INFINITY;
+    for (int o = 16; o; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      s_lo[a][wid] = lo;
+      s_hi[a][wid] = hi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int w = 0; w < kIniTile / 32; ++w) {
+      lo = fminf(lo, s_lo[threadIdx.x][w]);
+      hi = fmaxf(hi, s_hi[threadIdx.x][w]);
+    }
+    boxes[blockIdx.x].lo[threadIdx.x] = lo;
+    boxes[blockIdx.x].hi[threadIdx.x] = hi;
+  }
+}
+
+// binary32 squared distance in the specified order (no contraction)
+__device__ __forceinline__ float dist2(float ax, float ay, float az, float bx, float by, float bz) {
+  const float dx = fsub(bx, ax), dy = fsub(by, ay), dz = fsub(bz, az);
+  return fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz));
+}
+
+// a lower bound of the squared distance between two boxes (exact arithmetic
+// up to a few roundings; callers apply the margin)
+__device__ __forceinline__ float box_gap2(const IniBox& a, const IniBox& b) {
+  float s = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float g = fmaxf(0.f, fmaxf(b.lo[d] - a.hi[d], a.lo[d] - b.hi[d]));
+    s += g * g;
+  }
+  return s;
+}
+
+// Sorted insertion of key into best[0..K) (ascending), dropping the largest.
+template <int K>
+__device__ __forceinline__ void topk_insert(unsigned long long (&best)[K], unsigned long long key) {
+#pragma unroll
+  for (int t = K - 1; t > 0; --t) {
+    const unsigned long long prev = best[t - 1];
+    best[t] = prev > key ? prev : (best[t] > key ? key : best[t]);
+  }
+  best[0] = best[0] > key ? key : best[0];
+}
+
+template <int K>
+__global__ void __launch_bounds__(kIniTile) k_ini_knn(const float* __restrict__ pts, uint32_t n,
+                                                      const IniBox* __restrict__ boxes, uint32_t n_tiles, int k,
+                                                      int32_t* __restrict__ knn, int64_t* __restrict__ pairs) {
+  __shared__ float sx[kIniTile], sy[kIniTile], sz[kIniTile];
+  __shared__ uint32_t s_list[kIniMaxTiles];
+  __shared__ uint32_t s_nlist, s_worst;
+  __shared__ uint32_t s_wmax[kIniTile / 32];
+  const uint32_t qt = blockIdx.x;
+  const uint32_t i = qt * kIniTile + threadIdx.x;
+  const bool valid = i < n;
+  const float qx = valid ? pts[3 * i] : 0.f, qy = valid ? pts[3 * i + 1] : 0.f, qz = valid ? pts[3 * i + 2] : 0.f;
+  unsigned long long best[K];
+#pragma unroll
+  for (int t = 0; t < K; ++t) best[t] = ~0ull;
+
+  const uint32_t n_valid = n - qt * kIniTile < static_cast<uint32_t>(kIniTile) ? n - qt * kIniTile : kIniTile;
+  unsigned long long evaluated = 0;   // (query, candidate) distances of this CTA
+  auto visit = [&](uint32_t tile) {
+    const uint32_t base = tile * kIniTile;
+    const uint32_t cnt = n - base < static_cast<uint32_t>(kIniTile) ? n - base : kIniTile;
+    evaluated += static_cast<unsigned long long>(cnt) * n_valid;
+    __syncthreads();   // the previous tile is no longer read
+    if (threadIdx.x < cnt) {
+      sx[threadIdx.x] = pts[3 * (base + threadIdx.x)];
+      sy[threadIdx.x] = pts[3 * (base + threadIdx.x) + 1];
+      sz[threadIdx.x] = pts[3 * (base + threadIdx.x) + 2];
+    }
+    __syncthreads();
+    if (!valid) return;
+    uint32_t worst = static_cast<uint32_t>(best[K - 1] >> 32);
+    for (uint32_t j = 0; j < cnt; ++j) {
+      const uint32_t d = __float_as_uint(dist2(qx, qy, qz, sx[j], sy[j], sz[j]));
+      if (d > worst) continue;
+      const unsigned long long key = (static_cast<unsigned long long>(d) << 32) | (base + j);
+      if (key < best[K - 1]) {
+        topk_insert<K>(best, key);
+        worst = static_cast<uint32_t>(best[K - 1] >> 32);
+      }
+    }
+  };
+
+  // the own tile and its neighbours in index order (a scan's consecutive
+  // points are neighbours in space)
+  for (int w = 0; w < kIniWindow; ++w) {
+    const int off = (w & 1) ? (w + 1) / 2 : -(w / 2);
+    const long long t = static_cast<long long>(qt) + off;
+    if (t < 0 || t >= static_cast<long long>(n_tiles)) continue;   // uniform across the CTA
+    visit(static_cast<uint32_t>(t));
+  }
+  // the CTA's K-th distance (largest over its queries) and the tiles that
+  // can still hold a closer point
+  const uint32_t mine = valid ? static_cast<uint32_t>(best[K - 1] >> 32) : 0u;
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, mine);
+  if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = wmax;
+  if (threadIdx.x == 0) s_nlist = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t m = 0;
+    for (int w = 0; w < kIniTile / 32; ++w) m = m > s_wmax[w] ? m : s_wmax[w];
+    s_worst = m;
+  }
+  __syncthreads();
+  const uint32_t wb = s_worst;
+  const bool bounded = wb < 0x7f800000u;   // finite: every query holds K candidates
+  const float worst = __uint_as_float(wb);
+  const IniBox qb = boxes[qt];
+  for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+    const long long d = static_cast<long long>(t) - static_cast<long long>(qt);
+    if (d >= -(kIniWindow / 2) && d <= kIniWindow / 2) continue;        // visited
+    if (bounded && box_gap2(qb, boxes[t]) * 0.99999f > worst) continue;  // provably too far
+    s_list[atomicAdd(&s_nlist, 1u)] = t;
+  }
+  __syncthreads();
+  const uint32_t nl = s_nlist;
+  for (uint32_t l = 0; l < nl; ++l) visit(s_list[l]);
+  if (pairs && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(pairs), evaluated);
+  if (valid)
+#pragma unroll
+    for (int t = 0; t < K; ++t)
+      if (t < k) knn[static_cast<size_t>(i) * k + t] = static_cast<int32_t>(static_cast<uint32_t>(best[t]));
+}
+
+// One cyclic-Jacobi rotation zeroing A[p][q] of the symmetric 3x3 A and
+// accumulating it into V (Golub & Van Loan, the symmetric Schur
+// decomposition of the 2x2 subproblem): A <- J^T A J, V <- V J.
+__device__ __forceinline__ void jacobi_rotate(float (&A)[3][3], float (&V)[3][3], int p, int q) {
+  const float apq = A[p][q];
+  if (fabsf(apq) < 1e-36f) return;
+  const float theta = (A[q][q] - A[p][p]) / (2.f * apq);
+  float t;
+  if (fabsf(theta) > 1e18f) {
+    t = 0.5f / theta;
+  } else {
+    t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+  }
+  const float c = rsqrtf(t * t + 1.f), s = t * c;
+  float B[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {   // B = A J
+    B[r][p] = c * A[r][p] - s * A[r][q];
+    B[r][q] = s * A[r][p] + c * A[r][q];
+    B[r][3 - p - q] = A[r][3 - p - q];
+  }
+#pragma unroll
+  for (int cidx = 0; cidx < 3; ++cidx) {   // A = J^T B
+    A[p][cidx] = c * B[p][cidx] - s * B[q][cidx];
+    A[q][cidx] = s * B[p][cidx] + c * B[q][cidx];
+    A[3 - p - q][cidx] = B[3 - p - q][cidx];
+  }
+  A[p][q] = 0.f;
+  A[q][p] = 0.f;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float vp = V[r][p], vq = V[r][q];
+    V[r][p] = c * vp - s * vq;
+    V[r][q] = s * vp + c * vq;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ini_frame(const float* __restrict__ pts, uint32_t n,
+                                                   const int32_t* __restrict__ knn, IniParams P,
+                                                   lgs_surfel_params_out out, float* __restrict__ lam,
+                                                   float* __restrict__ conf) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float px = pts[3 * i], py = pts[3 * i + 1], pz = pts[3 * i + 2];
+  const int k = P.k;
+  // neighbour offsets from the point (exact for points within a factor of
+  // two of each other, Sterbenz), their mean, and the centred second moments
+  float mx = 0.f, my = 0.f, mz = 0.f;
+  for (int t = 0; t < k; ++t) {
+    const int j = knn[static_cast<size_t>(i) * k + t];
+    mx += pts[3 * j] - px;
+    my += pts[3 * j + 1] - py;
+    mz += pts[3 * j + 2] - pz;
+  }
+  const float ik = 1.f / static_cast<float>(k);
+  mx *= ik;
+  my *= ik;
+  mz *= ik;
+  float cxx = 0.f, cxy = 0.f, cxz = 0.f, cyy = 0.f, cyz = 0.f, czz = 0.f;
+  for (int t = 0; t < k; ++t) {
+    const int j = knn[static_cast<size_t>(i) * k + t];
+    const float dx = (pts[3 * j] - px) - mx, dy = (pts[3 * j + 1] - py) - my, dz = (pts[3 * j + 2] - pz) - mz;
+    cxx += dx * dx;
+    cxy += dx * dy;
+    cxz += dx * dz;
+    cyy += dy * dy;
+    cyz += dy * dz;
+    czz += dz * dz;
+  }
+  float A[3][3] = {{cxx * ik, cxy * ik, cxz * ik}, {cxy * ik, cyy * ik, cyz * ik}, {cxz * ik, cyz * ik, czz * ik}};
+  float V[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+  for (int sweep = 0; sweep < 6; ++sweep) {
+    jacobi_rotate(A, V, 0, 1);
+    jacobi_rotate(A, V, 0, 2);
+    jacobi_rotate(A, V, 1, 2);
+  }
+  // eigenpairs in descending order
+  float ev[3] = {A[0][0], A[1][1], A[2][2]};
+  int o[3] = {0, 1, 2};
+  if (ev[o[0]] < ev[o[1]]) { const int x = o[0]; o[0] = o[1]; o[1] = x; }
+  if (ev[o[1]] < ev[o[2]]) { const int x = o[1]; o[1] = o[2]; o[2] = x; }
+  if (ev[o[0]] < ev[o[1]]) { const int x = o[0]; o[0] = o[1]; o[1] = x; }
+  const float l0 = fmaxf(ev[o[0]], 0.f), l1 = fmaxf(ev[o[1]], 0.f), l2 = fmaxf(ev[o[2]], 0.f);
+  float3 e0 = make_float3(V[0][o[0]], V[1][o[0]], V[2][o[0]]);
+  float3 nn = make_float3(V[0][o[2]], V[1][o[2]], V[2][o[2]]);
+  // the normal turned toward the sensor (the origin of the sensor frame)
+  if (nn.x * px + nn.y * py + nn.z * pz > 0.f) nn = make_float3(-nn.x, -nn.y, -nn.z);
+  float nl = rsqrtf(nn.x * nn.x + nn.y * nn.y + nn.z * nn.z);
+  nn = make_float3(nn.x * nl, nn.y * nl, nn.z * nl);
+  const float en = e0.x * nn.x + e0.y * nn.y + e0.z * nn.z;
+  e0 = make_float3(e0.x - en * nn.x, e0.y - en * nn.y, e0.z - en * nn.z);
+  nl = rsqrtf(e0.x * e0.x + e0.y * e0.y + e0.z * e0.z);
+  const float3 tu = make_float3(e0.x * nl, e0.y * nl, e0.z * nl);
+  const float3 tv = make_float3(nn.y * tu.z - nn.z * tu.y, nn.z * tu.x - nn.x * tu.z, nn.x * tu.y - nn.y * tu.x);
+  // range-adaptive scale: clip(kappa max(|p|, 1) sigma_tan, s_min, s_max)
+  const float rng = sqrtf(px * px + py * py + pz * pz);
+  const float sg0 = sqrtf(l0), sg1 = sqrtf(l1);
+  const float t1 = sg0 > 0.f ? sg1 / sg0 : 1.f;   // sigma_tan = (1, sigma_1 / sigma_0)
+  const float r = fmaxf(rng, 1.f);
+  const float s0 = fminf(fmaxf(P.kappa * r, P.s_min), P.s_max);
+  const float s1 = fminf(fmaxf(P.kappa * r * t1, P.s_min), P.s_max);
+  // physics-based confidence and opacity
+  const float cosv = fabsf(nn.x * px + nn.y * py + nn.z * pz) / rng;
+  const float ramp = fminf(fmaxf((cosv - P.c0) / (1.f - P.c0 + P.eps), 0.f), 1.f);
+  const float q = rng / P.r0;
+  const float u = expf(-q * q) * ramp;
+  const float alpha = P.alpha_min + (P.alpha_max - P.alpha_min) * u;
+  // world frame: Rw = R [t_u t_v n]; quaternion by the largest of
+  // 1 + tr, 1 + 2 R_ii - tr (Shepperd's rule), w >= 0
+  float W[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    W[a][0] = P.R[3 * a] * tu.x + P.R[3 * a + 1] * tu.y + P.R[3 * a + 2] * tu.z;
+    W[a][1] = P.R[3 * a] * tv.x + P.R[3 * a + 1] * tv.y + P.R[3 * a + 2] * tv.z;
+    W[a][2] = P.R[3 * a] * nn.x + P.R[3 * a + 1] * nn.y + P.R[3 * a + 2] * nn.z;
+  }
+  const float tr = W[0][0] + W[1][1] + W[2][2];
+  const float c0 = 1.f + tr, c1 = 1.f + 2.f * W[0][0] - tr, c2 = 1.f + 2.f * W[1][1] - tr,
+              c3 = 1.f + 2.f * W[2][2] - tr;
+  float qw, qx, qy, qz;
+  if (c0 >= c1 && c0 >= c2 && c0 >= c3) {
+    const float h = 2.f * sqrtf(c0);
+    qw = 0.25f * h; qx = (W[2][1] - W[1][2]) / h; qy = (W[0][2] - W[2][0]) / h; qz = (W[1][0] - W[0][1]) / h;
+  } else if (c1 >= c2 && c1 >= c3) {
+    const float h = 2.f * sqrtf(c1);
+    qw = (W[2][1] - W[1][2]) / h; qx = 0.25f * h; qy = (W[0][1] + W[1][0]) / h; qz = (W[0][2] + W[2][0]) / h;
+  } else if (c2 >= c3) {
+    const float h = 2.f * sqrtf(c2);
+    qw = (W[0][2] - W[2][0]) / h; qx = (W[0][1] + W[1][0]) / h; qy = 0.25f * h; qz = (W[1][2] + W[2][1]) / h;
+  } else {
+    const float h = 2.f * sqrtf(c3);
+    qw = (W[1][0] - W[0][1]) / h; qx = (W[0][2] + W[2][0]) / h; qy = (W[1][2] + W[2][1]) / h; qz = 0.25f * h;
+  }
+  const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz) * (qw < 0.f ? -1.f : 1.f);
+  out.quat[4 * i] = qw * qn;
+  out.quat[4 * i + 1] = qx * qn;
+  out.quat[4 * i + 2] = qy * qn;
+  out.quat[4 * i + 3] = qz * qn;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    out.mean[3 * i + a] = P.R[3 * a] * px + P.R[3 * a + 1] * py + P.R[3 * a + 2] * pz + P.t[a];
+  out.log_scale[2 * i] = logf(s0);
+  out.log_scale[2 * i + 1] = logf(s1);
+  out.opacity_logit[i] = logf(alpha / (1.f - alpha));
+  lam[3 * i] = l0;
+  lam[3 * i + 1] = l1;
+  lam[3 * i + 2] = l2;
+  conf[i] = u;
+}
+
+template <int K>
+void launch_knn(const float* pts, uint32_t n, const IniBox* boxes, uint32_t n_tiles, int k, int32_t* knn,
+                int64_t* pairs, cudaStream_t s) {
+  k_ini_knn<K><<<n_tiles, kIniTile, 0, s>>>(pts, n, boxes, n_tiles, k, knn, pairs);
+}
+
+}  // namespace
+
+size_t init_scratch_bytes(int64_t n) {
+  const int64_t tiles = (n + kIniTile - 1) / kIniTile;
+  return static_cast<size_t>(tiles > 0 ? tiles : 1) * sizeof(IniBox);
+}
+
+int64_t init_max_points() { return static_cast<int64_t>(kIniMaxTiles) * kIniTile; }
+
+cudaError_t launch_keyframe_init(const float* pts, int64_t n64, const float pose[12], const lgs_init_params& p,
+                                 void* scratch, int32_t* knn, const lgs_surfel_params_out& out, float* lam,
+                                 float* conf, int64_t* pairs, cudaStream_t s) {
+  const uint32_t n = static_cast<uint32_t>(n64);
+  if (n == 0) return cudaSuccess;
+  const uint32_t n_tiles = (n + kIniTile - 1) / kIniTile;
+  IniBox* boxes = static_cast<IniBox*>(scratch);
+  k_ini_boxes<<<n_tiles, kIniTile, 0, s>>>(pts, n, boxes);
+  if (p.k <= 8) launch_knn<8>(pts, n, boxes, n_tiles, p.k, knn, pairs, s);
+  else if (p.k <= 16) launch_knn<16>(pts, n, boxes, n_tiles, p.k, knn, pairs, s);
+  else if (p.k <= 24) launch_knn<24>(pts, n, boxes, n_tiles, p.k, knn, pairs, s);
+  else launch_knn<32>(pts, n, boxes, n_tiles, p.k, knn, pairs, s);
+  IniParams P;
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) P.R[3 * a + b] = pose[4 * a + b];
+    P.t[a] = pose[4 * a + 3];
+  }
+  P.kappa = p.kappa;
+  P.s_min = p.s_min;
+  P.s_max = p.s_max;
+  P.r0 = p.r0;
+  P.c0 = p.c0;
+  P.eps = p.eps;
+  P.alpha_min = p.alpha_min;
+  P.alpha_max = p.alpha_max;
+  P.k = p.k;
+  k_ini_frame<<<(n + 255) / 256, 256, 0, s>>>(pts, n, knn, P, out, lam, conf);
+  return cudaGetLastError();
+}
+
+}  // namespace lgs

@@ -609,6 +609,13 @@ cudaError_t launch_manage(const lgs_surfels& M, const float* lam, const float* r
 cudaError_t launch_manage_gather(const int32_t* src, const uint8_t* role, const int64_t* counts, int64_t capacity,
                                  const void* in, void* out, int words, int zero_children, cudaStream_t s);
 
+// keyframe initialisation (lgs_init.cu)
+size_t init_scratch_bytes(int64_t n);
+int64_t init_max_points();
+cudaError_t launch_keyframe_init(const float* pts, int64_t n, const float pose[12], const lgs_init_params& p,
+                                 void* scratch, int32_t* knn, const lgs_surfel_params_out& out, float* lam,
+                                 float* conf, int64_t* pairs, cudaStream_t s);
+
 size_t trackable_scratch_bytes(int64_t n);
 cudaError_t launch_trackable(const lgs_surfels& M, const uint8_t* mask, const int32_t* last_kf, int32_t k_min,
                              float logit_min, float thick, float eps, float w_max, void* scratch, int32_t* index,

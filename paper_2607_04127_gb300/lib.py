@@ -85,7 +85,8 @@ EXPORTS = [
     "lgs_session_set_timing", "lgs_session_kernel_times", "lgs_image_loss_noalloc", "lgs_adam_step_batch",
     "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version", "lgs_trackable_scratch_bytes",
     "lgs_trackable_targets", "lgs_manage_default_params", "lgs_manage_scratch_bytes", "lgs_manage_capacity", "lgs_manage_launches",
-    "lgs_map_manage", "lgs_map_gather",
+    "lgs_map_manage", "lgs_map_gather", "lgs_init_default_params", "lgs_init_scratch_bytes", "lgs_init_max_points",
+    "lgs_keyframe_init",
 ]
 
 
@@ -128,6 +129,10 @@ def load():
         "lgs_manage_launches": ([P], i32),
         "lgs_map_manage": ([P, P, P, P, P, ctypes.c_size_t, P, P, i64, P, P, P, P], S),
         "lgs_map_gather": ([P, P, P, i64, P, P, i32, i32, P], S),
+        "lgs_init_default_params": ([P], None),
+        "lgs_init_scratch_bytes": ([i64], ctypes.c_size_t),
+        "lgs_init_max_points": ([], i64),
+        "lgs_keyframe_init": ([P, i64, P, P, P, ctypes.c_size_t, P, P, P, P, P, P], S),
         "lgs_session_set_tuning": ([P, P], S),
         "lgs_session_set_timing": ([P, i32], S),
         "lgs_session_kernel_times": ([P, P, P], S),
@@ -405,6 +410,30 @@ def lgs_map_manage(surfels, lam_ptr, res_ptr, params, scratch_ptr, scratch_bytes
 def lgs_map_gather(src_ptr, role_ptr, counts_ptr, capacity, in_ptr, out_ptr, words_per_row, zero_children, stream):
     _check(load().lgs_map_gather(P(src_ptr), P(role_ptr), P(counts_ptr), int(capacity), P(in_ptr), P(out_ptr),
                                  int(words_per_row), int(zero_children), P(stream)))
+
+
+class lgs_init_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("kappa", ctypes.c_float), ("s_min", ctypes.c_float),
+                ("s_max", ctypes.c_float), ("r0", ctypes.c_float), ("c0", ctypes.c_float), ("eps", ctypes.c_float),
+                ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float)]
+
+
+def lgs_init_default_params() -> lgs_init_params:
+    p = lgs_init_params()
+    load().lgs_init_default_params(_ref(p))
+    return p
+
+
+def lgs_init_scratch_bytes(n) -> int:
+    return int(load().lgs_init_scratch_bytes(int(n)))
+
+
+def lgs_keyframe_init(points_ptr, n, pose, params, scratch_ptr, scratch_bytes, knn_ptr, out, lam_ptr, u_ptr, stream,
+                      pairs_ptr=0):
+    pose_arr = (ctypes.c_float * 12)(*[float(x) for x in pose])
+    _check(load().lgs_keyframe_init(P(points_ptr), int(n), pose_arr, _ref(params), P(scratch_ptr), scratch_bytes,
+                                    P(knn_ptr), _ref(out), P(lam_ptr), P(u_ptr), P(pairs_ptr) if pairs_ptr else None,
+                                    P(stream)))
 
 
 def surfels_struct(mean, quat, log_scale, logit) -> lgs_surfels:

@@ -630,3 +630,18 @@ def manage_signals(points: np.ndarray, k: int = 20, seed: int = 0, noise: float 
         res[a:a + step] = np.abs(((pts[a:a + step] - mu) * v[:, :, 0]).sum(1))
     res += np.abs(np.random.default_rng(seed).normal(0.0, noise, pts.shape[0]))
     return lam.astype(np.float32), res.astype(np.float32)
+
+
+def keyframe_points(seed: int = 0, H: int = 128, W: int = 1024, elev_deg: float = 45.0, yaw: float = 0.3,
+                    t=(0.0, 0.0, 0.0), drop: float = 0.1):
+    """One simulated scan of the street (range noise 2 cm, ray drops) as the
+    points of a keyframe in the sensor frame, in scan order (row-major over
+    the range image), with its pose.  Returns (points float32 [n, 3], pose
+    float64 [12])."""
+    rng = np.random.default_rng(seed)
+    scene = street_scene(rng, keep_clear=((t[0], t[1]),))
+    fr = lidar_frame(H, W, (16, 16), elev_deg=elev_deg, pose=pose_matrix(yaw, t))
+    _, pw, _, valid = simulate_scan(scene, fr, rng, drop=drop)
+    P = np.asarray(fr.pose, np.float64).reshape(3, 4)
+    ps = (pw.reshape(-1, 3)[valid.reshape(-1)] - P[:, 3]) @ P[:, :3]
+    return ps.astype(np.float32), P.reshape(-1)
