@@ -502,7 +502,7 @@ def run_keyframe(args):
     rows of the same scan."""
     import numpy as np
     import torch
-    from paper_2607_04127_gb300 import build, keyframe, scenes
+    from paper_2607_04127_gb300 import build, keyframe, lib, scenes
     build.build()
     pts, pose = scenes.keyframe_points(11, 128, 1024)
     n = len(pts)
@@ -576,7 +576,7 @@ def run_keyframe(args):
                 cpu_baseline=dict(value=done / cpu_s, unit="points/s", cores=1, kind="oracle",
                                   sample=f"{done} sampled rows of the same scan in {cpu_s:.1f} s (NumPy brute-force "
                                          f"k-NN over all {n} points, FP64 frames)"),
-                gpu_launches=3 * steps, clocks=clk.summary())
+                gpu_launches=int(lib.load().lgs_init_launches()) * steps, clocks=clk.summary())
     print(json.dumps(line), flush=True)
 
 

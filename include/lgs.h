@@ -481,6 +481,8 @@ LGS_API void lgs_init_default_params(lgs_init_params* p);
 LGS_API size_t lgs_init_scratch_bytes(int64_t n);
 /* Points per call at most (2^20). */
 LGS_API int64_t lgs_init_max_points(void);
+/* Kernel launches one lgs_keyframe_init call makes (for launch accounting). */
+LGS_API int32_t lgs_init_launches(void);
 
 /* points [n][3]: device, the scan's points in the sensor frame, finite and
  * not at the origin; pose: host, 12 floats (sensor -> world, R row-major |

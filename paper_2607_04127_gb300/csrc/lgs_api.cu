@@ -788,6 +788,8 @@ size_t lgs_init_scratch_bytes(int64_t n) { return lgs::init_scratch_bytes(n < 0 
 
 int64_t lgs_init_max_points(void) { return lgs::init_max_points(); }
 
+int32_t lgs_init_launches(void) { return lgs::init_launches(); }
+
 lgs_status lgs_keyframe_init(const float* points, int64_t n, const float pose[12], const lgs_init_params* p,
                              void* scratch, size_t scratch_bytes, int32_t* knn, const lgs_surfel_params_out* out,
                              float* lam, float* u, int64_t* pairs, void* stream) {

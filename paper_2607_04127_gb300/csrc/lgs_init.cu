@@ -4,13 +4,16 @@
 // initialisation, the physics-based confidence u of Eq. physconf and the
 // opacity of Eq. alpha_init).
 //
-// Three launches: per-tile bounding boxes of the points (tiles of 256
-// consecutive points); the k nearest neighbours (one CTA per query tile, an
-// exact top-K kept sorted in registers, candidate tiles staged in shared
-// memory; the CTA's own and neighbouring tiles first, then only tiles whose
-// box can still hold a point closer than the CTA's current K-th distance);
-// the frame of each point (covariance of the neighbourhood, cyclic Jacobi
-// eigendecomposition, scales, confidence, opacity, orientation).
+// Launches: the points go into spatial order first (a counting sort by a
+// 21-bit Morton code of a uniform grid over the scan's extent: 7 bits per
+// axis), so that a tile of 256 consecutive points is compact; per-tile
+// bounding boxes; the k nearest neighbours (one CTA per query tile, an exact
+// top-K kept sorted in registers, candidate tiles staged in shared memory;
+// the CTA's own and adjacent tiles first, then only tiles whose box can still
+// hold a point closer than the CTA's current K-th distance); the frame of
+// each point (covariance of the neighbourhood, cyclic Jacobi
+// eigendecomposition, scales, confidence, opacity, orientation).  Keys carry
+// the original index, so the order of the sort never shows in a result.
 //
 // The neighbour sets are integer outcomes: the squared distance that decides
 // them is binary32 ((dx dx + dy dy) + dz dz), each operation correctly
@@ -28,8 +31,11 @@ namespace lgs {
 namespace {
 
 constexpr int kIniTile = 256;        // points per tile = queries per CTA
-constexpr int kIniWindow = 17;       // tiles visited before pruning: own, +-1, ..., +-8
+constexpr int kIniWindow = 3;        // tiles visited before pruning: own, +-1
 constexpr int kIniMaxTiles = 4096;   // n <= 2^20
+constexpr int kIniCellBits = 7;      // Morton grid: 2^7 cells per axis
+constexpr uint32_t kIniCells = 1u << (3 * kIniCellBits);
+constexpr int kIniSorted = 1024;     // candidate lists up to this long are visited nearest first
 
 struct IniBox {
   float lo[3], hi[3];
@@ -71,6 +77,79 @@ __global__ void __launch_bounds__(kIniTile) k_ini_boxes(const float* __restrict_
   }
 }
 
+// The scan's extent from the tile boxes (one CTA) and the grid's cell size.
+__global__ void __launch_bounds__(256) k_ini_extent(const IniBox* __restrict__ boxes, uint32_t n_tiles,
+                                                    float* __restrict__ ext) {
+  __shared__ float s_v[6][8];
+  float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x)
+    for (int a = 0; a < 3; ++a) {
+      v[a] = fminf(v[a], boxes[t].lo[a]);
+      v[3 + a] = fmaxf(v[3 + a], boxes[t].hi[a]);
+    }
+  for (int a = 0; a < 6; ++a)
+    for (int o = 16; o; o >>= 1) {
+      const float w = __shfl_xor_sync(0xffffffffu, v[a], o);
+      v[a] = a < 3 ? fminf(v[a], w) : fmaxf(v[a], w);
+    }
+  if ((threadIdx.x & 31) == 0)
+    for (int a = 0; a < 6; ++a) s_v[a][threadIdx.x >> 5] = v[a];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float r = s_v[threadIdx.x][0];
+    for (int w = 1; w < 8; ++w) r = threadIdx.x < 3 ? fminf(r, s_v[threadIdx.x][w]) : fmaxf(r, s_v[threadIdx.x][w]);
+    ext[threadIdx.x] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float span = fmaxf(fmaxf(ext[3] - ext[0], ext[4] - ext[1]), ext[5] - ext[2]);
+    ext[6] = fmaxf(span, 1e-20f) * (1.0001f / static_cast<float>(1 << kIniCellBits));   // cell edge
+  }
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t x) {   // bits b -> 3b
+  uint32_t r = 0;
+#pragma unroll
+  for (int b = 0; b < kIniCellBits; ++b) r |= ((x >> b) & 1u) << (3 * b);
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_ini_zero(uint32_t* __restrict__ a, uint32_t len) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) a[i] = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_ini_cells(const float* __restrict__ pts, uint32_t n,
+                                                   const float* __restrict__ ext, uint32_t* __restrict__ cell,
+                                                   uint32_t* __restrict__ cnt) {
+  const float h = ext[6];
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float q = floorf((pts[3 * i + a] - ext[a]) / h);
+    c[a] = static_cast<uint32_t>(fminf(fmaxf(q, 0.f), static_cast<float>((1 << kIniCellBits) - 1)));
+  }
+  const uint32_t code = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+  cell[i] = code;
+  atomicAdd(&cnt[code], 1u);
+}
+
+// points into cell order (order within a cell arbitrary), with their index
+__global__ void __launch_bounds__(256) k_ini_scatter(const float* __restrict__ pts, uint32_t n,
+                                                     const uint32_t* __restrict__ cell, const uint32_t* __restrict__ off,
+                                                     uint32_t* __restrict__ cnt, float* __restrict__ sp,
+                                                     uint32_t* __restrict__ orig) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t c = cell[i];
+  const uint32_t pos = off[c] + atomicSub(&cnt[c], 1u) - 1u;
+  sp[3 * pos] = pts[3 * i];
+  sp[3 * pos + 1] = pts[3 * i + 1];
+  sp[3 * pos + 2] = pts[3 * i + 2];
+  orig[pos] = i;
+}
+
 // binary32 squared distance in the specified order (no contraction)
 __device__ __forceinline__ float dist2(float ax, float ay, float az, float bx, float by, float bz) {
   const float dx = fsub(bx, ax), dy = fsub(by, ay), dz = fsub(bz, az);
@@ -101,11 +180,16 @@ __device__ __forceinline__ void topk_insert(unsigned long long (&best)[K], unsig
 }
 
 template <int K>
-__global__ void __launch_bounds__(kIniTile) k_ini_knn(const float* __restrict__ pts, uint32_t n,
+__global__ void __launch_bounds__(kIniTile) k_ini_knn(const float* __restrict__ pts,
+                                                      const uint32_t* __restrict__ orig, uint32_t n,
                                                       const IniBox* __restrict__ boxes, uint32_t n_tiles, int k,
                                                       int32_t* __restrict__ knn, int64_t* __restrict__ pairs) {
   __shared__ float sx[kIniTile], sy[kIniTile], sz[kIniTile];
+  __shared__ uint32_t s_id[kIniTile];
   __shared__ uint32_t s_list[kIniMaxTiles];
+  __shared__ float s_bd[kIniSorted];          // box distances of the first kIniSorted listed tiles
+  __shared__ uint32_t s_st[kIniSorted];       // the listed tiles by ascending (box distance, tile)
+  __shared__ float s_sbd[kIniSorted];
   __shared__ uint32_t s_nlist, s_worst;
   __shared__ uint32_t s_wmax[kIniTile / 32];
   const uint32_t qt = blockIdx.x;
@@ -127,6 +211,7 @@ __global__ void __launch_bounds__(kIniTile) k_ini_knn(const float* __restrict__ 
       sx[threadIdx.x] = pts[3 * (base + threadIdx.x)];
       sy[threadIdx.x] = pts[3 * (base + threadIdx.x) + 1];
       sz[threadIdx.x] = pts[3 * (base + threadIdx.x) + 2];
+      s_id[threadIdx.x] = orig[base + threadIdx.x];
     }
     __syncthreads();
     if (!valid) return;
@@ -134,7 +219,7 @@ __global__ void __launch_bounds__(kIniTile) k_ini_knn(const float* __restrict__ 
     for (uint32_t j = 0; j < cnt; ++j) {
       const uint32_t d = __float_as_uint(dist2(qx, qy, qz, sx[j], sy[j], sz[j]));
       if (d > worst) continue;
-      const unsigned long long key = (static_cast<unsigned long long>(d) << 32) | (base + j);
+      const unsigned long long key = (static_cast<unsigned long long>(d) << 32) | s_id[j];
       if (key < best[K - 1]) {
         topk_insert<K>(best, key);
         worst = static_cast<uint32_t>(best[K - 1] >> 32);
@@ -150,37 +235,73 @@ __global__ void __launch_bounds__(kIniTile) k_ini_knn(const float* __restrict__ 
     if (t < 0 || t >= static_cast<long long>(n_tiles)) continue;   // uniform across the CTA
     visit(static_cast<uint32_t>(t));
   }
-  // the CTA's K-th distance (largest over its queries) and the tiles that
-  // can still hold a closer point
-  const uint32_t mine = valid ? static_cast<uint32_t>(best[K - 1] >> 32) : 0u;
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, mine);
-  if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = wmax;
+  // the CTA's K-th distance: the largest over its queries (bits of a
+  // non-negative float; 0xffffffff while some query holds fewer than K)
+  auto cta_worst = [&]() -> uint32_t {
+    const uint32_t mine = valid ? static_cast<uint32_t>(best[K - 1] >> 32) : 0u;
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, mine);
+    __syncthreads();   // s_wmax / s_worst of the previous call are read
+    if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = wmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t m = 0;
+      for (int w = 0; w < kIniTile / 32; ++w) m = m > s_wmax[w] ? m : s_wmax[w];
+      s_worst = m;
+    }
+    __syncthreads();
+    return s_worst;
+  };
+  // tiles whose box can still hold a point closer than the CTA's K-th
+  // distance (a box provably farther cannot; the margin covers rounding)
+  auto too_far = [](float bd, uint32_t wb) {
+    return wb < 0x7f800000u && bd * 0.99999f > __uint_as_float(wb);
+  };
+  uint32_t wb = cta_worst();
   if (threadIdx.x == 0) s_nlist = 0;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t m = 0;
-    for (int w = 0; w < kIniTile / 32; ++w) m = m > s_wmax[w] ? m : s_wmax[w];
-    s_worst = m;
-  }
-  __syncthreads();
-  const uint32_t wb = s_worst;
-  const bool bounded = wb < 0x7f800000u;   // finite: every query holds K candidates
-  const float worst = __uint_as_float(wb);
   const IniBox qb = boxes[qt];
   for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
     const long long d = static_cast<long long>(t) - static_cast<long long>(qt);
-    if (d >= -(kIniWindow / 2) && d <= kIniWindow / 2) continue;        // visited
-    if (bounded && box_gap2(qb, boxes[t]) * 0.99999f > worst) continue;  // provably too far
-    s_list[atomicAdd(&s_nlist, 1u)] = t;
+    if (d >= -(kIniWindow / 2) && d <= kIniWindow / 2) continue;   // visited
+    const float bd = box_gap2(qb, boxes[t]);
+    if (too_far(bd, wb)) continue;
+    const uint32_t at = atomicAdd(&s_nlist, 1u);
+    s_list[at] = t;
+    if (at < static_cast<uint32_t>(kIniSorted)) s_bd[at] = bd;
   }
   __syncthreads();
   const uint32_t nl = s_nlist;
-  for (uint32_t l = 0; l < nl; ++l) visit(s_list[l]);
+  if (nl <= static_cast<uint32_t>(kIniSorted)) {
+    // nearest first (rank of each entry by (box distance, tile)); stop at
+    // the first box the shrinking K-th distance rules out: every later one
+    // is at least as far
+    for (uint32_t e = threadIdx.x; e < nl; e += blockDim.x) {
+      const float bd = s_bd[e];
+      const uint32_t te = s_list[e];
+      uint32_t rank = 0;
+      for (uint32_t f = 0; f < nl; ++f) {
+        const float bf = s_bd[f];
+        rank += (bf < bd || (bf == bd && s_list[f] < te)) ? 1u : 0u;
+      }
+      s_st[rank] = te;
+      s_sbd[rank] = bd;
+    }
+    __syncthreads();
+    for (uint32_t l = 0; l < nl; ++l) {
+      if (too_far(s_sbd[l], wb)) break;   // uniform: wb is the CTA's
+      visit(s_st[l]);
+      wb = cta_worst();
+    }
+  } else {
+    for (uint32_t l = 0; l < nl; ++l) visit(s_list[l]);
+  }
   if (pairs && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(pairs), evaluated);
-  if (valid)
+  if (valid) {
+    const size_t row = static_cast<size_t>(orig[i]) * k;
 #pragma unroll
     for (int t = 0; t < K; ++t)
-      if (t < k) knn[static_cast<size_t>(i) * k + t] = static_cast<int32_t>(static_cast<uint32_t>(best[t]));
+      if (t < k) knn[row + t] = static_cast<int32_t>(static_cast<uint32_t>(best[t]));
+  }
 }
 
 // One cyclic-Jacobi rotation zeroing A[p][q] of the symmetric 3x3 A and
@@ -334,19 +455,45 @@ __global__ void __launch_bounds__(256) k_ini_frame(const float* __restrict__ pts
 }
 
 template <int K>
-void launch_knn(const float* pts, uint32_t n, const IniBox* boxes, uint32_t n_tiles, int k, int32_t* knn,
-                int64_t* pairs, cudaStream_t s) {
-  k_ini_knn<K><<<n_tiles, kIniTile, 0, s>>>(pts, n, boxes, n_tiles, k, knn, pairs);
+void launch_knn(const float* sp, const uint32_t* orig, uint32_t n, const IniBox* boxes, uint32_t n_tiles, int k,
+                int32_t* knn, int64_t* pairs, cudaStream_t s) {
+  k_ini_knn<K><<<n_tiles, kIniTile, 0, s>>>(sp, orig, n, boxes, n_tiles, k, knn, pairs);
+}
+
+// Scratch: tile boxes, the extent, cells and their counts / offsets, scan
+// partials, the points in cell order and their original indices.
+struct IniLayout {
+  size_t boxes, ext, cell, cnt, off, part, sp, orig, total;
+};
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+IniLayout ini_layout(int64_t n) {
+  IniLayout L{};
+  const size_t N = static_cast<size_t>(n > 0 ? n : 1);
+  const size_t tiles = (N + kIniTile - 1) / kIniTile;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
+  L.boxes = take(tiles * sizeof(IniBox));
+  L.ext = take(8 * sizeof(float));
+  L.cell = take(4 * N);
+  L.cnt = take(4 * static_cast<size_t>(kIniCells));
+  L.off = take(4 * (static_cast<size_t>(kIniCells) + 1));
+  L.part = take(scan_partials_bytes(kIniCells));
+  L.sp = take(12 * N);
+  L.orig = take(4 * N);
+  L.total = o;
+  return L;
 }
 
 }  // namespace
 
-size_t init_scratch_bytes(int64_t n) {
-  const int64_t tiles = (n + kIniTile - 1) / kIniTile;
-  return static_cast<size_t>(tiles > 0 ? tiles : 1) * sizeof(IniBox);
-}
+size_t init_scratch_bytes(int64_t n) { return ini_layout(n).total; }
 
 int64_t init_max_points() { return static_cast<int64_t>(kIniMaxTiles) * kIniTile; }
+
+// zero, boxes, extent, cells, scan (3), scatter, boxes, k-NN, frame
+int init_launches() { return 11; }
 
 cudaError_t launch_keyframe_init(const float* pts, int64_t n64, const float pose[12], const lgs_init_params& p,
                                  void* scratch, int32_t* knn, const lgs_surfel_params_out& out, float* lam,
@@ -354,12 +501,28 @@ cudaError_t launch_keyframe_init(const float* pts, int64_t n64, const float pose
   const uint32_t n = static_cast<uint32_t>(n64);
   if (n == 0) return cudaSuccess;
   const uint32_t n_tiles = (n + kIniTile - 1) / kIniTile;
-  IniBox* boxes = static_cast<IniBox*>(scratch);
+  const IniLayout L = ini_layout(n);
+  char* b = static_cast<char*>(scratch);
+  IniBox* boxes = reinterpret_cast<IniBox*>(b + L.boxes);
+  float* ext = reinterpret_cast<float*>(b + L.ext);
+  uint32_t* cell = reinterpret_cast<uint32_t*>(b + L.cell);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
+  uint32_t* off = reinterpret_cast<uint32_t*>(b + L.off);
+  uint32_t* part = reinterpret_cast<uint32_t*>(b + L.part);
+  float* sp = reinterpret_cast<float*>(b + L.sp);
+  uint32_t* orig = reinterpret_cast<uint32_t*>(b + L.orig);
+  const uint32_t g = (n + 255) / 256;
+  k_ini_zero<<<512, 256, 0, s>>>(cnt, kIniCells);
   k_ini_boxes<<<n_tiles, kIniTile, 0, s>>>(pts, n, boxes);
-  if (p.k <= 8) launch_knn<8>(pts, n, boxes, n_tiles, p.k, knn, pairs, s);
-  else if (p.k <= 16) launch_knn<16>(pts, n, boxes, n_tiles, p.k, knn, pairs, s);
-  else if (p.k <= 24) launch_knn<24>(pts, n, boxes, n_tiles, p.k, knn, pairs, s);
-  else launch_knn<32>(pts, n, boxes, n_tiles, p.k, knn, pairs, s);
+  k_ini_extent<<<1, 256, 0, s>>>(boxes, n_tiles, ext);
+  k_ini_cells<<<g, 256, 0, s>>>(pts, n, ext, cell, cnt);
+  exclusive_scan_u32(cnt, off, kIniCells, part, s);
+  k_ini_scatter<<<g, 256, 0, s>>>(pts, n, cell, off, cnt, sp, orig);
+  k_ini_boxes<<<n_tiles, kIniTile, 0, s>>>(sp, n, boxes);
+  if (p.k <= 8) launch_knn<8>(sp, orig, n, boxes, n_tiles, p.k, knn, pairs, s);
+  else if (p.k <= 16) launch_knn<16>(sp, orig, n, boxes, n_tiles, p.k, knn, pairs, s);
+  else if (p.k <= 24) launch_knn<24>(sp, orig, n, boxes, n_tiles, p.k, knn, pairs, s);
+  else launch_knn<32>(sp, orig, n, boxes, n_tiles, p.k, knn, pairs, s);
   IniParams P;
   for (int a = 0; a < 3; ++a) {
     for (int b = 0; b < 3; ++b) P.R[3 * a + b] = pose[4 * a + b];

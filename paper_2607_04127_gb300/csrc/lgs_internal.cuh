@@ -609,9 +609,15 @@ cudaError_t launch_manage(const lgs_surfels& M, const float* lam, const float* r
 cudaError_t launch_manage_gather(const int32_t* src, const uint8_t* role, const int64_t* counts, int64_t capacity,
                                  const void* in, void* out, int words, int zero_children, cudaStream_t s);
 
+// exclusive scan of uint32 (out[len] = total; in may equal out; part holds
+// scan_partials_bytes(len) bytes), defined in lgs_manage.cu
+size_t scan_partials_bytes(uint64_t len);
+void exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t len, uint32_t* part, cudaStream_t s);
+
 // keyframe initialisation (lgs_init.cu)
 size_t init_scratch_bytes(int64_t n);
 int64_t init_max_points();
+int init_launches();
 cudaError_t launch_keyframe_init(const float* pts, int64_t n, const float pose[12], const lgs_init_params& p,
                                  void* scratch, int32_t* knn, const lgs_surfel_params_out& out, float* lam,
                                  float* conf, int64_t* pairs, cudaStream_t s);

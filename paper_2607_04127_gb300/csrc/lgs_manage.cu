@@ -963,6 +963,12 @@ int sm_count() {
 
 size_t manage_scratch_bytes(int64_t n) { return mg_layout(n).total; }
 
+size_t scan_partials_bytes(uint64_t len) { return 4 * (static_cast<size_t>(scan_blocks(len)) + 1); }
+
+void exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t len, uint32_t* part, cudaStream_t s) {
+  launch_scan(in, out, len, part, s);
+}
+
 int manage_kernel_count(int n_passes) {
   // residual keys, 3 digits, score; per pass: 3 digits, insert, measure,
   // scan (3), scatter, decide, 6 digits, apply; split: 3 digits, split keys,

@@ -85,7 +85,7 @@ EXPORTS = [
     "lgs_session_set_timing", "lgs_session_kernel_times", "lgs_image_loss_noalloc", "lgs_adam_step_batch",
     "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version", "lgs_trackable_scratch_bytes",
     "lgs_trackable_targets", "lgs_manage_default_params", "lgs_manage_scratch_bytes", "lgs_manage_capacity", "lgs_manage_launches",
-    "lgs_map_manage", "lgs_map_gather", "lgs_init_default_params", "lgs_init_scratch_bytes", "lgs_init_max_points",
+    "lgs_map_manage", "lgs_map_gather", "lgs_init_default_params", "lgs_init_scratch_bytes", "lgs_init_max_points", "lgs_init_launches",
     "lgs_keyframe_init",
 ]
 
@@ -132,6 +132,7 @@ def load():
         "lgs_init_default_params": ([P], None),
         "lgs_init_scratch_bytes": ([i64], ctypes.c_size_t),
         "lgs_init_max_points": ([], i64),
+        "lgs_init_launches": ([], i32),
         "lgs_keyframe_init": ([P, i64, P, P, P, ctypes.c_size_t, P, P, P, P, P, P], S),
         "lgs_session_set_tuning": ([P, P], S),
         "lgs_session_set_timing": ([P, i32], S),
