@@ -10,8 +10,9 @@
 // bounding boxes; the k nearest neighbours (one CTA per query tile, an exact
 // top-K kept sorted in registers, candidate tiles staged in shared memory;
 // the CTA's own and adjacent tiles first, then only tiles whose box can still
-// hold a point closer than the CTA's current K-th distance); the frame of
-// each point (covariance of the neighbourhood, cyclic Jacobi
+// hold a point closer than the CTA's current K-th distance, nearest first;
+// each warp skips the tiles provably beyond its own K-th distances); the
+// frame of each point (covariance of the neighbourhood, cyclic Jacobi
 // eigendecomposition, scales, confidence, opacity, orientation).  Keys carry
 // the original index, so the order of the sort never shows in a result.
 //
@@ -200,12 +201,27 @@ __global__ void __launch_bounds__(kIniTile) k_ini_knn(const float* __restrict__ 
 #pragma unroll
   for (int t = 0; t < K; ++t) best[t] = ~0ull;
 
-  const uint32_t n_valid = n - qt * kIniTile < static_cast<uint32_t>(kIniTile) ? n - qt * kIniTile : kIniTile;
-  unsigned long long evaluated = 0;   // (query, candidate) distances of this CTA
+  unsigned long long evaluated = 0;   // (query, candidate) distances of this warp's lane 0
+  // the warp's own query box: a tile whose box is provably beyond every one
+  // of the warp's K-th distances is skipped by the warp alone
+  IniBox wbox;
+  {
+    const float v[3] = {qx, qy, qz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float lo = valid ? v[a] : INFINITY, hi = valid ? v[a] : -INFINITY;
+      for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      wbox.lo[a] = lo;
+      wbox.hi[a] = hi;
+    }
+  }
+  const uint32_t w_valid = __popc(__ballot_sync(0xffffffffu, valid));
   auto visit = [&](uint32_t tile) {
     const uint32_t base = tile * kIniTile;
     const uint32_t cnt = n - base < static_cast<uint32_t>(kIniTile) ? n - base : kIniTile;
-    evaluated += static_cast<unsigned long long>(cnt) * n_valid;
     __syncthreads();   // the previous tile is no longer read
     if (threadIdx.x < cnt) {
       sx[threadIdx.x] = pts[3 * (base + threadIdx.x)];
@@ -214,6 +230,10 @@ __global__ void __launch_bounds__(kIniTile) k_ini_knn(const float* __restrict__ 
       s_id[threadIdx.x] = orig[base + threadIdx.x];
     }
     __syncthreads();
+    if (w_valid == 0) return;   // uniform across the warp
+    const uint32_t wworst = __reduce_max_sync(0xffffffffu, valid ? static_cast<uint32_t>(best[K - 1] >> 32) : 0u);
+    if (wworst < 0x7f800000u && box_gap2(wbox, boxes[tile]) * 0.99999f > __uint_as_float(wworst)) return;
+    evaluated += static_cast<unsigned long long>(cnt) * w_valid;
     if (!valid) return;
     uint32_t worst = static_cast<uint32_t>(best[K - 1] >> 32);
     for (uint32_t j = 0; j < cnt; ++j) {
@@ -295,7 +315,8 @@ __global__ void __launch_bounds__(kIniTile) k_ini_knn(const float* __restrict__ 
   } else {
     for (uint32_t l = 0; l < nl; ++l) visit(s_list[l]);
   }
-  if (pairs && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(pairs), evaluated);
+  if (pairs && (threadIdx.x & 31) == 0 && evaluated)
+    atomicAdd(reinterpret_cast<unsigned long long*>(pairs), evaluated);
   if (valid) {
     const size_t row = static_cast<size_t>(orig[i]) * k;
 #pragma unroll
