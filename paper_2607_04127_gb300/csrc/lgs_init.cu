@@ -542,6 +542,7 @@ cudaError_t launch_keyframe_init(const float* pts, int64_t n64, const float pose
   k_ini_boxes<<<n_tiles, kIniTile, 0, s>>>(sp, n, boxes);
   if (p.k <= 8) launch_knn<8>(sp, orig, n, boxes, n_tiles, p.k, knn, pairs, s);
   else if (p.k <= 16) launch_knn<16>(sp, orig, n, boxes, n_tiles, p.k, knn, pairs, s);
+  else if (p.k <= 20) launch_knn<20>(sp, orig, n, boxes, n_tiles, p.k, knn, pairs, s);
   else if (p.k <= 24) launch_knn<24>(sp, orig, n, boxes, n_tiles, p.k, knn, pairs, s);
   else launch_knn<32>(sp, orig, n, boxes, n_tiles, p.k, knn, pairs, s);
   IniParams P;
