@@ -10,19 +10,25 @@
 // function of the inputs, whatever the launch shape or the order of atomics.
 //
 // Quantiles (the lower order statistic sorted[floor(q (n - 1))]) and caps (the
-// first k of an order) are exact: an 8-bit radix select over 64-bit keys
-// finds the k-th smallest key, one histogram launch and one one-CTA pick per
-// digit.  Groups of a cover-and-prune pass live in an open-addressing hash
-// table keyed by the biased 2D voxel; the representative (largest logit,
-// then lowest index) is an atomicMax over a packed key; members scatter their
-// squared cover radii into per-group buckets, and each member decides alone
-// whether it is inside its group's cover region by counting its bucket's
-// strictly smaller radii (the decision equals "radius <= the k-th smallest").
+// first k of an order) are exact: a radix select over 64-bit keys in 11-bit
+// digits finds the k-th smallest key, one kernel per digit whose last CTA to
+// finish picks the bin; from the second digit on, the keys still matching
+// the prefix go to a compaction buffer that the next digit reads instead of
+// the full array.  Groups of a cover-and-prune pass live in an
+// open-addressing hash table keyed by the biased 2D voxel; the representative
+// (largest logit, then lowest index) is an atomicMax over a packed key;
+// members scatter (squared cover radius, index) pairs into per-group
+// buckets.  A member is covered when its radius is at most the group's k-th
+// smallest: small groups decide one warp per group by counting strictly
+// smaller radii staged in shared memory, large groups find the k-th smallest
+// by a one-CTA radix select over the bucket.
 //
 // Launches (one stream, no host synchronisation, counts written on the
-// device): init; residual quantile; score and opacity prune; per pass: the
-// survivors' score quantile, table clear, insert, measure, bucket scan,
-// scatter, decide, cap select, apply; then the split quantile, split keys,
+// device; 71 with three passes): residual keys (and the select's reset),
+// residual quantile; score, opacity prune, the survivors' keys and the table
+// clear; per pass: the survivors' score quantile, insert, measure, bucket
+// scan, scatter, decide, cap select, apply (which also writes the next
+// quantile's keys and clears the table); then the split quantile, split keys,
 // split cap select, weights, output scan, write.
 #include <cuda_runtime.h>
 
