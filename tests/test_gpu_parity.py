@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Bars (spec tolerances): sort order, tile lists and tile ranges
+Bars (the required tolerances): sort order, tile lists and tile ranges
 bit-exact; expected depth and opacity within 1e-5 relative, normals within
 1e-4; gradients within 1e-3 relative.  "Relative" has a floor,
 tol * max(|y|, 1e-3 max|y|), and every bar adds the uncertainty the oracle

@@ -1,6 +1,6 @@
 """Pins of the FP64 CPU oracle against what the paper's definitions and plain
 mathematics fix (closed forms, invariants, brute force, finite differences),
-so that a mistake in the oracle fails here before it is used to judge the
+so that a mistake in the oracle fails here before it is used to check the
 CUDA path.  CPU only.
 
 Definitions pinned (paper Sec. 3.1 map representation, Sec. 3.4 map
