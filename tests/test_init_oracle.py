@@ -169,3 +169,20 @@ def test_confidence_uses_the_range_itself(oi):
     r = np.linalg.norm(pts.astype(np.float64), axis=1)
     # the patch lies in the plane x = 0.5 (normal -x), so c = 0.5 / |p|
     assert np.allclose(out["u"], np.exp(-r * r) * (0.5 / r - 0.1) / (0.9 + 1e-6), rtol=1e-7)
+
+
+def test_exact_scaling_invariance(oi):
+    """Doubling every point is exact in binary32: squared distances scale by
+    exactly 4 (same neighbour lists, same order), the covariance by exactly
+    4, so the eigenvalues scale by 4 and the frames do not change."""
+    rng = np.random.default_rng(13)
+    pts = (rng.normal(size=(600, 3)) * [4.0, 2.0, 0.3] + [15.0, -3.0, 1.0]).astype(F)
+    a = oi.initialise(pts, np.eye(3, 4).ravel(), oi.Params(k=12))
+    b = oi.initialise(pts * F(2), np.eye(3, 4).ravel(), oi.Params(k=12))
+    assert np.array_equal(a["knn"], b["knn"])
+    ia, da = oi.knn(pts, 12)
+    ib, db = oi.knn(pts * F(2), 12)
+    assert np.array_equal(ia, ib) and np.array_equal(db, da * F(4))
+    assert np.allclose(b["lam"], 4 * a["lam"], rtol=1e-12, atol=1e-15)
+    gap = (a["lam"][:, 1] - a["lam"][:, 2]) > 1e-6 * a["lam"][:, 0]
+    assert np.allclose(b["normal_s"][gap], a["normal_s"][gap], atol=1e-9)
