@@ -79,7 +79,9 @@ class MapManager:
         for a in arrays:
             if not (a.is_cuda and a.is_contiguous() and a.element_size() == 4):
                 raise ValueError("gathered arrays must be contiguous 32-bit CUDA tensors")
-            words = a[0].numel() if a.dim() > 1 else 1
+            words = 1
+            for d in a.shape[1:]:
+                words *= int(d)
             o = torch.empty((max(out["capacity"], 1),) + tuple(a.shape[1:]), dtype=a.dtype, device=a.device)
             lib.lgs_map_gather(out["src"].data_ptr(), out["role"].data_ptr(), out["counts"].data_ptr(),
                                out["capacity"], a.data_ptr(), o.data_ptr(), words, int(zero_children), s)
