@@ -288,6 +288,18 @@ def test_manage_equals_brute_force(mg, oracle, seed, n):
     assert out["counts"][2:5].sum() > 0 and out["counts"][5] > 0
 
 
+@pytest.mark.parametrize("kw", [
+    dict(voxel=0.3, q_plane=0.9, q_cover=0.5, slab=0.5, prune_cap=1.0, q_split=0.5, split_cap=1.0),   # no caps
+    dict(voxel=2.5, q_plane=1.0, q_cover=1.0, slab=10.0, prune_cap=0.5, q_split=0.95, split_cap=0.02),
+    dict(voxel=1.0, n_passes=2, q_plane=0.4, q_cover=0.3, slab=0.02, prune_cap=0.0, q_split=0.0, split_cap=0.05),
+])
+def test_manage_equals_brute_force_other_parameters(mg, oracle, kw):
+    mean, quat, ls, logit, lam, res = _clustered(5, 120)
+    P = mg.Params(**kw)
+    out = mg.manage(mean, quat, ls, logit, lam, res, P)
+    assert out["src"].tolist() == _brute(mean, quat, ls, logit, lam, res, P, mg, oracle)
+
+
 # --- M8 ------------------------------------------------------------------------
 def test_manage_invariants(mg):
     mean, quat, ls, logit, lam, res = _clustered(11, 3000)
