@@ -7,8 +7,13 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
  * baseline leg of the benchmark may load this library.  It shares no code,
- * header, table or constant generator with the CUDA library; it is built by
- * gcc from this one file.
+ * header, table or constant generator with the CUDA library; gcc builds it
+ * from this file and lgs_fp32_allowance.c.
+ *
+ * This file is the method and nothing else.  What a binary32 evaluation of
+ * the same inputs may differ by (the allowance the parity tests add to their
+ * bars) lives in lgs_fp32_allowance.c, which re-walks the evaluations made
+ * here; the method never reads it.
  *
  * Two precisions, on purpose:
  *  (i)  Binning (which surfels are listed for which angular tile) and the
@@ -23,7 +28,7 @@
  *
  * Readings of points the paper leaves open (pixel grid, pose convention,
  * cut-offs, clamps, termination rule, depth order) are listed in the design
- * notes; every constant below carries its reading.
+ * notes; every constant carries its reading (lgs_oracle_impl.h).
  *
  * Parity pins (tests, not this file): single surfel facing the ray (closed
  * form), coaxial stacks (transmittance = product of (1-a)), tiled == brute
@@ -39,21 +44,7 @@
 #include <omp.h>
 #endif
 
-/* ------------------------------------------------------------------------ */
-/* Constants (the oracle's own copy)                                         */
-/* ------------------------------------------------------------------------ */
-#define T_NEAR   0.2          /* ray parameter must exceed this (m)           */
-#define Q_CUT    9.0          /* Gaussian support: u^2+v^2 <= 9 (3 sigma)      */
-#define A_MIN    (1.0 / 255.0)/* contributions below this opacity are skipped  */
-#define A_MAX    0.99         /* per-surfel opacity clamp                      */
-#define T_STOP   1e-4         /* stop before T would drop below this           */
-#define DEN_EPS  1e-6         /* grazing rays |n.d| < DEN_EPS are skipped       */
-#define EPS_A    1e-6         /* D = S_t / (A + EPS_A)                         */
-#define EPS_N    1e-6         /* N = S_n / sqrt(|S_n|^2 + EPS_N^2)             */
-#define EPS_LOG  1e-6         /* L_alpha = -mean log(A + EPS_LOG)              */
-#define FLAG_REL 1e-3         /* band around a threshold that flags a pixel    */
-#define DEN_FLAG 1e-5         /* |n.d| below this flags a pixel                 */
-#define EPS32    5.9604644775390625e-08  /* 2^-24, unit roundoff of binary32  */
+#include "lgs_oracle_impl.h"
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -311,19 +302,6 @@ int64_t lgso_bin_frame(const float* mean, const float* log_scale, int64_t n,
 /* ------------------------------------------------------------------------ */
 /* Part II: FP64 forward                                                     */
 /* ------------------------------------------------------------------------ */
-typedef struct {
-    double mu[3], tu[3], tv[3], n[3];   /* sensor frame */
-    double su, sv, alpha;
-    double qh[4], qnorm;                /* unit quaternion (w,x,y,z), |q| */
-} surf64;
-
-typedef struct {
-    int H, W, th, tw, ntr, ntc;
-    double emin, emax, R[9], o[3];
-} frame64;
-
-static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
-
 /* Rotation matrix of a unit quaternion (w,x,y,z), row-major; its columns are
  * the tangent axes t_u = R e0, t_v = R e1 and the normal n = R e2. */
 static void quat_to_rot(const double* q, double* R)
@@ -334,7 +312,7 @@ static void quat_to_rot(const double* q, double* R)
     R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
 }
 
-static void make_frame(frame64* F, int H, int W, int th, int tw, double emin, double emax, const double* pose)
+void make_frame(frame64* F, int H, int W, int th, int tw, double emin, double emax, const double* pose)
 {
     F->H = H; F->W = W; F->th = th; F->tw = tw;
     F->ntr = (H + th - 1) / th; F->ntc = (W + tw - 1) / tw;
@@ -372,92 +350,39 @@ static void surf_to_sensor(const double* mean, const double* quat, const double*
 /* Unit ray of pixel (r, c): elevation theta_r = emax - (r + 1/2)(emax-emin)/H
  * (row 0 at the top), azimuth phi_c = (c + 1/2) 2 pi / W counter-clockwise
  * from the sensor +x axis; d = (cos th cos ph, cos th sin ph, sin th). */
-static void pixel_ray(const frame64* F, int r, int c, double* d)
+void pixel_ray(const frame64* F, int r, int c, double* d)
 {
     double th = F->emax - (r + 0.5) * (F->emax - F->emin) / F->H;
     double ph = (c + 0.5) * 2.0 * M_PI / F->W;
     d[0] = cos(th) * cos(ph); d[1] = cos(th) * sin(ph); d[2] = sin(th);
 }
 
-enum { FL_DEN = 1, FL_TNEAR = 2, FL_QCUT = 4, FL_AMIN = 8, FL_AMAX = 16, FL_TSTOP = 32 };
-
-static int near_thr(double v, double thr) { return fabs(v - thr) <= FLAG_REL * fabs(thr); }
-
-typedef struct { int valid, flags; double den, t, x[3], u, v, q, G, araw, a; } eval64;
-
 /* One ray / surfel evaluation: plane intersection t = (n.mu)/(n.d), local
  * coordinates u = t_u.(t d - mu)/s_u, v = t_v.(t d - mu)/s_v, Gaussian
  * G = exp(-(u^2+v^2)/2), opacity a = min(alpha G, 0.99), with the skip rules
- * |n.d| < 1e-6, t <= t_near, u^2+v^2 > 9, a < 1/255. */
-/* Binary32 uncertainty of one evaluation (test infrastructure): an FP32
- * evaluation sees the sensor-frame geometry and the ray rounded to 24 bits,
- * so h = n.mu is known to about EPS32 |mu| and n.d to about EPS32; the ray
- * parameter t = h/(n.d) then has relative uncertainty
- *   dt/t = EPS32 (2 + 2/|n.d| + |mu|/|h|),
- * and a local coordinate u = t_u.(t d - mu)/s_u, of terms up to max(t,|mu|)/s,
- *   ek   = EPS32 max(t, |mu|)/s_min (2 + 1/|n.d| + |mu|/|h|). */
-static void fp32_unc(const surf64* s, double den, double t, double* ek, double* dt)
+ * |n.d| < 1e-6, t <= t_near, u^2+v^2 > 9, a < 1/255 (valid = 0 when one
+ * applies; the quantities after the failing rule are not formed). */
+void eval_pair(const surf64* s, const double* d, eval64* e)
 {
-    double g = 1.0 / fabs(den);
-    double rho = sqrt(dot3(s->mu, s->mu));
-    double h = fabs(t * den);
-    double hr = rho / (h > 1e-30 ? h : 1e-30);
-    double smin = s->su < s->sv ? s->su : s->sv;
-    *ek = EPS32 * ((fabs(t) > rho ? fabs(t) : rho) / smin) * (2.0 + g + hr);
-    *dt = fabs(t) * EPS32 * (2.0 + 2.0 * g + hr);
-}
-
-static void eval_pair(const surf64* s, const double* d, eval64* e)
-{
-    e->valid = 0; e->flags = 0;
+    e->valid = 0;
     e->den = dot3(s->n, d);
-    if (fabs(e->den) <= DEN_FLAG) e->flags |= FL_DEN;
     if (fabs(e->den) < DEN_EPS) return;
     e->t = dot3(s->n, s->mu) / e->den;
-    /* binary32 uncertainty of t and of the local coordinates (see fp32_bound):
-     * a decision is "near" its threshold when it lies within the larger of
-     * FLAG_REL and a few times that uncertainty */
-    double ek, dt;
-    fp32_unc(s, e->den, e->t, &ek, &dt);
-    if (fabs(e->t - T_NEAR) <= FLAG_REL * T_NEAR + 4.0 * dt) e->flags |= FL_TNEAR;
     if (e->t <= T_NEAR) return;
     for (int k = 0; k < 3; ++k) e->x[k] = e->t * d[k] - s->mu[k];
     e->u = dot3(s->tu, e->x) / s->su;
     e->v = dot3(s->tv, e->x) / s->sv;
     e->q = e->u * e->u + e->v * e->v;
-    double dq = 2.0 * (fabs(e->u) + fabs(e->v)) * ek;
-    if (fabs(e->q - Q_CUT) <= FLAG_REL * Q_CUT + 4.0 * dq) e->flags |= FL_QCUT;
     if (e->q > Q_CUT) return;
     e->G = exp(-0.5 * e->q);
     e->araw = s->alpha * e->G;
     e->a = e->araw < A_MAX ? e->araw : A_MAX;
-    double da = e->araw * (2.0 * dq + 4.0 * EPS32);     /* relative error of G is dq/2 */
-    if (fabs(e->araw - A_MAX) <= FLAG_REL * A_MAX + da) e->flags |= FL_AMAX;
-    if (fabs(e->a - A_MIN) <= FLAG_REL * A_MIN + da) e->flags |= FL_AMIN;
     if (e->a < A_MIN) return;
     e->valid = 1;
 }
 
-/* The same quantities as eval_pair with no skip applied (t, u, v, q, G, a
- * computed whatever the thresholds say); used to size the contribution of a
- * near-threshold evaluation that a binary32 evaluation may decide otherwise. */
-static void force_eval(const surf64* s, const double* d, eval64* e)
-{
-    e->flags = 0;
-    e->den = dot3(s->n, d);
-    e->t = dot3(s->n, s->mu) / e->den;
-    for (int k = 0; k < 3; ++k) e->x[k] = e->t * d[k] - s->mu[k];
-    e->u = dot3(s->tu, e->x) / s->su;
-    e->v = dot3(s->tv, e->x) / s->sv;
-    e->q = e->u * e->u + e->v * e->v;
-    e->G = exp(-0.5 * e->q);
-    e->araw = s->alpha * e->G;
-    e->a = e->araw < A_MAX ? e->araw : A_MAX;
-    e->valid = 1;
-}
-
-static surf64* sensor_surfels(const double* mean, const double* quat, const double* ls,
-                              const double* logit, int64_t n, const frame64* F)
+surf64* sensor_surfels(const double* mean, const double* quat, const double* ls,
+                       const double* logit, int64_t n, const frame64* F)
 {
     surf64* S = (surf64*)malloc(sizeof(surf64) * (n > 0 ? n : 1));
     for (int64_t i = 0; i < n; ++i) surf_to_sensor(mean, quat, ls, logit, i, F, S + i);
@@ -467,53 +392,21 @@ static surf64* sensor_surfels(const double* mean, const double* quat, const doub
 /* Front-to-back compositing of one pixel over list[0..len): for each valid
  * surfel, stop (without compositing it) if T (1 - a) < 1e-4, else
  * w = a T; A += w; S_t += w t; S_n += w (-sign(n.d)) n; T *= 1 - a.
- * Contributors are recorded in ck (list position), when ck != NULL. */
-typedef struct {
-    double A, St, Sn[3], T;
-    int32_t ncontrib;
-    int64_t neval;
-    int flags;
-    double flipA, flipAt;   /* sum of T a_w and T a_w |t| over near-threshold evaluations */
-    double flipa;           /* sum of a_w over near-threshold evaluations */
-} pix_out;
-
-/* Opacity (and ray parameter) the evaluation would have if its skip decision
- * went the other way: a FP32 evaluation may decide a near-threshold case
- * differently, and this is the size of what then changes. */
-static double would_be_a(const surf64* s, const eval64* e, double* t)
-{
-    if (e->flags & (FL_DEN | FL_TNEAR)) { *t = fabs(e->t); return s->alpha < A_MAX ? s->alpha : A_MAX; }
-    *t = fabs(e->t);
-    double a = s->alpha * exp(-0.5 * e->q);
-    return a < A_MAX ? a : A_MAX;
-}
-
-static int composite_pixel(const surf64* S, const uint32_t* list, int64_t len, const double* d,
-                           pix_out* o, int64_t* ck, double* cT)
+ * Contributors are recorded in ck (list position) with the transmittance
+ * before them in cT, when ck != NULL.  Returns their number. */
+int composite_pixel(const surf64* S, const uint32_t* list, int64_t len, const double* d,
+                    pix_out* o, int64_t* ck, double* cT)
 {
     o->A = 0; o->St = 0; o->Sn[0] = o->Sn[1] = o->Sn[2] = 0; o->T = 1.0;
-    o->ncontrib = 0; o->neval = 0; o->flags = 0; o->flipA = 0; o->flipAt = 0; o->flipa = 0;
+    o->ncontrib = 0; o->neval = 0;
     int nc = 0;
     for (int64_t k = 0; k < len; ++k) {
         const surf64* s = S + list[k];
         eval64 e;
         eval_pair(s, d, &e);
         o->neval++;
-        o->flags |= e.flags;
-        if (e.flags & (FL_DEN | FL_TNEAR | FL_QCUT | FL_AMIN)) {
-            double tw, aw = would_be_a(s, &e, &tw);
-            o->flipA += o->T * aw;
-            o->flipAt += o->T * aw * tw;
-            o->flipa += aw;
-        }
         if (!e.valid) continue;
         double Tn = o->T * (1.0 - e.a);
-        if (near_thr(Tn, T_STOP)) {
-            o->flags |= FL_TSTOP;
-            o->flipA += o->T * e.a;
-            o->flipAt += o->T * e.a * e.t;
-            o->flipa += e.a;
-        }
         if (Tn < T_STOP) break;
         double w = e.a * o->T;
         double sg = e.den > 0 ? -1.0 : 1.0;           /* -sign(n.d) */
@@ -528,46 +421,13 @@ static int composite_pixel(const surf64* S, const uint32_t* list, int64_t len, c
     return nc;
 }
 
-/* Error bound of the pixel's outputs implied by binary32 representation of
- * its inputs (test infrastructure, not part of the method).  A binary32
- * evaluation sees every sensor-frame coordinate and ray component rounded to
- * 24 bits; a local coordinate u = t_u.(t d - mu)/s_u then carries an error of
- * about EPS32 max(t, |mu|)/s, amplified by 1/|n.d| through t = (n.mu)/(n.d).
- * With e_k that error for contributor k:
- *   da_k = a_k ((|u_k| + |v_k|) e_k + 4 EPS32),  dt_k = t_k EPS32 (2 + 2/|n.d|),
- *   eA   = sum_k T_k da_k                      (|dA/da_k| <= T_k)
- *   eD   = sum_k |dD/da_k| da_k + w_k dt_k / (A + 1e-6),
- *   dD/da_k = [T_k (t_k - D) - sum_{j>k} w_j (t_j - D)/(1 - a_k)] / (A + 1e-6). */
-static void fp32_bound(const surf64* S, const uint32_t* list, const double* d, int nc, const int64_t* ck,
-                       const double* cT, const pix_out* o, double* eA, double* eD)
-{
-    double Dh = o->St / (o->A + EPS_A);
-    double ea = 0, ed = 0, suffix = 0;
-    for (int m = nc - 1; m >= 0; --m) {
-        const surf64* s = S + list[ck[m]];
-        eval64 e;
-        eval_pair(s, d, &e);
-        double T = cT[m], w = e.a * T;
-        double ek, dt;
-        fp32_unc(s, e.den, e.t, &ek, &dt);
-        double da = e.a * ((fabs(e.u) + fabs(e.v)) * ek + 4.0 * EPS32);
-        ea += T * da;
-        double dDda = (T * fabs(e.t - Dh) + suffix / (1.0 - e.a)) / (o->A + EPS_A);
-        ed += dDda * da + w * dt / (o->A + EPS_A);
-        suffix += w * fabs(e.t - Dh);
-    }
-    /* decisions within FLAG_REL of a threshold: the contribution that may flip */
-    ea += o->flipA;
-    ed += (o->flipAt + Dh * o->flipA) / (o->A + EPS_A);
-    *eA = ea;
-    *eD = ed;
-}
-
 /* Forward render of one frame.  ranges[2*tile] / ranges[2*tile+1] delimit the
  * tile's list in vals (surfel indices in depth order).  Outputs are planar
- * [H*W] (S_n: [3][H*W]).  pix_flag marks pixels where some evaluated quantity
- * lies within FLAG_REL of a threshold (a FP32 evaluation may decide those
- * differently). */
+ * [H*W] (S_n: [3][H*W]).  When pix_flag, eA and eD are given, the binary32
+ * allowance of every pixel is added (lgs_fp32_allowance.c): pix_flag marks
+ * pixels where some evaluated quantity lies near a threshold (a binary32
+ * evaluation may decide it differently), eA / eD bound the opacity and depth
+ * a binary32 evaluation of the same inputs may give. */
 void lgso_render_fwd(const double* mean, const double* quat, const double* ls, const double* logit,
                      int64_t n, int H, int W, int th, int tw, double emin, double emax,
                      const double* pose, const int64_t* ranges, const uint32_t* vals,
@@ -583,6 +443,7 @@ void lgso_render_fwd(const double* mean, const double* quat, const double* ls, c
     int64_t maxlen = 1;
     for (int64_t t = 0; t < ntiles; ++t)
         if (ranges[2 * t + 1] - ranges[2 * t] > maxlen) maxlen = ranges[2 * t + 1] - ranges[2 * t];
+    const int unc = pix_flag && eA && eD;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel
@@ -604,12 +465,15 @@ void lgso_render_fwd(const double* mean, const double* quat, const double* ls, c
                 int nc = composite_pixel(S, vals + b, e - b, d, &o, ck, cT);
                 int64_t p = (int64_t)r * W + c;
                 if (nvalid) nvalid[p] = nc;
-                if (eA && eD) fp32_bound(S, vals + b, d, nc, ck, cT, &o, eA + p, eD + p);
+                if (unc) {
+                    pix_unc u;
+                    fwd_allowance(S, vals + b, d, &o, nc, ck, cT, &u, eA + p, eD + p);
+                    pix_flag[p] = (uint8_t)u.flags;
+                }
                 A[p] = o.A; St[p] = o.St; Tf[p] = o.T;
                 Sn[p] = o.Sn[0]; Sn[HW + p] = o.Sn[1]; Sn[2 * HW + p] = o.Sn[2];
                 if (ncontrib) ncontrib[p] = o.ncontrib;
                 if (neval) neval[p] = o.neval;
-                if (pix_flag) pix_flag[p] = (uint8_t)o.flags;
             }
     }
     free(ck); free(cT);
@@ -652,9 +516,6 @@ int64_t lgso_coverage_misses(const double* mean, const double* quat, const doubl
 /* ------------------------------------------------------------------------ */
 /* Part III: FP64 reverse mode                                               */
 /* ------------------------------------------------------------------------ */
-/* gradient w.r.t. the sensor-frame surfel quantities */
-typedef struct { double mu[3], tu[3], tv[3], n[3], su, sv, alpha; } sgrad;
-
 /* Sensor-frame gradient of one contribution: evaluation e of surfel s at
  * transmittance T (before it), with suffix = sum over the later contributors
  * of w_j (g.c_j).  With c = (1, t, n') and w = a T:
@@ -662,25 +523,14 @@ typedef struct { double mu[3], tu[3], tv[3], n[3], su, sv, alpha; } sgrad;
  * because every later weight carries the factor (1 - a).  Adds into *g and
  * returns g.c.  use_clamp = 0 differentiates through alpha G even where a is
  * clamped at 0.99 (the size of what a clamp decision switches on or off). */
-static double contrib_grad_m(const surf64* s, const eval64* e, const double* d, double T, double suffix,
-                             double gA, double gSt, const double* gSn, int use_clamp, int majorant, sgrad* g)
+double contrib_grad(const surf64* s, const eval64* e, const double* d, double T, double suffix,
+                    double gA, double gSt, const double* gSn, int use_clamp, sgrad* g)
 {
     double sg = e->den > 0 ? -1.0 : 1.0;
     double np[3] = { sg * s->n[0], sg * s->n[1], sg * s->n[2] };
     double gc = gA + gSt * e->t + dot3(gSn, np);
     double w = e->a * T;
     double dLda = T * gc - suffix / (1.0 - e->a);
-    double gSn_m[3];
-    if (majorant) {
-        /* the same chain with every term of g.c and dL/da taken in absolute
-         * value: the magnitudes a binary32 evaluation rounds, whatever cancels */
-        gc = fabs(gA) + fabs(gSt * e->t) + fabs(gSn[0]) + fabs(gSn[1]) + fabs(gSn[2]);
-        dLda = T * gc + fabs(suffix) / (1.0 - e->a);
-        gSt = fabs(gSt);
-        for (int k = 0; k < 3; ++k) gSn_m[k] = fabs(gSn[k]);
-        gSn = gSn_m;
-        sg = 1.0;
-    }
     /* direct terms of S_t and S_n (the sign flip has zero derivative) */
     double dLdt = w * gSt;
     for (int k = 0; k < 3; ++k) g->n[k] += w * sg * gSn[k];
@@ -709,15 +559,6 @@ static double contrib_grad_m(const surf64* s, const eval64* e, const double* d, 
     return gc;
 }
 
-static double contrib_grad(const surf64* s, const eval64* e, const double* d, double T, double suffix,
-                           double gA, double gSt, const double* gSn, int use_clamp, sgrad* g)
-{
-    return contrib_grad_m(s, e, d, T, suffix, gA, gSt, gSn, use_clamp, 0, g);
-}
-
-static void chain_to_params(const surf64* s, const sgrad* g, const frame64* F,
-                            double* dmean, double* dquat, double* dls, double* dlogit);
-
 static void sgrad_add(sgrad* a, const sgrad* b)
 {
     for (int k = 0; k < 3; ++k) {
@@ -726,294 +567,31 @@ static void sgrad_add(sgrad* a, const sgrad* b)
     a->su += b->su; a->sv += b->sv; a->alpha += b->alpha;
 }
 
-/* |raw-parameter gradient| (mean 3, quat 4, log-scale 2, logit 1) of one contribution */
-static void raw_abs(const surf64* s, const sgrad* g, const frame64* F, double* r)
-{
-    double dm[3] = { 0, 0, 0 }, dq[4] = { 0, 0, 0, 0 }, dl[2] = { 0, 0 }, dg = 0;
-    chain_to_params(s, g, F, dm, dq, dl, &dg);
-    for (int k = 0; k < 3; ++k) r[k] = fabs(dm[k]);
-    for (int k = 0; k < 4; ++k) r[3 + k] = fabs(dq[k]);
-    r[7] = fabs(dl[0]); r[8] = fabs(dl[1]); r[9] = fabs(dg);
-}
-
-static void rot_jacobian(const double* q, double J[9][4]);
-
-/* Majorant of the raw-parameter gradient of one contribution: the chain of
- * chain_to_params with every product in absolute value, i.e. the sum of the
- * magnitudes that a binary32 evaluation of the chain adds up (a rotation of an
- * isotropic surfel about its normal, for one, cancels exactly in FP64 but not
- * in binary32). */
-static void raw_major(const surf64* s, const sgrad* g, const frame64* F, double* r)
-{
-    double dcol[3][3];
-    for (int a = 0; a < 3; ++a) {
-        double gm = 0, g0 = 0, g1 = 0, g2 = 0;
-        for (int k = 0; k < 3; ++k) {
-            double R = fabs(F->R[3 * a + k]);
-            gm += R * fabs(g->mu[k]);
-            g0 += R * fabs(g->tu[k]);
-            g1 += R * fabs(g->tv[k]);
-            g2 += R * fabs(g->n[k]);
-        }
-        r[a] = gm;
-        dcol[0][a] = g0; dcol[1][a] = g1; dcol[2][a] = g2;
-    }
-    double J[9][4];
-    rot_jacobian(s->qh, J);
-    double dqh[4] = { 0, 0, 0, 0 };
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            for (int c = 0; c < 4; ++c) dqh[c] += dcol[b][a] * fabs(J[3 * a + b][c]);
-    double pr = 0;
-    for (int c = 0; c < 4; ++c) pr += dqh[c] * fabs(s->qh[c]);
-    for (int c = 0; c < 4; ++c) r[3 + c] = (dqh[c] + fabs(s->qh[c]) * pr) / s->qnorm;
-    r[7] = fabs(g->su) * s->su;
-    r[8] = fabs(g->sv) * s->sv;
-    r[9] = fabs(g->alpha) * s->alpha * (1.0 - s->alpha);
-}
-
-/* The evaluation e with its local coordinates moved by (du, dv), its depth by
- * dtt and n.d by dden, the skip and clamp decisions kept: the inputs a
- * binary32 evaluation may see instead of e's (u and v are absolute
- * uncertainties, so terms proportional to a small u, v or offset x are
- * covered too). */
-static void perturb_eval(const surf64* s, const eval64* e, double du, double dv, double dtt, double dden,
-                         eval64* p)
-{
-    *p = *e;
-    p->den = e->den + dden;
-    p->t = e->t + dtt;
-    p->u = e->u + du;
-    p->v = e->v + dv;
-    for (int k = 0; k < 3; ++k) p->x[k] = e->x[k] + du * s->su * s->tu[k] + dv * s->sv * s->tv[k];
-    p->q = p->u * p->u + p->v * p->v;
-    p->G = exp(-0.5 * p->q);
-    p->araw = s->alpha * p->G;
-    p->a = e->araw < A_MAX ? p->araw : A_MAX;
-}
-
-static void add10(double* dst, const double* r, double f)
-{
-    for (int c = 0; c < 10; ++c) {
-#ifdef _OPENMP
-#pragma omp atomic
-#endif
-        dst[c] += f * r[c];
-    }
-}
-
-/* First-order binary32 uncertainty of the opacity of one evaluation: a
- * re-derived with u, v moved by their uncertainty ek, t by dt and n.d by 4
- * ulp, the changes added in absolute value, plus 4 ulp of rounding. */
-static double opacity_unc(const surf64* s, const eval64* e)
-{
-    double ek, dt;
-    fp32_unc(s, e->den, e->t, &ek, &dt);
-    const double dden = (e->den > 0 ? 4.0 : -4.0) * EPS32;
-    const double steps[4][4] = { { ek, 0, 0, 0 }, { 0, ek, 0, 0 }, { 0, 0, dt, 0 }, { 0, 0, 0, dden } };
-    double da = 4.0 * EPS32 * e->a;
-    for (int k = 0; k < 4; ++k) {
-        eval64 p;
-        perturb_eval(s, e, steps[k][0], steps[k][1], steps[k][2], steps[k][3], &p);
-        da += fabs(p.a - e->a);
-    }
-    return da;
-}
-
-/* First-order binary32 uncertainty of one contribution c0 (into r[10], raw
- * parameters): c0 re-derived with u, v moved by their uncertainty ek, t by
- * dt, n.d by 4 ulp, the transmittance T by the relative amount eT and the
- * suffix by dS, the six changes added in absolute value.  Propagating the
- * inputs' errors this way (instead of scaling a majorant) keeps the size of
- * cancelling upstream terms out of the bound, and keeps terms proportional to
- * a small u, v or offset x in it. */
-static void contrib_unc(const surf64* s, const eval64* e, const double* d, double T, double suffix, double eT,
-                        double dS, double gA, double gSt, const double* gSn, const frame64* F, const sgrad* c0,
-                        double* r)
-{
-    double ek, dt;
-    fp32_unc(s, e->den, e->t, &ek, &dt);
-    const double dden = (e->den > 0 ? 4.0 : -4.0) * EPS32;
-    const double steps[4][4] = { { ek, 0, 0, 0 }, { 0, ek, 0, 0 }, { 0, 0, dt, 0 }, { 0, 0, 0, dden } };
-    for (int c = 0; c < 10; ++c) r[c] = 0;
-    for (int k = 0; k < 6; ++k) {
-        eval64 p;
-        double Tk = T, Sk = suffix;
-        if (k < 4) perturb_eval(s, e, steps[k][0], steps[k][1], steps[k][2], steps[k][3], &p);
-        else p = *e;
-        if (k == 4) Tk = T * (1.0 + eT);
-        if (k == 5) Sk = suffix + dS;
-        sgrad g;
-        memset(&g, 0, sizeof(g));
-        contrib_grad(s, &p, d, Tk, Sk, gA, gSt, gSn, 1, &g);
-        for (int j = 0; j < 3; ++j) {
-            g.mu[j] -= c0->mu[j]; g.tu[j] -= c0->tu[j]; g.tv[j] -= c0->tv[j]; g.n[j] -= c0->n[j];
-        }
-        g.su -= c0->su; g.sv -= c0->sv; g.alpha -= c0->alpha;
-        double q[10];
-        raw_abs(s, &g, F, q);
-        for (int c = 0; c < 10; ++c) r[c] += q[c];
-    }
-}
-
-#define FL_HARD (FL_DEN | FL_TNEAR)
-#define FL_SOFT (FL_QCUT | FL_AMIN)
-
 /* Reverse mode through composite_pixel for one pixel with upstream gradients
- * (gA, gSt, gSn) of (A, S_t, S_n).  Besides the gradient (into G) it records,
- * per surfel and raw parameter (when gabs / gflip are given):
- *   gabs  += a majorant of each contribution (its terms in absolute value:
- *            the conditioning of the sums and of the chain to the raw
- *            parameters);
- *   gflip += twice the first-order change of the contribution under the
- *            binary32 uncertainties of its inputs (contrib_unc: u, v, t, n.d,
- *            the transmittance before it and the suffix after it, where a
- *            near-threshold decision of another entry counts as an
- *            uncertainty of its whole opacity), and
- *   gflip += what a near-threshold decision of the surfel's own can change:
- *            its whole would-be contribution; a grazing or near-plane
- *            decision makes the surfel's value undetermined (gflip = inf). */
-/* Opacity that a binary32 evaluation may add or drop at a near-threshold
- * decision of evaluated entry k of a pixel (contributor or not; 0 if none). */
-static double flip_opacity(const surf64* s, const double* d, const eval64* e, int is_contrib, int last_contrib,
-                           int stop_entry, const pix_out* o)
-{
-    int tstop = (o->flags & FL_TSTOP) != 0;
-    if (is_contrib) {
-        if ((e->flags & FL_SOFT) || (tstop && last_contrib)) return e->a;
-        if (e->flags & FL_AMAX) return fabs(e->araw - A_MAX);
-        return 0.0;
-    }
-    if ((e->flags & FL_SOFT) || (tstop && stop_entry)) {
-        eval64 f;
-        force_eval(s, d, &f);
-        return f.a;
-    }
-    return 0.0;
-}
-
+ * (gA, gSt, gSn) of (A, S_t, S_n): the contributors in reverse order, each
+ * with its transmittance cT and the suffix over the later contributors
+ * (per-pixel contributor lists are what this oracle stores; the GPU
+ * recomputes them). */
 static void backward_pixel(const surf64* S, const uint32_t* list, const double* d, int nc,
-                           const int64_t* ck, const double* cT, const pix_out* o, double gA, double gSt,
-                           const double* gSn, const frame64* F, sgrad* G, double* gabs, double* gflip,
-                           double* tmp, double* suf, double* et)
+                           const int64_t* ck, const double* cT, double gA, double gSt,
+                           const double* gSn, sgrad* G)
 {
-    const int unc = gflip && gabs;
-    double suffix = 0.0, suffix_abs = 0.0, dS = 0.0;
-    if (unc) {
-        /* et[m]: relative uncertainty of the transmittance before contributor m:
-         * the earlier opacities' binary32 uncertainties, the opacities that a
-         * near-threshold decision may add or drop, and the roundings of the
-         * products / quotients that carry it */
-        double acc = 2.0 * nc * EPS32;
-        int mm = 0;
-        for (int64_t k = 0; k < o->neval; ++k) {
-            const surf64* s = S + list[k];
-            int is_contrib = mm < nc && ck[mm] == k;
-            eval64 e;
-            eval_pair(s, d, &e);
-            int stop_entry = (k == o->neval - 1) && !is_contrib && e.valid;
-            double fa = flip_opacity(s, d, &e, is_contrib, mm == nc - 1, stop_entry, o);
-            if (is_contrib) {
-                et[mm++] = acc;
-                acc += (opacity_unc(s, &e) + fa) / (1.0 - e.a);
-            } else if (fa > 0) {
-                acc += fa / (1.0 - fa);
-            }
-        }
-    }
-    int mm = nc - 1;
-    for (int64_t k = o->neval - 1; k >= 0; --k) {
-        uint32_t i = list[k];
+    double suffix = 0.0;
+    for (int m = nc - 1; m >= 0; --m) {
+        uint32_t i = list[ck[m]];
         const surf64* s = S + i;
         eval64 e;
         eval_pair(s, d, &e);                   /* recompute the same evaluation */
-        if (mm < 0 || ck[mm] != k) {
-            /* not composited: a near-threshold entry may still be in binary32,
-             * adding its term to the suffix of the contributors before it */
-            if (!unc) continue;
-            int stop_entry = (k == o->neval - 1) && e.valid;
-            double fa = flip_opacity(s, d, &e, 0, 0, stop_entry, o);
-            if (fa > 0) {
-                eval64 f;
-                force_eval(s, d, &f);
-                double np = f.den > 0 ? -1.0 : 1.0;
-                double gcw = gA + gSt * f.t + np * dot3(gSn, s->n);
-                dS += fa * (mm + 1 < nc ? cT[mm + 1] : o->T) * fabs(gcw);
-            }
-            continue;
-        }
-        const int m = mm--;
-        double T = cT[m];
         sgrad c;
         memset(&c, 0, sizeof(c));
-        double gc = contrib_grad(s, &e, d, T, suffix, gA, gSt, gSn, 1, &c);
-        suffix += e.a * T * gc;
-        suf[m] = suffix;                       /* sum over contributors >= m */
+        double gc = contrib_grad(s, &e, d, cT[m], suffix, gA, gSt, gSn, 1, &c);
+        suffix += e.a * cT[m] * gc;
         sgrad_add(G + i, &c);
-        if (gabs) {
-            sgrad cm;
-            memset(&cm, 0, sizeof(cm));
-            double gcm = contrib_grad_m(s, &e, d, T, suffix_abs, gA, gSt, gSn, 1, 1, &cm);
-            suffix_abs += e.a * T * gcm;
-            raw_major(s, &cm, F, tmp + 10 * m);
-            add10(gabs + 10 * (int64_t)i, tmp + 10 * m, 1.0);
-        }
-        if (unc) {
-            double r[10], ek, dt;
-            /* suffix - w gc: the suffix over the later contributors only */
-            contrib_unc(s, &e, d, T, suffix - e.a * T * gc, et[m], dS, gA, gSt, gSn, F, &c, r);
-            add10(gflip + 10 * (int64_t)i, r, 2.0);
-            /* this term's own uncertainty, for the contributors before it */
-            fp32_unc(s, e.den, e.t, &ek, &dt);
-            double w = e.a * T;
-            double fa = flip_opacity(s, d, &e, 1, m == nc - 1, 0, o);
-            dS += (opacity_unc(s, &e) + fa) * T * fabs(gc) + w * fabs(gSt) * dt + et[m] * fabs(w * gc);
-        }
-        if (gflip && (e.flags & FL_AMAX)) {
-            sgrad u;
-            memset(&u, 0, sizeof(u));
-            double r[10];
-            contrib_grad(s, &e, d, T, m + 1 < nc ? suf[m + 1] : 0.0, gA, gSt, gSn, 0, &u);
-            raw_abs(s, &u, F, r);
-            add10(gflip + 10 * (int64_t)i, r, 1.0);
-        }
-    }
-    if (!unc || !o->flags) return;
-    if (o->flags & FL_TSTOP && nc > 0) add10(gflip + 10 * (int64_t)list[ck[nc - 1]], tmp + 10 * (nc - 1), 1.0);
-    /* the surfels whose own decision is near a threshold */
-    mm = 0;
-    for (int64_t k = 0; k < o->neval; ++k) {
-        while (mm < nc && ck[mm] < k) ++mm;
-        int is_contrib = mm < nc && ck[mm] == k;
-        uint32_t i = list[k];
-        const surf64* s = S + i;
-        eval64 e;
-        eval_pair(s, d, &e);
-        if (e.flags & FL_HARD) {
-            for (int c = 0; c < 10; ++c) gflip[10 * (int64_t)i + c] = INFINITY;
-            continue;
-        }
-        int stop_entry = (k == o->neval - 1) && !is_contrib && e.valid;
-        if (!(e.flags & FL_SOFT) && !stop_entry) continue;
-        if (is_contrib) {
-            add10(gflip + 10 * (int64_t)i, tmp + 10 * mm, 1.0);
-            continue;
-        }
-        eval64 f;
-        force_eval(s, d, &f);
-        double T = mm < nc ? cT[mm] : o->T;
-        double sx = mm < nc ? suf[mm] : 0.0;
-        sgrad u;
-        memset(&u, 0, sizeof(u));
-        double r[10];
-        contrib_grad(s, &f, d, T, sx, gA, gSt, gSn, 1, &u);
-        raw_abs(s, &u, F, r);
-        add10(gflip + 10 * (int64_t)i, r, 1.0);
     }
 }
 
 /* d R(q)_{ab} / d q_c for a unit quaternion q = (w,x,y,z); R row-major. */
-static void rot_jacobian(const double* q, double J[9][4])
+void rot_jacobian(const double* q, double J[9][4])
 {
     double w = q[0], x = q[1], y = q[2], z = q[3];
     double t[9][4] = {
@@ -1032,7 +610,7 @@ static void rot_jacobian(const double* q, double J[9][4])
 
 /* Chain the sensor-frame gradient of surfel i to the raw parameters
  * (mean, quaternion, log-scale, logit); accumulates (+=). */
-static void chain_to_params(const surf64* s, const sgrad* g, const frame64* F,
+void chain_to_params(const surf64* s, const sgrad* g, const frame64* F,
                             double* dmean, double* dquat, double* dls, double* dlogit)
 {
     /* mu_s = R^T (mu_w - o)  =>  d mu_w = R d mu_s; same for the axes */
@@ -1064,9 +642,9 @@ static void chain_to_params(const surf64* s, const sgrad* g, const frame64* F,
 
 /* Backward of one frame: accumulates (+=) dL/d(mean, quat, log_scale, logit)
  * for upstream gradients gA, gSt [H*W], gSn [3][H*W].  When gabs and gflip
- * ([n][10]: mean 3, quat 4, log-scale 2, logit 1) are given, also accumulates
- * per surfel the sum of |per-pixel contributions| and the near-threshold
- * uncertainty described at backward_pixel. */
+ * ([n][10]: mean 3, quat 4, log-scale 2, logit 1) are given, the binary32
+ * allowance of the gradient is added (lgs_fp32_allowance.c): per surfel the
+ * majorant of its per-pixel contributions and their binary32 uncertainty. */
 void lgso_render_bwd(const double* mean, const double* quat, const double* ls, const double* logit,
                      int64_t n, int H, int W, int th, int tw, double emin, double emax,
                      const double* pose, const int64_t* ranges, const uint32_t* vals,
@@ -1081,6 +659,7 @@ void lgso_render_bwd(const double* mean, const double* quat, const double* ls, c
     int64_t maxlen = 1;
     for (int64_t t = 0; t < ntiles; ++t)
         if (ranges[2 * t + 1] - ranges[2 * t] > maxlen) maxlen = ranges[2 * t + 1] - ranges[2 * t];
+    const int unc = gabs && gflip;
     int nth = 1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -1098,9 +677,9 @@ void lgso_render_bwd(const double* mean, const double* quat, const double* ls, c
         sgrad* G = Gall + (size_t)tid * (n > 0 ? n : 1);
         int64_t* ck = (int64_t*)malloc(sizeof(int64_t) * maxlen);
         double* cT = (double*)malloc(sizeof(double) * maxlen);
-        double* tmp = (double*)malloc(sizeof(double) * 10 * maxlen);
-        double* suf = (double*)malloc(sizeof(double) * maxlen);
-        double* et = (double*)malloc(sizeof(double) * maxlen);
+        double* tmp = unc ? (double*)malloc(sizeof(double) * 10 * maxlen) : NULL;
+        double* suf = unc ? (double*)malloc(sizeof(double) * maxlen) : NULL;
+        double* et = unc ? (double*)malloc(sizeof(double) * maxlen) : NULL;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
@@ -1115,8 +694,14 @@ void lgso_render_bwd(const double* mean, const double* quat, const double* ls, c
                     int nc = composite_pixel(S, vals + b, e - b, d, &o, ck, cT);
                     int64_t p = (int64_t)r * W + c;
                     double gsn[3] = { gSn[p], gSn[HW + p], gSn[2 * HW + p] };
-                    backward_pixel(S, vals + b, d, nc, ck, cT, &o, gA[p], gSt[p], gsn, &F, G, gabs, gflip,
-                                   tmp, suf, et);
+                    backward_pixel(S, vals + b, d, nc, ck, cT, gA[p], gSt[p], gsn, G);
+                    if (unc) {
+                        pix_unc u;
+                        double ea, ed;
+                        fwd_allowance(S, vals + b, d, &o, nc, ck, cT, &u, &ea, &ed);
+                        bwd_allowance(S, vals + b, d, nc, ck, cT, &o, &u, gA[p], gSt[p], gsn, &F, gabs, gflip,
+                                      tmp, suf, et, NULL);
+                    }
                 }
         }
         free(ck); free(cT); free(tmp); free(suf); free(et);

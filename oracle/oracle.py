@@ -22,6 +22,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lgs_oracle.c")
+# the method and, in its own translation unit, the binary32 allowance the
+# parity tests add to their bars; both include the shared internal header
+_SOURCES = [_SRC, os.path.join(_HERE, "lgs_fp32_allowance.c")]
+_DEPS = _SOURCES + [os.path.join(_HERE, "lgs_oracle_impl.h")]
 _LIB_PATH = os.path.join(_HERE, "liblgs_oracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -38,16 +42,20 @@ LAMBDA_NS = 0.01
 S_MAX = 1.0
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (binary32 binning needs -ffp-contract=off)."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+def build(force: bool = False, out: str | None = None, defines=()) -> str:
+    """Compile the oracle with gcc (binary32 binning needs -ffp-contract=off).
+    ``out`` and ``defines`` (``NAME=value`` strings) build a variant elsewhere:
+    the allowance tests plant a mistake in a bound that way."""
+    path = out or _LIB_PATH
+    if (not force and out is None and os.path.exists(path)
+            and all(os.path.getmtime(path) >= os.path.getmtime(f) for f in _DEPS)):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+           "-fPIC", "-shared", *[f"-D{d}" for d in defines], *_SOURCES, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 def _load():
@@ -81,6 +89,11 @@ def _load():
         lib.lgso_surf_normal_loss.restype = f64
         lib.lgso_scale_reg.argtypes = [P, i64, f64, f64, P]
         lib.lgso_scale_reg.restype = f64
+        lib.lgso_pixel_detail.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, f64, f64, P, P, P, i32, i32,
+                                          f64, f64, P, i64] + [P] * 17
+        lib.lgso_pixel_detail.restype = i64
+        lib.lgso_contrib_with.argtypes = [P, P, P, P, i64, i32, i32, f64, f64, P, i32, i32, P, f64, f64, f64, f64,
+                                          P, P]
         _lib = lib
         return lib
 
@@ -221,6 +234,66 @@ def render_bwd(surfels, frame, ranges, vals, gA, gSt, gSn, params64=None, grads=
                         _p(grads["mean"]), _p(grads["quat"]), _p(grads["log_scale"]), _p(grads["logit"]),
                         _p(grads["abs"]), _p(grads["flip"]), int(nthreads))
     return grads
+
+
+# --- the binary32 allowance, one pixel at a time (its pins) -------------------
+def pixel_detail(surfels, frame, ranges, vals, r: int, c: int, gA=1.0, gSt=0.0, gSn=(0.0, 0.0, 0.0),
+                 params64=None, lib=None):
+    """Every list entry the method evaluated at pixel (r, c), with the
+    allowance's per-entry and per-contributor values (see lgso_pixel_detail).
+    ``lib``: a variant build of the oracle (a planted mistake)."""
+    lib = lib or _load()
+    m, q, ls, lg = params64 if params64 is not None else _params64(surfels)
+    fa = _frame_args(frame)
+    t = (r // frame.tile_h) * (-(-frame.W // frame.tile_w)) + c // frame.tile_w
+    ranges = _c(ranges, np.int64)
+    cap = max(int(ranges[t, 1] - ranges[t, 0]), 1)
+    item = np.zeros(cap, np.uint32); valid = np.zeros(cap, np.int32); flags = np.zeros(cap, np.int32)
+    contrib = np.zeros(cap, np.int32); ev = np.zeros((cap, 8)); unc = np.zeros((cap, 4)); would = np.zeros(cap)
+    grad = np.zeros((cap, 10)); gunc = np.zeros((cap, 10)); gmaj = np.zeros((cap, 10))
+    T = np.zeros(cap); S = np.zeros(cap); eT = np.zeros(cap); dS = np.zeros(cap); pix = np.zeros(8)
+    pfl = np.zeros(1, np.int32); nco = np.zeros(1, np.int32)
+    gsn = _c(np.asarray(gSn, np.float64), np.float64)
+    k = lib.lgso_pixel_detail(_p(m), _p(q), _p(ls), _p(lg), m.shape[0], *fa[:6], _p(fa[6]), _p(ranges),
+                              _p(_c(vals, np.uint32)), int(r), int(c), float(gA), float(gSt), _p(gsn), cap,
+                              _p(item), _p(valid), _p(flags), _p(contrib), _p(ev), _p(unc), _p(would), _p(grad),
+                              _p(gunc), _p(gmaj), _p(T), _p(S), _p(eT), _p(dS), _p(pix), _p(pfl), _p(nco))
+    if k < 0:
+        raise ValueError("more evaluated entries than the tile list holds")
+    nc = int(nco[0])
+    return dict(item=item[:k], valid=valid[:k].astype(bool), flags=flags[:k], contrib=contrib[:k], den=ev[:k, 0],
+                t=ev[:k, 1], u=ev[:k, 2], v=ev[:k, 3], q=ev[:k, 4], G=ev[:k, 5], a=ev[:k, 6], araw=ev[:k, 7],
+                eu=unc[:k, 0], ev=unc[:k, 1], dt=unc[:k, 2], da=unc[:k, 3], would=would[:k], grad=grad[:nc], gunc=gunc[:nc],
+                gmaj=gmaj[:nc], T=T[:nc], S=S[:nc], eT=eT[:nc], dS=dS[:nc], A=pix[0], S_t=pix[1],
+                S_n=pix[2:5].copy(), T_final=pix[5], eA=pix[6], eD=pix[7], pflags=int(pfl[0]), nc=nc)
+
+
+def contrib_with(surfels, frame, i: int, r: int, c: int, den, t, u, v, G, a, araw, T, S, gA=1.0, gSt=0.0,
+                 gSn=(0.0, 0.0, 0.0), params64=None, lib=None):
+    """The method's raw-parameter contribution of surfel i at pixel (r, c)
+    from the given evaluation quantities, transmittance and suffix (see
+    lgso_contrib_with)."""
+    lib = lib or _load()
+    m, q, ls, lg = params64 if params64 is not None else _params64(surfels)
+    fa = _frame_args(frame)
+    q7 = np.array([den, t, u, v, G, a, araw], np.float64)
+    out = np.zeros(10)
+    lib.lgso_contrib_with(_p(m), _p(q), _p(ls), _p(lg), int(i), frame.H, frame.W, fa[4], fa[5], _p(fa[6]), int(r),
+                          int(c), _p(q7), float(T), float(S), float(gA), float(gSt),
+                          _p(_c(np.asarray(gSn, np.float64), np.float64)), _p(out))
+    return out
+
+
+def variant(defines, path):
+    """A separately built oracle with the given -D defines (a planted
+    mistake), loaded with the argument types of the oracle's own library."""
+    build(force=True, out=path, defines=defines)
+    lib = ctypes.CDLL(path)
+    base = _load()
+    for name in ("lgso_pixel_detail", "lgso_contrib_with", "lgso_render_fwd", "lgso_render_bwd"):
+        getattr(lib, name).argtypes = getattr(base, name).argtypes
+        getattr(lib, name).restype = getattr(base, name).restype
+    return lib
 
 
 def loss_image(fwd, D, Ng, lam_alpha=LAMBDA_ALPHA, lam_n=LAMBDA_N, lam_ng=LAMBDA_NG, scale=1.0, lam_ns=0.0,
