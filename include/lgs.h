@@ -523,9 +523,12 @@ LGS_API lgs_status lgs_keyframe_init(const float* points, int64_t n, const float
  * sized for at most LGS_NOALLOC_MAX_FRAMES frames per call; more frames are
  * rejected with LGS_ERR_INVALID_ARG.  The caller zeroes nothing: the scratch
  * is zero when the library loads and every call leaves it at zero on the
- * device when it completes.  The first call on a device looks up the scratch's address
- * (cudaGetSymbolAddress, with that device current) and caches it, so make one
- * call on each device before timing-critical use.  Every call on a device
+ * device when it completes.  Every call looks up the scratch's address in
+ * the current device's context (cudaGetSymbolAddress, with that device
+ * current; nothing is cached, so the address stays right after a device
+ * reset or in a new context).  The first call in a context may load the
+ * library's device code there, so make one call on each device before any
+ * stream capture or timing-critical use.  Every call on a device
  * shares the one scratch: calls that overlap in time (on other streams or
  * from other threads) corrupt each other's results and must be serialised by
  * the caller. */

@@ -56,8 +56,12 @@
 #endif
 
 enum { FL_DEN = 1, FL_TNEAR = 2, FL_QCUT = 4, FL_AMIN = 8, FL_AMAX = 16, FL_TSTOP = 32 };
-#define FL_HARD (FL_DEN | FL_TNEAR)
-#define FL_SOFT (FL_QCUT | FL_AMIN)
+/* A grazing decision (|n.d| near 1e-6) may admit a surfel at an unbounded
+ * ray parameter: its gradient is undetermined.  The other near-threshold
+ * decisions (the near plane, the cut-off, the 1/255 skip) are bounded by the
+ * contribution they may add or drop. */
+#define FL_HARD FL_DEN
+#define FL_SOFT (FL_TNEAR | FL_QCUT | FL_AMIN)
 
 static int near_thr(double v, double thr) { return fabs(v - thr) <= FLAG_REL * fabs(thr); }
 
@@ -135,11 +139,11 @@ static double opacity_unc(const surf64* s, const eval64* e);
  * went the other way: a FP32 evaluation may decide a near-threshold case
  * differently, and this is the size of what then changes (the opacity with
  * its own binary32 uncertainty, since the flipped evaluation sees slightly
- * different u, v).  A grazing or near-plane decision may admit the surfel at
- * its full opacity. */
+ * different u, v).  A grazing decision may admit the surfel at its full
+ * opacity. */
 static double would_be_a(const surf64* s, const double* d, const eval64* e, int flags, double* t)
 {
-    if (flags & (FL_DEN | FL_TNEAR)) {
+    if (flags & FL_HARD) {
         *t = fabs(dot3(s->n, s->mu) / e->den);
         return s->alpha < A_MAX ? s->alpha : A_MAX;
     }

@@ -15,7 +15,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "lgs_internal.cuh"
 
@@ -139,28 +138,20 @@ __global__ void __launch_bounds__(kNaThreads) k_na_main(NaFrames fr, NaScratch s
   }
 }
 
-std::mutex g_mu;
-void* g_addr[64] = {};
-
 }  // namespace
 
 size_t noalloc_scratch_bytes() { return kScratchBytes; }
 
-// Device address of the static scratch on the current device: looked up
-// once per device (with that device current) and cached.
+// Device address of the static scratch in the current device's context,
+// looked up on every call (with that device current).  Nothing is cached:
+// after a device reset, or in a new primary context, the module is loaded
+// again at another address, and a cached pointer would be stale.  The first
+// lookup in a context may load the library's device code there.
 cudaError_t noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

@@ -14,9 +14,12 @@ def to_dev(surf):
 
 
 def run(maps, frames, targets=None, frame_map=None, tuning=None, read_bins=False, loss=LOSS,
-        grads_init=None, session=None, repeat_fwd=1):
+        grads_init=None, session=None, repeat_fwd=1, single=False):
     """maps: list of scenes.Surfels; frames: list of scenes.Frame; targets:
-    list of scenes.Target (or None for forward only)."""
+    list of scenes.Target (or None for forward only).  single: one map,
+    through the single-map calls (lgs_bin_sort, lgs_render_fwd, lgs_loss,
+    lgs_render_bwd) instead of their batch forms."""
+    assert not single or len(maps) == 1
     import torch
     dev = torch.device("cuda")
     T = [to_dev(m) for m in maps]
@@ -25,11 +28,23 @@ def run(maps, frames, targets=None, frame_map=None, tuning=None, read_bins=False
     fm = list(frame_map) if frame_map is not None else [0] * len(frames)
     sess = session or lib.Session()
     lib.lgs_session_set_tuning(sess.handle, **(tuning or {}))
-    sess.bin_sort(S, fr, fm)
     stream = torch.cuda.current_stream().cuda_stream
+    if single:
+        sess.reserve([maps[0].n], fr, fm, max(1024, 4 * maps[0].n))
+        lib.lgs_bin_sort(sess.handle, S[0], fr, stream)
+        st, req = lib.lgs_session_status(sess.handle)
+        if st == lib.LGS_ERR_CAPACITY:          # grow to what the device reported, bin again
+            sess.reserve([maps[0].n], fr, fm, req + 1024)
+            lib.lgs_bin_sort(sess.handle, S[0], fr, stream)
+        sess.check_status()
+    else:
+        sess.bin_sort(S, fr, fm)
     outs = [lib.alloc_fwd(f, dev) for f in frames]
     for _ in range(repeat_fwd):
-        lib.lgs_render_fwd_batch(sess.handle, S, fr, fm, [o.struct() for o in outs], stream)
+        if single:
+            lib.lgs_render_fwd(sess.handle, S[0], fr, [o.struct() for o in outs], stream)
+        else:
+            lib.lgs_render_fwd_batch(sess.handle, S, fr, fm, [o.struct() for o in outs], stream)
     res = dict(fwd=[dict(A=o.A, S_t=o.S_t, S_n=o.S_n, T_final=o.T_final, n_contrib=o.n_contrib) for o in outs])
     if read_bins:
         n_items = sum(maps[fm[f]].n for f in range(len(frames)))
@@ -49,15 +64,24 @@ def run(maps, frames, targets=None, frame_map=None, tuning=None, read_bins=False
                     a.copy_(torch.from_numpy(np.asarray(b, np.float32)))
             grads.append(g)
         lp = lib.lgs_loss_params(**loss)
-        lib.lgs_loss_batch(sess.handle, S, fr, fm, [o.struct() for o in outs],
-                           [lib.lgs_target(d.data_ptr(), n.data_ptr()) for d, n in tg], lp,
-                           [lib.lgs_fwd_grad_out(g["dA"].data_ptr(), g["dS_t"].data_ptr(), g["dS_n"].data_ptr())
-                            for g in gp],
-                           [lib.grad_struct(*g) for g in grads], loss_out.data_ptr(), stream)
-        lib.lgs_render_bwd_batch(sess.handle, S, fr, fm, [o.struct() for o in outs],
-                                 [lib.lgs_fwd_grad(g["dA"].data_ptr(), g["dS_t"].data_ptr(), g["dS_n"].data_ptr())
-                                  for g in gp],
-                                 [lib.grad_struct(*g) for g in grads], stream)
+        if single:
+            lib.lgs_loss(sess.handle, S[0], fr, [o.struct() for o in outs],
+                         [lib.lgs_target(d.data_ptr(), n.data_ptr()) for d, n in tg], lp,
+                         [lib.lgs_fwd_grad_out(g["dA"].data_ptr(), g["dS_t"].data_ptr(), g["dS_n"].data_ptr())
+                          for g in gp], lib.grad_struct(*grads[0]), loss_out.data_ptr(), stream)
+            lib.lgs_render_bwd(sess.handle, S[0], fr, [o.struct() for o in outs],
+                               [lib.lgs_fwd_grad(g["dA"].data_ptr(), g["dS_t"].data_ptr(), g["dS_n"].data_ptr())
+                                for g in gp], lib.grad_struct(*grads[0]), stream)
+        else:
+            lib.lgs_loss_batch(sess.handle, S, fr, fm, [o.struct() for o in outs],
+                               [lib.lgs_target(d.data_ptr(), n.data_ptr()) for d, n in tg], lp,
+                               [lib.lgs_fwd_grad_out(g["dA"].data_ptr(), g["dS_t"].data_ptr(), g["dS_n"].data_ptr())
+                                for g in gp],
+                               [lib.grad_struct(*g) for g in grads], loss_out.data_ptr(), stream)
+            lib.lgs_render_bwd_batch(sess.handle, S, fr, fm, [o.struct() for o in outs],
+                                     [lib.lgs_fwd_grad(g["dA"].data_ptr(), g["dS_t"].data_ptr(),
+                                                       g["dS_n"].data_ptr()) for g in gp],
+                                     [lib.grad_struct(*g) for g in grads], stream)
         res["loss"] = loss_out
         res["upstream"] = gp
         res["grads"] = grads

@@ -20,9 +20,13 @@ dropped from the check):
     n.d, the transmittance before it, the suffix after it, near-threshold
     decisions of the pixel's other entries counted as whole opacities) and
     the would-be contribution of the surfel's own near-threshold decisions; a
-    grazing or near-plane decision makes a surfel's gradient undetermined
-    (inf, counted: < 0.1 % of the street map's surfels, up to 7 % in the
-    grazing-heavy random test shells).
+    grazing decision makes a surfel's gradient undetermined (inf, counted:
+    0.02 % of the street map's surfels, at most 0.75 % in the random test
+    shells).
+
+Beyond that, each case requires the share of values that meet the plain bar
+(no allowance) measured for it on a GB300, less a small margin (PLAIN).
+The allowance itself is pinned on the CPU (tests/test_fp32_allowance.py).
 
 The loss and the backward are each checked on identical inputs: the oracle's
 loss on the GPU's forward outputs, the oracle's backward with the GPU's
@@ -109,6 +113,32 @@ def grazing_ground_seam(seed=12):
 CASES = cases()
 IDS = [c[0] for c in CASES]
 
+# Share of values that must meet the plain bar (without any allowance) and
+# the largest share of undetermined surfel gradients, per case: the fractions
+# measured on a GB300 (forward outputs are reproducible bit for bit; the
+# gradients vary with the order of float atomics) less a small margin, 0.002
+# for the forward and 0.001 for the gradients.  Measured (A, D, gradients):
+#   box_room 0.9705 1.0000 0.99967   shell_32x64 0.9927 1.0000 0.99875
+#   ragged 0.9887 0.9951 0.99857     near_sensor_poles 1.0000 1.0000 1.00000
+#   shell_pose 0.9936 0.9990 0.99917 clamped_opacity 0.9973 0.9998 0.99933
+#   grazing_seam 0.9614 0.9997 0.99839  street (200k) 0.9990 1.0000 0.99994
+# The undetermined surfels (a grazing |n.d| decision within the binary32
+# uncertainty of 1e-6 at some pixel) are those the oracle flags: 0 to 0.75 %.
+PLAIN = {
+    "box_room_32x512": (0.9685, 0.998, 0.9986, 0.0),
+    "shell_32x64": (0.9907, 0.998, 0.9977, 0.0025),
+    "ragged_37x100_8x8": (0.9867, 0.9931, 0.9975, 0.0043),
+    "near_sensor_poles": (0.998, 0.998, 0.999, 0.0),
+    "shell_64x256_8x32_pose": (0.9916, 0.997, 0.9981, 0.0075),
+    "clamped_opacity": (0.9953, 0.9978, 0.9983, 0.0),
+    "grazing_ground_seam": (0.9594, 0.9977, 0.9973, 0.0046),
+    "street_full": (0.997, 0.9980, 0.9989, 0.0002),
+}
+# the other GPU tests (batches, tunings, long lists): the weakest measured
+# case's bars; undetermined 1.8 % was measured for the random shell of the
+# multi-map batch
+DEFAULT_PLAIN = (0.959, 0.993, 0.997, 0.02)
+
 
 @pytest.mark.parametrize("name,surf,frame,tgt", CASES, ids=IDS)
 def test_bins_bit_exact(oracle, name, surf, frame, tgt):
@@ -157,8 +187,9 @@ def test_forward_parity(oracle, name, surf, frame, tgt):
     of = oracle.render_fwd(surf, frame, o["ranges"], o["vals"])
     r = compare_forward(g["fwd"][0], of)
     assert_forward(r)
-    # most pixels meet the plain 1e-5 bar without any uncertainty term
-    assert r["A"][1] > 0.95 and r["D"][1] > 0.99, (r["A"][1], r["D"][1])
+    # the case's measured share of pixels meets the plain bar without any
+    # uncertainty term
+    assert r["A"][1] >= PLAIN[name][0] and r["D"][1] >= PLAIN[name][1], (name, r["A"][1], r["D"][1])
 
 
 def oracle_grads(oracle, surf, frames, ups, scale_reg=True):
@@ -192,11 +223,14 @@ def compare_grads(gg, og, tol=1e-3):
     return out
 
 
-def assert_grads(r):
+def assert_grads(r, case=None):
+    """Every value within its bar; the case's share (or the default) within
+    the plain bar; at most the case's share undetermined."""
+    plain = PLAIN.get(case, DEFAULT_PLAIN)
     for name in ("mean", "quat", "log_scale", "logit"):
         assert r[name][0] <= 1.0, (name, r)
-        assert r[name][1] > 0.99, (name, r)
-    assert r["undetermined"] < 0.1, r
+        assert r[name][1] >= plain[2], (name, case, r)
+    assert r["undetermined"] <= plain[3], (case, r)
 
 
 def gpu_upstream(g, f):
@@ -240,7 +274,7 @@ def test_loss_and_backward_parity(oracle, name, surf, frame, tgt):
     Lo, _, _, _ = oracle.forward_backward(surf, [frame], [(tgt.D, tgt.N)])
     assert g["loss"][0] == pytest.approx(Lo, rel=1e-5)
     og = oracle_grads(oracle, surf, [frame], [gpu_upstream(g, 0)])
-    assert_grads(compare_grads(g["grads"][0], og))
+    assert_grads(compare_grads(g["grads"][0], og), name)
 
 
 NS_CASES = [(c, lam) for c in CASES if c[0] in ("box_room_32x512", "ragged_37x100_8x8", "near_sensor_poles")
@@ -285,7 +319,36 @@ def test_surface_normal_term_parity(oracle, name, surf, frame, tgt, lam_ns):
     Ls = oracle.scale_reg(surf.log_scale)
     assert g["loss"][0] == pytest.approx(Lf + Ls, rel=1e-5)
     og = oracle_grads(oracle, surf, [frame], [gpu_upstream(g, 0)])
-    assert_grads(compare_grads(g["grads"][0], og))
+    assert_grads(compare_grads(g["grads"][0], og), name)
+
+
+SINGLE_CASES = [c for c in CASES if c[0] in ("box_room_32x512", "ragged_37x100_8x8", "near_sensor_poles")]
+
+
+@pytest.mark.parametrize("name,surf,frame,tgt", SINGLE_CASES, ids=[c[0] for c in SINGLE_CASES])
+def test_single_map_calls(oracle, name, surf, frame, tgt):
+    """The single-map calls of the boundary (lgs_bin_sort, lgs_render_fwd,
+    lgs_loss, lgs_render_bwd) called directly through the C ABI: bins equal
+    the oracle's bit for bit; forward outputs and the loss vector equal the
+    batch calls' bit for bit (gradients up to the order of float atomics);
+    forward and gradients match the oracle."""
+    from tests import _gpu
+    g1 = _gpu.run([surf], [frame], targets=[tgt], read_bins=True, single=True)
+    gb = _gpu.run([surf], [frame], targets=[tgt])
+    tp, ip, rg, dk = g1["bins"]
+    o = oracle.bin_frame(surf, frame)
+    keys = (tp.astype(np.uint64) << np.uint64(32)) | dk[ip].astype(np.uint64)
+    assert np.array_equal(keys, o["keys"]) and np.array_equal(ip, o["vals"])
+    assert np.array_equal(rg.astype(np.int64), o["ranges"])
+    for k in ("A", "S_t", "S_n", "T_final", "n_contrib"):
+        assert np.array_equal(g1["fwd"][0][k], gb["fwd"][0][k]), k
+    assert np.array_equal(g1["loss"], gb["loss"])
+    for a, b in zip(g1["grads"][0], gb["grads"][0]):
+        assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
+    of = oracle.render_fwd(surf, frame, o["ranges"], o["vals"])
+    assert_forward(compare_forward(g1["fwd"][0], of))
+    og = oracle_grads(oracle, surf, [frame], [gpu_upstream(g1, 0)])
+    assert_grads(compare_grads(g1["grads"][0], og), name)
 
 
 TUNINGS = ([dict(fwd_batch=0, bwd_batch=0, group=g, persistent=p) for g in (1, 2, 4, 16) for p in (0, 1)]
@@ -445,11 +508,11 @@ def test_full_size_street_frame(oracle):
     of = oracle.render_fwd(surf, frame, o["ranges"], o["vals"])
     r = compare_forward(g["fwd"][0], of)
     assert_forward(r)
-    assert r["A"][1] > 0.99 and r["D"][1] > 0.999, (r["A"][1], r["D"][1])
+    assert r["A"][1] >= PLAIN["street_full"][0] and r["D"][1] >= PLAIN["street_full"][1], (r["A"][1], r["D"][1])
     Limg = check_loss_on_gpu_forward(oracle, g, [frame], [tgt], [1.0])
     assert g["loss"][0] == pytest.approx(Limg + oracle.scale_reg(surf.log_scale), rel=1e-5)
     og = oracle_grads(oracle, surf, [frame], [gpu_upstream(g, 0)])
-    assert_grads(compare_grads(g["grads"][0], og))
+    assert_grads(compare_grads(g["grads"][0], og), "street_full")
 
 
 def _fused_vs_separate(maps, frames, fmap, targets, lambda_ns=0.0):
