@@ -1,29 +1,34 @@
 #!/usr/bin/env python
 """Benchmark: fwd+bwd rays/s of the differentiable spherical surfel rasterizer
 on the 200k-surfel 128 x 1024 street frame (one mapping step = bin + sort,
-forward, mapping loss, backward to every surfel parameter).
+forward, mapping loss, backward to every surfel parameter), with the
+mapping window, the batched uneven maps and the 32-session serving loop as
+sub-objects of the same line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload street|mapping|batched|serving]
+                  [--workload street|mapping|batched|serving|tracking|manage|keyframe]
 
 One process per GPU (torchrun for N > 1); every rank renders its own replica
 of the workload (the path has no exchange step), so scaling is weak and the
 reported value is the sum over ranks.  Prints one JSON line on rank 0.
 
 The reference arm (--impl reference) times the FP64 CPU oracle on the host
-cores on a bounded sample of the same workload.
+cores: K steps (after W warm-up steps), each a bounded band of tile rows of
+the same street frame.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import math
+import multiprocessing
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
 import time
+import concurrent.futures as cf
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -32,23 +37,35 @@ METRIC = "fwd+bwd rays/s at 200k surfels, 128x1024"
 UNIT = "rays/s"
 WORKLOAD = dict(workload="street 200k surfels, 128x1024 range image, +-45 deg", surfels=200_000,
                 H=128, W=1024, frames=1, loss="depth L1 + 0.1 opacity BCE + 0.05 normal cosine + 10 scale")
-# FP32 operations (FMA = 2) counted from the definition: an evaluation forms
-# three dot products with the ray (n.d, a_u.d, a_v.d: 15), t = h/den (1),
-# u, v (4), q (3), exp(-q/2) (2) and alpha G (1) plus the clamp (1) = 27; a
-# composited pair adds T(1-a), w, A, S_t and the flipped normal sum (12); the
-# reverse step of a contributing pair (dL/da through T and the suffix, and the
-# chain to h, n, a_u, b_u, a_v, b_v, alpha as the reverse mode of the
-# evaluation) costs 70.
-FLOP_EVAL = 27
-FLOP_COMPOSITE = 12
-FLOP_BWD_VALID = 70
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x lanes x FMA x max clock
+
+# Algorithmic work per stage of a step (the hot path's measurement budget):
+#   A1 preprocess       112 B per item (40 B parameters in, 64 B record + key
+#                       + box + count out)
+#   A2-A4 bin and sort  12 B per pair emitted, 24 B per pair for one sort pass
+#                       (the per-tile sort reads and writes each key once)
+#   A5 forward          35 FP32 instructions and 2 MUFU (reciprocal, exp2) per
+#                       evaluation up to the stop point; 28 B per pixel out,
+#                       64 B per pair of records read
+#   A6 loss             60 B per pixel
+#   A7 backward         80 FP32 instructions per contributing pair (and 1
+#                       MUFU); 64 B per pair of records read.  The backward
+#                       recomputes the forward per tile, so a second figure
+#                       adds the 35 instructions and 2 MUFU of every
+#                       evaluation up to each pixel's last contributor
+#   A8 chain            130 B per surfel
+# FLOPs (FMA = 2), a secondary figure: 27 per evaluation, 12 more per
+# composited pair, 70 more per contributing pair in the backward.
+B_PREPROCESS, B_EMIT, B_SORT_PASS, B_FWD_PIXEL, B_RECORD = 112, 12, 24, 28, 64
+B_LOSS_PIXEL, B_CHAIN = 60, 130
+I_EVAL, M_EVAL, I_BWD_CONTRIB, M_BWD_CONTRIB = 35, 2, 80, 1
+FLOP_EVAL, FLOP_COMPOSITE, FLOP_BWD_VALID = 27, 12, 70
+FP32_LANES_PER_SM, MUFU_PER_SM = 128, 16
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", default=None, help="tile shape HxW (default: the renderer's)")
@@ -58,11 +75,14 @@ def parse():
     ap.add_argument("--persistent", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0, help="wall-time budget of the reference arm")
     ap.add_argument("--manage-n", type=int, default=2_000_000, help="map size of the manage workload")
     ap.add_argument("--workload", default="street",
                     choices=["street", "mapping", "batched", "serving", "tracking", "manage", "keyframe"],
-                    help="street: the headline line; the others print their own line")
-    ap.add_argument("--no-serving", action="store_true", help="skip the reduced serving run of the street line")
+                    help="street: the headline line (with the mapping, batched and serving sub-objects)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="street line only: skip the mapping, batched and serving sub-objects")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving sub-object")
     ap.add_argument("--serve-seconds", type=float, default=None)
     return ap.parse_args()
 
@@ -119,38 +139,139 @@ def replicas_value(local_seconds: float, units_per_rank: float, world: int, devi
     return t, world * units_per_rank / t
 
 
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def device_peaks(dev_index: int):
+    """Peaks of the GPU the step runs on: SM count queried from the device,
+    maximum SM clock from nvidia-smi (else the measured-peaks record, else
+    the part's 2070 MHz), HBM the measured copy bandwidth (else the 6.8 TB/s
+    fallback)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    mhz, clk_src = None, None
+    try:
+        q = subprocess.run(["nvidia-smi", f"--id={dev_index}", "--query-gpu=clocks.max.sm",
+                            "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+        mhz = float(q.stdout.strip().splitlines()[0])
+        clk_src = "nvidia-smi clocks.max.sm"
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        pass
+    mp = measured_peaks()
+    if mhz is None:
+        mhz, clk_src = float(mp.get("sm_max_mhz", 2070.0)), "MEASURED_PEAKS.json sm_max_mhz"
+    hbm = mp.get("hbm_gbs")
+    return dict(sms=sms, sm_max_mhz=mhz, fp32_instr_per_s=sms * FP32_LANES_PER_SM * mhz * 1e6,
+                mufu_per_s=sms * MUFU_PER_SM * mhz * 1e6, hbm_gbs=hbm if hbm else 6800.0,
+                source=f"{sms} SMs (device properties), {mhz:.0f} MHz ({clk_src}); FP32 issue = SMs x "
+                       f"{FP32_LANES_PER_SM} lanes x clock, MUFU = SMs x {MUFU_PER_SM} x clock; HBM "
+                       + ("measured copy bandwidth" if hbm else "fallback 6.8 TB/s"))
+
+
+def street_config(tuning: dict, tile, world: int = 1) -> dict:
+    """The config both arms report for the street line."""
+    return dict(WORKLOAD, parallelism=f"replicas x{world}", tile=f"{tile[0]}x{tile[1]}", **tuning,
+                l2="flushed between steps (256 MB write); per-step CUDA events, flush not timed")
+
+
+def gen_pool():
+    """A process pool for the seeded input generators, started with spawn
+    before the first CUDA call (the workers import only NumPy code)."""
+    return cf.ProcessPoolExecutor(max_workers=min(32, os.cpu_count() or 1),
+                                  mp_context=multiprocessing.get_context("spawn"))
+
+
 # ---------------------------------------------------------------------------
-def cpu_baseline(seconds: float):
-    """The oracle, as it stands, on the full street frame, repeated for about
-    ``seconds`` of wall time on all host cores."""
-    from oracle import oracle as O
+# The oracle on the host cores (the CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_band(surf, frame, tgt, t0: int, rows: int):
+    """Tile rows [t0, t0 + rows) of the frame as a frame of their own (the same
+    pixel rays, the elevation bounds of the band) with their targets."""
     from paper_2607_04127_gb300 import scenes
+    th = frame.tile_h
+    r0, r1 = t0 * th, min((t0 + rows) * th, frame.H)
+    dth = (frame.elev_max - frame.elev_min) / frame.H
+    band = scenes.Frame(r1 - r0, frame.W, frame.tile_h, frame.tile_w, frame.elev_max - r1 * dth,
+                        frame.elev_max - r0 * dth, frame.pose)
+    return band, tgt.D[r0:r1].copy(), tgt.N[:, r0:r1].copy()
+
+
+def oracle_step(O, surf, band):
+    """One fwd + loss + bwd pass of the FP64 oracle over a band: the method
+    alone, on all host cores (OpenMP over tiles)."""
+    frame, D, N = band
+    O.forward_backward(surf, [frame], [(D, N)], nthreads=0, allowance=False)
+
+
+def street_for_oracle():
+    from oracle import oracle as O
+    from paper_2607_04127_gb300 import render, scenes
     O.build()
     surf, frame, tgt = scenes.street()
-    reps = 0
-    t0 = time.perf_counter()
-    while True:
-        O.forward_backward(surf, [frame], [(tgt.D, tgt.N)], nthreads=0)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or reps >= 50:
-            break
+    return O, surf, frame.with_tiles(*render.DEFAULT_TILE), tgt
+
+
+def cpu_baseline(seconds: float):
+    """The oracle, as it stands, on bands of 4 tile rows of the street frame
+    (cycling through the frame) for about ``seconds`` of wall time."""
+    O, surf, frame, tgt = street_for_oracle()
+    ntr = -(-frame.H // frame.tile_h)
+    rows, k, pix, el = 4, 0, 0, 0.0
+    while el < seconds or k == 0:
+        band = oracle_band(surf, frame, tgt, (k * rows) % ntr, rows)
+        t0 = time.perf_counter()
+        oracle_step(O, surf, band)
+        el += time.perf_counter() - t0
+        pix += band[0].H * band[0].W
+        k += 1
     cores = os.cpu_count() or 1
-    return dict(value=reps * frame.H * frame.W / el, unit=UNIT, cores=cores, kind="oracle",
-                sample=f"{reps} full fwd+loss+bwd passes of the street frame (FP64 oracle, OpenMP over tiles, "
-                       f"{cores} threads) in {el:.1f} s")
+    return dict(value=pix / el, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{k} bands of {rows} tile rows ({rows * frame.tile_h} x {frame.W} rays each) of the street "
+                       f"frame: FP64 oracle fwd + loss + bwd, the method without its test allowance, OpenMP over "
+                       f"tiles on {cores} threads, {el:.1f} s")
 
 
 def run_reference(args):
+    """The reference arm: the oracle on the host cores, --warmup untimed and
+    --steps timed steps, each one band of tile rows of the street frame sized
+    so that the whole run takes about --ref-seconds."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    cb = cpu_baseline(args.cpu_seconds)
-    line = dict(metric=METRIC, value=cb["value"], unit=UNIT, n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=1e3 * WORKLOAD["H"] * WORKLOAD["W"] / cb["value"],
-                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(WORKLOAD, parallelism="host cores"), impl="reference", cpu_baseline=cb,
-                e2e=dict(value=cb["value"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    from paper_2607_04127_gb300 import render
+    O, surf, frame, tgt = street_for_oracle()
+    ntr = -(-frame.H // frame.tile_h)
+    # calibrate on one band of 2 tile rows (the first warm-up step)
+    t0 = time.perf_counter()
+    oracle_step(O, surf, oracle_band(surf, frame, tgt, 0, 2))
+    per_row = (time.perf_counter() - t0) / 2
+    W, K = max(args.warmup, 1), max(args.steps, 1)
+    rows = int(min(ntr, max(1, math.floor(args.ref_seconds / (K + W) / max(per_row, 1e-6)))))
+    for w in range(W - 1):
+        oracle_step(O, surf, oracle_band(surf, frame, tgt, (w * rows) % ntr, rows))
+    ms, pix = [], 0
+    for k in range(K):
+        band = oracle_band(surf, frame, tgt, (k * rows) % ntr, rows)
+        t0 = time.perf_counter()
+        oracle_step(O, surf, band)
+        ms.append((time.perf_counter() - t0) * 1e3)
+        pix += band[0].H * band[0].W
+    el = sum(ms) / 1e3
+    value = pix / el
+    cores = os.cpu_count() or 1
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=K, warmup=W,
+                ms_per_step=statistics.mean(ms), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic (seeded street scene, see scenes.street)",
+                config=street_config(dict(render.DEFAULT_TUNING), render.DEFAULT_TILE, world), impl="reference",
+                cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle",
+                                  sample=f"each step one band of {rows} of {ntr} tile rows ({rows * frame.tile_h} x "
+                                         f"{frame.W} rays) of the street frame, bands cycling; FP64 oracle fwd + "
+                                         f"loss + bwd, the method without its test allowance, {cores} threads"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
 
@@ -216,14 +337,19 @@ class Clocks:
                     reasons=reasons, samples=len(rows))
 
 
+
+
 # ---------------------------------------------------------------------------
-def serving_work(n_sessions, sizes_range, seed=0, shapes=((128, 1024),)):
+# Mapping window, batched maps, serving: sub-objects of the street line (and
+# lines of their own with --workload)
+# ---------------------------------------------------------------------------
+def serving_work(n_sessions, sizes_range, seed=0, shapes=((128, 1024),), pool=None):
     """Maps with log-uniform sizes in ``sizes_range``, one keyframe each."""
     import numpy as np
     from paper_2607_04127_gb300 import render, scenes
     rng = np.random.default_rng(seed)
     sizes = np.exp(rng.uniform(np.log(sizes_range[0]), np.log(sizes_range[1]), n_sessions)).astype(int)
-    return scenes.street_maps(seed, [int(x) for x in sizes], list(shapes), tile=render.DEFAULT_TILE)
+    return scenes.street_maps(seed, [int(x) for x in sizes], list(shapes), tile=render.DEFAULT_TILE, pool=pool)
 
 
 def serving_run(work, seconds, seed=0, plain=False, slots=16, iters=10, budget=150 << 30, keep_latest=True,
@@ -232,123 +358,153 @@ def serving_run(work, seconds, seed=0, plain=False, slots=16, iters=10, budget=1
     ``iters``-iteration render-and-optimise requests for its keyframe;
     returns the latency statistics.  ``slo_ms``: deadline admission."""
     import numpy as np
+    import torch
     from paper_2607_04127_gb300 import serve
     rng = np.random.default_rng(seed)
     srv = serve.Server(hbm_budget_bytes=budget, slots=slots, plain=plain, keep_latest=keep_latest, slo_ms=slo_ms)
-    sids = []
-    for sid, (surf, fr, _) in enumerate(work):
-        if srv.open_session(sid, surf, fr.H * fr.W):
-            sids.append(sid)
+    sids = [sid for sid, (surf, fr, _) in enumerate(work) if srv.open_session(sid, surf, fr.H * fr.W) != "rejected"]
     reqs = serve.poisson_requests(rng, sids, lambda sid, k: work[sid][1], lambda sid, k: work[sid][2], seconds,
                                   rate_range=rates, iters=iters)
-    # warm-up request (kernels, workspace), not timed
-    srv.run([serve.Request(sids[0], work[sids[0]][1], work[sids[0]][2], 0.0, 2)])
+    # warm-up requests (kernels, workspace, tick model), not timed
+    srv.run([serve.Request(sid, work[sid][1], work[sid][2], 0.0, 2) for sid in sids[:slots]])
     srv.dropped.clear()
     srv.late.clear()
-    done = srv.run(reqs)
+    srv.unserved.clear()
+    torch.cuda.synchronize()
+    with Clocks(0) as clk:
+        done = srv.run(reqs)
     st = serve.latency_stats(done, seconds, len(reqs), len(srv.rejected_sessions), len(work), len(srv.dropped),
-                             len(srv.late))
+                             len(srv.late), len(srv.unserved), len(srv.admitted_late) + len(srv.session_queue),
+                             srv.overflow_ticks)
     sizes = [s.n for s, _, _ in work]
     mode = "plain per-request" if plain else f"continuous batching, {slots} slots"
     if slo_ms:
         mode += f", deadline admission {slo_ms:g} ms"
     st.update(sessions=len(work), map_sizes=[int(min(sizes)), int(max(sizes))], seconds=seconds, iters=iters,
-              rate_hz=list(rates), keep_latest=keep_latest, mode=mode)
+              rate_hz=list(rates), keep_latest=keep_latest, mode=mode, budget_gb=budget / 2 ** 30,
+              loss_first_mean=float(np.mean([r.losses[0] for r in done])) if done else None,
+              loss_last_mean=float(np.mean([r.losses[-1] for r in done])) if done else None,
+              clocks=clk.summary())
     srv.close()
     return st
 
 
-def run_mapping(args):
-    """Differentiable mapping window: 1M-surfel street track, 8 keyframes
-    (128 x 1024) rendered together, 10 Adam iterations; fused and autograd
-    drivers."""
+def mapping_sub(pool=None, inputs=None):
+    """Differentiable mapping window: the 1M-surfel street track, 8 keyframes
+    (128 x 1024) rendered together, 10 Adam iterations; the fused driver and
+    the autograd.Function driver."""
     import torch
-    from paper_2607_04127_gb300 import build, mapping, render, scenes
-    build.build()
-    surf, frames, targets = scenes.street_track()
+    from paper_2607_04127_gb300 import mapping, render, scenes
+    surf, frames, targets = inputs if inputs is not None else scenes.street_track(pool=pool)
     frames = [f.with_tiles(*render.DEFAULT_TILE) for f in frames]
     res = {}
-    for ag in (False, True):
-        w = mapping.MappingWindow(surf, frames, targets, autograd=ag)
-        w.run(2)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        L = w.run(10)
-        b.record()
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b)
-        rays = 10 * sum(f.H * f.W for f in frames)
-        res["autograd" if ag else "fused"] = dict(ms_per_iteration=ms / 10, rays_per_s=rays / (ms / 1e3),
-                                                  loss_first=float(L[0]), loss_last=float(L[-1]))
-        w.close()
-    line = dict(metric="mapping window rays/s (1M surfels, 8 keyframes 128x1024, 10 Adam iterations)",
-                value=res["fused"]["rays_per_s"], unit="rays/s", higher_is_better=True, dtype="f32",
-                data="synthetic (seeded 200 m street track, scenes.street_track)", n_gpus=1,
-                config=dict(workload="mapping window", surfels=surf.n, keyframes=len(frames), iterations=10,
-                            tile="%dx%d" % render.DEFAULT_TILE), drivers=res)
-    print(json.dumps(line), flush=True)
+    with Clocks(0) as clk:
+        for ag in (False, True):
+            w = mapping.MappingWindow(surf, frames, targets, autograd=ag)
+            w.run(2)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            L = w.run(10)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            rays = 10 * sum(f.H * f.W for f in frames)
+            res["autograd" if ag else "fused"] = dict(ms_per_iteration=ms / 10, rays_per_s=rays / (ms / 1e3),
+                                                      loss_first=float(L[0]), loss_last=float(L[-1]))
+            w.close()
+    return dict(metric="mapping window rays/s (1M surfels, 8 keyframes 128x1024, 10 Adam iterations)",
+                value=res["fused"]["rays_per_s"], unit="rays/s", surfels=surf.n, keyframes=len(frames),
+                iterations=10, tile="%dx%d" % render.DEFAULT_TILE, drivers=res, clocks=clk.summary(),
+                data="synthetic (seeded 200 m street track, scenes.street_track)")
 
 
-def run_batched(args):
+def batched_inputs(pool=None):
+    from paper_2607_04127_gb300 import render, scenes
+    sizes = ([50_000, 100_000, 250_000, 500_000, 1_000_000, 2_000_000] * 3)[:16]
+    return scenes.street_maps(1, sizes, [(64, 1024), (128, 1024), (128, 2048)], tile=render.DEFAULT_TILE, pool=pool)
+
+
+def batched_sub(pool=None, inputs=None):
     """Sixteen independent maps of 50k..2M surfels with 64x1024 / 128x1024 /
     128x2048 frames: one call per stage (autotuned, persistent, CUDA graph)
     against sixteen sequential plain launches."""
     import torch
-    from paper_2607_04127_gb300 import autotune, batched, build, render, scenes
-    build.build()
-    sizes = [50_000, 100_000, 250_000, 500_000, 1_000_000, 2_000_000] * 3
-    sizes = sizes[:16]
-    work = scenes.street_maps(1, sizes, [(64, 1024), (128, 1024), (128, 2048)], tile=render.DEFAULT_TILE)
+    from paper_2607_04127_gb300 import autotune, batched, render, scenes
+    work = inputs if inputs is not None else batched_inputs(pool)
     maps, frames, targets = zip(*work)
+    sizes = [m.n for m in maps]
     rays = sum(f.H * f.W for f in frames)
     steps = 10
-    seq = batched.SequentialMaps(maps, frames, targets)
-    t_seq = autotune.time_steps(seq, steps)
-    seq.close()
+    with Clocks(0) as clk:
+        seq = batched.SequentialMaps(maps, frames, targets)
+        t_seq = autotune.time_steps(seq, steps)
+        seq.close()
 
-    def make(tile, tun):
-        return batched.BatchedMaps(maps, [f.with_tiles(*tile) for f in frames], targets, tuning=tun)
+        def make(tile, tun):
+            return batched.BatchedMaps(maps, [f.with_tiles(*tile) for f in frames], targets, tuning=tun)
 
-    tile, tun, log = autotune.autotune(make, steps=3)
-    B = make(tile, tun)
-    B.capture()
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(steps):
-        B.replay()
-    b.record()
-    torch.cuda.synchronize()
-    B.rast.session.check_status()
-    t_b = a.elapsed_time(b) / steps
-    B.close()
-    line = dict(metric="batched fwd+bwd rays/s, 16 uneven maps (8.7M surfels) in one launch per stage",
-                value=rays / (t_b / 1e3), unit="rays/s", higher_is_better=True, dtype="f32", n_gpus=1,
-                data="synthetic (seeded street maps, scenes.street_maps)",
-                config=dict(workload="16 maps 50k-2M surfels, 64x1024/128x1024/128x2048", surfels=int(sum(sizes)),
-                            rays=rays, tile="%dx%d" % tile, **tun, graph=True),
-                ms_per_step=t_b, sequential=dict(ms_per_step=t_seq, rays_per_s=rays / (t_seq / 1e3),
-                                                 tile="%dx%d" % render.DEFAULT_TILE),
-                speedup_vs_sequential=t_seq / t_b, autotune_ms=log)
-    print(json.dumps(line), flush=True)
+        tile, tun, log = autotune.autotune(make, steps=3)
+        B = make(tile, tun)
+        B.capture()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            B.replay()
+        b.record()
+        torch.cuda.synchronize()
+        B.rast.session.check_status()
+        t_b = a.elapsed_time(b) / steps
+        B.close()
+    return dict(metric="batched fwd+bwd rays/s, 16 uneven maps (8.7M surfels) in one launch per stage",
+                value=rays / (t_b / 1e3), unit="rays/s", surfels=int(sum(sizes)), rays=rays,
+                config=dict(tile="%dx%d" % tile, **tun, graph=True), ms_per_step=t_b,
+                sequential=dict(ms_per_step=t_seq, rays_per_s=rays / (t_seq / 1e3),
+                                tile="%dx%d" % render.DEFAULT_TILE),
+                speedup_vs_sequential=t_seq / t_b, autotune_ms=log, clocks=clk.summary(),
+                data="synthetic (seeded street maps, scenes.street_maps)")
+
+
+def serving32_sub(seconds: float, pool=None, inputs=None):
+    """Thirty-two sessions (100k..2M surfels), Poisson 10-20 Hz each, 10
+    iterations per request, 150 GB budget: continuous batching, deadline
+    admission (50 ms) and per-request plain launches."""
+    work = inputs if inputs is not None else serving_work(32, (100_000, 2_000_000), seed=2, pool=pool)
+    b = serving_run(work, seconds, seed=2)
+    d = serving_run(work, seconds, seed=2, slo_ms=50.0)
+    p = serving_run(work, seconds, seed=2, plain=True)
+    return dict(metric="serving p50/p99 frame latency and frames/s, 32 mapping sessions", value=d["p99_ms"],
+                unit="ms (p99, deadline admission 50 ms)", higher_is_better=False,
+                data="synthetic (seeded street maps, Poisson request streams)", serving_slo=d, serving=b, plain=p)
+
+
+def _standalone(args, fn, **kw):
+    from paper_2607_04127_gb300 import build
+    pool = gen_pool()
+    try:
+        build.build()
+        import torch
+        torch.cuda.set_device(0)
+        sub = fn(pool=pool, **kw)
+    finally:
+        pool.shutdown()
+    sub.setdefault("higher_is_better", True)
+    sub.update(n_gpus=1, dtype="f32")
+    print(json.dumps(sub), flush=True)
+
+
+def run_mapping(args):
+    _standalone(args, mapping_sub)
+
+
+def run_batched(args):
+    _standalone(args, batched_sub)
 
 
 def run_serving(args):
-    """Thirty-two sessions (100k..2M surfels), Poisson 10-20 Hz each, 10
-    iterations per request, 150 GB budget: continuous batching against
-    per-request plain launches."""
-    from paper_2607_04127_gb300 import build
-    build.build()
-    secs = args.serve_seconds or 10.0
-    work = serving_work(32, (100_000, 2_000_000), seed=2)
-    b = serving_run(work, secs, seed=2)
-    d = serving_run(work, secs, seed=2, slo_ms=50.0)
-    p = serving_run(work, secs, seed=2, plain=True)
-    line = dict(metric="serving p50/p99 frame latency and frames/s, 32 mapping sessions", value=d["p99_ms"],
-                unit="ms (p99, deadline admission 50 ms)", higher_is_better=False, dtype="f32", n_gpus=1,
-                data="synthetic (seeded street maps, Poisson request streams)", serving_slo=d, serving=b, plain=p)
-    print(json.dumps(line), flush=True)
+    _standalone(args, serving32_sub, seconds=args.serve_seconds or 10.0)
+
 
 
 def run_tracking(args):
@@ -573,7 +729,8 @@ def run_keyframe(args):
     cpu_s = time.perf_counter() - t0
     # ALU roofline: 8 FP32 operations per evaluated distance (3 sub, 3 mul,
     # 2 add) against one operation per FP32 lane per clock
-    lanes_peak = 152 * 128 * 2.07e9 / 1e12
+    pk = device_peaks(0)
+    lanes_peak = pk["fp32_instr_per_s"] / 1e12
     achieved = n_pairs * 8 / step_s / 1e12
     line = dict(metric="keyframe initialisation: points/s (exact 20-NN covariance, eigendecomposition, scale, "
                        "confidence, opacity)",
@@ -585,8 +742,8 @@ def run_keyframe(args):
                             l2="flushed between steps (256 MB write)"),
                 roofline=dict(bound="alu", kernel="whole call (k-NN dominant)", achieved=achieved,
                               peak=lanes_peak, unit="Tops/s", frac=achieved / lanes_peak, traffic=None,
-                              note="8 FP32 operations per evaluated distance over the call's CUDA-event time; "
-                                   "peak = 152 SMs x 128 FP32 lanes x 2.07 GHz"),
+                              note="8 FP32 operations per evaluated distance over the call's CUDA-event time",
+                              peak_source=pk["source"]),
                 e2e=dict(value=n / e2e_s, unit="points/s", h2d_bytes_per_step=n * 12, d2h_bytes_per_step=d2h),
                 cpu_baseline=dict(value=done / cpu_s, unit="points/s", cores=1, kind="oracle",
                                   sample=f"{done} sampled rows of the same scan in {cpu_s:.1f} s (NumPy brute-force "
@@ -595,10 +752,73 @@ def run_keyframe(args):
     print(json.dumps(line), flush=True)
 
 
+
+
+# ---------------------------------------------------------------------------
+# The street line
+# ---------------------------------------------------------------------------
+def street_roofline(pk, kernels_ms, ms_step, c, n_items, hw, n_surf, tuning):
+    """Per-stage roofline of a street step from the measurement budget above
+    (max of bytes / HBM, FP32 instructions / FP32 issue, MUFU / MUFU issue per
+    stage), the step fraction (sum of the stage rooflines over the measured
+    step), and the dominant compositing kernel in instruction units."""
+    P, E_f, E_b, C = c["pairs"], c["alg_f"], c["alg_b"], c["contrib"]
+    hbm = pk["hbm_gbs"] * 1e9
+
+    def stage(name, ms, byts=0.0, instr=0.0, mufu=0.0):
+        t = {"hbm": byts / hbm, "alu": instr / pk["fp32_instr_per_s"], "mufu": mufu / pk["mufu_per_s"]}
+        bound = max(t, key=t.get)
+        return dict(stage=name, ms=ms, roofline_ms=t[bound] * 1e3, bound=bound,
+                    frac=t[bound] * 1e3 / ms if ms else None, bytes=byts, fp32_instr=instr, mufu=mufu)
+
+    stages = [
+        stage("bin and sort (A1-A4)", kernels_ms["bin"],
+              B_PREPROCESS * n_items + B_EMIT * P + B_SORT_PASS * P),
+        stage("forward with the loss epilogue (A5, A6)", kernels_ms["fwd"],
+              B_FWD_PIXEL * hw + B_RECORD * P + B_LOSS_PIXEL * hw, I_EVAL * E_f, M_EVAL * E_f),
+        stage("mask counts, scale regulariser, loss vector (A6)", kernels_ms["loss"], 16 * hw + 16 * n_surf),
+        stage("backward (A7)", kernels_ms["bwd"], B_RECORD * P, I_BWD_CONTRIB * C, M_BWD_CONTRIB * C),
+        stage("chain to the parameters (A8)", kernels_ms["bwd_chain"], B_CHAIN * n_surf),
+    ]
+    bwd_re = stage("backward (A7) with its re-evaluation", kernels_ms["bwd"], B_RECORD * P,
+                   I_BWD_CONTRIB * C + I_EVAL * E_b, M_BWD_CONTRIB * C + M_EVAL * E_b)
+    roof = sum(s["roofline_ms"] for s in stages)
+    roof_re = roof - stages[3]["roofline_ms"] + bwd_re["roofline_ms"]
+    dom = "bwd" if kernels_ms["bwd"] >= kernels_ms["fwd"] else "fwd"
+    t_dom = kernels_ms[dom] / 1e3
+    instr = I_BWD_CONTRIB * C if dom == "bwd" else I_EVAL * E_f
+    instr_re = I_BWD_CONTRIB * C + I_EVAL * E_b if dom == "bwd" else instr
+    flops = (FLOP_EVAL * E_b + FLOP_BWD_VALID * C) if dom == "bwd" else (FLOP_EVAL * E_f + FLOP_COMPOSITE * C)
+    peak = pk["fp32_instr_per_s"] / 1e12
+    return dict(bound="alu", kernel=kname(tuning, dom), achieved=instr / t_dom / 1e12, peak=peak, unit="Tinstr/s",
+                frac=instr / t_dom / 1e12 / peak, traffic=measured_traffic(kname(tuning, dom)),
+                achieved_with_reevaluation=instr_re / t_dom / 1e12, frac_with_reevaluation=instr_re / t_dom / 1e12 / peak,
+                frac_step=roof / ms_step, frac_step_with_reevaluation=roof_re / ms_step, roofline_step_ms=roof,
+                stages=stages, peak_source=pk["source"],
+                flops=dict(achieved=flops / t_dom / 1e12, peak=2 * peak, unit="TFLOP/s", frac=flops / t_dom / 1e12 / (2 * peak),
+                           note="FMA = 2; 27 FLOP per evaluation, 12 per composited, 70 per contributing pair"))
+
+
 def run_ours(args):
+    import threading
+    rank, world, local = dist_env()
+    extras = world == 1 and not args.no_extras
+    pool, box, gen = None, {}, None
+    if extras:
+        # the sub-objects' inputs are generated on the host cores while the
+        # street frame is set up, and are complete before its timed region
+        pool = gen_pool()
+        from paper_2607_04127_gb300 import scenes
+
+        def produce():
+            box["mapping"] = scenes.street_track(pool=pool)
+            box["batched"] = batched_inputs(pool)
+            if not args.no_serving:
+                box["serving"] = serving_work(32, (100_000, 2_000_000), seed=2, pool=pool)
+        gen = threading.Thread(target=produce, daemon=True)
+        gen.start()
     import torch
     import torch.distributed as dist
-    rank, world, local = dist_env()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
@@ -626,14 +846,19 @@ def run_ours(args):
         rast.step([params], targets, grads)
     torch.cuda.synchronize()
     rast.session.check_status()
+    if gen is not None:
+        gen.join()
+        pool.shutdown()
+    pk = device_peaks(dev.index)
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     c0 = rast.counters()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with Clocks(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(dev.index)).split(",")[0])
-                if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else dev.index) as clk:
+    gpu_id = int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[0]) if os.environ.get(
+        "CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else dev.index
+    with Clocks(gpu_id) as clk:
         t_wall = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
@@ -644,32 +869,27 @@ def run_ours(args):
             rast.forward_loss([params], targets, grads[0:1], S)   # loss in the forward's epilogue
             e[2].record(stream)
             rast.backward([params], grads, S=S)
-            e[4].record(stream)
+            e[3].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
     rast.session.check_status()
     c1 = rast.counters()
-    step_ms = [e[0].elapsed_time(e[4]) for e in ev]
-    fwd_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    bwd_ms = [e[2].elapsed_time(e[4]) for e in ev]
-    bin_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    clocks = clk.summary()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     rays = frame.H * frame.W
     total_s, value = replicas_value(sum(step_ms) / 1e3, args.steps * rays, world, dev)
+    ms_step = total_s * 1e3 / args.steps
+    launches_per_step = (c1["launches"] - c0["launches"]) / args.steps
 
     # algorithmic work of one step (counters are cumulative since the last
     # bin_sort): forward = list entries up to each pixel's stop point, backward
-    # = entries up to each pixel's last contributor (the sum of n_contrib)
+    # = entries up to each pixel's last contributor (the sum of n_contrib);
+    # the backward's contributing pairs are the forward's composited pairs
     c_last = rast.counters()
-    evf, evb = c_last["evals_fwd"], c_last["evals_bwd"]
-    cf, cb_ = c_last["contrib_fwd"], c_last["contrib_bwd"]
-    alg_f = c_last["alg_fwd"]
-    alg_b = int(rast.out[0].n_contrib.sum().item())
-    fl_fwd = FLOP_EVAL * alg_f + FLOP_COMPOSITE * cf
-    # the backward's contributing pairs are exactly the forward's composited
-    # pairs (the chunked backward does not count them again)
-    fl_bwd = FLOP_EVAL * alg_b + FLOP_BWD_VALID * cf
+    work = dict(pairs=c_last["n_pairs"], alg_f=c_last["alg_fwd"], alg_b=int(rast.out[0].n_contrib.sum().item()),
+                contrib=c_last["contrib_fwd"])
 
     # device time of every kernel group, from events the library records
     # around its own launches on this stream (a separate pass of the same steps)
@@ -683,10 +903,7 @@ def run_ours(args):
     kt = rast.kernel_times()
     rast.set_timing(False)
     kernels_ms = {g: (ms / n if n else 0.0) for g, (ms, n) in kt.items()}
-    fwd_s, bwd_s = kernels_ms["fwd"] / 1e3, kernels_ms["bwd"] / 1e3
-    dominant = "bwd" if bwd_s >= fwd_s else "fwd"
-    achieved = (fl_bwd / bwd_s if dominant == "bwd" else fl_fwd / fwd_s) / 1e12
-    launches_per_step = (c1["launches"] - c0["launches"]) / args.steps
+    roof = street_roofline(pk, kernels_ms, ms_step, work, surf.n, rays, surf.n, rast.tuning)
 
     # end to end through the public API with host buffers
     host = [p.cpu().pin_memory() for p in params]
@@ -716,48 +933,42 @@ def run_ours(args):
         ee[k][1].record(stream)
     torch.cuda.synchronize()
     e2e_s, e2e_value = replicas_value(sum(e[0].elapsed_time(e[1]) for e in ee) / 1e3, e2e_steps * rays, world, dev)
+    rast.close()
 
+    sub = {}
+    if extras and rank == 0:
+        sub["mapping"] = mapping_sub(inputs=box["mapping"])
+        sub["batched"] = batched_sub(inputs=box["batched"])
+        if not args.no_serving:
+            sub["serving"] = serving32_sub(args.serve_seconds or 5.0, inputs=box["serving"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
-    serving = None
-    if rank == 0 and not args.no_serving:
-        rast.close()
-        work = serving_work(8, (100_000, 400_000), seed=4)
-        serving = serving_run(work, args.serve_seconds or 2.0, seed=4, iters=10)
-        serving_slo = serving_run(work, args.serve_seconds or 2.0, seed=4, iters=10, slo_ms=50.0)
-    clocks = clk.summary()
     if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
         return
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
-        ms_per_step=total_s * 1e3 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="f32", data="synthetic (seeded street scene, see scenes.street)",
-        config=dict(WORKLOAD, parallelism=f"replicas x{world}", tile=f"{tile[0]}x{tile[1]}", **rast.tuning,
-                    l2="flushed between steps (256 MB write); per-step CUDA events, flush not timed"),
-        evals_per_s=world * args.steps * (alg_f + alg_b) / total_s,
-        stages_ms=dict(bin_sort=statistics.mean(bin_ms), fwd_loss=statistics.mean(fwd_ms),
-                       bwd=statistics.mean(bwd_ms)),
+        config=street_config(rast.tuning, tile, world),
+        evals_per_s=world * args.steps * (work["alg_f"] + work["alg_b"]) / total_s,
+        stages_ms={k: statistics.mean([e[i].elapsed_time(e[i + 1]) for e in ev])
+                   for i, k in enumerate(("bin_sort", "fwd_loss", "bwd"))},
         kernels_ms=kernels_ms,
-        work=dict(pairs=c_last["n_pairs"], visible_items=c_last["n_visible"], alg_evals_fwd=alg_f,
-                  alg_evals_bwd=alg_b, culled_evals_fwd=evf, culled_evals_bwd=evb or None, composited_fwd=cf,
-                  valid_bwd=cb_ or cf),
-        roofline=dict(bound="alu", kernel=kname(rast.tuning, dominant), achieved=achieved,
-                      peak=PEAK_FP32_TFLOPS, unit="TFLOP/s", frac=achieved / PEAK_FP32_TFLOPS,
-                      traffic=measured_traffic(kname(rast.tuning, dominant)),
-                      peak_source="derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz"),
+        work=dict(pairs=work["pairs"], visible_items=c_last["n_visible"], alg_evals_fwd=work["alg_f"],
+                  alg_evals_bwd=work["alg_b"], culled_evals_fwd=c_last["evals_fwd"],
+                  composited_fwd=work["contrib"]),
+        roofline=roof,
         e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
         gpu_launches=int(round(launches_per_step * args.steps)),
         clocks=clocks, wall_s=t_wall,
     )
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    if serving is not None:
-        line["serving"] = serving
-        line["serving_slo"] = serving_slo
+    line.update(sub)
     print(json.dumps(line), flush=True)
-    if serving is None:
-        rast.close()
     if world > 1:
         dist.destroy_process_group()
 

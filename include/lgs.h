@@ -197,6 +197,30 @@ LGS_API lgs_status lgs_session_set_workspace(lgs_session s, void* dev_ptr, size_
  * LGS_ERR_TIMEOUT or LGS_ERR_DEVICE_CHECK.  required_pairs may be NULL. */
 LGS_API lgs_status lgs_session_status(lgs_session s, int64_t* required_pairs);
 
+/* The head of the device status word, as lgs_session_status_enqueue copies
+ * it: pairs the last lgs_bin_sort needed and emitted, items covering a tile,
+ * and the error flags (nonzero: capacity overflow, a bounded wait that gave
+ * up, a failed device bounds check). */
+typedef struct {
+    uint64_t required_pairs, n_pairs;
+    uint32_t n_visible, overflow, timeout, check;
+} lgs_status_word;
+
+/* Non-blocking form of lgs_session_status: enqueue on `stream` a copy of the
+ * status word as it stands when the stream reaches this point (after the
+ * session's last lgs_bin_sort and the calls after it) into *out, which must
+ * be pinned host memory of sizeof(lgs_status_word) bytes.  No host
+ * synchronisation: the caller decodes *out with lgs_status_of_word once an
+ * event recorded after this call has completed (a serving loop keeps
+ * several steps in flight this way).  LGS_ERR_STATE before any
+ * lgs_bin_sort. */
+LGS_API lgs_status lgs_session_status_enqueue(lgs_session s, lgs_status_word* out, void* stream);
+
+/* The status a copied word reports: LGS_OK, LGS_ERR_CAPACITY,
+ * LGS_ERR_TIMEOUT or LGS_ERR_DEVICE_CHECK (LGS_ERR_INVALID_ARG if w is
+ * NULL).  Pure host function. */
+LGS_API lgs_status lgs_status_of_word(const lgs_status_word* w);
+
 /* Synchronise and return the pair count of the last bin_sort. */
 LGS_API lgs_status lgs_session_pair_count(lgs_session s, int64_t* n_pairs);
 

@@ -190,8 +190,10 @@ def _frame_args(frame):
             float(np.float32(frame.elev_max)), _c(np.asarray(frame.pose, np.float32), np.float64))
 
 
-def render_fwd(surfels, frame, ranges, vals, params64=None, nthreads: int = 0):
-    """FP64 forward of one frame over the given tile lists."""
+def render_fwd(surfels, frame, ranges, vals, params64=None, nthreads: int = 0, allowance: bool = True):
+    """FP64 forward of one frame over the given tile lists.  allowance=False
+    skips the binary32 allowance (flags, fp32_err_A / fp32_err_D are zero):
+    the method alone, as the CPU baseline times it."""
     lib = _load()
     m, q, ls, lg = params64 if params64 is not None else _params64(surfels)
     H, W = frame.H, frame.W
@@ -201,8 +203,8 @@ def render_fwd(surfels, frame, ranges, vals, params64=None, nthreads: int = 0):
     fa = _frame_args(frame)
     lib.lgso_render_fwd(_p(m), _p(q), _p(ls), _p(lg), m.shape[0], *fa[:6], _p(fa[6]),
                         _p(_c(ranges, np.int64)), _p(_c(vals, np.uint32)),
-                        _p(A), _p(St), _p(Sn), _p(Tf), _p(nc), _p(ne), _p(fl), _p(nv), _p(eA), _p(eD),
-                        int(nthreads))
+                        _p(A), _p(St), _p(Sn), _p(Tf), _p(nc), _p(ne), _p(fl) if allowance else None, _p(nv),
+                        _p(eA) if allowance else None, _p(eD) if allowance else None, int(nthreads))
     return dict(A=A.reshape(H, W), S_t=St.reshape(H, W), S_n=Sn.reshape(3, H, W),
                 T_final=Tf.reshape(H, W), n_contrib=nc.reshape(H, W), n_eval=ne.reshape(H, W),
                 flags=fl.reshape(H, W), n_valid=nv.reshape(H, W), fp32_err_A=eA.reshape(H, W),
@@ -219,8 +221,9 @@ def coverage_misses(surfels, frame, ranges, vals, params64=None) -> int:
 
 
 def render_bwd(surfels, frame, ranges, vals, gA, gSt, gSn, params64=None, grads=None,
-               nthreads: int = 0):
-    """FP64 backward of one frame; accumulates into ``grads`` (dict of arrays)."""
+               nthreads: int = 0, allowance: bool = True):
+    """FP64 backward of one frame; accumulates into ``grads`` (dict of arrays).
+    allowance=False skips the binary32 allowance (abs / flip untouched)."""
     lib = _load()
     m, q, ls, lg = params64 if params64 is not None else _params64(surfels)
     n = m.shape[0]
@@ -232,7 +235,8 @@ def render_bwd(surfels, frame, ranges, vals, gA, gSt, gSn, params64=None, grads=
                         _p(_c(ranges, np.int64)), _p(_c(vals, np.uint32)),
                         _p(_c(gA, np.float64)), _p(_c(gSt, np.float64)), _p(_c(gSn, np.float64)),
                         _p(grads["mean"]), _p(grads["quat"]), _p(grads["log_scale"]), _p(grads["logit"]),
-                        _p(grads["abs"]), _p(grads["flip"]), int(nthreads))
+                        _p(grads["abs"]) if allowance else None, _p(grads["flip"]) if allowance else None,
+                        int(nthreads))
     return grads
 
 
@@ -334,10 +338,11 @@ def scale_reg(log_scale, s_max=S_MAX, lam_s=LAMBDA_S, dls=None):
 
 def forward_backward(surfels, frames, targets, lam_alpha=LAMBDA_ALPHA, lam_n=LAMBDA_N,
                      lam_ng=LAMBDA_NG, lam_s=LAMBDA_S, s_max=S_MAX, params64=None, nthreads: int = 0,
-                     brute: bool = False, lam_ns: float = 0.0):
+                     brute: bool = False, lam_ns: float = 0.0, allowance: bool = True):
     """The whole step for a window of frames: per frame bin, render, image
     loss (averaged over frames), backward; plus lam_s L_scale once.
-    ``targets`` is a list of (D, Ng).  Returns (L, per-frame forwards, grads, bins)."""
+    ``targets`` is a list of (D, Ng).  Returns (L, per-frame forwards, grads, bins).
+    allowance=False: the method alone (no binary32 allowance)."""
     n = surfels.mean.shape[0]
     grads = dict(mean=np.zeros((n, 3)), quat=np.zeros((n, 4)), log_scale=np.zeros((n, 2)),
                  logit=np.zeros(n), abs=np.zeros((n, 10)), flip=np.zeros((n, 10)))
@@ -350,10 +355,10 @@ def forward_backward(surfels, frames, targets, lam_alpha=LAMBDA_ALPHA, lam_n=LAM
             b = dict(ranges=ranges, vals=vals)
         else:
             b = bin_frame(surfels, frame)
-        fw = render_fwd(surfels, frame, b["ranges"], b["vals"], params64, nthreads)
+        fw = render_fwd(surfels, frame, b["ranges"], b["vals"], params64, nthreads, allowance)
         Lf, g, _ = loss_image(fw, D, Ng, lam_alpha, lam_n, lam_ng, scale=1.0 / F, lam_ns=lam_ns, frame=frame)
         render_bwd(surfels, frame, b["ranges"], b["vals"], g["dA"], g["dS_t"], g["dS_n"], params64,
-                   grads, nthreads)
+                   grads, nthreads, allowance)
         L += Lf
         fwds.append(fw); bins.append(b)
     ls = params64[2] if params64 is not None else surfels.log_scale

@@ -2,6 +2,8 @@
 // argument validation and the launch sequence of every entry point.
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 #include <vector>
 
 #include <cmath>
@@ -529,6 +531,36 @@ lgs_status lgs_session_status(lgs_session s, int64_t* required_pairs) {
                 static_cast<unsigned long long>(s->h_status->required_pairs), static_cast<long long>(s->lay.pairs_cap));
   if (s->h_status->timeout) return fail(LGS_ERR_TIMEOUT, "a bounded device wait gave up");
   if (s->h_status->check) return fail(LGS_ERR_DEVICE_CHECK, "device bounds check failed");
+  return LGS_OK;
+}
+
+// lgs_status_word is the head of the device Status word, copied as bytes
+static_assert(offsetof(Status, required_pairs) == offsetof(lgs_status_word, required_pairs), "status layout");
+static_assert(offsetof(Status, n_pairs) == offsetof(lgs_status_word, n_pairs), "status layout");
+static_assert(offsetof(Status, n_vis) == offsetof(lgs_status_word, n_visible), "status layout");
+static_assert(offsetof(Status, overflow) == offsetof(lgs_status_word, overflow), "status layout");
+static_assert(offsetof(Status, timeout) == offsetof(lgs_status_word, timeout), "status layout");
+static_assert(offsetof(Status, check) == offsetof(lgs_status_word, check), "status layout");
+
+lgs_status lgs_session_status_enqueue(lgs_session s, lgs_status_word* out, void* stream) {
+  lgs_status st = enter(s);
+  if (st != LGS_OK) return st;
+  if (!out) return fail(LGS_ERR_INVALID_ARG, "out is NULL");
+  if (!s->ws) return fail(LGS_ERR_NO_WORKSPACE, "no workspace");
+  if (!s->binned) return fail(LGS_ERR_STATE, "no lgs_bin_sort yet");
+  const WsPtrs w = lgs::ws_ptrs(s->ws, s->lay);
+  const cudaError_t e = cudaMemcpyAsync(out, w.st, sizeof(lgs_status_word), cudaMemcpyDeviceToHost,
+                                        static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  return LGS_OK;
+}
+
+lgs_status lgs_status_of_word(const lgs_status_word* w) {
+  if (!w) return fail(LGS_ERR_INVALID_ARG, "word is NULL");
+  if (w->overflow)
+    return fail(LGS_ERR_CAPACITY, "%llu pairs needed", static_cast<unsigned long long>(w->required_pairs));
+  if (w->timeout) return fail(LGS_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (w->check) return fail(LGS_ERR_DEVICE_CHECK, "device bounds check failed");
   return LGS_OK;
 }
 

@@ -86,7 +86,7 @@ EXPORTS = [
     "lgs_status_string", "lgs_last_error", "lgs_constants", "lgs_version", "lgs_trackable_scratch_bytes",
     "lgs_trackable_targets", "lgs_manage_default_params", "lgs_manage_scratch_bytes", "lgs_manage_capacity", "lgs_manage_launches",
     "lgs_map_manage", "lgs_map_gather", "lgs_init_default_params", "lgs_init_scratch_bytes", "lgs_init_max_points", "lgs_init_launches",
-    "lgs_keyframe_init",
+    "lgs_keyframe_init", "lgs_session_status_enqueue", "lgs_status_of_word",
 ]
 
 
@@ -109,6 +109,8 @@ def load():
         "lgs_session_set_workspace": ([P, P, sz], S),
         "lgs_session_status": ([P, ctypes.POINTER(i64)], S),
         "lgs_session_pair_count": ([P, ctypes.POINTER(i64)], S),
+        "lgs_session_status_enqueue": ([P, P, P], S),
+        "lgs_status_of_word": ([P], S),
         "lgs_session_counters": ([P, P], S),
         "lgs_session_bins": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)], S),
         "lgs_session_read_bins": ([P, P, P, P, P, i64], S),
@@ -330,6 +332,27 @@ def lgs_loss(h, surfels, frames, fwd, targets, params, grads_out, grad, loss_out
     _check(load().lgs_loss(h, _ref(surfels), _arr(lgs_frame, frames), len(frames), _arr(lgs_fwd_out, fwd),
                            _arr(lgs_target, targets), _ref(params), _arr(lgs_fwd_grad_out, grads_out),
                            _ref(grad) if grad is not None else None, P(loss_out_ptr), P(stream)))
+
+
+class lgs_status_word(ctypes.Structure):
+    _fields_ = [("required_pairs", ctypes.c_uint64), ("n_pairs", ctypes.c_uint64), ("n_visible", ctypes.c_uint32),
+                ("overflow", ctypes.c_uint32), ("timeout", ctypes.c_uint32), ("check", ctypes.c_uint32)]
+
+
+STATUS_WORD_BYTES = ctypes.sizeof(lgs_status_word)
+
+
+def lgs_session_status_enqueue(h, out_ptr: int, stream):
+    """Enqueue a copy of the status word into pinned host memory at out_ptr
+    (STATUS_WORD_BYTES bytes); no synchronisation."""
+    _check(load().lgs_session_status_enqueue(h, P(out_ptr), P(stream)))
+
+
+def lgs_status_of_word(out_ptr: int):
+    """(status code, required pairs) of a copied status word (read it only
+    after the copy has completed)."""
+    w = lgs_status_word.from_address(out_ptr)
+    return int(load().lgs_status_of_word(P(out_ptr))), int(w.required_pairs)
 
 
 def lgs_session_set_tuning(h, fwd_batch: int = 128, bwd_batch: int = 0, group: int = 2, persistent: int = 0):

@@ -205,7 +205,12 @@ def cast(scene: Scene, origin: np.ndarray, dirs: np.ndarray, max_range: float = 
             nrm = np.concatenate([p / r, np.zeros((M, 1))], 1)
             take(t, nrm, ok)
     if len(scene.boxes):
-        _cast_boxes(scene.boxes, o, d, tbest, nbest)
+        # a box entirely beyond max_range cannot give a kept hit (hits beyond
+        # it are discarded below): only the nearer boxes are tested
+        B = np.asarray(scene.boxes, np.float64).reshape(-1, 6)
+        gap = np.maximum(np.maximum(B[:, :3] - o, o - B[:, 3:]), 0.0)
+        near = (gap * gap).sum(1) <= max_range * max_range
+        _cast_boxes(B[near], o, d, tbest, nbest)
     tbest[tbest > max_range] = np.inf
     return tbest, nbest
 
@@ -434,38 +439,50 @@ def street(seed: int = 0, n: int = 200_000, H: int = 128, W: int = 1024, tile=(1
     return surf, f0, tgt
 
 
+def _track_scan(scene, seed: int, i: int, x: float, map_H: int, map_W: int, tile):
+    """Map scan i of street_track (points, normals of the valid returns), from
+    its own generator (seed, i)."""
+    rng = np.random.default_rng([seed, i])
+    fr = lidar_frame(map_H, map_W, tile, pose=pose_matrix(0.05 * i, (x, 0.0, 0.0)))
+    _, p, nr, v = simulate_scan(scene, fr, rng)
+    return p[v], nr[v]
+
+
+def _track_keyframe(scene, seed: int, j: int, x: float, H: int, W: int, tile):
+    rng = np.random.default_rng([seed, 10_000 + j])
+    fr = lidar_frame(H, W, tile, pose=pose_matrix(0.02 * j, (x, 0.0, 0.0)))
+    D, p, nr, v = simulate_scan(scene, fr, rng)
+    return fr, target_from_scan(D, p, v, true_normals=nr)
+
+
 def street_track(seed: int = 0, n: int = 1_000_000, n_keyframes: int = 8, spacing: float = 3.0,
                  length: float = 200.0, H: int = 128, W: int = 1024, tile=(16, 16),
-                 map_H: int = 64, map_W: int = 1024):
+                 map_H: int = 64, map_W: int = 1024, pool=None):
     """Street extended to a ``length`` m track.  The map: surfels at returns of
     scans every ``spacing`` m along the track (``map_H`` x ``map_W`` beams,
     true surface normals, range-adaptive scales), sub-sampled to ``n``.  The
     keyframes: ``n_keyframes`` consecutive poses ``spacing`` m apart in the
-    middle of the track, each with its own target scan (H x W)."""
+    middle of the track, each with its own target scan (H x W).  Every scan
+    has its own generator, so ``pool`` (an executor) may simulate them in
+    parallel."""
     rng = np.random.default_rng(seed)
     xs = np.arange(-length / 2, length / 2 + 1e-6, spacing)
     scene = street_scene(rng, x_extent=(-length / 2 - 10, length / 2 + 10),
                          n_boxes=int(2000 * (length + 20) / 120), keep_clear=[(x, 0.0) for x in xs])
-    pts_l, org_l, nrm_l = [], [], []
-    for i, x in enumerate(xs):
-        fr = lidar_frame(map_H, map_W, tile, pose=pose_matrix(0.05 * i, (x, 0.0, 0.0)))
-        _, p, nr, v = simulate_scan(scene, fr, rng)
-        pts_l.append(p[v]); nrm_l.append(nr[v])
-        org_l.append(np.broadcast_to(np.array([x, 0.0, 0.0]), (int(v.sum()), 3)))
-    pts = np.concatenate(pts_l); org = np.concatenate(org_l); nrm = np.concatenate(nrm_l)
+    K = len(xs)
+    scans = _map(pool, _track_scan, [scene] * K, [seed] * K, range(K), list(xs), [map_H] * K, [map_W] * K,
+                 [tile] * K)
+    pts = np.concatenate([p for p, _ in scans])
+    nrm = np.concatenate([q for _, q in scans])
+    org = np.concatenate([np.broadcast_to(np.array([x, 0.0, 0.0]), (len(p), 3)) for x, (p, _) in zip(xs, scans)])
     sel = rng.choice(pts.shape[0], size=min(n, pts.shape[0]), replace=False)
     sel.sort()
     kappa = _kappa(lidar_frame(map_H, map_W, tile))
     surf = surfels_from_points(pts[sel], org[sel], rng, kappa, normals=nrm[sel])
     k0 = len(xs) // 2 - n_keyframes // 2
-    frames, targets = [], []
-    for j in range(n_keyframes):
-        x = xs[k0 + j]
-        fr = lidar_frame(H, W, tile, pose=pose_matrix(0.02 * j, (x, 0.0, 0.0)))
-        D, p, nr, v = simulate_scan(scene, fr, rng)
-        frames.append(fr)
-        targets.append(target_from_scan(D, p, v, true_normals=nr))
-    return surf, frames, targets
+    kf = _map(pool, _track_keyframe, [scene] * n_keyframes, [seed] * n_keyframes, range(n_keyframes),
+              [xs[k0 + j] for j in range(n_keyframes)], [H] * n_keyframes, [W] * n_keyframes, [tile] * n_keyframes)
+    return surf, [f for f, _ in kf], [t for _, t in kf]
 
 
 def random_shell(seed: int, n: int, r_range=(2.0, 20.0), scale_range=(0.05, 0.6),
@@ -556,13 +573,34 @@ def sample_street_surfaces(scene: Scene, rng: np.random.Generator, n: int, x_ran
     return np.concatenate(P), np.concatenate(N)
 
 
-def street_maps(seed: int, sizes, shapes, tile=(8, 8), spacing: float = 25.0, noise_targets: bool = True):
+def _street_map(scene, seed: int, i: int, n: int, x: float, shape, tile):
+    """Map i of street_maps, from its own generator (seed, i)."""
+    rng = np.random.default_rng([seed, i])
+    H, W = shape
+    half = 20.0 + n / 25000.0
+    pts, nrm = sample_street_surfaces(scene, rng, int(n), (x - half, x + half))
+    o = np.array([x, 0.0, 0.0])
+    fr = lidar_frame(H, W, tile, pose=pose_matrix(0.1 * i, (x, 0.0, 0.0)))
+    surf = surfels_from_points(pts, np.broadcast_to(o, pts.shape), rng, _kappa(fr), normals=nrm)
+    D, p, nr, v = simulate_scan(scene, fr, rng)
+    return surf, fr, target_from_scan(D, p, v, true_normals=nr)
+
+
+def _map(pool, fn, *iterables):
+    """map over a concurrent.futures executor, or serially without one (the
+    results do not depend on it: every item has its own generator)."""
+    return list(pool.map(fn, *iterables)) if pool is not None else list(map(fn, *iterables))
+
+
+def street_maps(seed: int, sizes, shapes, tile=(8, 8), spacing: float = 25.0, noise_targets: bool = True,
+                pool=None):
     """Independent maps of uneven size along one long street (one per entry of
     ``sizes``), each with one frame of shape ``shapes[i % len(shapes)]`` (H, W)
     at the map's centre and its simulated target scan.  Map ``i`` holds
     ``sizes[i]`` surfels on the street's surfaces within +-(20 + n / 25k) m
-    of its sensor, with range-adaptive scales.  Returns [(surfels, frame,
-    target)]."""
+    of its sensor, with range-adaptive scales, drawn from its own generator
+    (seed, i), so ``pool`` (an executor) may build the maps in parallel.
+    Returns [(surfels, frame, target)]."""
     rng = np.random.default_rng(seed)
     M = len(sizes)
     xs = (np.arange(M) - (M - 1) / 2) * spacing
@@ -570,17 +608,8 @@ def street_maps(seed: int, sizes, shapes, tile=(8, 8), spacing: float = 25.0, no
     scene = street_scene(rng, x_extent=(xs[0] - span - 10, xs[-1] + span + 10),
                          n_boxes=int(2000 * (xs[-1] - xs[0] + 2 * span) / 120),
                          keep_clear=[(x, 0.0) for x in xs])
-    out = []
-    for i, (n, x) in enumerate(zip(sizes, xs)):
-        H, W = shapes[i % len(shapes)]
-        half = 20.0 + n / 25000.0
-        pts, nrm = sample_street_surfaces(scene, rng, int(n), (x - half, x + half))
-        o = np.array([x, 0.0, 0.0])
-        fr = lidar_frame(H, W, tile, pose=pose_matrix(0.1 * i, (x, 0.0, 0.0)))
-        surf = surfels_from_points(pts, np.broadcast_to(o, pts.shape), rng, _kappa(fr), normals=nrm)
-        D, p, nr, v = simulate_scan(scene, fr, rng)
-        out.append((surf, fr, target_from_scan(D, p, v, true_normals=nr)))
-    return out
+    return _map(pool, _street_map, [scene] * M, [seed] * M, range(M), [int(n) for n in sizes], list(xs),
+                [shapes[i % len(shapes)] for i in range(M)], [tile] * M)
 
 
 # --- inputs of map management --------------------------------------------------

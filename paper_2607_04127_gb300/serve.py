@@ -3,30 +3,43 @@
 Every session owns one surfel map whose parameters, gradients and Adam
 moments stay resident on the device.  Clients submit render-and-optimise
 requests (one keyframe: pose + measured range image + tracking normals,
-``iters`` mapping iterations).  Sessions are admitted against an HBM budget
-(resident bytes of the map and its optimiser state plus the per-frame
-buffers); a session that does not fit is rejected.
+``iters`` mapping iterations); a client's last request may close its session.
+
+Admission by HBM budget.  A session is charged its resident bytes (the map and
+its optimiser state, its share of the workspace, its frame buffers).  One that
+fits is admitted; one that does not waits in a first-come queue and is
+admitted as soon as closed sessions free enough memory; its requests wait
+meanwhile (with ``keep_latest`` only the newest).  Only a session larger than
+the whole budget is rejected, and requests of sessions never admitted by the
+end of a run count as unserved.
 
 The scheduler runs ticks.  A tick takes every active request one mapping
 iteration further with ONE call per stage over all of their frames (each
 frame renders its own session's map: ``lgs_*_batch`` with a frame->map
-table), then one Adam step per map.  Requests that arrived meanwhile join at
-the next tick as slots free up (at most ``slots`` active requests, at most
-one per session: a session's keyframes update the same map and are served in
-arrival order).  A request completes after ``iters`` ticks; its latency is
-completion time minus arrival time.  With ``keep_latest`` a session keeps at
-most one waiting request: a newer keyframe supersedes a waiting older one,
-which is dropped and counted (mapping always works on the newest keyframe),
-so queues stay bounded under overload.
+table), then one fused Adam launch over their maps.  Requests that arrived
+meanwhile join at the next tick as slots free up (at most ``slots`` active
+requests, at most one per session: a session's keyframes update the same map
+and are served in arrival order).  A request completes after ``iters`` ticks;
+its latency is the time its last tick is seen complete minus its arrival.
+
+Ticks are pipelined: the host enqueues a tick without waiting for the device
+(at most ``pipeline`` ticks in flight) and retires finished ticks by polling
+their CUDA events.  Each tick copies its loss values and the status word of
+its binning into pinned host memory on the stream (lgs_session_status_enqueue),
+so no tick needs a host round trip; the pair capacity of the workspace
+follows the pair density seen in retired ticks, with head-room.  A tick whose
+binning still overflowed is counted (its iteration ran on an empty render).
+
+With ``keep_latest`` a session keeps at most one waiting request: a newer
+keyframe supersedes a waiting older one, which is dropped and counted
+(mapping always works on the newest keyframe), so queues stay bounded.
 
 With ``slo_ms`` the scheduler admits by deadline: a tick's duration is
 modelled as ``a + kappa * (surfels of its active maps)`` with ``kappa``
-learned online from measured ticks, and a waiting request joins only if the
-simulated remaining ticks let every active request, itself included, finish
-within ``slo_ms`` of its arrival (with a safety factor); otherwise it is
-rejected at once and counted.  Completed requests then meet the latency
-target by construction of the admission, at the price of the reported
-rejection rate.
+learned online from the device time of retired ticks, and a waiting request
+joins only if the simulated remaining ticks let every active request, itself
+included, finish within ``slo_ms`` of its arrival (with a safety factor);
+otherwise it is rejected at once and counted.
 
 ``plain=True`` serves the same requests one at a time with per-request
 launches (the baseline the batched form is measured against).
@@ -44,6 +57,7 @@ from . import lib, render
 
 BYTES_PER_SURFEL = 160          # parameters, gradients, Adam m and v: 4 x 10 floats
 WORKSPACE_PER_SURFEL = 220      # record, box, keys, counters, moments, about 6 pairs (upper estimate)
+FRAME_BYTES_PER_PIXEL = 40      # forward planes, upstream planes, targets
 
 
 @dataclasses.dataclass
@@ -53,15 +67,17 @@ class Request:
     target: object              # scenes.Target
     arrival: float              # seconds since the start of the run
     iters: int = 10
+    close: bool = False         # the client's last request: close the session after it
     done_iters: int = 0
     start: float | None = None
     finish: float | None = None
     losses: list = dataclasses.field(default_factory=list)
+    degraded: bool = False      # one of its ticks overflowed the pair capacity
     buffers: object = None      # device buffers while active: (target tensors, FwdBuffers, upstream planes)
 
 
 class MapSession:
-    def __init__(self, sid: int, surf, device):
+    def __init__(self, sid: int, surf, device, need: int):
         self.sid = sid
         self.params = render.map_tensors(surf, device)
         self.grads = [torch.zeros_like(p) for p in self.params]
@@ -70,92 +86,190 @@ class MapSession:
         self.v = torch.zeros(10 * n, device=device)
         self.t = 0
         self.n = n
+        self.need = need            # bytes charged against the budget
+        self.closing = False
 
     @property
     def resident_bytes(self) -> int:
         return BYTES_PER_SURFEL * self.n
 
 
+def session_bytes(n_surfels: int, frame_pixels: int) -> int:
+    """Bytes a session is charged: map and optimiser state, workspace share,
+    one frame's buffers."""
+    return (BYTES_PER_SURFEL + WORKSPACE_PER_SURFEL) * n_surfels + FRAME_BYTES_PER_PIXEL * frame_pixels
+
+
+class _Tick:
+    """One tick in flight: its requests (in frame order), those whose last
+    iteration it runs, CUDA events around it, pinned copies of its losses and
+    of its binning's status word."""
+
+    def __init__(self, reqs, items: int, surfels: int):
+        self.reqs = list(reqs)
+        self.last: list[Request] = []
+        self.items = items
+        self.surfels = surfels
+        self.start = self.end = None
+        self.loss = None
+        self.status = None
+        self.first = False
+
+
 class Server:
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 150 << 30, slots: int = 16,
+    def __init__(self, device=0, hbm_budget_bytes: int = 150 << 30, slots: int = 16,
                  tuning: dict | None = None, lr=(1e-3, 1e-3, 5e-3, 5e-3), plain: bool = False,
-                 keep_latest: bool = False, slo_ms: float | None = None, slo_margin: float = 0.8):
-        self.device = torch.device("cuda", device)
+                 keep_latest: bool = False, slo_ms: float | None = None, slo_margin: float = 0.8,
+                 pipeline: int = 2, headroom: float = 1.3):
+        self.device = device if isinstance(device, torch.device) else torch.device("cuda", device)
         self.budget = hbm_budget_bytes
         self.slots = 1 if plain else slots
         self.tuning = tuning
         self.lr = lr
         self.plain = plain
+        self.pipeline = max(1, int(pipeline))
+        self.headroom = headroom
         self.sessions: dict[int, MapSession] = {}
-        self.rejected_sessions: list[int] = []
+        self.session_queue: collections.deque = collections.deque()   # (sid, surf, need) waiting for memory
+        self.rejected_sessions: list[int] = []    # larger than the whole budget
+        self.admitted_late: list[int] = []        # waited in the queue, then admitted
+        self.closed_sessions: list[int] = []
         self.used = 0
         self.rast = None
         self.keep_latest = keep_latest
-        self.dropped: list[Request] = []
+        self.dropped: list[Request] = []          # superseded by a newer keyframe of their session
+        self.unserved: list[Request] = []         # their session was never admitted (or was closed)
         self.slo = slo_ms / 1e3 if slo_ms else None
         self.slo_margin = slo_margin
-        self.late: list[Request] = []      # rejected by the deadline admission
-        self.tick_base = 4e-4              # seconds of a tick independent of the maps (host work, launches)
-        self.kappa = None                  # seconds per surfel-iteration, learned from measured ticks
+        self.late: list[Request] = []             # rejected by the deadline admission
+        self.tick_base = 4e-4                     # seconds of a tick independent of the maps
+        self.kappa = None                         # seconds per surfel-iteration, learned from retired ticks
+        self.overflow_ticks = 0
         self._ticks = 0
-        self._grew = False                 # the last tick grew the workspace (and ran twice)
 
-    # -- admission ----------------------------------------------------------
-    def open_session(self, sid: int, surf, frame_pixels: int) -> bool:
-        need = BYTES_PER_SURFEL * surf.n + WORKSPACE_PER_SURFEL * surf.n + 40 * frame_pixels
-        if self.used + need > self.budget:
+    # -- admission ------------------------------------------------------------
+    def open_session(self, sid: int, surf, frame_pixels: int) -> str:
+        """'admitted' (resident now), 'waiting' (queued until memory frees up)
+        or 'rejected' (larger than the whole budget)."""
+        need = session_bytes(surf.n, frame_pixels)
+        if need > self.budget:
             self.rejected_sessions.append(sid)
-            return False
-        self.sessions[sid] = MapSession(sid, surf, self.device)
+            return "rejected"
+        if not self.session_queue and self.used + need <= self.budget:
+            self._admit(sid, surf, need)
+            return "admitted"
+        self.session_queue.append((sid, surf, need))
+        return "waiting"
+
+    def _admit(self, sid, surf, need):
+        self.sessions[sid] = MapSession(sid, surf, self.device, need)
         self.used += need
-        return True
+
+    def _admit_waiting(self):
+        """First come, first served: admit queued sessions while the head fits."""
+        while self.session_queue and self.used + self.session_queue[0][2] <= self.budget:
+            sid, surf, need = self.session_queue.popleft()
+            self._admit(sid, surf, need)
+            self.admitted_late.append(sid)
+
+    def close_session(self, sid: int):
+        """Release a session's map and memory and admit waiting sessions.  The
+        caller makes sure no tick of it is in flight (the serving loop closes
+        a session when the tick of its last request has retired)."""
+        s = self.sessions.pop(sid, None)
+        if s is None:
+            return
+        self.used -= s.need
+        self.closed_sessions.append(sid)
+        self._admit_waiting()
 
     def close(self):
         if self.rast is not None:
             self.rast.close()
+            self.rast = None
         self.sessions.clear()
 
-    # -- one tick -------------------------------------------------------------
-    def _tick(self, active):
-        """One iteration of every active request: one call per stage over their
-        frames, a capacity check at the tick's single synchronisation, one
-        fused Adam launch over their maps.  Returns the per-map losses."""
+    # -- one tick: enqueue, poll, wait, read --------------------------------------
+    def _enqueue_tick(self, active) -> _Tick:
+        """Enqueue one iteration of every active request: one call per stage
+        over their frames, one fused Adam launch over their maps, the status
+        word and the losses copied to pinned memory; no host synchronisation
+        (but on the server's first tick, which sizes the workspace)."""
         for r in active:
             if r.buffers is None:      # device buffers for the request's lifetime
                 r.buffers = (render.target_tensors(r.target, self.device), lib.alloc_fwd(r.frame, self.device),
                              render.upstream_planes(r.frame, self.device))
+        maps = [self.sessions[r.session] for r in active]
+        tick = _Tick(active, items=sum(s.n for s in maps), surfels=sum(s.n for s in maps))
         frames = [r.frame for r in active]
         fmap = list(range(len(active)))
-        outs = [r.buffers[1] for r in active]
-        ups = [r.buffers[2] for r in active]
         if self.rast is None:
             self.rast = render.Rasterizer(frames, frame_map=fmap, device=self.device.index, tuning=self.tuning)
-        self.rast.set_frames(frames, fmap, outs=outs, ups=ups)
-        maps = [self.sessions[r.session] for r in active]
+            self.rast.session.headroom = self.headroom
+        self.rast.set_frames(frames, fmap, outs=[r.buffers[1] for r in active], ups=[r.buffers[2] for r in active])
+        stream = torch.cuda.current_stream(self.device)
+        tick.start = torch.cuda.Event(enable_timing=True)
+        tick.end = torch.cuda.Event(enable_timing=True)
+        tick.loss = torch.empty(len(active), dtype=torch.float32, pin_memory=True)
+        tick.status = torch.zeros(lib.STATUS_WORD_BYTES, dtype=torch.uint8, pin_memory=True)
+        tick.first = self._ticks == 0
+        tick.start.record(stream)
         params = [s.params for s in maps]
         grads = [s.grads for s in maps]      # zero: the previous Adam step cleared them
-        targets = [r.buffers[0] for r in active]
-        out = self.rast.step(params, targets, grads, check=False)
-        torch.cuda.synchronize(self.device)
-        st, _ = lib.lgs_session_status(self.rast.session.handle)
-        self._grew = st == lib.LGS_ERR_CAPACITY
-        if st == lib.LGS_ERR_CAPACITY:       # grow the workspace and redo the tick
-            for g in grads:
-                for x in g:
-                    x.zero_()
-            out = self.rast.step(params, targets, grads, check=True)
-        F = len(active)
-        k = 1 + lib.LOSS_TERMS * F
-        losses = out[k: k + F].cpu().numpy()
+        out = self.rast.step(params, [r.buffers[0] for r in active], grads, check=tick.first)
+        lib.lgs_session_status_enqueue(self.rast.session.handle, tick.status.data_ptr(), stream.cuda_stream)
+        k = 1 + lib.LOSS_TERMS * len(active)
+        tick.loss.copy_(out[k: k + len(active)], non_blocking=True)
         for s in maps:
             s.t += 1
         render.adam_step_batch([(s.params, s.grads, s.m, s.v, s.t, self.lr) for s in maps], zero_grad=True)
-        return losses
+        tick.end.record(stream)
+        self._ticks += 1
+        return tick
 
-    # -- deadline admission --------------------------------------------------
-    def _learn(self, active, seconds: float):
-        n = sum(self.sessions[r.session].n for r in active)
-        k = max(seconds - self.tick_base, 0.0) / max(n, 1)
+    def _tick_ready(self, tick) -> bool:
+        return tick.end.query()
+
+    def _wait_tick(self, tick):
+        tick.end.synchronize()
+
+    def _read_tick(self, tick):
+        """(status, required pairs, device seconds, per-request losses) of a
+        completed tick."""
+        st, req = lib.lgs_status_of_word(tick.status.data_ptr())
+        return st, req, tick.start.elapsed_time(tick.end) / 1e3, tick.loss.numpy().tolist()
+
+    def _retire(self, tick, now: float):
+        """Book a completed tick: its losses, the completions of its requests'
+        last iterations, the capacity and tick models.  Returns the completed
+        requests."""
+        st, req, seconds, losses = self._read_tick(tick)
+        density = req / max(tick.items, 1)
+        if st == lib.LGS_ERR_CAPACITY:
+            self.overflow_ticks += 1
+            for r in tick.reqs:
+                r.degraded = True
+        elif st != lib.LGS_OK:
+            raise lib.LgsError(st, "device status of a serving tick")
+        if self.rast is not None and density * 1.15 > self.rast.session.pairs_per_item:
+            # the workspace follows the densest binning seen, with head-room
+            self.rast.session.pairs_per_item = self.headroom * density
+        if not tick.first and st == lib.LGS_OK:
+            self._learn(tick.surfels, seconds)
+        for r, l in zip(tick.reqs, losses):
+            r.losses.append(float(l))
+        done = []
+        for r in tick.last:
+            r.finish = now
+            r.buffers = None
+            done.append(r)
+            if r.close:
+                self.close_session(r.session)
+        return done
+
+    # -- deadline admission --------------------------------------------------------
+    def _learn(self, surfels: int, seconds: float):
+        k = max(seconds - self.tick_base, 0.0) / max(surfels, 1)
         self.kappa = k if self.kappa is None else 0.5 * self.kappa + 0.5 * k
 
     def _feasible(self, active, now: float) -> bool:
@@ -176,31 +290,42 @@ class Server:
             rem = nxt
         return True
 
-    # -- the loop ---------------------------------------------------------------
+    # -- the loop -------------------------------------------------------------------
     def run(self, requests):
         """Serve ``requests`` (sorted by arrival; times relative to now).
         Returns the completed requests."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = collections.deque()
         active, done = [], []
-        busy = set()
+        inflight = collections.deque()
+        busy = set()          # sessions with an active request
         t0 = time.perf_counter()
-        while pending or waiting or active:
+        while pending or waiting or active or inflight:
+            # retire the ticks the device has finished (no blocking)
+            while inflight and self._tick_ready(inflight[0]):
+                done += self._retire(inflight.popleft(), time.perf_counter() - t0)
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 r = pending.popleft()
-                if r.session not in self.sessions:
+                s = self.sessions.get(r.session)
+                if r.session in self.rejected_sessions or r.session in self.closed_sessions or (s and s.closing):
+                    self.unserved.append(r)
                     continue
                 if self.keep_latest:
                     for old in [w for w in waiting if w.session == r.session]:
                         waiting.remove(old)
                         self.dropped.append(old)
                 waiting.append(r)
-            # fill free slots, at most one request per session, in arrival order
+            # fill free slots, at most one request per session, in arrival order;
+            # requests of sessions still queued for memory keep waiting
             keep = collections.deque()
             while waiting:
                 r = waiting.popleft()
-                if len(active) < self.slots and r.session not in busy:
+                s = self.sessions.get(r.session)
+                if s is not None and s.closing:
+                    self.unserved.append(r)
+                    continue
+                if s is not None and len(active) < self.slots and r.session not in busy:
                     if self.slo is not None and self.kappa is not None and not self._feasible(active + [r], now):
                         self.late.append(r)      # would miss its deadline or make another one miss
                         continue
@@ -210,31 +335,32 @@ class Server:
                 else:
                     keep.append(r)
             waiting = keep
-            if not active:
-                if pending:
-                    time.sleep(max(0.0, min(pending[0].arrival - now, 0.002)))
+            if active and len(inflight) < self.pipeline:
+                tick = self._enqueue_tick(active)
+                still = []
+                for r in active:
+                    r.done_iters += 1
+                    if r.done_iters >= r.iters:
+                        # the slot and the session are free for the next tick (the
+                        # stream orders that tick after this one)
+                        tick.last.append(r)
+                        busy.discard(r.session)
+                        if r.close:
+                            self.sessions[r.session].closing = True
+                    else:
+                        still.append(r)
+                active = still
+                inflight.append(tick)
                 continue
-            t_tick = time.perf_counter()
-            L = self._tick(active)     # per-map loss (one frame per map); the tick ends synchronised
-            # the tick model learns from ordinary ticks only: not the server's
-            # first (buffers and workspace are created) nor one that grew the
-            # workspace and ran twice
-            if self._ticks > 0 and not self._grew:
-                self._learn(active, time.perf_counter() - t_tick)
-            self._ticks += 1
-            now = time.perf_counter() - t0
-            still = []
-            for r, l in zip(active, L):
-                r.done_iters += 1
-                r.losses.append(float(l))
-                if r.done_iters >= r.iters:
-                    r.finish = now
-                    done.append(r)
-                    busy.discard(r.session)
-                    r.buffers = None
-                else:
-                    still.append(r)
-            active = still
+            if inflight:
+                self._wait_tick(inflight[0])
+                continue
+            if pending:
+                time.sleep(max(0.0, min(pending[0].arrival - now, 0.002)))
+            elif waiting:
+                # nothing runs and nothing arrives: these sessions' memory never frees up
+                self.unserved.extend(waiting)
+                waiting.clear()
         return done
 
 
@@ -255,15 +381,18 @@ def poisson_requests(rng: np.random.Generator, sessions, frames_of, targets_of, 
 
 
 def latency_stats(done, duration: float, offered: int, rejected_sessions: int, n_sessions: int, dropped: int = 0,
-                  late: int = 0):
+                  late: int = 0, unserved: int = 0, waited_sessions: int = 0, overflow_ticks: int = 0):
     """p50 / p99 latency (ms) of the completed requests, completed frames per
-    second of wall time, and the rejections: sessions refused at admission,
-    requests superseded by a newer keyframe of their session, requests
-    refused by the deadline admission."""
+    second of wall time, and the rejections: sessions refused at admission
+    (larger than the budget), requests superseded by a newer keyframe of their
+    session, requests refused by the deadline admission, requests of sessions
+    that were never admitted; sessions that waited for memory."""
     lat = np.array([r.finish - r.arrival for r in done]) * 1e3
     wall = max([r.finish for r in done] + [duration])
     return dict(completed=len(done), offered=offered, p50_ms=float(np.percentile(lat, 50)) if len(lat) else None,
                 p99_ms=float(np.percentile(lat, 99)) if len(lat) else None,
                 frames_per_s=len(done) / wall, rejected_sessions=rejected_sessions,
-                session_rejection_rate=rejected_sessions / max(n_sessions, 1), dropped_requests=dropped,
-                deadline_rejected=late, request_rejection_rate=(dropped + late) / max(offered, 1))
+                session_rejection_rate=rejected_sessions / max(n_sessions, 1), waited_sessions=waited_sessions,
+                dropped_requests=dropped, deadline_rejected=late, unserved_requests=unserved,
+                request_rejection_rate=(dropped + late + unserved) / max(offered, 1),
+                overflow_ticks=overflow_ticks)

@@ -40,7 +40,7 @@ def _serve(workload, sids, **kw):
     srv = serve.Server(**kw)
     for sid in sids:
         surf, fr, _ = workload[sid]
-        assert srv.open_session(sid, surf, fr.H * fr.W)
+        assert srv.open_session(sid, surf, fr.H * fr.W) == "admitted"
     done = srv.run(_requests(workload, sids))
     params = {sid: [p.cpu().numpy() for p in srv.sessions[sid].params] for sid in sids}
     losses = {}
@@ -76,15 +76,47 @@ def test_plain_server_matches_batched(workload):
 
 
 def test_admission_by_budget(workload):
+    """A budget for two sessions: a third waits in the queue, a session
+    larger than the whole budget is rejected."""
     from paper_2607_04127_gb300 import serve
     surf, fr, _ = workload[2]
-    one = serve.BYTES_PER_SURFEL * surf.n + serve.WORKSPACE_PER_SURFEL * surf.n + 40 * fr.H * fr.W
+    one = serve.session_bytes(surf.n, fr.H * fr.W)
     srv = serve.Server(hbm_budget_bytes=int(2.5 * one))
-    assert srv.open_session(0, surf, fr.H * fr.W)
-    assert srv.open_session(1, surf, fr.H * fr.W)
-    assert not srv.open_session(2, surf, fr.H * fr.W)
-    assert srv.rejected_sessions == [2]
+    assert srv.open_session(0, surf, fr.H * fr.W) == "admitted"
+    assert srv.open_session(1, surf, fr.H * fr.W) == "admitted"
+    assert srv.open_session(2, surf, fr.H * fr.W) == "waiting"
+    big = scenes.street_maps(6, [4 * surf.n], [SHAPES[0]], tile=(8, 8))[0][0]
+    assert srv.open_session(3, big, fr.H * fr.W) == "rejected"
+    assert srv.rejected_sessions == [3] and [q[0] for q in srv.session_queue] == [2]
     srv.close()
+
+
+def test_waiting_session_is_admitted_when_one_closes(workload):
+    """Session 2 waits for memory; session 0's client closes it after its
+    request; session 2 is then admitted, its request (queued since t = 0)
+    runs after session 0's, and its losses equal those of a solo run."""
+    from paper_2607_04127_gb300 import serve
+    surf, fr, tgt = workload[2]
+    one = serve.session_bytes(surf.n, fr.H * fr.W)
+    srv = serve.Server(hbm_budget_bytes=int(2.5 * one), slots=8)
+    for sid in (0, 1):
+        assert srv.open_session(sid, surf, fr.H * fr.W) == "admitted"
+    assert srv.open_session(2, surf, fr.H * fr.W) == "waiting"
+    reqs = [serve.Request(0, fr, tgt, 0.0, 3, close=True), serve.Request(1, fr, tgt, 0.0, 3),
+            serve.Request(2, fr, tgt, 0.0, 3)]
+    done = srv.run(reqs)
+    assert len(done) == 3 and not srv.unserved
+    assert srv.closed_sessions == [0] and srv.admitted_late == [2]
+    assert reqs[2].start >= reqs[0].finish
+    assert srv.used <= srv.budget
+    srv.close()
+    solo = serve.Server(slots=8)
+    assert solo.open_session(2, surf, fr.H * fr.W) == "admitted"
+    alone = serve.Request(2, fr, tgt, 0.0, 3)
+    solo.run([alone])
+    solo.close()
+    assert alone.losses[0] == reqs[2].losses[0]
+    assert np.allclose(alone.losses, reqs[2].losses, rtol=1e-4)
 
 
 def test_poisson_stream_latency_stats(workload):
