@@ -792,10 +792,12 @@ def street_roofline(pk, kernels_ms, ms_step, c, n_items, hw, n_surf, tuning):
     peak = pk["fp32_instr_per_s"] / 1e12
     return dict(bound="alu", kernel=kname(tuning, dom), achieved=instr / t_dom / 1e12, peak=peak, unit="Tinstr/s",
                 frac=instr / t_dom / 1e12 / peak, traffic=measured_traffic(kname(tuning, dom)),
-                achieved_with_reevaluation=instr_re / t_dom / 1e12, frac_with_reevaluation=instr_re / t_dom / 1e12 / peak,
+                achieved_with_reevaluation=instr_re / t_dom / 1e12,
+                frac_with_reevaluation=instr_re / t_dom / 1e12 / peak,
                 frac_step=roof / ms_step, frac_step_with_reevaluation=roof_re / ms_step, roofline_step_ms=roof,
                 stages=stages, peak_source=pk["source"],
-                flops=dict(achieved=flops / t_dom / 1e12, peak=2 * peak, unit="TFLOP/s", frac=flops / t_dom / 1e12 / (2 * peak),
+                flops=dict(achieved=flops / t_dom / 1e12, peak=2 * peak, unit="TFLOP/s",
+                           frac=flops / t_dom / 1e12 / (2 * peak),
                            note="FMA = 2; 27 FLOP per evaluation, 12 per composited, 70 per contributing pair"))
 
 

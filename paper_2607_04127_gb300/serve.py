@@ -26,9 +26,11 @@ Ticks are pipelined: the host enqueues a tick without waiting for the device
 (at most ``pipeline`` ticks in flight) and retires finished ticks by polling
 their CUDA events.  Each tick copies its loss values and the status word of
 its binning into pinned host memory on the stream (lgs_session_status_enqueue),
-so no tick needs a host round trip; the pair capacity of the workspace
-follows the pair density seen in retired ticks, with head-room.  A tick whose
-binning still overflowed is counted (its iteration ran on an empty render).
+so no tick needs a host round trip.  The pair capacity of a tick is the sum
+of its maps' pair densities (pairs per surfel, each measured once by a
+checked binning of the session's first request, the only synchronisation)
+times a head-room.  A tick whose binning still overflowed is counted (its
+iteration ran on an empty render) and the densities grow.
 
 With ``keep_latest`` a session keeps at most one waiting request: a newer
 keyframe supersedes a waiting older one, which is dropped and counted
@@ -36,9 +38,12 @@ keyframe supersedes a waiting older one, which is dropped and counted
 
 With ``slo_ms`` the scheduler admits by deadline: a tick's duration is
 modelled as ``a + kappa * (surfels of its active maps)`` with ``kappa``
-learned online from the device time of retired ticks, and a waiting request
-joins only if the simulated remaining ticks let every active request, itself
-included, finish within ``slo_ms`` of its arrival (with a safety factor);
+learned online from retired ticks (the device time between the ends of
+back-to-back ticks, or the host's enqueueing interval when that paced the
+device), and a waiting request joins only
+if the simulated remaining ticks, after those in flight, let every active
+request, itself included, finish within ``slo_ms`` of its arrival (with a
+safety factor);
 otherwise it is rejected at once and counted.
 
 ``plain=True`` serves the same requests one at a time with per-request
@@ -110,7 +115,9 @@ class _Tick:
         self.last: list[Request] = []
         self.items = items
         self.surfels = surfels
-        self.start = self.end = None
+        self.start = self.end = self.prev_end = None
+        self.t_enqueue = 0.0            # host time the tick's enqueueing began
+        self.host_period = None         # host time since the previous tick's enqueueing began
         self.loss = None
         self.status = None
         self.first = False
@@ -145,7 +152,10 @@ class Server:
         self.tick_base = 4e-4                     # seconds of a tick independent of the maps
         self.kappa = None                         # seconds per surfel-iteration, learned from retired ticks
         self.overflow_ticks = 0
+        self.density: dict[int, float] = {}       # pairs per surfel of each session's binning (probed)
         self._ticks = 0
+        self._last_end = None                     # end event of the last enqueued tick
+        self._last_enqueue = None                 # host time the last tick's enqueueing began
 
     # -- admission ------------------------------------------------------------
     def open_session(self, sid: int, surf, frame_pixels: int) -> str:
@@ -194,29 +204,42 @@ class Server:
         """Enqueue one iteration of every active request: one call per stage
         over their frames, one fused Adam launch over their maps, the status
         word and the losses copied to pinned memory; no host synchronisation
-        (but on the server's first tick, which sizes the workspace)."""
+        (but the one-off density probe of a session's first request)."""
         for r in active:
             if r.buffers is None:      # device buffers for the request's lifetime
                 r.buffers = (render.target_tensors(r.target, self.device), lib.alloc_fwd(r.frame, self.device),
                              render.upstream_planes(r.frame, self.device))
         maps = [self.sessions[r.session] for r in active]
         tick = _Tick(active, items=sum(s.n for s in maps), surfels=sum(s.n for s in maps))
+        tick.t_enqueue = time.perf_counter()
+        if self._last_enqueue is not None:
+            tick.host_period = tick.t_enqueue - self._last_enqueue
+        self._last_enqueue = tick.t_enqueue
         frames = [r.frame for r in active]
         fmap = list(range(len(active)))
         if self.rast is None:
             self.rast = render.Rasterizer(frames, frame_map=fmap, device=self.device.index, tuning=self.tuning)
             self.rast.session.headroom = self.headroom
+        probed = [r for r in active if r.session not in self.density]
+        for r in probed:
+            self._probe(r)
+        # pair capacity of this tick: every map at its own density, with head-room
+        want = sum(self.sessions[r.session].n * self.density[r.session] for r in active)
+        self.rast.session.pairs_per_item = self.headroom * want / max(tick.items, 1)
         self.rast.set_frames(frames, fmap, outs=[r.buffers[1] for r in active], ups=[r.buffers[2] for r in active])
         stream = torch.cuda.current_stream(self.device)
         tick.start = torch.cuda.Event(enable_timing=True)
         tick.end = torch.cuda.Event(enable_timing=True)
         tick.loss = torch.empty(len(active), dtype=torch.float32, pin_memory=True)
         tick.status = torch.zeros(lib.STATUS_WORD_BYTES, dtype=torch.uint8, pin_memory=True)
-        tick.first = self._ticks == 0
+        tick.first = bool(probed)
+        # back to back with the previous tick: the device time between their
+        # ends is this tick's period (launch gaps included)
+        tick.prev_end = self._last_end if self._last_end is not None and not self._last_end.query() else None
         tick.start.record(stream)
         params = [s.params for s in maps]
         grads = [s.grads for s in maps]      # zero: the previous Adam step cleared them
-        out = self.rast.step(params, [r.buffers[0] for r in active], grads, check=tick.first)
+        out = self.rast.step(params, [r.buffers[0] for r in active], grads, check=False)
         lib.lgs_session_status_enqueue(self.rast.session.handle, tick.status.data_ptr(), stream.cuda_stream)
         k = 1 + lib.LOSS_TERMS * len(active)
         tick.loss.copy_(out[k: k + len(active)], non_blocking=True)
@@ -224,8 +247,19 @@ class Server:
             s.t += 1
         render.adam_step_batch([(s.params, s.grads, s.m, s.v, s.t, self.lr) for s in maps], zero_grad=True)
         tick.end.record(stream)
+        self._last_end = tick.end
         self._ticks += 1
         return tick
+
+    def _probe(self, r):
+        """A session's pair density (pairs per surfel of its binning), measured
+        once, the first time one of its requests runs: a checked binning of
+        its map alone (it synchronises, and grows the workspace if needed)."""
+        s = self.sessions[r.session]
+        self.rast.set_frames([r.frame], [0], outs=[r.buffers[1]], ups=[r.buffers[2]])
+        self.rast.bin_sort([s.params], check=True)
+        _, req = lib.lgs_session_status(self.rast.session.handle)
+        self.density[r.session] = req / max(s.n, 1)
 
     def _tick_ready(self, tick) -> bool:
         return tick.end.query()
@@ -237,23 +271,31 @@ class Server:
         """(status, required pairs, device seconds, per-request losses) of a
         completed tick."""
         st, req = lib.lgs_status_of_word(tick.status.data_ptr())
-        return st, req, tick.start.elapsed_time(tick.end) / 1e3, tick.loss.numpy().tolist()
+        t0 = tick.prev_end if tick.prev_end is not None else tick.start
+        seconds = t0.elapsed_time(tick.end) / 1e3
+        if tick.prev_end is None and tick.host_period is not None:
+            # the device idled before this tick: the host's enqueueing paced it
+            seconds = max(seconds, tick.host_period)
+        return st, req, seconds, tick.loss.numpy().tolist()
 
     def _retire(self, tick, now: float):
         """Book a completed tick: its losses, the completions of its requests'
         last iterations, the capacity and tick models.  Returns the completed
         requests."""
         st, req, seconds, losses = self._read_tick(tick)
-        density = req / max(tick.items, 1)
         if st == lib.LGS_ERR_CAPACITY:
+            # a denser binning than probed: its iteration ran on an empty
+            # render (counted); the sessions' densities follow what it needed
             self.overflow_ticks += 1
+            est = sum(self.sessions[r.session].n * self.density.get(r.session, 0.0) for r in tick.reqs
+                      if r.session in self.sessions)
+            grow = max(1.0, req / max(est, 1.0))
             for r in tick.reqs:
                 r.degraded = True
+                if r.session in self.density:
+                    self.density[r.session] *= grow
         elif st != lib.LGS_OK:
             raise lib.LgsError(st, "device status of a serving tick")
-        if self.rast is not None and density * 1.15 > self.rast.session.pairs_per_item:
-            # the workspace follows the densest binning seen, with head-room
-            self.rast.session.pairs_per_item = self.headroom * density
         if not tick.first and st == lib.LGS_OK:
             self._learn(tick.surfels, seconds)
         for r, l in zip(tick.reqs, losses):
@@ -272,12 +314,13 @@ class Server:
         k = max(seconds - self.tick_base, 0.0) / max(surfels, 1)
         self.kappa = k if self.kappa is None else 0.5 * self.kappa + 0.5 * k
 
-    def _feasible(self, active, now: float) -> bool:
-        """Simulate the remaining ticks of ``active`` (no further arrivals):
-        does every request finish within the margin of its deadline?"""
+    def _feasible(self, active, now: float, backlog: float = 0.0) -> bool:
+        """Simulate the remaining ticks of ``active`` (no further arrivals),
+        after ``backlog`` seconds of ticks already in flight: does every
+        request finish within the margin of its deadline?"""
         rem = [(r.iters - r.done_iters, self.sessions[r.session].n, r.arrival + self.slo_margin * self.slo)
                for r in active]
-        t = now
+        t = now + backlog
         while rem:
             t += self.tick_base + self.kappa * sum(n for _, n, _ in rem)
             nxt = []
@@ -326,7 +369,10 @@ class Server:
                     self.unserved.append(r)
                     continue
                 if s is not None and len(active) < self.slots and r.session not in busy:
-                    if self.slo is not None and self.kappa is not None and not self._feasible(active + [r], now):
+                    backlog = (sum(self.tick_base + self.kappa * t.surfels for t in inflight)
+                               if self.kappa is not None else 0.0)
+                    if self.slo is not None and self.kappa is not None and \
+                            not self._feasible(active + [r], now, backlog):
                         self.late.append(r)      # would miss its deadline or make another one miss
                         continue
                     r.start = now
