@@ -260,7 +260,10 @@ LGS_API lgs_status lgs_session_kernel_times(lgs_session s, double* ms, int64_t* 
  * at the sum of the tile counts of frames < f), item_of_pair[P] (frame-major
  * item f*n + surfel for one map), ranges[2*T] (start, end per global tile;
  * (0, 0) for a tile without pairs),
- * depth_key[items] (binary32 bits of |mu_sensor|). */
+ * depth_key[items] (binary32 bits of |mu_sensor|).  The binning itself does
+ * not store the tile of each pair (its ranges give it): when tile_of_pair is
+ * requested, this call fills it on the session's last stream and
+ * synchronises with that stream. */
 LGS_API lgs_status lgs_session_bins(lgs_session s, const uint32_t** tile_of_pair, const uint32_t** item_of_pair,
                             const uint32_t** ranges, const uint32_t** depth_key);
 

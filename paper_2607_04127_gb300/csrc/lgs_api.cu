@@ -207,6 +207,7 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
   L.box = take(16 * I);
   L.key = take(4 * I);
   L.cnt = take(4 * I);
+  L.tset = take(8 * I);
   L.tcur = take(4 * T);
   L.pkey = take(8 * P);
   L.ptile = take(4 * P);
@@ -220,6 +221,7 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
   L.cbase = take(4 * T);
   L.ckpt = take(sizeof(float) * 6 * static_cast<size_t>(tile_pixels) * static_cast<size_t>(C));
   L.sortl = take(4 * T);
+  L.midl = take(4 * T);
   L.chunks_cap = C;
   L.total = off;
   L.items_cap = items;
@@ -624,7 +626,13 @@ lgs_status lgs_session_bins(lgs_session s, const uint32_t** tile_of_pair, const 
   if (!s) return fail(LGS_ERR_INVALID_ARG, "session is NULL");
   if (!s->binned) return fail(LGS_ERR_STATE, "no lgs_bin_sort yet");
   const WsPtrs w = lgs::ws_ptrs(s->ws, s->lay);
-  if (tile_of_pair) *tile_of_pair = w.ptile;
+  if (tile_of_pair) {
+    // the binning does not write the tile of each pair; fill it now
+    cudaError_t e = lgs::launch_fill_tile_of_pair(w, s->desc->n_tiles, s->last_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->last_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tile of pair");
+    *tile_of_pair = w.ptile;
+  }
   if (item_of_pair) *item_of_pair = w.pv;
   if (ranges) *ranges = reinterpret_cast<const uint32_t*>(w.ranges);
   if (depth_key) *depth_key = w.key;
@@ -641,6 +649,11 @@ lgs_status lgs_session_read_bins(lgs_session s, uint32_t* tile_of_pair, uint32_t
                 static_cast<long long>(cap_pairs));
   const WsPtrs w = lgs::ws_ptrs(s->ws, s->lay);
   cudaError_t e = cudaSuccess;
+  if (tile_of_pair && np) {
+    // the binning does not write the tile of each pair; fill it now
+    e = lgs::launch_fill_tile_of_pair(w, s->desc->n_tiles, s->last_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->last_stream);
+  }
   if (tile_of_pair && np && e == cudaSuccess)
     e = cudaMemcpy(tile_of_pair, w.ptile, 4 * np, cudaMemcpyDeviceToHost);
   if (item_of_pair && np && e == cudaSuccess)

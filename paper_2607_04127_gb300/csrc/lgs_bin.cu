@@ -4,19 +4,23 @@
 //   k_tables      per frame: binary32 sine / direction tables of the tile
 //                 rows and columns (pixel-centre extremes of each tile)
 //   k_preprocess  per (frame, surfel) item: 64 B compositing record, pixel
-//                 box, depth key = bits of binary32 |mu_sensor|; counts one
-//                 per covered tile (atomic per-tile counters)
+//                 box, depth key = bits of binary32 |mu_sensor|; the item's
+//                 tiles (a range of tile rows times a circular range of tile
+//                 columns, stored per item) and one count per covered tile
+//                 (shared-memory counters per CTA, one atomic per tile)
 //   k_tile_scan   one CTA: exclusive scan of the tile counts -> every tile's
 //                 [start, end) and its fill cursor; capacity check; the
 //                 longest-first tile order of the persistent kernels; the
-//                 list of tiles longer than kLongList
+//                 lists of tiles longer than kLongList, 2048 and 1024 keys
 //   k_emit        every item appends (depth key << 32 | item) to the bucket
-//                 of each tile it covers (order inside a bucket arbitrary)
-//   k_tile_sort_merge / k_tile_sort
-//                 sort every bucket by the 64-bit key: up to 2048 keys by a
-//                 merge sort in shared memory, longer buckets by a bitonic
-//                 network (up to 4096 in shared memory, beyond that chunks
-//                 merged through global memory); then write the item list
+//                 of each tile of its stored set (order inside a bucket
+//                 arbitrary)
+//   k_tile_sort_all
+//                 sort every bucket by the 64-bit key in one launch: up to
+//                 1024 keys by a merge sort on half a CTA, up to 2048 on a
+//                 whole CTA, longer buckets by a bitonic network (up to 4096
+//                 in shared memory, beyond that chunks merged through global
+//                 memory); then write the item list
 // The result is the order of the key (tile, depth, item): per tile, by depth,
 // ties by item index.
 #include <cuda_runtime.h>
@@ -64,6 +68,7 @@ __global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, St
     st->count_ticket = 0;
     st->n_long = 0;
     st->n_big = 0;
+    st->n_mid = 0;
     st->long_counter_fwd = 0;
     st->long_counter_bwd = 0;
     st->long_done_fwd = 0;
@@ -120,6 +125,101 @@ __device__ __forceinline__ uint32_t for_each_tile(const BinGeom& g, const FrameD
   return n;
 }
 
+// The tiles an item's bounding cone meets form a product of tile rows and
+// tile columns (the row test depends on the row only, the column test on
+// the column only).  The passing rows form one range and the passing columns
+// one circular range (the cone is convex in elevation and in azimuth, and a
+// tile between two passing tiles lies deep inside the cone), so an item's
+// tiles are stored as rows [r0, r1] and nc columns from c0 on, modulo the
+// column count.  Should the passing rows or columns not form one range (a
+// decision at the binary32 edge of the cone), tile_set returns false and the
+// caller enumerates the tiles one by one instead (for_each_tile).
+struct TileSet {
+  int r0, r1, c0, nc;
+};
+
+constexpr uint32_t kTsEnumerate = 0xffffffffu;   // stored tile set: enumerate tile by tile
+
+__device__ __forceinline__ bool tile_set(const BinGeom& g, const FrameDev& F, const float* __restrict__ tab,
+                                         const float4& pbox, TileSet& t) {
+  const float4* ct = reinterpret_cast<const float4*>(tab + F.col_tab);
+  t.r0 = 0;
+  t.r1 = -1;
+  t.c0 = 0;
+  t.nc = 0;
+  if (F.ntr >= 0xffff || F.ntc >= 0xffff) return false;
+  int ra = 0, rb = F.ntr - 1;
+  if (!g.all_rows) {
+    ra = max(0, static_cast<int>(pbox.x) / F.th);
+    rb = min(F.ntr - 1, static_cast<int>(pbox.y) / F.th);
+  }
+  int r0 = -1, r1 = -1, nr = 0;
+  for (int r = ra; r <= rb; ++r) {
+    if (!bin_row_hit(g, tab[F.row_tab + 2 * r], tab[F.row_tab + 2 * r + 1])) continue;
+    if (r0 < 0) r0 = r;
+    r1 = r;
+    ++nr;
+  }
+  if (nr == 0) return true;
+  if (nr != r1 - r0 + 1) return false;
+  ColWin w;
+  bin_col_window(g, F, w);
+  // the candidate columns in circular order (the window's second range
+  // continues the first across the azimuth seam)
+  int prev = -1, runs = 0, first = 0, second = 0, n = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int ja = pass ? w.b0 : w.a0, jb = pass ? w.b1 : w.a1;
+    for (int jc = ja; jc <= jb; ++jc) {
+      if (!bin_col_hit(g, ct[jc])) continue;
+      if (prev < 0 || jc != (prev + 1 == F.ntc ? 0 : prev + 1)) {
+        ++runs;
+        if (runs == 1) first = jc;
+        else second = jc;
+      }
+      prev = jc;
+      ++n;
+    }
+  }
+  if (n == 0) return true;
+  if (runs == 1) {
+    t.c0 = first;
+  } else if (runs == 2 && first == 0 && prev == F.ntc - 1) {
+    t.c0 = second;        // one range across the seam, seen from column 0
+  } else {
+    return false;
+  }
+  t.r0 = r0;
+  t.r1 = r1;
+  t.nc = n;
+  return true;
+}
+
+template <class Fn>
+__device__ __forceinline__ void for_each_in_set(const TileSet& t, const FrameDev& F, Fn fn) {
+  for (int r = t.r0; r <= t.r1; ++r) {
+    const uint32_t rowbase = F.tile_base + static_cast<uint32_t>(r * F.ntc);
+    for (int k = 0; k < t.nc; ++k) {
+      int jc = t.c0 + k;
+      if (jc >= F.ntc) jc -= F.ntc;
+      fn(rowbase + static_cast<uint32_t>(jc));
+    }
+  }
+}
+
+__device__ __forceinline__ uint2 pack_set(const TileSet& t) {
+  return make_uint2(static_cast<uint32_t>(t.r0) | (static_cast<uint32_t>(t.r1 < 0 ? 0 : t.r1) << 16),
+                    static_cast<uint32_t>(t.c0) | (static_cast<uint32_t>(t.nc) << 16));
+}
+
+__device__ __forceinline__ TileSet unpack_set(uint2 p) {
+  TileSet t;
+  t.r0 = static_cast<int>(p.x & 0xffffu);
+  t.r1 = static_cast<int>(p.x >> 16);
+  t.c0 = static_cast<int>(p.y & 0xffffu);
+  t.nc = static_cast<int>(p.y >> 16);
+  return t;
+}
+
 // Per-CTA tile counters in shared memory: when all of a CTA's items belong
 // to one frame with at most kAggTiles tiles, its per-tile atomics go to
 // shared memory and each tile it touched gets one global atomic (items are
@@ -154,7 +254,8 @@ __device__ __forceinline__ AggWin agg_window(const Desc& D) {
 __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, const float* __restrict__ tab,
                                                      float4* __restrict__ rec, float4* __restrict__ box,
                                                      uint32_t* __restrict__ key, uint32_t* __restrict__ cnt,
-                                                     uint32_t* __restrict__ tcount, Status* __restrict__ st) {
+                                                     uint2* __restrict__ tset, uint32_t* __restrict__ tcount,
+                                                     Status* __restrict__ st) {
   __shared__ uint32_t s_cnt[kAggTiles];
   const int64_t item = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool live = item < D->n_items;
@@ -177,8 +278,19 @@ __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, 
     bin_geom(M.mean + 3 * i, M.ls + 2 * i, F, g);
     key[item] = __float_as_uint(g.r);
     const float4 pb = pixel_box(g, F);
-    if (aw.local) c = for_each_tile(g, F, tab, pb, [&](uint32_t t) { atomicAdd(s_cnt + (t - aw.base), 1u); });
-    else c = for_each_tile(g, F, tab, pb, [&](uint32_t t) { atomicAdd(tcount + t, 1u); });
+    TileSet ts;
+    const auto count = [&](uint32_t t) {
+      if (aw.local) atomicAdd(s_cnt + (t - aw.base), 1u);
+      else atomicAdd(tcount + t, 1u);
+    };
+    if (tile_set(g, F, tab, pb, ts)) {
+      for_each_in_set(ts, F, count);
+      c = static_cast<uint32_t>((ts.r1 - ts.r0 + 1) * ts.nc);
+      tset[item] = pack_set(ts);
+    } else {
+      c = for_each_tile(g, F, tab, pb, count);
+      tset[item] = make_uint2(kTsEnumerate, kTsEnumerate);
+    }
     cnt[item] = c;
 
     // compositing record (accuracy only): rotation of the unit quaternion,
@@ -229,6 +341,7 @@ constexpr int kScanCta = 1024;
 // in one launch: a bucket's sort is a long serial chain, so every bucket
 // runs concurrently); longer ones the bitonic network, over their own list.
 constexpr int kMergeMax = 2048;
+constexpr int kMergeSmall = 1024;   // buckets up to this size: the 128-thread merge sort
 constexpr int kOrderBuckets = 33;
 __device__ __forceinline__ int order_bucket(uint32_t n) { return kOrderBuckets - 1 - (n ? 32 - __clz(n) : 0); }
 
@@ -236,7 +349,7 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
                                                           uint2* __restrict__ ranges, Status* __restrict__ st,
                                                           int64_t cap, uint32_t* __restrict__ order,
                                                           uint32_t* __restrict__ longt, uint32_t* __restrict__ cbase,
-                                                          uint32_t* __restrict__ sortl) {
+                                                          uint32_t* __restrict__ sortl, uint32_t* __restrict__ midl) {
   __shared__ unsigned long long s_w[32];
   __shared__ uint32_t s_wc[32];
   __shared__ unsigned long long s_carry;
@@ -343,8 +456,10 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
     pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & ((1u << lane) - 1u));
     if (b >= 0) order[pos] = t;
     if (t < n_tiles && rg.y - rg.x > kLongList) longt[atomicAdd(&st->n_long, 1u)] = t;
-    // buckets beyond the merge sort, for the bitonic sort
+    // buckets beyond the merge sort, for the bitonic sort; those beyond the
+    // 128-thread merge sort, for its 256-thread form
     if (t < n_tiles && rg.y - rg.x > kMergeMax) sortl[atomicAdd(&st->n_big, 1u)] = t;
+    if (t < n_tiles && rg.y - rg.x > kMergeSmall && rg.y - rg.x <= kMergeMax) midl[atomicAdd(&st->n_mid, 1u)] = t;
   }
 }
 
@@ -353,30 +468,45 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_emit(const Desc* __restrict__ D, const float* __restrict__ tab,
                                                const uint32_t* __restrict__ key, const uint32_t* __restrict__ cnt,
-                                               const float4* __restrict__ box,
-                                               uint32_t* __restrict__ tcur, const uint2* __restrict__ ranges,
-                                               Status* __restrict__ st, unsigned long long* __restrict__ pkey) {
+                                               const uint2* __restrict__ tset, uint32_t* __restrict__ tcur,
+                                               const uint2* __restrict__ ranges, Status* __restrict__ st,
+                                               unsigned long long* __restrict__ pkey) {
   __shared__ uint32_t s_cnt[kAggTiles], s_base[kAggTiles];
   if (st->overflow) return;
   const int64_t item = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const AggWin aw = agg_window(*D);
   uint32_t c = 0;
-  BinGeom g;
-  float4 pb = make_float4(0.f, 0.f, 0.f, 0.f);
   const FrameDev* F = nullptr;
   unsigned long long k = 0;
+  // the item's tiles: its stored set, or (a set that is not one range) the
+  // counting pass's enumeration repeated from the geometry
+  TileSet ts{0, -1, 0, 0};
+  bool slow = false;
+  BinGeom g;
+  float4 pb = make_float4(0.f, 0.f, 0.f, 0.f);
   if (item < D->n_items) {
     c = cnt[item];
     if (c) {
       const int f = frame_of_item(*D, item);
       F = &D->f[f];
-      const MapDev& M = D->m[F->map];
-      const int64_t i = item - F->item_base;
-      bin_geom(M.mean + 3 * i, M.ls + 2 * i, *F, g);
-      pb = pixel_box(g, *F);   // the sphere box the counting pass used (the stored box is the culling box)
       k = (static_cast<unsigned long long>(key[item]) << 32) | static_cast<uint32_t>(item);
+      const uint2 packed = tset[item];
+      slow = packed.x == kTsEnumerate;
+      if (slow) {
+        const MapDev& M = D->m[F->map];
+        const int64_t i = item - F->item_base;
+        bin_geom(M.mean + 3 * i, M.ls + 2 * i, *F, g);
+        pb = pixel_box(g, *F);   // the sphere box the counting pass used (the stored box is the culling box)
+      } else {
+        ts = unpack_set(packed);
+      }
     }
   }
+  const auto tiles = [&](auto fn) -> uint32_t {
+    if (slow) return for_each_tile(g, *F, tab, pb, fn);
+    for_each_in_set(ts, *F, fn);
+    return static_cast<uint32_t>((ts.r1 - ts.r0 + 1) * ts.nc);
+  };
   // the enumeration repeats the counting pass exactly, so every slot lies
   // inside the tile's run; a slot outside it is dropped and recorded
   const auto put = [&](uint32_t t, uint32_t pos) {
@@ -385,7 +515,7 @@ __global__ void __launch_bounds__(256) k_emit(const Desc* __restrict__ D, const 
   };
   if (!aw.local) {
     if (c) {
-      const uint32_t n = for_each_tile(g, *F, tab, pb, [&](uint32_t t) { put(t, atomicAdd(tcur + t, 1u)); });
+      const uint32_t n = tiles([&](uint32_t t) { put(t, atomicAdd(tcur + t, 1u)); });
       if (n != c) st->check = 1u;
     }
     return;
@@ -394,7 +524,7 @@ __global__ void __launch_bounds__(256) k_emit(const Desc* __restrict__ D, const 
   for (uint32_t t = threadIdx.x; t < aw.n; t += blockDim.x) s_cnt[t] = 0u;
   __syncthreads();
   if (c) {
-    const uint32_t n = for_each_tile(g, *F, tab, pb, [&](uint32_t t) { atomicAdd(s_cnt + (t - aw.base), 1u); });
+    const uint32_t n = tiles([&](uint32_t t) { atomicAdd(s_cnt + (t - aw.base), 1u); });
     if (n != c) st->check = 1u;
   }
   __syncthreads();
@@ -406,7 +536,7 @@ __global__ void __launch_bounds__(256) k_emit(const Desc* __restrict__ D, const 
     }
   }
   __syncthreads();
-  if (c) for_each_tile(g, *F, tab, pb, [&](uint32_t t) {
+  if (c) tiles([&](uint32_t t) {
     const uint32_t lt = t - aw.base;
     put(t, s_base[lt] + atomicAdd(s_cnt + lt, 1u));
   });
@@ -419,7 +549,6 @@ __global__ void __launch_bounds__(256) k_emit(const Desc* __restrict__ D, const 
 // compares i with its mirror i ^ (k - 1), the later steps are half-cleaners
 // (i, i + j).  Every comparator puts the minimum at the lower index, so
 // positions past the end of a bucket act as +infinity and are never touched.
-constexpr int kSortCta = 512;
 constexpr int kSortSmem = 4096;   // keys sorted in shared memory at once
 
 __device__ __forceinline__ void cas(unsigned long long* a, uint32_t i, uint32_t j) {
@@ -521,25 +650,29 @@ __device__ __forceinline__ void sort8(unsigned long long (&k)[8]) {
 // 8-key rows of consecutive threads start in different banks.
 __device__ __forceinline__ uint32_t pad8(uint32_t x) { return x + (x >> 3); }
 
-constexpr int kMergeCta = kMergeMax / 8;   // 8 keys per thread
+// Barrier of the threads sorting one bucket: the whole CTA (id 0), or one
+// half of it (ids 1, 2 with 128 threads each), so that the two halves of a
+// CTA sort two buckets independently.
+template <int ID>
+__device__ __forceinline__ void part_sync(uint32_t nthr) {
+  if (ID == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(nthr) : "memory");
+}
 
-__global__ void __launch_bounds__(kMergeCta) k_tile_sort_merge(const uint2* __restrict__ ranges,
-                                                               const Status* __restrict__ st,
-                                                               const unsigned long long* __restrict__ pkey,
-                                                               uint32_t* __restrict__ ptile,
-                                                               uint32_t* __restrict__ pv) {
-  __shared__ unsigned long long sa[kMergeMax + kMergeMax / 8], sb[kMergeMax + kMergeMax / 8];
-  if (st->overflow) return;
-  const uint32_t tile = blockIdx.x;
+// One bucket of at most 8 * nthr keys sorted by threads t = 0 .. nthr - 1 of
+// one part of a CTA (barrier BAR), in sa / sb (pad8 of 8 * nthr keys each).
+template <int BAR>
+__device__ __forceinline__ void merge_sort_bucket(uint32_t tile, const uint2* __restrict__ ranges,
+                                                  const unsigned long long* __restrict__ pkey,
+                                                  uint32_t* __restrict__ pv, unsigned long long* sa,
+                                                  unsigned long long* sb, uint32_t t, uint32_t nthr) {
   const uint2 rg = ranges[tile];
   const uint32_t n = rg.y - rg.x;
-  if (n == 0 || n > kMergeMax) return;
   uint32_t N = 8;
   while (N < n) N <<= 1;
   const unsigned long long* g = pkey + rg.x;
-  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) sa[pad8(i)] = i < n ? g[i] : ~0ull;
-  __syncthreads();
-  const uint32_t t = threadIdx.x;
+  for (uint32_t i = t; i < N; i += nthr) sa[pad8(i)] = i < n ? g[i] : ~0ull;
+  part_sync<BAR>(nthr);
   const bool act = 8 * t < N;
   if (act) {
     unsigned long long k[8];
@@ -549,7 +682,7 @@ __global__ void __launch_bounds__(kMergeCta) k_tile_sort_merge(const uint2* __re
 #pragma unroll
     for (int r = 0; r < 8; ++r) sa[9 * t + r] = k[r];
   }
-  __syncthreads();
+  part_sync<BAR>(nthr);
   unsigned long long *src = sa, *dst = sb;
   for (uint32_t L = 8; L < N; L <<= 1) {
     if (act) {
@@ -575,27 +708,17 @@ __global__ void __launch_bounds__(kMergeCta) k_tile_sort_merge(const uint2* __re
         j += !takeA;
       }
     }
-    __syncthreads();
+    part_sync<BAR>(nthr);
     unsigned long long* tmp = src;
     src = dst;
     dst = tmp;
   }
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    pv[rg.x + i] = static_cast<uint32_t>(src[pad8(i)]);
-    ptile[rg.x + i] = tile;
-  }
+  for (uint32_t i = t; i < n; i += nthr) pv[rg.x + i] = static_cast<uint32_t>(src[pad8(i)]);
 }
 
-// ---- longer buckets: one CTA -----------------------------------------------
-__global__ void __launch_bounds__(kSortCta) k_tile_sort(const uint2* __restrict__ ranges, const Status* __restrict__ st,
-                                                        const uint32_t* __restrict__ sortl, uint32_t n_tiles,
-                                                        unsigned long long* __restrict__ pkey,
-                                                        uint32_t* __restrict__ ptile, uint32_t* __restrict__ pv) {
-  __shared__ unsigned long long s[kSortSmem];
-  if (st->overflow) return;
-  for (uint32_t kk = blockIdx.x; kk < st->n_big; kk += gridDim.x) {
-  __syncthreads();   // the previous tile's readers are done with s
-  const uint32_t tile = sortl[kk];
+// ---- buckets beyond 2048 keys: a bitonic network over the whole CTA --------
+__device__ void bitonic_bucket(uint32_t tile, const uint2* __restrict__ ranges, unsigned long long* __restrict__ pkey,
+                               uint32_t* __restrict__ pv, unsigned long long* s) {
   const uint2 rg = ranges[tile];
   const uint32_t n = rg.y - rg.x;
   unsigned long long* g = pkey + rg.x;
@@ -604,11 +727,8 @@ __global__ void __launch_bounds__(kSortCta) k_tile_sort(const uint2* __restrict_
     while (N < n) N <<= 1;
     chunk_load(s, g, 0, n, N);
     smem_sort(s, N);
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      pv[rg.x + i] = static_cast<uint32_t>(s[i]);
-      ptile[rg.x + i] = tile;
-    }
-    continue;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) pv[rg.x + i] = static_cast<uint32_t>(s[i]);
+    return;
   }
   // long bucket: sorted chunks of kSortSmem, then the merge steps whose
   // stride spans chunks run in global memory (this CTA only; __syncthreads
@@ -641,18 +761,73 @@ __global__ void __launch_bounds__(kSortCta) k_tile_sort(const uint2* __restrict_
       chunk_store(s, g, b, n, S);
     }
   }
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    pv[rg.x + i] = static_cast<uint32_t>(g[i]);
-    ptile[rg.x + i] = tile;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) pv[rg.x + i] = static_cast<uint32_t>(g[i]);
+}
+
+// ---- every bucket in one launch ------------------------------------------------
+// The first n_lead CTAs take the long buckets, which take longest, from the
+// tile scan's lists (beyond 2048 keys the bitonic network, then those of
+// 1025..2048 keys the merge sort over the whole CTA), looping until the lists
+// are done; every other CTA sorts two buckets of at most 1024 keys, one per
+// half (128 threads, its own named barrier).  Shared memory: two halves of
+// two 1152-key buffers, or one pair of 2304-key buffers, or 4096 keys of the
+// bitonic network.
+constexpr int kSortAllCta = 256;
+constexpr int kSortAllSmem = 2 * (kMergeMax + kMergeMax / 8);   // 4608 keys, 36 KB
+static_assert(kSortAllSmem >= kSortSmem, "the bitonic network fits the merge buffers");
+static_assert(kSortAllCta == kMergeMax / 8 && kSortAllCta == 2 * (kMergeSmall / 8), "thread counts");
+
+__global__ void __launch_bounds__(kSortAllCta) k_tile_sort_all(const uint2* __restrict__ ranges,
+                                                                const Status* __restrict__ st,
+                                                                const uint32_t* __restrict__ sortl,
+                                                                const uint32_t* __restrict__ midl,
+                                                                uint32_t n_tiles, uint32_t n_lead,
+                                                                unsigned long long* __restrict__ pkey,
+                                                                uint32_t* __restrict__ pv) {
+  __shared__ unsigned long long s[kSortAllSmem];
+  if (st->overflow) return;
+  if (blockIdx.x < n_lead) {
+    for (uint32_t k = blockIdx.x; k < st->n_big; k += n_lead) {
+      __syncthreads();   // the previous bucket's readers are done with s
+      bitonic_bucket(sortl[k], ranges, pkey, pv, s);
+    }
+    for (uint32_t k = blockIdx.x; k < st->n_mid; k += n_lead) {
+      __syncthreads();
+      merge_sort_bucket<0>(midl[k], ranges, pkey, pv, s, s + kMergeMax + kMergeMax / 8, threadIdx.x, kSortAllCta);
+    }
+    return;
   }
-  }
+  const uint32_t half = threadIdx.x >> 7;
+  const uint32_t tile = 2 * (blockIdx.x - n_lead) + half;
+  if (tile >= n_tiles) return;
+  const uint2 rg = ranges[tile];
+  const uint32_t n = rg.y - rg.x;
+  if (n == 0 || n > kMergeSmall) return;   // empty, or a list of the lead CTAs
+  unsigned long long* sa = s + half * 2 * (kMergeSmall + kMergeSmall / 8);
+  unsigned long long* sb = sa + kMergeSmall + kMergeSmall / 8;
+  if (half == 0) merge_sort_bucket<1>(tile, ranges, pkey, pv, sa, sb, threadIdx.x & 127u, 128);
+  else merge_sort_bucket<2>(tile, ranges, pkey, pv, sa, sb, threadIdx.x & 127u, 128);
+}
+
+// The tile of every pair (sorted order), written only when a caller asks for
+// it (the session's bin read-back): one CTA per tile fills its run.
+__global__ void k_fill_tile_of_pair(const uint2* __restrict__ ranges, const Status* __restrict__ st,
+                                    uint32_t* __restrict__ ptile) {
+  if (st->overflow) return;
+  const uint2 rg = ranges[blockIdx.x];
+  for (uint32_t i = rg.x + threadIdx.x; i < rg.y; i += blockDim.x) ptile[i] = blockIdx.x;
+}
+
+cudaError_t launch_fill_tile_of_pair(const WsPtrs& w, uint32_t n_tiles, cudaStream_t s) {
+  if (n_tiles) k_fill_tile_of_pair<<<n_tiles, 256, 0, s>>>(w.ranges, w.st, w.ptile);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Orchestration
 // ---------------------------------------------------------------------------
 // kernels launch_bin enqueues (memsets not counted)
-int bin_kernel_count(uint32_t) { return 6; }
+int bin_kernel_count(uint32_t) { return 5; }
 
 cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n_items, uint32_t n_tiles,
                        cudaStream_t s) {
@@ -664,17 +839,17 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
                                     static_cast<uint32_t>(loss_part_bytes() / 4));
   const int64_t ni = n_items > 0 ? n_items : 1;
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
-  k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tcur, w.st);
+  k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tset, w.tcur, w.st);
   k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work, w.longt, w.cbase,
-                                     w.sortl);
-  k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.box, w.tcur, w.ranges, w.st, w.pkey);
+                                     w.sortl, w.midl);
+  k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.tset, w.tcur, w.ranges, w.st, w.pkey);
   if (n_tiles > 0) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned few = static_cast<unsigned>(sms) < n_tiles ? static_cast<unsigned>(sms) : n_tiles;
-    k_tile_sort_merge<<<n_tiles, kMergeCta, 0, s>>>(w.ranges, w.st, w.pkey, w.ptile, w.pv);
-    k_tile_sort<<<few, kSortCta, 0, s>>>(w.ranges, w.st, w.sortl, n_tiles, w.pkey, w.ptile, w.pv);
+    const unsigned grid = few + (n_tiles + 1) / 2;
+    k_tile_sort_all<<<grid, kSortAllCta, 0, s>>>(w.ranges, w.st, w.sortl, w.midl, n_tiles, few, w.pkey, w.pv);
   }
   return cudaGetLastError();
 }

@@ -74,11 +74,12 @@ struct Status {
   unsigned int n_chunks;              // backward chunks of the last binning (kChunk list entries each)
   unsigned int count_ticket;          // mask-count CTAs finished (the last one adds up; self-resetting)
   unsigned int n_big;                 // buckets of more than 2048 keys (the bitonic sort)
+  unsigned int n_mid;                 // buckets of 1025..2048 keys (the wide merge sort)
 };
 
 struct Layout {
-  size_t desc, status, tables, rec, box, key, cnt, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part, cbase,
-      ckpt, sortl, total;
+  size_t desc, status, tables, rec, box, key, cnt, tset, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part,
+      cbase, ckpt, sortl, midl, total;
   int64_t items_cap, pairs_cap, chunks_cap;
   uint32_t tiles_cap;
   uint32_t tables_cap;     // floats
@@ -93,6 +94,7 @@ struct WsPtrs {
   float4* box;             // [items] conservative pixel box: row_lo, row_hi, col centre, col half-width
   uint32_t* key;           // depth key per item
   uint32_t* cnt;           // tile count per item
+  uint2* tset;             // tile set per item: rows (first | last << 16), columns (first | count << 16)
   uint32_t* tcur;          // [tiles] pair counts, then fill cursors
   unsigned long long* pkey;// [pairs] (depth key << 32 | item), bucketed by tile, then sorted
   uint32_t* ptile;         // [pairs] tile of every pair (sorted order)
@@ -105,6 +107,7 @@ struct WsPtrs {
   uint32_t* cbase;         // [tiles] first backward chunk of every tile
   float* ckpt;             // [chunks][6][tile pixels] forward checkpoint at every chunk end
   uint32_t* sortl;         // [tiles] tiles whose bucket exceeds the merge sort (st->n_big of them)
+  uint32_t* midl;          // [tiles] tiles whose bucket takes the wide merge sort (st->n_mid of them)
 };
 
 inline WsPtrs ws_ptrs(void* base, const Layout& L) {
@@ -117,6 +120,7 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.box = reinterpret_cast<float4*>(b + L.box);
   p.key = reinterpret_cast<uint32_t*>(b + L.key);
   p.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
+  p.tset = reinterpret_cast<uint2*>(b + L.tset);
   p.tcur = reinterpret_cast<uint32_t*>(b + L.tcur);
   p.pkey = reinterpret_cast<unsigned long long*>(b + L.pkey);
   p.ptile = reinterpret_cast<uint32_t*>(b + L.ptile);
@@ -129,6 +133,7 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.cbase = reinterpret_cast<uint32_t*>(b + L.cbase);
   p.ckpt = reinterpret_cast<float*>(b + L.ckpt);
   p.sortl = reinterpret_cast<uint32_t*>(b + L.sortl);
+  p.midl = reinterpret_cast<uint32_t*>(b + L.midl);
   return p;
 }
 
@@ -584,6 +589,8 @@ cudaError_t launch_write_desc(const Desc& h, Desc* d, Status* st, cudaStream_t s
 cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n_items, uint32_t n_tiles,
                        cudaStream_t s);
 int bin_kernel_count(uint32_t n_tiles);
+// the tile of every pair of the last binning into w.ptile (on request only)
+cudaError_t launch_fill_tile_of_pair(const WsPtrs& w, uint32_t n_tiles, cudaStream_t s);
 cudaError_t launch_raster_fwd(const Layout& L, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch, int group,
                               int persistent, cudaStream_t s);
 // chunked: the forward was the shared-memory walk, which wrote the chunk

@@ -59,7 +59,7 @@ def test_results_same_alone_and_in_the_mix(workload):
         # the first iteration renders identical inputs: identical loss; later
         # ones differ only through the order of float atomics in the gradients
         assert l1[sid][0] == losses[sid][0]
-        assert np.allclose(l1[sid], losses[sid], rtol=1e-4)
+        assert np.allclose(l1[sid], losses[sid], rtol=1e-3)
         for a, b in zip(params[sid], p1[sid]):
             d = np.abs(a - b)
             assert np.mean(d <= 1e-6 + 1e-6 * np.abs(b)) > 0.99
@@ -71,8 +71,12 @@ def test_plain_server_matches_batched(workload):
     _, pb, lb = _serve(workload, sids, slots=8)
     _, pp, lp = _serve(workload, sids, plain=True)
     for sid in sids:
+        # the first iteration renders identical inputs: identical loss; the
+        # later ones differ through the order of float atomics in the
+        # gradients, which these small maps' losses (swinging twentyfold from
+        # one iteration to the next) amplify to about 1e-4
         assert lp[sid][0] == lb[sid][0]
-        assert np.allclose(lp[sid], lb[sid], rtol=1e-4)
+        assert np.allclose(lp[sid], lb[sid], rtol=1e-3), (sid, lp[sid], lb[sid])
 
 
 def test_admission_by_budget(workload):
