@@ -214,3 +214,53 @@ def test_track_subset_gradients_vs_oracle_and_differences(oracle):
         used += 1
     assert used >= 15, used
     w.close()
+
+
+def test_window_grows_and_budgets_its_map_on_the_device(oracle):
+    """A box-room window takes a keyframe scan of the room from another pose
+    (lgs_keyframe_init: the new surfels join with zero Adam moments), then one
+    map-management step (lgs_map_manage, lgs_map_gather): every row of the
+    new map carries the moments of its source row, children start at zero,
+    the source mapping equals the oracle's management of the same map and
+    signals, and two more iterations give a finite loss with the session's
+    status OK."""
+    import torch
+    from oracle import manage as omg
+    from paper_2607_04127_gb300 import mapping
+    surf, frame, tgt = scenes.box_room()
+    win = mapping.MappingWindow(surf, [frame], [tgt], autograd=False)
+    win.run(3)
+    # a scan of the same room from 1 m aside, as points in its sensor frame
+    rng = np.random.default_rng(3)
+    pose = scenes.pose_matrix(0.3, (1.0, -0.5, 2.0))
+    kf = scenes.Frame(32, 512, 16, 16, -math.radians(15), math.radians(15), pose)
+    _, pw, _, valid = scenes.simulate_scan(scenes.Scene(room=(-10.0, 10.0, -10.0, 10.0, 0.0, 5.0)), kf, rng)
+    P = np.asarray(pose, np.float64).reshape(3, 4)
+    pts = ((pw.reshape(-1, 3)[valid.reshape(-1)] - P[:, 3]) @ P[:, :3]).astype(np.float32)
+    n0 = win.n
+    m0, v0 = win.m.clone(), win.v.clone()
+    win.insert_keyframe(torch.from_numpy(pts).cuda(), P.reshape(-1))
+    n1 = win.n
+    assert n1 == n0 + len(pts)
+    # the old rows keep their moments, the new ones start at zero
+    for old, new in ((m0, win.m), (v0, win.v)):
+        for a, b in zip(mapping.state_blocks(old, n0), mapping.state_blocks(new, n1)):
+            assert torch.equal(b[:n0], a) and not b[n0:].any()
+    win.run(1)
+    # management with signals from the map's own neighbourhoods
+    host = [p.detach().cpu().numpy() for p in win.params]
+    lam, res = scenes.manage_signals(host[0])
+    m1, v1 = win.m.clone(), win.v.clone()
+    counts, src = win.manage(torch.from_numpy(lam).cuda(), torch.from_numpy(res).cuda())
+    want = omg.manage(*host, lam, res, omg.Params())
+    src = src.cpu().numpy()
+    assert counts == want["counts"].tolist() and np.array_equal(src, want["src"])
+    child = want["role"] != 0
+    for old, new in ((m1, win.m), (v1, win.v)):
+        for a, b in zip(mapping.state_blocks(old, n1), mapping.state_blocks(new, counts[0])):
+            a, b = a.cpu().numpy(), b.cpu().numpy()
+            assert np.array_equal(b[~child], a[src[~child]]) and not b[child].any()
+    L = win.run(2)
+    assert torch.isfinite(L).all()
+    win.rast.session.check_status()
+    win.close()

@@ -119,3 +119,24 @@ def test_autograd_window_keeps_leaf_parameters(monkeypatch):
         _FakeManager.src = torch.tensor([0, 2, 2, 3, 5], dtype=torch.int32)
         _FakeManager.role = torch.tensor([0, 1, 2, 0, 0], dtype=torch.uint8)
     assert all(p.is_leaf and p.requires_grad for p in w.params) and w.grads is None
+
+
+def test_first_step_of_an_inserted_row_at_a_late_step(oracle):
+    """Rows that join the window (keyframe insertion, split children) start
+    from zero Adam moments but share the window's step count t, so their
+    bias correction is that of step t, not 1: their first update is
+    lr (1 - b1) / (1 - b1^t) / sqrt((1 - b2) / (1 - b2^t)) (2.51 lr at
+    t = 1000, sqrt(10) lr as t grows, for the default betas), where a fresh
+    optimiser would move them by lr.  This is the behaviour the window has (a
+    per-row step count would need a per-row bias correction in the Adam
+    kernel)."""
+    import math
+    import numpy as np
+    lr, g, b1, b2 = 1e-3, np.array([0.37, -2.0e-4, 5.0]), 0.9, 0.999
+    for t in (1000, 100_000):
+        p, _, _ = oracle.adam(np.zeros(3), g, np.zeros(3), np.zeros(3), t, lr)
+        step = lr * (1 - b1) / (1 - b1 ** t) / math.sqrt((1 - b2) / (1 - b2 ** t))
+        assert np.allclose(np.abs(p), step, rtol=1e-9)
+    assert step == np.float64(step) and abs(step / lr - math.sqrt(10.0)) < 1e-9
+    p1, _, _ = oracle.adam(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr)
+    assert np.allclose(np.abs(p1), lr, rtol=1e-9)
