@@ -776,7 +776,7 @@ def street_roofline(pk, kernels_ms, ms_step, c, n_items, hw, n_surf, tuning):
               B_PREPROCESS * n_items + B_EMIT * P + B_SORT_PASS * P),
         stage("forward with the loss epilogue (A5, A6)", kernels_ms["fwd"],
               B_FWD_PIXEL * hw + B_RECORD * P + B_LOSS_PIXEL * hw, I_EVAL * E_f, M_EVAL * E_f),
-        stage("mask counts, scale regulariser, loss vector (A6)", kernels_ms["loss"], 16 * hw + 16 * n_surf),
+        stage("mask counts and scale regulariser (A6; the loss vector is written by the forward)", kernels_ms["loss"], 16 * hw + 16 * n_surf),
         stage("backward (A7)", kernels_ms["bwd"], B_RECORD * P, I_BWD_CONTRIB * C, M_BWD_CONTRIB * C),
         stage("chain to the parameters (A8)", kernels_ms["bwd_chain"], B_CHAIN * n_surf),
     ]

@@ -904,16 +904,14 @@ lgs_status lgs_render_fwd_loss_batch(lgs_session s, const lgs_surfels* maps, int
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if ((e = write_desc(s, d, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
-  if ((e = timed(s, LGS_TIME_LOSS, cs, [&] { return lgs::launch_loss_counts(w, d, cs); })) != cudaSuccess)
-    return cuda_fail(e, "loss counts");
-  if ((e = timed(s, LGS_TIME_FWD, cs,
-                 [&] { return lgs::launch_raster_fwd_loss(w, d, w.pv, s->tune.persistent, *params, cs); })) !=
-      cudaSuccess)
-    return cuda_fail(e, "raster_fwd_loss");
   if ((e = timed(s, LGS_TIME_LOSS, cs,
-                 [&] { return lgs::launch_loss_finish(w, d, *params, scale_grad, loss_out, cs); })) != cudaSuccess)
-    return cuda_fail(e, "loss finish");
-  s->launches += 4;   // counts, per-tile and long-list forward, regulariser and loss vector
+                 [&] { return lgs::launch_loss_counts(w, d, *params, scale_grad, cs); })) != cudaSuccess)
+    return cuda_fail(e, "loss counts");
+  if ((e = timed(s, LGS_TIME_FWD, cs, [&] {
+         return lgs::launch_raster_fwd_loss(w, d, w.pv, s->tune.persistent, *params, loss_out, cs);
+       })) != cudaSuccess)
+    return cuda_fail(e, "raster_fwd_loss");
+  s->launches += 3;   // counts and regulariser, per-tile forward, long-list forward (which writes the loss vector)
   s->last_stream = cs;
   s->ckpt_valid = true;
   return LGS_OK;

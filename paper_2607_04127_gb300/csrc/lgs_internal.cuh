@@ -563,6 +563,56 @@ __device__ __forceinline__ void cta_add_fix(long long v, unsigned long long* acc
   }
 }
 
+// Loss vector (Eq. totalloss) from the fixed-point totals of a loss call:
+// per frame the means of its terms, per map the frames' image terms over its
+// frame count plus lambda_s times its regulariser sum, and the total; then
+// the totals, the mask counts and the ticket are cleared for the next call.
+// Run by the first warp of the CTA that finished last (after a fence).
+__device__ __forceinline__ void finish_loss_vector(const Desc& D, const lgs_loss_params& P, int* ctot,
+                                                   unsigned long long* acc, float* out, Status* st) {
+  __shared__ float s_fr[LGS_MAX_FRAMES];
+  const int lane = threadIdx.x & 31;
+  __threadfence();
+  if (lane == 0) st->loss_ticket = 0;
+  const int nf = D.n_frames, nmap = D.n_maps;
+  for (int f = lane; f < nf; f += 32) {
+    const int nd = __ldcg(ctot + 2 * f), nn = __ldcg(ctot + 2 * f + 1);
+    const unsigned long long* a = acc + 4 * f;
+    const float Ld = fix_mean(static_cast<long long>(__ldcg(a)), kFixD, nd);
+    const float La = fix_mean(static_cast<long long>(__ldcg(a + 1)), kFixU, nd);
+    const float Ln = fix_mean(static_cast<long long>(__ldcg(a + 2)), kFixU, nn);
+    const float Ls = fix_mean(static_cast<long long>(__ldcg(a + 3)), kFixU, nd);
+    float* o = out + 1 + LGS_LOSS_TERMS * f;
+    o[0] = Ld;
+    o[1] = La;
+    o[2] = Ln;
+    o[3] = Ls;
+    s_fr[f] = (Ld + P.lambda_alpha * La + P.lambda_n * P.lambda_ng * Ln + P.lambda_n * P.lambda_ns * Ls) /
+              static_cast<float>(D.m[D.f[f].map].n_frames);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    float Lmap[LGS_MAX_MAPS];
+    for (int m = 0; m < nmap; ++m) Lmap[m] = 0.0f;
+    for (int f = 0; f < nf; ++f) Lmap[D.f[f].map] += s_fr[f];
+    float L = 0.0f;
+    for (int m = 0; m < nmap; ++m) {
+      const long long sr = static_cast<long long>(__ldcg(acc + 4 * LGS_MAX_FRAMES + m));
+      Lmap[m] += P.lambda_s * (static_cast<float>(sr) / kFixD);
+      out[1 + LGS_LOSS_TERMS * nf + m] = Lmap[m];
+      L += Lmap[m];
+    }
+    out[0] = L;
+  }
+  __syncwarp();
+  for (int f = lane; f < nf; f += 32) {
+    ctot[2 * f] = 0;
+    ctot[2 * f + 1] = 0;
+    for (int k = 0; k < 4; ++k) acc[4 * f + k] = 0ull;
+  }
+  for (int m = lane; m < nmap; m += 32) acc[4 * LGS_MAX_FRAMES + m] = 0ull;
+}
+
 // Frame of a global tile id (binary search over the frames' tile bases).
 __device__ __forceinline__ int frame_of_tile(const Desc& D, uint32_t tile) {
   int lo = 0, hi = D.n_frames - 1;
@@ -634,10 +684,9 @@ cudaError_t launch_trackable(const lgs_surfels& M, const uint8_t* mask, const in
                              float logit_min, float thick, float eps, float w_max, void* scratch, int32_t* index,
                              float* mean, float* cov, float* weight, int64_t* count, cudaStream_t s);
 cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_t* pv, int persistent,
-                                   const lgs_loss_params& p, cudaStream_t s);
-cudaError_t launch_loss_counts(const WsPtrs& w, const Desc& h, cudaStream_t s);
-cudaError_t launch_loss_finish(const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
-                               float* loss_out, cudaStream_t s);
+                                   const lgs_loss_params& p, float* loss_out, cudaStream_t s);
+cudaError_t launch_loss_counts(const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
+                               cudaStream_t s);
 size_t noalloc_scratch_bytes();
 cudaError_t noalloc_scratch(void** out);
 cudaError_t launch_image_loss_noalloc(void* scratch, int n_frames, const int32_t* H, const int32_t* W,

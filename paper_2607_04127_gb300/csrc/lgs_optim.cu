@@ -31,16 +31,33 @@ __device__ __forceinline__ int map_of_surfel(const Desc& D, int64_t s) {
   return lo;
 }
 
-__global__ void __launch_bounds__(256, 4) k_preprocess_bwd(const Desc* __restrict__ D, float* __restrict__ g13) {
+__global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__ D, float* __restrict__ g13) {
   const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= D->n_surf) return;
   const int m = map_of_surfel(*D, s);
   const MapDev& M = D->m[m];
   const int64_t i = s - M.surf_base;
   if (i >= M.n) return;
+  // every load that does not depend on another one is issued here, before
+  // the first store (the stores below would keep the compiler from moving
+  // them up): the parameters, the gradient sums this surfel adds into, and
+  // the moments of the map's first frame; the kernel is bound by the latency
+  // of these loads, not by their bytes
   const float4 q = reinterpret_cast<const float4*>(M.quat)[i];
   const float lg = M.logit[i];
   const float ls0 = M.ls[2 * i], ls1 = M.ls[2 * i + 1];
+  const float oq0 = M.d_quat[4 * i], oq1 = M.d_quat[4 * i + 1], oq2 = M.d_quat[4 * i + 2], oq3 = M.d_quat[4 * i + 3];
+  const float om0 = M.d_mean[3 * i], om1 = M.d_mean[3 * i + 1], om2 = M.d_mean[3 * i + 2];
+  const float ol0 = M.d_ls[2 * i], ol1 = M.d_ls[2 * i + 1], olg = M.d_logit[i];
+  int f0 = 0;
+  while (f0 < D->n_frames && D->f[f0].map != m) ++f0;
+  float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa, pc = pa;
+  if (f0 < D->n_frames) {
+    const float4* gp = reinterpret_cast<const float4*>(g13 + 16 * (D->f[f0].item_base + i));
+    pa = gp[0];
+    pb = gp[1];
+    pc = gp[2];
+  }
   const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
   const float inv = rsqrtf(qn2);
   const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
@@ -52,11 +69,11 @@ __global__ void __launch_bounds__(256, 4) k_preprocess_bwd(const Desc* __restric
   float gm[3] = {0.f, 0.f, 0.f}, G0[3] = {0.f, 0.f, 0.f}, G1[3] = {0.f, 0.f, 0.f}, G2[3] = {0.f, 0.f, 0.f};
   float gls0 = 0.f, gls1 = 0.f, gsum = 0.f;
   bool any = false;
-  for (int f = 0; f < D->n_frames; ++f) {
+  for (int f = f0; f < D->n_frames; ++f) {
     const FrameDev& F = D->f[f];
     if (F.map != m) continue;
     float4* gp = reinterpret_cast<float4*>(g13 + 16 * (F.item_base + i));
-    const float4 a = gp[0], b = gp[1], c = gp[2];
+    const float4 a = f == f0 ? pa : gp[0], b = f == f0 ? pb : gp[1], c = f == f0 ? pc : gp[2];
     if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f && b.x == 0.f && b.y == 0.f && b.z == 0.f &&
         b.w == 0.f && c.x == 0.f && c.y == 0.f && c.z == 0.f && c.w == 0.f)
       continue;
@@ -110,16 +127,16 @@ __global__ void __launch_bounds__(256, 4) k_preprocess_bwd(const Desc* __restric
                    G1[2] * 2.f * y + G2[0] * 2.f * x + G2[1] * 2.f * y;
   // through q_hat = q / |q|
   const float pr = gw * w + gx * x + gy * y + gz * z;
-  M.d_quat[4 * i] += (gw - w * pr) * inv;
-  M.d_quat[4 * i + 1] += (gx - x * pr) * inv;
-  M.d_quat[4 * i + 2] += (gy - y * pr) * inv;
-  M.d_quat[4 * i + 3] += (gz - z * pr) * inv;
-  M.d_mean[3 * i] += gm[0];
-  M.d_mean[3 * i + 1] += gm[1];
-  M.d_mean[3 * i + 2] += gm[2];
-  M.d_ls[2 * i] += gls0;
-  M.d_ls[2 * i + 1] += gls1;
-  M.d_logit[i] += gsum * (1.f - alpha);
+  M.d_quat[4 * i] = oq0 + (gw - w * pr) * inv;
+  M.d_quat[4 * i + 1] = oq1 + (gx - x * pr) * inv;
+  M.d_quat[4 * i + 2] = oq2 + (gy - y * pr) * inv;
+  M.d_quat[4 * i + 3] = oq3 + (gz - z * pr) * inv;
+  M.d_mean[3 * i] = om0 + gm[0];
+  M.d_mean[3 * i + 1] = om1 + gm[1];
+  M.d_mean[3 * i + 2] = om2 + gm[2];
+  M.d_ls[2 * i] = ol0 + gls0;
+  M.d_ls[2 * i + 1] = ol1 + gls1;
+  M.d_logit[i] = olg + gsum * (1.f - alpha);
 }
 
 cudaError_t launch_preprocess_bwd(const Layout&, const WsPtrs& w, const Desc& h, cudaStream_t s) {
@@ -137,9 +154,40 @@ cudaError_t launch_preprocess_bwd(const Layout&, const WsPtrs& w, const Desc& h,
 // ---------------------------------------------------------------------------
 constexpr int kLossBlocks = 256;  // CTAs per frame and map
 
+// Eq. scaleloss of map mi over this CTA's share of its surfels: sum of
+// max(s) - s_max over the surfels above the threshold (fixed point) into the
+// map's accumulator, and lambda_s max(s) added to d log s of the larger axis.
+__device__ void scale_reg_row(const Desc& D, const lgs_loss_params& P, int write_grad, unsigned long long* acc,
+                              int mi, long long* s_ll) {
+  const MapDev& M = D.m[mi];
+  long long sr = 0;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < M.n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float s0 = expf(M.ls[2 * i]), s1 = expf(M.ls[2 * i + 1]);
+    const bool first = s0 >= s1;
+    const float sm = first ? s0 : s1;
+    if (sm > P.s_max) {
+      // the sum takes at most 1 km per surfel (the gradient is exact)
+      sr += to_fix(fminf(sm - P.s_max, 1e3f), kFixD);
+      if (write_grad) M.d_ls[2 * i + (first ? 0 : 1)] += P.lambda_s * sm;
+    }
+  }
+  cta_add_fix(sr, acc + 4 * LGS_MAX_FRAMES + mi, s_ll);
+}
+
 // Mask counts |M_D|, |M_N| of every frame: one integer atomic per CTA into
-// ctot[F][2] (zero on entry: cleared by the binning and by the loss).
-__global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, int* __restrict__ ctot) {
+// ctot[F][2] (zero on entry: cleared by the binning and by the loss).  Rows
+// y >= n_frames (when launched with them): the scale regulariser of map
+// y - n_frames, which needs no rendered value, so a forward with the
+// image-loss epilogue leaves only the loss vector for after it.
+__global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, int* __restrict__ ctot,
+                                                    lgs_loss_params P, int write_grad,
+                                                    unsigned long long* __restrict__ acc) {
+  if (blockIdx.y >= static_cast<unsigned>(D->n_frames)) {
+    __shared__ long long s_ll[8];
+    scale_reg_row(*D, P, write_grad, acc, blockIdx.y - D->n_frames, s_ll);
+    return;
+  }
   const FrameDev& F = D->f[blockIdx.y];
   const int HW = F.H * F.W;
   int md = 0, mn = 0;
@@ -292,21 +340,7 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
     cta_add_fix(ln, acc + 4 * f + 2, s_ll);
     cta_add_fix(ls, acc + 4 * f + 3, s_ll);
   } else {
-    const int mi = blockIdx.y - nfr;
-    const MapDev& M = D->m[mi];
-    long long sr = 0;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < M.n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-      const float s0 = expf(M.ls[2 * i]), s1 = expf(M.ls[2 * i + 1]);
-      const bool first = s0 >= s1;
-      const float sm = first ? s0 : s1;
-      if (sm > P.s_max) {
-        // the sum takes at most 1 km per surfel (the gradient is exact)
-        sr += to_fix(fminf(sm - P.s_max, 1e3f), kFixD);
-        if (write_grad) M.d_ls[2 * i + (first ? 0 : 1)] += P.lambda_s * sm;
-      }
-    }
-    cta_add_fix(sr, acc + 4 * LGS_MAX_FRAMES + mi, s_ll);
+    scale_reg_row(*D, P, write_grad, acc, blockIdx.y - nfr, s_ll);
   }
 
   // last CTA: the means and the loss vector from the fixed-point totals (no
@@ -319,72 +353,26 @@ __global__ void __launch_bounds__(256) k_loss_main(const Desc* __restrict__ D, S
   }
   __syncthreads();
   if (!s_last || threadIdx.x >= 32) return;
-  __threadfence();
-  __shared__ float s_fr[LGS_MAX_FRAMES];
-  const int lane = threadIdx.x;
-  if (lane == 0) st->loss_ticket = 0;
-  const int nf = D->n_frames, nmap = D->n_maps;
-  for (int f = lane; f < nf; f += 32) {
-    const int nd = __ldcg(ctot + 2 * f), nn = __ldcg(ctot + 2 * f + 1);
-    const unsigned long long* a = acc + 4 * f;
-    const float Ld = fix_mean(static_cast<long long>(__ldcg(a)), kFixD, nd);
-    const float La = fix_mean(static_cast<long long>(__ldcg(a + 1)), kFixU, nd);
-    const float Ln = fix_mean(static_cast<long long>(__ldcg(a + 2)), kFixU, nn);
-    const float Ls = fix_mean(static_cast<long long>(__ldcg(a + 3)), kFixU, nd);
-    float* o = out + 1 + LGS_LOSS_TERMS * f;
-    o[0] = Ld;
-    o[1] = La;
-    o[2] = Ln;
-    o[3] = Ls;
-    s_fr[f] = (Ld + P.lambda_alpha * La + P.lambda_n * P.lambda_ng * Ln + P.lambda_n * P.lambda_ns * Ls) /
-              static_cast<float>(D->m[D->f[f].map].n_frames);
-  }
-  __syncwarp();
-  if (lane == 0) {
-    float Lmap[LGS_MAX_MAPS];
-    for (int m = 0; m < nmap; ++m) Lmap[m] = 0.0f;
-    for (int f = 0; f < nf; ++f) Lmap[D->f[f].map] += s_fr[f];
-    float L = 0.0f;
-    for (int m = 0; m < nmap; ++m) {
-      const long long sr = static_cast<long long>(__ldcg(acc + 4 * LGS_MAX_FRAMES + m));
-      Lmap[m] += P.lambda_s * (static_cast<float>(sr) / kFixD);
-      out[1 + LGS_LOSS_TERMS * nf + m] = Lmap[m];
-      L += Lmap[m];
-    }
-    out[0] = L;
-  }
-  __syncwarp();
-  for (int f = lane; f < nf; f += 32) {
-    ctot[2 * f] = 0;
-    ctot[2 * f + 1] = 0;
-    for (int k = 0; k < 4; ++k) acc[4 * f + k] = 0ull;
-  }
-  for (int m = lane; m < nmap; m += 32) acc[4 * LGS_MAX_FRAMES + m] = 0ull;
+  finish_loss_vector(*D, P, ctot, acc, out, st);
 }
 
 cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
                         float* loss_out, cudaStream_t s) {
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(w.loss_part);
   int* ctot = loss_counts_ptr(w);
-  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, ctot);
+  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, ctot, p, 0, acc);
   k_loss_main<<<dim3(kLossBlocks, h.n_frames + h.n_maps), 256, 0, s>>>(w.desc, w.st, p, scale_grad ? 1 : 0, ctot,
                                                                         acc, loss_out, h.n_frames);
   return cudaGetLastError();
 }
 
-// The loss around a forward with the image-loss epilogue: mask counts before
-// it (the epilogue normalises by them), the scale regulariser and the loss
-// vector after it.
-cudaError_t launch_loss_counts(const WsPtrs& w, const Desc& h, cudaStream_t s) {
-  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, loss_counts_ptr(w));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_loss_finish(const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
-                               float* loss_out, cudaStream_t s) {
-  k_loss_main<<<dim3(kLossBlocks, h.n_maps), 256, 0, s>>>(w.desc, w.st, p, scale_grad ? 1 : 0, loss_counts_ptr(w),
-                                                          reinterpret_cast<unsigned long long*>(w.loss_part),
-                                                          loss_out, 0);
+// Before a forward with the image-loss epilogue: the mask counts (the
+// epilogue normalises by them) and the scale regulariser; the forward's
+// long-list kernel writes the loss vector when every pixel is done.
+cudaError_t launch_loss_counts(const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
+                               cudaStream_t s) {
+  k_loss_count<<<dim3(kLossBlocks, h.n_frames + h.n_maps), 256, 0, s>>>(
+      w.desc, loss_counts_ptr(w), p, scale_grad ? 1 : 0, reinterpret_cast<unsigned long long*>(w.loss_part));
   return cudaGetLastError();
 }
 

@@ -679,8 +679,9 @@ __device__ __forceinline__ void stage_hit(const float4* __restrict__ rec, uint32
 // the warp and added to the frame's loss sums (one atomic per term and warp).
 struct LossEpi {
   lgs_loss_params P;
-  const int* ctot;               // mask counts [frame][2], complete before the forward
-  unsigned long long* acc;       // fixed-point sums [frame][4]
+  int* ctot;                     // mask counts [frame][2], complete before the forward
+  unsigned long long* acc;       // fixed-point sums [frame][4], then [maps] of the regulariser
+  float* out;                    // loss vector, written by the long-list forward's last CTA
 };
 
 __device__ __forceinline__ void loss_epilogue(const Desc& D, const LossEpi& L, int f, bool inside, int64_t pix,
@@ -1180,10 +1181,9 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
                                                   LossEpi loss) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_long = st->n_long;
-  if (n_long == 0) return;
   uint32_t evals = 0, contrib = 0, alg = 0;
   LongPix P;
-  while (long_item(*D, ranges, longt, n_long, warp_claim(&st->long_counter_fwd), P)) {
+  while (n_long && long_item(*D, ranges, longt, n_long, warp_claim(&st->long_counter_fwd), P)) {
     if (!P.inside) continue;
     const FrameDev& F = *P.F;
     float dx, dy, dz;
@@ -1252,7 +1252,7 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
     // the warp holds one pixel: lane 0 alone takes its loss terms
     if (LOSS) loss_epilogue(*D, loss, static_cast<int>(P.F - D->f), lane == 0, P.pix, P.HW, A, St, Sx, Sy, Sz);
   }
-  long_finish(&st->long_counter_fwd, &st->long_done_fwd);
+  if (n_long) long_finish(&st->long_counter_fwd, &st->long_done_fwd);
   unsigned long long ev = evals, co = contrib, al = alg;
   for (int o = 16; o > 0; o >>= 1) {
     ev += __shfl_xor_sync(0xffffffffu, ev, o);
@@ -1261,6 +1261,19 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
   if (lane == 0 && ev) atomicAdd(&st->evals_fwd, ev);
   if (lane == 0 && co) atomicAdd(&st->contrib_fwd, co);
   if (lane == 0 && al) atomicAdd(&st->alg_fwd, al);
+  if (LOSS) {
+    // this launch follows the per-tile forward on the stream, so when its
+    // last CTA is done every pixel's epilogue has added its terms: that CTA
+    // writes the loss vector (the regulariser was summed before the forward)
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(&st->loss_ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) finish_loss_vector(*D, loss.P, loss.ctot, loss.acc, loss.out, st);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_bwd_long(const Desc* __restrict__ D, const uint2* __restrict__ ranges,
@@ -1463,12 +1476,12 @@ static cudaError_t launch_raster_bwd_chunks(const WsPtrs& w, const uint32_t* pv,
 // The shared-memory forward with the image-loss epilogue (and the long-list
 // forward with the same epilogue).
 cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_t* pv, int persistent,
-                                   const lgs_loss_params& p, cudaStream_t s) {
+                                   const lgs_loss_params& p, float* loss_out, cudaStream_t s) {
   if (persistent) {
     cudaError_t e = cudaMemsetAsync(&w.st->work_counter, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
   }
-  LossEpi loss{p, loss_counts_ptr(w), reinterpret_cast<unsigned long long*>(w.loss_part)};
+  LossEpi loss{p, loss_counts_ptr(w), reinterpret_cast<unsigned long long*>(w.loss_part), loss_out};
   const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
   k_fwd_s<true><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, persistent ? w.work : nullptr, w.st,
                                              persistent, w.cbase, w.ckpt, loss);
