@@ -352,8 +352,8 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
                                                           uint32_t* __restrict__ sortl, uint32_t* __restrict__ midl) {
   __shared__ unsigned long long s_w[32];
   __shared__ uint32_t s_wc[32];
-  __shared__ unsigned long long s_carry;
-  __shared__ uint32_t s_ccarry;
+  __shared__ unsigned long long s_carry, s_tot;
+  __shared__ uint32_t s_ccarry, s_ctot;
   __shared__ uint32_t s_bucket[kOrderBuckets];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) {
@@ -383,16 +383,30 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
       s_wc[wid] = vc;
     }
     __syncthreads();
-    unsigned long long wpre = 0, tot = 0;
-    uint32_t cpre = 0, ctot = 0;
-    for (int i = 0; i < 32; ++i) {
-      if (i < wid) {
-        wpre += s_w[i];
-        cpre += s_wc[i];
+    // warp 0 turns the 32 warp totals into exclusive prefixes and the pass total
+    if (wid == 0) {
+      const unsigned long long x0 = s_w[lane];
+      const uint32_t c0 = s_wc[lane];
+      unsigned long long y = x0;
+      uint32_t yc = c0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long z = __shfl_up_sync(0xffffffffu, y, o);
+        const uint32_t zc = __shfl_up_sync(0xffffffffu, yc, o);
+        if (lane >= o) {
+          y += z;
+          yc += zc;
+        }
       }
-      tot += s_w[i];
-      ctot += s_wc[i];
+      s_w[lane] = y - x0;
+      s_wc[lane] = yc - c0;
+      if (lane == 31) {
+        s_tot = y;
+        s_ctot = yc;
+      }
     }
+    __syncthreads();
+    const unsigned long long wpre = s_w[wid], tot = s_tot;
+    const uint32_t cpre = s_wc[wid], ctot = s_ctot;
     const unsigned long long start = s_carry + wpre + v - x;
     if (t < n_tiles) {
       // offsets past the capacity are never used: the emission is skipped

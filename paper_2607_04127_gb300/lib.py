@@ -355,7 +355,13 @@ def lgs_status_of_word(out_ptr: int):
     return int(load().lgs_status_of_word(P(out_ptr))), int(w.required_pairs)
 
 
-def lgs_session_set_tuning(h, fwd_batch: int = 128, bwd_batch: int = 0, group: int = 2, persistent: int = 0):
+# The session's own defaults (lgs_session_create): every knob left out of a
+# set_tuning call takes these.
+DEFAULT_TUNING = dict(fwd_batch=0, bwd_batch=0, group=16, persistent=0)
+
+
+def lgs_session_set_tuning(h, fwd_batch: int = DEFAULT_TUNING["fwd_batch"], bwd_batch: int = DEFAULT_TUNING["bwd_batch"],
+                           group: int = DEFAULT_TUNING["group"], persistent: int = DEFAULT_TUNING["persistent"]):
     _check(load().lgs_session_set_tuning(h, _ref(lgs_tuning(fwd_batch, bwd_batch, group, persistent))))
 
 

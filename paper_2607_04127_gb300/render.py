@@ -48,7 +48,7 @@ def target_tensors(tgt, device="cuda"):
 # 200k-surfel 128 x 1024 street frame renders fastest with 8 x 8 tiles and
 # both passes as an independent walk per warp that stages the records of each
 # 32-entry chunk's hits in its own shared memory.
-DEFAULT_TUNING = dict(fwd_batch=0, bwd_batch=0, group=16, persistent=0)
+DEFAULT_TUNING = dict(lib.DEFAULT_TUNING)
 DEFAULT_TILE = (8, 8)
 
 

@@ -358,16 +358,21 @@ TUNINGS = ([dict(fwd_batch=0, bwd_batch=0, group=g, persistent=p) for g in (1, 2
 
 def test_tuning_and_tile_shape_do_not_change_results(oracle):
     """Every compositing variant and tile shape gives bit-identical forward
-    outputs and loss; gradients agree up to the order of the float atomics."""
+    outputs (n_contrib, which indexes the tile's own list, within each tile
+    shape) and loss; gradients agree up to the order of the float atomics."""
     surf, frame, tgt = scenes.box_room()
     from tests import _gpu
-    ref = _gpu.run([surf], [frame], targets=[tgt])
+    ref = _gpu.run([surf], [frame], targets=[tgt], tuning=dict(fwd_batch=0, bwd_batch=0, group=16, persistent=0))
     gref = [np.asarray(x, np.float64) for x in ref["grads"][0]]
     for tile in ((8, 8), (16, 16), (8, 32), (32, 8)):
+        # n_contrib indexes the tile's own list: compared within a tile shape
+        ref_t = _gpu.run([surf], [frame.with_tiles(*tile)], targets=[tgt],
+                         tuning=dict(fwd_batch=0, bwd_batch=0, group=16, persistent=0))
         for tun in TUNINGS:
             g = _gpu.run([surf], [frame.with_tiles(*tile)], targets=[tgt], tuning=tun)
             for k in ("A", "S_t", "S_n", "T_final"):
                 assert np.array_equal(g["fwd"][0][k], ref["fwd"][0][k]), (tile, tun, k)
+            assert np.array_equal(g["fwd"][0]["n_contrib"], ref_t["fwd"][0]["n_contrib"]), (tile, tun)
             assert np.array_equal(g["loss"], ref["loss"]), (tile, tun)
             for a, b in zip(g["grads"][0], gref):
                 assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max()), (tile, tun)
