@@ -79,7 +79,7 @@ struct Status {
 
 struct Layout {
   size_t desc, status, tables, rec, box, key, cnt, tset, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part,
-      cbase, ckpt, sortl, midl, total;
+      cbase, ckpt, cmask, sortl, midl, total;
   int64_t items_cap, pairs_cap, chunks_cap;
   uint32_t tiles_cap;
   uint32_t tables_cap;     // floats
@@ -106,6 +106,7 @@ struct WsPtrs {
   double* loss_part;       // loss partial sums and mask counts
   uint32_t* cbase;         // [tiles] first backward chunk of every tile
   float* ckpt;             // [chunks][6][tile pixels] forward checkpoint at every chunk end
+  uint32_t* cmask;         // [chunks][4 windows][tile pixels] entries each pixel composited, one bit per entry
   uint32_t* sortl;         // [tiles] tiles whose bucket exceeds the merge sort (st->n_big of them)
   uint32_t* midl;          // [tiles] tiles whose bucket takes the wide merge sort (st->n_mid of them)
 };
@@ -132,6 +133,7 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.loss_part = reinterpret_cast<double*>(b + L.loss_part);
   p.cbase = reinterpret_cast<uint32_t*>(b + L.cbase);
   p.ckpt = reinterpret_cast<float*>(b + L.ckpt);
+  p.cmask = reinterpret_cast<uint32_t*>(b + L.cmask);
   p.sortl = reinterpret_cast<uint32_t*>(b + L.sortl);
   p.midl = reinterpret_cast<uint32_t*>(b + L.midl);
   return p;

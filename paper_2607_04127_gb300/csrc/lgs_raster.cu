@@ -718,12 +718,15 @@ __device__ __forceinline__ void loss_epilogue(const Desc& D, const LossEpi& L, i
 // fastest on the street frame: 2 leaves latency exposed, 4 costs registers)
 constexpr int FWD_HITS = 3;
 
+// At most 72 registers: 14 CTAs of an 8 x 8 tile (64 threads) per SM, so
+// the 2048 tiles of a 128 x 1024 frame fit in one wave on 152 SMs (75
+// registers leave 72 tiles for a second wave).
 template <bool LOSS>
-__global__ void __launch_bounds__(kMaxTileThreads)
+__global__ void __maxnreg__(72)
     k_fwd_s(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
             const float4* __restrict__ rec, const float4* __restrict__ box, const uint32_t* __restrict__ order,
             Status* __restrict__ st, int persistent, const uint32_t* __restrict__ cbase, float* __restrict__ ckpt,
-            LossEpi loss) {
+            uint32_t* __restrict__ cmask, LossEpi loss) {
   __shared__ WarpRecs s_w[kMaxTileThreads / 32];
   const int lane = threadIdx.x & 31;
   WarpRecs& sw = s_w[threadIdx.x >> 5];
@@ -760,6 +763,9 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         ++chunk;
       }
       if (__all_sync(0xffffffffu, done)) break;
+      // the pixel's composited entries of this window, one bit each, for the
+      // chunked backward (every window the warp walks gets its word)
+      uint32_t* mword = cmask + (static_cast<int64_t>(cbase[tile]) * 4 + (base - tc.start) / 32) * npx + threadIdx.x;
       const uint32_t j = base + lane;
       uint32_t item = 0;
       bool hit = false;
@@ -768,11 +774,15 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         hit = box_hits(__ldg(box + item), wb);
       }
       uint32_t m = __ballot_sync(0xffffffffu, hit);
-      if (!m) continue;
+      if (!m) {
+        *mword = 0u;
+        continue;
+      }
       __syncwarp();
       if (hit) stage_hit(rec, item, sw, lane);
       __syncwarp();
       const int k0 = static_cast<int>(base - tc.start) + 1;
+      uint32_t cbits = 0;
       // composite one evaluated hit without branches: lanes that are done or
       // see an invalid pair add zeros and keep T (t and the weight are zeroed
       // first, so no inf or NaN of a rejected pair reaches the sums)
@@ -798,6 +808,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
         T = comp ? Tn : T;
         last = comp ? k0 + bq : last;
         contrib += comp;
+        cbits |= comp ? 1u << bq : 0u;
         stop_at = stop ? k0 + bq : stop_at;
         done = done || stop;
       };
@@ -825,6 +836,7 @@ __global__ void __launch_bounds__(kMaxTileThreads)
           if (bq[q] >= 0) composite(eq[q], r0q[q], bq[q]);
         if (__all_sync(0xffffffffu, done)) break;
       } while (m);
+      *mword = cbits;
     }
     if (tc.end > tc.start) checkpoint();
     if (tc.inside) {
@@ -973,7 +985,8 @@ constexpr int kBwdChunkCta = 256;
 __global__ void __launch_bounds__(kBwdChunkCta)
     k_bwd_c(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
             const float4* __restrict__ rec, const float4* __restrict__ box, float* __restrict__ g13,
-            const uint32_t* __restrict__ cbase, const float* __restrict__ ckpt, Status* __restrict__ st) {
+            const uint32_t* __restrict__ cbase, const float* __restrict__ ckpt, const uint32_t* __restrict__ cmask,
+            Status* __restrict__ st) {
   __shared__ WarpRecs s_w[kBwdChunkCta / 32];
   __shared__ uint32_t s_item[kBwdChunkCta / 32][32];
   const int lane = threadIdx.x & 31;
@@ -1010,7 +1023,6 @@ __global__ void __launch_bounds__(kBwdChunkCta)
     const int k_lo = static_cast<int>(c * kChunk);
     const int nc = inside ? F.nc[pix] : 0;
     const bool act = nc > k_lo;
-    const WarpBox wb = warp_box(act, r, col, F.W);
     float dx = 0.f, dy = 0.f, dz = 0.f;
     float T = 1.f, S = 0.f, gA = 0.f, gSt = 0.f, gSx = 0.f, gSy = 0.f, gSz = 0.f;
     if (act) {
@@ -1028,20 +1040,19 @@ __global__ void __launch_bounds__(kBwdChunkCta)
         S += gA * q[npx] + gSt * q[2 * npx] + gSx * q[3 * npx] + gSy * q[4 * npx] + gSz * q[5 * npx];
       }
     }
-    // entries [k_lo, k_hi) of the list, walked down in 32-entry steps; a
-    // lane takes the entries below its pixel's n_contrib
+    // entries [k_lo, k_hi) of the list, walked down in 32-entry steps: a
+    // step's hits are the entries some pixel of the warp composited (the
+    // forward's window masks), and a lane takes the ones its pixel did
     const uint32_t len = rg.y - rg.x;
     const int k_hi = static_cast<int>(min(min(static_cast<uint32_t>(k_lo) + kChunk, len),
                                           static_cast<uint32_t>(__reduce_max_sync(0xffffffffu, act ? nc : 0))));
     for (int k0 = k_lo + ((k_hi - k_lo + 31) / 32 - 1) * 32; k0 >= k_lo; k0 -= 32) {
-      uint32_t item = 0;
-      bool hit = false;
-      if (k0 + lane < k_hi) {
-        item = __ldg(pv + rg.x + k0 + lane);
-        hit = box_hits(__ldg(box + item), wb);
-      }
-      uint32_t m = __ballot_sync(0xffffffffu, hit);
+      const uint32_t word =
+          act ? __ldg(cmask + (static_cast<int64_t>(cbase[tile]) * 4 + static_cast<uint32_t>(k0) / 32) * npx + vt) : 0u;
+      uint32_t m = __reduce_or_sync(0xffffffffu, word);
       if (!m) continue;
+      const bool hit = (m >> lane) & 1u;
+      const uint32_t item = hit ? __ldg(pv + rg.x + k0 + lane) : 0u;
       __syncwarp();
       if (hit) {
         stage_hit(rec, item, sw, lane);
@@ -1051,12 +1062,12 @@ __global__ void __launch_bounds__(kBwdChunkCta)
       do {
         const int bq = 31 - __clz(m);
         m &= ~(1u << bq);
-        const bool in = k0 + bq < nc;
+        // the pixel composited this entry: its evaluation (the forward's,
+        // bit for bit) is valid
+        const bool valid = (word >> bq) & 1u;
         const float4 r0 = sw.r0[bq];
         Eval e;
         eval_pair(r0, sw.r1[bq], sw.r2[bq], sw.al[bq], dx, dy, dz, e);
-        const bool valid = in && e.valid;
-        if (!__any_sync(0xffffffffu, valid)) continue;
         // invalid lanes: zero opacity and finite inputs, so every moment is
         // exactly 0 and T, S pass through unchanged
         const float a = valid ? e.a : 0.f;
@@ -1418,7 +1429,7 @@ static cudaError_t launch_raster_fwd_tiles(const WsPtrs& w, const Desc& h, const
     case 0:
       if (group == 16)
         k_fwd_s<false><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent,
-                                                    w.cbase, w.ckpt, LossEpi{});
+                                                    w.cbase, w.ckpt, w.cmask, LossEpi{});
       else if (group == 1) k_fwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       else if (group == 2) k_fwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       else k_fwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
@@ -1469,7 +1480,7 @@ static cudaError_t launch_raster_bwd_chunks(const WsPtrs& w, const uint32_t* pv,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_c, kBwdChunkCta, 0);
   k_bwd_c<<<sms * (per_sm > 0 ? per_sm : 1), kBwdChunkCta, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13,
-                                                                     w.cbase, w.ckpt, w.st);
+                                                                     w.cbase, w.ckpt, w.cmask, w.st);
   return cudaGetLastError();
 }
 
@@ -1484,7 +1495,7 @@ cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_
   LossEpi loss{p, loss_counts_ptr(w), reinterpret_cast<unsigned long long*>(w.loss_part), loss_out};
   const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
   k_fwd_s<true><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, persistent ? w.work : nullptr, w.st,
-                                             persistent, w.cbase, w.ckpt, loss);
+                                             persistent, w.cbase, w.ckpt, w.cmask, loss);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_long(true, w, pv, s, &loss);
