@@ -778,6 +778,8 @@ __global__ void __maxnreg__(72)
         *mword = 0u;
         continue;
       }
+      const uint32_t m_hits = m;
+      const bool done_before = done;
       __syncwarp();
       if (hit) stage_hit(rec, item, sw, lane);
       __syncwarp();
@@ -788,7 +790,6 @@ __global__ void __maxnreg__(72)
       // first, so no inf or NaN of a rejected pair reaches the sums)
       const auto composite = [&](const Eval& e, const float4& r0, int bq) {
         const bool act = !done && e.valid;
-        evals += !done;
         const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.a));
         const bool stop = act && Tn < 1e-4f;
         const bool comp = act && !(Tn < 1e-4f);
@@ -806,8 +807,6 @@ __global__ void __maxnreg__(72)
         cSy = fmaf(ws, r0.y, cSy);
         cSz = fmaf(ws, r0.z, cSz);
         T = comp ? Tn : T;
-        last = comp ? k0 + bq : last;
-        contrib += comp;
         cbits |= comp ? 1u << bq : 0u;
         stop_at = stop ? k0 + bq : stop_at;
         done = done || stop;
@@ -837,6 +836,13 @@ __global__ void __maxnreg__(72)
         if (__all_sync(0xffffffffu, done)) break;
       } while (m);
       *mword = cbits;
+      // the window's statistics from its bits: composited pairs, the last
+      // one, and the hits evaluated before the pixel stopped (through the
+      // stop entry when it stopped in this window)
+      if (cbits) last = k0 + (31 - __clz(cbits));
+      contrib += __popc(cbits);
+      if (!done_before)
+        evals += __popc(stop_at >= k0 ? m_hits & (0xffffffffu >> (31 - (stop_at - k0))) : m_hits);
     }
     if (tc.end > tc.start) checkpoint();
     if (tc.inside) {
