@@ -45,8 +45,11 @@ cudaError_t launch_write_desc(const Desc& h, Desc* d, Status*, cudaStream_t s) {
 }
 
 __global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, Status* __restrict__ st,
-                         uint32_t* __restrict__ loss_acc, uint32_t loss_words) {
+                         uint32_t* __restrict__ loss_acc, uint32_t loss_words, uint32_t* __restrict__ tcount,
+                         uint32_t n_tiles) {
   const FrameDev& F = D->f[blockIdx.x];
+  // the tile counts start at zero (k_preprocess adds into them)
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_tiles; i += gridDim.x * blockDim.x) tcount[i] = 0u;
   // the loss accumulators start every binning at zero
   if (blockIdx.x == 0)
     for (uint32_t i = threadIdx.x; i < loss_words; i += blockDim.x) loss_acc[i] = 0u;
@@ -641,7 +644,7 @@ __device__ void chunk_store(const unsigned long long* s, unsigned long long* g, 
 // thread finds where its 8 outputs start in its pair of runs by a binary
 // search along the merge path (ties, which only the padding has, go to the
 // first run) and merges them sequentially.  The bucket is padded with +inf to
-// N = 8 * 2^m keys.
+// a whole number N of 8-key rows; a pass's last runs may be shorter than L.
 
 __device__ __forceinline__ void cas_reg(unsigned long long& a, unsigned long long& b) {
   const unsigned long long x = a, y = b;
@@ -682,8 +685,7 @@ __device__ __forceinline__ void merge_sort_bucket(uint32_t tile, const uint2* __
                                                   unsigned long long* sb, uint32_t t, uint32_t nthr) {
   const uint2 rg = ranges[tile];
   const uint32_t n = rg.y - rg.x;
-  uint32_t N = 8;
-  while (N < n) N <<= 1;
+  const uint32_t N = n > 8 ? (n + 7u) & ~7u : 8u;   // padded to whole 8-key rows only
   const unsigned long long* g = pkey + rg.x;
   for (uint32_t i = t; i < N; i += nthr) sa[pad8(i)] = i < n ? g[i] : ~0ull;
   part_sync<BAR>(nthr);
@@ -696,15 +698,21 @@ __device__ __forceinline__ void merge_sort_bucket(uint32_t tile, const uint2* __
 #pragma unroll
     for (int r = 0; r < 8; ++r) sa[9 * t + r] = k[r];
   }
-  part_sync<BAR>(nthr);
+  // a pass over runs of L keys reads only the 2 L keys of its thread group's
+  // pair of runs: up to L = 128 those are the 256 keys of the thread's own
+  // warp, so the passes before it need only a warp barrier
+  __syncwarp();
   unsigned long long *src = sa, *dst = sb;
   for (uint32_t L = 8; L < N; L <<= 1) {
     if (act) {
       const uint32_t tpp = L / 4;                  // threads per pair of runs
       const uint32_t pair = t / tpp, d = 8 * (t % tpp);
-      const uint32_t a0 = 2 * L * pair, b0 = a0 + L;   // runs A = [a0, a0 + L), B = [b0, b0 + L)
+      // runs A = [a0, a0 + la), B = [b0, b0 + lb): L keys each, the last
+      // ones shorter (B empty when A is the last run)
+      const uint32_t a0 = 2 * L * pair, b0 = a0 + L;
+      const uint32_t la = min(L, N - a0), lb = b0 < N ? min(L, N - b0) : 0u;
       // i = number of the first d outputs taken from A
-      uint32_t lo = d > L ? d - L : 0, hi = d < L ? d : L;
+      uint32_t lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
       while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         if (src[pad8(a0 + mid)] > src[pad8(b0 + d - mid - 1)]) hi = mid;
@@ -715,18 +723,20 @@ __device__ __forceinline__ void merge_sort_bucket(uint32_t tile, const uint2* __
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         // ties (only the +inf padding) go to A first, as in the search
-        const unsigned long long a = i < L ? src[pad8(a0 + i)] : ~0ull, b = j < L ? src[pad8(b0 + j)] : ~0ull;
-        const bool takeA = j >= L || (i < L && a <= b);
+        const unsigned long long a = i < la ? src[pad8(a0 + i)] : ~0ull, b = j < lb ? src[pad8(b0 + j)] : ~0ull;
+        const bool takeA = j >= lb || (i < la && a <= b);
         dst[o + r] = takeA ? a : b;
         i += takeA;
         j += !takeA;
       }
     }
-    part_sync<BAR>(nthr);
+    if (2 * L <= 128) __syncwarp();
+    else part_sync<BAR>(nthr);
     unsigned long long* tmp = src;
     src = dst;
     dst = tmp;
   }
+  part_sync<BAR>(nthr);   // the list is written from every warp's keys
   for (uint32_t i = t; i < n; i += nthr) pv[rg.x + i] = static_cast<uint32_t>(src[pad8(i)]);
 }
 
@@ -845,12 +855,8 @@ int bin_kernel_count(uint32_t) { return 5; }
 
 cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n_items, uint32_t n_tiles,
                        cudaStream_t s) {
-  cudaError_t e;
-  const uint32_t T = n_tiles > 0 ? n_tiles : 1;
-  e = cudaMemsetAsync(w.tcur, 0, sizeof(uint32_t) * T, s);
-  if (e != cudaSuccess) return e;
   k_tables<<<n_frames, 256, 0, s>>>(w.desc, w.tables, w.st, reinterpret_cast<uint32_t*>(w.loss_part),
-                                    static_cast<uint32_t>(loss_part_bytes() / 4));
+                                    static_cast<uint32_t>(loss_part_bytes() / 4), w.tcur, n_tiles);
   const int64_t ni = n_items > 0 ? n_items : 1;
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
   k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tset, w.tcur, w.st);
