@@ -338,6 +338,8 @@ __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, 
 // ---------------------------------------------------------------------------
 constexpr int kScanCta = 1024;
 
+constexpr uint32_t kLenCache = 4096;   // tiles whose list length the scan keeps in shared memory
+
 // Bucket of a tile list length for the longest-first order: floor(log2(n)) + 1
 // (0 for an empty tile), reversed so that bucket 0 holds the longest lists.
 // Buckets of up to kMergeMax keys take the merge sort (one CTA per tile, all
@@ -358,6 +360,7 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
   __shared__ unsigned long long s_carry, s_tot;
   __shared__ uint32_t s_ccarry, s_ctot;
   __shared__ uint32_t s_bucket[kOrderBuckets];
+  __shared__ uint32_t s_len[kLenCache];   // list lengths of the first tiles, kept for the order passes
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) {
     s_carry = 0;
@@ -414,6 +417,7 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
     if (t < n_tiles) {
       // offsets past the capacity are never used: the emission is skipped
       const uint32_t s32 = static_cast<uint32_t>(start);
+      if (t < kLenCache) s_len[t] = static_cast<uint32_t>(x);
       tcur[t] = s32;
       ranges[t] = x ? make_uint2(s32, static_cast<uint32_t>(start + x)) : make_uint2(0u, 0u);   // empty: (0, 0)
       // first chunk of the tile (non-decreasing over tiles: the chunk of a
@@ -445,38 +449,49 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
   __syncthreads();
   // one shared atomic per distinct class in a warp (most tiles of a frame
   // fall in a few classes, so per-tile atomics would serialise)
+  // list length of tile t as the ranges now hold it
+  const auto tile_len = [&](uint32_t t) -> uint32_t {
+    if (over) return 0u;
+    if (t < kLenCache) return s_len[t];
+    const uint2 rg = ranges[t];
+    return rg.y - rg.x;
+  };
   for (uint32_t b0 = 0; b0 < n_tiles; b0 += kScanCta) {
     const uint32_t t = b0 + tid;
-    const int b = t < n_tiles ? order_bucket(ranges[t].y - ranges[t].x) : -1;
+    const int b = t < n_tiles ? order_bucket(tile_len(t)) : -1;
     const uint32_t peers = __match_any_sync(0xffffffffu, b);
     if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_bucket[b], static_cast<uint32_t>(__popc(peers)));
   }
   __syncthreads();
-  if (tid == 0) {
-    uint32_t acc = 0;
-    for (int b = 0; b < kOrderBuckets; ++b) {
-      const uint32_t c = s_bucket[b];
-      s_bucket[b] = acc;
-      acc += c;
+  // exclusive prefix of the 33 class counts by one warp (class 32 after the
+  // other 32)
+  static_assert(kOrderBuckets == 33, "one class per lane plus the last");
+  if (wid == 0) {
+    const uint32_t c = s_bucket[lane];
+    uint32_t y = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
     }
+    s_bucket[lane] = y - c;
+    if (lane == 31) s_bucket[32] = y;
   }
   __syncthreads();
   for (uint32_t b0 = 0; b0 < n_tiles; b0 += kScanCta) {
     const uint32_t t = b0 + tid;
-    uint2 rg = make_uint2(0u, 0u);
-    if (t < n_tiles) rg = ranges[t];
-    const int b = t < n_tiles ? order_bucket(rg.y - rg.x) : -1;
+    const uint32_t len = t < n_tiles ? tile_len(t) : 0u;
+    const int b = t < n_tiles ? order_bucket(len) : -1;
     const uint32_t peers = __match_any_sync(0xffffffffu, b);
     const int leader = __ffs(peers) - 1;
     uint32_t pos = 0;
     if (b >= 0 && lane == leader) pos = atomicAdd(&s_bucket[b], static_cast<uint32_t>(__popc(peers)));
     pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & ((1u << lane) - 1u));
     if (b >= 0) order[pos] = t;
-    if (t < n_tiles && rg.y - rg.x > kLongList) longt[atomicAdd(&st->n_long, 1u)] = t;
+    if (len > kLongList) longt[atomicAdd(&st->n_long, 1u)] = t;
     // buckets beyond the merge sort, for the bitonic sort; those beyond the
     // 128-thread merge sort, for its 256-thread form
-    if (t < n_tiles && rg.y - rg.x > kMergeMax) sortl[atomicAdd(&st->n_big, 1u)] = t;
-    if (t < n_tiles && rg.y - rg.x > kMergeSmall && rg.y - rg.x <= kMergeMax) midl[atomicAdd(&st->n_mid, 1u)] = t;
+    if (len > kMergeMax) sortl[atomicAdd(&st->n_big, 1u)] = t;
+    if (len > kMergeSmall && len <= kMergeMax) midl[atomicAdd(&st->n_mid, 1u)] = t;
   }
 }
 
