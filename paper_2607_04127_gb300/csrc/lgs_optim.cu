@@ -201,9 +201,23 @@ __global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, 
     md += __shfl_xor_sync(0xffffffffu, md, o);
     mn += __shfl_xor_sync(0xffffffffu, mn, o);
   }
+  // one atomic per CTA and count (every CTA of a frame adds to the same two
+  // words, so per-warp atomics would queue at one L2 address)
+  __shared__ int s_md[8], s_mn[8];
+  const int wid = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    if (md) atomicAdd(ctot + 2 * blockIdx.y, md);
-    if (mn) atomicAdd(ctot + 2 * blockIdx.y + 1, mn);
+    s_md[wid] = md;
+    s_mn[wid] = mn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0, b = 0;
+    for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) {
+      a += s_md[k];
+      b += s_mn[k];
+    }
+    if (a) atomicAdd(ctot + 2 * blockIdx.y, a);
+    if (b) atomicAdd(ctot + 2 * blockIdx.y + 1, b);
   }
 }
 
