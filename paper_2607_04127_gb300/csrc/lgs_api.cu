@@ -221,7 +221,6 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
   L.cbase = take(4 * T);
   L.ckpt = take(sizeof(float) * 6 * static_cast<size_t>(tile_pixels) * static_cast<size_t>(C));
   L.cmask = take(sizeof(uint32_t) * 4 * static_cast<size_t>(tile_pixels) * static_cast<size_t>(C));
-  L.sortl = take(4 * T);
   L.midl = take(4 * T);
   L.chunks_cap = C;
   L.total = off;

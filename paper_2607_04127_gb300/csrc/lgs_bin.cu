@@ -16,11 +16,12 @@
 //                 of each tile of its stored set (order inside a bucket
 //                 arbitrary)
 //   k_tile_sort_all
-//                 sort every bucket by the 64-bit key in one launch: up to
-//                 1024 keys by a merge sort on half a CTA, up to 2048 on a
-//                 whole CTA, longer buckets by a bitonic network (up to 4096
-//                 in shared memory, beyond that chunks merged through global
-//                 memory); then write the item list
+//                 sort every bucket of up to 2048 keys by the 64-bit key in
+//                 one launch: up to 1024 keys by a merge sort on half a CTA,
+//                 up to 2048 on a whole CTA; then write the item list
+//   k_sort_long   longer buckets, one 1024-thread CTA each, longest first:
+//                 8192-key chunks sorted in shared memory, merged pairwise
+//                 through global memory; then the item list
 // The result is the order of the key (tile, depth, item): per tile, by depth,
 // ties by item index.
 #include <cuda_runtime.h>
@@ -72,6 +73,7 @@ __global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, St
     st->n_long = 0;
     st->n_big = 0;
     st->n_mid = 0;
+    st->long_sort_counter = 0;
     st->long_counter_fwd = 0;
     st->long_counter_bwd = 0;
     st->long_done_fwd = 0;
@@ -344,7 +346,7 @@ constexpr uint32_t kLenCache = 4096;   // tiles whose list length the scan keeps
 // (0 for an empty tile), reversed so that bucket 0 holds the longest lists.
 // Buckets of up to kMergeMax keys take the merge sort (one CTA per tile, all
 // in one launch: a bucket's sort is a long serial chain, so every bucket
-// runs concurrently); longer ones the bitonic network, over their own list.
+// runs concurrently); longer ones k_sort_long, in this longest-first order.
 constexpr int kMergeMax = 2048;
 constexpr int kMergeSmall = 1024;   // buckets up to this size: the 128-thread merge sort
 constexpr int kOrderBuckets = 33;
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
                                                           uint2* __restrict__ ranges, Status* __restrict__ st,
                                                           int64_t cap, uint32_t* __restrict__ order,
                                                           uint32_t* __restrict__ longt, uint32_t* __restrict__ cbase,
-                                                          uint32_t* __restrict__ sortl, uint32_t* __restrict__ midl) {
+                                                          uint32_t* __restrict__ midl) {
   __shared__ unsigned long long s_w[32];
   __shared__ uint32_t s_wc[32];
   __shared__ unsigned long long s_carry, s_tot;
@@ -488,9 +490,9 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
     pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & ((1u << lane) - 1u));
     if (b >= 0) order[pos] = t;
     if (len > kLongList) longt[atomicAdd(&st->n_long, 1u)] = t;
-    // buckets beyond the merge sort, for the bitonic sort; those beyond the
-    // 128-thread merge sort, for its 256-thread form
-    if (len > kMergeMax) sortl[atomicAdd(&st->n_big, 1u)] = t;
+    // buckets beyond the merge sort (k_sort_long's, found through the
+    // order); those beyond the 128-thread merge sort, for its 256-thread form
+    if (len > kMergeMax) atomicAdd(&st->n_big, 1u);
     if (len > kMergeSmall && len <= kMergeMax) midl[atomicAdd(&st->n_mid, 1u)] = t;
   }
 }
@@ -577,82 +579,6 @@ __global__ void __launch_bounds__(256) k_emit(const Desc* __restrict__ D, const 
 // ---------------------------------------------------------------------------
 // Per-tile sort
 // ---------------------------------------------------------------------------
-// Bitonic network in its ascending-only form: the first step of every merge
-// compares i with its mirror i ^ (k - 1), the later steps are half-cleaners
-// (i, i + j).  Every comparator puts the minimum at the lower index, so
-// positions past the end of a bucket act as +infinity and are never touched.
-constexpr int kSortSmem = 4096;   // keys sorted in shared memory at once
-
-__device__ __forceinline__ void cas(unsigned long long* a, uint32_t i, uint32_t j) {
-  const unsigned long long x = a[i], y = a[j];
-  if (x > y) {
-    a[i] = y;
-    a[j] = x;
-  }
-}
-
-// Comparator p of a step with stride j = 2^lj (half-cleaner) or of the
-// mirror step of a merge of blocks k = 2^(lj+1): its lower index.  For
-// strides below 64 the 32 comparators of a warp stay inside one 64-key
-// block, so those steps need only a warp barrier.
-__device__ __forceinline__ uint32_t lower_index(uint32_t p, uint32_t lj) {
-  return ((p >> lj) << (lj + 1)) | (p & ((1u << lj) - 1u));
-}
-
-// Barrier around a step of the given stride: a step that crosses warps
-// (stride >= 64) is fenced by block barriers on both sides; between two
-// warp-local steps a warp barrier suffices.
-__device__ __forceinline__ void step_sync(uint32_t stride) {
-  if (stride >= 64) __syncthreads();
-  else __syncwarp();
-}
-
-// Full sort of s[0, N) in shared memory (N a power of two <= kSortSmem).
-__device__ void smem_sort(unsigned long long* s, uint32_t N) {
-  for (uint32_t lk = 1; (1u << lk) <= N; ++lk) {
-    const uint32_t k = 1u << lk;
-    if ((k >> 1) >= 64) __syncthreads();
-    for (uint32_t p = threadIdx.x; p < N / 2; p += blockDim.x) {
-      const uint32_t i = lower_index(p, lk - 1);
-      cas(s, i, i ^ (k - 1));
-    }
-    step_sync(k >> 1);
-    for (int lj = static_cast<int>(lk) - 2; lj >= 0; --lj) {
-      if ((1u << lj) >= 64) __syncthreads();
-      for (uint32_t p = threadIdx.x; p < N / 2; p += blockDim.x) {
-        const uint32_t i = lower_index(p, lj);
-        cas(s, i, i + (1u << lj));
-      }
-      step_sync(1u << lj);
-    }
-  }
-  __syncthreads();
-}
-
-// Half-cleaners j = S/2 .. 1 on s[0, S) (the tail of a merge step).
-__device__ void smem_clean(unsigned long long* s, uint32_t S) {
-  for (int lj = 31 - __clz(S) - 1; lj >= 0; --lj) {
-    if ((1u << lj) >= 64) __syncthreads();
-    for (uint32_t p = threadIdx.x; p < S / 2; p += blockDim.x) {
-      const uint32_t i = lower_index(p, lj);
-      cas(s, i, i + (1u << lj));
-    }
-    step_sync(1u << lj);
-  }
-  __syncthreads();
-}
-
-__device__ void chunk_load(unsigned long long* s, const unsigned long long* g, uint32_t base, uint32_t n, uint32_t S) {
-  for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) s[i] = base + i < n ? g[base + i] : ~0ull;
-  __syncthreads();
-}
-
-__device__ void chunk_store(const unsigned long long* s, unsigned long long* g, uint32_t base, uint32_t n, uint32_t S) {
-  for (uint32_t i = threadIdx.x; i < S; i += blockDim.x)
-    if (base + i < n) g[base + i] = s[i];
-  __syncthreads();
-}
-
 // ---- buckets of at most 2048 keys: merge sort in shared memory -----------
 // Every thread sorts 8 keys in registers (a 19-comparator network), then
 // runs of 8, 16, ... keys are merged pairwise until one run remains: each
@@ -691,17 +617,14 @@ __device__ __forceinline__ void part_sync(uint32_t nthr) {
   else asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(nthr) : "memory");
 }
 
-// One bucket of at most 8 * nthr keys sorted by threads t = 0 .. nthr - 1 of
-// one part of a CTA (barrier BAR), in sa / sb (pad8 of 8 * nthr keys each).
+// The n <= 8 * nthr keys g[0, n) sorted by threads t = 0 .. nthr - 1 of one
+// part of a CTA (barrier BAR) in sa / sb (pad8 of 8 * nthr keys each);
+// returns the buffer that holds them (key i at pad8(i)), after a barrier.
 template <int BAR>
-__device__ __forceinline__ void merge_sort_bucket(uint32_t tile, const uint2* __restrict__ ranges,
-                                                  const unsigned long long* __restrict__ pkey,
-                                                  uint32_t* __restrict__ pv, unsigned long long* sa,
-                                                  unsigned long long* sb, uint32_t t, uint32_t nthr) {
-  const uint2 rg = ranges[tile];
-  const uint32_t n = rg.y - rg.x;
+__device__ __forceinline__ unsigned long long* smem_merge_sort(const unsigned long long* __restrict__ g, uint32_t n,
+                                                               unsigned long long* sa, unsigned long long* sb,
+                                                               uint32_t t, uint32_t nthr) {
   const uint32_t N = n > 8 ? (n + 7u) & ~7u : 8u;   // padded to whole 8-key rows only
-  const unsigned long long* g = pkey + rg.x;
   for (uint32_t i = t; i < N; i += nthr) sa[pad8(i)] = i < n ? g[i] : ~0ull;
   part_sync<BAR>(nthr);
   const bool act = 8 * t < N;
@@ -751,74 +674,180 @@ __device__ __forceinline__ void merge_sort_bucket(uint32_t tile, const uint2* __
     src = dst;
     dst = tmp;
   }
-  part_sync<BAR>(nthr);   // the list is written from every warp's keys
+  part_sync<BAR>(nthr);   // the result is read from every warp's keys
+  return src;
+}
+
+// One bucket of at most 8 * nthr keys: sorted in shared memory, its item list
+// written.
+template <int BAR>
+__device__ __forceinline__ void merge_sort_bucket(uint32_t tile, const uint2* __restrict__ ranges,
+                                                  const unsigned long long* __restrict__ pkey,
+                                                  uint32_t* __restrict__ pv, unsigned long long* sa,
+                                                  unsigned long long* sb, uint32_t t, uint32_t nthr) {
+  const uint2 rg = ranges[tile];
+  const uint32_t n = rg.y - rg.x;
+  const unsigned long long* src = smem_merge_sort<BAR>(pkey + rg.x, n, sa, sb, t, nthr);
   for (uint32_t i = t; i < n; i += nthr) pv[rg.x + i] = static_cast<uint32_t>(src[pad8(i)]);
 }
 
-// ---- buckets beyond 2048 keys: a bitonic network over the whole CTA --------
-__device__ void bitonic_bucket(uint32_t tile, const uint2* __restrict__ ranges, unsigned long long* __restrict__ pkey,
-                               uint32_t* __restrict__ pv, unsigned long long* s) {
-  const uint2 rg = ranges[tile];
-  const uint32_t n = rg.y - rg.x;
-  unsigned long long* g = pkey + rg.x;
-  if (n <= kSortSmem) {
-    uint32_t N = 2;
-    while (N < n) N <<= 1;
-    chunk_load(s, g, 0, n, N);
-    smem_sort(s, N);
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) pv[rg.x + i] = static_cast<uint32_t>(s[i]);
-    return;
+// ---- buckets beyond 2048 keys: one CTA each, merged through global memory --
+// A long bucket is sorted by one CTA of kLongSortCta threads: chunks of
+// kLongChunk keys in shared memory (smem_merge_sort), then passes that merge
+// pairs of sorted runs into runs twice as long, ping-ponging between the key
+// array and a second buffer made of the pair-tile and item arrays (high and
+// low 32 bits of each key; the pair tiles are rewritten on request only, and
+// the item list is the keys' low half, so a result left there is already the
+// list).  A pass writes its output in tiles of kLongChunk keys: the tile's
+// first and last merge-path diagonals are found by binary searches in global
+// memory (one per thread, for up to kLongSortCta tiles at once), its two input
+// ranges loaded into shared memory, and every thread merges its 8 outputs.
+// O(n log n) per bucket instead of the bitonic network's O(n log^2 n).
+constexpr int kLongSortCta = 1024;
+constexpr uint32_t kLongChunk = 8 * kLongSortCta;   // 8192 keys
+constexpr size_t kLongSortSmem = 2 * sizeof(unsigned long long) * (kLongChunk + kLongChunk / 8) +
+                                 sizeof(uint32_t) * (kLongSortCta + 1);   // two key buffers, the diagonals
+
+// A bucket's keys: 64-bit words, or split into high and low 32-bit halves.
+struct KeyBuf {
+  unsigned long long* k;
+  uint32_t *hi, *lo;
+  __device__ __forceinline__ unsigned long long get(uint32_t i) const {
+    return k ? k[i] : (static_cast<unsigned long long>(hi[i]) << 32) | lo[i];
   }
-  // long bucket: sorted chunks of kSortSmem, then the merge steps whose
-  // stride spans chunks run in global memory (this CTA only; __syncthreads
-  // orders its global accesses), the rest per chunk in shared memory
-  const uint32_t S = kSortSmem;
-  uint32_t N = S;
-  while (N < n) N <<= 1;
-  for (uint32_t b = 0; b < n; b += S) {
-    chunk_load(s, g, b, n, S);
-    smem_sort(s, S);
-    chunk_store(s, g, b, n, S);
-  }
-  for (uint32_t lk = 31 - __clz(2 * S); (1u << lk) <= N; ++lk) {
-    const uint32_t k = 1u << lk;
-    for (uint32_t p = threadIdx.x; p < N / 2; p += blockDim.x) {
-      const uint32_t i = lower_index(p, lk - 1), j = i ^ (k - 1);
-      if (j < n) cas(g, i, j);
-    }
-    __syncthreads();
-    for (uint32_t lj = lk - 2; (1u << lj) >= S; --lj) {
-      for (uint32_t p = threadIdx.x; p < N / 2; p += blockDim.x) {
-        const uint32_t i = lower_index(p, lj);
-        if (i + (1u << lj) < n) cas(g, i, i + (1u << lj));
-      }
-      __syncthreads();
-    }
-    for (uint32_t b = 0; b < n; b += S) {
-      chunk_load(s, g, b, n, S);
-      smem_clean(s, S);
-      chunk_store(s, g, b, n, S);
+  __device__ __forceinline__ void put(uint32_t i, unsigned long long v) const {
+    if (k) {
+      k[i] = v;
+    } else {
+      hi[i] = static_cast<uint32_t>(v >> 32);
+      lo[i] = static_cast<uint32_t>(v);
     }
   }
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) pv[rg.x + i] = static_cast<uint32_t>(g[i]);
+};
+
+// Merge-path split: how many of the first d outputs of merging A[0, la) and
+// B[0, lb) come from A (keys are distinct).
+__device__ __forceinline__ uint32_t path_split(const KeyBuf& X, uint32_t a0, uint32_t la, uint32_t b0, uint32_t lb,
+                                               uint32_t d) {
+  uint32_t lo = d > lb ? d - lb : 0u, hi = d < la ? d : la;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (X.get(a0 + mid) > X.get(b0 + d - mid - 1)) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
 }
 
-// ---- every bucket in one launch ------------------------------------------------
-// The first n_lead CTAs take the long buckets, which take longest, from the
-// tile scan's lists (beyond 2048 keys the bitonic network, then those of
-// 1025..2048 keys the merge sort over the whole CTA), looping until the lists
-// are done; every other CTA sorts two buckets of at most 1024 keys, one per
-// half (128 threads, its own named barrier).  Shared memory: two halves of
-// two 1152-key buffers, or one pair of 2304-key buffers, or 4096 keys of the
-// bitonic network.
+__global__ void __launch_bounds__(kLongSortCta) k_sort_long(const uint2* __restrict__ ranges,
+                                                             Status* __restrict__ st,
+                                                             const uint32_t* __restrict__ order,
+                                                             uint32_t n_tiles, unsigned long long* __restrict__ pkey,
+                                                             uint32_t* __restrict__ ptile, uint32_t* __restrict__ pv) {
+  extern __shared__ __align__(16) unsigned long long s_long[];
+  unsigned long long* sa = s_long;
+  unsigned long long* sb = s_long + kLongChunk + kLongChunk / 8;
+  uint32_t* s_split = reinterpret_cast<uint32_t*>(sb + kLongChunk + kLongChunk / 8);
+  __shared__ uint32_t s_claim;
+  if (st->overflow || st->n_big == 0) return;
+  const uint32_t t = threadIdx.x;
+  while (true) {
+    // buckets in the tile scan's longest-first order; the long ones come
+    // first, so the first list of at most kMergeMax keys ends the work
+    __syncthreads();
+    if (t == 0) s_claim = atomicAdd(&st->long_sort_counter, 1u);
+    __syncthreads();
+    const uint32_t k = s_claim;
+    if (k >= n_tiles) return;
+    const uint32_t tile = order[k];
+    const uint2 rg = ranges[tile];
+    const uint32_t n = rg.y - rg.x;
+    if (order_bucket(n) > order_bucket(kMergeMax + 1)) return;   // a shorter class: no long list follows
+    if (n <= kMergeMax) continue;
+    KeyBuf X{pkey + rg.x, nullptr, nullptr}, Y{nullptr, ptile + rg.x, pv + rg.x};
+    // sorted chunks, in place
+    for (uint32_t c0 = 0; c0 < n; c0 += kLongChunk) {
+      const uint32_t m = min(kLongChunk, n - c0);
+      const unsigned long long* res = smem_merge_sort<0>(X.k + c0, m, sa, sb, t, kLongSortCta);
+      for (uint32_t i = t; i < m; i += kLongSortCta) X.k[c0 + i] = res[pad8(i)];
+      __syncthreads();
+    }
+    // merge passes: runs of R keys into runs of 2 R
+    bool in_x = true;
+    for (uint32_t R = kLongChunk; R < n; R <<= 1) {
+      const KeyBuf& S = in_x ? X : Y;
+      const KeyBuf& Dst = in_x ? Y : X;
+      const uint32_t n_out = (n + kLongChunk - 1) / kLongChunk;   // output tiles (a run pair holds whole tiles)
+      for (uint32_t q0 = 0; q0 < n_out; q0 += kLongSortCta) {
+        // first diagonal of output tiles q0 + t (and the end of the last one)
+        __syncthreads();
+        for (uint32_t q = q0 + t; q <= min(q0 + kLongSortCta, n_out); q += kLongSortCta) {
+          const uint32_t o = min(q * kLongChunk, n);
+          uint32_t p = o / (2 * R);
+          if (o == n && o % (2 * R) == 0 && o > 0) --p;   // the end diagonal of the last pair
+          const uint32_t a0 = 2 * R * p, la = min(R, n - a0), b0 = a0 + R;
+          const uint32_t lb = b0 < n ? min(R, n - b0) : 0u;
+          s_split[q - q0] = path_split(S, a0, la, b0, lb, o - a0);
+        }
+        __syncthreads();
+        const uint32_t q1 = min(q0 + kLongSortCta, n_out);
+        for (uint32_t q = q0; q < q1; ++q) {
+          const uint32_t o = q * kLongChunk, oe = min(o + kLongChunk, n);
+          const uint32_t p = o / (2 * R);
+          const uint32_t a0 = 2 * R * p, la = min(R, n - a0), b0 = a0 + R;
+          const uint32_t d0 = o - a0, d1 = oe - a0;
+          const uint32_t i0 = s_split[q - q0];
+          // the tile's end diagonal: the next tile's first one, or the whole
+          // pair when the tile closes it
+          const uint32_t i1 = d1 == la + (b0 < n ? min(R, n - b0) : 0u) ? la : s_split[q + 1 - q0];
+          const uint32_t j0 = d0 - i0, j1 = d1 - i1;
+          const uint32_t na = i1 - i0, nb = j1 - j0;
+          // A's part then B's part, in shared memory
+          for (uint32_t i = t; i < na; i += kLongSortCta) sa[i] = S.get(a0 + i0 + i);
+          for (uint32_t i = t; i < nb; i += kLongSortCta) sa[na + i] = S.get(b0 + j0 + i);
+          __syncthreads();
+          const uint32_t d = 8 * t;
+          if (d < na + nb) {
+            uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
+            while (lo < hi) {
+              const uint32_t mid = (lo + hi) >> 1;
+              if (sa[mid] > sa[na + d - mid - 1]) hi = mid;
+              else lo = mid + 1;
+            }
+            uint32_t i = lo, j = d - lo;
+            const uint32_t cnt = min(8u, na + nb - d);
+            for (uint32_t r = 0; r < cnt; ++r) {
+              const unsigned long long a = i < na ? sa[i] : ~0ull, b = j < nb ? sa[na + j] : ~0ull;
+              const bool takeA = j >= nb || (i < na && a < b);
+              Dst.put(o + d + r, takeA ? a : b);
+              i += takeA;
+              j += !takeA;
+            }
+          }
+          __syncthreads();
+        }
+      }
+      in_x = !in_x;
+    }
+    // the item list: the keys' low halves (already in place when the result
+    // is in the split buffer)
+    if (in_x)
+      for (uint32_t i = t; i < n; i += kLongSortCta) pv[rg.x + i] = static_cast<uint32_t>(X.k[i]);
+  }
+}
+
+// ---- every bucket of at most 2048 keys in one launch ------------------------
+// The first n_lead CTAs take the buckets of 1025..2048 keys from the tile
+// scan's list (the merge sort over the whole CTA), looping until it is done;
+// every other CTA sorts two buckets of at most 1024 keys, one per half (128
+// threads, its own named barrier).  Shared memory: two halves of two
+// 1152-key buffers, or one pair of 2304-key buffers.  Longer buckets are
+// k_sort_long's.
 constexpr int kSortAllCta = 256;
 constexpr int kSortAllSmem = 2 * (kMergeMax + kMergeMax / 8);   // 4608 keys, 36 KB
-static_assert(kSortAllSmem >= kSortSmem, "the bitonic network fits the merge buffers");
 static_assert(kSortAllCta == kMergeMax / 8 && kSortAllCta == 2 * (kMergeSmall / 8), "thread counts");
 
 __global__ void __launch_bounds__(kSortAllCta) k_tile_sort_all(const uint2* __restrict__ ranges,
                                                                 const Status* __restrict__ st,
-                                                                const uint32_t* __restrict__ sortl,
                                                                 const uint32_t* __restrict__ midl,
                                                                 uint32_t n_tiles, uint32_t n_lead,
                                                                 unsigned long long* __restrict__ pkey,
@@ -826,10 +855,6 @@ __global__ void __launch_bounds__(kSortAllCta) k_tile_sort_all(const uint2* __re
   __shared__ unsigned long long s[kSortAllSmem];
   if (st->overflow) return;
   if (blockIdx.x < n_lead) {
-    for (uint32_t k = blockIdx.x; k < st->n_big; k += n_lead) {
-      __syncthreads();   // the previous bucket's readers are done with s
-      bitonic_bucket(sortl[k], ranges, pkey, pv, s);
-    }
     for (uint32_t k = blockIdx.x; k < st->n_mid; k += n_lead) {
       __syncthreads();
       merge_sort_bucket<0>(midl[k], ranges, pkey, pv, s, s + kMergeMax + kMergeMax / 8, threadIdx.x, kSortAllCta);
@@ -876,7 +901,7 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
   k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tset, w.tcur, w.st);
   k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work, w.longt, w.cbase,
-                                     w.sortl, w.midl);
+                                     w.midl);
   k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.tset, w.tcur, w.ranges, w.st, w.pkey);
   if (n_tiles > 0) {
     int dev = 0, sms = 152;
@@ -884,7 +909,17 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned few = static_cast<unsigned>(sms) < n_tiles ? static_cast<unsigned>(sms) : n_tiles;
     const unsigned grid = few + (n_tiles + 1) / 2;
-    k_tile_sort_all<<<grid, kSortAllCta, 0, s>>>(w.ranges, w.st, w.sortl, w.midl, n_tiles, few, w.pkey, w.pv);
+    k_tile_sort_all<<<grid, kSortAllCta, 0, s>>>(w.ranges, w.st, w.midl, n_tiles, few, w.pkey, w.pv);
+    // the long buckets: one CTA each, longest first (no work, and an early
+    // exit, when the tile scan found none)
+    static bool smem_set[64] = {false};
+    if (dev < 64 && !smem_set[dev]) {
+      const cudaError_t e = cudaFuncSetAttribute(k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(kLongSortSmem));
+      if (e != cudaSuccess) return e;
+      smem_set[dev] = true;
+    }
+    k_sort_long<<<sms, kLongSortCta, kLongSortSmem, s>>>(w.ranges, w.st, w.work, n_tiles, w.pkey, w.ptile, w.pv);
   }
   return cudaGetLastError();
 }

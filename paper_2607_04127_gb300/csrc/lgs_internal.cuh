@@ -75,11 +75,12 @@ struct Status {
   unsigned int count_ticket;          // mask-count CTAs finished (the last one adds up; self-resetting)
   unsigned int n_big;                 // buckets of more than 2048 keys (the bitonic sort)
   unsigned int n_mid;                 // buckets of 1025..2048 keys (the wide merge sort)
+  unsigned int long_sort_counter;     // tile order positions claimed by the long-bucket sort
 };
 
 struct Layout {
   size_t desc, status, tables, rec, box, key, cnt, tset, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part,
-      cbase, ckpt, cmask, sortl, midl, total;
+      cbase, ckpt, cmask, midl, total;
   int64_t items_cap, pairs_cap, chunks_cap;
   uint32_t tiles_cap;
   uint32_t tables_cap;     // floats
@@ -107,7 +108,6 @@ struct WsPtrs {
   uint32_t* cbase;         // [tiles] first backward chunk of every tile
   float* ckpt;             // [chunks][6][tile pixels] forward checkpoint at every chunk end
   uint32_t* cmask;         // [chunks][4 windows][tile pixels] entries each pixel composited, one bit per entry
-  uint32_t* sortl;         // [tiles] tiles whose bucket exceeds the merge sort (st->n_big of them)
   uint32_t* midl;          // [tiles] tiles whose bucket takes the wide merge sort (st->n_mid of them)
 };
 
@@ -134,7 +134,6 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.cbase = reinterpret_cast<uint32_t*>(b + L.cbase);
   p.ckpt = reinterpret_cast<float*>(b + L.ckpt);
   p.cmask = reinterpret_cast<uint32_t*>(b + L.cmask);
-  p.sortl = reinterpret_cast<uint32_t*>(b + L.sortl);
   p.midl = reinterpret_cast<uint32_t*>(b + L.midl);
   return p;
 }

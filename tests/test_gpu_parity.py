@@ -419,11 +419,14 @@ def test_gradients_accumulate(oracle):
         assert np.allclose(a, 2 * b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
 
 
-@pytest.mark.parametrize("n,lo,hi", [(5000, 2048, 4096), (12000, 4096, 1 << 30)])
+@pytest.mark.parametrize("n,lo,hi", [(5000, 2048, 4096), (12000, 4096, 1 << 30), (40000, 16384, 1 << 30)])
 def test_long_tile_bucket_bit_exact(oracle, n, lo, hi):
-    """Buckets beyond the merge sort's 2048 keys take the shared-memory
-    bitonic network (up to 4096) or its chunked path through global memory
-    (beyond), and lists beyond 4096 entries the entry-parallel compositing
+    """Buckets beyond the merge sort's 2048 keys take the long-bucket sort
+    (8192-key chunks in shared memory, then merge passes through global
+    memory: none for a bucket of at most 8192 keys, one pass up to 16384,
+    two for the 40000-surfel cloud's bucket of about 18,500 keys, whose
+    third chunk first has no run to merge with), and lists beyond 4096
+    entries the entry-parallel compositing
     kernels: bins stay bit-exact, forward and gradients match the oracle."""
     from tests import _gpu
     rng = np.random.default_rng(11)
