@@ -48,6 +48,9 @@ struct lgs_session_s {
   bool timing = false;
   std::vector<Timed> timed;
   std::vector<cudaEvent_t> ev_pool;
+  // side stream of the binning: the long-bucket sort runs on it alongside the
+  // short buckets' sort, forked from and joined to the caller's stream
+  lgs::SideStream side{nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -433,6 +436,12 @@ lgs_status lgs_session_create(int device, size_t hbm_budget_bytes, lgs_session* 
     return cuda_fail(e, "session create");
   }
   memset(s->h_status, 0, sizeof(Status));
+  if ((e = cudaStreamCreateWithFlags(&s->side.s, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->side.join, cudaEventDisableTiming)) != cudaSuccess) {
+    lgs_session_destroy(s);
+    return cuda_fail(e, "session create");
+  }
   *out = s;
   return LGS_OK;
 }
@@ -444,6 +453,12 @@ lgs_status lgs_session_destroy(lgs_session s) {
     cudaFreeHost(s->h_status);
   }
   drop_timing(s);
+  if (s->side.s || s->side.fork || s->side.join) {
+    cudaSetDevice(s->device);
+    if (s->side.fork) cudaEventDestroy(s->side.fork);
+    if (s->side.join) cudaEventDestroy(s->side.join);
+    if (s->side.s) cudaStreamDestroy(s->side.s);
+  }
   if (!s->ev_pool.empty()) {
     cudaSetDevice(s->device);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
@@ -696,7 +711,7 @@ lgs_status lgs_bin_sort_batch(lgs_session s, const lgs_surfels* maps, int n_maps
     s->g13_zero_off = L.g13;
   }
   if ((e = write_desc(s, *s->desc, w.desc, cs, s->launches)) != cudaSuccess) return cuda_fail(e, "write_desc");
-  if ((e = timed(s, LGS_TIME_BIN, cs, [&] { return lgs::launch_bin(L, w, n_frames, p.n_items, p.n_tiles, cs); })) !=
+  if ((e = timed(s, LGS_TIME_BIN, cs, [&] { return lgs::launch_bin(L, w, n_frames, p.n_items, p.n_tiles, s->side, cs); })) !=
       cudaSuccess)
     return cuda_fail(e, "bin");
   s->launches += lgs::bin_kernel_count(p.n_tiles);

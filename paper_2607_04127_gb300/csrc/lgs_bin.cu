@@ -894,7 +894,7 @@ cudaError_t launch_fill_tile_of_pair(const WsPtrs& w, uint32_t n_tiles, cudaStre
 int bin_kernel_count(uint32_t) { return 5; }
 
 cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n_items, uint32_t n_tiles,
-                       cudaStream_t s) {
+                       const SideStream& side, cudaStream_t s) {
   k_tables<<<n_frames, 256, 0, s>>>(w.desc, w.tables, w.st, reinterpret_cast<uint32_t*>(w.loss_part),
                                     static_cast<uint32_t>(loss_part_bytes() / 4), w.tcur, n_tiles);
   const int64_t ni = n_items > 0 ? n_items : 1;
@@ -909,9 +909,8 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned few = static_cast<unsigned>(sms) < n_tiles ? static_cast<unsigned>(sms) : n_tiles;
     const unsigned grid = few + (n_tiles + 1) / 2;
-    k_tile_sort_all<<<grid, kSortAllCta, 0, s>>>(w.ranges, w.st, w.midl, n_tiles, few, w.pkey, w.pv);
-    // the long buckets: one CTA each, longest first (no work, and an early
-    // exit, when the tile scan found none)
+    // the long buckets: one CTA each, longest first (an early exit when the
+    // tile scan found none), on the side stream alongside the short buckets
     static bool smem_set[64] = {false};
     if (dev < 64 && !smem_set[dev]) {
       const cudaError_t e = cudaFuncSetAttribute(k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -919,7 +918,15 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
       if (e != cudaSuccess) return e;
       smem_set[dev] = true;
     }
-    k_sort_long<<<sms, kLongSortCta, kLongSortSmem, s>>>(w.ranges, w.st, w.work, n_tiles, w.pkey, w.ptile, w.pv);
+    cudaError_t e = cudaEventRecord(side.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side.s, side.fork, 0);
+    if (e != cudaSuccess) return e;
+    k_sort_long<<<sms, kLongSortCta, kLongSortSmem, side.s>>>(w.ranges, w.st, w.work, n_tiles, w.pkey, w.ptile,
+                                                               w.pv);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(side.join, side.s)) != cudaSuccess) return e;
+    k_tile_sort_all<<<grid, kSortAllCta, 0, s>>>(w.ranges, w.st, w.midl, n_tiles, few, w.pkey, w.pv);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, side.join, 0)) != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

@@ -637,8 +637,13 @@ __device__ __forceinline__ int frame_of_item(const Desc& D, int64_t item) {
 // Host-side launchers (one per translation unit).
 // ---------------------------------------------------------------------------
 cudaError_t launch_write_desc(const Desc& h, Desc* d, Status* st, cudaStream_t s);
+// A second stream with its fork and join events (owned by a session).
+struct SideStream {
+  cudaStream_t s;
+  cudaEvent_t fork, join;
+};
 cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n_items, uint32_t n_tiles,
-                       cudaStream_t s);
+                       const SideStream& side, cudaStream_t s);
 int bin_kernel_count(uint32_t n_tiles);
 // the tile of every pair of the last binning into w.ptile (on request only)
 cudaError_t launch_fill_tile_of_pair(const WsPtrs& w, uint32_t n_tiles, cudaStream_t s);
