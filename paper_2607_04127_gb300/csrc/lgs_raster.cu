@@ -1228,6 +1228,8 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
           ++evals;
         }
       }
+      // a window without a valid pair leaves T and the sums as they are
+      if (!__any_sync(0xffffffffu, valid)) continue;
       // P_j = prod_{i <= j} (1 - a_i) over the valid lanes
       float Pj = valid ? __fsub_rn(1.0f, e.a) : 1.0f;
 #pragma unroll
@@ -1242,11 +1244,13 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
       const bool inc = valid && lane < fs;
       const float w = inc ? e.a * (T * Pex) : 0.f;
       const float ws = valid && e.den > 0.f ? -w : w;
-      A += warp_sum(w);
-      St += warp_sum(inc ? w * e.t : 0.f);
-      Sx += warp_sum(ws * nx);
-      Sy += warp_sum(ws * ny);
-      Sz += warp_sum(ws * nz);
+      // every lane sums its own entries' terms; the pixel's totals are the
+      // warp sums of these after the walk
+      A += w;
+      if (inc) St = fmaf(w, e.t, St);   // (e is unset on lanes without a box hit)
+      Sx = fmaf(ws, nx, Sx);
+      Sy = fmaf(ws, ny, Sy);
+      Sz = fmaf(ws, nz, Sz);
       contrib += inc;
       const uint32_t im = __ballot_sync(0xffffffffu, inc);
       if (im) last = static_cast<int>(base - P.start) + (31 - __clz(im)) + 1;
@@ -1256,6 +1260,11 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
         break;
       }
     }
+    A = warp_sum(A);
+    St = warp_sum(St);
+    Sx = warp_sum(Sx);
+    Sy = warp_sum(Sy);
+    Sz = warp_sum(Sz);
     if (lane == 0) {
       F.A[P.pix] = A;
       F.St[P.pix] = St;
