@@ -222,7 +222,8 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
   L.loss_part = take(lgs::loss_part_bytes());
   const int64_t C = chunk_cap(pairs_cap, tiles);
   L.cbase = take(4 * T);
-  L.ckpt = take(sizeof(float) * 6 * static_cast<size_t>(tile_pixels) * static_cast<size_t>(C));
+  L.ckpt = take(sizeof(float) * lgs::kCkptSlots * static_cast<size_t>(tile_pixels) * static_cast<size_t>(C));
+  L.csuf = take(sizeof(float) * static_cast<size_t>(tile_pixels) * static_cast<size_t>(C));
   L.cmask = take(sizeof(uint32_t) * 4 * static_cast<size_t>(tile_pixels) * static_cast<size_t>(C));
   L.midl = take(4 * T);
   L.chunks_cap = C;

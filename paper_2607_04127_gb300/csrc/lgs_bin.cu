@@ -373,9 +373,8 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
   for (uint32_t b0 = 0; b0 < n_tiles; b0 += kScanCta) {
     const uint32_t t = b0 + tid;
     const unsigned long long x = t < n_tiles ? tcur[t] : 0ull;
-    // backward chunks of the list: ceil(n / kChunk) for n <= kLongList
-    // entries (longer lists have their own kernels)
-    const uint32_t xc = x <= kLongList ? static_cast<uint32_t>((x + kChunk - 1) / kChunk) : 0u;
+    // backward chunks of the list: ceil(n / kChunk)
+    const uint32_t xc = static_cast<uint32_t>((x + kChunk - 1) / kChunk);
     unsigned long long v = x;
     uint32_t vc = xc;
     for (int o = 1; o < 32; o <<= 1) {

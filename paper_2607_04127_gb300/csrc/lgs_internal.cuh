@@ -80,7 +80,7 @@ struct Status {
 
 struct Layout {
   size_t desc, status, tables, rec, box, key, cnt, tset, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part,
-      cbase, ckpt, cmask, midl, total;
+      cbase, ckpt, csuf, cmask, midl, total;
   int64_t items_cap, pairs_cap, chunks_cap;
   uint32_t tiles_cap;
   uint32_t tables_cap;     // floats
@@ -106,7 +106,8 @@ struct WsPtrs {
   uint32_t* longt;         // tiles with lists longer than kLongList (st->n_long of them)
   double* loss_part;       // loss partial sums and mask counts
   uint32_t* cbase;         // [tiles] first backward chunk of every tile
-  float* ckpt;             // [chunks][6][tile pixels] forward checkpoint at every chunk end
+  float* ckpt;             // [chunks][kCkptSlots][tile pixels] forward checkpoint at every chunk end
+  float* csuf;             // [chunks][tile pixels] long lists: the suffix of the later chunks (backward)
   uint32_t* cmask;         // [chunks][4 windows][tile pixels] entries each pixel composited, one bit per entry
   uint32_t* midl;          // [tiles] tiles whose bucket takes the wide merge sort (st->n_mid of them)
 };
@@ -133,6 +134,7 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.loss_part = reinterpret_cast<double*>(b + L.loss_part);
   p.cbase = reinterpret_cast<uint32_t*>(b + L.cbase);
   p.ckpt = reinterpret_cast<float*>(b + L.ckpt);
+  p.csuf = reinterpret_cast<float*>(b + L.csuf);
   p.cmask = reinterpret_cast<uint32_t*>(b + L.cmask);
   p.midl = reinterpret_cast<uint32_t*>(b + L.midl);
   return p;
@@ -437,6 +439,9 @@ constexpr uint32_t kLongList = 4096;
 // transmittance and the chunk's own sums of w, w t and w n' (a checkpoint of
 // six floats), so every chunk's reverse walk can start on its own.
 constexpr uint32_t kChunk = 128;
+// Floats of a checkpoint per (chunk, pixel): T at the chunk end and the
+// chunk's own sums of w, w t and w n.
+constexpr int kCkptSlots = 6;
 
 struct Eval {
   float den, rden, t, ud, vd, u, v, q, G, araw, a;

@@ -748,7 +748,7 @@ __global__ void __maxnreg__(72)
     uint32_t chunk = 0;
     const int npx = static_cast<int>(blockDim.x);
     const auto checkpoint = [&]() {
-      float* o = ckpt + (static_cast<int64_t>(cbase[tile] + chunk) * 6) * npx + threadIdx.x;
+      float* o = ckpt + (static_cast<int64_t>(cbase[tile] + chunk) * kCkptSlots) * npx + threadIdx.x;
       o[0] = T;
       o[npx] = cA;
       o[2 * npx] = cSt;
@@ -992,6 +992,7 @@ __global__ void __launch_bounds__(kBwdChunkCta)
     k_bwd_c(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
             const float4* __restrict__ rec, const float4* __restrict__ box, float* __restrict__ g13,
             const uint32_t* __restrict__ cbase, const float* __restrict__ ckpt, const uint32_t* __restrict__ cmask,
+            const float* __restrict__ csuf,
             Status* __restrict__ st) {
   __shared__ WarpRecs s_w[kBwdChunkCta / 32];
   __shared__ uint32_t s_item[kBwdChunkCta / 32][32];
@@ -1038,12 +1039,16 @@ __global__ void __launch_bounds__(kBwdChunkCta)
       gSx = F.gSn[pix];
       gSy = F.gSn[HW + pix];
       gSz = F.gSn[2 * static_cast<int64_t>(HW) + pix];
-      const float* o = ckpt + (static_cast<int64_t>(cbase[tile] + c) * 6) * npx + vt;
+      const float* o = ckpt + (static_cast<int64_t>(cbase[tile] + c) * kCkptSlots) * npx + vt;
       T = o[0];
-      const uint32_t c_last = static_cast<uint32_t>(nc - 1) / kChunk;
-      for (uint32_t c2 = c + 1; c2 <= c_last; ++c2) {
-        const float* q = ckpt + (static_cast<int64_t>(cbase[tile] + c2) * 6) * npx + vt;
-        S += gA * q[npx] + gSt * q[2 * npx] + gSx * q[3 * npx] + gSy * q[4 * npx] + gSz * q[5 * npx];
+      if (rg.y - rg.x > kLongList) {
+        S = csuf[static_cast<int64_t>(cbase[tile] + c) * npx + vt];   // the suffix k_long_suffix wrote
+      } else {
+        const uint32_t c_last = static_cast<uint32_t>(nc - 1) / kChunk;
+        for (uint32_t c2 = c + 1; c2 <= c_last; ++c2) {
+          const float* q = ckpt + (static_cast<int64_t>(cbase[tile] + c2) * kCkptSlots) * npx + vt;
+          S += gA * q[npx] + gSt * q[2 * npx] + gSx * q[3 * npx] + gSy * q[4 * npx] + gSz * q[5 * npx];
+        }
       }
     }
     // entries [k_lo, k_hi) of the list, walked down in 32-entry steps: a
@@ -1053,8 +1058,14 @@ __global__ void __launch_bounds__(kBwdChunkCta)
     const int k_hi = static_cast<int>(min(min(static_cast<uint32_t>(k_lo) + kChunk, len),
                                           static_cast<uint32_t>(__reduce_max_sync(0xffffffffu, act ? nc : 0))));
     for (int k0 = k_lo + ((k_hi - k_lo + 31) / 32 - 1) * 32; k0 >= k_lo; k0 -= 32) {
-      const uint32_t word =
-          act ? __ldg(cmask + (static_cast<int64_t>(cbase[tile]) * 4 + static_cast<uint32_t>(k0) / 32) * npx + vt) : 0u;
+      // entries below the pixel's n_contrib only (a long list's pixels stop
+      // on their own, so their words past it are not this step's)
+      const int lim = nc - k0;
+      uint32_t word = 0u;
+      if (act && lim > 0) {
+        word = __ldg(cmask + (static_cast<int64_t>(cbase[tile]) * 4 + static_cast<uint32_t>(k0) / 32) * npx + vt);
+        if (lim < 32) word &= (1u << lim) - 1u;
+      }
       uint32_t m = __reduce_or_sync(0xffffffffu, word);
       if (!m) continue;
       const bool hit = (m >> lane) & 1u;
@@ -1133,13 +1144,25 @@ __global__ void __launch_bounds__(kBwdChunkCta)
 // every valid lane adds its own entry's 12 moments with atomics.  The products
 // and sums associate differently from the per-tile kernels (same values to a
 // few ulps).
+// Thread of the per-tile forward that holds tile pixel (lr, lc) (the inverse
+// of pixel_of_thread): the chunk checkpoints and window masks are laid out by
+// it.
+__device__ __forceinline__ int thread_of_pixel(const FrameDev& F, int lr, int lc) {
+  if ((F.tw & 7) == 0 && (F.th & 3) == 0) {
+    const int wpr = F.tw >> 3;
+    return ((((lr >> 2) * wpr) + (lc >> 3)) << 5) | ((lr & 3) << 3) | (lc & 7);
+  }
+  return lr * F.tw + lc;
+}
+
 struct LongPix {
   const FrameDev* F;
   int r, c;
   bool inside;
-  uint32_t start, end;
+  uint32_t start, end, tile;
   int64_t pix;
   int HW;
+  int vt;   // the pixel's thread in the per-tile layout (checkpoints, masks)
 };
 
 __device__ __forceinline__ bool long_item(const Desc& D, const uint2* __restrict__ ranges,
@@ -1154,6 +1177,8 @@ __device__ __forceinline__ bool long_item(const Desc& D, const uint2* __restrict
   const int lt = static_cast<int>(tile - F.tile_base);
   const int ti = lt / F.ntc, tj = lt - ti * F.ntc;
   p.F = &F;
+  p.tile = tile;
+  p.vt = thread_of_pixel(F, static_cast<int>(k) / F.tw, static_cast<int>(k) % F.tw);
   p.r = ti * F.th + static_cast<int>(k) / F.tw;
   p.c = tj * F.tw + static_cast<int>(k) % F.tw;
   p.inside = p.r < F.H && p.c < F.W;
@@ -1195,7 +1220,8 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
                                                   const uint32_t* __restrict__ pv, const float4* __restrict__ rec,
                                                   const float4* __restrict__ box,
                                                   const uint32_t* __restrict__ longt, Status* __restrict__ st,
-                                                  LossEpi loss) {
+                                                  const uint32_t* __restrict__ cbase, float* __restrict__ ckpt,
+                                                  uint32_t* __restrict__ cmask, LossEpi loss) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_long = st->n_long;
   uint32_t evals = 0, contrib = 0, alg = 0;
@@ -1212,7 +1238,29 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
     pb.W = static_cast<float>(F.W);
     float T = 1.f, A = 0.f, St = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f;
     int last = 0, stop_at = -1;
-    for (uint32_t base = P.start; base < P.end; base += 32) {
+    // the chunked backward's inputs, laid out as the per-tile forward's: the
+    // pixel's composited entries of every window it walks (one bit each) and,
+    // at the end of every chunk it walks, T and the chunk's own sums
+    const int npx = D->th * D->tw;
+    const int64_t cb = static_cast<int64_t>(cbase[P.tile]);
+    float cA = 0.f, cSt = 0.f, cSx = 0.f, cSy = 0.f, cSz = 0.f;
+    const auto checkpoint = [&](uint32_t chunk) {
+      const float a = warp_sum(cA), b = warp_sum(cSt), x = warp_sum(cSx), y = warp_sum(cSy), z = warp_sum(cSz);
+      if (lane == 0) {
+        float* o = ckpt + ((cb + chunk) * kCkptSlots) * npx + P.vt;
+        o[0] = T;
+        o[npx] = a;
+        o[2 * npx] = b;
+        o[3 * npx] = x;
+        o[4 * npx] = y;
+        o[5 * npx] = z;
+      }
+      cA = cSt = cSx = cSy = cSz = 0.f;
+    };
+    uint32_t win = 0;
+    for (uint32_t base = P.start; base < P.end; base += 32, ++win) {
+      if (win > 0 && win % 4 == 0) checkpoint(win / 4 - 1);
+      uint32_t* mword = cmask + (cb * 4 + win) * npx + P.vt;
       const uint32_t j = base + lane;
       bool valid = false;
       Eval e;
@@ -1229,7 +1277,10 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
         }
       }
       // a window without a valid pair leaves T and the sums as they are
-      if (!__any_sync(0xffffffffu, valid)) continue;
+      if (!__any_sync(0xffffffffu, valid)) {
+        if (lane == 0) *mword = 0u;
+        continue;
+      }
       // P_j = prod_{i <= j} (1 - a_i) over the valid lanes
       float Pj = valid ? __fsub_rn(1.0f, e.a) : 1.0f;
 #pragma unroll
@@ -1251,8 +1302,14 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
       Sx = fmaf(ws, nx, Sx);
       Sy = fmaf(ws, ny, Sy);
       Sz = fmaf(ws, nz, Sz);
+      cA += w;
+      if (inc) cSt = fmaf(w, e.t, cSt);
+      cSx = fmaf(ws, nx, cSx);
+      cSy = fmaf(ws, ny, cSy);
+      cSz = fmaf(ws, nz, cSz);
       contrib += inc;
       const uint32_t im = __ballot_sync(0xffffffffu, inc);
+      if (lane == 0) *mword = im;
       if (im) last = static_cast<int>(base - P.start) + (31 - __clz(im)) + 1;
       T *= __shfl_sync(0xffffffffu, fs < 32 ? Pex : Pj, fs < 32 ? fs : 31);
       if (sm) {
@@ -1260,6 +1317,8 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
         break;
       }
     }
+    // the chunk holding the walk's last window (the list end or the stop)
+    if (P.end > P.start) checkpoint((win > 0 && stop_at < 0 ? win - 1 : win) / 4);
     A = warp_sum(A);
     St = warp_sum(St);
     Sx = warp_sum(Sx);
@@ -1393,16 +1452,59 @@ __global__ void __launch_bounds__(256) k_bwd_long(const Desc* __restrict__ D, co
   if (lane == 0 && co) atomicAdd(&st->contrib_bwd, co);
 }
 
+// Chunked backward over the long lists: the suffix S of every chunk (the sum
+// over the pixel's later chunks c' of gA dA_c' + gSt dSt_c' + gS . dSn_c'),
+// written to a buffer of its own (the checkpoints stay as the forward wrote
+// them, for any further backward), so that k_bwd_c reads it instead of
+// summing, per work item, up to thousands of later chunks.  One thread per (long tile, pixel), from its last contributor's
+// chunk down.
+__global__ void __launch_bounds__(256) k_long_suffix(const Desc* __restrict__ D, const uint2* __restrict__ ranges,
+                                                     const uint32_t* __restrict__ longt,
+                                                     const Status* __restrict__ st,
+                                                     const uint32_t* __restrict__ cbase,
+                                                     const float* __restrict__ ckpt, float* __restrict__ csuf) {
+  const uint32_t n_long = st->n_long;
+  if (n_long == 0) return;
+  const uint32_t tp = static_cast<uint32_t>(D->th * D->tw);
+  const int npx = static_cast<int>(tp);
+  for (uint32_t id = blockIdx.x * blockDim.x + threadIdx.x; id < n_long * tp; id += gridDim.x * blockDim.x) {
+    LongPix P;
+    long_item(*D, ranges, longt, n_long, id, P);
+    if (!P.inside) continue;
+    const FrameDev& F = *P.F;
+    const int nc = F.nc[P.pix];
+    if (nc <= 0) continue;
+    const float gA = F.gA[P.pix], gSt = F.gSt[P.pix];
+    const float gSx = F.gSn[P.pix], gSy = F.gSn[P.HW + P.pix], gSz = F.gSn[2 * static_cast<int64_t>(P.HW) + P.pix];
+    const int64_t cb = static_cast<int64_t>(cbase[P.tile]);
+    float S = 0.f;
+    for (int c = (nc - 1) / static_cast<int>(kChunk); c >= 0; --c) {
+      const float* q = ckpt + (cb + c) * kCkptSlots * npx + P.vt;
+      csuf[(cb + c) * npx + P.vt] = S;
+      S += gA * q[npx] + gSt * q[2 * npx] + gSx * q[3 * npx] + gSy * q[4 * npx] + gSz * q[5 * npx];
+    }
+  }
+}
+
 // The work counters start at zero (reset at binning and by the last warp of
 // every launch), so no memset precedes the launch.
 static cudaError_t launch_long(bool fwd, const WsPtrs& w, const uint32_t* pv, cudaStream_t s,
                                const LossEpi* loss = nullptr) {
-  int dev = 0, sms = 152;
+  int dev = 0, sms = 152, per_sm = 2;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = 2 * sms;   // warps claim (tile, pixel) items until none are left
-  if (fwd && loss) k_fwd_long<true><<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.longt, w.st, *loss);
-  else if (fwd) k_fwd_long<false><<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.longt, w.st, LossEpi{});
+  // as many CTAs as fit (the walks are bound by load latency); warps claim
+  // (tile, pixel) items until none are left
+  if (fwd && loss) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_long<true>, 256, 0);
+  else if (fwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_long<false>, 256, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_long, 256, 0);
+  const int grid = sms * (per_sm > 0 ? per_sm : 1);
+  if (fwd && loss)
+    k_fwd_long<true><<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.longt, w.st, w.cbase, w.ckpt, w.cmask,
+                                          *loss);
+  else if (fwd)
+    k_fwd_long<false><<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.longt, w.st, w.cbase, w.ckpt,
+                                           w.cmask, LossEpi{});
   else k_bwd_long<<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13, w.longt, w.st);
   return cudaGetLastError();
 }
@@ -1495,7 +1597,7 @@ static cudaError_t launch_raster_bwd_chunks(const WsPtrs& w, const uint32_t* pv,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_c, kBwdChunkCta, 0);
   k_bwd_c<<<sms * (per_sm > 0 ? per_sm : 1), kBwdChunkCta, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13,
-                                                                     w.cbase, w.ckpt, w.cmask, w.st);
+                                                                     w.cbase, w.ckpt, w.cmask, w.csuf, w.st);
   return cudaGetLastError();
 }
 
@@ -1518,8 +1620,17 @@ cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_
 
 cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
                               int group, int persistent, bool chunked, cudaStream_t s) {
-  cudaError_t e = chunked ? launch_raster_bwd_chunks(w, pv, s)
-                          : launch_raster_bwd_tiles(w, h, pv, batch, group, persistent, s);
+  if (chunked) {
+    // long lists take the chunked path too: their suffixes first
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_long_suffix<<<4 * sms, 256, 0, s>>>(w.desc, w.ranges, w.longt, w.st, w.cbase, w.ckpt, w.csuf);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_raster_bwd_chunks(w, pv, s);
+  }
+  cudaError_t e = launch_raster_bwd_tiles(w, h, pv, batch, group, persistent, s);
   if (e != cudaSuccess) return e;
   return launch_long(false, w, pv, s);
 }

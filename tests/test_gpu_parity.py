@@ -453,6 +453,46 @@ def test_long_tile_bucket_bit_exact(oracle, n, lo, hi):
     assert_grads(compare_grads(g["grads"][0], og))
 
 
+def test_second_backward_of_a_long_list_forward():
+    """Lists beyond 4096 entries take the chunked backward with per-chunk
+    suffixes computed at backward time: a second backward of the same
+    forward (same upstream planes) gives the same gradients as the first, up
+    to the order of float atomics."""
+    import torch
+    from paper_2607_04127_gb300 import render
+    rng = np.random.default_rng(11)
+    n = 12000
+    frame = scenes.Frame(32, 512, 16, 16, -0.26, 0.26)
+    az = 0.3 + rng.uniform(-0.035, 0.035, n)
+    el = rng.uniform(-0.035, 0.035, n)
+    r = rng.uniform(6.0, 12.0, n)
+    mean = np.stack([r * np.cos(el) * np.cos(az), r * np.cos(el) * np.sin(az), r * np.sin(el)], 1)
+    surf = scenes.Surfels(mean.astype(np.float32), rng.normal(size=(n, 4)).astype(np.float32),
+                          np.log(rng.uniform(0.005, 0.02, (n, 2))).astype(np.float32),
+                          rng.normal(size=n).astype(np.float32))
+    tgt = scenes.targets_for(frame, surf, 7)
+    dev = torch.device("cuda", 0)
+    params = render.map_tensors(surf, dev)
+    targets = [render.target_tensors(tgt, dev)]
+    rast = render.Rasterizer([frame], device=0)
+    try:
+        g1 = [[torch.zeros_like(p) for p in params]]
+        S = rast.bin_sort([params], check=True)
+        assert rast.counters()["n_pairs"] > 0
+        rast.forward_loss([params], targets, None, S)
+        rast.backward([params], g1, S=S)
+        g2 = [[torch.zeros_like(p) for p in params]]
+        rast.backward([params], g2, S=S)
+        torch.cuda.synchronize()
+        rast.session.check_status()
+        for a, b in zip(g2[0], g1[0]):
+            a, b = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+            assert np.abs(b).max() > 0
+            assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
+    finally:
+        rast.close()
+
+
 def test_empty_and_invisible_maps(oracle):
     from tests import _gpu
     frame = scenes.Frame(32, 64, 16, 16, -0.2, 0.2)
