@@ -37,10 +37,12 @@ keyframe supersedes a waiting older one, which is dropped and counted
 (mapping always works on the newest keyframe), so queues stay bounded.
 
 With ``slo_ms`` the scheduler admits by deadline: a tick's duration is
-modelled as ``a + kappa * (surfels of its active maps)`` with ``kappa``
+modelled as the longer of the device's, ``a`` plus each active map's own cost
+per iteration, and the host's enqueueing, a cost per request; both are
 learned online from retired ticks (the device time between the ends of
-back-to-back ticks, or the host's enqueueing interval when that paced the
-device), and a waiting request joins only
+back-to-back ticks, else a tick's own device span, and the host loop's
+time per tick while it never idled).  A map's cost starts at a learned rate per binning pair times its
+pairs and follows the ticks it runs in.  A waiting request joins only
 if the simulated remaining ticks, after those in flight, let every active
 request, itself included, finish within ``slo_ms`` of its arrival (with a
 safety factor);
@@ -112,11 +114,15 @@ class _Tick:
 
     def __init__(self, reqs, items: int, surfels: int):
         self.reqs = list(reqs)
+        self.sids = [r.session for r in self.reqs]
         self.last: list[Request] = []
         self.items = items
         self.surfels = surfels
+        self.predicted = None           # modelled seconds, when it was enqueued
         self.start = self.end = self.prev_end = None
         self.t_enqueue = 0.0            # host time the tick's enqueueing began
+        self.enqueue_seconds = None     # host time its enqueueing took
+        self.busy_period = None         # host time since the previous enqueueing, when the loop never idled
         self.host_period = None         # host time since the previous tick's enqueueing began
         self.loss = None
         self.status = None
@@ -126,7 +132,7 @@ class _Tick:
 class Server:
     def __init__(self, device=0, hbm_budget_bytes: int = 150 << 30, slots: int = 16,
                  tuning: dict | None = None, lr=(1e-3, 1e-3, 5e-3, 5e-3), plain: bool = False,
-                 keep_latest: bool = False, slo_ms: float | None = None, slo_margin: float = 0.8,
+                 keep_latest: bool = False, slo_ms: float | None = None, slo_margin: float = 0.6,
                  pipeline: int = 2, headroom: float = 1.3):
         self.device = device if isinstance(device, torch.device) else torch.device("cuda", device)
         self.budget = hbm_budget_bytes
@@ -150,12 +156,15 @@ class Server:
         self.slo_margin = slo_margin
         self.late: list[Request] = []             # rejected by the deadline admission
         self.tick_base = 4e-4                     # seconds of a tick independent of the maps
-        self.kappa = None                         # seconds per surfel-iteration, learned from retired ticks
+        self.kappa = None                         # seconds per pair-iteration, learned from retired ticks
+        self.cost: dict[int, float] = {}          # device seconds per iteration of each session's map
+        self.host_per_req = None                  # host seconds to enqueue one request's iteration
         self.overflow_ticks = 0
         self.density: dict[int, float] = {}       # pairs per surfel of each session's binning (probed)
         self._ticks = 0
         self._last_end = None                     # end event of the last enqueued tick
         self._last_enqueue = None                 # host time the last tick's enqueueing began
+        self._idled = True                        # the loop slept or waited since the last enqueueing
 
     # -- admission ------------------------------------------------------------
     def open_session(self, sid: int, surf, frame_pixels: int) -> str:
@@ -214,7 +223,10 @@ class Server:
         tick.t_enqueue = time.perf_counter()
         if self._last_enqueue is not None:
             tick.host_period = tick.t_enqueue - self._last_enqueue
+            if not self._idled:
+                tick.busy_period = tick.host_period
         self._last_enqueue = tick.t_enqueue
+        self._idled = False
         frames = [r.frame for r in active]
         fmap = list(range(len(active)))
         if self.rast is None:
@@ -247,6 +259,9 @@ class Server:
             s.t += 1
         render.adam_step_batch([(s.params, s.grads, s.m, s.v, s.t, self.lr) for s in maps], zero_grad=True)
         tick.end.record(stream)
+        tick.enqueue_seconds = time.perf_counter() - tick.t_enqueue
+        if self.kappa is not None:
+            tick.predicted = self._tick_model(tick.sids)
         self._last_end = tick.end
         self._ticks += 1
         return tick
@@ -271,11 +286,11 @@ class Server:
         """(status, required pairs, device seconds, per-request losses) of a
         completed tick."""
         st, req = lib.lgs_status_of_word(tick.status.data_ptr())
+        # device time: from the previous tick's end when the two ran back to
+        # back (launch gaps included), else the tick's own span (the host's
+        # pace is modelled apart, from its enqueueing time)
         t0 = tick.prev_end if tick.prev_end is not None else tick.start
         seconds = t0.elapsed_time(tick.end) / 1e3
-        if tick.prev_end is None and tick.host_period is not None:
-            # the device idled before this tick: the host's enqueueing paced it
-            seconds = max(seconds, tick.host_period)
         return st, req, seconds, tick.loss.numpy().tolist()
 
     def _retire(self, tick, now: float):
@@ -297,7 +312,7 @@ class Server:
         elif st != lib.LGS_OK:
             raise lib.LgsError(st, "device status of a serving tick")
         if not tick.first and st == lib.LGS_OK:
-            self._learn(tick.surfels, seconds)
+            self._learn(tick, seconds)
         for r, l in zip(tick.reqs, losses):
             r.losses.append(float(l))
         done = []
@@ -310,26 +325,64 @@ class Server:
         return done
 
     # -- deadline admission --------------------------------------------------------
-    def _learn(self, surfels: int, seconds: float):
-        k = max(seconds - self.tick_base, 0.0) / max(surfels, 1)
+    def _pairs(self, sid) -> float:
+        """Pairs of a session's binning: its surfels at its probed density
+        (the mean of the probed ones before its first run)."""
+        d = self.density.get(sid)
+        if d is None:
+            d = float(np.mean(list(self.density.values()))) if self.density else 8.0
+        return self.sessions[sid].n * d
+
+    def _session_cost(self, sid) -> float:
+        c = self.cost.get(sid)
+        return c if c is not None else self.kappa * self._pairs(sid)
+
+    def _tick_model(self, sids) -> float:
+        """Modelled seconds of a tick over these sessions' maps: the device's
+        (a base plus every map's own cost) or the host's enqueueing, which
+        paces the device when it is the longer."""
+        dev = self.tick_base + sum(self._session_cost(s) for s in sids)
+        host = self.host_per_req * len(sids) if self.host_per_req is not None else 0.0
+        return max(dev, host)
+
+    def _learn(self, tick, seconds: float):
+        """Fit the tick model to a retired tick: the host's cost per request
+        from the loop's time since the previous enqueueing when the loop never
+        idled in between (else the enqueueing's own time), and from the device
+        time the pair rate and every map's own cost, scaled by the damped
+        ratio of measured to modelled."""
+        host = getattr(tick, "busy_period", None)
+        if host is None:
+            host = getattr(tick, "enqueue_seconds", None)
+        if host is not None:
+            h = host / max(len(tick.sids), 1)
+            self.host_per_req = h if self.host_per_req is None else 0.5 * self.host_per_req + 0.5 * h
+        y = max(seconds - self.tick_base, 0.0)
+        pairs = sum(self._pairs(s) for s in tick.sids if s in self.sessions)
+        k = y / max(pairs, 1.0)
         self.kappa = k if self.kappa is None else 0.5 * self.kappa + 0.5 * k
+        sids = [s for s in tick.sids if s in self.sessions]
+        pred = sum(self._session_cost(s) for s in sids)
+        if pred > 0:
+            f = (y / pred) ** 0.5
+            for s in sids:
+                self.cost[s] = self._session_cost(s) * f
 
     def _feasible(self, active, now: float, backlog: float = 0.0) -> bool:
         """Simulate the remaining ticks of ``active`` (no further arrivals),
         after ``backlog`` seconds of ticks already in flight: does every
         request finish within the margin of its deadline?"""
-        rem = [(r.iters - r.done_iters, self.sessions[r.session].n, r.arrival + self.slo_margin * self.slo)
-               for r in active]
+        rem = [(r.iters - r.done_iters, r.session, r.arrival + self.slo_margin * self.slo) for r in active]
         t = now + backlog
         while rem:
-            t += self.tick_base + self.kappa * sum(n for _, n, _ in rem)
+            t += self._tick_model([sid for _, sid, _ in rem])
             nxt = []
-            for k, n, dl in rem:
+            for k, sid, dl in rem:
                 if k == 1:
                     if t > dl:
                         return False
                 else:
-                    nxt.append((k - 1, n, dl))
+                    nxt.append((k - 1, sid, dl))
             rem = nxt
         return True
 
@@ -369,8 +422,8 @@ class Server:
                     self.unserved.append(r)
                     continue
                 if s is not None and len(active) < self.slots and r.session not in busy:
-                    backlog = (sum(self.tick_base + self.kappa * t.surfels for t in inflight)
-                               if self.kappa is not None else 0.0)
+                    backlog = (sum(t.predicted if t.predicted is not None else self._tick_model(t.sids)
+                                   for t in inflight) if self.kappa is not None else 0.0)
                     if self.slo is not None and self.kappa is not None and \
                             not self._feasible(active + [r], now, backlog):
                         self.late.append(r)      # would miss its deadline or make another one miss
@@ -399,9 +452,11 @@ class Server:
                 inflight.append(tick)
                 continue
             if inflight:
+                self._idled = True
                 self._wait_tick(inflight[0])
                 continue
             if pending:
+                self._idled = True
                 time.sleep(max(0.0, min(pending[0].arrival - now, 0.002)))
             elif waiting:
                 # nothing runs and nothing arrives: these sessions' memory never frees up

@@ -15,6 +15,7 @@ def _server(kappa=1e-8, base=1e-3, slo_ms=50.0, margin=1.0):
 
 def _req(srv, sid, n, arrival, iters, done=0):
     srv.sessions[sid] = types.SimpleNamespace(n=n)
+    srv.density[sid] = 1.0      # one binning pair per surfel: the model's cost is kappa * n
     r = serve.Request(sid, None, None, arrival, iters)
     r.done_iters = done
     return r
@@ -40,6 +41,37 @@ def test_batch_ticks_slow_every_member_until_it_leaves():
     # the margin scales the deadline: 34 ms does not fit 0.6 x 50 ms
     srv.slo_margin = 0.6
     assert not srv._feasible([a, b], 0.0)
+
+
+def _tick(sids, host_period=None, paced_by_host=False, enqueue_seconds=None):
+    return types.SimpleNamespace(sids=list(sids), host_period=host_period, enqueue_seconds=enqueue_seconds,
+                                 prev_end=None if paced_by_host else object())
+
+
+def test_map_costs_are_learned_per_session():
+    # two maps of the same size whose iterations cost 2 ms and 6 ms on the
+    # device: ticks that run them alone separate their costs, and a tick of
+    # both is modelled as the sum
+    srv = _server(kappa=None, base=1e-3)
+    _req(srv, 0, 100_000, 0.0, 10)
+    _req(srv, 1, 100_000, 0.0, 10)
+    for _ in range(12):
+        srv._learn(_tick([0]), 1e-3 + 2e-3)
+        srv._learn(_tick([1]), 1e-3 + 6e-3)
+    assert srv._tick_model([0]) == pytest.approx(3e-3, rel=0.1)
+    assert srv._tick_model([1]) == pytest.approx(7e-3, rel=0.1)
+    assert srv._tick_model([0, 1]) == pytest.approx(9e-3, rel=0.1)
+
+
+def test_host_paced_ticks_set_a_floor_per_request():
+    # the host needed 10 ms to enqueue a tick of two requests: a tick of four
+    # is modelled at no less than 20 ms; time the host spent idle between
+    # ticks (a long interval before a host-paced tick) does not count
+    srv = _server(kappa=1e-9, base=1e-3)
+    for k in range(4):
+        _req(srv, k, 1000, 0.0, 10)
+    srv._learn(_tick([0, 1], host_period=0.5, paced_by_host=True, enqueue_seconds=10e-3), 10e-3)
+    assert 20e-3 * 0.999 <= srv._tick_model([0, 1, 2, 3]) <= 21e-3
 
 
 def test_latency_stats_count_deadline_rejections():
