@@ -226,6 +226,13 @@ Layout make_layout(int64_t items, uint32_t tiles, int64_t pairs_cap, uint32_t ta
   L.csuf = take(sizeof(float) * static_cast<size_t>(tile_pixels) * static_cast<size_t>(C));
   L.cmask = take(sizeof(uint32_t) * 4 * static_cast<size_t>(tile_pixels) * static_cast<size_t>(C));
   L.midl = take(4 * T);
+  // backward queues: class 0 takes at most every (chunk, warp block) item,
+  // every other class at most one item per (tile, warp block)
+  const size_t blocks = tile_pixels >= 32 ? tile_pixels / 32 : 1;
+  L.bq_cap0 = static_cast<uint32_t>(static_cast<size_t>(C) * blocks);
+  L.bq_capk = static_cast<uint32_t>(T * blocks);
+  L.bwm = take(sizeof(uint32_t) * T * blocks);
+  L.bq = take(sizeof(uint2) * (static_cast<size_t>(L.bq_cap0) + (lgs::kBwdClasses - 1) * static_cast<size_t>(L.bq_capk)));
   L.chunks_cap = C;
   L.total = off;
   L.items_cap = items;

@@ -50,6 +50,14 @@ struct Desc {
   MapDev m[LGS_MAX_MAPS];
 };
 
+// Queues of the chunked backward's work items, in the order warps claim
+// them: class 0 holds the chunks a warp block walks in full (and every chunk
+// of a long list), classes 1 .. kBwdClasses-1 the chunk in which the block's
+// last composited entry lies, by decreasing length of its walked part.  The
+// costliest items go first, so the backward ends on short ones.  Built at
+// the start of every backward from the forward's per-block last entries.
+constexpr int kBwdClasses = 9;
+
 // Status words (device, in the workspace).
 struct Status {
   unsigned long long required_pairs;  // pairs the last bin_sort needed
@@ -60,6 +68,7 @@ struct Status {
   unsigned int check;                 // a checked-build bounds check failed
   unsigned int work_counter;          // persistent scheduler: next work item
   unsigned int work_counter2;
+  unsigned int bq_count[kBwdClasses]; // backward items queued per class (follows work_counter2: one memset)
   unsigned int n_long;                // tiles whose list is longer than kLongList
   unsigned int long_counter_fwd;      // work counters of the long-list kernels (self-resetting)
   unsigned int long_counter_bwd;
@@ -80,8 +89,9 @@ struct Status {
 
 struct Layout {
   size_t desc, status, tables, rec, box, key, cnt, tset, tcur, pkey, ptile, pv, ranges, g13, work, longt, loss_part,
-      cbase, ckpt, csuf, cmask, midl, total;
+      cbase, ckpt, csuf, cmask, midl, bwm, bq, total;
   int64_t items_cap, pairs_cap, chunks_cap;
+  uint32_t bq_cap0, bq_capk;  // capacity of the backward queue of class 0 and of each other class
   uint32_t tiles_cap;
   uint32_t tables_cap;     // floats
   int32_t loss_blocks;
@@ -110,6 +120,9 @@ struct WsPtrs {
   float* csuf;             // [chunks][tile pixels] long lists: the suffix of the later chunks (backward)
   uint32_t* cmask;         // [chunks][4 windows][tile pixels] entries each pixel composited, one bit per entry
   uint32_t* midl;          // [tiles] tiles whose bucket takes the wide merge sort (st->n_mid of them)
+  uint32_t* bwm;           // [tiles][warp blocks] the block's largest n_contrib (short lists; written by k_fwd_s)
+  uint2* bq;               // backward work queues: (chunk * blocks per tile + block, tile); class 0 first
+  uint32_t bq_cap0, bq_capk;
 };
 
 inline WsPtrs ws_ptrs(void* base, const Layout& L) {
@@ -137,6 +150,10 @@ inline WsPtrs ws_ptrs(void* base, const Layout& L) {
   p.csuf = reinterpret_cast<float*>(b + L.csuf);
   p.cmask = reinterpret_cast<uint32_t*>(b + L.cmask);
   p.midl = reinterpret_cast<uint32_t*>(b + L.midl);
+  p.bwm = reinterpret_cast<uint32_t*>(b + L.bwm);
+  p.bq = reinterpret_cast<uint2*>(b + L.bq);
+  p.bq_cap0 = L.bq_cap0;
+  p.bq_capk = L.bq_capk;
   return p;
 }
 

@@ -179,10 +179,14 @@ __device__ void scale_reg_row(const Desc& D, const lgs_loss_params& P, int write
 // ctot[F][2] (zero on entry: cleared by the binning and by the loss).  Rows
 // y >= n_frames (when launched with them): the scale regulariser of map
 // y - n_frames, which needs no rendered value, so a forward with the
-// image-loss epilogue leaves only the loss vector for after it.
+// image-loss epilogue leaves only the loss vector for after it.  The first
+// CTA also zeroes that forward's counters (`clear`, n_clear words: its tile
+// counter), which spares the forward a memset.
 __global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, int* __restrict__ ctot,
                                                     lgs_loss_params P, int write_grad,
-                                                    unsigned long long* __restrict__ acc) {
+                                                    unsigned long long* __restrict__ acc,
+                                                    unsigned int* __restrict__ clear, int n_clear) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && static_cast<int>(threadIdx.x) < n_clear) clear[threadIdx.x] = 0u;
   if (blockIdx.y >= static_cast<unsigned>(D->n_frames)) {
     __shared__ long long s_ll[8];
     scale_reg_row(*D, P, write_grad, acc, blockIdx.y - D->n_frames, s_ll);
@@ -374,7 +378,8 @@ cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs
                         float* loss_out, cudaStream_t s) {
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(w.loss_part);
   int* ctot = loss_counts_ptr(w);
-  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, ctot, p, 0, acc);
+  // (between a forward and its backward: the forward's queues stay)
+  k_loss_count<<<dim3(kLossBlocks, h.n_frames), 256, 0, s>>>(w.desc, ctot, p, 0, acc, nullptr, 0);
   k_loss_main<<<dim3(kLossBlocks, h.n_frames + h.n_maps), 256, 0, s>>>(w.desc, w.st, p, scale_grad ? 1 : 0, ctot,
                                                                         acc, loss_out, h.n_frames);
   return cudaGetLastError();
@@ -382,11 +387,13 @@ cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs
 
 // Before a forward with the image-loss epilogue: the mask counts (the
 // epilogue normalises by them) and the scale regulariser; the forward's
-// long-list kernel writes the loss vector when every pixel is done.
+// long-list kernel writes the loss vector when every pixel is done.  Also
+// zeroes the forward's tile counter.
 cudaError_t launch_loss_counts(const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
                                cudaStream_t s) {
   k_loss_count<<<dim3(kLossBlocks, h.n_frames + h.n_maps), 256, 0, s>>>(
-      w.desc, loss_counts_ptr(w), p, scale_grad ? 1 : 0, reinterpret_cast<unsigned long long*>(w.loss_part));
+      w.desc, loss_counts_ptr(w), p, scale_grad ? 1 : 0, reinterpret_cast<unsigned long long*>(w.loss_part),
+      &w.st->work_counter, 1);
   return cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@
 // butterfly reduce-scatter (16 shuffles), 15 lanes add them into a shared
 // per-batch accumulator, and the CTA flushes one atomic add per (surfel,
 // component) into the per-item gradient buffer.
+#include <cstddef>
 #include <cuda_runtime.h>
 
 #include "lgs_internal.cuh"
@@ -726,7 +727,7 @@ __global__ void __maxnreg__(72)
     k_fwd_s(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
             const float4* __restrict__ rec, const float4* __restrict__ box, const uint32_t* __restrict__ order,
             Status* __restrict__ st, int persistent, const uint32_t* __restrict__ cbase, float* __restrict__ ckpt,
-            uint32_t* __restrict__ cmask, LossEpi loss) {
+            uint32_t* __restrict__ cmask, uint32_t* __restrict__ bwm, LossEpi loss) {
   __shared__ WarpRecs s_w[kMaxTileThreads / 32];
   const int lane = threadIdx.x & 31;
   WarpRecs& sw = s_w[threadIdx.x >> 5];
@@ -855,6 +856,9 @@ __global__ void __maxnreg__(72)
       F.nc[tc.pix] = last;
       alg += stop_at >= 0 ? static_cast<uint32_t>(stop_at) : tc.end - tc.start;
     }
+    // the block's largest n_contrib: the backward's chunks of this block end there
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, static_cast<uint32_t>(last));
+    if (lane == 0) bwm[tile * (blockDim.x >> 5) + (threadIdx.x >> 5)] = wmax;
     if (LOSS) loss_epilogue(*D, loss, tc.f, tc.inside, tc.pix, tc.HW, A, St, Sx, Sy, Sz);
   }
   unsigned long long ev = evals, co = contrib;
@@ -980,11 +984,15 @@ __global__ void __launch_bounds__(kMaxTileThreads)
 // ---------------------------------------------------------------------------
 // Chunked backward (group 16 after the shared-memory forward): a work item
 // is one warp's 4 x 8 pixel block of a tile over one chunk of kChunk list
-// entries, claimed through an atomic counter.  The reverse walk of chunk c
-// starts from the forward's checkpoint: T at the end of the chunk, and the
-// suffix S = sum over the later chunks c' of gA dA_c' + gSt dSt_c' + gS .
-// dSn_c' (their own sums of w, w t, w n').  Items are independent, so a
-// frame offers several times more warps than pixel blocks.
+// entries, claimed through an atomic counter from k_bwd_prep's queues: only
+// chunks that hold one of the block's composited entries, chunks walked in
+// full first, then the last ones by decreasing walked length (a warp that
+// claims late gets a short item, so the SMs finish together).  The reverse
+// walk of chunk c starts from the forward's checkpoint: T at the end of the
+// chunk, and the suffix S = sum over the later chunks c' of gA dA_c' + gSt
+// dSt_c' + gS . dSn_c' (their own sums of w, w t, w n').  Items are
+// independent, so a frame offers several times more warps than pixel
+// blocks.
 // ---------------------------------------------------------------------------
 constexpr int kBwdChunkCta = 256;
 
@@ -992,7 +1000,7 @@ __global__ void __launch_bounds__(kBwdChunkCta)
     k_bwd_c(const Desc* __restrict__ D, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pv,
             const float4* __restrict__ rec, const float4* __restrict__ box, float* __restrict__ g13,
             const uint32_t* __restrict__ cbase, const float* __restrict__ ckpt, const uint32_t* __restrict__ cmask,
-            const float* __restrict__ csuf,
+            const float* __restrict__ csuf, const uint2* __restrict__ bq, uint32_t bq_cap0, uint32_t bq_capk,
             Status* __restrict__ st) {
   __shared__ WarpRecs s_w[kBwdChunkCta / 32];
   __shared__ uint32_t s_item[kBwdChunkCta / 32][32];
@@ -1000,22 +1008,27 @@ __global__ void __launch_bounds__(kBwdChunkCta)
   WarpRecs& sw = s_w[threadIdx.x >> 5];
   uint32_t* si = s_item[threadIdx.x >> 5];
   const int npx = D->th * D->tw, wpt = npx >> 5;
-  const uint32_t n_work = st->n_chunks * static_cast<uint32_t>(wpt);
+  // the forward's queues, claimed in class order: lane l < kBwdClasses holds
+  // class l's size (clamped to its capacity) and the items before its end
+  const uint32_t qn = lane < kBwdClasses ? min(st->bq_count[lane], lane == 0 ? bq_cap0 : bq_capk) : 0u;
+  uint32_t qend = qn;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, qend, o);
+    if (lane >= o) qend += x;
+  }
+  const uint32_t n_work = __shfl_sync(0xffffffffu, qend, kBwdClasses - 1);
   while (true) {
     uint32_t id = 0;
     if (lane == 0) id = atomicAdd(&st->work_counter2, 1u);
     id = __shfl_sync(0xffffffffu, id, 0);
     if (id >= n_work) break;
-    const uint32_t k = id / static_cast<uint32_t>(wpt);
-    const int vt = static_cast<int>(id - k * static_cast<uint32_t>(wpt)) * 32 + lane;   // thread of the tile
-    // tile of chunk k: the last tile whose first chunk is <= k (tiles
-    // without chunks share their successor's first chunk)
-    uint32_t lo = 0, hi = D->n_tiles - 1;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi + 1) >> 1;
-      if (__ldg(cbase + mid) <= k) lo = mid; else hi = mid - 1;
-    }
-    const uint32_t tile = lo, c = k - __ldg(cbase + lo);
+    const int cls = __ffs(__ballot_sync(0xffffffffu, lane < kBwdClasses && id < qend)) - 1;
+    const uint32_t first = __shfl_sync(0xffffffffu, qend - qn, cls);
+    const uint2 q = __ldg(bq + (cls == 0 ? 0u : bq_cap0 + static_cast<uint32_t>(cls - 1) * bq_capk) + (id - first));
+    const uint32_t k = q.x / static_cast<uint32_t>(wpt);
+    const int vt = static_cast<int>(q.x - k * static_cast<uint32_t>(wpt)) * 32 + lane;   // thread of the tile
+    const uint32_t tile = q.y, c = k - __ldg(cbase + tile);
     const int f = frame_of_tile(*D, tile);
     const FrameDev& F = D->f[f];
     const int lt = static_cast<int>(tile - F.tile_base);
@@ -1042,7 +1055,7 @@ __global__ void __launch_bounds__(kBwdChunkCta)
       const float* o = ckpt + (static_cast<int64_t>(cbase[tile] + c) * kCkptSlots) * npx + vt;
       T = o[0];
       if (rg.y - rg.x > kLongList) {
-        S = csuf[static_cast<int64_t>(cbase[tile] + c) * npx + vt];   // the suffix k_long_suffix wrote
+        S = csuf[static_cast<int64_t>(cbase[tile] + c) * npx + vt];   // the suffix k_bwd_prep wrote
       } else {
         const uint32_t c_last = static_cast<uint32_t>(nc - 1) / kChunk;
         for (uint32_t c2 = c + 1; c2 <= c_last; ++c2) {
@@ -1452,37 +1465,155 @@ __global__ void __launch_bounds__(256) k_bwd_long(const Desc* __restrict__ D, co
   if (lane == 0 && co) atomicAdd(&st->contrib_bwd, co);
 }
 
-// Chunked backward over the long lists: the suffix S of every chunk (the sum
-// over the pixel's later chunks c' of gA dA_c' + gSt dSt_c' + gS . dSn_c'),
-// written to a buffer of its own (the checkpoints stay as the forward wrote
-// them, for any further backward), so that k_bwd_c reads it instead of
-// summing, per work item, up to thousands of later chunks.  One thread per (long tile, pixel), from its last contributor's
-// chunk down.
-__global__ void __launch_bounds__(256) k_long_suffix(const Desc* __restrict__ D, const uint2* __restrict__ ranges,
-                                                     const uint32_t* __restrict__ longt,
-                                                     const Status* __restrict__ st,
-                                                     const uint32_t* __restrict__ cbase,
-                                                     const float* __restrict__ ckpt, float* __restrict__ csuf) {
-  const uint32_t n_long = st->n_long;
-  if (n_long == 0) return;
-  const uint32_t tp = static_cast<uint32_t>(D->th * D->tw);
-  const int npx = static_cast<int>(tp);
-  for (uint32_t id = blockIdx.x * blockDim.x + threadIdx.x; id < n_long * tp; id += gridDim.x * blockDim.x) {
-    LongPix P;
-    long_item(*D, ranges, longt, n_long, id, P);
-    if (!P.inside) continue;
-    const FrameDev& F = *P.F;
-    const int nc = F.nc[P.pix];
-    if (nc <= 0) continue;
-    const float gA = F.gA[P.pix], gSt = F.gSt[P.pix];
-    const float gSx = F.gSn[P.pix], gSy = F.gSn[P.HW + P.pix], gSz = F.gSn[2 * static_cast<int64_t>(P.HW) + P.pix];
-    const int64_t cb = static_cast<int64_t>(cbase[P.tile]);
-    float S = 0.f;
-    for (int c = (nc - 1) / static_cast<int>(kChunk); c >= 0; --c) {
-      const float* q = ckpt + (cb + c) * kCkptSlots * npx + P.vt;
-      csuf[(cb + c) * npx + P.vt] = S;
-      S += gA * q[npx] + gSt * q[2 * npx] + gSx * q[3 * npx] + gSy * q[4 * npx] + gSz * q[5 * npx];
+// Before the chunked backward (one launch):
+// (1) its work queues, from the forward's largest n_contrib of every (tile,
+//     warp block) (a long list: its length): one thread per tile, warp-
+//     aggregated reservations (one atomic per warp for class 0, one per
+//     class present and block for the others).  A tile's full chunks are
+//     queued chunk by chunk, its blocks side by side: they read the same
+//     list entries, so warps that claim them together share those loads in
+//     L2.  The queue sizes are zero on entry (cleared with the claim
+//     counter).
+// (2) over the long lists: the suffix S of every chunk (the sum over the
+//     pixel's later chunks c' of gA dA_c' + gSt dSt_c' + gS . dSn_c'),
+//     written to a buffer of its own (the checkpoints stay as the forward
+//     wrote them, for any further backward), so that k_bwd_c reads it
+//     instead of summing, per work item, up to thousands of later chunks.
+//     One CTA per (long tile, warp block): its eight warps split the
+//     block's chunks into segments (lane = pixel), sum their segment while
+//     parking every chunk's term in the suffix buffer, add up the later
+//     segments' sums in shared memory, then walk their segment down.  A
+//     list of 2,000 chunks is eight chains of 250, not one of 2,000.
+constexpr int kMaxBlocks = kMaxTileThreads / 32;
+
+__global__ void __launch_bounds__(256) k_bwd_prep(const Desc* __restrict__ D, const uint2* __restrict__ ranges,
+                                                  const uint32_t* __restrict__ longt, Status* __restrict__ st,
+                                                  const uint32_t* __restrict__ cbase,
+                                                  const uint32_t* __restrict__ bwm, uint2* __restrict__ bq,
+                                                  uint32_t cap0, uint32_t capk,
+                                                  const float* __restrict__ ckpt, float* __restrict__ csuf) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t blocks = static_cast<uint32_t>(D->th * D->tw) >> 5;
+  const uint32_t n_tiles = D->n_tiles;
+  // (1) a warp-uniform loop: every lane reaches the warp collectives
+  for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < n_tiles; t0 += gridDim.x * blockDim.x) {
+    const uint32_t tile = t0 + static_cast<uint32_t>(lane);
+    const bool ok = tile < n_tiles;
+    // a long list's blocks take every chunk (its pixels' walks end in
+    // k_fwd_long, which keeps no per-block maximum)
+    const uint32_t len = ok ? ranges[tile].y - ranges[tile].x : 0u;
+    uint32_t wm[kMaxBlocks];
+    uint32_t nfull = 0, nf_max = 0;
+#pragma unroll
+    for (int b = 0; b < kMaxBlocks; ++b) {
+      wm[b] = ok && static_cast<uint32_t>(b) < blocks ? (len > kLongList ? len : bwm[tile * blocks + b]) : 0u;
+      nfull += wm[b] / kChunk;
+      nf_max = max(nf_max, wm[b] / kChunk);
     }
+    const uint32_t c0 = ok ? cbase[tile] : 0u;
+    // class 0: the tile's full chunks, placed by an inclusive warp scan
+    uint32_t incl = nfull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += x;
+    }
+    uint32_t pos = 0;
+    if (lane == 31 && incl) pos = atomicAdd(&st->bq_count[0], incl);
+    pos = __shfl_sync(0xffffffffu, pos, 31) + incl - nfull;
+    for (uint32_t c = 0; c < nf_max; ++c) {
+#pragma unroll
+      for (int b = 0; b < kMaxBlocks; ++b) {
+        if (c < wm[b] / kChunk) {
+          if (pos < cap0) bq[pos] = make_uint2((c0 + c) * blocks + static_cast<uint32_t>(b), tile);
+          ++pos;
+        }
+      }
+    }
+    // every block's chunk holding its last entry: the class of its walked
+    // length (longest first), one reservation per class present
+#pragma unroll
+    for (int b = 0; b < kMaxBlocks; ++b) {
+      if (static_cast<uint32_t>(b) >= blocks) break;
+      const uint32_t rem = wm[b] % kChunk;
+      const uint32_t cls = rem ? 1u + ((kChunk - rem) * (kBwdClasses - 1)) / kChunk : 0u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, cls);
+      const int leader = __ffs(peers) - 1;
+      uint32_t bk = 0;
+      if (cls && lane == leader) bk = atomicAdd(&st->bq_count[cls], static_cast<uint32_t>(__popc(peers)));
+      bk = __shfl_sync(0xffffffffu, bk, leader) + static_cast<uint32_t>(__popc(peers & ((1u << lane) - 1u)));
+      if (cls && bk < capk)
+        bq[cap0 + (cls - 1) * capk + bk] = make_uint2((c0 + wm[b] / kChunk) * blocks + static_cast<uint32_t>(b), tile);
+    }
+  }
+  // (2) requires 256 threads (eight segments); CTA-uniform loop
+  __shared__ float s_seg[8][32];
+  const uint32_t n_long = st->n_long;
+  const int npx = static_cast<int>(blocks) * 32;
+  const int wseg = threadIdx.x >> 5;
+  for (uint32_t it = blockIdx.x; it < n_long * blocks; it += gridDim.x) {
+    const uint32_t lt = it / blocks, blk = it - lt * blocks;
+    const uint32_t tile = longt[lt];
+    const FrameDev& F = D->f[frame_of_tile(*D, tile)];
+    const int ltile = static_cast<int>(tile - F.tile_base);
+    const int ti = ltile / F.ntc, tj = ltile - ti * F.ntc;
+    const int vt = static_cast<int>(blk) * 32 + lane;
+    int lr, lc;
+    pixel_of_thread(F, vt, lr, lc);
+    const int r = ti * F.th + lr, col = tj * F.tw + lc;
+    const int64_t pix = static_cast<int64_t>(r) * F.W + col;
+    const int HW = F.H * F.W;
+    const int nc = r < F.H && col < F.W ? F.nc[pix] : 0;
+    const int cl = nc > 0 ? (nc - 1) / static_cast<int>(kChunk) + 1 : 0;   // the pixel's chunks
+    const int seg = (__reduce_max_sync(0xffffffffu, static_cast<uint32_t>(cl)) + 7) / 8;
+    const int lo = wseg * seg, hi = min(lo + seg, cl);
+    float gA = 0.f, gSt = 0.f, gSx = 0.f, gSy = 0.f, gSz = 0.f;
+    if (hi > lo) {
+      gA = F.gA[pix];
+      gSt = F.gSt[pix];
+      gSx = F.gSn[pix];
+      gSy = F.gSn[HW + pix];
+      gSz = F.gSn[2 * static_cast<int64_t>(HW) + pix];
+    }
+    const int64_t cb = static_cast<int64_t>(cbase[tile]);
+    // pass 1: every chunk's term (parked in csuf) and the segment's sum
+    float tot = 0.f;
+    for (int c = hi - 1; c >= lo; c -= 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        v[u] = 0.f;
+        if (c - u >= lo) {
+          const float* q = ckpt + (cb + c - u) * kCkptSlots * npx + vt;
+          v[u] = gA * q[npx] + gSt * q[2 * npx] + gSx * q[3 * npx] + gSy * q[4 * npx] + gSz * q[5 * npx];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (c - u >= lo) {
+          csuf[(cb + c - u) * npx + vt] = v[u];
+          tot += v[u];
+        }
+      }
+    }
+    s_seg[wseg][lane] = tot;
+    __syncthreads();
+    float S = 0.f;
+    for (int w2 = 7; w2 > wseg; --w2) S += s_seg[w2][lane];
+    // pass 2: the suffix before every chunk of the segment, walking down
+    for (int c = hi - 1; c >= lo; c -= 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = c - u >= lo ? csuf[(cb + c - u) * npx + vt] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (c - u >= lo) {
+          csuf[(cb + c - u) * npx + vt] = S;
+          S += v[u];
+        }
+      }
+    }
+    __syncthreads();   // s_seg is rewritten by the next item
   }
 }
 
@@ -1546,7 +1677,7 @@ static cudaError_t launch_raster_fwd_tiles(const WsPtrs& w, const Desc& h, const
     case 0:
       if (group == 16)
         k_fwd_s<false><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent,
-                                                    w.cbase, w.ckpt, w.cmask, LossEpi{});
+                                                    w.cbase, w.ckpt, w.cmask, w.bwm, LossEpi{});
       else if (group == 1) k_fwd_w<1><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       else if (group == 2) k_fwd_w<2><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
       else k_fwd_w<4><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, ord, w.st, persistent);
@@ -1588,31 +1719,27 @@ cudaError_t launch_raster_fwd(const Layout&, const WsPtrs& w, const Desc& h, con
 }
 
 // Chunked backward: as many resident CTAs as fit, warps claim (chunk, pixel
-// block) items until none are left.
+// block) items from the queues k_bwd_prep built until none are left.
 static cudaError_t launch_raster_bwd_chunks(const WsPtrs& w, const uint32_t* pv, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(&w.st->work_counter2, 0, sizeof(unsigned int), s);
-  if (e != cudaSuccess) return e;
   int dev = 0, sms = 152, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_c, kBwdChunkCta, 0);
   k_bwd_c<<<sms * (per_sm > 0 ? per_sm : 1), kBwdChunkCta, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13,
-                                                                     w.cbase, w.ckpt, w.cmask, w.csuf, w.st);
+                                                                     w.cbase, w.ckpt, w.cmask, w.csuf, w.bq,
+                                                                     w.bq_cap0, w.bq_capk, w.st);
   return cudaGetLastError();
 }
 
 // The shared-memory forward with the image-loss epilogue (and the long-list
-// forward with the same epilogue).
+// forward with the same epilogue).  Follows launch_loss_counts on the same
+// stream, which zeroed the tile counter.
 cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_t* pv, int persistent,
                                    const lgs_loss_params& p, float* loss_out, cudaStream_t s) {
-  if (persistent) {
-    cudaError_t e = cudaMemsetAsync(&w.st->work_counter, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-  }
   LossEpi loss{p, loss_counts_ptr(w), reinterpret_cast<unsigned long long*>(w.loss_part), loss_out};
   const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
   k_fwd_s<true><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, persistent ? w.work : nullptr, w.st,
-                                             persistent, w.cbase, w.ckpt, w.cmask, loss);
+                                             persistent, w.cbase, w.ckpt, w.cmask, w.bwm, loss);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_long(true, w, pv, s, &loss);
@@ -1621,12 +1748,18 @@ cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_
 cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
                               int group, int persistent, bool chunked, cudaStream_t s) {
   if (chunked) {
-    // long lists take the chunked path too: their suffixes first
+    // the claim counter and the queue sizes (adjacent words) start at zero;
+    // then the queues and the long lists' suffixes, then the walk
+    static_assert(offsetof(Status, bq_count) == offsetof(Status, work_counter2) + sizeof(unsigned int),
+                  "the backward queue sizes follow the backward's claim counter");
+    cudaError_t e = cudaMemsetAsync(&w.st->work_counter2, 0, sizeof(unsigned int) * (1 + kBwdClasses), s);
+    if (e != cudaSuccess) return e;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_long_suffix<<<4 * sms, 256, 0, s>>>(w.desc, w.ranges, w.longt, w.st, w.cbase, w.ckpt, w.csuf);
-    cudaError_t e = cudaGetLastError();
+    k_bwd_prep<<<4 * sms, 256, 0, s>>>(w.desc, w.ranges, w.longt, w.st, w.cbase, w.bwm, w.bq, w.bq_cap0, w.bq_capk,
+                                       w.ckpt, w.csuf);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_raster_bwd_chunks(w, pv, s);
   }
