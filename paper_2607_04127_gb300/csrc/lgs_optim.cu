@@ -1,6 +1,7 @@
 // lgs_optim.cu -- chain of the per-record gradients to the raw surfel
 // parameters, the mapping loss (image terms + scale regulariser) with its
 // upstream gradients, and a fused Adam step.
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include "lgs_internal.cuh"
@@ -391,7 +392,19 @@ cudaError_t launch_loss(const Layout&, const WsPtrs& w, const Desc& h, const lgs
 // zeroes the forward's tile counter.
 cudaError_t launch_loss_counts(const WsPtrs& w, const Desc& h, const lgs_loss_params& p, bool scale_grad,
                                cudaStream_t s) {
-  k_loss_count<<<dim3(kLossBlocks, h.n_frames + h.n_maps), 256, 0, s>>>(
+  // one pixel or surfel per thread where it fits (a grid-stride loop would
+  // put a chain of DRAM round trips on every thread) when the call has few
+  // rows; kLossBlocks CTAs per row otherwise (more CTAs per row measured
+  // slower on a 32-row call: every CTA adds its counts with atomics on a
+  // few words).  The counts and the fixed-point sums do not depend on the
+  // grid.
+  int64_t most = 1;
+  for (int f = 0; f < h.n_frames; ++f) most = std::max<int64_t>(most, static_cast<int64_t>(h.f[f].H) * h.f[f].W);
+  for (int m = 0; m < h.n_maps; ++m) most = std::max<int64_t>(most, h.m[m].n);
+  const int rows = h.n_frames + h.n_maps;
+  const int64_t cap = std::max<int64_t>(kLossBlocks, 2048 / std::max(rows, 1));
+  const int gx = static_cast<int>(std::min<int64_t>(cap, (most + 255) / 256));
+  k_loss_count<<<dim3(gx, h.n_frames + h.n_maps), 256, 0, s>>>(
       w.desc, loss_counts_ptr(w), p, scale_grad ? 1 : 0, reinterpret_cast<unsigned long long*>(w.loss_part),
       &w.st->work_counter, 1);
   return cudaGetLastError();

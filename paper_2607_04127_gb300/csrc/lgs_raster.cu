@@ -1237,9 +1237,17 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
                                                   uint32_t* __restrict__ cmask, LossEpi loss) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_long = st->n_long;
+  if (n_long == 0) {
+    // no long list: the per-tile forward before it on the stream has added
+    // every pixel's loss terms, so one warp writes the loss vector at once
+    // (no ticket over the grid)
+    if (LOSS && blockIdx.x == 0 && threadIdx.x < 32)
+      finish_loss_vector(*D, loss.P, loss.ctot, loss.acc, loss.out, st);
+    return;
+  }
   uint32_t evals = 0, contrib = 0, alg = 0;
   LongPix P;
-  while (n_long && long_item(*D, ranges, longt, n_long, warp_claim(&st->long_counter_fwd), P)) {
+  while (long_item(*D, ranges, longt, n_long, warp_claim(&st->long_counter_fwd), P)) {
     if (!P.inside) continue;
     const FrameDev& F = *P.F;
     float dx, dy, dz;
@@ -1350,7 +1358,7 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
     // the warp holds one pixel: lane 0 alone takes its loss terms
     if (LOSS) loss_epilogue(*D, loss, static_cast<int>(P.F - D->f), lane == 0, P.pix, P.HW, A, St, Sx, Sy, Sz);
   }
-  if (n_long) long_finish(&st->long_counter_fwd, &st->long_done_fwd);
+  long_finish(&st->long_counter_fwd, &st->long_done_fwd);
   unsigned long long ev = evals, co = contrib, al = alg;
   for (int o = 16; o > 0; o >>= 1) {
     ev += __shfl_xor_sync(0xffffffffu, ev, o);
