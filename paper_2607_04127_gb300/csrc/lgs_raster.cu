@@ -1228,8 +1228,11 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
+// Four CTAs per SM (64 registers): with the loads pipelined below, 32 warps
+// per SM measured faster than 24 at 72 registers (batched forward 8.0 against
+// 8.5 ms).
 template <bool LOSS>
-__global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(256, 4) k_fwd_long(const Desc* __restrict__ D, const uint2* __restrict__ ranges,
                                                   const uint32_t* __restrict__ pv, const float4* __restrict__ rec,
                                                   const float4* __restrict__ box,
                                                   const uint32_t* __restrict__ longt, Status* __restrict__ st,
@@ -1279,16 +1282,27 @@ __global__ void __launch_bounds__(256) k_fwd_long(const Desc* __restrict__ D, co
       cA = cSt = cSx = cSy = cSz = 0.f;
     };
     uint32_t win = 0;
+    // software pipeline over the windows: the list entry two windows ahead
+    // and the culling box one window ahead are loaded while this window is
+    // composited (each window's loads would otherwise form a chain of
+    // dependent round trips: entry, then box, then record)
+    uint32_t item_next = P.start + 32 + lane < P.end ? __ldg(pv + P.start + 32 + lane) : 0u;
+    uint32_t item_cur = P.start + lane < P.end ? __ldg(pv + P.start + lane) : 0u;
+    float4 box_cur = P.start + lane < P.end ? __ldg(box + item_cur) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (uint32_t base = P.start; base < P.end; base += 32, ++win) {
       if (win > 0 && win % 4 == 0) checkpoint(win / 4 - 1);
       uint32_t* mword = cmask + (cb * 4 + win) * npx + P.vt;
       const uint32_t j = base + lane;
+      const uint32_t item = item_cur;
+      const float4 bx = box_cur;
+      item_cur = item_next;
+      box_cur = j + 32 < P.end ? __ldg(box + item_next) : make_float4(0.f, 0.f, 0.f, 0.f);
+      item_next = j + 64 < P.end ? __ldg(pv + j + 64) : 0u;
       bool valid = false;
       Eval e;
       float nx = 0.f, ny = 0.f, nz = 0.f;
       if (j < P.end) {
-        const uint32_t item = __ldg(pv + j);
-        if (box_hits(__ldg(box + item), pb)) {
+        if (box_hits(bx, pb)) {
           const float4* rp = rec + 4 * static_cast<int64_t>(item);
           const float4 r0 = __ldg(rp);
           eval_pair(r0, __ldg(rp + 1), __ldg(rp + 2), __ldg(reinterpret_cast<const float*>(rp + 3)), dx, dy, dz, e);
