@@ -758,6 +758,13 @@ __global__ void __maxnreg__(72)
       o[5 * npx] = cSz;
       cA = cSt = cSx = cSy = cSz = 0.f;
     };
+    // software pipeline over the windows: the list entry two windows ahead
+    // and the culling box one window ahead are loaded while this window is
+    // composited (entry, box and record would otherwise be a chain of
+    // dependent round trips per window)
+    uint32_t item_nx = tc.start + 32 + lane < tc.end ? __ldg(pv + tc.start + 32 + lane) : 0u;
+    uint32_t item_cur = tc.start + lane < tc.end ? __ldg(pv + tc.start + lane) : 0u;
+    float4 box_cur = tc.start + lane < tc.end ? __ldg(box + item_cur) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (uint32_t base = tc.start; base < tc.end; base += 32) {
       if (base - tc.start >= (chunk + 1) * kChunk) {
         checkpoint();
@@ -768,12 +775,13 @@ __global__ void __maxnreg__(72)
       // chunked backward (every window the warp walks gets its word)
       uint32_t* mword = cmask + (static_cast<int64_t>(cbase[tile]) * 4 + (base - tc.start) / 32) * npx + threadIdx.x;
       const uint32_t j = base + lane;
-      uint32_t item = 0;
+      const uint32_t item = item_cur;
+      const float4 bx = box_cur;
+      item_cur = item_nx;
+      box_cur = j + 32 < tc.end ? __ldg(box + item_nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+      item_nx = j + 64 < tc.end ? __ldg(pv + j + 64) : 0u;
       bool hit = false;
-      if (j < tc.end) {
-        item = __ldg(pv + j);
-        hit = box_hits(__ldg(box + item), wb);
-      }
+      if (j < tc.end) hit = box_hits(bx, wb);
       uint32_t m = __ballot_sync(0xffffffffu, hit);
       if (!m) {
         *mword = 0u;
