@@ -48,6 +48,8 @@ cudaError_t launch_write_desc(const Desc& h, Desc* d, Status*, cudaStream_t s) {
 __global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, Status* __restrict__ st,
                          uint32_t* __restrict__ loss_acc, uint32_t loss_words, uint32_t* __restrict__ tcount,
                          uint32_t n_tiles) {
+  pdl_wait();               // (launched after a kernel of this chain: wait for it)
+  pdl_launch_dependents();  // the next kernel may be dispatched now
   const FrameDev& F = D->f[blockIdx.x];
   // the tile counts start at zero (k_preprocess adds into them)
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_tiles; i += gridDim.x * blockDim.x) tcount[i] = 0u;
@@ -63,6 +65,7 @@ __global__ void k_tables(const Desc* __restrict__ D, float* __restrict__ tab, St
     st->check = 0;
     st->work_counter = 0;
     st->work_counter2 = 0;
+    for (int c = 0; c < kBwdClasses; ++c) st->bq_count[c] = 0;
     st->evals_fwd = 0;
     st->evals_bwd = 0;
     st->contrib_fwd = 0;
@@ -261,6 +264,8 @@ __global__ void __launch_bounds__(256) k_preprocess(const Desc* __restrict__ D, 
                                                      uint32_t* __restrict__ key, uint32_t* __restrict__ cnt,
                                                      uint2* __restrict__ tset, uint32_t* __restrict__ tcount,
                                                      Status* __restrict__ st) {
+  pdl_wait();               // (launched after a kernel of this chain: wait for it)
+  pdl_launch_dependents();  // the next kernel may be dispatched now
   __shared__ uint32_t s_cnt[kAggTiles];
   const int64_t item = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool live = item < D->n_items;
@@ -357,6 +362,8 @@ __global__ void __launch_bounds__(kScanCta) k_tile_scan(uint32_t* __restrict__ t
                                                           int64_t cap, uint32_t* __restrict__ order,
                                                           uint32_t* __restrict__ longt, uint32_t* __restrict__ cbase,
                                                           uint32_t* __restrict__ midl) {
+  pdl_wait();               // (launched after a kernel of this chain: wait for it)
+  pdl_launch_dependents();  // the next kernel may be dispatched now
   __shared__ unsigned long long s_w[32];
   __shared__ uint32_t s_wc[32];
   __shared__ unsigned long long s_carry, s_tot;
@@ -504,6 +511,8 @@ __global__ void __launch_bounds__(256) k_emit(const Desc* __restrict__ D, const 
                                                const uint2* __restrict__ tset, uint32_t* __restrict__ tcur,
                                                const uint2* __restrict__ ranges, Status* __restrict__ st,
                                                unsigned long long* __restrict__ pkey) {
+  pdl_wait();               // (launched after a kernel of this chain: wait for it)
+  pdl_launch_dependents();  // the next kernel may be dispatched now
   __shared__ uint32_t s_cnt[kAggTiles], s_base[kAggTiles];
   if (st->overflow) return;
   const int64_t item = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -898,10 +907,17 @@ cudaError_t launch_bin(const Layout& L, const WsPtrs& w, int n_frames, int64_t n
                                     static_cast<uint32_t>(loss_part_bytes() / 4), w.tcur, n_tiles);
   const int64_t ni = n_items > 0 ? n_items : 1;
   const unsigned gi = static_cast<unsigned>((ni + 255) / 256);
-  k_preprocess<<<gi, 256, 0, s>>>(w.desc, w.tables, w.rec, w.box, w.key, w.cnt, w.tset, w.tcur, w.st);
-  k_tile_scan<<<1, kScanCta, 0, s>>>(w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work, w.longt, w.cbase,
-                                     w.midl);
-  k_emit<<<gi, 256, 0, s>>>(w.desc, w.tables, w.key, w.cnt, w.tset, w.tcur, w.ranges, w.st, w.pkey);
+  // each of the next three follows a kernel of this chain: dispatched while
+  // its predecessor runs, it waits for it in its first instruction
+  cudaError_t e0 = launch_dep(k_preprocess, dim3(gi), dim3(256), 0, s, w.desc, w.tables, w.rec, w.box, w.key, w.cnt,
+                              w.tset, w.tcur, w.st);
+  if (e0 == cudaSuccess)
+    e0 = launch_dep(k_tile_scan, dim3(1), dim3(kScanCta), 0, s, w.tcur, n_tiles, w.ranges, w.st, L.pairs_cap, w.work,
+                    w.longt, w.cbase, w.midl);
+  if (e0 == cudaSuccess)
+    e0 = launch_dep(k_emit, dim3(gi), dim3(256), 0, s, w.desc, w.tables, w.key, w.cnt, w.tset, w.tcur, w.ranges, w.st,
+                    w.pkey);
+  if (e0 != cudaSuccess) return e0;
   if (n_tiles > 0) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);

@@ -10,6 +10,36 @@
 namespace lgs {
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched with launch_dep may be
+// dispatched while the previous kernel on its stream still runs: its CTAs
+// become resident and wait in pdl_wait() (griddepcontrol.wait: until that
+// kernel has completed and its memory is visible) before touching anything
+// it wrote.  A kernel calls pdl_launch_dependents() at its start so that
+// its successor's dispatch overlaps its own run; the successor is launched
+// only once every CTA of the kernel has started, so waiting CTAs never hold
+// the slots the kernel still needs.  Both are no-ops for a kernel launched
+// without the attribute.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // Descriptors (written once per call into the workspace by k_write_desc)
 // ---------------------------------------------------------------------------
 struct FrameDev {
@@ -68,7 +98,7 @@ struct Status {
   unsigned int check;                 // a checked-build bounds check failed
   unsigned int work_counter;          // persistent scheduler: next work item
   unsigned int work_counter2;
-  unsigned int bq_count[kBwdClasses]; // backward items queued per class (follows work_counter2: one memset)
+  unsigned int bq_count[kBwdClasses]; // backward items queued per class (zero between backwards)
   unsigned int n_long;                // tiles whose list is longer than kLongList
   unsigned int long_counter_fwd;      // work counters of the long-list kernels (self-resetting)
   unsigned int long_counter_bwd;

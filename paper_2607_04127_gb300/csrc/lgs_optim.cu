@@ -32,7 +32,16 @@ __device__ __forceinline__ int map_of_surfel(const Desc& D, int64_t s) {
   return lo;
 }
 
-__global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__ D, float* __restrict__ g13) {
+__global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__ D, float* __restrict__ g13,
+                                                        Status* __restrict__ st) {
+  pdl_wait();               // (launched after a kernel of this chain: wait for it)
+  pdl_launch_dependents();  // the next kernel may be dispatched now
+  // the backward before it is done: its claim counter and work-queue sizes
+  // start the next chunked backward at zero
+  if (blockIdx.x == 0 && threadIdx.x <= static_cast<unsigned>(kBwdClasses)) {
+    if (threadIdx.x == 0) st->work_counter2 = 0u;
+    else st->bq_count[threadIdx.x - 1] = 0u;
+  }
   const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= D->n_surf) return;
   const int m = map_of_surfel(*D, s);
@@ -142,8 +151,9 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const Desc* __restrict__
 
 cudaError_t launch_preprocess_bwd(const Layout&, const WsPtrs& w, const Desc& h, cudaStream_t s) {
   const int64_t n = h.n_surf > 0 ? h.n_surf : 1;
-  k_preprocess_bwd<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(w.desc, w.g13);
-  return cudaGetLastError();
+  // follows the backward's last kernel on the stream: dispatched while it runs
+  return launch_dep(k_preprocess_bwd, dim3(static_cast<unsigned>((n + 255) / 256)), dim3(256), 0, s, w.desc, w.g13,
+                    w.st);
 }
 
 // ---------------------------------------------------------------------------
@@ -187,6 +197,8 @@ __global__ void __launch_bounds__(256) k_loss_count(const Desc* __restrict__ D, 
                                                     lgs_loss_params P, int write_grad,
                                                     unsigned long long* __restrict__ acc,
                                                     unsigned int* __restrict__ clear, int n_clear) {
+  pdl_wait();               // (launched after a kernel of this chain: wait for it)
+  pdl_launch_dependents();  // the next kernel may be dispatched now
   if (blockIdx.x == 0 && blockIdx.y == 0 && static_cast<int>(threadIdx.x) < n_clear) clear[threadIdx.x] = 0u;
   if (blockIdx.y >= static_cast<unsigned>(D->n_frames)) {
     __shared__ long long s_ll[8];

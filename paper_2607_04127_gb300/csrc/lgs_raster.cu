@@ -728,6 +728,8 @@ __global__ void __maxnreg__(72)
             const float4* __restrict__ rec, const float4* __restrict__ box, const uint32_t* __restrict__ order,
             Status* __restrict__ st, int persistent, const uint32_t* __restrict__ cbase, float* __restrict__ ckpt,
             uint32_t* __restrict__ cmask, uint32_t* __restrict__ bwm, LossEpi loss) {
+  pdl_wait();               // (launched after a kernel of this chain: wait for it)
+  pdl_launch_dependents();  // the next kernel may be dispatched now
   __shared__ WarpRecs s_w[kMaxTileThreads / 32];
   const int lane = threadIdx.x & 31;
   WarpRecs& sw = s_w[threadIdx.x >> 5];
@@ -1010,6 +1012,8 @@ __global__ void __launch_bounds__(kBwdChunkCta)
             const uint32_t* __restrict__ cbase, const float* __restrict__ ckpt, const uint32_t* __restrict__ cmask,
             const float* __restrict__ csuf, const uint2* __restrict__ bq, uint32_t bq_cap0, uint32_t bq_capk,
             Status* __restrict__ st) {
+  pdl_wait();               // (launched after a kernel of this chain: wait for it)
+  pdl_launch_dependents();  // the next kernel may be dispatched now
   __shared__ WarpRecs s_w[kBwdChunkCta / 32];
   __shared__ uint32_t s_item[kBwdChunkCta / 32][32];
   const int lane = threadIdx.x & 31;
@@ -1145,7 +1149,8 @@ __global__ void __launch_bounds__(kBwdChunkCta)
       } while (m);
     }
   }
-  // (no statistics counters: the backward's contributions are the forward's
+  // (the claim counter and the queue sizes are zeroed for the next backward
+  // by k_preprocess_bwd, which follows on the stream; no statistics counters: the backward's contributions are the forward's
   // composited pairs, counted there)
 }
 
@@ -1246,6 +1251,8 @@ __global__ void __launch_bounds__(256, 4) k_fwd_long(const Desc* __restrict__ D,
                                                   const uint32_t* __restrict__ longt, Status* __restrict__ st,
                                                   const uint32_t* __restrict__ cbase, float* __restrict__ ckpt,
                                                   uint32_t* __restrict__ cmask, LossEpi loss) {
+  pdl_wait();               // (launched after a kernel of this chain: wait for it)
+  pdl_launch_dependents();  // the next kernel may be dispatched now
   const int lane = threadIdx.x & 31;
   const uint32_t n_long = st->n_long;
   if (n_long == 0) {
@@ -1522,6 +1529,8 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const Desc* __restrict__ D, co
                                                   const uint32_t* __restrict__ bwm, uint2* __restrict__ bq,
                                                   uint32_t cap0, uint32_t capk,
                                                   const float* __restrict__ ckpt, float* __restrict__ csuf) {
+  pdl_wait();               // (launched after a kernel of this chain: wait for it)
+  pdl_launch_dependents();  // the next kernel may be dispatched now
   const int lane = threadIdx.x & 31;
   const uint32_t blocks = static_cast<uint32_t>(D->th * D->tw) >> 5;
   const uint32_t n_tiles = D->n_tiles;
@@ -1660,6 +1669,8 @@ static cudaError_t launch_long(bool fwd, const WsPtrs& w, const uint32_t* pv, cu
   else if (fwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_long<false>, 256, 0);
   else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_long, 256, 0);
   const int grid = sms * (per_sm > 0 ? per_sm : 1);
+  // (a plain launch: dispatched during the shared-memory forward, its CTAs
+  // made the 16-map batch's long-list forward 7.9 -> 14.7 ms)
   if (fwd && loss)
     k_fwd_long<true><<<grid, 256, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.longt, w.st, w.cbase, w.ckpt, w.cmask,
                                           *loss);
@@ -1755,10 +1766,8 @@ static cudaError_t launch_raster_bwd_chunks(const WsPtrs& w, const uint32_t* pv,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_c, kBwdChunkCta, 0);
-  k_bwd_c<<<sms * (per_sm > 0 ? per_sm : 1), kBwdChunkCta, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, w.g13,
-                                                                     w.cbase, w.ckpt, w.cmask, w.csuf, w.bq,
-                                                                     w.bq_cap0, w.bq_capk, w.st);
-  return cudaGetLastError();
+  return launch_dep(k_bwd_c, dim3(sms * (per_sm > 0 ? per_sm : 1)), dim3(kBwdChunkCta), 0, s, w.desc, w.ranges, pv,
+                    w.rec, w.box, w.g13, w.cbase, w.ckpt, w.cmask, w.csuf, w.bq, w.bq_cap0, w.bq_capk, w.st);
 }
 
 // The shared-memory forward with the image-loss epilogue (and the long-list
@@ -1768,9 +1777,9 @@ cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_
                                    const lgs_loss_params& p, float* loss_out, cudaStream_t s) {
   LossEpi loss{p, loss_counts_ptr(w), reinterpret_cast<unsigned long long*>(w.loss_part), loss_out};
   const int grid = persistent ? persistent_grid(h.th * h.tw) : static_cast<int>(h.n_tiles);
-  k_fwd_s<true><<<grid, h.th * h.tw, 0, s>>>(w.desc, w.ranges, pv, w.rec, w.box, persistent ? w.work : nullptr, w.st,
-                                             persistent, w.cbase, w.ckpt, w.cmask, w.bwm, loss);
-  cudaError_t e = cudaGetLastError();
+  // (follows k_loss_count on the stream: dispatched while it runs)
+  cudaError_t e = launch_dep(k_fwd_s<true>, dim3(grid), dim3(h.th * h.tw), 0, s, w.desc, w.ranges, pv, w.rec, w.box,
+                             persistent ? w.work : nullptr, w.st, persistent, w.cbase, w.ckpt, w.cmask, w.bwm, loss);
   if (e != cudaSuccess) return e;
   return launch_long(true, w, pv, s, &loss);
 }
@@ -1778,18 +1787,15 @@ cudaError_t launch_raster_fwd_loss(const WsPtrs& w, const Desc& h, const uint32_
 cudaError_t launch_raster_bwd(const Layout&, const WsPtrs& w, const Desc& h, const uint32_t* pv, int batch,
                               int group, int persistent, bool chunked, cudaStream_t s) {
   if (chunked) {
-    // the claim counter and the queue sizes (adjacent words) start at zero;
-    // then the queues and the long lists' suffixes, then the walk
-    static_assert(offsetof(Status, bq_count) == offsetof(Status, work_counter2) + sizeof(unsigned int),
-                  "the backward queue sizes follow the backward's claim counter");
-    cudaError_t e = cudaMemsetAsync(&w.st->work_counter2, 0, sizeof(unsigned int) * (1 + kBwdClasses), s);
-    if (e != cudaSuccess) return e;
+    // the claim counter and the queue sizes are zero here (cleared at
+    // binning and after every backward by k_preprocess_bwd); the queues and
+    // the long lists' suffixes, then the walk
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     k_bwd_prep<<<4 * sms, 256, 0, s>>>(w.desc, w.ranges, w.longt, w.st, w.cbase, w.bwm, w.bq, w.bq_cap0, w.bq_capk,
                                        w.ckpt, w.csuf);
-    e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_raster_bwd_chunks(w, pv, s);
   }
