@@ -124,6 +124,28 @@ def dist_env():
     return rank, world, local
 
 
+def gpu_local_cpus(gpu_id: int):
+    """The CPUs of the GPU's own NUMA node (its PCI device's local_cpulist
+    in sysfs, bus id from nvidia-smi) that this thread may run on; None when
+    unknown.  Pinned host pages are placed on the node of the thread that
+    allocates them, so the end-to-end section allocates and copies from
+    there."""
+    try:
+        r = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i", str(gpu_id)],
+                           capture_output=True, text=True, timeout=30)
+        dom, rest = r.stdout.strip().split(":", 1)
+        with open(f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest.lower()}/local_cpulist") as f:
+            text = f.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return None
+
+
 def replicas_value(local_seconds: float, units_per_rank: float, world: int, device=None):
     """Whole-job throughput of ``world`` independent replicas: every rank
     processed ``units_per_rank`` in ``local_seconds``; the job lasts as long
@@ -907,7 +929,12 @@ def run_ours(args):
     kernels_ms = {g: (ms / n if n else 0.0) for g, (ms, n) in kt.items()}
     roof = street_roofline(pk, kernels_ms, ms_step, work, surf.n, rays, surf.n, rast.tuning)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers, the host side on
+    # the GPU's own NUMA node (restored afterwards)
+    saved_cpus = os.sched_getaffinity(0)
+    local_cpus = gpu_local_cpus(gpu_id)
+    if local_cpus:
+        os.sched_setaffinity(0, local_cpus)
     host = [p.cpu().pin_memory() for p in params]
     host_t = [t.cpu().pin_memory() for t in targets[0]]
     dev_p = [torch.empty_like(p) for p in params]
@@ -934,6 +961,7 @@ def run_ours(args):
         out_l.copy_(L[:1], non_blocking=True)
         ee[k][1].record(stream)
     torch.cuda.synchronize()
+    os.sched_setaffinity(0, saved_cpus)
     e2e_s, e2e_value = replicas_value(sum(e[0].elapsed_time(e[1]) for e in ee) / 1e3, e2e_steps * rays, world, dev)
     rast.close()
 
@@ -963,7 +991,8 @@ def run_ours(args):
                   alg_evals_bwd=work["alg_b"], culled_evals_fwd=c_last["evals_fwd"],
                   composited_fwd=work["contrib"]),
         roofline=roof,
-        e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+        e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                 host_cpus=f"GPU-local NUMA node, {len(local_cpus)} CPUs" if local_cpus else "not bound"),
         gpu_launches=int(round(launches_per_step * args.steps)),
         clocks=clocks, wall_s=t_wall,
     )
