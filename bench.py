@@ -135,15 +135,20 @@ def gpu_local_cpus(gpu_id: int):
                            capture_output=True, text=True, timeout=30)
         dom, rest = r.stdout.strip().split(":", 1)
         with open(f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest.lower()}/local_cpulist") as f:
-            text = f.read().strip()
-        cpus = set()
-        for part in text.split(","):
-            a, _, b = part.partition("-")
-            cpus.update(range(int(a), int(b or a) + 1))
-        cpus &= os.sched_getaffinity(0)
+            cpus = parse_cpulist(f.read()) & os.sched_getaffinity(0)
         return cpus or None
     except (OSError, ValueError, subprocess.SubprocessError):
         return None
+
+
+def parse_cpulist(text: str) -> set:
+    """The CPUs of a kernel CPU list ("0-3,8,10-11")."""
+    cpus = set()
+    for part in text.strip().split(","):
+        if part:
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+    return cpus
 
 
 def replicas_value(local_seconds: float, units_per_rank: float, world: int, device=None):
